@@ -1,0 +1,224 @@
+"""Pins for the oracle's LRC-Katz parts: partition (Section 3.2, Steps
+2-3), Lemma 1, the exact inverse of Eq. 13, Theorem 1, the Lanczos step of
+Algorithm 1, PCG of Algorithm 2, and the warm-start network's gradients."""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.sparse.csgraph import connected_components
+
+import oracle as O
+from paper_1912_06525_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def W_of(g):
+    return O.adjacency(g.n, g.rowptr, g.col, g.val)
+
+
+def random_partition(W, rng, sep_frac):
+    """Any separator set and any grouping of the remaining components into
+    blocks gives an invertible M11 (Lemma 1 holds for every such split)."""
+    n = W.shape[0]
+    sep = rng.random(n) < sep_frac
+    rest = np.nonzero(~sep)[0]
+    _, lab = connected_components(W[rest][:, rest], directed=False)
+    groups = {}
+    for node, l in zip(rest, lab):
+        groups.setdefault(l, []).append(node)
+    comps = list(groups.values())
+    rng.shuffle(comps)
+    blocks = []  # merge neighbouring components at random into one block
+    for c in comps:
+        if blocks and rng.random() < 0.3:
+            blocks[-1] = blocks[-1] + list(c)
+        else:
+            blocks.append(list(c))
+    blocks = [list(rng.permutation(b)) for b in blocks]
+    perm = np.array([v for b in blocks for v in b] + list(rng.permutation(np.nonzero(sep)[0])),
+                    dtype=np.int64)
+    iperm = np.empty(n, dtype=np.int64)
+    iperm[perm] = np.arange(n)
+    bp = np.concatenate([[0], np.cumsum([len(b) for b in blocks])]).astype(np.int64)
+    return {"perm": perm, "iperm": iperm, "block_ptr": bp, "n1": int(bp[-1]),
+            "n2": n - int(bp[-1])}
+
+
+# ---------------------------------------------------------------- partition
+def test_partition_golden_path7():
+    g = synth.path(7)
+    p = O.partition(g.n, g.rowptr, g.col, n_hubs=0, block_max=3, split=True)
+    want = {}
+    for line in open(os.path.join(GOLDEN, "partition_path7.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, *v = line.split()
+            want[k] = [int(x) for x in v]
+    assert p["perm"].tolist() == want["perm"]
+    assert p["block_ptr"].tolist() == want["block_ptr"]
+    assert p["n1"] == want["n1"][0] and p["n2"] == want["n2"][0]
+
+
+def test_partition_star_hub():
+    g = synth.star(5)
+    p = O.partition(g.n, g.rowptr, g.col, n_hubs=1, block_max=4)
+    assert p["perm"].tolist() == [1, 2, 3, 4, 5, 0]
+    assert p["block_ptr"].tolist() == [0, 1, 2, 3, 4, 5]
+
+
+@pytest.mark.parametrize("split,hubs,bmax", [(True, 0, 16), (True, 10, 32), (False, 20, 8)])
+def test_partition_properties(split, hubs, bmax):
+    g = synth.chung_lu(600, 2.1, 6.0, 120.0, seed=7)
+    W = W_of(g)
+    p = O.partition(g.n, g.rowptr, g.col, hubs, bmax, split)
+    O.check_partition(W, p)
+    sizes = np.diff(p["block_ptr"])
+    if split:
+        assert sizes.max() <= bmax
+    assert (np.diff(sizes) >= 0).all()
+    deg = g.degrees()
+    top = np.lexsort((np.arange(g.n), -deg))[:hubs]
+    assert set(top.tolist()) <= set(p["perm"][p["n1"]:].tolist())
+
+
+# ------------------------------------------------------------------ Lemma 1
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_lemma1_any_partition_gives_direct_solution(seed):
+    rng = np.random.default_rng(seed)
+    g = synth.sbm_bernoulli([25, 25, 30], 0.15, 0.02, seed=seed + 40, weighted=True)
+    W = W_of(g)
+    b = 0.85 / O.lambda_max(W)
+    part = random_partition(W, rng, 0.25)
+    O.check_partition(W, part)
+    idx = O.lrc_build(W, b, part, rank=4, block_max=10 ** 9)
+    Q = [0, 26, 79]
+    B = b * W[:, Q].toarray()
+    res = O.lrc_query(idx, B, tol=1e-14)
+    Kd = O.katz_direct(W, b, Q)
+    assert O.error_inf_rel(res["K"], Kd).max() < 1e-11
+    # Eq. 7: F equals B2 - M12^T M11^{-1} B1 written out densely
+    n1 = part["n1"]
+    Mp = (np.eye(g.n) - b * W.toarray())[part["perm"]][:, part["perm"]]
+    Bp = B[part["perm"]]
+    F = Bp[n1:] - Mp[:n1, n1:].T @ np.linalg.solve(Mp[:n1, :n1], Bp[:n1])
+    np.testing.assert_allclose(res["F"], F, rtol=1e-10, atol=1e-15)
+
+
+def test_lrc_with_project_partition_and_large_blocks():
+    g = synth.chung_lu(400, 2.1, 5.0, 80.0, seed=3)
+    W = W_of(g)
+    b = 0.9 / O.lambda_max(W)
+    Q = [1, 50, 399]
+    for split, bmax in [(True, 8), (False, 8)]:
+        res, idx = O.katz_lrc(W, b, Q, n_hubs=8, block_max=bmax, rank=6, split=split)
+        assert O.error_inf_rel(res["K"], O.katz_direct(W, b, Q)).max() < 1e-11
+
+
+# ----------------------------------------- Eq. 13, Theorem 1 and Lanczos
+def _idx(seed=0, rank=5, hubs=6):
+    g = synth.chung_lu(300, 2.1, 6.0, 60.0, seed=seed)
+    W = W_of(g)
+    b = 0.9 / O.lambda_max(W)
+    part = O.partition(g.n, g.rowptr, g.col, hubs, 6, True)
+    return W, b, O.lrc_build(W, b, part, rank, block_max=6)
+
+
+def test_full_rank_correction_is_exact_inverse():
+    """With all n2 eigenpairs, S~^{-1} = S^{-1} (Eq. 13) and PCG converges
+    in one iteration."""
+    W, b, idx0 = _idx(rank=10 ** 6)
+    n2 = idx0["n2"]
+    # Lanczos stops on an invariant subspace; eigenvalue 0 of R (separator
+    # nodes without M11 neighbours) contributes D = 0, so every nonzero
+    # sigma must be present.
+    sig_all = np.sort(np.linalg.eigvalsh(idx0["R"]))[::-1]
+    nz = sig_all[sig_all > 1e-10]
+    np.testing.assert_allclose(idx0["sigma"][: len(nz)], nz, rtol=1e-9)
+    St = idx0["M22inv"] + idx0["Wr"] @ np.diag(idx0["D"]) @ idx0["Wr"].T
+    np.testing.assert_allclose(St @ idx0["S"], np.eye(n2), atol=1e-9)
+    B = b * W[:, [3, 9]].toarray()
+    res = O.lrc_query(idx0, B, tol=1e-9)
+    assert (res["iters"] <= 1).all() and res["iters"].max() == 1
+
+
+def test_rank_zero_is_plain_M22_preconditioner():
+    W, b, idx = _idx(rank=0)
+    assert idx["Wr"].shape[1] == 0
+    B = b * W[:, [4]].toarray()
+    res = O.lrc_query(idx, B, tol=1e-13)
+    assert O.error_inf_rel(res["K"], O.katz_direct(W, b, [4])).max() < 1e-11
+
+
+@pytest.mark.parametrize("rank", [1, 4, 9])
+def test_theorem1_spectrum(rank):
+    """eig(S S~^{-1}) = {1 (rank times)} U {1 - sigma_i, i > rank}
+    with sigma the eigenvalues of R (Theorem 1)."""
+    W, b, idx = _idx(seed=1, rank=rank)
+    sig_all = np.sort(np.linalg.eigvalsh(idx["R"]))[::-1]
+    want = np.sort(np.concatenate([np.ones(rank), 1 - sig_all[rank:]]))
+    got = O.schur_precond_spectrum(idx)
+    np.testing.assert_allclose(got, want, atol=1e-9)
+
+
+def test_ritz_values_match_dense_eigenvalues_and_bounds():
+    W, b, idx = _idx(seed=2, rank=8)
+    sig_all = np.sort(np.linalg.eigvalsh(idx["R"]))[::-1]
+    np.testing.assert_allclose(idx["sigma"], sig_all[:8], rtol=1e-9, atol=1e-12)
+    assert (sig_all >= -1e-12).all() and (sig_all < 1).all()
+    # W_r^T M22 W_r = I (W_r = L^{-T} U_r with orthonormal U_r)
+    G = idx["Wr"].T @ idx["M22"] @ idx["Wr"]
+    np.testing.assert_allclose(G, np.eye(8), atol=1e-9)
+    # S = L (I - R) L^T (the identity before Eq. 11)
+    L = idx["L"]
+    np.testing.assert_allclose(L @ (np.eye(idx["n2"]) - idx["R"]) @ L.T, idx["S"], atol=1e-10)
+
+
+def test_pcg_fewer_iterations_with_more_rank():
+    W, b, i1 = _idx(seed=3, rank=1)
+    _, _, i8 = _idx(seed=3, rank=12)
+    B = b * W[:, [0, 5, 8, 13]].toarray()
+    it1 = O.lrc_query(i1, B, tol=1e-10)["iters"]
+    it8 = O.lrc_query(i8, B, tol=1e-10)["iters"]
+    assert it8.sum() <= it1.sum()
+
+
+# ------------------------------------------------------------ warm-start MLP
+def test_gelu_exact_values():
+    from math import erf, sqrt
+    for x in [-3.0, -0.5, 0.0, 0.7, 2.5]:
+        assert O.gelu(np.array(x)) == pytest.approx(0.5 * x * (1 + erf(x / sqrt(2))), rel=1e-14, abs=1e-300)
+
+
+def test_mlp_gradients_finite_differences():
+    rng = np.random.default_rng(0)
+    X = rng.normal(size=(7, 5))
+    T = rng.normal(size=(7, 3))
+    W1 = rng.normal(size=(6, 5)) * 0.5
+    b1 = rng.normal(size=6) * 0.1
+    W2 = rng.normal(size=(3, 6)) * 0.5
+    b2 = rng.normal(size=3) * 0.1
+    params = [W1, b1, W2, b2]
+    loss, grads = O.mlp_loss_grad(X, T, *params)
+    h = 1e-6
+    for p, g in zip(params, grads):
+        it = np.nditer(p, flags=["multi_index"])
+        for _ in it:
+            i = it.multi_index
+            old = p[i]
+            p[i] = old + h
+            lp, _ = O.mlp_loss_grad(X, T, *params)
+            p[i] = old - h
+            lm, _ = O.mlp_loss_grad(X, T, *params)
+            p[i] = old
+            assert g[i] == pytest.approx((lp - lm) / (2 * h), rel=1e-6, abs=1e-8)
+
+
+def test_adamw_first_step_closed_form():
+    """From zero moments, bias correction makes the first step
+    -lr * g/(|g|+eps) - lr*wd*p."""
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -0.01, 0.0])
+    p1, m, v = O.adamw_step(p, g, np.zeros(3), np.zeros(3), 1, lr=0.1, wd=0.01)
+    want = p - 0.1 * (g / (np.abs(g) + 1e-8) + 0.01 * p)
+    np.testing.assert_allclose(p1, want, rtol=1e-12)
