@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark: Katz queries/s at 1e-6 relative error on the n=4M modular graph.
+
+One step = one batch of b=1,024 uniformly drawn query nodes answered by
+LRC-Katz (``katz_query_batch``: RHS build, M11 solves, couplings, PCG on the
+Schur complement with the rank-128 low-rank preconditioner, back-solve,
+FP64 iterative refinement to the 1e-6 infinity-norm error bound) followed
+by the top-20 link-prediction candidates of every query (``linkpred_topk``).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Katz queries/sec at 1e-6 rel. error (n=4M); SpMM % of HBM roofline vs plain CG"
+UNIT = "queries/s"
+
+# ncu DRAM traffic per launch of the dominant kernel, keyed by the source hash
+# of the kernel file it was measured on (null once the kernel changes).
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
+    ap.add_argument("--c", type=float, default=0.9, help="beta = c / lambda_max")
+    ap.add_argument("--method", default="lrc", choices=["lrc", "cg"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cg", action="store_true")
+    return ap.parse_args()
+
+
+def workload_desc(g, b, c, rank, scale):
+    return {
+        "workload": (f"modular SBM n={g.n:,} (512 lognormal communities, degree 20, 5% inter, "
+                     f"2,000 hubs x ~5,000 edges), BF16 values, b={b} queries, r={rank}, "
+                     f"beta={c}/lambda_max, tol 1e-6 (inf-norm error bound)"),
+        "n": g.n, "nnz": g.nnz, "global_batch": b, "rank": rank, "c": c, "scale": scale,
+        "l2_flush": "inputs larger than L2 (graph 0.6 GB, FP32 n x b block 16 GB)",
+    }
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev), "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- helpers
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("kernels_vec.cu", "kernels.h", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1912_06525_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def oracle_sample(g, beta, c, q_sample, tol):
+    """FP64 oracle CG (as it stands) on a few query columns; the stopping
+    rule is set so the oracle meets the same error bound as the GPU."""
+    import oracle
+    W = oracle.adjacency(g.n, g.rowptr, g.col, g.val)
+    B = beta * W[:, q_sample].toarray()
+    ratio = (np.abs(B).max(axis=0) / np.sqrt((B * B).sum(axis=0))).min()
+    rtol = tol * (1 - c) * ratio
+    t = time.perf_counter()
+    K, it = oracle.katz_cg(W, beta, q_sample, rtol=rtol, B=B)
+    dt = time.perf_counter() - t
+    return K, dt, it, rtol
+
+
+# ---------------------------------------------------------------- reference
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_1912_06525_gb300 import synth
+    import oracle
+    g, q, c, r = synth.workload(3, args.scale)
+    c = args.c
+    W = oracle.adjacency(g.n, g.rowptr, g.col, g.val)
+    lam = oracle.lambda_max(W)
+    beta = c / lam
+    times = []
+    for s in range(args.warmup + args.steps):
+        qs = q[s % len(q): s % len(q) + 1]
+        _, dt, it, rtol = oracle_sample(g, beta, c, qs, 1e-6)
+        if s >= args.warmup:
+            times.append(dt)
+    ms = 1000 * float(np.mean(times))
+    value = 1000.0 / ms
+    cfg = workload_desc(g, len(q), c, r, args.scale)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": cfg,
+           "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
+                            "sample": "1 query of the batch per step, FP64 CG (SciPy CSR) to "
+                                      "the same 1e-6 error bound"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- ours
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    import __graft_entry__
+    from paper_1912_06525_gb300 import katz, synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    g, q, c, rank_r = synth.workload(3, args.scale)
+    c = args.c
+    b = len(q)
+    if world > 1:  # replicas: each rank answers its own batch
+        q = synth.queries(g.n, b, seed=synth.BASE_SEED + 300 + rank)
+    t0 = time.perf_counter()
+    lam = katz.katz_lambda_max(g, steps=96)
+    beta = c / lam
+    n_hubs = int(g.meta["hubs"].shape[0])
+    idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_BF16, rank=rank_r,
+                                n_hubs=n_hubs, block_max=64, split=False)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    info = idx.info()
+
+    qd = torch.from_numpy(q).to(dev)
+    K = torch.empty((g.n, b), dtype=torch.float32, device=dev)
+    ids = torch.empty((b, 20), dtype=torch.int32, device=dev)
+    sc = torch.empty((b, 20), dtype=torch.float64, device=dev)
+    qfn = katz.katz_query_batch if args.method == "lrc" else katz.cg_query_batch
+    last = {}
+
+    def step(qq, KK, ii, ss):
+        st, it, rel = qfn(idx, qq, KK, out_dtype=katz.KATZ_F32, tol=1e-6)
+        katz.linkpred_topk(idx, qq, KK, katz.KATZ_F32, 20, ii, ss)
+        last.update(st=st, it=it, rel=rel)
+
+    for _ in range(args.warmup):
+        step(qd, K, ids, sc)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local if world == 1 else local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = katz.katz_launch_count()
+    katz.katz_profile_enable(True)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(qd, K, ids, sc)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = katz.katz_launch_count() - l0
+    prof = {t: katz.katz_profile_read(t) for t in
+            ("spmm_f32", "spmm_f64", "block_solve_f32", "gemm_f32")}
+    katz.katz_profile_enable(False)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(world, ms)
+    value = world * b / (ms / 1000.0)
+    lrc_stats = dict(last["st"])
+    lrc_iters = float(np.mean(last["it"]))
+
+    # ---- plain CG on the same batch (the comparison method)
+    cg = None
+    if not args.no_cg:
+        katz.katz_profile_enable(True)
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        st_cg, it_cg, rel_cg = katz.cg_query_batch(idx, qd, K, out_dtype=katz.KATZ_F32, tol=1e-6)
+        torch.cuda.synchronize()
+        cg_ms = 1000 * (time.perf_counter() - c0)
+        pc = katz.katz_profile_read("spmm_f32")
+        katz.katz_profile_enable(False)
+        hbm, _ = peaks()
+        cg = {"queries_per_s": b / (cg_ms / 1000), "ms_per_batch": cg_ms,
+              "mean_iters": float(np.mean(it_cg)), "refine_steps": st_cg["refine_steps"],
+              "max_rel_res": st_cg["max_rel_res"],
+              "spmm_f32_gbs": pc["bytes"] / (pc["ms"] / 1e3) / 1e9 if pc["ms"] else None,
+              "spmm_f32_frac": (pc["bytes"] / (pc["ms"] / 1e3) / 1e9) / hbm if pc["ms"] else None}
+        # restore the LRC answer for the parity sample below
+        step(qd, K, ids, sc)
+
+    # ---- end to end through the C-ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        qh = torch.from_numpy(q).pin_memory()
+        Kh = torch.empty((g.n, b), dtype=torch.float32).pin_memory()
+        idh = torch.empty((b, 20), dtype=torch.int32).pin_memory()
+        sch = torch.empty((b, 20), dtype=torch.float64).pin_memory()
+        n_e2e = max(1, min(args.steps, 3))
+        step(qh, Kh, idh, sch)
+        torch.cuda.synchronize()
+        barrier(world)
+        t = time.perf_counter()
+        for _ in range(n_e2e):
+            step(qh, Kh, idh, sch)
+        torch.cuda.synchronize()
+        barrier(world)
+        e2e_ms = max_over_ranks(world, 1000 * (time.perf_counter() - t) / n_e2e)
+        e2e = {"value": world * b / (e2e_ms / 1000), "unit": UNIT,
+               "h2d_bytes_per_step": int(q.nbytes),
+               "d2h_bytes_per_step": int(g.n * b * 4 + b * 20 * (4 + 8))}
+        del Kh
+
+    # ---- roofline of the dominant kernel
+    hbm, src = peaks()
+    shares = {t: p["ms"] for t, p in prof.items() if p["launches"]}
+    tot = sum(shares.values()) or 1.0
+    dom = max(shares, key=shares.get) if shares else "spmm_f32"
+    p = prof[dom]
+    ach = p["bytes"] / (p["ms"] / 1e3) / 1e9 if p["ms"] else 0.0
+    roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "peak_source": f"{src} (hbm_gbs)",
+            "traffic": NCU_TRAFFIC.get((dom, kernel_hash())),
+            "launches_per_step": p["launches"] / args.steps,
+            "alg_bytes_per_launch": p["bytes"] / max(1, p["launches"]),
+            "share_of_step": p["ms"] / (ms * args.steps)}
+    kernels = {t: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+                   "gbs": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] else None}
+               for t, v in prof.items() if v["launches"]}
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1)
+    cpu = None
+    parity = None
+    if world == 1 and rank == 0 and not args.no_cpu_baseline:
+        ns = 2
+        qs = q[:ns]
+        Kref, dt, it, rtol = oracle_sample(g, beta, c, qs, 1e-6)
+        import oracle
+        Kg = K[:, :ns].double().cpu().numpy()
+        parity = float(oracle.error_inf_rel(Kg, Kref).max())
+        cpu = {"value": ns / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{ns} of the {b} queries, FP64 CG (SciPy CSR, 1 thread) to the same "
+                         f"1e-6 error bound (rtol {rtol:.2e}), {dt:.1f} s"}
+
+    if rank == 0:
+        cfg = workload_desc(g, b, c, rank_r, args.scale)
+        cfg.update({"method": args.method, "parallelism": "replicas" if world > 1 else "single",
+                    "n2": info["n2"], "n1": info["n1"], "index_build_s": build_s,
+                    "lambda_max": lam})
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32 (bf16 matrix values, f64 refinement)", "data": "synthetic",
+               "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": int(launches), "clocks": clk,
+               "lrc": {"mean_iters": lrc_iters, **{k: lrc_stats[k] for k in
+                                                   ("refine_steps", "max_rel_res", "status")}},
+               "cg": cg, "kernels": kernels, "max_err_vs_oracle_sample": parity}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * katz.h - C ABI of the GB300 Katz-query library (libkatz.so).
+ *
+ * The library answers Katz proximity queries on an undirected graph
+ * (Coskun, Baggag, Koyuturk, "Fast Computation of Katz Index for Efficient
+ * Processing of Link Prediction Queries"):
+ *
+ *     K = sum_{l>=1} beta^l W^l = (I - beta W)^{-1} - I        (Eqs. 1-2)
+ *     k_q = column q of K solves  M k_q = beta W e_q,  M = I - beta W  (Eq. 3)
+ *
+ * with the paper's LRC-Katz method (block partition of M, Lemma 1, Eqs.
+ * 4-7, low-rank corrected Schur preconditioner Eq. 14, Algorithms 1-2) and,
+ * as the comparison method, plain conjugate gradients on M.  The paper's
+ * damping factor alpha is written beta here and its adjacency G is W.
+ *
+ * Conventions for every entry point
+ *   - Return value: KATZ_OK (0) or one of the KATZ_E* codes below.  No call
+ *     aborts the process; katz_last_error() gives a one-line reason for the
+ *     last failure on the calling thread.
+ *   - Graph arrays passed to katz_index_build are host pointers; the index
+ *     copies them and owns all device memory it allocates.
+ *   - Vector/matrix arguments marked "host or device" may be either; the
+ *     library inspects the pointer.  Host buffers are staged through device
+ *     memory owned by the index (pinned host memory copies fastest).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All work is issued on it; every call returns only after its
+ *     results are complete and visible to the host and to later work on
+ *     that stream.
+ *   - Dense n x b blocks (one column per query) are NODE-MAJOR: entry
+ *     (node i, query j) is at X[i*ld + j], ld >= b.
+ *   - An index is not thread safe: calls on one index must not overlap.
+ */
+#ifndef KATZ_H
+#define KATZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define KATZ_OK 0
+#define KATZ_EINVAL 1  /* bad argument: malformed/asymmetric CSR, query id out of range, b <= 0 */
+#define KATZ_ENOTSPD 2 /* beta * lambda_max >= 1 detected: M is not positive definite (Section 3.1) */
+#define KATZ_ENOCONV 3 /* an iteration or refinement cap was hit; outputs and stats are still filled */
+#define KATZ_ENOMEM 4  /* a device or host allocation failed */
+#define KATZ_ECUDA 5   /* a CUDA runtime error */
+
+/* ---- element types ---- */
+#define KATZ_UNIT 0 /* values: pattern only, every stored weight is exactly 1 */
+#define KATZ_F64 1
+#define KATZ_F32 2
+#define KATZ_BF16 3
+
+/* ---- query precision modes ---- */
+#define KATZ_PREC_F32 0   /* FP32 solve only (no refinement) */
+#define KATZ_PREC_MIXED 1 /* FP32 inner solves + FP64 residual iterative refinement */
+#define KATZ_PREC_F64 2   /* every vector and reduction in FP64 (reference speed path) */
+
+/* ---- stopping criteria ---- */
+#define KATZ_TOL_RESIDUAL 0  /* stop column j when ||b_j - M k_j||_2 <= tol * ||b_j||_2 */
+#define KATZ_TOL_ERROR_INF 1 /* stop when ||b_j - M k_j||_2 <= tol * (1 - beta*lambda) * ||b_j||_inf,
+                                which guarantees ||k_j - k_j*||_inf <= tol * ||k_j*||_inf for
+                                non-negative weights (||M^{-1}||_2 = 1/(1 - beta*lambda), k* >= b >= 0) */
+
+typedef struct katz_index katz_index; /* opaque; owns all device memory of one graph */
+
+/* Symmetric CSR adjacency W of an undirected graph, HOST pointers.
+ * rowptr[n+1] (int64, rowptr[0] = 0, non-decreasing), col[nnz] (int32 in
+ * [0, n), no self-loops, W symmetric with equal weights both ways), val[nnz]
+ * weights (> 0) or NULL for unit weights. */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int64_t* rowptr;
+  const int32_t* col;
+  const double* val;
+} katz_csr;
+
+typedef struct {
+  int32_t value_dtype;   /* storage of W values on the device: KATZ_UNIT/F64/F32/BF16
+                            (values are rounded to nearest-even; UNIT requires all ones) */
+  int32_t build_lrc;     /* 0: graph only (CG queries); 1: also the LRC-Katz index (Algorithm 1) */
+  int32_t rank;          /* r: number of eigenpairs of R kept (Eq. 14); 0 allowed */
+  int32_t n_hubs;        /* highest-degree nodes forced into the separator */
+  int32_t block_max;     /* largest M11 diagonal block stored as a dense inverse */
+  int32_t split;         /* 1: split components larger than block_max by BFS level sets;
+                            0: keep them whole (their M11 block is solved iteratively) */
+  int32_t lanczos_steps; /* Lanczos steps on R; 0 = max(2r, r+20) */
+  int32_t n2_max;        /* largest separator accepted (dense S and M22^{-1}); 0 = 16384 */
+  uint64_t seed;         /* SplitMix64 seed of the Lanczos start vector */
+} katz_build_opts;
+
+typedef struct {
+  double tol;          /* see tol_kind */
+  int32_t tol_kind;    /* KATZ_TOL_RESIDUAL or KATZ_TOL_ERROR_INF */
+  int32_t precision;   /* KATZ_PREC_* */
+  int32_t max_iter;    /* cap on iterations of each inner CG / PCG solve (0 = 2000) */
+  int32_t max_refine;  /* cap on FP64 refinement steps (0 = 12) */
+  int32_t rhs_width;   /* columns solved together (0 = all b at once) */
+  int32_t warm_start;  /* 1: start LRC from the learned warm start (needs a trained network) */
+} katz_query_opts;
+
+typedef struct {
+  int32_t iters;        /* inner iterations summed over refinement steps (max over columns) */
+  int32_t refine_steps; /* FP64 residual evaluations performed */
+  double max_rel_res;   /* max_j ||b_j - M k_j||_2 / ||b_j||_2 of the returned K (FP64) */
+  double ms[8];         /* phase times: [0] total, [1] rhs, [2] inner solve, [3] residual */
+} katz_stats;
+
+typedef struct {
+  int64_t n, nnz, n1, n2;
+  int32_t n_blocks, n_large_blocks, rank, value_dtype;
+  double beta;
+  double lambda_max_R; /* largest Ritz value sigma_1 of R (0 if rank 0) */
+  int64_t device_bytes;
+} katz_index_info;
+
+/* ---------------------------------------------------------------- graph */
+
+/* Largest eigenvalue lambda_max of the symmetric W (= ||W||_2 for W >= 0),
+ * the bound of Section 3.1 (beta < 1/||W||_2), by FP64 Lanczos on the GPU
+ * (`steps` iterations, 0 = 64).  W is host CSR as above.  *out receives
+ * lambda_max.  Errors: KATZ_EINVAL on a malformed CSR. */
+int katz_lambda_max(const katz_csr* W, int32_t steps, double* out, void* stream);
+
+/* Build the query index for damping `beta` (Algorithm 1, "Preprocess").
+ * Always: validates W (CSR shape, symmetry), uploads it.  With
+ * opts->build_lrc: partitions and reorders M (Section 3.2, Steps 2-3;
+ * project reading: hubs + BFS level-set separators), inverts the M11
+ * diagonal blocks (Step 4: Cholesky, then the inverse), forms M12, M22,
+ * the dense Schur complement S = M22 - M12^T M11^{-1} M12 (Lemma 1),
+ * M22^{-1} (blocked Gauss-Jordan), and the top `rank` eigenpairs of
+ * R = L^{-1} M12^T M11^{-1} M12 L^{-T} (Eqs. 8-11, M22 = L L^T).  R is
+ * similar to M22^{-1} T (T = M12^T M11^{-1} M12), so Lanczos runs on that
+ * operator in the M22 inner product; its Ritz vectors are W_r = L^{-T} U_r
+ * directly and L is never formed.  Stored: W_r D^{1/2}, D = diag(sigma/(1-sigma)).
+ * lambda_max is measured at build; beta*lambda_max >= 1 -> KATZ_ENOTSPD.
+ * On success *out owns the index (free with katz_index_free). */
+int katz_index_build(const katz_csr* W, double beta, const katz_build_opts* opts,
+                     void* stream, katz_index** out);
+
+void katz_index_free(katz_index* idx);
+
+int katz_index_get_info(const katz_index* idx, katz_index_info* info);
+
+/* Copy the partition (host outputs): perm[n] (perm[new] = old node),
+ * block_ptr[n_blocks+1].  Either pointer may be NULL. */
+int katz_index_get_partition(const katz_index* idx, int64_t* perm, int64_t* block_ptr);
+
+/* The partition alone (Section 3.2, Steps 2-3; project reading: the
+ * n_hubs highest-degree nodes plus, when `split`, BFS median-level
+ * separators of components larger than block_max).  Host-only: runs no GPU
+ * code.  perm[n] (perm[new] = old node), block_ptr[n+1] (host, caller
+ * owned; entries after the last block are untouched), *n_blocks and *n1
+ * receive the block count and the number of non-separator nodes. */
+int katz_partition(const katz_csr* W, int32_t n_hubs, int32_t block_max, int32_t split,
+                   int64_t* perm, int64_t* block_ptr, int64_t* n_blocks, int64_t* n1);
+
+/* Copy the kept Ritz values sigma_1 >= ... >= sigma_r of R (host, rank). */
+int katz_index_get_sigma(const katz_index* idx, double* sigma);
+
+/* ---------------------------------------------------------------- queries */
+
+/* Katz vectors of b query nodes by LRC-Katz (Algorithm 2 with Lemma 1):
+ * RHS b_j = beta W e_{q_j} (Eq. 3); F = B2 - M12^T M11^{-1} B1 (Eq. 7); PCG
+ * on S K2 = F preconditioned by S~^{-1} = M22^{-1} + W_r D W_r^T (Eq. 14);
+ * K1 = M11^{-1}(B1 - M12 K2) (Eq. 6); merge and un-permute.  With
+ * KATZ_PREC_MIXED the LRC solve runs in FP32 and FP64 residuals of the full
+ * system drive iterative refinement until opts->tol is met.
+ * q[b]: int32 node ids (host or device).  K_out: n x b node-major, ld = ldk,
+ * element type out_dtype (KATZ_F32 or KATZ_F64), host or device.
+ * stats may be NULL; iters_out[b] / rel_res_out[b] (host, may be NULL)
+ * receive per-column iteration counts and final FP64 relative residuals.
+ * Needs an index built with build_lrc = 1. */
+int katz_query_batch(const katz_index* idx, const int32_t* q, int32_t b,
+                     const katz_query_opts* opts, void* K_out, int32_t out_dtype,
+                     int64_t ldk, katz_stats* stats, int32_t* iters_out,
+                     double* rel_res_out, void* stream);
+
+/* Same contract, solved by plain multi-RHS conjugate gradients on M (the
+ * comparison method of Sections 1 and 4), zero initial guess. */
+int cg_query_batch(const katz_index* idx, const int32_t* q, int32_t b,
+                   const katz_query_opts* opts, void* K_out, int32_t out_dtype,
+                   int64_t ldk, katz_stats* stats, int32_t* iters_out,
+                   double* rel_res_out, void* stream);
+
+/* Katz link prediction (Section 3.3): for each query column j of K (n x b
+ * node-major, ld = ldk, k_dtype KATZ_F32 or KATZ_F64, device or host),
+ * rank every node except q_j and its neighbours by K[:, j] descending, ties
+ * by node id ascending, and write the first `k` ids (int32) and scores
+ * (double) to ids_out[b*k] / scores_out[b*k] (host or device, row j =
+ * query j).  Missing candidates get id -1, score 0.  k <= 64. */
+int linkpred_topk(const katz_index* idx, const int32_t* q, int32_t b,
+                  const void* K, int32_t k_dtype, int64_t ldk, int32_t k,
+                  int32_t* ids_out, double* scores_out, void* stream);
+
+/* Y = M X = X - beta W X for n x b node-major blocks in node order
+ * (X, Y device pointers, ld = b, dtype KATZ_F32 or KATZ_F64).  The sparse
+ * product of Eq. 3, exposed for step-level testing. */
+int katz_apply_M(const katz_index* idx, const void* X, void* Y, int32_t b,
+                 int32_t dtype, void* stream);
+
+/* ---------------------------------------------------------- measurement */
+
+/* Number of kernels this library has launched in this process (all calls). */
+int64_t katz_launch_count(void);
+
+/* Start (on != 0) or stop timing tagged kernel launches with CUDA events on
+ * their launching stream; every call resets the totals.  Tags:
+ * "spmm_f32" / "spmm_f64" (CSR products, Eq. 3 and the couplings),
+ * "block_solve_f32" / "block_solve_f64" (M11 blocks), "gemm_f32" /
+ * "gemm_f64" (dense Schur / preconditioner products). */
+int katz_profile_enable(int32_t on);
+
+/* Totals for one tag since the last katz_profile_enable: launches, summed
+ * device time in ms, and summed algorithmic bytes (CSR arrays + dense
+ * operands read once + outputs written once). */
+int katz_profile_read(const char* tag, int64_t* launches, double* total_ms, double* alg_bytes);
+
+const char* katz_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KATZ_H */

@@ -1,0 +1,343 @@
+// extern "C" boundary of libkatz.so (declared in include/katz.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "index.h"
+#include "kernels_dense.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+template <class F>
+int guarded(F&& f) {
+  try {
+    g_last_error.clear();
+    return f();
+  } catch (const katz::Error& e) {
+    return fail(e.code, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(KATZ_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(KATZ_ECUDA, e.what());
+  }
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Validate a host CSR and copy it into katz::HostCsr.
+katz::HostCsr read_csr(const katz_csr* W) {
+  KATZ_REQUIRE(W && W->rowptr && (W->col || W->nnz == 0), KATZ_EINVAL, "null CSR");
+  KATZ_REQUIRE(W->n >= 0 && W->n < (int64_t(1) << 31), KATZ_EINVAL, "n out of range");
+  KATZ_REQUIRE(W->rowptr[0] == 0 && W->rowptr[W->n] == W->nnz, KATZ_EINVAL,
+               "rowptr must start at 0 and end at nnz");
+  katz::HostCsr h;
+  h.nrows = h.ncols = W->n;
+  h.rowptr.assign(W->rowptr, W->rowptr + W->n + 1);
+  h.col.assign(W->col, W->col + W->nnz);
+  if (W->val) h.val.assign(W->val, W->val + W->nnz);
+  for (int64_t i = 0; i < W->n; ++i) {
+    KATZ_REQUIRE(h.rowptr[i + 1] >= h.rowptr[i], KATZ_EINVAL, "rowptr not monotone");
+    for (int64_t k = h.rowptr[i]; k < h.rowptr[i + 1]; ++k) {
+      const int64_t c = h.col[k];
+      KATZ_REQUIRE(c >= 0 && c < W->n, KATZ_EINVAL, "column index out of range");
+      KATZ_REQUIRE(c != i, KATZ_EINVAL, "self-loop at node " + std::to_string(i));
+      if (W->val) KATZ_REQUIRE(h.val[k] > 0 && std::isfinite(h.val[k]), KATZ_EINVAL,
+                               "weights must be positive and finite");
+    }
+  }
+  // symmetry: the transpose pattern (with values) must equal the original
+  std::vector<int64_t> cnt(W->n + 1, 0);
+  for (int64_t k = 0; k < W->nnz; ++k) cnt[h.col[k] + 1]++;
+  for (int64_t i = 0; i < W->n; ++i) cnt[i + 1] += cnt[i];
+  KATZ_REQUIRE(cnt == h.rowptr, KATZ_EINVAL, "W is not symmetric (row/column counts differ)");
+  std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+  std::vector<int32_t> tcol(W->nnz);
+  std::vector<double> tval(W->val ? W->nnz : 0);
+  for (int64_t i = 0; i < W->n; ++i)
+    for (int64_t k = h.rowptr[i]; k < h.rowptr[i + 1]; ++k) {
+      const int64_t d = pos[h.col[k]]++;
+      tcol[d] = (int32_t)i;
+      if (W->val) tval[d] = h.val[k];
+    }
+  // compare row by row as multisets (sort both)
+  std::vector<std::pair<int32_t, double>> a, b;
+  for (int64_t i = 0; i < W->n; ++i) {
+    a.clear();
+    b.clear();
+    for (int64_t k = h.rowptr[i]; k < h.rowptr[i + 1]; ++k) {
+      a.emplace_back(h.col[k], W->val ? h.val[k] : 1.0);
+      b.emplace_back(tcol[k], W->val ? tval[k] : 1.0);
+    }
+    std::sort(a.begin(), a.end());
+    std::sort(b.begin(), b.end());
+    KATZ_REQUIRE(a == b, KATZ_EINVAL, "W is not symmetric at row " + std::to_string(i));
+    for (size_t t = 1; t < a.size(); ++t)
+      KATZ_REQUIRE(a[t].first != a[t - 1].first, KATZ_EINVAL,
+                   "duplicate entry in row " + std::to_string(i));
+  }
+  return h;
+}
+
+// Device copy of the query ids (validated against n).
+const int32_t* stage_queries(katz_index* idx, const int32_t* q, int32_t b, cudaStream_t s) {
+  KATZ_REQUIRE(q != nullptr && b > 0, KATZ_EINVAL, "empty query list");
+  std::vector<int32_t> h(b);
+  if (is_device_ptr(q)) {
+    KATZ_CUDA(cudaMemcpyAsync(h.data(), q, 4 * size_t(b), cudaMemcpyDeviceToHost, s));
+    KATZ_CUDA(cudaStreamSynchronize(s));
+  } else {
+    std::memcpy(h.data(), q, 4 * size_t(b));
+  }
+  for (int j = 0; j < b; ++j)
+    KATZ_REQUIRE(h[j] >= 0 && h[j] < idx->n, KATZ_EINVAL,
+                 "query id " + std::to_string(h[j]) + " out of range");
+  int32_t* d = idx->ws.get<int32_t>("api.q", b);
+  KATZ_CUDA(cudaMemcpyAsync(d, h.data(), 4 * size_t(b), cudaMemcpyHostToDevice, s));
+  return d;
+}
+
+int do_query(const katz_index* cidx, bool lrc, const int32_t* q, int32_t b,
+             const katz_query_opts* opts, void* K_out, int32_t out_dtype, int64_t ldk,
+             katz_stats* stats, int32_t* iters_out, double* rel_res_out, void* stream) {
+  return guarded([&]() {
+    KATZ_REQUIRE(cidx && opts && K_out, KATZ_EINVAL, "null argument");
+    KATZ_REQUIRE(out_dtype == KATZ_F32 || out_dtype == KATZ_F64, KATZ_EINVAL, "out_dtype");
+    KATZ_REQUIRE(ldk >= b, KATZ_EINVAL, "ldk < b");
+    KATZ_REQUIRE(opts->tol > 0, KATZ_EINVAL, "tol must be positive");
+    katz_index* idx = const_cast<katz_index*>(cidx);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int32_t* qd = stage_queries(idx, q, b, s);
+    katz::QueryOut out;
+    out.dtype = out_dtype;
+    out.ldk = ldk;
+    const bool dev = is_device_ptr(K_out);
+    const size_t es = out_dtype == KATZ_F64 ? 8 : 4;
+    if (dev) {
+      out.K = K_out;
+    } else {
+      out.K = idx->ws.get<uint8_t>("api.K", es * size_t(idx->n) * ldk);
+    }
+    std::vector<int32_t> it;
+    std::vector<double> rr;
+    const int st = katz::run_queries(*idx, lrc, qd, b, *opts, out, stats, it, rr, s);
+    if (!dev && (st == KATZ_OK || st == KATZ_ENOCONV)) {
+      KATZ_CUDA(cudaMemcpyAsync(K_out, out.K, es * size_t(idx->n) * ldk, cudaMemcpyDeviceToHost, s));
+      KATZ_CUDA(cudaStreamSynchronize(s));
+    }
+    if (iters_out) std::memcpy(iters_out, it.data(), 4 * it.size());
+    if (rel_res_out) std::memcpy(rel_res_out, rr.data(), 8 * rr.size());
+    if (st == KATZ_ENOCONV) g_last_error = "iteration or refinement cap reached";
+    if (st == KATZ_ENOTSPD) g_last_error = "CG breakdown: p^T A p <= 0 (M not positive definite)";
+    return st;
+  });
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* katz_last_error(void) { return g_last_error.c_str(); }
+
+int katz_lambda_max(const katz_csr* W, int32_t steps, double* out, void* stream) {
+  return guarded([&]() {
+    KATZ_REQUIRE(out, KATZ_EINVAL, "null output");
+    katz::HostCsr h = read_csr(W);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    katz::GraphPart g;
+    katz::upload_csr(h, h.val.empty() ? KATZ_UNIT : KATZ_F64, g.csr, s);
+    std::vector<int32_t> heavy;
+    for (int64_t i = 0; i < h.nrows; ++i)
+      if (h.rowptr[i + 1] - h.rowptr[i] > katz::kHeavyRowNnz) heavy.push_back((int32_t)i);
+    g.n_heavy = (int64_t)heavy.size();
+    g.heavy.alloc(std::max<size_t>(1, heavy.size()));
+    if (!heavy.empty())
+      KATZ_CUDA(cudaMemcpy(g.heavy.p, heavy.data(), 4 * heavy.size(), cudaMemcpyHostToDevice));
+    katz::Workspace ws;
+    *out = katz::lambda_max_gpu(g, h.nrows, steps > 0 ? steps : 64, ws, s);
+    return KATZ_OK;
+  });
+}
+
+int katz_index_build(const katz_csr* W, double beta, const katz_build_opts* opts, void* stream,
+                     katz_index** out) {
+  return guarded([&]() {
+    KATZ_REQUIRE(out && opts, KATZ_EINVAL, "null argument");
+    *out = nullptr;
+    KATZ_REQUIRE(beta > 0 && std::isfinite(beta), KATZ_EINVAL, "beta must be positive");
+    KATZ_REQUIRE(opts->value_dtype >= KATZ_UNIT && opts->value_dtype <= KATZ_BF16, KATZ_EINVAL,
+                 "value_dtype");
+    katz::HostCsr h = read_csr(W);
+    if (opts->value_dtype == KATZ_UNIT)
+      for (double v : h.val)
+        KATZ_REQUIRE(v == 1.0, KATZ_EINVAL, "value_dtype UNIT needs all weights equal to 1");
+    auto* idx = new katz_index();
+    try {
+      katz::build_index(*idx, h, beta, *opts, static_cast<cudaStream_t>(stream));
+    } catch (...) {
+      delete idx;
+      throw;
+    }
+    *out = idx;
+    return KATZ_OK;
+  });
+}
+
+void katz_index_free(katz_index* idx) { delete idx; }
+
+int katz_index_get_info(const katz_index* idx, katz_index_info* info) {
+  return guarded([&]() {
+    KATZ_REQUIRE(idx && info, KATZ_EINVAL, "null argument");
+    std::memset(info, 0, sizeof(*info));
+    info->n = idx->n;
+    info->nnz = idx->nnz;
+    info->n1 = idx->n1;
+    info->n2 = idx->n2;
+    info->n_blocks = idx->lrc ? (int32_t)(idx->part.block_ptr.size() - 1) : 0;
+    info->n_large_blocks = idx->n_large;
+    info->rank = idx->rank;
+    info->value_dtype = idx->vdt;
+    info->beta = idx->beta;
+    info->lambda_max_R = idx->sigma.empty() ? 0.0 : idx->sigma[0];
+    int64_t bytes = idx->W.csr.bytes() + idx->Wp.csr.bytes() + idx->W12.csr.bytes() +
+                    idx->W21.csr.bytes() + idx->W11L.csr.bytes() + idx->S32.bytes() +
+                    idx->S64.bytes() + idx->M22inv32.bytes() + idx->M22inv64.bytes() +
+                    idx->Wr32.bytes() + idx->Wr64.bytes() + (int64_t)idx->ws.bytes();
+    for (auto& c : idx->classes) bytes += c.inv32.bytes() + c.inv64.bytes();
+    info->device_bytes = bytes;
+    return KATZ_OK;
+  });
+}
+
+int katz_index_get_partition(const katz_index* idx, int64_t* perm, int64_t* block_ptr) {
+  return guarded([&]() {
+    KATZ_REQUIRE(idx && idx->lrc, KATZ_EINVAL, "index has no partition");
+    if (perm) std::memcpy(perm, idx->part.perm.data(), 8 * idx->part.perm.size());
+    if (block_ptr)
+      std::memcpy(block_ptr, idx->part.block_ptr.data(), 8 * idx->part.block_ptr.size());
+    return KATZ_OK;
+  });
+}
+
+int katz_partition(const katz_csr* W, int32_t n_hubs, int32_t block_max, int32_t split,
+                   int64_t* perm, int64_t* block_ptr, int64_t* n_blocks, int64_t* n1) {
+  return guarded([&]() {
+    KATZ_REQUIRE(perm && block_ptr && n_blocks && n1, KATZ_EINVAL, "null output");
+    KATZ_REQUIRE(block_max > 0, KATZ_EINVAL, "block_max must be positive");
+    katz::HostCsr h = read_csr(W);
+    katz::Partition p = katz::partition_graph(h, std::max(0, n_hubs), block_max, split != 0);
+    std::memcpy(perm, p.perm.data(), 8 * p.perm.size());
+    std::memcpy(block_ptr, p.block_ptr.data(), 8 * p.block_ptr.size());
+    *n_blocks = (int64_t)p.block_ptr.size() - 1;
+    *n1 = p.n1;
+    return KATZ_OK;
+  });
+}
+
+int katz_index_get_sigma(const katz_index* idx, double* sigma) {
+  return guarded([&]() {
+    KATZ_REQUIRE(idx && sigma, KATZ_EINVAL, "null argument");
+    std::memcpy(sigma, idx->sigma.data(), 8 * idx->sigma.size());
+    return KATZ_OK;
+  });
+}
+
+int katz_query_batch(const katz_index* idx, const int32_t* q, int32_t b,
+                     const katz_query_opts* opts, void* K_out, int32_t out_dtype, int64_t ldk,
+                     katz_stats* stats, int32_t* iters_out, double* rel_res_out, void* stream) {
+  return do_query(idx, true, q, b, opts, K_out, out_dtype, ldk, stats, iters_out, rel_res_out,
+                  stream);
+}
+
+int cg_query_batch(const katz_index* idx, const int32_t* q, int32_t b,
+                   const katz_query_opts* opts, void* K_out, int32_t out_dtype, int64_t ldk,
+                   katz_stats* stats, int32_t* iters_out, double* rel_res_out, void* stream) {
+  return do_query(idx, false, q, b, opts, K_out, out_dtype, ldk, stats, iters_out, rel_res_out,
+                  stream);
+}
+
+int linkpred_topk(const katz_index* cidx, const int32_t* q, int32_t b, const void* K,
+                  int32_t k_dtype, int64_t ldk, int32_t k, int32_t* ids_out, double* scores_out,
+                  void* stream) {
+  return guarded([&]() {
+    KATZ_REQUIRE(cidx && K && ids_out && scores_out, KATZ_EINVAL, "null argument");
+    KATZ_REQUIRE(k > 0 && k <= 64, KATZ_EINVAL, "k must be in [1, 64]");
+    KATZ_REQUIRE(k_dtype == KATZ_F32 || k_dtype == KATZ_F64, KATZ_EINVAL, "k_dtype");
+    KATZ_REQUIRE(ldk >= b, KATZ_EINVAL, "ldk < b");
+    katz_index* idx = const_cast<katz_index*>(cidx);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int32_t* qd = stage_queries(idx, q, b, s);
+    const size_t es = k_dtype == KATZ_F64 ? 8 : 4;
+    const void* Kd = K;
+    if (!is_device_ptr(K)) {
+      void* t = idx->ws.get<uint8_t>("api.Kin", es * size_t(idx->n) * ldk);
+      KATZ_CUDA(cudaMemcpyAsync(t, K, es * size_t(idx->n) * ldk, cudaMemcpyHostToDevice, s));
+      Kd = t;
+    }
+    const int slices = (int)std::max<int64_t>(1, std::min<int64_t>(64, idx->n / 4096 + 1));
+    int32_t* wid = idx->ws.get<int32_t>("tk.id", size_t(slices) * b * k);
+    double* wsc = idx->ws.get<double>("tk.sc", size_t(slices) * b * k);
+    const bool dev_ids = is_device_ptr(ids_out), dev_sc = is_device_ptr(scores_out);
+    int32_t* ids = dev_ids ? ids_out : idx->ws.get<int32_t>("tk.oid", size_t(b) * k);
+    double* sc = dev_sc ? scores_out : idx->ws.get<double>("tk.osc", size_t(b) * k);
+    if (k_dtype == KATZ_F32)
+      katz::topk_columns_ws<float>(idx->W.view(), static_cast<const float*>(Kd), ldk, idx->n, qd, b,
+                                   k, ids, sc, wid, wsc, slices, s);
+    else
+      katz::topk_columns_ws<double>(idx->W.view(), static_cast<const double*>(Kd), ldk, idx->n, qd,
+                                    b, k, ids, sc, wid, wsc, slices, s);
+    if (!dev_ids)
+      KATZ_CUDA(cudaMemcpyAsync(ids_out, ids, 4 * size_t(b) * k, cudaMemcpyDeviceToHost, s));
+    if (!dev_sc)
+      KATZ_CUDA(cudaMemcpyAsync(scores_out, sc, 8 * size_t(b) * k, cudaMemcpyDeviceToHost, s));
+    KATZ_CUDA(cudaStreamSynchronize(s));
+    return KATZ_OK;
+  });
+}
+
+int katz_apply_M(const katz_index* cidx, const void* X, void* Y, int32_t b, int32_t dtype,
+                 void* stream) {
+  return guarded([&]() {
+    KATZ_REQUIRE(cidx && X && Y && b > 0, KATZ_EINVAL, "null argument");
+    KATZ_REQUIRE(dtype == KATZ_F32 || dtype == KATZ_F64, KATZ_EINVAL, "dtype");
+    KATZ_REQUIRE(is_device_ptr(X) && is_device_ptr(Y), KATZ_EINVAL, "X and Y must be device memory");
+    katz_index* idx = const_cast<katz_index*>(cidx);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t n = idx->n, ld = (b + 3) / 4 * 4;
+    // staged through padded buffers so vector loads stay 16-byte aligned
+    if (dtype == KATZ_F32) {
+      float* xs = idx->ws.get<float>("am.x", size_t(n) * ld);
+      float* ys = idx->ws.get<float>("am.y", size_t(n) * ld);
+      KATZ_CUDA(cudaMemsetAsync(xs, 0, 4 * size_t(n) * ld, s));
+      katz::copy2d<float>(static_cast<const float*>(X), b, xs, ld, n, b, 1.0, s);
+      katz::apply_M<float>(*idx, xs, ys, b, ld, s);
+      katz::copy2d<float>(ys, ld, static_cast<float*>(Y), b, n, b, 1.0, s);
+    } else {
+      double* xs = idx->ws.get<double>("am.x", size_t(n) * ld);
+      double* ys = idx->ws.get<double>("am.y", size_t(n) * ld);
+      KATZ_CUDA(cudaMemsetAsync(xs, 0, 8 * size_t(n) * ld, s));
+      katz::copy2d<double>(static_cast<const double*>(X), b, xs, ld, n, b, 1.0, s);
+      katz::apply_M<double>(*idx, xs, ys, b, ld, s);
+      katz::copy2d<double>(ys, ld, static_cast<double*>(Y), b, n, b, 1.0, s);
+    }
+    KATZ_CUDA(cudaStreamSynchronize(s));
+    return KATZ_OK;
+  });
+}
+
+}  // extern "C"

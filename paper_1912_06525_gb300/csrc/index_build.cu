@@ -1,0 +1,633 @@
+// Index construction (Algorithm 1, "Preprocess") and lambda_max.
+//
+// Host side (native C++): CSR validation, the vertex-separator partition and
+// reordering (Section 3.2, Steps 2-3), and assembly of the permuted CSR
+// blocks.  Device side: M11 block inverses (Step 4), the Schur complement S
+// (Lemma 1), M22^{-1}, and the Lanczos process on R (Eqs. 8-11).
+#include <algorithm>
+#include <cmath>
+#include <deque>
+#include <numeric>
+#include <thread>
+
+#include "index.h"
+#include "kernels_dense.h"
+
+namespace katz {
+
+template <class VT>
+int cg_solve(const GraphPart& A, double beta, const VT* B, int64_t ld, int64_t len, int b, VT* X,
+             const double* thr2, int max_iter, Workspace& ws, const std::string& tag,
+             std::vector<int32_t>* iters, cudaStream_t s);
+template <class VT>
+int m11_solve(katz_index& idx, const VT* X, VT* Y, int b, int64_t ld, double tolL, int max_iter,
+              std::vector<int32_t>* iters, cudaStream_t s);
+
+// ------------------------------------------------------------ uploads
+void upload_csr(const HostCsr& h, int vdt, DevCsr& d, cudaStream_t s) {
+  d.nrows = h.nrows;
+  d.ncols = h.ncols;
+  d.nnz = h.nnz();
+  d.vdt = vdt;
+  d.rowptr.alloc(h.nrows + 1);
+  KATZ_CUDA(cudaMemcpyAsync(d.rowptr.p, h.rowptr.data(), sizeof(int64_t) * (h.nrows + 1),
+                            cudaMemcpyHostToDevice, s));
+  d.col.alloc(std::max<int64_t>(d.nnz, 1));
+  if (d.nnz)
+    KATZ_CUDA(cudaMemcpyAsync(d.col.p, h.col.data(), sizeof(int32_t) * d.nnz,
+                              cudaMemcpyHostToDevice, s));
+  const size_t es = vdt_size(vdt);
+  if (es && d.nnz) {
+    std::vector<uint8_t> raw(es * d.nnz);
+    for (int64_t k = 0; k < d.nnz; ++k) {
+      const double w = h.val.empty() ? 1.0 : h.val[k];
+      if (vdt == KATZ_F64) reinterpret_cast<double*>(raw.data())[k] = w;
+      else if (vdt == KATZ_F32) reinterpret_cast<float*>(raw.data())[k] = float(w);
+      else reinterpret_cast<__nv_bfloat16*>(raw.data())[k] = __double2bfloat16(w);
+    }
+    d.val.alloc(raw.size());
+    KATZ_CUDA(cudaMemcpyAsync(d.val.p, raw.data(), raw.size(), cudaMemcpyHostToDevice, s));
+    KATZ_CUDA(cudaStreamSynchronize(s));
+  } else {
+    KATZ_CUDA(cudaStreamSynchronize(s));
+  }
+}
+
+static void upload_part(const HostCsr& h, int vdt, GraphPart& g, cudaStream_t s) {
+  upload_csr(h, vdt, g.csr, s);
+  std::vector<int32_t> heavy;
+  for (int64_t i = 0; i < h.nrows; ++i)
+    if (h.rowptr[i + 1] - h.rowptr[i] > kHeavyRowNnz) heavy.push_back((int32_t)i);
+  g.n_heavy = (int64_t)heavy.size();
+  g.heavy.alloc(std::max<size_t>(heavy.size(), 1));
+  if (!heavy.empty()) {
+    KATZ_CUDA(cudaMemcpyAsync(g.heavy.p, heavy.data(), sizeof(int32_t) * heavy.size(),
+                              cudaMemcpyHostToDevice, s));
+    KATZ_CUDA(cudaStreamSynchronize(s));
+  }
+}
+
+// ------------------------------------------------------------ partition
+// Node-for-node the reading stated with the oracle's partition():
+//  1. the n_hubs nodes of largest degree (ties: smaller id) -> separator;
+//  2. components of the rest are blocks; when splitting, a block larger than
+//     block_max is cut at the median BFS level (BFS from its smallest id;
+//     the last node reached roots a second BFS; first level k with
+//     2*cum_k >= size), recursively;
+//  3. blocks by (size, smallest id), ids ascending inside; separator last.
+namespace {
+struct Bfs {
+  const HostCsr& W;
+  std::vector<int32_t> stamp;  // allowed iff stamp[v] == cur
+  std::vector<int32_t> level;
+  std::vector<int32_t> seen;
+  int32_t cur = 0, seen_epoch = 0;
+  explicit Bfs(const HostCsr& w) : W(w), stamp(w.nrows, -1), level(w.nrows, -1), seen(w.nrows, 0) {}
+  // FIFO order from `start` over nodes stamped `cur`
+  void run(int64_t start, std::vector<int64_t>& order) {
+    ++seen_epoch;
+    order.clear();
+    order.push_back(start);
+    seen[start] = seen_epoch;
+    level[start] = 0;
+    for (size_t h = 0; h < order.size(); ++h) {
+      const int64_t u = order[h];
+      for (int64_t k = W.rowptr[u]; k < W.rowptr[u + 1]; ++k) {
+        const int64_t v = W.col[k];
+        if (stamp[v] == cur && seen[v] != seen_epoch) {
+          seen[v] = seen_epoch;
+          level[v] = level[u] + 1;
+          order.push_back(v);
+        }
+      }
+    }
+  }
+};
+}  // namespace
+
+Partition partition_graph(const HostCsr& W, int64_t n_hubs, int64_t block_max, bool split) {
+  const int64_t n = W.nrows;
+  std::vector<char> sep(n, 0);
+  if (n_hubs > 0) {
+    std::vector<int64_t> ord(n);
+    std::iota(ord.begin(), ord.end(), 0);
+    auto deg = [&](int64_t v) { return W.rowptr[v + 1] - W.rowptr[v]; };
+    const int64_t h = std::min(n_hubs, n);
+    std::partial_sort(ord.begin(), ord.begin() + h, ord.end(), [&](int64_t a, int64_t b) {
+      return deg(a) != deg(b) ? deg(a) > deg(b) : a < b;
+    });
+    for (int64_t i = 0; i < h; ++i) sep[ord[i]] = 1;
+  }
+  Bfs bfs(W);
+  std::vector<std::vector<int64_t>> blocks, pending;
+  std::vector<int64_t> order;
+  // components of the nodes stamped `stampv` among `nodes` (ascending)
+  auto components = [&](const std::vector<int64_t>& nodes, int32_t stampv) {
+    std::vector<std::vector<int64_t>> out;
+    bfs.cur = stampv;
+    const int32_t mark = bfs.seen_epoch + 1;  // nodes visited in this sweep
+    (void)mark;
+    std::vector<char> done;
+    for (int64_t s : nodes) {
+      if (bfs.stamp[s] != stampv) continue;
+      bfs.run(s, order);
+      std::vector<int64_t> comp(order.begin(), order.end());
+      for (int64_t v : comp) bfs.stamp[v] = -2 - stampv;  // leave the pool
+      std::sort(comp.begin(), comp.end());
+      out.push_back(std::move(comp));
+    }
+    return out;
+  };
+  int32_t next_stamp = 0;
+  {
+    std::vector<int64_t> all;
+    all.reserve(n);
+    for (int64_t v = 0; v < n; ++v)
+      if (!sep[v]) { all.push_back(v); bfs.stamp[v] = next_stamp; }
+    pending = components(all, next_stamp);
+    ++next_stamp;
+  }
+  while (!pending.empty()) {
+    std::vector<int64_t> c = std::move(pending.back());
+    pending.pop_back();
+    if (!split || (int64_t)c.size() <= block_max) {
+      blocks.push_back(std::move(c));
+      continue;
+    }
+    const int32_t st = next_stamp++;
+    for (int64_t v : c) bfs.stamp[v] = st;
+    bfs.cur = st;
+    bfs.run(c[0], order);
+    const int64_t root = order.back();
+    bfs.run(root, order);
+    int32_t depth = 0;
+    for (int64_t v : order) depth = std::max(depth, bfs.level[v]);
+    std::vector<int64_t> cnt(depth + 1, 0);
+    for (int64_t v : order) cnt[bfs.level[v]]++;
+    int64_t cum = 0;
+    int32_t kcut = 0;
+    for (int32_t k = 0; k <= depth; ++k) {
+      cum += cnt[k];
+      if (2 * cum >= (int64_t)c.size()) { kcut = k; break; }
+    }
+    std::vector<int64_t> rest;
+    for (int64_t v : c) {
+      if (bfs.level[v] == kcut) { sep[v] = 1; bfs.stamp[v] = -1; }
+      else rest.push_back(v);
+    }
+    const int32_t st2 = next_stamp++;
+    for (int64_t v : rest) bfs.stamp[v] = st2;
+    auto sub = components(rest, st2);
+    for (auto& x : sub) pending.push_back(std::move(x));
+  }
+  std::sort(blocks.begin(), blocks.end(), [](const std::vector<int64_t>& a, const std::vector<int64_t>& b) {
+    return a.size() != b.size() ? a.size() < b.size() : a[0] < b[0];
+  });
+  Partition p;
+  p.perm.reserve(n);
+  p.block_ptr.push_back(0);
+  for (auto& b : blocks) {
+    for (int64_t v : b) p.perm.push_back(v);
+    p.block_ptr.push_back((int64_t)p.perm.size());
+  }
+  p.n1 = (int64_t)p.perm.size();
+  for (int64_t v = 0; v < n; ++v)
+    if (sep[v]) p.perm.push_back(v);
+  p.n2 = n - p.n1;
+  return p;
+}
+
+// ------------------------------------------------------- Jacobi eigen (host)
+// Symmetric eigen-decomposition of a small dense matrix by cyclic Jacobi
+// rotations (Golub and Van Loan, Sec. 8.5).  A (m x m, row-major) is
+// destroyed; eigenvalues in w, eigenvectors in the columns of V.
+static void jacobi_eig(std::vector<double>& A, int m, std::vector<double>& w,
+                       std::vector<double>& V) {
+  V.assign(size_t(m) * m, 0.0);
+  for (int i = 0; i < m; ++i) V[size_t(i) * m + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0, tot = 0;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        const double a = A[size_t(i) * m + j];
+        tot += a * a;
+        if (i != j) off += a * a;
+      }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = A[size_t(p) * m + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double app = A[size_t(p) * m + p], aqq = A[size_t(q) * m + q];
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < m; ++k) {  // columns p, q
+          const double akp = A[size_t(k) * m + p], akq = A[size_t(k) * m + q];
+          A[size_t(k) * m + p] = c * akp - sn * akq;
+          A[size_t(k) * m + q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {  // rows p, q
+          const double apk = A[size_t(p) * m + k], aqk = A[size_t(q) * m + k];
+          A[size_t(p) * m + k] = c * apk - sn * aqk;
+          A[size_t(q) * m + k] = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double vkp = V[size_t(k) * m + p], vkq = V[size_t(k) * m + q];
+          V[size_t(k) * m + p] = c * vkp - sn * vkq;
+          V[size_t(k) * m + q] = sn * vkp + c * vkq;
+        }
+      }
+  }
+  w.resize(m);
+  for (int i = 0; i < m; ++i) w[i] = A[size_t(i) * m + i];
+}
+
+static std::vector<double> splitmix64_uniform(uint64_t seed, int64_t count) {
+  std::vector<double> out(count);
+  for (int64_t i = 0; i < count; ++i) {
+    uint64_t z = seed + uint64_t(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    out[i] = double(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+  }
+  return out;
+}
+
+static double dget(const double* p, cudaStream_t s) {
+  double h = 0;
+  KATZ_CUDA(cudaMemcpyAsync(&h, p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  KATZ_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
+// ----------------------------------------------------------- lambda_max
+// Plain Lanczos on W from the normalised all-ones vector; the largest Ritz
+// value of the tridiagonal matrix is returned.
+double lambda_max_gpu(const GraphPart& W, int64_t n, int steps, Workspace& ws, cudaStream_t s) {
+  if (n == 0 || W.csr.nnz == 0) return 0.0;
+  const int64_t ld = 2;
+  double* v = ws.get<double>("lm.v", n * ld);
+  double* vp = ws.get<double>("lm.vp", n * ld);
+  double* w = ws.get<double>("lm.w", n * ld);
+  double* dd = ws.get<double>("lm.d", 2);
+  std::vector<double> ones(n * ld, 0.0);
+  for (int64_t i = 0; i < n; ++i) ones[i * ld] = 1.0 / std::sqrt(double(n));
+  KATZ_CUDA(cudaMemcpyAsync(v, ones.data(), sizeof(double) * n * ld, cudaMemcpyHostToDevice, s));
+  KATZ_CUDA(cudaMemsetAsync(vp, 0, sizeof(double) * n * ld, s));
+  std::vector<double> al, be;
+  double bprev = 0;
+  for (int j = 0; j < steps; ++j) {
+    spmm<double>(W.view(), W.heavy.p, W.n_heavy, 1.0, v, ld, 0.0, nullptr, ld, w, ld, 1, nullptr,
+                 0, nullptr, s);
+    KATZ_CUDA(cudaMemsetAsync(dd, 0, sizeof(double) * 2, s));
+    coldot<double>(v, ld, w, ld, n, 1, dd, s);
+    const double a = dget(dd, s);
+    al.push_back(a);
+    scale_copy<double>(v, ld, w, ld, n, 1, -a, true, s);
+    if (j > 0) scale_copy<double>(vp, ld, w, ld, n, 1, -bprev, true, s);
+    KATZ_CUDA(cudaMemsetAsync(dd, 0, sizeof(double) * 2, s));
+    coldot<double>(w, ld, w, ld, n, 1, dd, s);
+    const double bn = std::sqrt(dget(dd, s));
+    if (bn <= 1e-12 * std::max(1.0, std::fabs(a)) || j == steps - 1) break;
+    be.push_back(bn);
+    std::swap(vp, v);                                           // vp <- v
+    scale_copy<double>(w, ld, v, ld, n, 1, 1.0 / bn, false, s);  // v <- w / bn
+    bprev = bn;
+  }
+  const int m = (int)al.size();
+  std::vector<double> T(size_t(m) * m, 0.0), ev, V;
+  for (int i = 0; i < m; ++i) {
+    T[size_t(i) * m + i] = al[i];
+    if (i + 1 < m) T[size_t(i) * m + i + 1] = T[size_t(i + 1) * m + i] = be[i];
+  }
+  jacobi_eig(T, m, ev, V);
+  return *std::max_element(ev.begin(), ev.end());
+}
+
+// --------------------------------------------------------- device helpers
+__global__ void identity_cols_kernel(double* E, int64_t ld, int64_t rows, int64_t j0, int cw) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cw; c += gridDim.x * blockDim.x)
+    if (j0 + c < rows) E[(j0 + c) * ld + c] = 1.0;
+}
+
+__global__ void dense_from_csr_kernel(Csr A, double beta, double* D, int64_t ld) {
+  for (int64_t i = blockIdx.x; i < A.nrows; i += gridDim.x) {
+    if (threadIdx.x == 0) D[i * ld + i] = 1.0;
+    for (int64_t k = A.rowptr[i] + threadIdx.x; k < A.rowptr[i + 1]; k += blockDim.x) {
+      double w = 1.0;
+      if (A.vdt == KATZ_F64) w = static_cast<const double*>(A.val)[k];
+      else if (A.vdt == KATZ_F32) w = static_cast<const float*>(A.val)[k];
+      else if (A.vdt == KATZ_BF16) w = __bfloat162float(static_cast<const __nv_bfloat16*>(A.val)[k]);
+      D[i * ld + A.col[k]] -= beta * w;
+    }
+  }
+}
+
+__global__ void sub_kernel(const double* A, const double* B, double* C, int64_t total) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x)
+    C[e] = A[e] - B[e];
+}
+
+__global__ void to_f32_kernel(const double* A, float* B, int64_t total) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x)
+    B[e] = float(A[e]);
+}
+
+static unsigned blocks_for(int64_t total) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), int64_t(num_sms()) * 16));
+}
+
+// ------------------------------------------------------------- build
+void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_build_opts& o,
+                 cudaStream_t s) {
+  idx.n = W.nrows;
+  idx.nnz = W.nnz();
+  idx.beta = beta;
+  idx.vdt = o.value_dtype;
+  upload_part(W, o.value_dtype, idx.W, s);
+  idx.lambda = lambda_max_gpu(idx.W, idx.n, 96, idx.ws, s);
+  KATZ_REQUIRE(beta * idx.lambda < 1.0, KATZ_ENOTSPD,
+               "beta * lambda_max = " + std::to_string(beta * idx.lambda) +
+                   " >= 1: M = I - beta W is not positive definite");
+  if (!o.build_lrc) return;
+
+  idx.lrc = true;
+  idx.rank = std::max(0, o.rank);
+  idx.block_max = o.block_max > 0 ? o.block_max : 64;
+  idx.split = o.split;
+  KATZ_REQUIRE(idx.block_max <= 128, KATZ_EINVAL, "block_max must be <= 128");
+  const int64_t n2_max = o.n2_max > 0 ? o.n2_max : 16384;
+  Partition& P = idx.part;
+  P = partition_graph(W, std::max(0, o.n_hubs), idx.block_max, o.split != 0);
+  const int64_t n = idx.n, n1 = P.n1, n2 = P.n2;
+  idx.n1 = n1;
+  idx.n2 = n2;
+  KATZ_REQUIRE(n2 <= n2_max, KATZ_EINVAL,
+               "separator has " + std::to_string(n2) + " nodes > n2_max " + std::to_string(n2_max));
+  std::vector<int32_t> iperm(n), perm32(n);
+  for (int64_t i = 0; i < n; ++i) {
+    perm32[i] = (int32_t)P.perm[i];
+    iperm[P.perm[i]] = (int32_t)i;
+  }
+  idx.perm.alloc(n);
+  idx.iperm.alloc(n);
+  KATZ_CUDA(cudaMemcpyAsync(idx.perm.p, perm32.data(), 4 * n, cudaMemcpyHostToDevice, s));
+  KATZ_CUDA(cudaMemcpyAsync(idx.iperm.p, iperm.data(), 4 * n, cudaMemcpyHostToDevice, s));
+
+  // --- large-block region
+  const int64_t nblocks = (int64_t)P.block_ptr.size() - 1;
+  int64_t first_large = nblocks;
+  for (int64_t bi = 0; bi < nblocks; ++bi)
+    if (P.block_ptr[bi + 1] - P.block_ptr[bi] > idx.block_max) { first_large = bi; break; }
+  idx.n1s = P.block_ptr[first_large];
+  idx.n_large = (int)(nblocks - first_large);
+
+  // --- permuted CSR pieces (host), rows in index order, columns sorted
+  HostCsr Wp, W12, W21, W22, W11L;
+  Wp.nrows = Wp.ncols = n;
+  W12.nrows = n1; W12.ncols = n2;
+  W21.nrows = n2; W21.ncols = n1;
+  W22.nrows = W22.ncols = n2;
+  W11L.nrows = W11L.ncols = n1 - idx.n1s;
+  const bool has_val = !W.val.empty();
+  Wp.rowptr.assign(n + 1, 0);
+  Wp.col.resize(idx.nnz);
+  if (has_val) Wp.val.resize(idx.nnz);
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t o0 = P.perm[i];
+    Wp.rowptr[i + 1] = Wp.rowptr[i] + (W.rowptr[o0 + 1] - W.rowptr[o0]);
+  }
+  {
+    const int nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (int t = 0; t < nth; ++t)
+      th.emplace_back([&, t]() {
+        std::vector<std::pair<int32_t, double>> tmp;
+        for (int64_t i = t; i < n; i += nth) {
+          const int64_t o0 = P.perm[i];
+          tmp.clear();
+          for (int64_t k = W.rowptr[o0]; k < W.rowptr[o0 + 1]; ++k)
+            tmp.emplace_back(iperm[W.col[k]], has_val ? W.val[k] : 1.0);
+          std::sort(tmp.begin(), tmp.end(),
+                    [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+                      return a.first < b.first;
+                    });
+          int64_t d = Wp.rowptr[i];
+          for (auto& e : tmp) {
+            Wp.col[d] = e.first;
+            if (has_val) Wp.val[d] = e.second;
+            ++d;
+          }
+        }
+      });
+    for (auto& x : th) x.join();
+  }
+  auto sub = [&](HostCsr& out, int64_t r0, int64_t r1, int64_t c0, int64_t c1) {
+    out.rowptr.assign(r1 - r0 + 1, 0);
+    for (int64_t i = r0; i < r1; ++i) {
+      int64_t cnt = 0;
+      for (int64_t k = Wp.rowptr[i]; k < Wp.rowptr[i + 1]; ++k)
+        cnt += (Wp.col[k] >= c0 && Wp.col[k] < c1);
+      out.rowptr[i - r0 + 1] = out.rowptr[i - r0] + cnt;
+    }
+    out.col.resize(out.rowptr.back());
+    if (has_val) out.val.resize(out.rowptr.back());
+    int64_t d = 0;
+    for (int64_t i = r0; i < r1; ++i)
+      for (int64_t k = Wp.rowptr[i]; k < Wp.rowptr[i + 1]; ++k)
+        if (Wp.col[k] >= c0 && Wp.col[k] < c1) {
+          out.col[d] = (int32_t)(Wp.col[k] - c0);
+          if (has_val) out.val[d] = Wp.val[k];
+          ++d;
+        }
+  };
+  sub(W12, 0, n1, n1, n);
+  sub(W21, n1, n, 0, n1);
+  sub(W22, n1, n, n1, n);
+  sub(W11L, idx.n1s, n1, idx.n1s, n1);
+  upload_part(Wp, o.value_dtype, idx.Wp, s);
+  upload_part(W12, o.value_dtype, idx.W12, s);
+  upload_part(W21, o.value_dtype, idx.W21, s);
+  upload_part(W11L, o.value_dtype, idx.W11L, s);
+  GraphPart W22d;
+  upload_part(W22, o.value_dtype, W22d, s);
+
+  // --- M11 dense block inverses by size class (Step 4)
+  DBuf<int> flag(1);
+  KATZ_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+  idx.classes.clear();
+  int64_t bi = 0;
+  while (bi < first_large) {
+    const int64_t sz = P.block_ptr[bi + 1] - P.block_ptr[bi];
+    int S = 1;
+    while (S < sz) S *= 2;
+    std::vector<int64_t> st;
+    std::vector<int32_t> sizes;
+    while (bi < first_large) {
+      const int64_t z = P.block_ptr[bi + 1] - P.block_ptr[bi];
+      if (z > S) break;
+      st.push_back(P.block_ptr[bi]);
+      sizes.push_back((int32_t)z);
+      ++bi;
+    }
+    BlockClass c;
+    c.S = S;
+    c.count = (int64_t)st.size();
+    c.start.alloc(c.count);
+    c.size.alloc(c.count);
+    KATZ_CUDA(cudaMemcpyAsync(c.start.p, st.data(), 8 * c.count, cudaMemcpyHostToDevice, s));
+    KATZ_CUDA(cudaMemcpyAsync(c.size.p, sizes.data(), 4 * c.count, cudaMemcpyHostToDevice, s));
+    c.inv64.alloc(size_t(c.count) * S * S);
+    c.inv32.alloc(size_t(c.count) * S * S);
+    block_inverses(idx.Wp.view(), c.start.p, c.size.p, c.count, S, beta, c.inv64.p, flag.p, s);
+    to_f32_kernel<<<blocks_for(c.count * S * S), 256, 0, s>>>(c.inv64.p, c.inv32.p,
+                                                              c.count * int64_t(S) * S);
+    KATZ_CHECK_LAUNCH();
+    idx.classes.push_back(std::move(c));
+  }
+  int hflag = 0;
+  KATZ_CUDA(cudaMemcpyAsync(&hflag, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  KATZ_CUDA(cudaStreamSynchronize(s));
+  KATZ_REQUIRE(hflag == 0, KATZ_ENOTSPD, "an M11 diagonal block is not positive definite");
+
+  if (n2 == 0) {
+    idx.rank = 0;
+    return;
+  }
+  // --- T = M12^T M11^{-1} M12 = beta^2 W21 M11^{-1} W12 (FP64, by columns)
+  const int64_t ld2 = (n2 + 3) / 4 * 4;
+  idx.ld2 = ld2;
+  DBuf<double> T(size_t(n2) * ld2);
+  KATZ_CUDA(cudaMemsetAsync(T.p, 0, T.bytes(), s));
+  {
+    const int cw_max = (int)std::min<int64_t>(256, (n2 + 1) / 2 * 2);
+    const int64_t ldc = (cw_max + 3) / 4 * 4;
+    DBuf<double> E(size_t(n2) * ldc), U(size_t(std::max<int64_t>(n1, 1)) * ldc),
+        V(size_t(std::max<int64_t>(n1, 1)) * ldc);
+    for (int64_t j0 = 0; j0 < n2; j0 += cw_max) {
+      const int cw = (int)std::min<int64_t>(cw_max, n2 - j0);
+      if (n1 == 0) break;
+      KATZ_CUDA(cudaMemsetAsync(E.p, 0, E.bytes(), s));
+      identity_cols_kernel<<<1, 256, 0, s>>>(E.p, ldc, n2, j0, cw);
+      KATZ_CHECK_LAUNCH();
+      KATZ_CUDA(cudaMemsetAsync(U.p, 0, U.bytes(), s));
+      spmm<double>(idx.W12.view(), idx.W12.heavy.p, idx.W12.n_heavy, beta, E.p, ldc, 0.0, nullptr,
+                   ldc, U.p, ldc, cw, nullptr, 0, nullptr, s);
+      const int st = m11_solve<double>(idx, U.p, V.p, cw, ldc, 1e-14, 5000, nullptr, s);
+      KATZ_REQUIRE(st != KATZ_ENOTSPD, KATZ_ENOTSPD, "M11 is not positive definite");
+      spmm<double>(idx.W21.view(), idx.W21.heavy.p, idx.W21.n_heavy, beta, V.p, ldc, 0.0, nullptr,
+                   ldc, T.p + j0, ld2, cw, nullptr, 0, nullptr, s);
+    }
+  }
+  // --- M22 (dense), S = M22 - T, M22^{-1}
+  DBuf<double> M22(size_t(n2) * ld2);
+  KATZ_CUDA(cudaMemsetAsync(M22.p, 0, M22.bytes(), s));
+  dense_from_csr_kernel<<<(unsigned)std::min<int64_t>(n2, 65535), 128, 0, s>>>(W22d.view(), beta,
+                                                                               M22.p, ld2);
+  KATZ_CHECK_LAUNCH();
+  idx.S64.alloc(size_t(n2) * ld2);
+  sub_kernel<<<blocks_for(n2 * ld2), 256, 0, s>>>(M22.p, T.p, idx.S64.p, n2 * ld2);
+  KATZ_CHECK_LAUNCH();
+  idx.M22inv64.alloc(size_t(n2) * ld2);
+  KATZ_CUDA(cudaMemcpyAsync(idx.M22inv64.p, M22.p, M22.bytes(), cudaMemcpyDeviceToDevice, s));
+  {
+    DBuf<double> gws(size_t(n2) * 64 * 2 + 64 * 64);
+    KATZ_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+    spd_inverse_inplace(idx.M22inv64.p, n2, ld2, gws.p, flag.p, s);
+    KATZ_CUDA(cudaMemcpyAsync(&hflag, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KATZ_CUDA(cudaStreamSynchronize(s));
+    KATZ_REQUIRE(hflag == 0, KATZ_ENOTSPD, "M22 is not positive definite");
+  }
+  idx.S32.alloc(size_t(n2) * ld2);
+  idx.M22inv32.alloc(size_t(n2) * ld2);
+  to_f32_kernel<<<blocks_for(n2 * ld2), 256, 0, s>>>(idx.S64.p, idx.S32.p, n2 * ld2);
+  to_f32_kernel<<<blocks_for(n2 * ld2), 256, 0, s>>>(idx.M22inv64.p, idx.M22inv32.p, n2 * ld2);
+  KATZ_CHECK_LAUNCH();
+
+  // --- Lanczos for the top-r eigenpairs of R = L^{-1} T L^{-T}.  R is
+  // similar to A = M22^{-1} T, which is self-adjoint in <x,y> = x^T M22 y;
+  // Lanczos on A in that inner product gives R's eigenvalues and, for each
+  // Ritz vector u of R, w = L^{-T} u directly (w^T M22 w = 1).  L itself is
+  // never formed.  Full reorthogonalisation (two Gram-Schmidt passes).
+  idx.sigma.clear();
+  if (idx.rank > 0) {
+    const int r = (int)std::min<int64_t>(idx.rank, n2);
+    int m = o.lanczos_steps > 0 ? o.lanczos_steps : std::max(2 * r, r + 20);
+    m = (int)std::min<int64_t>(std::max(m, r), n2);
+    const int64_t ldq = m + 1;
+    DBuf<double> Q(size_t(n2) * ldq), t(n2), wv(n2), u(n2), cvec(ldq), sc(2);
+    std::vector<double> v0 = splitmix64_uniform(o.seed, n2);
+    KATZ_CUDA(cudaMemcpyAsync(wv.p, v0.data(), 8 * n2, cudaMemcpyHostToDevice, s));
+    auto mdot = [&](const double* x, const double* y) {  // x^T M22 y
+      gemm<double>(false, n2, 1, n2, 1.0, M22.p, ld2, y, 1, 0.0, u.p, 1, s);
+      gemm<double>(true, 1, 1, n2, 1.0, x, 1, u.p, 1, 0.0, sc.p, 1, s);
+      return dget(sc.p, s);
+    };
+    double nrm = std::sqrt(mdot(wv.p, wv.p));
+    copy2d<double>(wv.p, 1, Q.p, ldq, n2, 1, 1.0 / nrm, s);
+    std::vector<double> al, be;
+    int k = m;
+    for (int j = 0; j < m; ++j) {
+      // t = T q_j ; w = M22^{-1} t
+      gemm<double>(false, n2, 1, n2, 1.0, T.p, ld2, Q.p + j, ldq, 0.0, t.p, 1, s);
+      gemm<double>(false, n2, 1, n2, 1.0, idx.M22inv64.p, ld2, t.p, 1, 0.0, wv.p, 1, s);
+      gemm<double>(true, 1, 1, n2, 1.0, Q.p + j, ldq, t.p, 1, 0.0, sc.p, 1, s);
+      al.push_back(dget(sc.p, s));
+      for (int pass = 0; pass < 2; ++pass) {
+        // w -= Q c, c = Q^T M22 w   (columns 0..j)
+        gemm<double>(false, n2, 1, n2, 1.0, M22.p, ld2, wv.p, 1, 0.0, u.p, 1, s);
+        gemm<double>(true, j + 1, 1, n2, 1.0, Q.p, ldq, u.p, 1, 0.0, cvec.p, 1, s);
+        gemm<double>(false, n2, 1, j + 1, -1.0, Q.p, ldq, cvec.p, 1, 1.0, wv.p, 1, s);
+      }
+      const double bj = std::sqrt(std::max(0.0, mdot(wv.p, wv.p)));
+      if (j == m - 1) break;
+      if (bj <= 1e-14 * std::max(1.0, std::fabs(al.back()))) { k = j + 1; break; }
+      be.push_back(bj);
+      copy2d<double>(wv.p, 1, Q.p + j + 1, ldq, n2, 1, 1.0 / bj, s);
+    }
+    k = (int)al.size();
+    std::vector<double> Tm(size_t(k) * k, 0.0), ev, Y;
+    for (int i = 0; i < k; ++i) {
+      Tm[size_t(i) * k + i] = al[i];
+      if (i + 1 < k) Tm[size_t(i) * k + i + 1] = Tm[size_t(i + 1) * k + i] = be[i];
+    }
+    jacobi_eig(Tm, k, ev, Y);
+    std::vector<int> ordr(k);
+    std::iota(ordr.begin(), ordr.end(), 0);
+    std::sort(ordr.begin(), ordr.end(), [&](int a, int b) { return ev[a] > ev[b]; });
+    const int rk = std::min(r, k);
+    idx.rank = rk;
+    std::vector<double> Ysel(size_t(k) * rk);
+    for (int c = 0; c < rk; ++c) {
+      idx.sigma.push_back(ev[ordr[c]]);
+      for (int i = 0; i < k; ++i) Ysel[size_t(i) * rk + c] = Y[size_t(i) * k + ordr[c]];
+    }
+    DBuf<double> Yd(Ysel.size()), Wd(size_t(n2) * rk);
+    KATZ_CUDA(cudaMemcpyAsync(Yd.p, Ysel.data(), 8 * Ysel.size(), cudaMemcpyHostToDevice, s));
+    gemm<double>(false, n2, rk, k, 1.0, Q.p, ldq, Yd.p, rk, 0.0, Wd.p, rk, s);
+    std::vector<double> Wh(size_t(n2) * rk);
+    KATZ_CUDA(cudaMemcpyAsync(Wh.data(), Wd.p, 8 * Wh.size(), cudaMemcpyDeviceToHost, s));
+    KATZ_CUDA(cudaStreamSynchronize(s));
+    // fold D = diag(sigma/(1-sigma)) in: W^ = W D^{1/2}
+    std::vector<float> Wf(Wh.size());
+    for (int c = 0; c < rk; ++c) {
+      const double sg = std::min(std::max(idx.sigma[c], 0.0), 1.0 - 1e-12);
+      const double f = std::sqrt(sg / (1.0 - sg));
+      for (int64_t i = 0; i < n2; ++i) {
+        Wh[size_t(i) * rk + c] *= f;
+        Wf[size_t(i) * rk + c] = float(Wh[size_t(i) * rk + c]);
+      }
+    }
+    idx.Wr64.alloc(Wh.size());
+    idx.Wr32.alloc(Wf.size());
+    KATZ_CUDA(cudaMemcpyAsync(idx.Wr64.p, Wh.data(), 8 * Wh.size(), cudaMemcpyHostToDevice, s));
+    KATZ_CUDA(cudaMemcpyAsync(idx.Wr32.p, Wf.data(), 4 * Wf.size(), cudaMemcpyHostToDevice, s));
+    KATZ_CUDA(cudaStreamSynchronize(s));
+  }
+}
+
+}  // namespace katz

@@ -1,0 +1,419 @@
+// Dense kernels: SIMT GEMM (FP32/FP64), batched M11 block inverses (Step 4:
+// Cholesky of each diagonal block, then the inverse), the small pivot-block
+// inverse of the blocked Gauss-Jordan used for M22^{-1}, and top-k of Katz
+// columns for link prediction (Section 3.3).
+#include "kernels.h"
+#include "kernels_dense.h"
+
+namespace katz {
+
+// ---------------------------------------------------------------- GEMM
+// 64x64 output tile per CTA, K step 16, 256 threads each owning a 4x4
+// micro-tile.  op(A) is A (M x K, row-major) or A^T (A stored K x M);
+// op(B) likewise.  lower_only skips tiles strictly above the diagonal.
+template <class VT, bool TA, bool TB>
+__global__ void __launch_bounds__(256) gemm_kernel(int64_t M, int64_t N, int64_t K, VT alpha,
+                                                   const VT* __restrict__ A, int64_t lda,
+                                                   const VT* __restrict__ B, int64_t ldb, VT beta,
+                                                   VT* __restrict__ C, int64_t ldc,
+                                                   int lower_only) {
+  __shared__ VT As[16][64 + 4];
+  __shared__ VT Bs[16][64 + 4];
+  const int64_t m0 = int64_t(blockIdx.y) * 64, n0 = int64_t(blockIdx.x) * 64;
+  if (lower_only && n0 > m0 + 63) return;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  VT acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = VT(0);
+  for (int64_t k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      int mm, kk;
+      if (!TA) { mm = e >> 4; kk = e & 15; } else { kk = e >> 6; mm = e & 63; }
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      VT v = VT(0);
+      if (gm < M && gk < K) v = TA ? A[gk * lda + gm] : A[gm * lda + gk];
+      As[kk][mm] = v;
+    }
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      int nn, kk;
+      if (!TB) { kk = e >> 6; nn = e & 63; } else { nn = e >> 4; kk = e & 15; }
+      const int64_t gn = n0 + nn, gk = k0 + kk;
+      VT v = VT(0);
+      if (gn < N && gk < K) v = TB ? B[gn * ldb + gk] : B[gk * ldb + gn];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      VT a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      VT* cp = C + gm * ldc + gn;
+      *cp = beta == VT(0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*cp);
+    }
+  }
+}
+
+template <class VT>
+void gemm2(bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alpha, const VT* A,
+           int64_t lda, const VT* B, int64_t ldb, double beta, VT* C, int64_t ldc, bool lower_only,
+           cudaStream_t s) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid((unsigned)ceil_div(N, 64), (unsigned)ceil_div(M, 64));
+  const int lo = lower_only ? 1 : 0;
+  prof_begin(s);
+#define KATZ_G(TA, TB)                                                                   \
+  gemm_kernel<VT, TA, TB><<<grid, 256, 0, s>>>(M, N, K, VT(alpha), A, lda, B, ldb, VT(beta), C, \
+                                               ldc, lo)
+  if (!transA && !transB) KATZ_G(false, false);
+  else if (transA && !transB) KATZ_G(true, false);
+  else if (!transA && transB) KATZ_G(false, true);
+  else KATZ_G(true, true);
+#undef KATZ_G
+  KATZ_CHECK_LAUNCH();
+  if (profiling())
+    prof_end(sizeof(VT) == 4 ? "gemm_f32" : "gemm_f64",
+             double(sizeof(VT)) * (double(M) * K + double(K) * N + double(M) * N), s);
+}
+template void gemm2<float>(bool, bool, int64_t, int64_t, int64_t, double, const float*, int64_t,
+                           const float*, int64_t, double, float*, int64_t, bool, cudaStream_t);
+template void gemm2<double>(bool, bool, int64_t, int64_t, int64_t, double, const double*, int64_t,
+                            const double*, int64_t, double, double*, int64_t, bool, cudaStream_t);
+
+template <class VT>
+void gemm(bool transA, int64_t M, int64_t N, int64_t K, double alpha, const VT* A, int64_t lda,
+          const VT* B, int64_t ldb, double beta, VT* C, int64_t ldc, cudaStream_t s) {
+  gemm2<VT>(transA, false, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, false, s);
+}
+template void gemm<float>(bool, int64_t, int64_t, int64_t, double, const float*, int64_t,
+                          const float*, int64_t, double, float*, int64_t, cudaStream_t);
+template void gemm<double>(bool, int64_t, int64_t, int64_t, double, const double*, int64_t,
+                           const double*, int64_t, double, double*, int64_t, cudaStream_t);
+
+// ------------------------------------------------- M11 block inverses
+// One CTA per diagonal block of M11 = I - beta W11.  The block is assembled
+// in shared memory from the (index-ordered) CSR rows, factorised in place
+// (M_blk = L1 L1^T, right-looking Cholesky), and its inverse written as
+// L1^{-T} L1^{-1}: thread j solves L1 y = e_j then L1^T x = y.  Output is the
+// S x S zero-padded inverse in FP64; a non-positive pivot sets *flag.
+__global__ void block_inverse_kernel(Csr W, const int64_t* start, const int32_t* size, int S,
+                                     double beta, double* inv, int* flag) {
+  extern __shared__ double Ls[];  // S x S
+  const int64_t blk = blockIdx.x;
+  const int64_t a = start[blk];
+  const int n = size[blk];
+  double* out = inv + blk * int64_t(S) * S;
+  for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
+    Ls[e] = 0.0;
+    out[e] = 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    Ls[r * S + r] = 1.0;
+    for (int64_t k = W.rowptr[a + r]; k < W.rowptr[a + r + 1]; ++k) {
+      const int64_t c = int64_t(W.col[k]) - a;
+      if (c >= 0 && c < n) {
+        double w = 1.0;
+        if (W.vdt == KATZ_F64) w = static_cast<const double*>(W.val)[k];
+        else if (W.vdt == KATZ_F32) w = static_cast<const float*>(W.val)[k];
+        else if (W.vdt == KATZ_BF16) w = __bfloat162float(static_cast<const __nv_bfloat16*>(W.val)[k]);
+        Ls[r * S + c] -= beta * w;
+      }
+    }
+  }
+  __syncthreads();
+  // right-looking Cholesky, lower triangle
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = Ls[j * S + j];
+      if (!(d > 0.0)) { bad = 1; Ls[j * S + j] = 1.0; }
+      else Ls[j * S + j] = sqrt(d);
+    }
+    __syncthreads();
+    const double dj = Ls[j * S + j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) Ls[i * S + j] /= dj;
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = j + 1 + e / m, k = j + 1 + e % m;
+      if (k <= i) Ls[i * S + k] -= Ls[i * S + j] * Ls[k * S + j];
+    }
+    __syncthreads();
+  }
+  if (bad && threadIdx.x == 0) atomicOr(flag, 1);
+  // inverse: row j of the (symmetric) inverse = solution of M x = e_j
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    double* x = out + int64_t(j) * S;  // scratch: row j
+    for (int i = 0; i < n; ++i) {  // forward: L y = e_j
+      double v = (i == j) ? 1.0 : 0.0;
+      for (int k = j; k < i; ++k) v -= Ls[i * S + k] * x[k];
+      x[i] = (i < j) ? 0.0 : v / Ls[i * S + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {  // backward: L^T x = y
+      double v = x[i];
+      for (int k = i + 1; k < n; ++k) v -= Ls[k * S + i] * x[k];
+      x[i] = v / Ls[i * S + i];
+    }
+  }
+}
+
+void block_inverses(const Csr& Wperm, const int64_t* start, const int32_t* size, int64_t count,
+                    int S, double beta, double* inv, int* flag, cudaStream_t s) {
+  if (count <= 0) return;
+  const size_t smem = size_t(S) * S * sizeof(double);
+  if (smem > 48 * 1024)
+    KATZ_CUDA(cudaFuncSetAttribute(block_inverse_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int threads = S >= 64 ? 256 : 128;
+  block_inverse_kernel<<<(unsigned)count, threads, smem, s>>>(Wperm, start, size, S, beta, inv,
+                                                              flag);
+  KATZ_CHECK_LAUNCH();
+}
+
+// ---------------------------------------- pivot-block inverse (Gauss-Jordan)
+// In-place inverse of an nb x nb SPD block (nb <= 64) held at P (ld).  Plain
+// Gauss-Jordan without pivoting, which is stable for SPD matrices; a
+// non-positive pivot sets *flag.
+__global__ void small_spd_inverse_kernel(double* P, int64_t ld, int nb, int* flag) {
+  __shared__ double A[64][65];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) A[e / nb][e % nb] = P[(e / nb) * ld + e % nb];
+  __syncthreads();
+  for (int k = 0; k < nb; ++k) {
+    const double piv = A[k][k];
+    if (!(piv > 0.0)) {  // uniform across the CTA: every thread reads the same value
+      if (threadIdx.x == 0) bad = 1;
+      break;
+    }
+    const double ip = 1.0 / piv;
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+      const int i = e / nb, j = e % nb;
+      if (i != k && j != k) A[i][j] -= A[i][k] * A[k][j] * ip;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+      if (j != k) {
+        A[k][j] *= ip;
+        A[j][k] = -A[j][k] * ip;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) A[k][k] = ip;
+    __syncthreads();
+  }
+  __syncthreads();
+  if (bad) {
+    if (threadIdx.x == 0) atomicOr(flag, 1);
+    return;
+  }
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) P[(e / nb) * ld + e % nb] = A[e / nb][e % nb];
+}
+
+void small_spd_inverse(double* P, int64_t ld, int nb, int* flag, cudaStream_t s) {
+  small_spd_inverse_kernel<<<1, 64, 0, s>>>(P, ld, nb, flag);
+  KATZ_CHECK_LAUNCH();
+}
+
+// strided sub-matrix copy (rows x cols), optional scale
+template <class VT>
+__global__ void copy2d_kernel(const VT* X, int64_t ldx, VT* Y, int64_t ldy, int64_t rows,
+                              int64_t cols, VT a) {
+  const int64_t total = rows * cols;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / cols, j = e - i * cols;
+    Y[i * ldy + j] = a * X[i * ldx + j];
+  }
+}
+template <class VT>
+void copy2d(const VT* X, int64_t ldx, VT* Y, int64_t ldy, int64_t rows, int64_t cols, double a,
+            cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  int64_t g = std::min<int64_t>(ceil_div(rows * cols, 256), int64_t(num_sms()) * 16);
+  copy2d_kernel<VT><<<(unsigned)std::max<int64_t>(1, g), 256, 0, s>>>(X, ldx, Y, ldy, rows, cols,
+                                                                    VT(a));
+  KATZ_CHECK_LAUNCH();
+}
+template void copy2d<float>(const float*, int64_t, float*, int64_t, int64_t, int64_t, double,
+                            cudaStream_t);
+template void copy2d<double>(const double*, int64_t, double*, int64_t, int64_t, int64_t, double,
+                             cudaStream_t);
+
+// Dense SPD inverse in place by blocked Gauss-Jordan (pivot blocks of 64):
+//   Pinv = A_kk^{-1};  Rp = Pinv A_k,: ;  A -= A_:,k Rp ;
+//   A_k,: = Rp ; A_:,k = -A_:,k Pinv ; A_kk = Pinv.
+// ws must hold n*64 (Rp) + n*64 (column copy) + 64*64 doubles.
+void spd_inverse_inplace(double* A, int64_t n, int64_t lda, double* ws, int* flag,
+                         cudaStream_t s) {
+  const int64_t NB = 64;
+  double* Rp = ws;
+  double* Cc = ws + n * NB;
+  double* Pinv = Cc + n * NB;
+  for (int64_t k = 0; k < n; k += NB) {
+    const int64_t nb = std::min(NB, n - k);
+    copy2d<double>(A + k * lda + k, lda, Pinv, NB, nb, nb, 1.0, s);
+    small_spd_inverse(Pinv, NB, (int)nb, flag, s);
+    // Rp (nb x n) = Pinv * A[k:k+nb, :]
+    gemm2<double>(false, false, nb, n, nb, 1.0, Pinv, NB, A + k * lda, lda, 0.0, Rp, n, false, s);
+    // Cc (n x nb) = A[:, k:k+nb]
+    copy2d<double>(A + k, lda, Cc, NB, n, nb, 1.0, s);
+    // A -= Cc * Rp
+    gemm2<double>(false, false, n, n, nb, -1.0, Cc, NB, Rp, n, 1.0, A, lda, false, s);
+    // row block k := Rp
+    copy2d<double>(Rp, n, A + k * lda, lda, nb, n, 1.0, s);
+    // column block k := -Cc * Pinv
+    gemm2<double>(false, false, n, nb, nb, -1.0, Cc, NB, Pinv, NB, 0.0, A + k, lda, false, s);
+    // pivot block := Pinv
+    copy2d<double>(Pinv, NB, A + k * lda + k, lda, nb, nb, 1.0, s);
+  }
+}
+
+// ---------------------------------------------------------------- top-k
+// Candidate order: score descending, node id ascending (a strict total
+// order, so every implementation selects the same set).
+__device__ __forceinline__ bool better(double sa, int ia, double sb, int ib) {
+  return sa > sb || (sa == sb && ia < ib);
+}
+
+constexpr int kTopMax = 64;
+
+// Pass 1: CTA (column j, row slice).  Each thread keeps a sorted top-k
+// list in local memory; the CTA merges them by repeated arg-max.
+template <class VT>
+__global__ void topk_partial_kernel(Csr W, const VT* K, int64_t ldk, int64_t n,
+                                    const int32_t* q, int k, int64_t rows_per_cta,
+                                    int32_t* pid, double* psc) {
+  const int j = blockIdx.y;
+  const int64_t r0 = int64_t(blockIdx.x) * rows_per_cta;
+  const int64_t r1 = min(n, r0 + rows_per_cta);
+  const int64_t qq = q[j];
+  const int64_t nb0 = W.rowptr[qq], nb1 = W.rowptr[qq + 1];
+  double ls[kTopMax];
+  int li[kTopMax];
+  int cnt = 0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    if (i == qq) continue;
+    const double v = double(K[i * ldk + j]);
+    if (cnt == k && !better(v, (int)i, ls[k - 1], li[k - 1])) continue;
+    // exclude current neighbours of q (sorted CSR row: binary search)
+    int64_t lo = nb0, hi = nb1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (W.col[mid] < i) lo = mid + 1; else hi = mid;
+    }
+    if (lo < nb1 && W.col[lo] == i) continue;
+    int p = cnt < k ? cnt++ : k - 1;
+    while (p > 0 && better(v, (int)i, ls[p - 1], li[p - 1])) {
+      ls[p] = ls[p - 1];
+      li[p] = li[p - 1];
+      --p;
+    }
+    ls[p] = v;
+    li[p] = (int)i;
+  }
+  __shared__ double ss[256];
+  __shared__ int si[256];
+  __shared__ int sw[256];
+  int head = 0;
+  const int64_t out = (int64_t(j) * gridDim.x + blockIdx.x) * k;
+  for (int t = 0; t < k; ++t) {
+    ss[threadIdx.x] = head < cnt ? ls[head] : -1.0 / 0.0;
+    si[threadIdx.x] = head < cnt ? li[head] : 0x7fffffff;
+    sw[threadIdx.x] = threadIdx.x;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) {
+        const int o = threadIdx.x + st;
+        if (better(ss[o], si[o], ss[threadIdx.x], si[threadIdx.x])) {
+          ss[threadIdx.x] = ss[o];
+          si[threadIdx.x] = si[o];
+          sw[threadIdx.x] = sw[o];
+        }
+      }
+      __syncthreads();
+    }
+    const int winner = sw[0];
+    const int wid = si[0];
+    const double wsc = ss[0];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      pid[out + t] = wid == 0x7fffffff ? -1 : wid;
+      psc[out + t] = wid == 0x7fffffff ? 0.0 : wsc;
+    }
+    if (threadIdx.x == winner && head < cnt) ++head;
+    __syncthreads();
+  }
+}
+
+// Pass 2: one CTA per column merges its slices' lists.
+__global__ void topk_merge_kernel(const int32_t* pid, const double* psc, int slices, int k,
+                                  int32_t* ids, double* scores) {
+  const int j = blockIdx.x;
+  const int64_t base = int64_t(j) * slices * k;
+  // Simple exact merge: thread 0 performs a k-way selection over all
+  // slices (slices * k candidates, small).
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < k; ++t) {
+      double best = -1.0 / 0.0;
+      int bid = 0x7fffffff;
+      int64_t bpos = -1;
+      for (int64_t e = 0; e < int64_t(slices) * k; ++e) {
+        const int id = pid[base + e];
+        if (id < 0) continue;
+        const double sc = psc[base + e];
+        if (better(sc, id, best, bid)) { best = sc; bid = id; bpos = e; }
+      }
+      if (bpos >= 0) {
+        ids[int64_t(j) * k + t] = bid;
+        scores[int64_t(j) * k + t] = best;
+        const_cast<int32_t*>(pid)[base + bpos] = -1;
+      } else {
+        ids[int64_t(j) * k + t] = -1;
+        scores[int64_t(j) * k + t] = 0.0;
+      }
+    }
+  }
+}
+
+template <class VT>
+void topk_columns_ws(const Csr& W, const VT* K, int64_t ldk, int64_t n, const int32_t* q, int b,
+                     int k, int32_t* ids, double* scores, int32_t* ws_id, double* ws_sc,
+                     int slices, cudaStream_t s) {
+  const int64_t rows_per = ceil_div(n, slices);
+  dim3 grid((unsigned)slices, (unsigned)b);
+  topk_partial_kernel<VT><<<grid, 256, 0, s>>>(W, K, ldk, n, q, k, rows_per, ws_id, ws_sc);
+  KATZ_CHECK_LAUNCH();
+  topk_merge_kernel<<<b, 32, 0, s>>>(ws_id, ws_sc, slices, k, ids, scores);
+  KATZ_CHECK_LAUNCH();
+}
+template void topk_columns_ws<float>(const Csr&, const float*, int64_t, int64_t, const int32_t*,
+                                     int, int, int32_t*, double*, int32_t*, double*, int,
+                                     cudaStream_t);
+template void topk_columns_ws<double>(const Csr&, const double*, int64_t, int64_t,
+                                      const int32_t*, int, int, int32_t*, double*, int32_t*,
+                                      double*, int, cudaStream_t);
+
+}  // namespace katz

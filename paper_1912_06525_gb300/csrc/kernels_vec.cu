@@ -1,0 +1,824 @@
+// HBM-bound kernels of the Katz query path: multi-RHS CSR SpMM on M (Eq. 3)
+// and on the coupling blocks (Lemma 1), fused column dot products, CG/PCG
+// vector updates, RHS construction, permutations and dense M11 block solves.
+//
+// Layout: dense n x b blocks are node-major, so one CSR entry (i, j) moves
+// the contiguous row X[j, :] (b values) with 16-byte vector loads.
+#include "kernels.h"
+
+namespace katz {
+
+// ---------------------------------------------------------------- helpers
+template <class VT> struct Acc { using type = VT; };
+
+template <int WT, class A>
+__device__ __forceinline__ A load_weight(const void* val, int64_t k) {
+  if constexpr (WT == KATZ_UNIT) {
+    return A(1);
+  } else if constexpr (WT == KATZ_F64) {
+    return A(static_cast<const double*>(val)[k]);
+  } else if constexpr (WT == KATZ_F32) {
+    return A(static_cast<const float*>(val)[k]);
+  } else {
+    return A(__bfloat162float(static_cast<const __nv_bfloat16*>(val)[k]));
+  }
+}
+
+template <class VT>
+__device__ __forceinline__ void vload(const VT* p, VT (&o)[VecOf<VT>::width]) {
+  using V = typename VecOf<VT>::type;
+  V v = *reinterpret_cast<const V*>(p);
+  if constexpr (VecOf<VT>::width == 4) {
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  } else {
+    o[0] = v.x; o[1] = v.y;
+  }
+}
+template <class VT>
+__device__ __forceinline__ void vstore(VT* p, const VT (&o)[VecOf<VT>::width]) {
+  using V = typename VecOf<VT>::type;
+  V v;
+  if constexpr (VecOf<VT>::width == 4) {
+    v.x = o[0]; v.y = o[1]; v.z = o[2]; v.w = o[3];
+  } else {
+    v.x = o[0]; v.y = o[1];
+  }
+  *reinterpret_cast<V*>(p) = v;
+}
+
+// Column accumulator: FP32 partial sums are flushed into FP64 every
+// kFlush rows so long reductions keep FP64 accuracy at FP32 cost.
+constexpr int kFlush = 16;
+
+// ---------------------------------------------------------------- SpMM
+template <class VT>
+struct SpmmParams {
+  Csr A;
+  double alpha, gamma;
+  const VT* X; int64_t ldx;
+  const VT* Z; int64_t ldz;
+  VT* Y; int64_t ldy;
+  const VT* V; int64_t ldv;
+  double* dots;
+  int b;
+  int skip_heavy;
+};
+
+// One group of TPR threads per row; each thread owns VPT vectors of VW
+// columns: thread t of the group covers columns
+//   tile0 + (v*TPR + t)*VW .. +VW-1, v < VPT.
+// Rows are visited grid-stride so concurrent groups sweep neighbouring rows
+// (their gathers share L2 lines of X for graphs with locality).
+template <class VT, int WT, int TPR, int VPT, bool DOT>
+__global__ void __launch_bounds__(256) spmm_rows_kernel(SpmmParams<VT> p) {
+  constexpr int VW = VecOf<VT>::width;
+  constexpr int TILE = TPR * VW * VPT;
+  using A = typename Acc<VT>::type;
+  const int t = threadIdx.x % TPR;
+  const int64_t group = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / TPR;
+  const int64_t ngroups = (int64_t(gridDim.x) * blockDim.x) / TPR;
+  const int lane = threadIdx.x & 31;
+  const unsigned gmask = (TPR == 32) ? 0xffffffffu : (((1u << TPR) - 1u) << (lane / TPR * TPR));
+  const int tile0 = blockIdx.y * TILE;
+  const A alpha = A(p.alpha), gamma = A(p.gamma);
+  bool cval[VPT];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) cval[v] = tile0 + (v * TPR + t) * VW < p.b;
+  double dsum[VPT][VW];
+  A dpart[VPT][VW];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v)
+#pragma unroll
+    for (int w = 0; w < VW; ++w) { dsum[v][w] = 0.0; dpart[v][w] = A(0); }
+  int since_flush = 0;
+
+  for (int64_t i = group; i < p.A.nrows; i += ngroups) {
+    const int64_t k0 = p.A.rowptr[i], k1 = p.A.rowptr[i + 1];
+    if (p.skip_heavy && k1 - k0 > kHeavyRowNnz) continue;
+    A acc[VPT][VW];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v)
+#pragma unroll
+      for (int w = 0; w < VW; ++w) acc[v][w] = A(0);
+    for (int64_t kb = k0; kb < k1; kb += TPR) {
+      const int64_t k = kb + t;
+      int cj = 0;
+      A wj = A(0);
+      if (k < k1) {
+        cj = p.A.col[k];
+        wj = load_weight<WT, A>(p.A.val, k);
+      }
+      const int cnt = (int)(k1 - kb < TPR ? k1 - kb : TPR);
+#pragma unroll 4
+      for (int s = 0; s < cnt; ++s) {
+        const int j = __shfl_sync(gmask, cj, s, TPR);
+        const A wv = (WT == KATZ_UNIT) ? A(1) : __shfl_sync(gmask, wj, s, TPR);
+        const VT* xr = p.X + int64_t(j) * p.ldx + tile0 + t * VW;
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          if (cval[v]) {
+            VT xv[VW];
+            vload<VT>(xr + v * TPR * VW, xv);
+#pragma unroll
+            for (int w = 0; w < VW; ++w) acc[v][w] += wv * xv[w];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      if (!cval[v]) continue;
+      const int64_t c = tile0 + (v * TPR + t) * VW;
+      VT y[VW];
+      if (p.Z != nullptr) {
+        VT z[VW];
+        vload<VT>(p.Z + i * p.ldz + c, z);
+#pragma unroll
+        for (int w = 0; w < VW; ++w) y[w] = VT(gamma * z[w] + alpha * acc[v][w]);
+      } else {
+#pragma unroll
+        for (int w = 0; w < VW; ++w) y[w] = VT(alpha * acc[v][w]);
+      }
+      vstore<VT>(p.Y + i * p.ldy + c, y);
+      if constexpr (DOT) {
+        VT vv[VW];
+        vload<VT>(p.V + i * p.ldv + c, vv);
+#pragma unroll
+        for (int w = 0; w < VW; ++w) dpart[v][w] += A(y[w]) * A(vv[w]);
+      }
+    }
+    if constexpr (DOT) {
+      if (++since_flush == kFlush) {
+        since_flush = 0;
+#pragma unroll
+        for (int v = 0; v < VPT; ++v)
+#pragma unroll
+          for (int w = 0; w < VW; ++w) { dsum[v][w] += double(dpart[v][w]); dpart[v][w] = A(0); }
+      }
+    }
+  }
+  if constexpr (DOT) {
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      if (!cval[v]) continue;
+      const int64_t c = tile0 + (v * TPR + t) * VW;
+#pragma unroll
+      for (int w = 0; w < VW; ++w) {
+        const double d = dsum[v][w] + double(dpart[v][w]);
+        if (d != 0.0) atomicAdd(p.dots + c + w, d);
+      }
+    }
+  }
+}
+
+// Heavy rows: CTA = (heavy row, column slice of 32*VW columns); its 8
+// warps split the row's entries; partial sums meet in shared memory.
+template <class VT, int WT, bool DOT>
+__global__ void __launch_bounds__(256) spmm_heavy_kernel(SpmmParams<VT> p, const int32_t* heavy) {
+  constexpr int VW = VecOf<VT>::width;
+  using A = typename Acc<VT>::type;
+  __shared__ A red[8][32 * VW];
+  const int64_t i = heavy[blockIdx.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t c = int64_t(blockIdx.y) * 32 * VW + lane * VW;
+  const bool cv = c < p.b;
+  const int64_t k0 = p.A.rowptr[i], k1 = p.A.rowptr[i + 1];
+  A acc[VW];
+#pragma unroll
+  for (int w = 0; w < VW; ++w) acc[w] = A(0);
+  for (int64_t kb = k0 + warp * 32; kb < k1; kb += 8 * 32) {
+    const int64_t k = kb + lane;
+    int cj = 0;
+    A wj = A(0);
+    if (k < k1) {
+      cj = p.A.col[k];
+      wj = load_weight<WT, A>(p.A.val, k);
+    }
+    const int cnt = (int)(k1 - kb < 32 ? k1 - kb : 32);
+#pragma unroll 4
+    for (int s = 0; s < cnt; ++s) {
+      const int j = __shfl_sync(0xffffffffu, cj, s);
+      const A wv = __shfl_sync(0xffffffffu, wj, s);
+      if (cv) {
+        VT xv[VW];
+        vload<VT>(p.X + int64_t(j) * p.ldx + c, xv);
+#pragma unroll
+        for (int w = 0; w < VW; ++w) acc[w] += wv * xv[w];
+      }
+    }
+  }
+#pragma unroll
+  for (int w = 0; w < VW; ++w) red[warp][lane * VW + w] = acc[w];
+  __syncthreads();
+  if (warp == 0 && cv) {
+    A s[VW];
+#pragma unroll
+    for (int w = 0; w < VW; ++w) {
+      s[w] = A(0);
+      for (int q = 0; q < 8; ++q) s[w] += red[q][lane * VW + w];
+    }
+    VT y[VW];
+    if (p.Z != nullptr) {
+      VT z[VW];
+      vload<VT>(p.Z + i * p.ldz + c, z);
+#pragma unroll
+      for (int w = 0; w < VW; ++w) y[w] = VT(A(p.gamma) * z[w] + A(p.alpha) * s[w]);
+    } else {
+#pragma unroll
+      for (int w = 0; w < VW; ++w) y[w] = VT(A(p.alpha) * s[w]);
+    }
+    vstore<VT>(p.Y + i * p.ldy + c, y);
+    if constexpr (DOT) {
+      VT vv[VW];
+      vload<VT>(p.V + i * p.ldv + c, vv);
+#pragma unroll
+      for (int w = 0; w < VW; ++w) atomicAdd(p.dots + c + w, double(A(y[w]) * A(vv[w])));
+    }
+  }
+}
+
+template <class VT, int WT, int TPR, int VPT>
+static void launch_rows(const SpmmParams<VT>& p, dim3 grid, cudaStream_t s) {
+  if (p.dots)
+    spmm_rows_kernel<VT, WT, TPR, VPT, true><<<grid, 256, 0, s>>>(p);
+  else
+    spmm_rows_kernel<VT, WT, TPR, VPT, false><<<grid, 256, 0, s>>>(p);
+}
+
+template <class VT, int WT>
+static void spmm_dispatch(SpmmParams<VT>& p, const int32_t* heavy, int64_t n_heavy,
+                          cudaStream_t s, const SpmmCfg& cfg) {
+  constexpr int VW = VecOf<VT>::width;
+  const int nvec = (p.b + VW - 1) / VW;
+  // threads per row and vectors per thread cover min(b, cap) columns
+  int tpr = 1;
+  while (tpr < 32 && tpr < nvec) tpr *= 2;
+  int vpt = 1;
+  const int vcap = cfg.col_tile > 0 ? max(1, cfg.col_tile / (VW * 32)) : (sizeof(VT) == 4 ? 8 : 8);
+  if (tpr == 32)
+    while (vpt < vcap && vpt * 32 < nvec) vpt *= 2;
+  const int tile = tpr * VW * vpt;
+  const int64_t tiles = ceil_div(p.b, tile);
+  const int64_t groups_per_cta = 256 / tpr;
+  int64_t ctas = ceil_div(p.A.nrows, groups_per_cta);
+  const int64_t cap = int64_t(num_sms()) * cfg.ctas_per_sm * (tpr == 32 ? 1 : 1);
+  ctas = std::max<int64_t>(1, std::min<int64_t>(ctas, std::max<int64_t>(1, cap / tiles)));
+  dim3 grid((unsigned)ctas, (unsigned)tiles);
+  p.skip_heavy = heavy != nullptr && n_heavy > 0;
+  if (p.A.nrows > 0) {
+#define KATZ_ROWS(T, V) \
+  if (tpr == T && vpt == V) { launch_rows<VT, WT, T, V>(p, grid, s); }
+    KATZ_ROWS(1, 1) else KATZ_ROWS(2, 1) else KATZ_ROWS(4, 1) else KATZ_ROWS(8, 1)
+    else KATZ_ROWS(16, 1) else KATZ_ROWS(32, 1) else KATZ_ROWS(32, 2) else KATZ_ROWS(32, 4)
+    else KATZ_ROWS(32, 8) else throw Error(KATZ_EINVAL, "spmm: unsupported shape");
+#undef KATZ_ROWS
+    KATZ_CHECK_LAUNCH();
+  }
+  if (p.skip_heavy) {
+    dim3 hg((unsigned)n_heavy, (unsigned)ceil_div(p.b, 32 * VW));
+    if (p.dots)
+      spmm_heavy_kernel<VT, WT, true><<<hg, 256, 0, s>>>(p, heavy);
+    else
+      spmm_heavy_kernel<VT, WT, false><<<hg, 256, 0, s>>>(p, heavy);
+    KATZ_CHECK_LAUNCH();
+  }
+}
+
+template <class VT>
+void spmm(const Csr& A, const int32_t* heavy, int64_t n_heavy, double alpha, const VT* X,
+          int64_t ldx, double gamma, const VT* Z, int64_t ldz, VT* Y, int64_t ldy, int b,
+          const VT* V, int64_t ldv, double* dots, cudaStream_t s, const SpmmCfg* cfg) {
+  SpmmCfg c = cfg ? *cfg : SpmmCfg{};
+  SpmmParams<VT> p{A, alpha, gamma, X, ldx, Z, ldz, Y, ldy, V, ldv, dots, b, 0};
+  if (gamma == 0.0) p.Z = nullptr;
+  KATZ_REQUIRE(b > 0 && ldx % VecOf<VT>::width == 0 && ldy % VecOf<VT>::width == 0 &&
+                   (p.Z == nullptr || ldz % VecOf<VT>::width == 0) &&
+                   (dots == nullptr || ldv % VecOf<VT>::width == 0) &&
+                   ldx >= b && ldy >= b &&
+                   (reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) % 16 == 0 &&
+                   reinterpret_cast<uintptr_t>(p.Z) % 16 == 0 &&
+                   reinterpret_cast<uintptr_t>(dots ? V : nullptr) % 16 == 0,
+               KATZ_EINVAL, "spmm: operands must be 16-byte aligned with padded rows");
+  prof_begin(s);
+  switch (A.vdt) {
+    case KATZ_UNIT: spmm_dispatch<VT, KATZ_UNIT>(p, heavy, n_heavy, s, c); break;
+    case KATZ_F64: spmm_dispatch<VT, KATZ_F64>(p, heavy, n_heavy, s, c); break;
+    case KATZ_F32: spmm_dispatch<VT, KATZ_F32>(p, heavy, n_heavy, s, c); break;
+    case KATZ_BF16: spmm_dispatch<VT, KATZ_BF16>(p, heavy, n_heavy, s, c); break;
+    default: throw Error(KATZ_EINVAL, "spmm: bad value dtype");
+  }
+  if (profiling()) {
+    // algorithmic bytes: CSR once, X once, Y written once, Z / V read once
+    const double sv = double(sizeof(VT)) * b;
+    const double bytes = 8.0 * (A.nrows + 1) + double(A.nnz) * (4 + vdt_size(A.vdt)) +
+                         sv * A.ncols + sv * A.nrows * (1 + (p.Z ? 1 : 0) + (dots ? 1 : 0));
+    prof_end(sizeof(VT) == 4 ? "spmm_f32" : "spmm_f64", bytes, s);
+  }
+}
+
+template void spmm<float>(const Csr&, const int32_t*, int64_t, double, const float*, int64_t,
+                          double, const float*, int64_t, float*, int64_t, int, const float*,
+                          int64_t, double*, cudaStream_t, const SpmmCfg*);
+template void spmm<double>(const Csr&, const int32_t*, int64_t, double, const double*, int64_t,
+                           double, const double*, int64_t, double*, int64_t, int, const double*,
+                           int64_t, double*, cudaStream_t, const SpmmCfg*);
+
+// ------------------------------------------------------- 2D vector launches
+// Threads: x over column vectors of a tile (TC vectors), y over rows.
+struct Grid2 {
+  dim3 grid, block;
+  int tc;
+};
+template <class VT>
+static Grid2 grid2(int64_t len, int b) {
+  constexpr int VW = VecOf<VT>::width;
+  const int nvec = (b + VW - 1) / VW;
+  int tc = 1;
+  while (tc < 32 && tc < nvec) tc *= 2;
+  const int ty = 256 / tc;
+  const int tiles = (nvec + tc - 1) / tc;
+  int64_t gx = ceil_div(len, ty);
+  const int64_t cap = int64_t(num_sms()) * 8;
+  gx = std::max<int64_t>(1, std::min<int64_t>(gx, std::max<int64_t>(1, cap / tiles)));
+  return {dim3((unsigned)gx, (unsigned)tiles), dim3(tc, ty), tc};
+}
+
+// block-level FP64 reduction of per-thread column partials (threads with
+// equal threadIdx.x share columns) followed by one atomicAdd per column.
+template <int VW>
+__device__ __forceinline__ void reduce_cols_atomic(double (&part)[VW], double* out, int64_t c,
+                                                   bool valid) {
+  __shared__ double sh[256 * 4];
+  const int tx = threadIdx.x, ty = threadIdx.y, tc = blockDim.x, tyn = blockDim.y;
+  const int tid = ty * tc + tx;
+#pragma unroll
+  for (int w = 0; w < VW; ++w) sh[tid * VW + w] = part[w];
+  __syncthreads();
+  for (int stride = tyn / 2; stride > 0; stride >>= 1) {
+    if (ty < stride) {
+#pragma unroll
+      for (int w = 0; w < VW; ++w) sh[tid * VW + w] += sh[((ty + stride) * tc + tx) * VW + w];
+    }
+    __syncthreads();
+  }
+  if (ty == 0 && valid) {
+#pragma unroll
+    for (int w = 0; w < VW; ++w)
+      if (sh[tx * VW + w] != 0.0) atomicAdd(out + c + w, sh[tx * VW + w]);
+  }
+}
+
+template <class VT>
+__global__ void coldot_kernel(const VT* A, int64_t lda, const VT* B, int64_t ldb, int64_t len,
+                              int b, double* dots) {
+  constexpr int VW = VecOf<VT>::width;
+  const int64_t c = (int64_t(blockIdx.y) * blockDim.x + threadIdx.x) * VW;
+  const bool valid = c < b;
+  double tot[VW];
+  VT part[VW];
+#pragma unroll
+  for (int w = 0; w < VW; ++w) { tot[w] = 0; part[w] = VT(0); }
+  int cnt = 0;
+  if (valid) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.y + threadIdx.y; i < len;
+         i += int64_t(gridDim.x) * blockDim.y) {
+      VT a[VW], bb[VW];
+      vload<VT>(A + i * lda + c, a);
+      vload<VT>(B + i * ldb + c, bb);
+#pragma unroll
+      for (int w = 0; w < VW; ++w) part[w] += a[w] * bb[w];
+      if (++cnt == kFlush) {
+        cnt = 0;
+#pragma unroll
+        for (int w = 0; w < VW; ++w) { tot[w] += double(part[w]); part[w] = VT(0); }
+      }
+    }
+  }
+#pragma unroll
+  for (int w = 0; w < VW; ++w) tot[w] += double(part[w]);
+  reduce_cols_atomic<VW>(tot, dots, c, valid);
+}
+
+template <class VT>
+void coldot(const VT* A, int64_t lda, const VT* B, int64_t ldb, int64_t len, int b, double* dots,
+            cudaStream_t s) {
+  if (len <= 0 || b <= 0) return;
+  Grid2 g = grid2<VT>(len, b);
+  coldot_kernel<VT><<<g.grid, g.block, 0, s>>>(A, lda, B, ldb, len, b, dots);
+  KATZ_CHECK_LAUNCH();
+}
+template void coldot<float>(const float*, int64_t, const float*, int64_t, int64_t, int, double*,
+                            cudaStream_t);
+template void coldot<double>(const double*, int64_t, const double*, int64_t, int64_t, int,
+                             double*, cudaStream_t);
+
+// ------------------------------------------------------------ CG updates
+template <class VT, bool ACC_RR>
+__global__ void cg_update_xr_kernel(VT* X, const VT* P, VT* R, const VT* Q, int64_t ld,
+                                    int64_t len, int b, ColState st) {
+  constexpr int VW = VecOf<VT>::width;
+  const int64_t c = (int64_t(blockIdx.y) * blockDim.x + threadIdx.x) * VW;
+  const bool valid = c < b;
+  VT a[VW];
+  bool any = false;
+#pragma unroll
+  for (int w = 0; w < VW; ++w) {
+    a[w] = VT(0);
+    if (valid && c + w < b && st.active[c + w]) {
+      a[w] = VT(st.rz[c + w] / st.pq[c + w]);
+      any = true;
+    }
+  }
+  double tot[VW];
+  VT part[VW];
+#pragma unroll
+  for (int w = 0; w < VW; ++w) { tot[w] = 0; part[w] = VT(0); }
+  int cnt = 0;
+  if (any) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.y + threadIdx.y; i < len;
+         i += int64_t(gridDim.x) * blockDim.y) {
+      VT x[VW], p[VW], r[VW], q[VW];
+      vload<VT>(X + i * ld + c, x);
+      vload<VT>(P + i * ld + c, p);
+      vload<VT>(R + i * ld + c, r);
+      vload<VT>(Q + i * ld + c, q);
+#pragma unroll
+      for (int w = 0; w < VW; ++w) {
+        x[w] += a[w] * p[w];
+        r[w] -= a[w] * q[w];
+        part[w] += r[w] * r[w];
+      }
+      vstore<VT>(X + i * ld + c, x);
+      vstore<VT>(R + i * ld + c, r);
+      if constexpr (ACC_RR) {
+        if (++cnt == kFlush) {
+          cnt = 0;
+#pragma unroll
+          for (int w = 0; w < VW; ++w) { tot[w] += double(part[w]); part[w] = VT(0); }
+        }
+      }
+    }
+  }
+  if constexpr (ACC_RR) {
+#pragma unroll
+    for (int w = 0; w < VW; ++w) tot[w] += double(part[w]);
+    reduce_cols_atomic<VW>(tot, st.rz_new, c, valid);
+  }
+}
+
+// rr accumulation for PCG happens separately (coldot of r with r); the
+// plain-CG variant accumulates r.r into rz_new directly (z = r).
+template <class VT>
+void cg_update_xr(VT* X, const VT* P, VT* R, const VT* Q, int64_t ld, int64_t len, int b,
+                  const ColState& st, bool acc_rr, cudaStream_t s) {
+  if (len <= 0) return;
+  Grid2 g = grid2<VT>(len, b);
+  if (acc_rr)
+    cg_update_xr_kernel<VT, true><<<g.grid, g.block, 0, s>>>(X, P, R, Q, ld, len, b, st);
+  else
+    cg_update_xr_kernel<VT, false><<<g.grid, g.block, 0, s>>>(X, P, R, Q, ld, len, b, st);
+  KATZ_CHECK_LAUNCH();
+}
+template void cg_update_xr<float>(float*, const float*, float*, const float*, int64_t, int64_t,
+                                  int, const ColState&, bool, cudaStream_t);
+template void cg_update_xr<double>(double*, const double*, double*, const double*, int64_t,
+                                   int64_t, int, const ColState&, bool, cudaStream_t);
+
+template <class VT>
+__global__ void cg_update_p_kernel(VT* P, const VT* Z, int64_t ld, int64_t len, int b,
+                                   ColState st) {
+  constexpr int VW = VecOf<VT>::width;
+  const int64_t c = (int64_t(blockIdx.y) * blockDim.x + threadIdx.x) * VW;
+  if (c >= b) return;
+  VT be[VW];
+  bool act[VW];
+  bool any = false;
+#pragma unroll
+  for (int w = 0; w < VW; ++w) {
+    act[w] = (c + w < b) && st.active[c + w];
+    be[w] = act[w] ? VT(st.rz_new[c + w] / st.rz[c + w]) : VT(0);
+    any |= act[w];
+  }
+  if (!any) return;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.y + threadIdx.y; i < len;
+       i += int64_t(gridDim.x) * blockDim.y) {
+    VT p[VW], z[VW];
+    vload<VT>(P + i * ld + c, p);
+    vload<VT>(Z + i * ld + c, z);
+#pragma unroll
+    for (int w = 0; w < VW; ++w)
+      if (act[w]) p[w] = z[w] + be[w] * p[w];
+    vstore<VT>(P + i * ld + c, p);
+  }
+}
+
+template <class VT>
+void cg_update_p(VT* P, const VT* Z, int64_t ld, int64_t len, int b, const ColState& st,
+                 cudaStream_t s) {
+  if (len <= 0) return;
+  Grid2 g = grid2<VT>(len, b);
+  cg_update_p_kernel<VT><<<g.grid, g.block, 0, s>>>(P, Z, ld, len, b, st);
+  KATZ_CHECK_LAUNCH();
+}
+template void cg_update_p<float>(float*, const float*, int64_t, int64_t, int, const ColState&,
+                                 cudaStream_t);
+template void cg_update_p<double>(double*, const double*, int64_t, int64_t, int, const ColState&,
+                                  cudaStream_t);
+
+__global__ void colstate_check_pq_kernel(ColState st, int b) {
+  for (int c = threadIdx.x; c < b; c += blockDim.x)
+    if (st.active[c] && !(st.pq[c] > 0.0)) {
+      atomicOr(st.flags, 1);
+      st.active[c] = 0;
+    }
+}
+void colstate_check_pq(const ColState& st, int b, cudaStream_t s) {
+  colstate_check_pq_kernel<<<1, 1024, 0, s>>>(st, b);
+  KATZ_CHECK_LAUNCH();
+}
+
+// Decide convergence from rr (plain CG: rr == rz_new), advance rz.
+__global__ void colstate_advance_kernel(ColState st, int b, int rotate_rz) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int local = 0;
+  for (int c = threadIdx.x; c < b; c += blockDim.x) {
+    if (st.active[c]) {
+      st.iters[c] += 1;
+      const double rr = st.rr ? st.rr[c] : st.rz_new[c];
+      const int still = rr > st.thr2[c];
+      // the p-update of this iteration runs only on columns still active
+      st.active[c] = still;
+      local += still;
+    }
+  }
+  atomicAdd(&cnt, local);
+  __syncthreads();
+  if (threadIdx.x == 0) *st.n_active = cnt;
+  (void)rotate_rz;
+}
+void colstate_advance(const ColState& st, int b, cudaStream_t s) {
+  colstate_advance_kernel<<<1, 1024, 0, s>>>(st, b, 0);
+  KATZ_CHECK_LAUNCH();
+}
+
+// After the p-update: rz <- rz_new; zero the accumulators.
+__global__ void colstate_rotate_kernel(ColState st, int b) {
+  for (int c = threadIdx.x; c < b; c += blockDim.x) {
+    st.rz[c] = st.rz_new[c];
+    st.rz_new[c] = 0.0;
+    st.pq[c] = 0.0;
+    if (st.rr) st.rr[c] = 0.0;
+  }
+}
+void colstate_rotate(const ColState& st, int b, cudaStream_t s) {
+  colstate_rotate_kernel<<<1, 1024, 0, s>>>(st, b);
+  KATZ_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------- misc vectors
+template <class VT>
+__global__ void scale_copy_kernel(const VT* X, int64_t ldx, VT* Y, int64_t ldy, int64_t len,
+                                  int b, VT a, int accumulate) {
+  const int64_t total = len * b;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / b, c = e - i * b;
+    const VT v = a * X[i * ldx + c];
+    Y[i * ldy + c] = accumulate ? Y[i * ldy + c] + v : v;
+  }
+}
+static dim3 flat_grid(int64_t total) {
+  int64_t g = ceil_div(total, 256);
+  return dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(g, int64_t(num_sms()) * 16)));
+}
+template <class VT>
+void scale_copy(const VT* X, int64_t ldx, VT* Y, int64_t ldy, int64_t len, int b, double a,
+                bool accumulate, cudaStream_t s) {
+  if (len <= 0 || b <= 0) return;
+  scale_copy_kernel<VT><<<flat_grid(len * b), 256, 0, s>>>(X, ldx, Y, ldy, len, b, VT(a),
+                                                            accumulate ? 1 : 0);
+  KATZ_CHECK_LAUNCH();
+}
+template void scale_copy<float>(const float*, int64_t, float*, int64_t, int64_t, int, double,
+                                bool, cudaStream_t);
+template void scale_copy<double>(const double*, int64_t, double*, int64_t, int64_t, int, double,
+                                 bool, cudaStream_t);
+
+template <class S, class D, bool ACC>
+__global__ void convert_kernel(const S* X, int64_t ldx, D* Y, int64_t ldy, int64_t len, int b) {
+  const int64_t total = len * b;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / b, c = e - i * b;
+    if constexpr (ACC)
+      Y[i * ldy + c] += D(X[i * ldx + c]);
+    else
+      Y[i * ldy + c] = D(X[i * ldx + c]);
+  }
+}
+void add_f32_to_f64(const float* X, int64_t ldx, double* Y, int64_t ldy, int64_t len, int b,
+                    cudaStream_t s) {
+  if (len <= 0 || b <= 0) return;
+  convert_kernel<float, double, true><<<flat_grid(len * b), 256, 0, s>>>(X, ldx, Y, ldy, len, b);
+  KATZ_CHECK_LAUNCH();
+}
+void convert_f64_to_f32(const double* X, int64_t ldx, float* Y, int64_t ldy, int64_t len, int b,
+                        cudaStream_t s) {
+  if (len <= 0 || b <= 0) return;
+  convert_kernel<double, float, false><<<flat_grid(len * b), 256, 0, s>>>(X, ldx, Y, ldy, len, b);
+  KATZ_CHECK_LAUNCH();
+}
+void convert_f32_to_f64(const float* X, int64_t ldx, double* Y, int64_t ldy, int64_t len, int b,
+                        cudaStream_t s) {
+  if (len <= 0 || b <= 0) return;
+  convert_kernel<float, double, false><<<flat_grid(len * b), 256, 0, s>>>(X, ldx, Y, ldy, len, b);
+  KATZ_CHECK_LAUNCH();
+}
+
+template <class VT>
+__global__ void gather_rows_kernel(const VT* X, int64_t ldx, const int32_t* map, VT* Y,
+                                   int64_t ldy, int64_t len, int b) {
+  const int64_t total = len * b;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / b, c = e - i * b;
+    Y[i * ldy + c] = X[int64_t(map[i]) * ldx + c];
+  }
+}
+template <class VT>
+void gather_rows(const VT* X, int64_t ldx, const int32_t* map, VT* Y, int64_t ldy, int64_t len,
+                 int b, cudaStream_t s) {
+  if (len <= 0 || b <= 0) return;
+  gather_rows_kernel<VT><<<flat_grid(len * b), 256, 0, s>>>(X, ldx, map, Y, ldy, len, b);
+  KATZ_CHECK_LAUNCH();
+}
+template void gather_rows<float>(const float*, int64_t, const int32_t*, float*, int64_t, int64_t,
+                                 int, cudaStream_t);
+template void gather_rows<double>(const double*, int64_t, const int32_t*, double*, int64_t,
+                                  int64_t, int, cudaStream_t);
+
+// One CTA per query column: scatter beta * W[q, i] to row pos(i).
+template <class VT, int WT>
+__global__ void build_rhs_kernel(Csr W, const int32_t* q, double beta, const int32_t* pos, VT* B,
+                                 int64_t ldb) {
+  const int j = blockIdx.x;
+  const int64_t qq = q[j];
+  const int64_t k0 = W.rowptr[qq], k1 = W.rowptr[qq + 1];
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    const int64_t i = W.col[k];
+    const int64_t r = pos ? pos[i] : i;
+    B[r * ldb + j] = VT(beta * load_weight<WT, double>(W.val, k));
+  }
+}
+template <class VT>
+void build_rhs(const Csr& W, const int32_t* q, int b, double beta, const int32_t* pos, VT* B,
+               int64_t ldb, cudaStream_t s) {
+  if (b <= 0) return;
+  switch (W.vdt) {
+    case KATZ_UNIT: build_rhs_kernel<VT, KATZ_UNIT><<<b, 256, 0, s>>>(W, q, beta, pos, B, ldb); break;
+    case KATZ_F64: build_rhs_kernel<VT, KATZ_F64><<<b, 256, 0, s>>>(W, q, beta, pos, B, ldb); break;
+    case KATZ_F32: build_rhs_kernel<VT, KATZ_F32><<<b, 256, 0, s>>>(W, q, beta, pos, B, ldb); break;
+    default: build_rhs_kernel<VT, KATZ_BF16><<<b, 256, 0, s>>>(W, q, beta, pos, B, ldb); break;
+  }
+  KATZ_CHECK_LAUNCH();
+}
+template void build_rhs<float>(const Csr&, const int32_t*, int, double, const int32_t*, float*,
+                               int64_t, cudaStream_t);
+template void build_rhs<double>(const Csr&, const int32_t*, int, double, const int32_t*, double*,
+                                int64_t, cudaStream_t);
+
+template <class VT>
+__global__ void col_norms_kernel(const VT* B, int64_t ld, int64_t len, int b, double* norm2,
+                                 unsigned long long* maxabs_bits) {
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= b) return;
+  double s = 0, m = 0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.y + threadIdx.y; i < len;
+       i += int64_t(gridDim.x) * blockDim.y) {
+    const double v = double(B[i * ld + c]);
+    s += v * v;
+    m = fmax(m, fabs(v));
+  }
+  if (s != 0.0) atomicAdd(norm2 + c, s);
+  if (m != 0.0) atomicMax(maxabs_bits + c, (unsigned long long)__double_as_longlong(m));
+}
+template <class VT>
+void col_norms(const VT* B, int64_t ld, int64_t len, int b, double* norm2, double* maxabs,
+               cudaStream_t s) {
+  KATZ_CUDA(cudaMemsetAsync(norm2, 0, sizeof(double) * b, s));
+  KATZ_CUDA(cudaMemsetAsync(maxabs, 0, sizeof(double) * b, s));
+  if (len <= 0) return;
+  const int tx = std::min(32, b);
+  dim3 block(tx, 256 / tx);
+  int64_t gx = std::min<int64_t>(ceil_div(len, block.y), int64_t(num_sms()) * 4);
+  dim3 grid((unsigned)std::max<int64_t>(1, gx), (unsigned)ceil_div(b, tx));
+  // non-negative doubles order like their bit patterns, so atomicMax on the
+  // bits gives the maximum
+  col_norms_kernel<VT><<<grid, block, 0, s>>>(B, ld, len, b, norm2,
+                                               reinterpret_cast<unsigned long long*>(maxabs));
+  KATZ_CHECK_LAUNCH();
+}
+template void col_norms<float>(const float*, int64_t, int64_t, int, double*, double*,
+                               cudaStream_t);
+template void col_norms<double>(const double*, int64_t, int64_t, int, double*, double*,
+                                cudaStream_t);
+
+__global__ void make_thresholds_kernel(const double* norm2, const double* maxabs, int b, double tol,
+                                       int kind, double omc, double* thr2) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < b; c += gridDim.x * blockDim.x) {
+    const double base = kind == KATZ_TOL_ERROR_INF ? maxabs[c] * omc : sqrt(norm2[c]);
+    const double t = tol * base;
+    thr2[c] = t * t;
+  }
+}
+void make_thresholds(const double* norm2, const double* maxabs, int b, double tol, int kind,
+                     double one_minus_c, double* thr2, cudaStream_t s) {
+  make_thresholds_kernel<<<(unsigned)ceil_div(b, 256), 256, 0, s>>>(norm2, maxabs, b, tol, kind,
+                                                                    one_minus_c, thr2);
+  KATZ_CHECK_LAUNCH();
+}
+
+// ------------------------------------------------------- M11 block solves
+// CTA = (group of blocks, column tile of TC columns).  Minv tiles and the
+// X tile are staged in shared memory; each thread accumulates RI output
+// rows of one column.
+template <class VT, int S>
+__global__ void __launch_bounds__(256) block_solve_kernel(const VT* inv, const int64_t* start,
+                                                          const int32_t* size, int64_t count,
+                                                          const VT* X, int64_t ldx, VT* Y,
+                                                          int64_t ldy, int b, int TC, int G) {
+  extern __shared__ unsigned char smraw[];
+  VT* sm_inv = reinterpret_cast<VT*>(smraw);       // G*S*S
+  VT* sm_x = sm_inv + size_t(G) * S * S;           // G*S*TC
+  const int64_t blk0 = int64_t(blockIdx.x) * G;
+  const int c0 = blockIdx.y * TC;
+  const int tc = min(TC, b - c0);
+  const int nb = (int)(count - blk0 < G ? count - blk0 : G);
+  for (int e = threadIdx.x; e < nb * S * S; e += blockDim.x)
+    sm_inv[e] = inv[(blk0 * S) * S + e];
+  for (int e = threadIdx.x; e < nb * S * tc; e += blockDim.x) {
+    const int g = e / (S * tc), rem = e - g * S * tc, r = rem / tc, c = rem - r * tc;
+    const int64_t bi = blk0 + g;
+    sm_x[(g * S + r) * TC + c] = r < size[bi] ? X[(start[bi] + r) * ldx + c0 + c] : VT(0);
+  }
+  __syncthreads();
+  const int outputs = nb * S * tc;
+  for (int o = threadIdx.x; o < outputs; o += blockDim.x) {
+    const int g = o / (S * tc), rem = o - g * S * tc, r = rem / tc, c = rem - r * tc;
+    const int64_t bi = blk0 + g;
+    if (r >= size[bi]) continue;
+    const VT* mi = sm_inv + (size_t(g) * S + r) * S;
+    const VT* xc = sm_x + size_t(g) * S * TC + c;
+    VT acc = VT(0);
+#pragma unroll 8
+    for (int k = 0; k < S; ++k) acc += mi[k] * xc[k * TC];
+    Y[(start[bi] + r) * ldy + c0 + c] = acc;
+  }
+}
+
+template <class VT, int S>
+static void launch_block_solve(const VT* inv, const int64_t* start, const int32_t* size,
+                               int64_t count, const VT* X, int64_t ldx, VT* Y, int64_t ldy, int b,
+                               cudaStream_t s) {
+  const int TC = std::min(b, S >= 64 ? 32 : 64);
+  int G = std::max(1, 2048 / (S * TC));
+  while (G > 1 && size_t(G) * S * (S + TC) * sizeof(VT) > 96 * 1024) G /= 2;
+  const size_t smem = size_t(G) * S * (S + TC) * sizeof(VT);
+  if (smem > 48 * 1024)
+    KATZ_CUDA(cudaFuncSetAttribute(block_solve_kernel<VT, S>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((unsigned)ceil_div(count, G), (unsigned)ceil_div(b, TC));
+  block_solve_kernel<VT, S><<<grid, 256, smem, s>>>(inv, start, size, count, X, ldx, Y, ldy, b,
+                                                     TC, G);
+  KATZ_CHECK_LAUNCH();
+}
+
+template <class VT>
+void block_solve(const VT* inv, const int64_t* start, const int32_t* size, int64_t count, int S,
+                 const VT* X, int64_t ldx, VT* Y, int64_t ldy, int b, cudaStream_t s) {
+  if (count <= 0 || b <= 0) return;
+  prof_begin(s);
+  switch (S) {
+    case 1: launch_block_solve<VT, 1>(inv, start, size, count, X, ldx, Y, ldy, b, s); break;
+    case 2: launch_block_solve<VT, 2>(inv, start, size, count, X, ldx, Y, ldy, b, s); break;
+    case 4: launch_block_solve<VT, 4>(inv, start, size, count, X, ldx, Y, ldy, b, s); break;
+    case 8: launch_block_solve<VT, 8>(inv, start, size, count, X, ldx, Y, ldy, b, s); break;
+    case 16: launch_block_solve<VT, 16>(inv, start, size, count, X, ldx, Y, ldy, b, s); break;
+    case 32: launch_block_solve<VT, 32>(inv, start, size, count, X, ldx, Y, ldy, b, s); break;
+    case 64: launch_block_solve<VT, 64>(inv, start, size, count, X, ldx, Y, ldy, b, s); break;
+    case 128: launch_block_solve<VT, 128>(inv, start, size, count, X, ldx, Y, ldy, b, s); break;
+    default: throw Error(KATZ_EINVAL, "block_solve: size class must be a power of two <= 128");
+  }
+  if (profiling()) {
+    const double bytes = double(sizeof(VT)) * (double(count) * S * S + 2.0 * double(count) * S * b);
+    prof_end(sizeof(VT) == 4 ? "block_solve_f32" : "block_solve_f64", bytes, s);
+  }
+}
+template void block_solve<float>(const float*, const int64_t*, const int32_t*, int64_t, int,
+                                 const float*, int64_t, float*, int64_t, int, cudaStream_t);
+template void block_solve<double>(const double*, const int64_t*, const int32_t*, int64_t, int,
+                                  const double*, int64_t, double*, int64_t, int, cudaStream_t);
+
+}  // namespace katz

@@ -1,0 +1,532 @@
+// Query solvers: plain multi-RHS CG on M (the comparison method), the
+// LRC-Katz solve (Lemma 1 with PCG on the Schur complement, Algorithm 2),
+// and the mixed-precision driver that wraps either one in FP64 iterative
+// refinement.
+#include <chrono>
+#include <cmath>
+
+#include "index.h"
+#include "kernels_dense.h"
+
+namespace katz {
+
+// ----------------------------------------------------------- small kernels
+__global__ void colstate_init_kernel(ColState st, int b, int use_rr) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) { cnt = 0; *st.flags = 0; }
+  __syncthreads();
+  int local = 0;
+  for (int c = threadIdx.x; c < b; c += blockDim.x) {
+    const double r2 = use_rr ? st.rr[c] : st.rz[c];
+    const int a = r2 > st.thr2[c];
+    st.active[c] = a;
+    st.iters[c] = 0;
+    st.pq[c] = 0.0;
+    st.rz_new[c] = 0.0;
+    if (st.rr) st.rr[c] = 0.0;
+    local += a;
+  }
+  atomicAdd(&cnt, local);
+  __syncthreads();
+  if (threadIdx.x == 0) *st.n_active = cnt;
+}
+
+// RHS norms straight from the sparse structure: b_j = beta W e_{q_j}.
+template <int WT>
+__global__ void rhs_norms_kernel(Csr W, const int32_t* q, double beta, double* norm2,
+                                 double* maxabs) {
+  const int j = blockIdx.x;
+  const int64_t k0 = W.rowptr[q[j]], k1 = W.rowptr[q[j] + 1];
+  double s = 0, m = 0;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    double w = 1.0;
+    if (WT == KATZ_F64) w = static_cast<const double*>(W.val)[k];
+    else if (WT == KATZ_F32) w = static_cast<const float*>(W.val)[k];
+    else if (WT == KATZ_BF16) w = __bfloat162float(static_cast<const __nv_bfloat16*>(W.val)[k]);
+    const double v = beta * w;
+    s += v * v;
+    m = fmax(m, fabs(v));
+  }
+  s = warp_sum(s);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(norm2 + j, s);
+    atomicMax(reinterpret_cast<unsigned long long*>(maxabs) + j,
+              (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// Residual correction: R[pos(i), j] += beta W[q_j, i] (adds the sparse RHS).
+template <int WT>
+__global__ void rhs_add_kernel(Csr W, const int32_t* q, double beta, const int32_t* pos,
+                               double* R, int64_t ld) {
+  const int j = blockIdx.x;
+  const int64_t k0 = W.rowptr[q[j]], k1 = W.rowptr[q[j] + 1];
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    double w = 1.0;
+    if (WT == KATZ_F64) w = static_cast<const double*>(W.val)[k];
+    else if (WT == KATZ_F32) w = static_cast<const float*>(W.val)[k];
+    else if (WT == KATZ_BF16) w = __bfloat162float(static_cast<const __nv_bfloat16*>(W.val)[k]);
+    const int64_t i = W.col[k];
+    const int64_t r = pos ? pos[i] : i;
+    R[r * ld + j] += beta * w;
+  }
+}
+
+// Per column: converged = rr <= thr2; inner threshold
+//   thr2_in = max(tau^2 rr, (0.3)^2 thr2)   (0 for converged columns).
+__global__ void inner_thresholds_kernel(const double* rr, const double* thr2, double tau, int b,
+                                        int* conv, double* thr2_in, int* n_open) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int local = 0;
+  for (int c = threadIdx.x; c < b; c += blockDim.x) {
+    const int cv = rr[c] <= thr2[c];
+    conv[c] = cv;
+    thr2_in[c] = cv ? 0.0 : fmax(tau * tau * rr[c], 0.09 * thr2[c]);
+    local += !cv;
+  }
+  atomicAdd(&cnt, local);
+  __syncthreads();
+  if (threadIdx.x == 0) *n_open = cnt;
+}
+
+template <class D>
+__global__ void masked_from_f64_kernel(const double* X, D* Y, int64_t ld, int64_t len, int b,
+                                       const int* conv) {
+  const int64_t total = len * ld;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t c = e % ld;
+    Y[e] = (c < b && !conv[c]) ? D(X[e]) : D(0);
+  }
+}
+
+template <class S>
+__global__ void gather_out_kernel(const double* K64, const S* K32, int64_t ld, const int32_t* map,
+                                  int64_t n, int b, void* out, int out_dt, int64_t ldk) {
+  const int64_t total = n * b;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / b, c = e - i * b;
+    const int64_t r = map ? map[i] : i;
+    const double v = K64 ? K64[r * ld + c] : double(K32[r * ld + c]);
+    if (out_dt == KATZ_F64)
+      static_cast<double*>(out)[i * ldk + c] = v;
+    else
+      static_cast<float*>(out)[i * ldk + c] = float(v);
+  }
+}
+
+static unsigned flat_blocks(int64_t total) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), int64_t(num_sms()) * 16));
+}
+
+// ------------------------------------------------------------ col state
+// Column arrays that receive vectorised reductions are padded to a multiple
+// of 4 entries (a reduction over a 4-wide vector writes all 4 lanes).
+static int bpad(int b) { return (b + 3) / 4 * 4; }
+
+static ColState make_state(Workspace& ws, const std::string& tag, int b, bool with_rr) {
+  ColState st;
+  st.rz = ws.get<double>(tag + ".rz", bpad(b));
+  st.pq = ws.get<double>(tag + ".pq", bpad(b));
+  st.rz_new = ws.get<double>(tag + ".rzn", bpad(b));
+  st.rr = with_rr ? ws.get<double>(tag + ".rr", bpad(b)) : nullptr;
+  st.thr2 = ws.get<double>(tag + ".thr2", b);
+  st.active = ws.get<int>(tag + ".act", b);
+  st.iters = ws.get<int>(tag + ".it", b);
+  st.flags = ws.get<int>(tag + ".flags", 1);
+  st.n_active = ws.get<int>(tag + ".nact", 1);
+  return st;
+}
+
+static int read_int(const int* dev, cudaStream_t s) {
+  int h = 0;
+  KATZ_CUDA(cudaMemcpyAsync(&h, dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+  KATZ_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
+// Adds the state's per-column iteration counts to iters (host).
+static void harvest_iters(const ColState& st, int b, std::vector<int32_t>* iters, cudaStream_t s) {
+  if (!iters) return;
+  std::vector<int32_t> h(b);
+  KATZ_CUDA(cudaMemcpyAsync(h.data(), st.iters, sizeof(int) * b, cudaMemcpyDeviceToHost, s));
+  KATZ_CUDA(cudaStreamSynchronize(s));
+  for (int c = 0; c < b; ++c) (*iters)[c] += h[c];
+}
+
+// ----------------------------------------------------------- plain CG
+// Solves (I - beta A) X = B for len x b blocks (ld), zero start, stopping
+// column c when ||r_c||^2 <= thr2[c].  Returns KATZ_OK / ENOTSPD / ENOCONV.
+template <class VT>
+int cg_solve(const GraphPart& A, double beta, const VT* B, int64_t ld, int64_t len, int b, VT* X,
+             const double* thr2, int max_iter, Workspace& ws, const std::string& tag,
+             std::vector<int32_t>* iters, cudaStream_t s) {
+  VT* R = ws.get<VT>(tag + ".R", size_t(len) * ld);
+  VT* P = ws.get<VT>(tag + ".P", size_t(len) * ld);
+  VT* Q = ws.get<VT>(tag + ".Q", size_t(len) * ld);
+  ColState st = make_state(ws, tag, b, false);
+  KATZ_CUDA(cudaMemcpyAsync(st.thr2, thr2, sizeof(double) * b, cudaMemcpyDeviceToDevice, s));
+  KATZ_CUDA(cudaMemsetAsync(X, 0, sizeof(VT) * len * ld, s));
+  KATZ_CUDA(cudaMemcpyAsync(R, B, sizeof(VT) * len * ld, cudaMemcpyDeviceToDevice, s));
+  KATZ_CUDA(cudaMemcpyAsync(P, B, sizeof(VT) * len * ld, cudaMemcpyDeviceToDevice, s));
+  KATZ_CUDA(cudaMemsetAsync(st.rz, 0, sizeof(double) * b, s));
+  coldot<VT>(R, ld, R, ld, len, b, st.rz, s);
+  colstate_init_kernel<<<1, 1024, 0, s>>>(st, b, 0);
+  KATZ_CHECK_LAUNCH();
+  int active = read_int(st.n_active, s);
+  int it = 0;
+  for (; it < max_iter && active > 0; ++it) {
+    spmm<VT>(A.view(), A.heavy.p, A.n_heavy, -beta, P, ld, 1.0, P, ld, Q, ld, b, P, ld, st.pq, s);
+    colstate_check_pq(st, b, s);
+    cg_update_xr<VT>(X, P, R, Q, ld, len, b, st, true, s);
+    colstate_advance(st, b, s);
+    cg_update_p<VT>(P, R, ld, len, b, st, s);
+    colstate_rotate(st, b, s);
+    active = read_int(st.n_active, s);
+  }
+  harvest_iters(st, b, iters, s);
+  const int flags = read_int(st.flags, s);
+  if (flags & 1) return KATZ_ENOTSPD;
+  return active > 0 ? KATZ_ENOCONV : KATZ_OK;
+}
+
+// thr2[c] = (tol * ||X_c||_2)^2 for a dense block.
+template <class VT>
+static void rel_thresholds(const VT* X, int64_t ld, int64_t len, int b, double tol, double* thr2,
+                           Workspace& ws, const std::string& tag, cudaStream_t s) {
+  double* n2 = ws.get<double>(tag + ".n2", b);
+  double* mx = ws.get<double>(tag + ".mx", b);
+  col_norms<VT>(X, ld, len, b, n2, mx, s);
+  make_thresholds(n2, mx, b, tol, KATZ_TOL_RESIDUAL, 1.0, thr2, s);
+}
+
+// ----------------------------------------------------------- M11^{-1}
+template <class VT>
+static const VT* inv_of(const BlockClass& c);
+template <>
+const float* inv_of<float>(const BlockClass& c) { return c.inv32.p; }
+template <>
+const double* inv_of<double>(const BlockClass& c) { return c.inv64.p; }
+
+// Y1 = M11^{-1} X1: dense block inverses for the small blocks (Step 4) and,
+// for blocks kept whole, CG on that diagonal block to relative tolerance tolL.
+template <class VT>
+int m11_solve(katz_index& idx, const VT* X, VT* Y, int b, int64_t ld, double tolL, int max_iter,
+              std::vector<int32_t>* iters, cudaStream_t s) {
+  for (auto& c : idx.classes)
+    block_solve<VT>(inv_of<VT>(c), c.start.p, c.size.p, c.count, c.S, X, ld, Y, ld, b, s);
+  int st = KATZ_OK;
+  if (idx.n1 > idx.n1s) {
+    const int64_t len = idx.n1 - idx.n1s;
+    double* thr2 = idx.ws.get<double>("L.thr", b);
+    rel_thresholds<VT>(X + idx.n1s * ld, ld, len, b, tolL, thr2, idx.ws, "L", s);
+    st = cg_solve<VT>(idx.W11L, idx.beta, X + idx.n1s * ld, ld, len, b, Y + idx.n1s * ld, thr2,
+                      max_iter, idx.ws, "L", iters, s);
+  }
+  return st;
+}
+
+// ------------------------------------------------- PCG on S K2 = F
+template <class VT> struct Dense;
+template <> struct Dense<float> {
+  static const float* S(const katz_index& i) { return i.S32.p; }
+  static const float* Minv(const katz_index& i) { return i.M22inv32.p; }
+  static const float* Wr(const katz_index& i) { return i.Wr32.p; }
+};
+template <> struct Dense<double> {
+  static const double* S(const katz_index& i) { return i.S64.p; }
+  static const double* Minv(const katz_index& i) { return i.M22inv64.p; }
+  static const double* Wr(const katz_index& i) { return i.Wr64.p; }
+};
+
+// Z = S~^{-1} R = M22^{-1} R + W^ (W^T R), with W^ = W_r D^{1/2} (Eq. 14).
+template <class VT>
+static void precond(const katz_index& idx, const VT* R, VT* Z, VT* Tm, int b, int64_t ld,
+                    cudaStream_t s) {
+  const int64_t n2 = idx.n2;
+  gemm<VT>(false, n2, b, n2, 1.0, Dense<VT>::Minv(idx), idx.ld2, R, ld, 0.0, Z, ld, s);
+  if (idx.rank > 0) {
+    gemm<VT>(true, idx.rank, b, n2, 1.0, Dense<VT>::Wr(idx), idx.rank, R, ld, 0.0, Tm, ld, s);
+    gemm<VT>(false, n2, b, idx.rank, 1.0, Dense<VT>::Wr(idx), idx.rank, Tm, ld, 1.0, Z, ld, s);
+  }
+}
+
+// Preconditioned CG (Hestenes-Stiefel form) on S K2 = F with S~^{-1} as the
+// preconditioner; zero start; column c stops when ||F_c - S K2_c||^2 <= thr2[c].
+template <class VT>
+int pcg_schur(katz_index& idx, const VT* F, VT* K2, int b, int64_t ld, const double* thr2,
+              int max_iter, std::vector<int32_t>* iters, cudaStream_t s) {
+  const int64_t n2 = idx.n2;
+  Workspace& ws = idx.ws;
+  VT* R = ws.get<VT>("S.R", size_t(n2) * ld);
+  VT* Z = ws.get<VT>("S.Z", size_t(n2) * ld);
+  VT* P = ws.get<VT>("S.P", size_t(n2) * ld);
+  VT* Q = ws.get<VT>("S.Q", size_t(n2) * ld);
+  VT* Tm = ws.get<VT>("S.T", size_t(std::max(1, idx.rank)) * ld);
+  ColState st = make_state(ws, "S", b, true);
+  KATZ_CUDA(cudaMemcpyAsync(st.thr2, thr2, sizeof(double) * b, cudaMemcpyDeviceToDevice, s));
+  KATZ_CUDA(cudaMemsetAsync(K2, 0, sizeof(VT) * n2 * ld, s));
+  KATZ_CUDA(cudaMemcpyAsync(R, F, sizeof(VT) * n2 * ld, cudaMemcpyDeviceToDevice, s));
+  precond<VT>(idx, R, Z, Tm, b, ld, s);
+  KATZ_CUDA(cudaMemcpyAsync(P, Z, sizeof(VT) * n2 * ld, cudaMemcpyDeviceToDevice, s));
+  KATZ_CUDA(cudaMemsetAsync(st.rz, 0, sizeof(double) * b, s));
+  KATZ_CUDA(cudaMemsetAsync(st.rr, 0, sizeof(double) * b, s));
+  coldot<VT>(R, ld, Z, ld, n2, b, st.rz, s);
+  coldot<VT>(R, ld, R, ld, n2, b, st.rr, s);
+  colstate_init_kernel<<<1, 1024, 0, s>>>(st, b, 1);
+  KATZ_CHECK_LAUNCH();
+  int active = read_int(st.n_active, s);
+  for (int it = 0; it < max_iter && active > 0; ++it) {
+    gemm<VT>(false, n2, b, n2, 1.0, Dense<VT>::S(idx), idx.ld2, P, ld, 0.0, Q, ld, s);
+    coldot<VT>(P, ld, Q, ld, n2, b, st.pq, s);
+    colstate_check_pq(st, b, s);
+    cg_update_xr<VT>(K2, P, R, Q, ld, n2, b, st, false, s);
+    coldot<VT>(R, ld, R, ld, n2, b, st.rr, s);
+    precond<VT>(idx, R, Z, Tm, b, ld, s);
+    coldot<VT>(R, ld, Z, ld, n2, b, st.rz_new, s);
+    colstate_advance(st, b, s);
+    cg_update_p<VT>(P, Z, ld, n2, b, st, s);
+    colstate_rotate(st, b, s);
+    active = read_int(st.n_active, s);
+  }
+  harvest_iters(st, b, iters, s);
+  const int flags = read_int(st.flags, s);
+  if (flags & 1) return KATZ_ENOTSPD;
+  return active > 0 ? KATZ_ENOCONV : KATZ_OK;
+}
+
+// --------------------------------------------------------- LRC solve
+// D = M^{-1} Rin for n x b blocks in index order (Lemma 1):
+//   Y1 = M11^{-1} R1;  F = R2 - M12^T Y1 = R2 + beta W21 Y1   (Eq. 7)
+//   S K2 = F by PCG with S~^{-1}                              (Eq. 14)
+//   K1 = M11^{-1}(R1 - M12 K2) = M11^{-1}(R1 + beta W12 K2)   (Eq. 6)
+template <class VT>
+int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double tol_s,
+              double tol_l, int max_iter, std::vector<int32_t>* iters, cudaStream_t s) {
+  const int64_t n1 = idx.n1, n2 = idx.n2;
+  const VT* R1 = Rin;
+  const VT* R2 = Rin + n1 * ld;
+  VT* D1 = D;
+  VT* D2 = D + n1 * ld;
+  VT* Y1 = idx.ws.get<VT>("lrc.Y1", size_t(std::max<int64_t>(n1, 1)) * ld);
+  int status = KATZ_OK;
+  auto merge = [&](int st) { if (st != KATZ_OK && status == KATZ_OK) status = st; };
+  if (n1 > 0) merge(m11_solve<VT>(idx, R1, Y1, b, ld, tol_l, max_iter, nullptr, s));
+  if (n2 > 0) {
+    VT* F = idx.ws.get<VT>("lrc.F", size_t(n2) * ld);
+    if (n1 > 0)
+      spmm<VT>(idx.W21.view(), idx.W21.heavy.p, idx.W21.n_heavy, idx.beta, Y1, ld, 1.0, R2, ld, F,
+               ld, b, nullptr, 0, nullptr, s);
+    else
+      KATZ_CUDA(cudaMemcpyAsync(F, R2, sizeof(VT) * n2 * ld, cudaMemcpyDeviceToDevice, s));
+    double* thr2 = idx.ws.get<double>("lrc.thrF", b);
+    rel_thresholds<VT>(F, ld, n2, b, tol_s, thr2, idx.ws, "lrcF", s);
+    merge(pcg_schur<VT>(idx, F, D2, b, ld, thr2, max_iter, iters, s));
+  }
+  if (n1 > 0) {
+    const VT* T1 = R1;
+    if (n2 > 0) {
+      spmm<VT>(idx.W12.view(), idx.W12.heavy.p, idx.W12.n_heavy, idx.beta, D2, ld, 1.0, R1, ld, Y1,
+               ld, b, nullptr, 0, nullptr, s);
+      T1 = Y1;
+    }
+    merge(m11_solve<VT>(idx, T1, D1, b, ld, tol_l, max_iter, nullptr, s));
+  }
+  return status;
+}
+
+// ------------------------------------------------------- apply M (test)
+template <class VT>
+void apply_M(const katz_index& idx, const VT* X, VT* Y, int b, int64_t ld, cudaStream_t s) {
+  spmm<VT>(idx.W.view(), idx.W.heavy.p, idx.W.n_heavy, -idx.beta, X, ld, 1.0, X, ld, Y, ld, b,
+           nullptr, 0, nullptr, s);
+}
+template void apply_M<float>(const katz_index&, const float*, float*, int, int64_t, cudaStream_t);
+template void apply_M<double>(const katz_index&, const double*, double*, int, int64_t,
+                              cudaStream_t);
+
+// ------------------------------------------------- query driver
+template <class VT>
+static int inner_solve(katz_index& idx, bool use_lrc, const VT* Rin, VT* D, int b, int64_t ld,
+                       const double* thr2_in, double tol_rel, int max_iter,
+                       std::vector<int32_t>* iters, cudaStream_t s) {
+  if (use_lrc) return lrc_solve<VT>(idx, Rin, D, b, ld, tol_rel, tol_rel * 0.1, max_iter, iters, s);
+  // shares the scratch of the large-block M11 solve (never live at once)
+  return cg_solve<VT>(idx.W, idx.beta, Rin, ld, idx.n, b, D, thr2_in, max_iter, idx.ws, "L",
+                      iters, s);
+}
+
+static void rhs_norms(const Csr& W, const int32_t* q, int b, double beta, double* norm2,
+                      double* maxabs, cudaStream_t s) {
+  KATZ_CUDA(cudaMemsetAsync(norm2, 0, sizeof(double) * b, s));
+  KATZ_CUDA(cudaMemsetAsync(maxabs, 0, sizeof(double) * b, s));
+  switch (W.vdt) {
+    case KATZ_UNIT: rhs_norms_kernel<KATZ_UNIT><<<b, 128, 0, s>>>(W, q, beta, norm2, maxabs); break;
+    case KATZ_F64: rhs_norms_kernel<KATZ_F64><<<b, 128, 0, s>>>(W, q, beta, norm2, maxabs); break;
+    case KATZ_F32: rhs_norms_kernel<KATZ_F32><<<b, 128, 0, s>>>(W, q, beta, norm2, maxabs); break;
+    default: rhs_norms_kernel<KATZ_BF16><<<b, 128, 0, s>>>(W, q, beta, norm2, maxabs); break;
+  }
+  KATZ_CHECK_LAUNCH();
+}
+
+static void rhs_add(const Csr& W, const int32_t* q, int b, double beta, const int32_t* pos,
+                    double* R, int64_t ld, cudaStream_t s) {
+  switch (W.vdt) {
+    case KATZ_UNIT: rhs_add_kernel<KATZ_UNIT><<<b, 128, 0, s>>>(W, q, beta, pos, R, ld); break;
+    case KATZ_F64: rhs_add_kernel<KATZ_F64><<<b, 128, 0, s>>>(W, q, beta, pos, R, ld); break;
+    case KATZ_F32: rhs_add_kernel<KATZ_F32><<<b, 128, 0, s>>>(W, q, beta, pos, R, ld); break;
+    default: rhs_add_kernel<KATZ_BF16><<<b, 128, 0, s>>>(W, q, beta, pos, R, ld); break;
+  }
+  KATZ_CHECK_LAUNCH();
+}
+
+// R64 = B - M K64 (FP64) and rr[c] = ||R64_c||^2.
+static void residual64(katz_index& idx, bool use_lrc, const int32_t* q, int b, int64_t ld,
+                       const double* K64, double* R64, double* rr, cudaStream_t s) {
+  const GraphPart& G = use_lrc ? idx.Wp : idx.W;
+  const int32_t* pos = use_lrc ? idx.iperm.p : nullptr;
+  spmm<double>(G.view(), G.heavy.p, G.n_heavy, idx.beta, K64, ld, -1.0, K64, ld, R64, ld, b,
+               nullptr, 0, nullptr, s);
+  rhs_add(idx.W.view(), q, b, idx.beta, pos, R64, ld, s);
+  KATZ_CUDA(cudaMemsetAsync(rr, 0, sizeof(double) * b, s));
+  coldot<double>(R64, ld, R64, ld, idx.n, b, rr, s);
+}
+
+template <class VT>
+static int query_impl(katz_index& idx, bool use_lrc, const int32_t* q, int b,
+                      const katz_query_opts& o, const QueryOut& out, katz_stats* stats,
+                      std::vector<int32_t>& iters, std::vector<double>& relres, cudaStream_t s) {
+  using clk = std::chrono::steady_clock;
+  const auto t0 = clk::now();
+  const int64_t n = idx.n;
+  const int64_t ld = (b + 3) / 4 * 4;
+  const int max_iter = o.max_iter > 0 ? o.max_iter : 2000;
+  const int max_refine = o.max_refine > 0 ? o.max_refine : 12;
+  const bool mixed = o.precision == KATZ_PREC_MIXED;
+  const int32_t* pos = use_lrc ? idx.iperm.p : nullptr;
+  Workspace& ws = idx.ws;
+  iters.assign(b, 0);
+  relres.assign(b, 0.0);
+
+  double* bn2 = ws.get<double>("q.bn2", b);
+  double* bmx = ws.get<double>("q.bmx", b);
+  double* thr2 = ws.get<double>("q.thr2", b);
+  double* thr2_in = ws.get<double>("q.thr2in", b);
+  double* rr = ws.get<double>("q.rr", bpad(b));
+  int* conv = ws.get<int>("q.conv", b);
+  int* nopen = ws.get<int>("q.nopen", 1);
+  rhs_norms(idx.W.view(), q, b, idx.beta, bn2, bmx, s);
+  const double omc = std::max(1e-300, 1.0 - idx.beta * idx.lambda);
+  make_thresholds(bn2, bmx, b, o.tol, o.tol_kind, omc, thr2, s);
+  // inner solves aim below the outer target but not below what the inner
+  // precision can deliver
+  const double tau = (sizeof(VT) == 4) ? 2e-6 : 1e-13;
+  double tol_rel = (o.tol_kind == KATZ_TOL_RESIDUAL) ? o.tol : o.tol * omc;
+  tol_rel = std::max(tol_rel * 0.3, tau);
+
+  // step 0: solve with the exact RHS in the inner precision
+  VT* Rin = ws.get<VT>("q.Rin", size_t(n) * ld);
+  VT* Dv = ws.get<VT>("q.D", size_t(n) * ld);
+  KATZ_CUDA(cudaMemsetAsync(Rin, 0, sizeof(VT) * n * ld, s));
+  build_rhs<VT>(idx.W.view(), q, b, idx.beta, pos, Rin, ld, s);
+  inner_thresholds_kernel<<<1, 1024, 0, s>>>(bn2, thr2, tau, b, conv, thr2_in, nopen);
+  KATZ_CHECK_LAUNCH();
+  const auto t1 = clk::now();
+  int status = inner_solve<VT>(idx, use_lrc, Rin, Dv, b, ld, thr2_in, tol_rel, max_iter, &iters, s);
+  KATZ_CUDA(cudaStreamSynchronize(s));
+  const auto t2 = clk::now();
+  double ms_res = 0;
+  int refine = 0;
+  double* K64 = nullptr;
+  if (status == KATZ_OK || status == KATZ_ENOCONV) {
+    if (mixed || sizeof(VT) == 8) {
+      K64 = ws.get<double>("q.K64", size_t(n) * ld);
+      double* R64 = ws.get<double>("q.R64", size_t(n) * ld);
+      if constexpr (sizeof(VT) == 4)
+        convert_f32_to_f64(reinterpret_cast<const float*>(Dv), ld, K64, ld, n, (int)ld, s);
+      else
+        KATZ_CUDA(cudaMemcpyAsync(K64, Dv, sizeof(double) * n * ld, cudaMemcpyDeviceToDevice, s));
+      for (;;) {
+        const auto r0 = clk::now();
+        residual64(idx, use_lrc, q, b, ld, K64, R64, rr, s);
+        inner_thresholds_kernel<<<1, 1024, 0, s>>>(rr, thr2, tau, b, conv, thr2_in, nopen);
+        KATZ_CHECK_LAUNCH();
+        ++refine;
+        const int open = read_int(nopen, s);
+        ms_res += std::chrono::duration<double, std::milli>(clk::now() - r0).count();
+        if (open == 0) { status = KATZ_OK; break; }
+        if (refine > max_refine) { status = KATZ_ENOCONV; break; }
+        masked_from_f64_kernel<VT><<<flat_blocks(n * ld), 256, 0, s>>>(R64, Rin, ld, n, b, conv);
+        KATZ_CHECK_LAUNCH();
+        const int st = inner_solve<VT>(idx, use_lrc, Rin, Dv, b, ld, thr2_in, tol_rel, max_iter,
+                                       &iters, s);
+        if (st == KATZ_ENOTSPD) { status = st; break; }
+        if constexpr (sizeof(VT) == 4)
+          add_f32_to_f64(reinterpret_cast<const float*>(Dv), ld, K64, ld, n, (int)ld, s);
+        else
+          scale_copy<double>(reinterpret_cast<const double*>(Dv), ld, K64, ld, n, (int)ld, 1.0,
+                             true, s);
+      }
+      std::vector<double> hr(b), hb(b);
+      KATZ_CUDA(cudaMemcpyAsync(hr.data(), rr, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
+      KATZ_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
+      KATZ_CUDA(cudaStreamSynchronize(s));
+      for (int c = 0; c < b; ++c) relres[c] = hb[c] > 0 ? std::sqrt(hr[c] / hb[c]) : std::sqrt(hr[c]);
+    } else {
+      for (int c = 0; c < b; ++c) relres[c] = std::nan("");
+    }
+    // output (node order)
+    if (K64)
+      gather_out_kernel<float><<<flat_blocks(n * b), 256, 0, s>>>(K64, nullptr, ld, pos, n, b, out.K,
+                                                                  out.dtype, out.ldk);
+    else
+      gather_out_kernel<VT><<<flat_blocks(n * b), 256, 0, s>>>(nullptr, Dv, ld, pos, n, b, out.K,
+                                                               out.dtype, out.ldk);
+    KATZ_CHECK_LAUNCH();
+    KATZ_CUDA(cudaStreamSynchronize(s));
+  }
+  const auto t3 = clk::now();
+  if (stats) {
+    int mx = 0;
+    double mr = 0;
+    for (int c = 0; c < b; ++c) {
+      mx = std::max(mx, iters[c]);
+      if (!std::isnan(relres[c])) mr = std::max(mr, relres[c]);
+    }
+    stats->iters = mx;
+    stats->refine_steps = refine;
+    stats->max_rel_res = mr;
+    stats->ms[0] = std::chrono::duration<double, std::milli>(t3 - t0).count();
+    stats->ms[1] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    stats->ms[2] = std::chrono::duration<double, std::milli>(t2 - t1).count();
+    stats->ms[3] = ms_res;
+  }
+  return status;
+}
+
+int run_queries(katz_index& idx, bool use_lrc, const int32_t* q_dev, int b,
+                const katz_query_opts& o, const QueryOut& out, katz_stats* st,
+                std::vector<int32_t>& iters, std::vector<double>& relres, cudaStream_t s) {
+  KATZ_REQUIRE(!use_lrc || idx.lrc, KATZ_EINVAL, "index was built without the LRC part");
+  KATZ_REQUIRE(b > 0 && b <= 1024, KATZ_EINVAL, "b must be in [1, 1024]");
+  if (o.precision == KATZ_PREC_F64)
+    return query_impl<double>(idx, use_lrc, q_dev, b, o, out, st, iters, relres, s);
+  return query_impl<float>(idx, use_lrc, q_dev, b, o, out, st, iters, relres, s);
+}
+
+template int cg_solve<float>(const GraphPart&, double, const float*, int64_t, int64_t, int, float*,
+                             const double*, int, Workspace&, const std::string&,
+                             std::vector<int32_t>*, cudaStream_t);
+template int cg_solve<double>(const GraphPart&, double, const double*, int64_t, int64_t, int,
+                              double*, const double*, int, Workspace&, const std::string&,
+                              std::vector<int32_t>*, cudaStream_t);
+template int m11_solve<double>(katz_index&, const double*, double*, int, int64_t, double, int,
+                               std::vector<int32_t>*, cudaStream_t);
+template int m11_solve<float>(katz_index&, const float*, float*, int, int64_t, double, int,
+                              std::vector<int32_t>*, cudaStream_t);
+
+}  // namespace katz

@@ -1,0 +1,278 @@
+"""Thin ctypes binding of libkatz.so (declared in include/katz.h).
+
+Every function here only marshals arguments: the work happens in the CUDA
+library.  Names match the C entry points.  Device buffers are torch CUDA
+tensors; host buffers may be numpy arrays or CPU tensors (pinned CPU
+tensors copy fastest).  There is no fallback: if libkatz.so is missing or a
+call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkatz.so")
+
+# status codes / element types / modes (mirror include/katz.h)
+KATZ_OK, KATZ_EINVAL, KATZ_ENOTSPD, KATZ_ENOCONV, KATZ_ENOMEM, KATZ_ECUDA = range(6)
+KATZ_UNIT, KATZ_F64, KATZ_F32, KATZ_BF16 = range(4)
+KATZ_PREC_F32, KATZ_PREC_MIXED, KATZ_PREC_F64 = range(3)
+KATZ_TOL_RESIDUAL, KATZ_TOL_ERROR_INF = range(2)
+
+STATUS_NAMES = {0: "KATZ_OK", 1: "KATZ_EINVAL", 2: "KATZ_ENOTSPD", 3: "KATZ_ENOCONV",
+                4: "KATZ_ENOMEM", 5: "KATZ_ECUDA"}
+
+# every exported symbol of include/katz.h
+EXPORTS = ["katz_lambda_max", "katz_index_build", "katz_index_free", "katz_index_get_info",
+           "katz_index_get_partition", "katz_partition", "katz_index_get_sigma", "katz_query_batch",
+           "cg_query_batch", "linkpred_topk", "katz_apply_M", "katz_launch_count",
+           "katz_profile_enable", "katz_profile_read", "katz_last_error"]
+
+
+class KatzError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class katz_csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class katz_build_opts(C.Structure):
+    _fields_ = [("value_dtype", C.c_int32), ("build_lrc", C.c_int32), ("rank", C.c_int32),
+                ("n_hubs", C.c_int32), ("block_max", C.c_int32), ("split", C.c_int32),
+                ("lanczos_steps", C.c_int32), ("n2_max", C.c_int32), ("seed", C.c_uint64)]
+
+
+class katz_query_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("tol_kind", C.c_int32), ("precision", C.c_int32),
+                ("max_iter", C.c_int32), ("max_refine", C.c_int32), ("rhs_width", C.c_int32),
+                ("warm_start", C.c_int32)]
+
+
+class katz_stats(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("refine_steps", C.c_int32), ("max_rel_res", C.c_double),
+                ("ms", C.c_double * 8)]
+
+
+class katz_index_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("n1", C.c_int64), ("n2", C.c_int64),
+                ("n_blocks", C.c_int32), ("n_large_blocks", C.c_int32), ("rank", C.c_int32),
+                ("value_dtype", C.c_int32), ("beta", C.c_double), ("lambda_max_R", C.c_double),
+                ("device_bytes", C.c_int64)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded library; raises if libkatz.so has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1912_06525_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        L.katz_lambda_max.argtypes = [C.POINTER(katz_csr), i32, C.POINTER(dbl), vp]
+        L.katz_index_build.argtypes = [C.POINTER(katz_csr), dbl, C.POINTER(katz_build_opts), vp,
+                                       C.POINTER(vp)]
+        L.katz_index_free.argtypes = [vp]
+        L.katz_index_free.restype = None
+        L.katz_index_get_info.argtypes = [vp, C.POINTER(katz_index_info)]
+        L.katz_index_get_partition.argtypes = [vp, vp, vp]
+        L.katz_index_get_sigma.argtypes = [vp, vp]
+        L.katz_partition.argtypes = [C.POINTER(katz_csr), i32, i32, i32, vp, vp, vp, vp]
+        qargs = [vp, vp, i32, C.POINTER(katz_query_opts), vp, i32, i64, C.POINTER(katz_stats),
+                 vp, vp, vp]
+        L.katz_query_batch.argtypes = qargs
+        L.cg_query_batch.argtypes = qargs
+        L.linkpred_topk.argtypes = [vp, vp, i32, vp, i32, i64, i32, vp, vp, vp]
+        L.katz_apply_M.argtypes = [vp, vp, vp, i32, i32, vp]
+        L.katz_launch_count.argtypes = []
+        L.katz_launch_count.restype = C.c_int64
+        L.katz_profile_enable.argtypes = [i32]
+        L.katz_profile_read.argtypes = [C.c_char_p, vp, vp, vp]
+        L.katz_last_error.restype = C.c_char_p
+        for name in EXPORTS:
+            if name not in ("katz_index_free", "katz_last_error", "katz_launch_count"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def katz_last_error() -> str:
+    return lib().katz_last_error().decode()
+
+
+def _check(code: int, allow=(KATZ_OK,)) -> int:
+    if code not in allow:
+        raise KatzError(code, katz_last_error())
+    return code
+
+
+def _ptr(x):
+    """Address of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _csr(graph):
+    """katz_csr from an object with n, rowptr, col, val (val None = unit)."""
+    rowptr = np.ascontiguousarray(graph.rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(graph.col, dtype=np.int32)
+    val = None if graph.val is None else np.ascontiguousarray(graph.val, dtype=np.float64)
+    c = katz_csr(int(graph.n), int(rowptr[-1]), rowptr.ctypes.data, col.ctypes.data,
+                 None if val is None else val.ctypes.data)
+    return c, (rowptr, col, val)
+
+
+def katz_lambda_max(graph, steps: int = 0, stream=None) -> float:
+    c, keep = _csr(graph)
+    out = C.c_double()
+    _check(lib().katz_lambda_max(C.byref(c), steps, C.byref(out), _stream(stream)))
+    return out.value
+
+
+class KatzIndex:
+    """Owner of a katz_index* (freed on garbage collection)."""
+
+    def __init__(self, handle: int):
+        self.handle = C.c_void_p(handle)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.katz_index_free(self.handle)
+            self.handle = C.c_void_p(0)
+
+    def info(self) -> dict:
+        return katz_index_get_info(self)
+
+
+def katz_index_build(graph, beta: float, value_dtype: int = KATZ_F32, build_lrc: bool = True,
+                     rank: int = 16, n_hubs: int = 0, block_max: int = 64, split: bool = True,
+                     lanczos_steps: int = 0, n2_max: int = 0, seed: int = 20191212,
+                     stream=None) -> KatzIndex:
+    c, keep = _csr(graph)
+    o = katz_build_opts(value_dtype, int(build_lrc), rank, n_hubs, block_max, int(split),
+                        lanczos_steps, n2_max, seed)
+    h = C.c_void_p()
+    _check(lib().katz_index_build(C.byref(c), float(beta), C.byref(o), _stream(stream),
+                                  C.byref(h)))
+    return KatzIndex(h.value)
+
+
+def katz_index_get_info(index: KatzIndex) -> dict:
+    i = katz_index_info()
+    _check(lib().katz_index_get_info(index.handle, C.byref(i)))
+    return {f: getattr(i, f) for f, _ in katz_index_info._fields_}
+
+
+def katz_index_get_partition(index: KatzIndex):
+    info = katz_index_get_info(index)
+    perm = np.empty(info["n"], dtype=np.int64)
+    bp = np.empty(info["n_blocks"] + 1, dtype=np.int64)
+    _check(lib().katz_index_get_partition(index.handle, perm.ctypes.data, bp.ctypes.data))
+    return perm, bp, info["n1"], info["n2"]
+
+
+def katz_partition(graph, n_hubs: int, block_max: int, split: bool = True):
+    """Host-only partition; returns (perm, block_ptr, n1, n2)."""
+    c, keep = _csr(graph)
+    perm = np.empty(graph.n, dtype=np.int64)
+    bp = np.empty(graph.n + 1, dtype=np.int64)
+    nb = np.zeros(1, dtype=np.int64)
+    n1 = np.zeros(1, dtype=np.int64)
+    _check(lib().katz_partition(C.byref(c), n_hubs, block_max, int(split), perm.ctypes.data,
+                                bp.ctypes.data, nb.ctypes.data, n1.ctypes.data))
+    return perm, bp[: int(nb[0]) + 1].copy(), int(n1[0]), graph.n - int(n1[0])
+
+
+def katz_index_get_sigma(index: KatzIndex) -> np.ndarray:
+    info = katz_index_get_info(index)
+    s = np.empty(max(info["rank"], 1), dtype=np.float64)
+    _check(lib().katz_index_get_sigma(index.handle, s.ctypes.data))
+    return s[: info["rank"]]
+
+
+def _query(fn, index, q, K_out, out_dtype, tol, tol_kind, precision, max_iter, max_refine,
+           rhs_width, warm_start, stream):
+    b = int(q.shape[0])
+    o = katz_query_opts(float(tol), tol_kind, precision, max_iter, max_refine, rhs_width,
+                        warm_start)
+    st = katz_stats()
+    iters = np.zeros(b, dtype=np.int32)
+    rel = np.zeros(b, dtype=np.float64)
+    ldk = int(K_out.stride(0)) if hasattr(K_out, "stride") else int(K_out.strides[0] // K_out.itemsize)
+    code = fn(index.handle, _ptr(q), b, C.byref(o), _ptr(K_out), out_dtype, ldk, C.byref(st),
+              iters.ctypes.data, rel.ctypes.data, _stream(stream))
+    _check(code, allow=(KATZ_OK, KATZ_ENOCONV))
+    stats = {"iters": st.iters, "refine_steps": st.refine_steps, "max_rel_res": st.max_rel_res,
+             "ms": list(st.ms), "status": STATUS_NAMES[code]}
+    return stats, iters, rel
+
+
+def katz_query_batch(index, q, K_out, out_dtype=KATZ_F32, tol=1e-6,
+                     tol_kind=KATZ_TOL_ERROR_INF, precision=KATZ_PREC_MIXED, max_iter=0,
+                     max_refine=0, rhs_width=0, warm_start=0, stream=None):
+    """LRC-Katz (Algorithm 2).  q: int32 (b,) host or device; K_out: (n, b)
+    node-major float32/float64, host or device.  Returns (stats, iters, rel_res)."""
+    return _query(lib().katz_query_batch, index, q, K_out, out_dtype, tol, tol_kind, precision,
+                  max_iter, max_refine, rhs_width, warm_start, stream)
+
+
+def cg_query_batch(index, q, K_out, out_dtype=KATZ_F32, tol=1e-6, tol_kind=KATZ_TOL_ERROR_INF,
+                   precision=KATZ_PREC_MIXED, max_iter=0, max_refine=0, rhs_width=0,
+                   warm_start=0, stream=None):
+    """Plain CG on M (the comparison method); same contract as katz_query_batch."""
+    return _query(lib().cg_query_batch, index, q, K_out, out_dtype, tol, tol_kind, precision,
+                  max_iter, max_refine, rhs_width, warm_start, stream)
+
+
+def linkpred_topk(index, q, K, k_dtype, k, ids_out, scores_out, stream=None):
+    """Top-k link candidates per query column of K (Section 3.3)."""
+    b = int(q.shape[0])
+    ldk = int(K.stride(0)) if hasattr(K, "stride") else int(K.strides[0] // K.itemsize)
+    _check(lib().linkpred_topk(index.handle, _ptr(q), b, _ptr(K), k_dtype, ldk, k,
+                               _ptr(ids_out), _ptr(scores_out), _stream(stream)))
+
+
+def katz_apply_M(index, X, Y, b, dtype, stream=None):
+    """Y = M X = X - beta W X (device n x b blocks)."""
+    _check(lib().katz_apply_M(index.handle, _ptr(X), _ptr(Y), b, dtype, _stream(stream)))
+
+
+def katz_launch_count() -> int:
+    return int(lib().katz_launch_count())
+
+
+def katz_profile_enable(on: bool) -> None:
+    _check(lib().katz_profile_enable(int(on)))
+
+
+def katz_profile_read(tag: str) -> dict:
+    n = np.zeros(1, dtype=np.int64)
+    ms = np.zeros(1, dtype=np.float64)
+    by = np.zeros(1, dtype=np.float64)
+    _check(lib().katz_profile_read(tag.encode(), n.ctypes.data, ms.ctypes.data, by.ctypes.data))
+    return {"launches": int(n[0]), "ms": float(ms[0]), "bytes": float(by[0])}
