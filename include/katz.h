@@ -202,6 +202,17 @@ int linkpred_topk(const katz_index* idx, const int32_t* q, int32_t b,
 int katz_apply_M(const katz_index* idx, const void* X, void* Y, int32_t b,
                  int32_t dtype, void* stream);
 
+/* D = A * B^T on the tcgen05 tensor cores (BF16 operands, FP32
+ * accumulation in tensor memory): the kernel used for the rank-r
+ * correction products W^ (W^T R) of the preconditioner (Eq. 14), exposed
+ * for step-level testing.  A (M x K) and B (N x K) are device BF16
+ * row-major with K contiguous, row strides lda/ldb multiples of 8 elements,
+ * 16-byte aligned.  C (device FP32, M x N, ldc) = alpha*D + beta*C.
+ * Errors: KATZ_EINVAL on bad shapes/alignment, KATZ_ECUDA if the pipeline
+ * reported a timeout. */
+int katz_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int32_t M, int32_t N,
+                   int32_t K, float alpha, float beta, float* C, int64_t ldc, void* stream);
+
 /* ---------------------------------------------------------- measurement */
 
 /* Number of kernels this library has launched in this process (all calls). */

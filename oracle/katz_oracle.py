@@ -295,26 +295,37 @@ class _M11Solver:
         return Y
 
 
-def _lanczos_top(apply_R, n2: int, rank: int, steps: int, v0: np.ndarray):
+def _lanczos_top(apply_R, n2: int, rank: int, steps: int, v0: np.ndarray,
+                 res_tol: float = 1e-8):
     """Lanczos on the symmetric operator R with full reorthogonalisation
     (Algorithm 1, the Lanczos line, with R applied as a matrix-vector
-    product).  Returns the ``rank`` largest Ritz values (descending) and
-    their Ritz vectors (n2 x rank)."""
-    m = min(steps, n2)
-    V = np.zeros((n2, m + 1))
-    alpha = np.zeros(m)
-    beta = np.zeros(m)
+    product).  At least ``steps`` steps; then extended until the top
+    ``rank`` Ritz pairs have residual estimates beta_m |y_m,i| <=
+    res_tol * max(1, |theta_i|), or the Krylov space is exhausted.  Returns
+    the ``rank`` largest Ritz values (descending) and their Ritz vectors."""
+    cap = n2
+    V = np.zeros((n2, cap + 1))
+    alpha = np.zeros(cap)
+    beta = np.zeros(cap)
     V[:, 0] = v0 / np.linalg.norm(v0)
-    k = m
-    for j in range(m):
+    k = 0
+    check = min(steps, cap)
+    for j in range(cap):
         w = apply_R(V[:, j])
         alpha[j] = V[:, j] @ w
         w -= V[:, : j + 1] @ (V[:, : j + 1].T @ w)
         w -= V[:, : j + 1] @ (V[:, : j + 1].T @ w)
         beta[j] = np.linalg.norm(w)
+        k = j + 1
         if beta[j] <= 1e-14 * max(1.0, abs(alpha[j])):
-            k = j + 1
             break
+        if k >= check:
+            T = np.diag(alpha[:k]) + np.diag(beta[: k - 1], 1) + np.diag(beta[: k - 1], -1)
+            theta, Y = np.linalg.eigh(T)
+            top = np.argsort(-theta)[:rank]
+            if np.all(beta[j] * np.abs(Y[-1, top]) <= res_tol * np.maximum(1.0, np.abs(theta[top]))):
+                break
+            check = k + max(10, k // 2)
         V[:, j + 1] = w / beta[j]
     T = np.diag(alpha[:k]) + np.diag(beta[: k - 1], 1) + np.diag(beta[: k - 1], -1)
     theta, Y = np.linalg.eigh(T)

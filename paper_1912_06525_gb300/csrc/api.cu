@@ -6,6 +6,7 @@
 
 #include "index.h"
 #include "kernels_dense.h"
+#include "tc_gemm.h"
 
 namespace {
 
@@ -94,8 +95,10 @@ katz::HostCsr read_csr(const katz_csr* W) {
   return h;
 }
 
-// Device copy of the query ids (validated against n).
-const int32_t* stage_queries(katz_index* idx, const int32_t* q, int32_t b, cudaStream_t s) {
+// Device copy of the query ids (validated against n); the host copy is
+// returned in *host when given.
+const int32_t* stage_queries(katz_index* idx, const int32_t* q, int32_t b, cudaStream_t s,
+                             std::vector<int32_t>* host = nullptr) {
   KATZ_REQUIRE(q != nullptr && b > 0, KATZ_EINVAL, "empty query list");
   std::vector<int32_t> h(b);
   if (is_device_ptr(q)) {
@@ -109,6 +112,8 @@ const int32_t* stage_queries(katz_index* idx, const int32_t* q, int32_t b, cudaS
                  "query id " + std::to_string(h[j]) + " out of range");
   int32_t* d = idx->ws.get<int32_t>("api.q", b);
   KATZ_CUDA(cudaMemcpyAsync(d, h.data(), 4 * size_t(b), cudaMemcpyHostToDevice, s));
+  KATZ_CUDA(cudaStreamSynchronize(s));
+  if (host) *host = h;
   return d;
 }
 
@@ -122,7 +127,8 @@ int do_query(const katz_index* cidx, bool lrc, const int32_t* q, int32_t b,
     KATZ_REQUIRE(opts->tol > 0, KATZ_EINVAL, "tol must be positive");
     katz_index* idx = const_cast<katz_index*>(cidx);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int32_t* qd = stage_queries(idx, q, b, s);
+    std::vector<int32_t> qh;
+    const int32_t* qd = stage_queries(idx, q, b, s, &qh);
     katz::QueryOut out;
     out.dtype = out_dtype;
     out.ldk = ldk;
@@ -135,7 +141,7 @@ int do_query(const katz_index* cidx, bool lrc, const int32_t* q, int32_t b,
     }
     std::vector<int32_t> it;
     std::vector<double> rr;
-    const int st = katz::run_queries(*idx, lrc, qd, b, *opts, out, stats, it, rr, s);
+    const int st = katz::run_queries(*idx, lrc, qd, qh.data(), b, *opts, out, stats, it, rr, s);
     if (!dev && (st == KATZ_OK || st == KATZ_ENOCONV)) {
       KATZ_CUDA(cudaMemcpyAsync(K_out, out.K, es * size_t(idx->n) * ldk, cudaMemcpyDeviceToHost, s));
       KATZ_CUDA(cudaStreamSynchronize(s));
@@ -306,6 +312,27 @@ int linkpred_topk(const katz_index* cidx, const int32_t* q, int32_t b, const voi
     if (!dev_sc)
       KATZ_CUDA(cudaMemcpyAsync(scores_out, sc, 8 * size_t(b) * k, cudaMemcpyDeviceToHost, s));
     KATZ_CUDA(cudaStreamSynchronize(s));
+    return KATZ_OK;
+  });
+}
+
+int katz_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int32_t M, int32_t N,
+                   int32_t K, float alpha, float beta, float* C, int64_t ldc, void* stream) {
+  return guarded([&]() {
+    KATZ_REQUIRE(A && B && C && M > 0 && N > 0 && K > 0, KATZ_EINVAL, "bad GEMM arguments");
+    KATZ_REQUIRE(lda >= K && ldb >= K && ldc >= N && lda % 8 == 0 && ldb % 8 == 0, KATZ_EINVAL,
+                 "GEMM strides: lda, ldb >= K and multiples of 8; ldc >= N");
+    KATZ_REQUIRE(is_device_ptr(A) && is_device_ptr(B) && is_device_ptr(C), KATZ_EINVAL,
+                 "GEMM operands must be device memory");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    katz::DBuf<int> err(1);
+    KATZ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    katz::tc_gemm(static_cast<const __nv_bfloat16*>(A), lda, static_cast<const __nv_bfloat16*>(B),
+                  ldb, M, N, K, alpha, beta, C, ldc, nullptr, 0, 0, err.p, s);
+    int h = 0;
+    KATZ_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KATZ_CUDA(cudaStreamSynchronize(s));
+    KATZ_REQUIRE(h == 0, KATZ_ECUDA, "tcgen05 GEMM pipeline timed out");
     return KATZ_OK;
   });
 }

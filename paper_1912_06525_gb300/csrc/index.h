@@ -58,6 +58,7 @@ struct Partition {
 struct katz_index {
   int64_t n = 0, nnz = 0;
   double beta = 0, lambda = 0;
+  std::vector<int32_t> deg_h;  // node degrees (host), bound the RHS fix-up grid
   int vdt = KATZ_UNIT;
   katz::GraphPart W;  // node order
 
@@ -76,7 +77,12 @@ struct katz_index {
   int64_t ld2 = 0;  // leading dimension of the dense n2 x n2 objects
   katz::DBuf<float> S32, M22inv32, Wr32;  // Wr scaled by sqrt(sigma/(1-sigma)) per column
   katz::DBuf<double> S64, M22inv64, Wr64;
+  // BF16 copies of W^ for the tcgen05 rank-r products: Wb (n2 x ldr) and
+  // WbT (r x ldn2), row strides multiples of 8 elements
+  katz::DBuf<__nv_bfloat16> Wb, WbT;
+  int64_t ldr = 0, ldn2 = 0;
   std::vector<double> sigma;
+  int lanczos_steps = 0;
 
   katz::Workspace ws;
 };
@@ -100,7 +106,7 @@ struct QueryOut {
 
 // Runs a batch of queries (q on device) by LRC (use_lrc) or plain CG and
 // writes K (device).  Fills per-column iterations / residuals (host).
-int run_queries(katz_index& idx, bool use_lrc, const int32_t* q_dev, int b,
+int run_queries(katz_index& idx, bool use_lrc, const int32_t* q_dev, const int32_t* q_host, int b,
                 const katz_query_opts& o, const QueryOut& out, katz_stats* st,
                 std::vector<int32_t>& iters, std::vector<double>& relres, cudaStream_t s);
 

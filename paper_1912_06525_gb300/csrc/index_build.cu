@@ -197,52 +197,60 @@ Partition partition_graph(const HostCsr& W, int64_t n_hubs, int64_t block_max, b
   return p;
 }
 
-// ------------------------------------------------------- Jacobi eigen (host)
-// Symmetric eigen-decomposition of a small dense matrix by cyclic Jacobi
-// rotations (Golub and Van Loan, Sec. 8.5).  A (m x m, row-major) is
-// destroyed; eigenvalues in w, eigenvectors in the columns of V.
-static void jacobi_eig(std::vector<double>& A, int m, std::vector<double>& w,
-                       std::vector<double>& V) {
-  V.assign(size_t(m) * m, 0.0);
-  for (int i = 0; i < m; ++i) V[size_t(i) * m + i] = 1.0;
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0, tot = 0;
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) {
-        const double a = A[size_t(i) * m + j];
-        tot += a * a;
-        if (i != j) off += a * a;
+// -------------------------------------------- tridiagonal eigen (host)
+// Eigen-decomposition of the symmetric tridiagonal Lanczos matrix by
+// implicit-shift QL iterations (Golub and Van Loan, Sec. 8.3): d = diagonal,
+// e = sub-diagonal; on return d holds the eigenvalues and column j of Z
+// (k x k, row-major) the eigenvector of d[j].
+static void tridiag_ql(std::vector<double>& d, std::vector<double> e, std::vector<double>& Z, int k) {
+  e.resize(k, 0.0);
+  Z.assign(size_t(k) * k, 0.0);
+  for (int i = 0; i < k; ++i) Z[size_t(i) * k + i] = 1.0;
+  for (int l = 0; l < k; ++l) {
+    for (int iter = 0;; ++iter) {
+      int m = l;
+      for (; m < k - 1; ++m) {
+        const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+        if (std::fabs(e[m]) <= 1e-16 * dd) break;
       }
-    if (off <= 1e-30 * tot || off == 0.0) break;
-    for (int p = 0; p < m - 1; ++p)
-      for (int q = p + 1; q < m; ++q) {
-        const double apq = A[size_t(p) * m + q];
-        if (std::fabs(apq) < 1e-300) continue;
-        const double app = A[size_t(p) * m + p], aqq = A[size_t(q) * m + q];
-        const double theta = (aqq - app) / (2.0 * apq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
-        for (int k = 0; k < m; ++k) {  // columns p, q
-          const double akp = A[size_t(k) * m + p], akq = A[size_t(k) * m + q];
-          A[size_t(k) * m + p] = c * akp - sn * akq;
-          A[size_t(k) * m + q] = sn * akp + c * akq;
+      if (m == l) break;
+      if (iter > 200) throw std::runtime_error("tridiagonal QL did not converge");
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = std::hypot(g, 1.0);
+      g = d[m] - d[l] + e[l] / (g + std::copysign(r, g));
+      double s = 1.0, c = 1.0, p = 0.0;
+      bool split = false;
+      for (int i = m - 1; i >= l; --i) {
+        double f = s * e[i];
+        const double bb = c * e[i];
+        r = std::hypot(f, g);
+        e[i + 1] = r;
+        if (r == 0.0) {
+          d[i + 1] -= p;
+          e[m] = 0.0;
+          split = true;
+          break;
         }
-        for (int k = 0; k < m; ++k) {  // rows p, q
-          const double apk = A[size_t(p) * m + k], aqk = A[size_t(q) * m + k];
-          A[size_t(p) * m + k] = c * apk - sn * aqk;
-          A[size_t(q) * m + k] = sn * apk + c * aqk;
-        }
-        for (int k = 0; k < m; ++k) {
-          const double vkp = V[size_t(k) * m + p], vkq = V[size_t(k) * m + q];
-          V[size_t(k) * m + p] = c * vkp - sn * vkq;
-          V[size_t(k) * m + q] = sn * vkp + c * vkq;
+        s = f / r;
+        c = g / r;
+        g = d[i + 1] - p;
+        r = (d[i] - g) * s + 2.0 * c * bb;
+        p = s * r;
+        d[i + 1] = g + p;
+        g = c * r - bb;
+        for (int t = 0; t < k; ++t) {
+          f = Z[size_t(t) * k + i + 1];
+          Z[size_t(t) * k + i + 1] = s * Z[size_t(t) * k + i] + c * f;
+          Z[size_t(t) * k + i] = c * Z[size_t(t) * k + i] - s * f;
         }
       }
+      if (split) continue;
+      d[l] -= p;
+      e[l] = g;
+      e[m] = 0.0;
+    }
   }
-  w.resize(m);
-  for (int i = 0; i < m; ++i) w[i] = A[size_t(i) * m + i];
 }
-
 static std::vector<double> splitmix64_uniform(uint64_t seed, int64_t count) {
   std::vector<double> out(count);
   for (int64_t i = 0; i < count; ++i) {
@@ -297,12 +305,9 @@ double lambda_max_gpu(const GraphPart& W, int64_t n, int steps, Workspace& ws, c
     bprev = bn;
   }
   const int m = (int)al.size();
-  std::vector<double> T(size_t(m) * m, 0.0), ev, V;
-  for (int i = 0; i < m; ++i) {
-    T[size_t(i) * m + i] = al[i];
-    if (i + 1 < m) T[size_t(i) * m + i + 1] = T[size_t(i + 1) * m + i] = be[i];
-  }
-  jacobi_eig(T, m, ev, V);
+  std::vector<double> ev(al), Z;
+  be.resize(std::max(0, m - 1));
+  tridiag_ql(ev, be, Z, m);
   return *std::max_element(ev.begin(), ev.end());
 }
 
@@ -348,6 +353,8 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   idx.nnz = W.nnz();
   idx.beta = beta;
   idx.vdt = o.value_dtype;
+  idx.deg_h.resize(W.nrows);
+  for (int64_t i = 0; i < W.nrows; ++i) idx.deg_h[i] = (int32_t)(W.rowptr[i + 1] - W.rowptr[i]);
   upload_part(W, o.value_dtype, idx.W, s);
   idx.lambda = lambda_max_gpu(idx.W, idx.n, 96, idx.ws, s);
   KATZ_REQUIRE(beta * idx.lambda < 1.0, KATZ_ENOTSPD,
@@ -558,7 +565,9 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
     const int r = (int)std::min<int64_t>(idx.rank, n2);
     int m = o.lanczos_steps > 0 ? o.lanczos_steps : std::max(2 * r, r + 20);
     m = (int)std::min<int64_t>(std::max(m, r), n2);
-    const int64_t ldq = m + 1;
+    // capacity for extending past m until the top-r Ritz residuals converge
+    const int cap = (int)std::min<int64_t>(n2, std::max(4 * m, m + 200));
+    const int64_t ldq = cap + 1;
     DBuf<double> Q(size_t(n2) * ldq), t(n2), wv(n2), u(n2), cvec(ldq), sc(2);
     std::vector<double> v0 = splitmix64_uniform(o.seed, n2);
     KATZ_CUDA(cudaMemcpyAsync(wv.p, v0.data(), 8 * n2, cudaMemcpyHostToDevice, s));
@@ -569,9 +578,9 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
     };
     double nrm = std::sqrt(mdot(wv.p, wv.p));
     copy2d<double>(wv.p, 1, Q.p, ldq, n2, 1, 1.0 / nrm, s);
-    std::vector<double> al, be;
-    int k = m;
-    for (int j = 0; j < m; ++j) {
+    std::vector<double> al, be, ev, Y;
+    int check = m;
+    for (int j = 0; j < cap; ++j) {
       // t = T q_j ; w = M22^{-1} t
       gemm<double>(false, n2, 1, n2, 1.0, T.p, ld2, Q.p + j, ldq, 0.0, t.p, 1, s);
       gemm<double>(false, n2, 1, n2, 1.0, idx.M22inv64.p, ld2, t.p, 1, 0.0, wv.p, 1, s);
@@ -584,18 +593,32 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
         gemm<double>(false, n2, 1, j + 1, -1.0, Q.p, ldq, cvec.p, 1, 1.0, wv.p, 1, s);
       }
       const double bj = std::sqrt(std::max(0.0, mdot(wv.p, wv.p)));
-      if (j == m - 1) break;
-      if (bj <= 1e-14 * std::max(1.0, std::fabs(al.back()))) { k = j + 1; break; }
+      const int kk = j + 1;
+      if (bj <= 1e-14 * std::max(1.0, std::fabs(al.back()))) break;  // invariant subspace
+      if (kk >= check || kk == cap) {
+        // residual estimates beta_k |y_k,i| of the top-r Ritz pairs
+        ev = al;
+        std::vector<double> sub(be);
+        tridiag_ql(ev, sub, Y, kk);
+        std::vector<int> o2(kk);
+        std::iota(o2.begin(), o2.end(), 0);
+        std::sort(o2.begin(), o2.end(), [&](int a, int b) { return ev[a] > ev[b]; });
+        bool ok = true;
+        for (int c = 0; c < std::min(r, kk); ++c)
+          ok &= bj * std::fabs(Y[size_t(kk - 1) * kk + o2[c]]) <=
+                1e-8 * std::max(1.0, std::fabs(ev[o2[c]]));
+        if (ok || kk == cap) break;
+        check = kk + std::max(10, kk / 2);
+      }
       be.push_back(bj);
       copy2d<double>(wv.p, 1, Q.p + j + 1, ldq, n2, 1, 1.0 / bj, s);
     }
-    k = (int)al.size();
-    std::vector<double> Tm(size_t(k) * k, 0.0), ev, Y;
-    for (int i = 0; i < k; ++i) {
-      Tm[size_t(i) * k + i] = al[i];
-      if (i + 1 < k) Tm[size_t(i) * k + i + 1] = Tm[size_t(i + 1) * k + i] = be[i];
+    const int k = (int)al.size();
+    ev = al;
+    {
+      std::vector<double> sub(be.begin(), be.begin() + std::max(0, k - 1));
+      tridiag_ql(ev, sub, Y, k);
     }
-    jacobi_eig(Tm, k, ev, Y);
     std::vector<int> ordr(k);
     std::iota(ordr.begin(), ordr.end(), 0);
     std::sort(ordr.begin(), ordr.end(), [&](int a, int b) { return ev[a] > ev[b]; });
@@ -606,6 +629,7 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
       idx.sigma.push_back(ev[ordr[c]]);
       for (int i = 0; i < k; ++i) Ysel[size_t(i) * rk + c] = Y[size_t(i) * k + ordr[c]];
     }
+    idx.lanczos_steps = k;
     DBuf<double> Yd(Ysel.size()), Wd(size_t(n2) * rk);
     KATZ_CUDA(cudaMemcpyAsync(Yd.p, Ysel.data(), 8 * Ysel.size(), cudaMemcpyHostToDevice, s));
     gemm<double>(false, n2, rk, k, 1.0, Q.p, ldq, Yd.p, rk, 0.0, Wd.p, rk, s);
@@ -622,6 +646,21 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
         Wf[size_t(i) * rk + c] = float(Wh[size_t(i) * rk + c]);
       }
     }
+    // BF16 copies for the tensor-core products
+    idx.ldr = (rk + 7) / 8 * 8;
+    idx.ldn2 = (n2 + 7) / 8 * 8;
+    std::vector<__nv_bfloat16> wb(size_t(n2) * idx.ldr, __float2bfloat16(0.f)),
+        wbt(size_t(rk) * idx.ldn2, __float2bfloat16(0.f));
+    for (int64_t i = 0; i < n2; ++i)
+      for (int c = 0; c < rk; ++c) {
+        const __nv_bfloat16 v = __double2bfloat16(Wh[size_t(i) * rk + c]);
+        wb[size_t(i) * idx.ldr + c] = v;
+        wbt[size_t(c) * idx.ldn2 + i] = v;
+      }
+    idx.Wb.alloc(wb.size());
+    idx.WbT.alloc(wbt.size());
+    KATZ_CUDA(cudaMemcpyAsync(idx.Wb.p, wb.data(), 2 * wb.size(), cudaMemcpyHostToDevice, s));
+    KATZ_CUDA(cudaMemcpyAsync(idx.WbT.p, wbt.data(), 2 * wbt.size(), cudaMemcpyHostToDevice, s));
     idx.Wr64.alloc(Wh.size());
     idx.Wr32.alloc(Wf.size());
     KATZ_CUDA(cudaMemcpyAsync(idx.Wr64.p, Wh.data(), 8 * Wh.size(), cudaMemcpyHostToDevice, s));

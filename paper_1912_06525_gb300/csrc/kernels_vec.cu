@@ -34,6 +34,17 @@ __device__ __forceinline__ void vload(const VT* p, VT (&o)[VecOf<VT>::width]) {
     o[0] = v.x; o[1] = v.y;
   }
 }
+// read-only (non-coherent) load for operands no thread of the kernel writes
+template <class VT>
+__device__ __forceinline__ void vload_ro(const VT* p, VT (&o)[VecOf<VT>::width]) {
+  using V = typename VecOf<VT>::type;
+  V v = __ldg(reinterpret_cast<const V*>(p));
+  if constexpr (VecOf<VT>::width == 4) {
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  } else {
+    o[0] = v.x; o[1] = v.y;
+  }
+}
 template <class VT>
 __device__ __forceinline__ void vstore(VT* p, const VT (&o)[VecOf<VT>::width]) {
   using V = typename VecOf<VT>::type;
@@ -118,7 +129,7 @@ __global__ void __launch_bounds__(256) spmm_rows_kernel(SpmmParams<VT> p) {
         for (int v = 0; v < VPT; ++v) {
           if (cval[v]) {
             VT xv[VW];
-            vload<VT>(xr + v * TPR * VW, xv);
+            vload_ro<VT>(xr + v * TPR * VW, xv);
 #pragma unroll
             for (int w = 0; w < VW; ++w) acc[v][w] += wv * xv[w];
           }
@@ -201,7 +212,7 @@ __global__ void __launch_bounds__(256) spmm_heavy_kernel(SpmmParams<VT> p, const
       const A wv = __shfl_sync(0xffffffffu, wj, s);
       if (cv) {
         VT xv[VW];
-        vload<VT>(p.X + int64_t(j) * p.ldx + c, xv);
+        vload_ro<VT>(p.X + int64_t(j) * p.ldx + c, xv);
 #pragma unroll
         for (int w = 0; w < VW; ++w) acc[w] += wv * xv[w];
       }
@@ -254,7 +265,9 @@ static void spmm_dispatch(SpmmParams<VT>& p, const int32_t* heavy, int64_t n_hea
   int tpr = 1;
   while (tpr < 32 && tpr < nvec) tpr *= 2;
   int vpt = 1;
-  const int vcap = cfg.col_tile > 0 ? max(1, cfg.col_tile / (VW * 32)) : (sizeof(VT) == 4 ? 8 : 8);
+  // columns per warp-row tile: 256 floats / 128 doubles by default, so the
+  // accumulators and fused dot partials stay in registers without spills
+  const int vcap = cfg.col_tile > 0 ? max(1, cfg.col_tile / (VW * 32)) : 2;
   if (tpr == 32)
     while (vpt < vcap && vpt * 32 < nvec) vpt *= 2;
   const int tile = tpr * VW * vpt;
@@ -369,7 +382,8 @@ __device__ __forceinline__ void reduce_cols_atomic(double (&part)[VW], double* o
 }
 
 template <class VT>
-__global__ void coldot_kernel(const VT* A, int64_t lda, const VT* B, int64_t ldb, int64_t len,
+__global__ void coldot_kernel(const VT* __restrict__ A, int64_t lda, const VT* __restrict__ B,
+                              int64_t ldb, int64_t len,
                               int b, double* dots) {
   constexpr int VW = VecOf<VT>::width;
   const int64_t c = (int64_t(blockIdx.y) * blockDim.x + threadIdx.x) * VW;
@@ -414,7 +428,8 @@ template void coldot<double>(const double*, int64_t, const double*, int64_t, int
 
 // ------------------------------------------------------------ CG updates
 template <class VT, bool ACC_RR>
-__global__ void cg_update_xr_kernel(VT* X, const VT* P, VT* R, const VT* Q, int64_t ld,
+__global__ void cg_update_xr_kernel(VT* __restrict__ X, const VT* __restrict__ P,
+                                    VT* __restrict__ R, const VT* __restrict__ Q, int64_t ld,
                                     int64_t len, int b, ColState st) {
   constexpr int VW = VecOf<VT>::width;
   const int64_t c = (int64_t(blockIdx.y) * blockDim.x + threadIdx.x) * VW;
@@ -485,7 +500,8 @@ template void cg_update_xr<double>(double*, const double*, double*, const double
                                    int64_t, int, const ColState&, bool, cudaStream_t);
 
 template <class VT>
-__global__ void cg_update_p_kernel(VT* P, const VT* Z, int64_t ld, int64_t len, int b,
+__global__ void cg_update_p_kernel(VT* __restrict__ P, const VT* __restrict__ Z, int64_t ld,
+                                   int64_t len, int b,
                                    ColState st) {
   constexpr int VW = VecOf<VT>::width;
   const int64_t c = (int64_t(blockIdx.y) * blockDim.x + threadIdx.x) * VW;

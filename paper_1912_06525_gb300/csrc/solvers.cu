@@ -6,7 +6,9 @@
 #include <cmath>
 
 #include "index.h"
+#include "ff_residual.h"
 #include "kernels_dense.h"
+#include "tc_gemm.h"
 
 namespace katz {
 
@@ -244,11 +246,31 @@ template <> struct Dense<double> {
 };
 
 // Z = S~^{-1} R = M22^{-1} R + W^ (W^T R), with W^ = W_r D^{1/2} (Eq. 14).
+// FP32 path: the two rank-r products run on the tcgen05 tensor cores with
+// BF16 operands (a preconditioner only needs to be a fixed SPD
+// approximation; W^ and R^T are rounded once each, so the correction stays
+// symmetric positive semi-definite up to the FP32 accumulation).
 template <class VT>
-static void precond(const katz_index& idx, const VT* R, VT* Z, VT* Tm, int b, int64_t ld,
+static void precond(katz_index& idx, const VT* R, VT* Z, VT* Tm, int b, int64_t ld,
                     cudaStream_t s) {
   const int64_t n2 = idx.n2;
   gemm<VT>(false, n2, b, n2, 1.0, Dense<VT>::Minv(idx), idx.ld2, R, ld, 0.0, Z, ld, s);
+  if constexpr (sizeof(VT) == 4) {
+    if (idx.rank > 0) {
+      __nv_bfloat16* Rt = idx.ws.get<__nv_bfloat16>("S.Rt", size_t(b) * idx.ldn2);
+      __nv_bfloat16* Tt = idx.ws.get<__nv_bfloat16>("S.Tt", size_t(b) * idx.ldr);
+      int* err = idx.ws.get<int>("S.err", 1);
+      to_bf16_transposed(reinterpret_cast<const float*>(R), ld, n2, b, Rt, idx.ldn2, s);
+      // Tt (b x r) = (W^T R)^T
+      tc_gemm(idx.WbT.p, idx.ldn2, Rt, idx.ldn2, idx.rank, b, (int)n2, 1.f, 0.f, nullptr, 0, Tt,
+              idx.ldr, 1, err, s);
+      // Z += W^ T
+      tc_gemm(idx.Wb.p, idx.ldr, Tt, idx.ldr, (int)n2, b, idx.rank, 1.f, 1.f,
+              reinterpret_cast<float*>(Z), ld, nullptr, 0, 0, err, s);
+    }
+    (void)Tm;
+    return;
+  }
   if (idx.rank > 0) {
     gemm<VT>(true, idx.rank, b, n2, 1.0, Dense<VT>::Wr(idx), idx.rank, R, ld, 0.0, Tm, ld, s);
     gemm<VT>(false, n2, b, idx.rank, 1.0, Dense<VT>::Wr(idx), idx.rank, Tm, ld, 1.0, Z, ld, s);
@@ -268,6 +290,7 @@ int pcg_schur(katz_index& idx, const VT* F, VT* K2, int b, int64_t ld, const dou
   VT* Q = ws.get<VT>("S.Q", size_t(n2) * ld);
   VT* Tm = ws.get<VT>("S.T", size_t(std::max(1, idx.rank)) * ld);
   ColState st = make_state(ws, "S", b, true);
+  KATZ_CUDA(cudaMemsetAsync(ws.get<int>("S.err", 1), 0, sizeof(int), s));
   KATZ_CUDA(cudaMemcpyAsync(st.thr2, thr2, sizeof(double) * b, cudaMemcpyDeviceToDevice, s));
   KATZ_CUDA(cudaMemsetAsync(K2, 0, sizeof(VT) * n2 * ld, s));
   KATZ_CUDA(cudaMemcpyAsync(R, F, sizeof(VT) * n2 * ld, cudaMemcpyDeviceToDevice, s));
@@ -295,6 +318,8 @@ int pcg_schur(katz_index& idx, const VT* F, VT* K2, int b, int64_t ld, const dou
   }
   harvest_iters(st, b, iters, s);
   const int flags = read_int(st.flags, s);
+  KATZ_REQUIRE(read_int(ws.get<int>("S.err", 1), s) == 0, KATZ_ECUDA,
+               "tcgen05 GEMM pipeline timed out");
   if (flags & 1) return KATZ_ENOTSPD;
   return active > 0 ? KATZ_ENOCONV : KATZ_OK;
 }
@@ -394,6 +419,102 @@ static void residual64(katz_index& idx, bool use_lrc, const int32_t* q, int b, i
   rhs_add(idx.W.view(), q, b, idx.beta, pos, R64, ld, s);
   KATZ_CUDA(cudaMemsetAsync(rr, 0, sizeof(double) * b, s));
   coldot<double>(R64, ld, R64, ld, idx.n, b, rr, s);
+}
+
+// Mixed precision with a float-float residual (weights exact in FP32):
+// FP32 inner solves, K kept as an FP32 (hi, lo) pair, R = B - M K evaluated
+// in float-float and rounded to FP32 only after the cancellation.
+static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const int32_t* q_host,
+                          int b, const katz_query_opts& o, const QueryOut& out, katz_stats* stats,
+                          std::vector<int32_t>& iters, std::vector<double>& relres,
+                          cudaStream_t s) {
+  using clk = std::chrono::steady_clock;
+  const auto t0 = clk::now();
+  const int64_t n = idx.n;
+  const int64_t ld = (b + 3) / 4 * 4;
+  const int max_iter = o.max_iter > 0 ? o.max_iter : 2000;
+  const int max_refine = o.max_refine > 0 ? o.max_refine : 12;
+  const int32_t* pos = use_lrc ? idx.iperm.p : nullptr;
+  const GraphPart& G = use_lrc ? idx.Wp : idx.W;
+  Workspace& ws = idx.ws;
+  iters.assign(b, 0);
+  relres.assign(b, 0.0);
+  int64_t maxdeg = 0;
+  for (int j = 0; j < b; ++j) maxdeg = std::max<int64_t>(maxdeg, idx.deg_h[q_host[j]]);
+
+  double* bn2 = ws.get<double>("q.bn2", b);
+  double* bmx = ws.get<double>("q.bmx", b);
+  double* thr2 = ws.get<double>("q.thr2", b);
+  double* thr2_in = ws.get<double>("q.thr2in", b);
+  double* rr = ws.get<double>("q.rr", bpad(b));
+  int* conv = ws.get<int>("q.conv", b);
+  int* nopen = ws.get<int>("q.nopen", 1);
+  rhs_norms(idx.W.view(), q, b, idx.beta, bn2, bmx, s);
+  const double omc = std::max(1e-300, 1.0 - idx.beta * idx.lambda);
+  make_thresholds(bn2, bmx, b, o.tol, o.tol_kind, omc, thr2, s);
+  const double tau = 2e-6;
+  double tol_rel = (o.tol_kind == KATZ_TOL_RESIDUAL) ? o.tol : o.tol * omc;
+  tol_rel = std::max(tol_rel * 0.3, tau);
+
+  float* R = ws.get<float>("q.Rin", size_t(n) * ld);
+  float* D = ws.get<float>("q.D", size_t(n) * ld);
+  float* Kh = ws.get<float>("q.Kh", size_t(n) * ld);
+  float* Kl = ws.get<float>("q.Kl", size_t(n) * ld);
+  KATZ_CUDA(cudaMemsetAsync(R, 0, sizeof(float) * n * ld, s));
+  build_rhs<float>(idx.W.view(), q, b, idx.beta, pos, R, ld, s);
+  inner_thresholds_kernel<<<1, 1024, 0, s>>>(bn2, thr2, tau, b, conv, thr2_in, nopen);
+  KATZ_CHECK_LAUNCH();
+  const auto t1 = clk::now();
+  int status = inner_solve<float>(idx, use_lrc, R, Kh, b, ld, thr2_in, tol_rel, max_iter, &iters, s);
+  KATZ_CUDA(cudaMemsetAsync(Kl, 0, sizeof(float) * n * ld, s));
+  KATZ_CUDA(cudaStreamSynchronize(s));
+  const auto t2 = clk::now();
+  double ms_res = 0;
+  int refine = 0;
+  if (status == KATZ_OK || status == KATZ_ENOCONV) {
+    for (;;) {
+      const auto r0 = clk::now();
+      ff_residual(G.view(), idx.W.view(), q, pos, b, idx.beta, Kh, Kl, ld, R, maxdeg, s);
+      KATZ_CUDA(cudaMemsetAsync(rr, 0, sizeof(double) * bpad(b), s));
+      coldot<float>(R, ld, R, ld, n, b, rr, s);
+      inner_thresholds_kernel<<<1, 1024, 0, s>>>(rr, thr2, tau, b, conv, thr2_in, nopen);
+      KATZ_CHECK_LAUNCH();
+      ++refine;
+      const int open = read_int(nopen, s);
+      ms_res += std::chrono::duration<double, std::milli>(clk::now() - r0).count();
+      if (open == 0) { status = KATZ_OK; break; }
+      if (refine > max_refine) { status = KATZ_ENOCONV; break; }
+      mask_columns(R, ld, n, b, conv, s);
+      const int st = inner_solve<float>(idx, use_lrc, R, D, b, ld, thr2_in, tol_rel, max_iter,
+                                        &iters, s);
+      if (st == KATZ_ENOTSPD) { status = st; break; }
+      ff_add(Kh, Kl, D, n * ld, s);
+    }
+    std::vector<double> hr(b), hb(b);
+    KATZ_CUDA(cudaMemcpyAsync(hr.data(), rr, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
+    KATZ_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
+    KATZ_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < b; ++c) relres[c] = hb[c] > 0 ? std::sqrt(hr[c] / hb[c]) : std::sqrt(hr[c]);
+    ff_out(Kh, Kl, ld, pos, n, b, out.K, out.dtype, out.ldk, s);
+    KATZ_CUDA(cudaStreamSynchronize(s));
+  }
+  const auto t3 = clk::now();
+  if (stats) {
+    int mx = 0;
+    double mr = 0;
+    for (int c = 0; c < b; ++c) {
+      mx = std::max(mx, iters[c]);
+      mr = std::max(mr, relres[c]);
+    }
+    stats->iters = mx;
+    stats->refine_steps = refine;
+    stats->max_rel_res = mr;
+    stats->ms[0] = std::chrono::duration<double, std::milli>(t3 - t0).count();
+    stats->ms[1] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    stats->ms[2] = std::chrono::duration<double, std::milli>(t2 - t1).count();
+    stats->ms[3] = ms_res;
+  }
+  return status;
 }
 
 template <class VT>
@@ -508,11 +629,15 @@ static int query_impl(katz_index& idx, bool use_lrc, const int32_t* q, int b,
   return status;
 }
 
-int run_queries(katz_index& idx, bool use_lrc, const int32_t* q_dev, int b,
+int run_queries(katz_index& idx, bool use_lrc, const int32_t* q_dev, const int32_t* q_host, int b,
                 const katz_query_opts& o, const QueryOut& out, katz_stats* st,
                 std::vector<int32_t>& iters, std::vector<double>& relres, cudaStream_t s) {
   KATZ_REQUIRE(!use_lrc || idx.lrc, KATZ_EINVAL, "index was built without the LRC part");
   KATZ_REQUIRE(b > 0 && b <= 1024, KATZ_EINVAL, "b must be in [1, 1024]");
+  // FP64-valued graphs keep the FP64 residual (their weights need not be
+  // exact in FP32); the others use the float-float residual
+  if (o.precision == KATZ_PREC_MIXED && idx.vdt != KATZ_F64)
+    return query_mixed_ff(idx, use_lrc, q_dev, q_host, b, o, out, st, iters, relres, s);
   if (o.precision == KATZ_PREC_F64)
     return query_impl<double>(idx, use_lrc, q_dev, b, o, out, st, iters, relres, s);
   return query_impl<float>(idx, use_lrc, q_dev, b, o, out, st, iters, relres, s);

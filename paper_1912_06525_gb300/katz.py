@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "KATZ_OK", 1: "KATZ_EINVAL", 2: "KATZ_ENOTSPD", 3: "KATZ_ENOC
 # every exported symbol of include/katz.h
 EXPORTS = ["katz_lambda_max", "katz_index_build", "katz_index_free", "katz_index_get_info",
            "katz_index_get_partition", "katz_partition", "katz_index_get_sigma", "katz_query_batch",
-           "cg_query_batch", "linkpred_topk", "katz_apply_M", "katz_launch_count",
+           "cg_query_batch", "linkpred_topk", "katz_apply_M", "katz_gemm_bf16", "katz_launch_count",
            "katz_profile_enable", "katz_profile_read", "katz_last_error"]
 
 
@@ -94,6 +94,8 @@ def lib() -> C.CDLL:
         L.cg_query_batch.argtypes = qargs
         L.linkpred_topk.argtypes = [vp, vp, i32, vp, i32, i64, i32, vp, vp, vp]
         L.katz_apply_M.argtypes = [vp, vp, vp, i32, i32, vp]
+        L.katz_gemm_bf16.argtypes = [vp, i64, vp, i64, i32, i32, i32, C.c_float, C.c_float, vp,
+                                     i64, vp]
         L.katz_launch_count.argtypes = []
         L.katz_launch_count.restype = C.c_int64
         L.katz_profile_enable.argtypes = [i32]
@@ -114,6 +116,18 @@ def _check(code: int, allow=(KATZ_OK,)) -> int:
     if code not in allow:
         raise KatzError(code, katz_last_error())
     return code
+
+
+def _ld(x) -> int:
+    """Leading dimension (elements) of a row-major 2-D block; the columns
+    must be contiguous."""
+    if hasattr(x, "stride"):
+        if x.dim() != 2 or x.stride(1) != 1:
+            raise ValueError("expected a 2-D tensor with contiguous rows")
+        return int(x.stride(0))
+    if x.ndim != 2 or x.strides[1] != x.itemsize:
+        raise ValueError("expected a 2-D array with contiguous rows")
+    return int(x.strides[0] // x.itemsize)
 
 
 def _ptr(x):
@@ -223,7 +237,7 @@ def _query(fn, index, q, K_out, out_dtype, tol, tol_kind, precision, max_iter, m
     st = katz_stats()
     iters = np.zeros(b, dtype=np.int32)
     rel = np.zeros(b, dtype=np.float64)
-    ldk = int(K_out.stride(0)) if hasattr(K_out, "stride") else int(K_out.strides[0] // K_out.itemsize)
+    ldk = _ld(K_out)
     code = fn(index.handle, _ptr(q), b, C.byref(o), _ptr(K_out), out_dtype, ldk, C.byref(st),
               iters.ctypes.data, rel.ctypes.data, _stream(stream))
     _check(code, allow=(KATZ_OK, KATZ_ENOCONV))
@@ -252,7 +266,7 @@ def cg_query_batch(index, q, K_out, out_dtype=KATZ_F32, tol=1e-6, tol_kind=KATZ_
 def linkpred_topk(index, q, K, k_dtype, k, ids_out, scores_out, stream=None):
     """Top-k link candidates per query column of K (Section 3.3)."""
     b = int(q.shape[0])
-    ldk = int(K.stride(0)) if hasattr(K, "stride") else int(K.strides[0] // K.itemsize)
+    ldk = _ld(K)
     _check(lib().linkpred_topk(index.handle, _ptr(q), b, _ptr(K), k_dtype, ldk, k,
                                _ptr(ids_out), _ptr(scores_out), _stream(stream)))
 
@@ -276,3 +290,13 @@ def katz_profile_read(tag: str) -> dict:
     by = np.zeros(1, dtype=np.float64)
     _check(lib().katz_profile_read(tag.encode(), n.ctypes.data, ms.ctypes.data, by.ctypes.data))
     return {"launches": int(n[0]), "ms": float(ms[0]), "bytes": float(by[0])}
+
+
+def katz_gemm_bf16(A, B, C_out, K=None, alpha=1.0, beta=0.0, stream=None):
+    """C_out = alpha * A[:, :K] @ B[:, :K].T + beta * C_out on tcgen05 (A: M x ld,
+    B: N x ld BF16 device tensors with contiguous rows; C_out: M x N float32)."""
+    M = A.shape[0]
+    K = A.shape[1] if K is None else K
+    N = B.shape[0]
+    _check(lib().katz_gemm_bf16(_ptr(A), _ld(A), _ptr(B), _ld(B), M, N, K, alpha, beta,
+                                _ptr(C_out), _ld(C_out), _stream(stream)))

@@ -216,7 +216,7 @@ def test_linkpred_topk_matches_oracle():
     beta = 0.8 / O.lambda_max(W)
     idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_F32, build_lrc=False)
     q = synth.queries(g.n, 24, seed=8)
-    Kref = O.katz_direct(W, beta, q)
+    Kref = np.ascontiguousarray(O.katz_direct(W, beta, q))
     Kd = torch.from_numpy(Kref).cuda()
     ids = torch.empty((len(q), 20), dtype=torch.int32, device="cuda")
     sc = torch.empty((len(q), 20), dtype=torch.float64, device="cuda")
