@@ -202,6 +202,15 @@ int linkpred_topk(const katz_index* idx, const int32_t* q, int32_t b,
 int katz_apply_M(const katz_index* idx, const void* X, void* Y, int32_t b,
                  int32_t dtype, void* stream);
 
+/* Autotuner: times the candidate launch shapes of the multi-RHS CSR
+ * product (columns per warp-row tile in {128..1024} x CTAs per SM in
+ * {2..16}) on the index's operators for right-hand-side width b, keeps the
+ * fastest per operator for later queries with that b, and caches the
+ * choice per (rows, nnz, b, value type) in the process.  out[0] = chosen
+ * column tile (0 = default), out[1] = CTAs per SM; ms[0] = best time,
+ * ms[1] = time of the default shape (per product, FP32 vectors). */
+int katz_autotune(katz_index* idx, int32_t b, int32_t* out, double* ms, void* stream);
+
 /* D = A * B^T on the tcgen05 tensor cores (BF16 operands, FP32
  * accumulation in tensor memory): the kernel used for the rank-r
  * correction products W^ (W^T R) of the preconditioner (Eq. 14), exposed

@@ -295,9 +295,9 @@ int linkpred_topk(const katz_index* cidx, const int32_t* q, int32_t b, const voi
       KATZ_CUDA(cudaMemcpyAsync(t, K, es * size_t(idx->n) * ldk, cudaMemcpyHostToDevice, s));
       Kd = t;
     }
-    const int slices = (int)std::max<int64_t>(1, std::min<int64_t>(64, idx->n / 4096 + 1));
-    int32_t* wid = idx->ws.get<int32_t>("tk.id", size_t(slices) * b * k);
-    double* wsc = idx->ws.get<double>("tk.sc", size_t(slices) * b * k);
+    const int slices = (int)std::max<int64_t>(1, std::min<int64_t>(16, idx->n / 65536 + 1));
+    int32_t* wid = idx->ws.get<int32_t>("tk.id", size_t(slices) * 8 * b * k);
+    double* wsc = idx->ws.get<double>("tk.sc", size_t(slices) * 8 * b * k);
     const bool dev_ids = is_device_ptr(ids_out), dev_sc = is_device_ptr(scores_out);
     int32_t* ids = dev_ids ? ids_out : idx->ws.get<int32_t>("tk.oid", size_t(b) * k);
     double* sc = dev_sc ? scores_out : idx->ws.get<double>("tk.osc", size_t(b) * k);
@@ -312,6 +312,18 @@ int linkpred_topk(const katz_index* cidx, const int32_t* q, int32_t b, const voi
     if (!dev_sc)
       KATZ_CUDA(cudaMemcpyAsync(scores_out, sc, 8 * size_t(b) * k, cudaMemcpyDeviceToHost, s));
     KATZ_CUDA(cudaStreamSynchronize(s));
+    return KATZ_OK;
+  });
+}
+
+int katz_autotune(katz_index* idx, int32_t b, int32_t* out, double* ms, void* stream) {
+  return guarded([&]() {
+    KATZ_REQUIRE(idx && out && ms && b > 0 && b <= 1024, KATZ_EINVAL, "bad autotune arguments");
+    const katz::TuneResult r = katz::autotune(*idx, b, static_cast<cudaStream_t>(stream));
+    out[0] = r.col_tile;
+    out[1] = r.ctas_per_sm;
+    ms[0] = r.ms_best;
+    ms[1] = r.ms_default;
     return KATZ_OK;
   });
 }

@@ -19,6 +19,7 @@ class Workspace {
     return reinterpret_cast<T*>(b.p);
   }
   void clear() { bufs_.clear(); }
+  void release(const std::string& name) { bufs_.erase(name); }
   size_t bytes() const {
     size_t t = 0;
     for (auto& kv : bufs_) t += kv.second.bytes();
@@ -39,12 +40,18 @@ struct BlockClass {
   DBuf<double> inv64;
 };
 
-// A CSR with the list of its heavy rows.
+// A CSR with the list of its heavy rows and the SpMM launch shapes the
+// autotuner picked for it (per right-hand-side width b).
 struct GraphPart {
   DevCsr csr;
   DBuf<int32_t> heavy;
   int64_t n_heavy = 0;
+  std::map<int, SpmmCfg> tuned;
   Csr view() const { return csr.view(); }
+  const SpmmCfg* cfg(int b) const {
+    auto it = tuned.find(b);
+    return it == tuned.end() ? nullptr : &it->second;
+  }
 };
 
 struct Partition {
@@ -112,5 +119,13 @@ int run_queries(katz_index& idx, bool use_lrc, const int32_t* q_dev, const int32
 
 template <class VT>
 void apply_M(const katz_index& idx, const VT* X, VT* Y, int b, int64_t ld, cudaStream_t s);
+
+struct TuneResult {
+  int col_tile = 0, ctas_per_sm = 0, rhs_width = 0;
+  double ms_best = 0, ms_default = 0;
+};
+// Times candidate SpMM launch shapes on every operator of the index for
+// width b (FP32 vectors) and records the fastest; returns the result for W.
+TuneResult autotune(katz_index& idx, int b, cudaStream_t s);
 
 }  // namespace katz

@@ -300,100 +300,81 @@ __device__ __forceinline__ bool better(double sa, int ia, double sb, int ib) {
 
 constexpr int kTopMax = 64;
 
-// Pass 1: CTA (column j, row slice).  Each thread keeps a sorted top-k
-// list in local memory; the CTA merges them by repeated arg-max.
+// Pass 1: CTA = (row slice, tile of 32 query columns); lane c of every warp
+// owns column tile*32 + c, so each warp reads K row by row in coalesced
+// 128-byte segments.  Each (warp, column) keeps a sorted top-k list in
+// local memory; a candidate is tested against q's neighbours (binary search
+// in the sorted CSR row) only when it beats the current k-th entry.
+// Lists go to the scratch as [column][slice*8 + warp][k].
 template <class VT>
-__global__ void topk_partial_kernel(Csr W, const VT* K, int64_t ldk, int64_t n,
-                                    const int32_t* q, int k, int64_t rows_per_cta,
-                                    int32_t* pid, double* psc) {
-  const int j = blockIdx.y;
-  const int64_t r0 = int64_t(blockIdx.x) * rows_per_cta;
-  const int64_t r1 = min(n, r0 + rows_per_cta);
-  const int64_t qq = q[j];
-  const int64_t nb0 = W.rowptr[qq], nb1 = W.rowptr[qq + 1];
+__global__ void __launch_bounds__(256) topk_partial_kernel(Csr W, const VT* K, int64_t ldk,
+                                                           int64_t n, const int32_t* q, int b,
+                                                           int k, int64_t rows_per_slice,
+                                                           int32_t* pid, double* psc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.y * 32 + lane;
+  const bool cv = j < b;
+  const int64_t r0 = int64_t(blockIdx.x) * rows_per_slice;
+  const int64_t r1 = min(n, r0 + rows_per_slice);
+  const int64_t qq = cv ? q[j] : -1;
+  const int64_t nb0 = cv ? W.rowptr[qq] : 0, nb1 = cv ? W.rowptr[qq + 1] : 0;
   double ls[kTopMax];
   int li[kTopMax];
   int cnt = 0;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    if (i == qq) continue;
-    const double v = double(K[i * ldk + j]);
-    if (cnt == k && !better(v, (int)i, ls[k - 1], li[k - 1])) continue;
-    // exclude current neighbours of q (sorted CSR row: binary search)
-    int64_t lo = nb0, hi = nb1;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (W.col[mid] < i) lo = mid + 1; else hi = mid;
-    }
-    if (lo < nb1 && W.col[lo] == i) continue;
-    int p = cnt < k ? cnt++ : k - 1;
-    while (p > 0 && better(v, (int)i, ls[p - 1], li[p - 1])) {
-      ls[p] = ls[p - 1];
-      li[p] = li[p - 1];
-      --p;
-    }
-    ls[p] = v;
-    li[p] = (int)i;
-  }
-  __shared__ double ss[256];
-  __shared__ int si[256];
-  __shared__ int sw[256];
-  int head = 0;
-  const int64_t out = (int64_t(j) * gridDim.x + blockIdx.x) * k;
-  for (int t = 0; t < k; ++t) {
-    ss[threadIdx.x] = head < cnt ? ls[head] : -1.0 / 0.0;
-    si[threadIdx.x] = head < cnt ? li[head] : 0x7fffffff;
-    sw[threadIdx.x] = threadIdx.x;
-    __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-      if (threadIdx.x < st) {
-        const int o = threadIdx.x + st;
-        if (better(ss[o], si[o], ss[threadIdx.x], si[threadIdx.x])) {
-          ss[threadIdx.x] = ss[o];
-          si[threadIdx.x] = si[o];
-          sw[threadIdx.x] = sw[o];
-        }
+  if (cv) {
+    for (int64_t i = r0 + warp; i < r1; i += 8) {
+      const double v = double(K[i * ldk + j]);
+      if (i == qq) continue;
+      if (cnt == k && !better(v, (int)i, ls[k - 1], li[k - 1])) continue;
+      int64_t lo = nb0, hi = nb1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (W.col[mid] < i) lo = mid + 1; else hi = mid;
       }
-      __syncthreads();
+      if (lo < nb1 && W.col[lo] == i) continue;
+      int p = cnt < k ? cnt++ : k - 1;
+      while (p > 0 && better(v, (int)i, ls[p - 1], li[p - 1])) {
+        ls[p] = ls[p - 1];
+        li[p] = li[p - 1];
+        --p;
+      }
+      ls[p] = v;
+      li[p] = (int)i;
     }
-    const int winner = sw[0];
-    const int wid = si[0];
-    const double wsc = ss[0];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      pid[out + t] = wid == 0x7fffffff ? -1 : wid;
-      psc[out + t] = wid == 0x7fffffff ? 0.0 : wsc;
+    const int lists = gridDim.x * 8;
+    const int64_t out = (int64_t(j) * lists + blockIdx.x * 8 + warp) * k;
+    for (int t = 0; t < k; ++t) {
+      pid[out + t] = t < cnt ? li[t] : -1;
+      psc[out + t] = t < cnt ? ls[t] : 0.0;
     }
-    if (threadIdx.x == winner && head < cnt) ++head;
-    __syncthreads();
   }
 }
 
-// Pass 2: one CTA per column merges its slices' lists.
-__global__ void topk_merge_kernel(const int32_t* pid, const double* psc, int slices, int k,
+// Pass 2: one thread per column merges its sorted lists (k-way selection).
+__global__ void topk_merge_kernel(const int32_t* pid, const double* psc, int lists, int k, int b,
                                   int32_t* ids, double* scores) {
-  const int j = blockIdx.x;
-  const int64_t base = int64_t(j) * slices * k;
-  // Simple exact merge: thread 0 performs a k-way selection over all
-  // slices (slices * k candidates, small).
-  if (threadIdx.x == 0) {
-    for (int t = 0; t < k; ++t) {
-      double best = -1.0 / 0.0;
-      int bid = 0x7fffffff;
-      int64_t bpos = -1;
-      for (int64_t e = 0; e < int64_t(slices) * k; ++e) {
-        const int id = pid[base + e];
-        if (id < 0) continue;
-        const double sc = psc[base + e];
-        if (better(sc, id, best, bid)) { best = sc; bid = id; bpos = e; }
-      }
-      if (bpos >= 0) {
-        ids[int64_t(j) * k + t] = bid;
-        scores[int64_t(j) * k + t] = best;
-        const_cast<int32_t*>(pid)[base + bpos] = -1;
-      } else {
-        ids[int64_t(j) * k + t] = -1;
-        scores[int64_t(j) * k + t] = 0.0;
-      }
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= b) return;
+  const int64_t base = int64_t(j) * lists * k;
+  int head[kTopMax * 2];  // enough for up to 128 lists (16 slices x 8 warps)
+  for (int l = 0; l < lists; ++l) head[l] = 0;
+  for (int t = 0; t < k; ++t) {
+    double best = 0.0;
+    int bid = -1, bl = -1;
+    for (int l = 0; l < lists; ++l) {
+      if (head[l] >= k) continue;
+      const int id = pid[base + int64_t(l) * k + head[l]];
+      if (id < 0) continue;
+      const double sc = psc[base + int64_t(l) * k + head[l]];
+      if (bl < 0 || better(sc, id, best, bid)) { best = sc; bid = id; bl = l; }
+    }
+    if (bl >= 0) {
+      ids[int64_t(j) * k + t] = bid;
+      scores[int64_t(j) * k + t] = best;
+      head[bl]++;
+    } else {
+      ids[int64_t(j) * k + t] = -1;
+      scores[int64_t(j) * k + t] = 0.0;
     }
   }
 }
@@ -402,11 +383,13 @@ template <class VT>
 void topk_columns_ws(const Csr& W, const VT* K, int64_t ldk, int64_t n, const int32_t* q, int b,
                      int k, int32_t* ids, double* scores, int32_t* ws_id, double* ws_sc,
                      int slices, cudaStream_t s) {
+  KATZ_REQUIRE(slices * 8 <= 2 * kTopMax && k <= kTopMax, KATZ_EINVAL, "topk: too many lists");
   const int64_t rows_per = ceil_div(n, slices);
-  dim3 grid((unsigned)slices, (unsigned)b);
-  topk_partial_kernel<VT><<<grid, 256, 0, s>>>(W, K, ldk, n, q, k, rows_per, ws_id, ws_sc);
+  dim3 grid((unsigned)slices, (unsigned)ceil_div(b, 32));
+  topk_partial_kernel<VT><<<grid, 256, 0, s>>>(W, K, ldk, n, q, b, k, rows_per, ws_id, ws_sc);
   KATZ_CHECK_LAUNCH();
-  topk_merge_kernel<<<b, 32, 0, s>>>(ws_id, ws_sc, slices, k, ids, scores);
+  topk_merge_kernel<<<(unsigned)ceil_div(b, 64), 64, 0, s>>>(ws_id, ws_sc, slices * 8, k, b, ids,
+                                                             scores);
   KATZ_CHECK_LAUNCH();
 }
 template void topk_columns_ws<float>(const Csr&, const float*, int64_t, int64_t, const int32_t*,

@@ -705,35 +705,57 @@ template void build_rhs<float>(const Csr&, const int32_t*, int, double, const in
 template void build_rhs<double>(const Csr&, const int32_t*, int, double, const int32_t*, double*,
                                 int64_t, cudaStream_t);
 
+// Column sums of squares and max |x|: vector loads along the row (the
+// Grid2 layout of the other column reductions), FP64 partials.
 template <class VT>
-__global__ void col_norms_kernel(const VT* B, int64_t ld, int64_t len, int b, double* norm2,
-                                 unsigned long long* maxabs_bits) {
-  const int c = blockIdx.y * blockDim.x + threadIdx.x;
-  if (c >= b) return;
-  double s = 0, m = 0;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.y + threadIdx.y; i < len;
-       i += int64_t(gridDim.x) * blockDim.y) {
-    const double v = double(B[i * ld + c]);
-    s += v * v;
-    m = fmax(m, fabs(v));
+__global__ void col_norms_kernel(const VT* __restrict__ B, int64_t ld, int64_t len, int b,
+                                 double* norm2, unsigned long long* maxabs_bits) {
+  constexpr int VW = VecOf<VT>::width;
+  const int64_t c = (int64_t(blockIdx.y) * blockDim.x + threadIdx.x) * VW;
+  const bool valid = c < b;
+  double tot[VW], mx[VW];
+  VT part[VW];
+#pragma unroll
+  for (int w = 0; w < VW; ++w) { tot[w] = 0; mx[w] = 0; part[w] = VT(0); }
+  int cnt = 0;
+  if (valid) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.y + threadIdx.y; i < len;
+         i += int64_t(gridDim.x) * blockDim.y) {
+      VT v[VW];
+      vload<VT>(B + i * ld + c, v);
+#pragma unroll
+      for (int w = 0; w < VW; ++w) {
+        part[w] += v[w] * v[w];
+        mx[w] = fmax(mx[w], fabs(double(v[w])));
+      }
+      if (++cnt == kFlush) {
+        cnt = 0;
+#pragma unroll
+        for (int w = 0; w < VW; ++w) { tot[w] += double(part[w]); part[w] = VT(0); }
+      }
+    }
   }
-  if (s != 0.0) atomicAdd(norm2 + c, s);
-  if (m != 0.0) atomicMax(maxabs_bits + c, (unsigned long long)__double_as_longlong(m));
+#pragma unroll
+  for (int w = 0; w < VW; ++w) tot[w] += double(part[w]);
+  if (valid)
+#pragma unroll
+    for (int w = 0; w < VW; ++w)
+      if (c + w < b && mx[w] > 0)
+        atomicMax(maxabs_bits + c + w, (unsigned long long)__double_as_longlong(mx[w]));
+  reduce_cols_atomic<VW>(tot, norm2, c, valid);
 }
+
 template <class VT>
 void col_norms(const VT* B, int64_t ld, int64_t len, int b, double* norm2, double* maxabs,
                cudaStream_t s) {
   KATZ_CUDA(cudaMemsetAsync(norm2, 0, sizeof(double) * b, s));
   KATZ_CUDA(cudaMemsetAsync(maxabs, 0, sizeof(double) * b, s));
   if (len <= 0) return;
-  const int tx = std::min(32, b);
-  dim3 block(tx, 256 / tx);
-  int64_t gx = std::min<int64_t>(ceil_div(len, block.y), int64_t(num_sms()) * 4);
-  dim3 grid((unsigned)std::max<int64_t>(1, gx), (unsigned)ceil_div(b, tx));
+  Grid2 g = grid2<VT>(len, b);
   // non-negative doubles order like their bit patterns, so atomicMax on the
   // bits gives the maximum
-  col_norms_kernel<VT><<<grid, block, 0, s>>>(B, ld, len, b, norm2,
-                                               reinterpret_cast<unsigned long long*>(maxabs));
+  col_norms_kernel<VT><<<g.grid, g.block, 0, s>>>(B, ld, len, b, norm2,
+                                                   reinterpret_cast<unsigned long long*>(maxabs));
   KATZ_CHECK_LAUNCH();
 }
 template void col_norms<float>(const float*, int64_t, int64_t, int, double*, double*,

@@ -125,11 +125,11 @@ static unsigned flat_blocks(int64_t total) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), int64_t(num_sms()) * 16));
 }
 
-// ------------------------------------------------------------ col state
 // Column arrays that receive vectorised reductions are padded to a multiple
 // of 4 entries (a reduction over a 4-wide vector writes all 4 lanes).
 static int bpad(int b) { return (b + 3) / 4 * 4; }
 
+// ------------------------------------------------------------ col state
 static ColState make_state(Workspace& ws, const std::string& tag, int b, bool with_rr) {
   ColState st;
   st.rz = ws.get<double>(tag + ".rz", bpad(b));
@@ -182,7 +182,8 @@ int cg_solve(const GraphPart& A, double beta, const VT* B, int64_t ld, int64_t l
   int active = read_int(st.n_active, s);
   int it = 0;
   for (; it < max_iter && active > 0; ++it) {
-    spmm<VT>(A.view(), A.heavy.p, A.n_heavy, -beta, P, ld, 1.0, P, ld, Q, ld, b, P, ld, st.pq, s);
+    spmm<VT>(A.view(), A.heavy.p, A.n_heavy, -beta, P, ld, 1.0, P, ld, Q, ld, b, P, ld, st.pq, s,
+             A.cfg(b));
     colstate_check_pq(st, b, s);
     cg_update_xr<VT>(X, P, R, Q, ld, len, b, st, true, s);
     colstate_advance(st, b, s);
@@ -200,8 +201,8 @@ int cg_solve(const GraphPart& A, double beta, const VT* B, int64_t ld, int64_t l
 template <class VT>
 static void rel_thresholds(const VT* X, int64_t ld, int64_t len, int b, double tol, double* thr2,
                            Workspace& ws, const std::string& tag, cudaStream_t s) {
-  double* n2 = ws.get<double>(tag + ".n2", b);
-  double* mx = ws.get<double>(tag + ".mx", b);
+  double* n2 = ws.get<double>(tag + ".n2", bpad(b));
+  double* mx = ws.get<double>(tag + ".mx", bpad(b));
   col_norms<VT>(X, ld, len, b, n2, mx, s);
   make_thresholds(n2, mx, b, tol, KATZ_TOL_RESIDUAL, 1.0, thr2, s);
 }
@@ -345,7 +346,7 @@ int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double t
     VT* F = idx.ws.get<VT>("lrc.F", size_t(n2) * ld);
     if (n1 > 0)
       spmm<VT>(idx.W21.view(), idx.W21.heavy.p, idx.W21.n_heavy, idx.beta, Y1, ld, 1.0, R2, ld, F,
-               ld, b, nullptr, 0, nullptr, s);
+               ld, b, nullptr, 0, nullptr, s, idx.W21.cfg(b));
     else
       KATZ_CUDA(cudaMemcpyAsync(F, R2, sizeof(VT) * n2 * ld, cudaMemcpyDeviceToDevice, s));
     double* thr2 = idx.ws.get<double>("lrc.thrF", b);
@@ -356,7 +357,7 @@ int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double t
     const VT* T1 = R1;
     if (n2 > 0) {
       spmm<VT>(idx.W12.view(), idx.W12.heavy.p, idx.W12.n_heavy, idx.beta, D2, ld, 1.0, R1, ld, Y1,
-               ld, b, nullptr, 0, nullptr, s);
+               ld, b, nullptr, 0, nullptr, s, idx.W12.cfg(b));
       T1 = Y1;
     }
     merge(m11_solve<VT>(idx, T1, D1, b, ld, tol_l, max_iter, nullptr, s));
@@ -379,7 +380,7 @@ template <class VT>
 static int inner_solve(katz_index& idx, bool use_lrc, const VT* Rin, VT* D, int b, int64_t ld,
                        const double* thr2_in, double tol_rel, int max_iter,
                        std::vector<int32_t>* iters, cudaStream_t s) {
-  if (use_lrc) return lrc_solve<VT>(idx, Rin, D, b, ld, tol_rel, tol_rel * 0.1, max_iter, iters, s);
+  if (use_lrc) return lrc_solve<VT>(idx, Rin, D, b, ld, tol_rel, tol_rel, max_iter, iters, s);
   // shares the scratch of the large-block M11 solve (never live at once)
   return cg_solve<VT>(idx.W, idx.beta, Rin, ld, idx.n, b, D, thr2_in, max_iter, idx.ws, "L",
                       iters, s);

@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "KATZ_OK", 1: "KATZ_EINVAL", 2: "KATZ_ENOTSPD", 3: "KATZ_ENOC
 # every exported symbol of include/katz.h
 EXPORTS = ["katz_lambda_max", "katz_index_build", "katz_index_free", "katz_index_get_info",
            "katz_index_get_partition", "katz_partition", "katz_index_get_sigma", "katz_query_batch",
-           "cg_query_batch", "linkpred_topk", "katz_apply_M", "katz_gemm_bf16", "katz_launch_count",
+           "cg_query_batch", "linkpred_topk", "katz_apply_M", "katz_autotune", "katz_gemm_bf16", "katz_launch_count",
            "katz_profile_enable", "katz_profile_read", "katz_last_error"]
 
 
@@ -94,6 +94,7 @@ def lib() -> C.CDLL:
         L.cg_query_batch.argtypes = qargs
         L.linkpred_topk.argtypes = [vp, vp, i32, vp, i32, i64, i32, vp, vp, vp]
         L.katz_apply_M.argtypes = [vp, vp, vp, i32, i32, vp]
+        L.katz_autotune.argtypes = [vp, i32, vp, vp, vp]
         L.katz_gemm_bf16.argtypes = [vp, i64, vp, i64, i32, i32, i32, C.c_float, C.c_float, vp,
                                      i64, vp]
         L.katz_launch_count.argtypes = []
@@ -300,3 +301,12 @@ def katz_gemm_bf16(A, B, C_out, K=None, alpha=1.0, beta=0.0, stream=None):
     N = B.shape[0]
     _check(lib().katz_gemm_bf16(_ptr(A), _ld(A), _ptr(B), _ld(B), M, N, K, alpha, beta,
                                 _ptr(C_out), _ld(C_out), _stream(stream)))
+
+
+def katz_autotune(index, b: int, stream=None) -> dict:
+    """Tune the SpMM launch shape for width b; returns the choice and times."""
+    out = np.zeros(2, dtype=np.int32)
+    ms = np.zeros(2, dtype=np.float64)
+    _check(lib().katz_autotune(index.handle, b, out.ctypes.data, ms.ctypes.data, _stream(stream)))
+    return {"col_tile": int(out[0]), "ctas_per_sm": int(out[1]), "ms_best": float(ms[0]),
+            "ms_default": float(ms[1])}
