@@ -235,6 +235,7 @@ def main():
     build_s = time.perf_counter() - t0
     info = idx.info()
 
+    tune = katz.katz_autotune(idx, b)  # SpMM launch shape for this b (untimed)
     qd = torch.from_numpy(q).to(dev)
     K = torch.empty((g.n, b), dtype=torch.float32, device=dev)
     ids = torch.empty((b, 20), dtype=torch.int32, device=dev)
@@ -355,6 +356,7 @@ def main():
     if rank == 0:
         cfg = workload_desc(g, b, c, rank_r, args.scale)
         cfg.update({"method": args.method, "parallelism": "replicas" if world > 1 else "single",
+                    "spmm_autotune": tune,
                     "n2": info["n2"], "n1": info["n1"], "index_build_s": build_s,
                     "lambda_max": lam})
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

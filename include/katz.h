@@ -222,6 +222,72 @@ int katz_autotune(katz_index* idx, int32_t b, int32_t* out, double* ms, void* st
 int katz_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int32_t M, int32_t N,
                    int32_t K, float alpha, float beta, float* C, int64_t ldc, void* stream);
 
+/* ------------------------------------------------- learned warm start */
+
+typedef struct {
+  int32_t hidden;       /* hidden width (256) */
+  int32_t epochs;       /* passes over the training queries */
+  int32_t batch;        /* minibatch rows */
+  float lr;             /* AdamW learning rate */
+  float weight_decay;   /* AdamW decoupled weight decay */
+  uint64_t seed;        /* SplitMix64 seed of the initial weights and the row order */
+} katz_train_opts;
+
+typedef struct {
+  double initial_loss, final_loss; /* MSE of the first minibatch / whole training set */
+  int32_t steps;                   /* AdamW steps taken */
+  double ms;                       /* wall time (target solves + training) */
+} katz_train_stats;
+
+/* Train the warm-start network on Katz vectors the method itself computes.
+ * For each training query q (host ids, n_train of them) the LRC solve gives
+ * k_q; the target is c* = W_r^T M22 k2 (the M22-orthogonal coordinates of
+ * the separator part in the Lanczos basis W_r, W_r^T M22 W_r = I).  Input
+ * features (32): degree / mean degree, log(1 + degree) (standardised) and
+ * 30 spectral coordinates (row of W_r for separator nodes, of
+ * beta M11^{-1} W12 W_r otherwise; unit RMS per column).  Network: 32 ->
+ * hidden (exact GELU) -> r, BF16 weights, FP32 accumulation and FP32
+ * master weights, MSE loss, AdamW.  Afterwards katz_query_batch with
+ * opts->warm_start = 1 starts the Schur PCG from K2 = W_r MLP(x_q); a column
+ * whose warm residual is not below ||F|| starts from zero instead. */
+int katz_warmstart_train(katz_index* idx, const int32_t* q_train, int32_t n_train,
+                         const katz_train_opts* opts, katz_train_stats* stats, void* stream);
+
+/* One forward/backward of the warm-start network on device data, for
+ * gradient checks.  X (m x din), T (m x dout) FP32; params FP32 in the
+ * layout W1 (dh x din), b1 (dh), W2 (dout x dh), b2 (dout) -- the weights
+ * are rounded to BF16 as in training; grads (same layout) receive the
+ * gradients of the mean squared error 0.5/m * ||Y - T||^2, *loss its value. */
+int katz_mlp_loss_grad(int32_t m, int32_t din, int32_t dh, int32_t dout, const float* X,
+                       const float* T, const float* params, float* grads, double* loss,
+                       void* stream);
+
+/* ------------------------------------------------- many graphs at once */
+
+typedef struct katz_multi katz_multi; /* opaque; g independent graphs */
+
+/* Index g independent graphs of uneven size for batched queries.  Ws[g]:
+ * host CSRs as for katz_index_build; betas[g]: each graph's damping.  The
+ * graphs are stored as one block-diagonal CSR; lambda_max of every graph is
+ * measured and beta_g * lambda_g >= 1 gives KATZ_ENOTSPD.  value_dtype:
+ * KATZ_UNIT, KATZ_F32 or KATZ_BF16 (weights exact in FP32). */
+int katz_multi_build(int32_t g, const katz_csr* Ws, const double* betas, int32_t value_dtype,
+                     void* stream, katz_multi** out);
+
+void katz_multi_free(katz_multi* m);
+
+/* qpg queries of every graph (Eq. 3 per graph), solved together: one
+ * multi-RHS CG on the block-diagonal system with per-(graph, query) CG
+ * scalars and stopping, the iteration sequence captured once in a CUDA graph
+ * and replayed, float-float residual refinement to opts->tol.
+ * q[g*qpg]: graph-local node ids (host or device), graph-major.
+ * K_out: (sum of n_g) x qpg node-major (ld = ldk), rows in graph order;
+ * column j of graph g's rows is the Katz vector of graph g's j-th query.
+ * iters_out / rel_res_out (host, g*qpg, may be NULL).  qpg <= 64. */
+int katz_multi_query(const katz_multi* m, const int32_t* q, int32_t qpg,
+                     const katz_query_opts* opts, void* K_out, int32_t out_dtype, int64_t ldk,
+                     katz_stats* stats, int32_t* iters_out, double* rel_res_out, void* stream);
+
 /* ---------------------------------------------------------- measurement */
 
 /* Number of kernels this library has launched in this process (all calls). */

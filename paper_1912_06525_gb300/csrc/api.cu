@@ -1,5 +1,6 @@
 // extern "C" boundary of libkatz.so (declared in include/katz.h).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -155,6 +156,8 @@ int do_query(const katz_index* cidx, bool lrc, const int32_t* q, int32_t b,
 }
 
 }  // namespace
+
+void katz::set_last_error(const std::string& msg) { g_last_error = msg; }
 
 extern "C" {
 
@@ -313,6 +316,131 @@ int linkpred_topk(const katz_index* cidx, const int32_t* q, int32_t b, const voi
       KATZ_CUDA(cudaMemcpyAsync(scores_out, sc, 8 * size_t(b) * k, cudaMemcpyDeviceToHost, s));
     KATZ_CUDA(cudaStreamSynchronize(s));
     return KATZ_OK;
+  });
+}
+
+int katz_warmstart_train(katz_index* idx, const int32_t* q_train, int32_t n_train,
+                         const katz_train_opts* opts, katz_train_stats* stats, void* stream) {
+  return guarded([&]() {
+    KATZ_REQUIRE(idx && q_train && opts && n_train > 0, KATZ_EINVAL, "bad training arguments");
+    KATZ_REQUIRE(idx->lrc && idx->rank > 0, KATZ_EINVAL, "warm start needs an LRC index with rank > 0");
+    std::vector<int32_t> h(n_train);
+    if (is_device_ptr(q_train)) {
+      KATZ_CUDA(cudaMemcpy(h.data(), q_train, 4 * size_t(n_train), cudaMemcpyDeviceToHost));
+    } else {
+      std::memcpy(h.data(), q_train, 4 * size_t(n_train));
+    }
+    for (int32_t v : h) KATZ_REQUIRE(v >= 0 && v < idx->n, KATZ_EINVAL, "training id out of range");
+    const auto t0 = std::chrono::steady_clock::now();
+    double init = 0;
+    int steps = 0;
+    const double fin = katz::warmstart_train(
+        *idx, h.data(), n_train, opts->hidden > 0 ? opts->hidden : 256,
+        opts->epochs > 0 ? opts->epochs : 20, opts->batch > 0 ? opts->batch : 256,
+        opts->lr > 0 ? opts->lr : 1e-3f, opts->weight_decay, opts->seed, &init, &steps,
+        static_cast<cudaStream_t>(stream));
+    if (stats) {
+      stats->initial_loss = init;
+      stats->final_loss = fin;
+      stats->steps = steps;
+      stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return KATZ_OK;
+  });
+}
+
+int katz_mlp_loss_grad(int32_t m, int32_t din, int32_t dh, int32_t dout, const float* X,
+                       const float* T, const float* params, float* grads, double* loss,
+                       void* stream) {
+  return guarded([&]() {
+    KATZ_REQUIRE(m > 0 && din > 0 && dh > 0 && dout > 0 && X && T && params && grads && loss,
+                 KATZ_EINVAL, "bad arguments");
+    KATZ_REQUIRE(is_device_ptr(X) && is_device_ptr(T) && is_device_ptr(params) &&
+                     is_device_ptr(grads),
+                 KATZ_EINVAL, "device pointers required");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    katz::Mlp net;
+    net.din = din;
+    net.dh = dh;
+    net.dout = dout;
+    std::vector<float> h(net.n_params());
+    KATZ_CUDA(cudaMemcpy(h.data(), params, 4 * h.size(), cudaMemcpyDeviceToHost));
+    net.set_params(h.data(), s);
+    katz::Workspace ws;
+    *loss = net.loss_grad(X, T, m, ws, s);
+    KATZ_CUDA(cudaMemcpyAsync(grads, net.grads.p, 4 * h.size(), cudaMemcpyDeviceToDevice, s));
+    KATZ_CUDA(cudaStreamSynchronize(s));
+    return KATZ_OK;
+  });
+}
+
+int katz_multi_build(int32_t g, const katz_csr* Ws, const double* betas, int32_t value_dtype,
+                     void* stream, katz_multi** out) {
+  return guarded([&]() {
+    KATZ_REQUIRE(out && Ws && betas && g > 0, KATZ_EINVAL, "bad multi-graph arguments");
+    *out = nullptr;
+    std::vector<katz::HostCsr> hs;
+    hs.reserve(g);
+    for (int32_t i = 0; i < g; ++i) {
+      hs.push_back(read_csr(&Ws[i]));
+      if (value_dtype == KATZ_UNIT)
+        for (double v : hs.back().val)
+          KATZ_REQUIRE(v == 1.0, KATZ_EINVAL, "value_dtype UNIT needs all weights equal to 1");
+    }
+    auto* m = new katz_multi();
+    try {
+      katz::multi_build(*m, hs, betas, value_dtype, static_cast<cudaStream_t>(stream));
+    } catch (...) {
+      delete m;
+      throw;
+    }
+    *out = m;
+    return KATZ_OK;
+  });
+}
+
+void katz_multi_free(katz_multi* m) { delete m; }
+
+int katz_multi_query(const katz_multi* cm, const int32_t* q, int32_t qpg,
+                     const katz_query_opts* opts, void* K_out, int32_t out_dtype, int64_t ldk,
+                     katz_stats* stats, int32_t* iters_out, double* rel_res_out, void* stream) {
+  return guarded([&]() {
+    KATZ_REQUIRE(cm && q && opts && K_out && qpg > 0 && qpg <= 64, KATZ_EINVAL, "bad arguments");
+    KATZ_REQUIRE(out_dtype == KATZ_F32 || out_dtype == KATZ_F64, KATZ_EINVAL, "out_dtype");
+    KATZ_REQUIRE(ldk >= qpg && opts->tol > 0, KATZ_EINVAL, "ldk < qpg or tol <= 0");
+    katz_multi* m = const_cast<katz_multi*>(cm);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t total = int64_t(m->g) * qpg;
+    std::vector<int32_t> h(total);
+    if (is_device_ptr(q)) {
+      KATZ_CUDA(cudaMemcpyAsync(h.data(), q, 4 * size_t(total), cudaMemcpyDeviceToHost, s));
+      KATZ_CUDA(cudaStreamSynchronize(s));
+    } else {
+      std::memcpy(h.data(), q, 4 * size_t(total));
+    }
+    for (int32_t g = 0; g < m->g; ++g)
+      for (int j = 0; j < qpg; ++j) {
+        const int32_t v = h[size_t(g) * qpg + j];
+        KATZ_REQUIRE(v >= 0 && v < m->seg_ptr_h[g + 1] - m->seg_ptr_h[g], KATZ_EINVAL,
+                     "query id out of range in graph " + std::to_string(g));
+      }
+    int32_t* qd = m->ws.get<int32_t>("api.q", total);
+    KATZ_CUDA(cudaMemcpyAsync(qd, h.data(), 4 * size_t(total), cudaMemcpyHostToDevice, s));
+    const bool dev = is_device_ptr(K_out);
+    const size_t es = out_dtype == KATZ_F64 ? 8 : 4;
+    void* Kd = dev ? K_out : m->ws.get<uint8_t>("api.K", es * size_t(m->n) * ldk);
+    std::vector<int32_t> it;
+    std::vector<double> rr;
+    const int st = katz::multi_query(*m, qd, qpg, *opts, Kd, out_dtype, ldk, stats, it, rr, s);
+    if (!dev && (st == KATZ_OK || st == KATZ_ENOCONV)) {
+      KATZ_CUDA(cudaMemcpyAsync(K_out, Kd, es * size_t(m->n) * ldk, cudaMemcpyDeviceToHost, s));
+      KATZ_CUDA(cudaStreamSynchronize(s));
+    }
+    if (iters_out) std::memcpy(iters_out, it.data(), 4 * it.size());
+    if (rel_res_out) std::memcpy(rel_res_out, rr.data(), 8 * rr.size());
+    if (st == KATZ_ENOCONV) g_last_error = "iteration or refinement cap reached";
+    if (st == KATZ_ENOTSPD) g_last_error = "CG breakdown: p^T A p <= 0";
+    return st;
   });
 }
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <map>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -47,6 +48,9 @@ struct Error : std::runtime_error {
     if (!(cond)) throw ::katz::Error((code), (msg));      \
   } while (0)
 
+// Sets the message katz_last_error() returns on this thread.
+void set_last_error(const std::string& msg);
+
 // ------------------------------------------------------------ measurement
 void count_launch();
 int64_t launch_count();
@@ -80,6 +84,27 @@ struct DBuf {
   void ensure(size_t count) { if (count > n) alloc(count); }
   void release() { if (p) cudaFree(p); p = nullptr; n = 0; }
   size_t bytes() const { return n * sizeof(T); }
+};
+
+// Named, grow-only device scratch owned by an index.
+class Workspace {
+ public:
+  template <class T>
+  T* get(const std::string& name, size_t count) {
+    auto& b = bufs_[name];
+    b.ensure(count * sizeof(T));
+    return reinterpret_cast<T*>(b.p);
+  }
+  void clear() { bufs_.clear(); }
+  void release(const std::string& name) { bufs_.erase(name); }
+  size_t bytes() const {
+    size_t t = 0;
+    for (auto& kv : bufs_) t += kv.second.bytes();
+    return t;
+  }
+
+ private:
+  std::map<std::string, DBuf<uint8_t>> bufs_;
 };
 
 // ------------------------------------------------------------ sparse views

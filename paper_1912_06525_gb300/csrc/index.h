@@ -6,29 +6,9 @@
 #include <string>
 
 #include "kernels.h"
+#include "mlp.h"
 
 namespace katz {
-
-// Named, grow-only device scratch owned by an index.
-class Workspace {
- public:
-  template <class T>
-  T* get(const std::string& name, size_t count) {
-    auto& b = bufs_[name];
-    b.ensure(count * sizeof(T));
-    return reinterpret_cast<T*>(b.p);
-  }
-  void clear() { bufs_.clear(); }
-  void release(const std::string& name) { bufs_.erase(name); }
-  size_t bytes() const {
-    size_t t = 0;
-    for (auto& kv : bufs_) t += kv.second.bytes();
-    return t;
-  }
-
- private:
-  std::map<std::string, DBuf<uint8_t>> bufs_;
-};
 
 // Dense inverses of one size class of M11 diagonal blocks.
 struct BlockClass {
@@ -88,10 +68,37 @@ struct katz_index {
   // WbT (r x ldn2), row strides multiples of 8 elements
   katz::DBuf<__nv_bfloat16> Wb, WbT;
   int64_t ldr = 0, ldn2 = 0;
+  // unscaled Lanczos basis W_r (n2 x ldr4, FP32, W_r^T M22 W_r = I), W22
+  // (the separator block of W), and the learned warm start
+  katz::DBuf<float> Wr32u;
+  int64_t ldr4 = 0;
+  katz::GraphPart W22;
+  katz::Mlp mlp;
+  katz::DBuf<float> feat;  // n x 32 node features
   std::vector<double> sigma;
   int lanczos_steps = 0;
 
   katz::Workspace ws;
+};
+
+// g independent graphs stored as one block-diagonal CSR (multi-graph batch).
+struct katz_multi {
+  int32_t g = 0;
+  int64_t n = 0, nnz = 0;
+  int vdt = KATZ_F32;
+  std::vector<int64_t> seg_ptr_h;
+  std::vector<double> beta_h, lambda_h;
+  std::vector<int32_t> deg_h;
+  katz::GraphPart W;
+  katz::DBuf<int64_t> seg_ptr;
+  katz::DBuf<int32_t> seg;
+  katz::DBuf<float> bseg_hi, bseg_lo;
+  katz::DBuf<double> bseg64;
+  katz::Workspace ws;
+  cudaStream_t cap_stream = nullptr;
+  ~katz_multi() {
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
 };
 
 namespace katz {
@@ -119,6 +126,18 @@ int run_queries(katz_index& idx, bool use_lrc, const int32_t* q_dev, const int32
 
 template <class VT>
 void apply_M(const katz_index& idx, const VT* X, VT* Y, int b, int64_t ld, cudaStream_t s);
+
+void multi_build(katz_multi& m, const std::vector<HostCsr>& Ws, const double* betas, int vdt,
+                 cudaStream_t s);
+int multi_query(katz_multi& m, const int32_t* q_dev, int qpg, const katz_query_opts& o, void* Kout,
+                int out_dt, int64_t ldk, katz_stats* stats, std::vector<int32_t>& iters,
+                std::vector<double>& relres, cudaStream_t s);
+
+double warmstart_train(katz_index& idx, const int32_t* q_host, int n_train, int hidden, int epochs,
+                       int batch, float lr, float wd, uint64_t seed, double* init_loss, int* steps,
+                       cudaStream_t s);
+void warm_start_guess(katz_index& idx, const int32_t* q, int b, float* K20, int64_t ld,
+                      cudaStream_t s);
 
 struct TuneResult {
   int col_tile = 0, ctas_per_sm = 0, rhs_width = 0;

@@ -460,8 +460,8 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   upload_part(W12, o.value_dtype, idx.W12, s);
   upload_part(W21, o.value_dtype, idx.W21, s);
   upload_part(W11L, o.value_dtype, idx.W11L, s);
-  GraphPart W22d;
-  upload_part(W22, o.value_dtype, W22d, s);
+  upload_part(W22, o.value_dtype, idx.W22, s);
+  const GraphPart& W22d = idx.W22;
 
   // --- M11 dense block inverses by size class (Step 4)
   DBuf<int> flag(1);
@@ -636,6 +636,16 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
     std::vector<double> Wh(size_t(n2) * rk);
     KATZ_CUDA(cudaMemcpyAsync(Wh.data(), Wd.p, 8 * Wh.size(), cudaMemcpyDeviceToHost, s));
     KATZ_CUDA(cudaStreamSynchronize(s));
+    // unscaled basis (warm start features and targets)
+    idx.ldr4 = (rk + 3) / 4 * 4;
+    {
+      std::vector<float> wu(size_t(n2) * idx.ldr4, 0.f);
+      for (int64_t i = 0; i < n2; ++i)
+        for (int c = 0; c < rk; ++c) wu[size_t(i) * idx.ldr4 + c] = float(Wh[size_t(i) * rk + c]);
+      idx.Wr32u.alloc(wu.size());
+      KATZ_CUDA(cudaMemcpyAsync(idx.Wr32u.p, wu.data(), 4 * wu.size(), cudaMemcpyHostToDevice, s));
+      KATZ_CUDA(cudaStreamSynchronize(s));
+    }
     // fold D = diag(sigma/(1-sigma)) in: W^ = W D^{1/2}
     std::vector<float> Wf(Wh.size());
     for (int c = 0; c < rk; ++c) {

@@ -280,9 +280,31 @@ static void precond(katz_index& idx, const VT* R, VT* Z, VT* Tm, int b, int64_t 
 
 // Preconditioned CG (Hestenes-Stiefel form) on S K2 = F with S~^{-1} as the
 // preconditioner; zero start; column c stops when ||F_c - S K2_c||^2 <= thr2[c].
+// Columns whose warm residual is not below ||F||: restart from zero.
+template <class VT>
+__global__ void warm_fallback_kernel(VT* K2, VT* R, const VT* F, int64_t ld, int64_t len, int b,
+                                     double* rr, const double* ff) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < len * b;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / b;
+    const int c = int(e - i * b);
+    if (rr[c] >= ff[c]) {
+      K2[i * ld + c] = VT(0);
+      R[i * ld + c] = F[i * ld + c];
+    }
+  }
+}
+__global__ void warm_fallback_rr_kernel(double* rr, const double* ff, int b, int* n_fallback) {
+  for (int c = threadIdx.x; c < b; c += blockDim.x)
+    if (rr[c] >= ff[c]) {
+      rr[c] = ff[c];
+      atomicAdd(n_fallback, 1);
+    }
+}
+
 template <class VT>
 int pcg_schur(katz_index& idx, const VT* F, VT* K2, int b, int64_t ld, const double* thr2,
-              int max_iter, std::vector<int32_t>* iters, cudaStream_t s) {
+              int max_iter, std::vector<int32_t>* iters, cudaStream_t s, const VT* X0 = nullptr) {
   const int64_t n2 = idx.n2;
   Workspace& ws = idx.ws;
   VT* R = ws.get<VT>("S.R", size_t(n2) * ld);
@@ -293,14 +315,31 @@ int pcg_schur(katz_index& idx, const VT* F, VT* K2, int b, int64_t ld, const dou
   ColState st = make_state(ws, "S", b, true);
   KATZ_CUDA(cudaMemsetAsync(ws.get<int>("S.err", 1), 0, sizeof(int), s));
   KATZ_CUDA(cudaMemcpyAsync(st.thr2, thr2, sizeof(double) * b, cudaMemcpyDeviceToDevice, s));
-  KATZ_CUDA(cudaMemsetAsync(K2, 0, sizeof(VT) * n2 * ld, s));
   KATZ_CUDA(cudaMemcpyAsync(R, F, sizeof(VT) * n2 * ld, cudaMemcpyDeviceToDevice, s));
+  KATZ_CUDA(cudaMemsetAsync(st.rr, 0, sizeof(double) * b, s));
+  if (X0) {
+    // warm start: R = F - S K2(0), per-column fallback to zero
+    KATZ_CUDA(cudaMemcpyAsync(K2, X0, sizeof(VT) * n2 * ld, cudaMemcpyDeviceToDevice, s));
+    gemm<VT>(false, n2, b, n2, -1.0, Dense<VT>::S(idx), idx.ld2, K2, ld, 1.0, R, ld, s);
+    double* ff = ws.get<double>("S.ff", bpad(b));
+    int* nfb = ws.get<int>("S.nfb", 1);
+    KATZ_CUDA(cudaMemsetAsync(ff, 0, sizeof(double) * b, s));
+    KATZ_CUDA(cudaMemsetAsync(nfb, 0, sizeof(int), s));
+    coldot<VT>(F, ld, F, ld, n2, b, ff, s);
+    coldot<VT>(R, ld, R, ld, n2, b, st.rr, s);
+    warm_fallback_kernel<VT><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n2 * b, 256), 4096)), 256, 0, s>>>(
+        K2, R, F, ld, n2, b, st.rr, ff);
+    KATZ_CHECK_LAUNCH();
+    warm_fallback_rr_kernel<<<1, 1024, 0, s>>>(st.rr, ff, b, nfb);
+    KATZ_CHECK_LAUNCH();
+  } else {
+    KATZ_CUDA(cudaMemsetAsync(K2, 0, sizeof(VT) * n2 * ld, s));
+    coldot<VT>(R, ld, R, ld, n2, b, st.rr, s);
+  }
   precond<VT>(idx, R, Z, Tm, b, ld, s);
   KATZ_CUDA(cudaMemcpyAsync(P, Z, sizeof(VT) * n2 * ld, cudaMemcpyDeviceToDevice, s));
   KATZ_CUDA(cudaMemsetAsync(st.rz, 0, sizeof(double) * b, s));
-  KATZ_CUDA(cudaMemsetAsync(st.rr, 0, sizeof(double) * b, s));
   coldot<VT>(R, ld, Z, ld, n2, b, st.rz, s);
-  coldot<VT>(R, ld, R, ld, n2, b, st.rr, s);
   colstate_init_kernel<<<1, 1024, 0, s>>>(st, b, 1);
   KATZ_CHECK_LAUNCH();
   int active = read_int(st.n_active, s);
@@ -332,7 +371,8 @@ int pcg_schur(katz_index& idx, const VT* F, VT* K2, int b, int64_t ld, const dou
 //   K1 = M11^{-1}(R1 - M12 K2) = M11^{-1}(R1 + beta W12 K2)   (Eq. 6)
 template <class VT>
 int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double tol_s,
-              double tol_l, int max_iter, std::vector<int32_t>* iters, cudaStream_t s) {
+              double tol_l, int max_iter, std::vector<int32_t>* iters, cudaStream_t s,
+              const VT* K2_0 = nullptr) {
   const int64_t n1 = idx.n1, n2 = idx.n2;
   const VT* R1 = Rin;
   const VT* R2 = Rin + n1 * ld;
@@ -351,7 +391,7 @@ int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double t
       KATZ_CUDA(cudaMemcpyAsync(F, R2, sizeof(VT) * n2 * ld, cudaMemcpyDeviceToDevice, s));
     double* thr2 = idx.ws.get<double>("lrc.thrF", b);
     rel_thresholds<VT>(F, ld, n2, b, tol_s, thr2, idx.ws, "lrcF", s);
-    merge(pcg_schur<VT>(idx, F, D2, b, ld, thr2, max_iter, iters, s));
+    merge(pcg_schur<VT>(idx, F, D2, b, ld, thr2, max_iter, iters, s, K2_0));
   }
   if (n1 > 0) {
     const VT* T1 = R1;
@@ -379,8 +419,9 @@ template void apply_M<double>(const katz_index&, const double*, double*, int, in
 template <class VT>
 static int inner_solve(katz_index& idx, bool use_lrc, const VT* Rin, VT* D, int b, int64_t ld,
                        const double* thr2_in, double tol_rel, int max_iter,
-                       std::vector<int32_t>* iters, cudaStream_t s) {
-  if (use_lrc) return lrc_solve<VT>(idx, Rin, D, b, ld, tol_rel, tol_rel, max_iter, iters, s);
+                       std::vector<int32_t>* iters, cudaStream_t s, const VT* K2_0 = nullptr) {
+  if (use_lrc)
+    return lrc_solve<VT>(idx, Rin, D, b, ld, tol_rel, tol_rel, max_iter, iters, s, K2_0);
   // shares the scratch of the large-block M11 solve (never live at once)
   return cg_solve<VT>(idx.W, idx.beta, Rin, ld, idx.n, b, D, thr2_in, max_iter, idx.ws, "L",
                       iters, s);
@@ -465,8 +506,17 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   build_rhs<float>(idx.W.view(), q, b, idx.beta, pos, R, ld, s);
   inner_thresholds_kernel<<<1, 1024, 0, s>>>(bn2, thr2, tau, b, conv, thr2_in, nopen);
   KATZ_CHECK_LAUNCH();
+  const float* K20 = nullptr;
+  if (o.warm_start) {
+    KATZ_REQUIRE(use_lrc && idx.mlp.ready, KATZ_EINVAL,
+                 "warm_start needs an LRC query and a trained warm-start network");
+    float* g = ws.get<float>("q.K20", size_t(std::max<int64_t>(idx.n2, 1)) * ld);
+    warm_start_guess(idx, q, b, g, ld, s);
+    K20 = g;
+  }
   const auto t1 = clk::now();
-  int status = inner_solve<float>(idx, use_lrc, R, Kh, b, ld, thr2_in, tol_rel, max_iter, &iters, s);
+  int status = inner_solve<float>(idx, use_lrc, R, Kh, b, ld, thr2_in, tol_rel, max_iter, &iters, s,
+                                  K20);
   KATZ_CUDA(cudaMemsetAsync(Kl, 0, sizeof(float) * n * ld, s));
   KATZ_CUDA(cudaStreamSynchronize(s));
   const auto t2 = clk::now();
@@ -642,6 +692,18 @@ int run_queries(katz_index& idx, bool use_lrc, const int32_t* q_dev, const int32
   if (o.precision == KATZ_PREC_F64)
     return query_impl<double>(idx, use_lrc, q_dev, b, o, out, st, iters, relres, s);
   return query_impl<float>(idx, use_lrc, q_dev, b, o, out, st, iters, relres, s);
+}
+
+int run_queries_internal(katz_index& idx, const int32_t* q_dev, const int32_t* q_host, int b,
+                         const katz_query_opts& o, void* Kout, int out_dt, int64_t ldk,
+                         cudaStream_t s) {
+  QueryOut out;
+  out.K = Kout;
+  out.dtype = out_dt;
+  out.ldk = ldk;
+  std::vector<int32_t> it;
+  std::vector<double> rr;
+  return run_queries(idx, true, q_dev, q_host, b, o, out, nullptr, it, rr, s);
 }
 
 template int cg_solve<float>(const GraphPart&, double, const float*, int64_t, int64_t, int, float*,

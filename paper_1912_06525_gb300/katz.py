@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "KATZ_OK", 1: "KATZ_EINVAL", 2: "KATZ_ENOTSPD", 3: "KATZ_ENOC
 EXPORTS = ["katz_lambda_max", "katz_index_build", "katz_index_free", "katz_index_get_info",
            "katz_index_get_partition", "katz_partition", "katz_index_get_sigma", "katz_query_batch",
            "cg_query_batch", "linkpred_topk", "katz_apply_M", "katz_autotune", "katz_gemm_bf16", "katz_launch_count",
-           "katz_profile_enable", "katz_profile_read", "katz_last_error"]
+           "katz_profile_enable", "katz_profile_read", "katz_multi_build", "katz_multi_free",
+           "katz_multi_query", "katz_warmstart_train", "katz_mlp_loss_grad", "katz_last_error"]
 
 
 class KatzError(RuntimeError):
@@ -58,6 +59,16 @@ class katz_query_opts(C.Structure):
 class katz_stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("refine_steps", C.c_int32), ("max_rel_res", C.c_double),
                 ("ms", C.c_double * 8)]
+
+
+class katz_train_opts(C.Structure):
+    _fields_ = [("hidden", C.c_int32), ("epochs", C.c_int32), ("batch", C.c_int32),
+                ("lr", C.c_float), ("weight_decay", C.c_float), ("seed", C.c_uint64)]
+
+
+class katz_train_stats(C.Structure):
+    _fields_ = [("initial_loss", C.c_double), ("final_loss", C.c_double), ("steps", C.c_int32),
+                ("ms", C.c_double)]
 
 
 class katz_index_info(C.Structure):
@@ -97,13 +108,22 @@ def lib() -> C.CDLL:
         L.katz_autotune.argtypes = [vp, i32, vp, vp, vp]
         L.katz_gemm_bf16.argtypes = [vp, i64, vp, i64, i32, i32, i32, C.c_float, C.c_float, vp,
                                      i64, vp]
+        L.katz_multi_build.argtypes = [i32, vp, vp, i32, vp, C.POINTER(vp)]
+        L.katz_multi_free.argtypes = [vp]
+        L.katz_multi_free.restype = None
+        L.katz_multi_query.argtypes = [vp, vp, i32, C.POINTER(katz_query_opts), vp, i32, i64,
+                                       C.POINTER(katz_stats), vp, vp, vp]
+        L.katz_warmstart_train.argtypes = [vp, vp, i32, C.POINTER(katz_train_opts),
+                                           C.POINTER(katz_train_stats), vp]
+        L.katz_mlp_loss_grad.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp, vp, vp]
         L.katz_launch_count.argtypes = []
         L.katz_launch_count.restype = C.c_int64
         L.katz_profile_enable.argtypes = [i32]
         L.katz_profile_read.argtypes = [C.c_char_p, vp, vp, vp]
         L.katz_last_error.restype = C.c_char_p
         for name in EXPORTS:
-            if name not in ("katz_index_free", "katz_last_error", "katz_launch_count"):
+            if name not in ("katz_index_free", "katz_last_error", "katz_launch_count",
+                            "katz_multi_free"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -310,3 +330,68 @@ def katz_autotune(index, b: int, stream=None) -> dict:
     _check(lib().katz_autotune(index.handle, b, out.ctypes.data, ms.ctypes.data, _stream(stream)))
     return {"col_tile": int(out[0]), "ctas_per_sm": int(out[1]), "ms_best": float(ms[0]),
             "ms_default": float(ms[1])}
+
+
+class KatzMulti:
+    """Owner of a katz_multi* (many graphs answered together)."""
+
+    def __init__(self, handle: int, sizes):
+        self.handle = C.c_void_p(handle)
+        self.sizes = list(sizes)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.katz_multi_free(self.handle)
+            self.handle = C.c_void_p(0)
+
+
+def katz_multi_build(graphs, betas, value_dtype=KATZ_UNIT, stream=None) -> KatzMulti:
+    csrs, keep = [], []
+    for g in graphs:
+        c, k = _csr(g)
+        csrs.append(c)
+        keep.append(k)
+    arr = (katz_csr * len(csrs))(*csrs)
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    h = C.c_void_p()
+    _check(lib().katz_multi_build(len(csrs), C.cast(arr, C.c_void_p), b.ctypes.data, value_dtype,
+                                  _stream(stream), C.byref(h)))
+    return KatzMulti(h.value, [g.n for g in graphs])
+
+
+def katz_multi_query(multi, q, qpg, K_out, out_dtype=KATZ_F32, tol=1e-6,
+                     tol_kind=KATZ_TOL_ERROR_INF, max_iter=0, max_refine=0, stream=None):
+    """q: (g*qpg,) graph-local ids; K_out: (sum n_g, qpg).  Returns
+    (stats, iters (g*qpg,), rel_res (g*qpg,))."""
+    o = katz_query_opts(float(tol), tol_kind, KATZ_PREC_MIXED, max_iter, max_refine, 0, 0)
+    st = katz_stats()
+    total = len(multi.sizes) * qpg
+    iters = np.zeros(total, dtype=np.int32)
+    rel = np.zeros(total, dtype=np.float64)
+    code = lib().katz_multi_query(multi.handle, _ptr(q), qpg, C.byref(o), _ptr(K_out), out_dtype,
+                                  _ld(K_out), C.byref(st), iters.ctypes.data, rel.ctypes.data,
+                                  _stream(stream))
+    _check(code, allow=(KATZ_OK, KATZ_ENOCONV))
+    stats = {"iters": st.iters, "refine_steps": st.refine_steps, "max_rel_res": st.max_rel_res,
+             "ms": list(st.ms), "graph_replays": int(st.ms[4]), "status": STATUS_NAMES[code]}
+    return stats, iters, rel
+
+
+def katz_warmstart_train(index, q_train, hidden=256, epochs=20, batch=256, lr=1e-3,
+                         weight_decay=0.0, seed=20191212, stream=None) -> dict:
+    """Train the learned warm start on the method's own Katz vectors."""
+    q = np.ascontiguousarray(q_train, dtype=np.int32)
+    o = katz_train_opts(hidden, epochs, batch, lr, weight_decay, seed)
+    st = katz_train_stats()
+    _check(lib().katz_warmstart_train(index.handle, q.ctypes.data, len(q), C.byref(o),
+                                      C.byref(st), _stream(stream)))
+    return {"initial_loss": st.initial_loss, "final_loss": st.final_loss, "steps": st.steps,
+            "ms": st.ms}
+
+
+def katz_mlp_loss_grad(X, T, params, grads, din, dh, dout, stream=None) -> float:
+    """Forward/backward of the warm-start network on device tensors."""
+    loss = np.zeros(1, dtype=np.float64)
+    _check(lib().katz_mlp_loss_grad(int(X.shape[0]), din, dh, dout, _ptr(X), _ptr(T),
+                                    _ptr(params), _ptr(grads), loss.ctypes.data, _stream(stream)))
+    return float(loss[0])
