@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "KATZ_OK", 1: "KATZ_EINVAL", 2: "KATZ_ENOTSPD", 3: "KATZ_ENOC
 # every exported symbol of include/katz.h
 EXPORTS = ["katz_lambda_max", "katz_index_build", "katz_index_free", "katz_index_get_info",
            "katz_index_get_partition", "katz_partition", "katz_index_get_sigma", "katz_query_batch",
-           "cg_query_batch", "linkpred_topk", "katz_apply_M", "katz_autotune", "katz_gemm_bf16", "katz_launch_count",
+           "cg_query_batch", "linkpred_topk", "linkpred_topk_noalloc", "katz_apply_M", "katz_autotune", "katz_gemm_bf16", "katz_launch_count",
            "katz_profile_enable", "katz_profile_read", "katz_multi_build", "katz_multi_free",
            "katz_multi_query", "katz_warmstart_train", "katz_mlp_loss_grad", "katz_last_error"]
 
@@ -104,6 +104,7 @@ def lib() -> C.CDLL:
         L.katz_query_batch.argtypes = qargs
         L.cg_query_batch.argtypes = qargs
         L.linkpred_topk.argtypes = [vp, vp, i32, vp, i32, i64, i32, vp, vp, vp]
+        L.linkpred_topk_noalloc.argtypes = [vp, vp, i32, vp, i32, i64, i32, vp, vp, vp]
         L.katz_apply_M.argtypes = [vp, vp, vp, i32, i32, vp]
         L.katz_autotune.argtypes = [vp, i32, vp, vp, vp]
         L.katz_gemm_bf16.argtypes = [vp, i64, vp, i64, i32, i32, i32, C.c_float, C.c_float, vp,
@@ -290,6 +291,14 @@ def linkpred_topk(index, q, K, k_dtype, k, ids_out, scores_out, stream=None):
     ldk = _ld(K)
     _check(lib().linkpred_topk(index.handle, _ptr(q), b, _ptr(K), k_dtype, ldk, k,
                                _ptr(ids_out), _ptr(scores_out), _stream(stream)))
+
+
+def linkpred_topk_noalloc(index, q, K, k_dtype, k, ids_out, scores_out, stream=None):
+    """linkpred_topk with its scratch in a fixed library array (no device
+    allocation); q, K, ids_out and scores_out must be device tensors."""
+    b = int(q.shape[0])
+    _check(lib().linkpred_topk_noalloc(index.handle, _ptr(q), b, _ptr(K), k_dtype, _ld(K), k,
+                                       _ptr(ids_out), _ptr(scores_out), _stream(stream)))
 
 
 def katz_apply_M(index, X, Y, b, dtype, stream=None):
