@@ -44,17 +44,25 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
     ap.add_argument("--c", type=float, default=0.9, help="beta = c / lambda_max")
     ap.add_argument("--method", default="lrc", choices=["lrc", "cg"])
+    ap.add_argument("--workload", type=int, default=3, choices=[2, 3],
+                    help="3: n=4M modular graph (the metric's workload); 2: n=1M power law")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
     return ap.parse_args()
 
 
-def workload_desc(g, b, c, rank, scale):
+def workload_desc(g, b, c, rank, scale, workload=3):
+    if workload == 2:
+        desc = (f"Chung-Lu power law n={g.n:,} (exponent 2.1, mean degree 16, cap 20,000), "
+                f"FP32 values, b={b} queries, r={rank}, top-1% hubs, beta={c}/lambda_max, "
+                f"tol 1e-6 (inf-norm error bound)")
+    else:
+        desc = (f"modular SBM n={g.n:,} (512 lognormal communities, degree 20, 5% inter, "
+                f"2,000 hubs x ~5,000 edges), BF16 values, b={b} queries, r={rank}, "
+                f"beta={c}/lambda_max, tol 1e-6 (inf-norm error bound)")
     return {
-        "workload": (f"modular SBM n={g.n:,} (512 lognormal communities, degree 20, 5% inter, "
-                     f"2,000 hubs x ~5,000 edges), BF16 values, b={b} queries, r={rank}, "
-                     f"beta={c}/lambda_max, tol 1e-6 (inf-norm error bound)"),
+        "workload": desc,
         "n": g.n, "nnz": g.nnz, "global_batch": b, "rank": rank, "c": c, "scale": scale,
         "l2_flush": "inputs larger than L2 (graph 0.6 GB, FP32 n x b block 16 GB)",
     }
@@ -220,17 +228,21 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    g, q, c, rank_r = synth.workload(3, args.scale)
-    c = args.c
+    g, q, c, rank_r = synth.workload(args.workload, args.scale)
+    c = args.c if args.workload == 3 else 0.5
     b = len(q)
     if world > 1:  # replicas: each rank answers its own batch
         q = synth.queries(g.n, b, seed=synth.BASE_SEED + 300 + rank)
     t0 = time.perf_counter()
     lam = katz.katz_lambda_max(g, steps=96)
     beta = c / lam
-    n_hubs = int(g.meta["hubs"].shape[0])
-    idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_BF16, rank=rank_r,
-                                n_hubs=n_hubs, block_max=64, split=False)
+    if args.workload == 3:
+        n_hubs = int(g.meta["hubs"].shape[0])
+        idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_BF16, rank=rank_r,
+                                    n_hubs=n_hubs, block_max=64, split=False)
+    else:  # power law: the top-1% hubs shatter the rest into small blocks
+        idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_F32, rank=rank_r,
+                                    n_hubs=g.n // 100, block_max=64, split=True)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     info = idx.info()
@@ -354,7 +366,7 @@ def main():
                          f"1e-6 error bound (rtol {rtol:.2e}), {dt:.1f} s"}
 
     if rank == 0:
-        cfg = workload_desc(g, b, c, rank_r, args.scale)
+        cfg = workload_desc(g, b, c, rank_r, args.scale, args.workload)
         cfg.update({"method": args.method, "parallelism": "replicas" if world > 1 else "single",
                     "spmm_autotune": tune,
                     "n2": info["n2"], "n1": info["n1"], "index_build_s": build_s,

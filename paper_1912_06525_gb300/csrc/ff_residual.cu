@@ -56,10 +56,11 @@ __device__ __forceinline__ float weight(const void* val, int64_t k) {
   else return __bfloat162float(static_cast<const __nv_bfloat16*>(val)[k]);
 }
 
-// Warp per row and 128-column tile (4 per lane).  Float-float accumulation
-// of sum_j w_ij (hi_j + lo_j); R = beta*acc - k (the sparse RHS b is added
-// by ff_fix_rhs_kernel).  FP64-weighted graphs use FP32 weights here (exact
-// for the dyadic / unit weights used by this library's workloads).
+// Warp per row and 256-column tile (2 x 4 columns per lane).  Float-float
+// accumulation of sum_j w_ij (hi_j + lo_j); R = beta*acc - k (the sparse
+// RHS b is added by ff_fix_rhs_kernel).  FP64-weighted graphs use FP32
+// weights here (exact for the dyadic / unit weights used by this library's
+// workloads).
 template <int WT>
 __global__ void __launch_bounds__(256) ff_residual_kernel(Csr A, const float* __restrict__ Kh,
                                                           const float* __restrict__ Kl, int64_t ld,
@@ -67,11 +68,13 @@ __global__ void __launch_bounds__(256) ff_residual_kernel(Csr A, const float* __
   const int lane = threadIdx.x & 31;
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  const int c = blockIdx.y * 128 + lane * 4;
-  const bool cv = c < b;
+  const int c0 = blockIdx.y * 256 + lane * 4;
+  const bool cv0 = c0 < b, cv1 = c0 + 128 < b;
   for (int64_t i = warp; i < A.nrows; i += nwarps) {
     const int64_t k0 = A.rowptr[i], k1 = A.rowptr[i + 1];
-    FF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    FF acc[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) acc[t] = {0.f, 0.f};
     for (int64_t kb = k0; kb < k1; kb += 32) {
       const int64_t k = kb + lane;
       int cj = 0;
@@ -81,28 +84,41 @@ __global__ void __launch_bounds__(256) ff_residual_kernel(Csr A, const float* __
         wj = weight<WT>(A.val, k);
       }
       const int cnt = (int)(k1 - kb < 32 ? k1 - kb : 32);
-#pragma unroll 2
+#pragma unroll 4
       for (int s = 0; s < cnt; ++s) {
         const int j = __shfl_sync(0xffffffffu, cj, s);
         const float w = __shfl_sync(0xffffffffu, wj, s);
-        if (cv) {
-          const float4 h = __ldg(reinterpret_cast<const float4*>(Kh + int64_t(j) * ld + c));
-          const float4 l = __ldg(reinterpret_cast<const float4*>(Kl + int64_t(j) * ld + c));
+        const float* hr = Kh + int64_t(j) * ld + c0;
+        const float* lr = Kl + int64_t(j) * ld + c0;
+        if (cv0) {
+          const float4 h = __ldg(reinterpret_cast<const float4*>(hr));
+          const float4 l = __ldg(reinterpret_cast<const float4*>(lr));
           ff_axpy(acc[0], w, h.x, l.x);
           ff_axpy(acc[1], w, h.y, l.y);
           ff_axpy(acc[2], w, h.z, l.z);
           ff_axpy(acc[3], w, h.w, l.w);
         }
+        if (cv1) {
+          const float4 h = __ldg(reinterpret_cast<const float4*>(hr + 128));
+          const float4 l = __ldg(reinterpret_cast<const float4*>(lr + 128));
+          ff_axpy(acc[4], w, h.x, l.x);
+          ff_axpy(acc[5], w, h.y, l.y);
+          ff_axpy(acc[6], w, h.z, l.z);
+          ff_axpy(acc[7], w, h.w, l.w);
+        }
       }
     }
-    if (cv) {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int c = c0 + 128 * half;
+      if (half == 0 ? !cv0 : !cv1) continue;
       const float4 h = *reinterpret_cast<const float4*>(Kh + i * ld + c);
       const float4 l = *reinterpret_cast<const float4*>(Kl + i * ld + c);
       float4 r;
-      r.x = ff_residual(acc[0], beh, bel, h.x, l.x, 0.f, 0.f);
-      r.y = ff_residual(acc[1], beh, bel, h.y, l.y, 0.f, 0.f);
-      r.z = ff_residual(acc[2], beh, bel, h.z, l.z, 0.f, 0.f);
-      r.w = ff_residual(acc[3], beh, bel, h.w, l.w, 0.f, 0.f);
+      r.x = ff_residual(acc[4 * half + 0], beh, bel, h.x, l.x, 0.f, 0.f);
+      r.y = ff_residual(acc[4 * half + 1], beh, bel, h.y, l.y, 0.f, 0.f);
+      r.z = ff_residual(acc[4 * half + 2], beh, bel, h.z, l.z, 0.f, 0.f);
+      r.w = ff_residual(acc[4 * half + 3], beh, bel, h.w, l.w, 0.f, 0.f);
       *reinterpret_cast<float4*>(R + i * ld + c) = r;
     }
   }
@@ -187,7 +203,7 @@ void ff_residual(const Csr& A, const Csr& W, const int32_t* q, const int32_t* po
                    reinterpret_cast<uintptr_t>(R) % 16 == 0 && ld >= b,
                KATZ_EINVAL, "ff_residual: operands must be 16-byte aligned with padded rows");
   const float beh = float(beta), bel = float(beta - double(beh));
-  const int tiles = (int)ceil_div(b, 128);
+  const int tiles = (int)ceil_div(b, 256);
   int64_t ctas = std::min<int64_t>(ceil_div(A.nrows, 8), int64_t(num_sms()) * 8 / tiles);
   dim3 grid((unsigned)std::max<int64_t>(1, ctas), (unsigned)tiles);
   prof_begin(s);
