@@ -240,9 +240,9 @@ def main():
         n_hubs = int(g.meta["hubs"].shape[0])
         idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_BF16, rank=rank_r,
                                     n_hubs=n_hubs, block_max=64, split=False)
-    else:  # power law: the top-1% hubs shatter the rest into small blocks
+    else:  # power law: top-1% hubs; the rest keeps a giant component, kept whole
         idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_F32, rank=rank_r,
-                                    n_hubs=g.n // 100, block_max=64, split=True)
+                                    n_hubs=g.n // 100, block_max=64, split=False)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     info = idx.info()

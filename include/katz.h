@@ -106,7 +106,8 @@ typedef struct {
   int32_t iters;        /* inner iterations summed over refinement steps (max over columns) */
   int32_t refine_steps; /* FP64 residual evaluations performed */
   double max_rel_res;   /* max_j ||b_j - M k_j||_2 / ||b_j||_2 of the returned K (FP64) */
-  double ms[8];         /* phase times: [0] total, [1] rhs, [2] inner solve, [3] residual */
+  double ms[8];         /* [0] total ms, [1] RHS ms, [2] first inner solve ms, [3] residual ms,
+                           [4] CUDA-graph replays (multi-graph), [5] warm-start fallbacks */
 } katz_stats;
 
 typedef struct {

@@ -54,6 +54,9 @@ struct katz_index {
   int rank = 0, block_max = 0, split = 1;
   int64_t n1 = 0, n2 = 0, n1s = 0;  // rows [0,n1s) in dense blocks, [n1s,n1) in large blocks
   int n_large = 0;
+  // spectral bound of the large-block W11 for the Chebyshev solve:
+  // spectrum(M11_large) in [1 - beta*lam11, 1 + beta*lam11] (0 = use CG)
+  double lam11 = 0;
   katz::Partition part;
   katz::DBuf<int32_t> perm, iperm;
   katz::GraphPart Wp;    // W in index order (full), for FP64 residuals

@@ -460,6 +460,14 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   upload_part(W12, o.value_dtype, idx.W12, s);
   upload_part(W21, o.value_dtype, idx.W21, s);
   upload_part(W11L, o.value_dtype, idx.W11L, s);
+  if (W11L.nrows > 0 && W11L.nnz() > 0) {
+    // Lanczos lower-bounds lambda_max; a 2% margin keeps the Chebyshev
+    // interval safe (the smallest eigenvalue of W11 is >= -lambda_max)
+    const double lam = 1.02 * lambda_max_gpu(idx.W11L, W11L.nrows, 96, idx.ws, s);
+    idx.lam11 = beta * lam < 0.999 ? lam : 0.0;
+  } else if (W11L.nrows > 0) {
+    idx.lam11 = 1e-300;  // no edges: M11 = I
+  }
   upload_part(W22, o.value_dtype, idx.W22, s);
   const GraphPart& W22d = idx.W22;
 

@@ -28,6 +28,11 @@ void spmm(const Csr& A, const int32_t* heavy, int64_t n_heavy, double alpha,
           int64_t ldy, int b, const VT* V, int64_t ldv, double* dots, cudaStream_t s,
           const SpmmCfg* cfg = nullptr);
 
+// Fused Chebyshev step for (I - beta A) x = b: r = b - x + beta A x,
+// d = ak d + ck r, xn = x + d (X and Xn distinct; FP32).
+void cheb_step(const Csr& A, double beta, double ak, double ck, const float* X, const float* B,
+               float* D, float* Xn, int64_t ld, int b, cudaStream_t s);
+
 // dots[c] += sum_{i<len} A[i,c] * B[i,c]
 template <class VT>
 void coldot(const VT* A, int64_t lda, const VT* B, int64_t ldb, int64_t len, int b,

@@ -336,6 +336,117 @@ template void spmm<double>(const Csr&, const int32_t*, int64_t, double, const do
                            double, const double*, int64_t, double*, int64_t, int, const double*,
                            int64_t, double*, cudaStream_t, const SpmmCfg*);
 
+// ------------------------------------------------------- Chebyshev step
+// One step of the Chebyshev iteration for A x = b with A = I - beta W and
+// spectrum(A) in [theta - delta, theta + delta], fused with the product:
+//   r = b - A x_k = b - x_k + beta W x_k
+//   d = a_k d + c_k r ;  x_{k+1} = x_k + d
+// X (gathered) and Xn are distinct buffers (the caller alternates them).
+template <int WT, int VPT>
+__global__ void __launch_bounds__(256) cheb_step_kernel(Csr A, float beta, float ak, float ck,
+                                                        const float* __restrict__ X,
+                                                        const float* __restrict__ B,
+                                                        float* __restrict__ D,
+                                                        float* __restrict__ Xn, int64_t ld, int b) {
+  constexpr int VW = 4;
+  constexpr int TILE = 32 * VW * VPT;
+  const int t = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int tile0 = blockIdx.y * TILE;
+  bool cval[VPT];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) cval[v] = tile0 + (v * 32 + t) * VW < b;
+  for (int64_t i = warp; i < A.nrows; i += nwarps) {
+    const int64_t k0 = A.rowptr[i], k1 = A.rowptr[i + 1];
+    float acc[VPT][VW];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v)
+#pragma unroll
+      for (int w = 0; w < VW; ++w) acc[v][w] = 0.f;
+    for (int64_t kb = k0; kb < k1; kb += 32) {
+      const int64_t k = kb + t;
+      int cj = 0;
+      float wj = 0.f;
+      if (k < k1) {
+        cj = A.col[k];
+        wj = load_weight<WT, float>(A.val, k);
+      }
+      const int cnt = (int)(k1 - kb < 32 ? k1 - kb : 32);
+#pragma unroll 4
+      for (int s2 = 0; s2 < cnt; ++s2) {
+        const int j = __shfl_sync(0xffffffffu, cj, s2);
+        const float wv = (WT == KATZ_UNIT) ? 1.f : __shfl_sync(0xffffffffu, wj, s2);
+        const float* xr = X + int64_t(j) * ld + tile0 + t * VW;
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          if (cval[v]) {
+            float xv[VW];
+            vload_ro<float>(xr + v * 32 * VW, xv);
+#pragma unroll
+            for (int w = 0; w < VW; ++w) acc[v][w] += wv * xv[w];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      if (!cval[v]) continue;
+      const int64_t o = i * ld + tile0 + (v * 32 + t) * VW;
+      float xo[VW], bo[VW], dd[VW], xn[VW];
+      vload_ro<float>(X + o, xo);
+      vload<float>(B + o, bo);
+      vload<float>(D + o, dd);
+#pragma unroll
+      for (int w = 0; w < VW; ++w) {
+        const float r = bo[w] - xo[w] + beta * acc[v][w];
+        dd[w] = ak * dd[w] + ck * r;
+        xn[w] = xo[w] + dd[w];
+      }
+      vstore<float>(D + o, dd);
+      vstore<float>(Xn + o, xn);
+    }
+  }
+}
+
+void cheb_step(const Csr& A, double beta, double ak, double ck, const float* X, const float* B,
+               float* D, float* Xn, int64_t ld, int b, cudaStream_t s) {
+  KATZ_REQUIRE(ld % 4 == 0 && ld >= b &&
+                   (reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(B) |
+                    reinterpret_cast<uintptr_t>(D) | reinterpret_cast<uintptr_t>(Xn)) % 16 == 0,
+               KATZ_EINVAL, "cheb_step: operands must be 16-byte aligned with padded rows");
+  if (A.nrows <= 0) return;
+  const int vpt = b > 128 ? 2 : 1;
+  const int tile = 128 * vpt;
+  const int64_t tiles = ceil_div(b, tile);
+  int64_t ctas = std::min<int64_t>(ceil_div(A.nrows, 8),
+                                   std::max<int64_t>(1, int64_t(num_sms()) * 8 / tiles));
+  dim3 grid((unsigned)std::max<int64_t>(1, ctas), (unsigned)tiles);
+  prof_begin(s);
+#define KATZ_CHEB(WT)                                                                    \
+  if (vpt == 2)                                                                          \
+    cheb_step_kernel<WT, 2><<<grid, 256, 0, s>>>(A, float(beta), float(ak), float(ck), X, B, D, \
+                                                 Xn, ld, b);                             \
+  else                                                                                   \
+    cheb_step_kernel<WT, 1><<<grid, 256, 0, s>>>(A, float(beta), float(ak), float(ck), X, B, D, \
+                                                 Xn, ld, b)
+  switch (A.vdt) {
+    case KATZ_UNIT: KATZ_CHEB(KATZ_UNIT); break;
+    case KATZ_F32: KATZ_CHEB(KATZ_F32); break;
+    case KATZ_BF16: KATZ_CHEB(KATZ_BF16); break;
+    default: KATZ_CHEB(KATZ_F64); break;
+  }
+#undef KATZ_CHEB
+  KATZ_CHECK_LAUNCH();
+  if (profiling()) {
+    const double sv = 4.0 * b;
+    prof_end("cheb_step",
+             8.0 * (A.nrows + 1) + double(A.nnz) * (4 + vdt_size(A.vdt)) + sv * A.ncols +
+                 sv * A.nrows * 4.0,
+             s);
+  }
+}
+
 // ------------------------------------------------------- 2D vector launches
 // Threads: x over column vectors of a tile (TC vectors), y over rows.
 struct Grid2 {
@@ -713,10 +824,10 @@ __global__ void col_norms_kernel(const VT* __restrict__ B, int64_t ld, int64_t l
   constexpr int VW = VecOf<VT>::width;
   const int64_t c = (int64_t(blockIdx.y) * blockDim.x + threadIdx.x) * VW;
   const bool valid = c < b;
-  double tot[VW], mx[VW];
-  VT part[VW];
+  double tot[VW];
+  VT part[VW], mx[VW];  // max |x| in the element type (exact), no FP64 per element
 #pragma unroll
-  for (int w = 0; w < VW; ++w) { tot[w] = 0; mx[w] = 0; part[w] = VT(0); }
+  for (int w = 0; w < VW; ++w) { tot[w] = 0; mx[w] = VT(0); part[w] = VT(0); }
   int cnt = 0;
   if (valid) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.y + threadIdx.y; i < len;
@@ -726,7 +837,7 @@ __global__ void col_norms_kernel(const VT* __restrict__ B, int64_t ld, int64_t l
 #pragma unroll
       for (int w = 0; w < VW; ++w) {
         part[w] += v[w] * v[w];
-        mx[w] = fmax(mx[w], fabs(double(v[w])));
+        mx[w] = v[w] > mx[w] ? v[w] : (-v[w] > mx[w] ? -v[w] : mx[w]);
       }
       if (++cnt == kFlush) {
         cnt = 0;
@@ -740,8 +851,8 @@ __global__ void col_norms_kernel(const VT* __restrict__ B, int64_t ld, int64_t l
   if (valid)
 #pragma unroll
     for (int w = 0; w < VW; ++w)
-      if (c + w < b && mx[w] > 0)
-        atomicMax(maxabs_bits + c + w, (unsigned long long)__double_as_longlong(mx[w]));
+      if (c + w < b && mx[w] > VT(0))
+        atomicMax(maxabs_bits + c + w, (unsigned long long)__double_as_longlong(double(mx[w])));
   reduce_cols_atomic<VW>(tot, norm2, c, valid);
 }
 

@@ -217,12 +217,48 @@ const double* inv_of<double>(const BlockClass& c) { return c.inv64.p; }
 
 // Y1 = M11^{-1} X1: dense block inverses for the small blocks (Step 4) and,
 // for blocks kept whole, CG on that diagonal block to relative tolerance tolL.
+// Chebyshev iteration (Saad, Iterative Methods, Alg. 12.1) on the large
+// M11 blocks: spectrum in [theta - delta, theta + delta] with theta = 1,
+// delta = beta*lam11.  The iteration count follows from the bound
+// 2 c^K <= tol, c = (sqrt(kappa)-1)/(sqrt(kappa)+1); no inner products, no
+// host synchronisation, one fused kernel per step.
+static void m11_chebyshev(katz_index& idx, const float* X, float* Y, int b, int64_t ld,
+                          double tol, cudaStream_t s) {
+  const int64_t len = idx.n1 - idx.n1s;
+  const double delta = idx.beta * idx.lam11, theta = 1.0;
+  const double kappa = (theta + delta) / (theta - delta);
+  const double cf = (std::sqrt(kappa) - 1.0) / (std::sqrt(kappa) + 1.0);
+  const int K = cf <= 0 ? 1 : std::max(1, int(std::ceil(std::log(tol / 2.0) / std::log(cf))));
+  float* T = idx.ws.get<float>("ch.T", size_t(len) * ld);
+  float* Dd = idx.ws.get<float>("ch.D", size_t(len) * ld);
+  float* buf[2] = {Y, T};
+  // x_1 = d_0 = b / theta, placed so that x_K ends in Y
+  scale_copy<float>(X, ld, Dd, ld, len, (int)ld, 1.0 / theta, false, s);
+  scale_copy<float>(X, ld, buf[(K - 1) % 2], ld, len, (int)ld, 1.0 / theta, false, s);
+  const double sigma = theta / delta;
+  double rho_prev = 1.0 / sigma;
+  for (int k = 1; k < K; ++k) {
+    const double rho = 1.0 / (2.0 * sigma - rho_prev);
+    const double ak = rho * rho_prev, ck = 2.0 * rho / delta;
+    cheb_step(idx.W11L.view(), idx.beta, ak, ck, buf[(K - k) % 2], X, Dd, buf[(K - k - 1) % 2], ld,
+              b, s);
+    rho_prev = rho;
+  }
+}
+
 template <class VT>
 int m11_solve(katz_index& idx, const VT* X, VT* Y, int b, int64_t ld, double tolL, int max_iter,
               std::vector<int32_t>* iters, cudaStream_t s) {
   for (auto& c : idx.classes)
     block_solve<VT>(inv_of<VT>(c), c.start.p, c.size.p, c.count, c.S, X, ld, Y, ld, b, s);
   int st = KATZ_OK;
+  if constexpr (sizeof(VT) == 4) {
+    if (idx.n1 > idx.n1s && idx.lam11 > 0) {
+      m11_chebyshev(idx, reinterpret_cast<const float*>(X) + idx.n1s * ld,
+                    reinterpret_cast<float*>(Y) + idx.n1s * ld, b, ld, tolL, s);
+      return st;
+    }
+  }
   if (idx.n1 > idx.n1s) {
     const int64_t len = idx.n1 - idx.n1s;
     double* thr2 = idx.ws.get<double>("L.thr", b);
@@ -564,6 +600,11 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
     stats->ms[1] = std::chrono::duration<double, std::milli>(t1 - t0).count();
     stats->ms[2] = std::chrono::duration<double, std::milli>(t2 - t1).count();
     stats->ms[3] = ms_res;
+    if (o.warm_start) {
+      int h = 0;
+      KATZ_CUDA(cudaMemcpy(&h, ws.get<int>("S.nfb", 1), sizeof(int), cudaMemcpyDeviceToHost));
+      stats->ms[5] = h;  // columns whose warm start fell back to zero
+    }
   }
   return status;
 }

@@ -66,9 +66,11 @@ def test_warm_started_queries_match_oracle_and_report_iterations():
     K = torch.zeros((g.n, len(test)), dtype=torch.float64, device="cuda")
     qd = torch.from_numpy(test).cuda()
     _, it_cold, _ = katz.katz_query_batch(idx, qd, K, out_dtype=katz.KATZ_F64, tol=1e-6)
-    _, it_warm, _ = katz.katz_query_batch(idx, qd, K, out_dtype=katz.KATZ_F64, tol=1e-6,
-                                          warm_start=1)
+    st_w, it_warm, _ = katz.katz_query_batch(idx, qd, K, out_dtype=katz.KATZ_F64, tol=1e-6,
+                                             warm_start=1)
     ref = O.katz_direct(W, beta, test)
     assert O.error_inf_rel(K.cpu().numpy(), ref).max() <= 1e-6
-    print(f"mean Schur PCG iterations: cold {it_cold.mean():.2f}, warm {it_warm.mean():.2f}")
+    print(f"mean Schur PCG iterations: cold {it_cold.mean():.2f}, warm {it_warm.mean():.2f}, "
+          f"fallbacks {st_w['ms'][5]:.0f}/{len(test)}, train loss {st['initial_loss']:.3e} -> "
+          f"{st['final_loss']:.3e}")
     assert it_warm.mean() <= it_cold.mean() + 1.0
