@@ -283,7 +283,8 @@ def main():
     barrier(world)
     launches = katz.katz_launch_count() - l0
     prof = {t: katz.katz_profile_read(t) for t in
-            ("spmm_f32", "spmm_f64", "ff_residual", "block_solve_f32", "gemm_f32", "tc_gemm")}
+            ("spmm_f32", "spmm_f64", "cheb_step", "ff_residual", "fx_residual",
+             "block_solve_f32", "gemm_f32", "tc_gemm")}
     katz.katz_profile_enable(False)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps

@@ -23,4 +23,15 @@ void ff_out(const float* Kh, const float* Kl, int64_t ld, const int32_t* map, in
 // Zero the columns c with conv[c] != 0 (and the padding columns c >= b).
 void mask_columns(float* R, int64_t ld, int64_t len, int b, const int* conv, cudaStream_t s);
 
+// Unit-weight graphs: K in 64-bit fixed point, K[i][c] = Kfx[i][c] 2^-sh[c].
+// R = B - M K with exact integer sparse sums (see fx_residual.cu).
+void fx_residual(const Csr& A, const Csr& W, const int32_t* q, const int32_t* pos, int b,
+                 double beta, const long long* K, const int* sh, int64_t ld, float* R,
+                 int64_t maxdeg, cudaStream_t s);
+// K (+)= round(D 2^sh) (init: K = ...), rows x ld.
+void fx_add(long long* K, const float* D, int64_t rows, int64_t ld, const int* sh, int b,
+            bool init, cudaStream_t s);
+void fx_out(const long long* K, int64_t ld, const int* sh, const int32_t* map, int64_t n, int b,
+            void* out, int out_dt, int64_t ldk, cudaStream_t s);
+
 }  // namespace katz

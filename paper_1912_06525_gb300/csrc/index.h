@@ -46,6 +46,8 @@ struct katz_index {
   int64_t n = 0, nnz = 0;
   double beta = 0, lambda = 0;
   std::vector<int32_t> deg_h;  // node degrees (host), bound the RHS fix-up grid
+  int64_t maxdeg = 0;
+  bool unit_weights = false;  // every stored weight is exactly 1 (fixed-point residual)
   int vdt = KATZ_UNIT;
   katz::GraphPart W;  // node order
 

@@ -354,7 +354,14 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   idx.beta = beta;
   idx.vdt = o.value_dtype;
   idx.deg_h.resize(W.nrows);
-  for (int64_t i = 0; i < W.nrows; ++i) idx.deg_h[i] = (int32_t)(W.rowptr[i + 1] - W.rowptr[i]);
+  idx.maxdeg = 0;
+  for (int64_t i = 0; i < W.nrows; ++i) {
+    idx.deg_h[i] = (int32_t)(W.rowptr[i + 1] - W.rowptr[i]);
+    idx.maxdeg = std::max<int64_t>(idx.maxdeg, idx.deg_h[i]);
+  }
+  idx.unit_weights = true;
+  for (double v : W.val)
+    if (v != 1.0) { idx.unit_weights = false; break; }
   upload_part(W, o.value_dtype, idx.W, s);
   idx.lambda = lambda_max_gpu(idx.W, idx.n, 96, idx.ws, s);
   KATZ_REQUIRE(beta * idx.lambda < 1.0, KATZ_ENOTSPD,

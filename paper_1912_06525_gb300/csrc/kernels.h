@@ -28,10 +28,12 @@ void spmm(const Csr& A, const int32_t* heavy, int64_t n_heavy, double alpha,
           int64_t ldy, int b, const VT* V, int64_t ldv, double* dots, cudaStream_t s,
           const SpmmCfg* cfg = nullptr);
 
-// Fused Chebyshev step for (I - beta A) x = b: r = b - x + beta A x,
-// d = ak d + ck r, xn = x + d (X and Xn distinct; FP32).
-void cheb_step(const Csr& A, double beta, double ak, double ck, const float* X, const float* B,
-               float* D, float* Xn, int64_t ld, int b, cudaStream_t s);
+// Fused Chebyshev step for (I - beta A) x = b (FP32):
+//   x_{k+1} = x_k + ak (x_k - x_{k-1}) + ck (b - x_k + beta A x_k)
+// Xk != Xout; Xprev null means x_{k-1} = 0; Xprev may equal Xout.
+void cheb_step(const Csr& A, double beta, double ak, double ck, const float* Xk,
+               const float* Xprev, const float* B, float* Xout, int64_t ld, int b, cudaStream_t s,
+               const SpmmCfg* cfg = nullptr);
 
 // dots[c] += sum_{i<len} A[i,c] * B[i,c]
 template <class VT>

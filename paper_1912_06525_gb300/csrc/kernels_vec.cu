@@ -337,17 +337,19 @@ template void spmm<double>(const Csr&, const int32_t*, int64_t, double, const do
                            int64_t, double*, cudaStream_t, const SpmmCfg*);
 
 // ------------------------------------------------------- Chebyshev step
-// One step of the Chebyshev iteration for A x = b with A = I - beta W and
-// spectrum(A) in [theta - delta, theta + delta], fused with the product:
+// One step of the Chebyshev iteration for A x = b with A = I - beta W,
+// written as a three-term recurrence (no direction array), fused with the
+// product:
 //   r = b - A x_k = b - x_k + beta W x_k
-//   d = a_k d + c_k r ;  x_{k+1} = x_k + d
-// X (gathered) and Xn are distinct buffers (the caller alternates them).
+//   x_{k+1} = x_k + a_k (x_k - x_{k-1}) + c_k r
+// Xk is gathered and must differ from Xout; Xprev may be null (x_{k-1} = 0)
+// and may equal Xout (each row reads its own x_{k-1} before writing).
 template <int WT, int VPT>
 __global__ void __launch_bounds__(256) cheb_step_kernel(Csr A, float beta, float ak, float ck,
-                                                        const float* __restrict__ X,
-                                                        const float* __restrict__ B,
-                                                        float* __restrict__ D,
-                                                        float* __restrict__ Xn, int64_t ld, int b) {
+                                                        const float* __restrict__ Xk,
+                                                        const float* Xprev,
+                                                        const float* __restrict__ B, float* Xout,
+                                                        int64_t ld, int b) {
   constexpr int VW = 4;
   constexpr int TILE = 32 * VW * VPT;
   const int t = threadIdx.x & 31;
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(Csr A, float beta, float
       for (int s2 = 0; s2 < cnt; ++s2) {
         const int j = __shfl_sync(0xffffffffu, cj, s2);
         const float wv = (WT == KATZ_UNIT) ? 1.f : __shfl_sync(0xffffffffu, wj, s2);
-        const float* xr = X + int64_t(j) * ld + tile0 + t * VW;
+        const float* xr = Xk + int64_t(j) * ld + tile0 + t * VW;
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
           if (cval[v]) {
@@ -393,43 +395,43 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(Csr A, float beta, float
     for (int v = 0; v < VPT; ++v) {
       if (!cval[v]) continue;
       const int64_t o = i * ld + tile0 + (v * 32 + t) * VW;
-      float xo[VW], bo[VW], dd[VW], xn[VW];
-      vload_ro<float>(X + o, xo);
+      float xo[VW], bo[VW], xp[VW] = {0.f, 0.f, 0.f, 0.f}, xn[VW];
+      vload_ro<float>(Xk + o, xo);
       vload<float>(B + o, bo);
-      vload<float>(D + o, dd);
+      if (Xprev) vload<float>(Xprev + o, xp);
 #pragma unroll
       for (int w = 0; w < VW; ++w) {
         const float r = bo[w] - xo[w] + beta * acc[v][w];
-        dd[w] = ak * dd[w] + ck * r;
-        xn[w] = xo[w] + dd[w];
+        xn[w] = xo[w] + ak * (xo[w] - xp[w]) + ck * r;
       }
-      vstore<float>(D + o, dd);
-      vstore<float>(Xn + o, xn);
+      vstore<float>(Xout + o, xn);
     }
   }
 }
 
-void cheb_step(const Csr& A, double beta, double ak, double ck, const float* X, const float* B,
-               float* D, float* Xn, int64_t ld, int b, cudaStream_t s) {
-  KATZ_REQUIRE(ld % 4 == 0 && ld >= b &&
-                   (reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(B) |
-                    reinterpret_cast<uintptr_t>(D) | reinterpret_cast<uintptr_t>(Xn)) % 16 == 0,
+void cheb_step(const Csr& A, double beta, double ak, double ck, const float* Xk,
+               const float* Xprev, const float* B, float* Xout, int64_t ld, int b, cudaStream_t s,
+               const SpmmCfg* cfg) {
+  KATZ_REQUIRE(ld % 4 == 0 && ld >= b && Xk != Xout &&
+                   (reinterpret_cast<uintptr_t>(Xk) | reinterpret_cast<uintptr_t>(Xprev) |
+                    reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(Xout)) % 16 == 0,
                KATZ_EINVAL, "cheb_step: operands must be 16-byte aligned with padded rows");
   if (A.nrows <= 0) return;
   const int vpt = b > 128 ? 2 : 1;
   const int tile = 128 * vpt;
   const int64_t tiles = ceil_div(b, tile);
+  const int cps = cfg && cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm : 8;
   int64_t ctas = std::min<int64_t>(ceil_div(A.nrows, 8),
-                                   std::max<int64_t>(1, int64_t(num_sms()) * 8 / tiles));
+                                   std::max<int64_t>(1, int64_t(num_sms()) * cps / tiles));
   dim3 grid((unsigned)std::max<int64_t>(1, ctas), (unsigned)tiles);
   prof_begin(s);
-#define KATZ_CHEB(WT)                                                                    \
-  if (vpt == 2)                                                                          \
-    cheb_step_kernel<WT, 2><<<grid, 256, 0, s>>>(A, float(beta), float(ak), float(ck), X, B, D, \
-                                                 Xn, ld, b);                             \
-  else                                                                                   \
-    cheb_step_kernel<WT, 1><<<grid, 256, 0, s>>>(A, float(beta), float(ak), float(ck), X, B, D, \
-                                                 Xn, ld, b)
+#define KATZ_CHEB(WT)                                                                       \
+  if (vpt == 2)                                                                             \
+    cheb_step_kernel<WT, 2><<<grid, 256, 0, s>>>(A, float(beta), float(ak), float(ck), Xk, Xprev, \
+                                                 B, Xout, ld, b);                           \
+  else                                                                                      \
+    cheb_step_kernel<WT, 1><<<grid, 256, 0, s>>>(A, float(beta), float(ak), float(ck), Xk, Xprev, \
+                                                 B, Xout, ld, b)
   switch (A.vdt) {
     case KATZ_UNIT: KATZ_CHEB(KATZ_UNIT); break;
     case KATZ_F32: KATZ_CHEB(KATZ_F32); break;
@@ -439,10 +441,11 @@ void cheb_step(const Csr& A, double beta, double ak, double ck, const float* X, 
 #undef KATZ_CHEB
   KATZ_CHECK_LAUNCH();
   if (profiling()) {
+    // algorithmic: CSR once, x_k once, rows of x_k, b, x_{k-1} read once, x_{k+1} written
     const double sv = 4.0 * b;
     prof_end("cheb_step",
              8.0 * (A.nrows + 1) + double(A.nnz) * (4 + vdt_size(A.vdt)) + sv * A.ncols +
-                 sv * A.nrows * 4.0,
+                 sv * A.nrows * (Xprev ? 3.0 : 2.0),
              s);
   }
 }

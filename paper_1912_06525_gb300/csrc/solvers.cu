@@ -218,30 +218,37 @@ const double* inv_of<double>(const BlockClass& c) { return c.inv64.p; }
 // Y1 = M11^{-1} X1: dense block inverses for the small blocks (Step 4) and,
 // for blocks kept whole, CG on that diagonal block to relative tolerance tolL.
 // Chebyshev iteration (Saad, Iterative Methods, Alg. 12.1) on the large
-// M11 blocks: spectrum in [theta - delta, theta + delta] with theta = 1,
-// delta = beta*lam11.  The iteration count follows from the bound
-// 2 c^K <= tol, c = (sqrt(kappa)-1)/(sqrt(kappa)+1); no inner products, no
-// host synchronisation, one fused kernel per step.
+// M11 blocks, in three-term form: spectrum in [1 - delta, 1 + delta] with
+// delta = beta*lam11 (centre 1), so x_1 = b and
+//   x_{k+1} = x_k + rho_k rho_{k-1} (x_k - x_{k-1}) + (2 rho_k / delta) r_k,
+//   rho_0 = delta, rho_k = 1 / (2/delta - rho_{k-1}).
+// The iteration count follows from the bound 2 c^K <= tol with
+// c = (sqrt(kappa)-1)/(sqrt(kappa)+1).  No inner products, no host
+// synchronisation, one fused kernel per step; two buffers (x_{k+1}
+// overwrites x_{k-1} row by row).
 static void m11_chebyshev(katz_index& idx, const float* X, float* Y, int b, int64_t ld,
                           double tol, cudaStream_t s) {
   const int64_t len = idx.n1 - idx.n1s;
-  const double delta = idx.beta * idx.lam11, theta = 1.0;
-  const double kappa = (theta + delta) / (theta - delta);
+  const double delta = idx.beta * idx.lam11;
+  const double kappa = (1.0 + delta) / (1.0 - delta);
   const double cf = (std::sqrt(kappa) - 1.0) / (std::sqrt(kappa) + 1.0);
   const int K = cf <= 0 ? 1 : std::max(1, int(std::ceil(std::log(tol / 2.0) / std::log(cf))));
+  if (K == 1) {
+    KATZ_CUDA(cudaMemcpyAsync(Y, X, sizeof(float) * len * ld, cudaMemcpyDeviceToDevice, s));
+    return;
+  }
   float* T = idx.ws.get<float>("ch.T", size_t(len) * ld);
-  float* Dd = idx.ws.get<float>("ch.D", size_t(len) * ld);
-  float* buf[2] = {Y, T};
-  // x_1 = d_0 = b / theta, placed so that x_K ends in Y
-  scale_copy<float>(X, ld, Dd, ld, len, (int)ld, 1.0 / theta, false, s);
-  scale_copy<float>(X, ld, buf[(K - 1) % 2], ld, len, (int)ld, 1.0 / theta, false, s);
-  const double sigma = theta / delta;
-  double rho_prev = 1.0 / sigma;
+  // x_k for k >= 2 alternates between Y and T so that x_K lands in Y
+  auto slot = [&](int k) { return ((K - k) % 2 == 0) ? Y : T; };
+  const double sigma = 1.0 / delta;
+  double rho_prev = delta;  // rho_0 = 1/sigma
+  const SpmmCfg* cfg = idx.W11L.cfg(b);
   for (int k = 1; k < K; ++k) {
     const double rho = 1.0 / (2.0 * sigma - rho_prev);
     const double ak = rho * rho_prev, ck = 2.0 * rho / delta;
-    cheb_step(idx.W11L.view(), idx.beta, ak, ck, buf[(K - k) % 2], X, Dd, buf[(K - k - 1) % 2], ld,
-              b, s);
+    const float* xk = k == 1 ? X : slot(k);
+    const float* xprev = k == 1 ? nullptr : (k == 2 ? X : slot(k - 1));
+    cheb_step(idx.W11L.view(), idx.beta, ak, ck, xk, xprev, X, slot(k + 1), ld, b, s, cfg);
     rho_prev = rho;
   }
 }
@@ -536,8 +543,28 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
 
   float* R = ws.get<float>("q.Rin", size_t(n) * ld);
   float* D = ws.get<float>("q.D", size_t(n) * ld);
-  float* Kh = ws.get<float>("q.Kh", size_t(n) * ld);
-  float* Kl = ws.get<float>("q.Kl", size_t(n) * ld);
+  // K: 64-bit fixed point for unit-weight graphs, else a float-float pair
+  const bool fixed = idx.unit_weights && idx.vdt != KATZ_F64;
+  float* Kh = nullptr;
+  float* Kl = nullptr;
+  long long* Kfx = nullptr;
+  int* sh = ws.get<int>("q.sh", b);
+  if (fixed) {
+    Kfx = ws.get<long long>("q.Kfx", size_t(n) * ld);
+    std::vector<double> hb(b);
+    KATZ_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
+    KATZ_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> hs(b);
+    for (int c = 0; c < b; ++c) {
+      const double B = std::sqrt(hb[c]) / omc;  // >= ||k_c||_inf
+      const double top = 16.0 * double(idx.maxdeg + 1) * B;
+      hs[c] = top > 0 ? std::min(100, std::max(0, int(std::floor(62.0 - std::log2(top))))) : 0;
+    }
+    KATZ_CUDA(cudaMemcpyAsync(sh, hs.data(), sizeof(int) * b, cudaMemcpyHostToDevice, s));
+  } else {
+    Kh = ws.get<float>("q.Kh", size_t(n) * ld);
+    Kl = ws.get<float>("q.Kl", size_t(n) * ld);
+  }
   KATZ_CUDA(cudaMemsetAsync(R, 0, sizeof(float) * n * ld, s));
   build_rhs<float>(idx.W.view(), q, b, idx.beta, pos, R, ld, s);
   inner_thresholds_kernel<<<1, 1024, 0, s>>>(bn2, thr2, tau, b, conv, thr2_in, nopen);
@@ -551,9 +578,12 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
     K20 = g;
   }
   const auto t1 = clk::now();
-  int status = inner_solve<float>(idx, use_lrc, R, Kh, b, ld, thr2_in, tol_rel, max_iter, &iters, s,
-                                  K20);
-  KATZ_CUDA(cudaMemsetAsync(Kl, 0, sizeof(float) * n * ld, s));
+  int status = inner_solve<float>(idx, use_lrc, R, fixed ? D : Kh, b, ld, thr2_in, tol_rel,
+                                  max_iter, &iters, s, K20);
+  if (fixed)
+    fx_add(Kfx, D, n, ld, sh, b, true, s);
+  else
+    KATZ_CUDA(cudaMemsetAsync(Kl, 0, sizeof(float) * n * ld, s));
   KATZ_CUDA(cudaStreamSynchronize(s));
   const auto t2 = clk::now();
   double ms_res = 0;
@@ -561,7 +591,10 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   if (status == KATZ_OK || status == KATZ_ENOCONV) {
     for (;;) {
       const auto r0 = clk::now();
-      ff_residual(G.view(), idx.W.view(), q, pos, b, idx.beta, Kh, Kl, ld, R, maxdeg, s);
+      if (fixed)
+        fx_residual(G.view(), idx.W.view(), q, pos, b, idx.beta, Kfx, sh, ld, R, maxdeg, s);
+      else
+        ff_residual(G.view(), idx.W.view(), q, pos, b, idx.beta, Kh, Kl, ld, R, maxdeg, s);
       KATZ_CUDA(cudaMemsetAsync(rr, 0, sizeof(double) * bpad(b), s));
       coldot<float>(R, ld, R, ld, n, b, rr, s);
       inner_thresholds_kernel<<<1, 1024, 0, s>>>(rr, thr2, tau, b, conv, thr2_in, nopen);
@@ -572,17 +605,35 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
       if (open == 0) { status = KATZ_OK; break; }
       if (refine > max_refine) { status = KATZ_ENOCONV; break; }
       mask_columns(R, ld, n, b, conv, s);
-      const int st = inner_solve<float>(idx, use_lrc, R, D, b, ld, thr2_in, tol_rel, max_iter,
+      // the correction solve only has to bring every open column below its
+      // threshold: relative tolerance = tightest 0.3 * thr_c / ||r_c||
+      double tol_step = 1.0;
+      {
+        std::vector<double> hr(b), ht(b);
+        KATZ_CUDA(cudaMemcpyAsync(hr.data(), rr, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
+        KATZ_CUDA(cudaMemcpyAsync(ht.data(), thr2, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
+        KATZ_CUDA(cudaStreamSynchronize(s));
+        for (int c = 0; c < b; ++c)
+          if (hr[c] > ht[c] && hr[c] > 0) tol_step = std::min(tol_step, 0.3 * std::sqrt(ht[c] / hr[c]));
+        tol_step = std::max(tol_step, tau);
+      }
+      const int st = inner_solve<float>(idx, use_lrc, R, D, b, ld, thr2_in, tol_step, max_iter,
                                         &iters, s);
       if (st == KATZ_ENOTSPD) { status = st; break; }
-      ff_add(Kh, Kl, D, n * ld, s);
+      if (fixed)
+        fx_add(Kfx, D, n, ld, sh, b, false, s);
+      else
+        ff_add(Kh, Kl, D, n * ld, s);
     }
     std::vector<double> hr(b), hb(b);
     KATZ_CUDA(cudaMemcpyAsync(hr.data(), rr, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
     KATZ_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
     KATZ_CUDA(cudaStreamSynchronize(s));
     for (int c = 0; c < b; ++c) relres[c] = hb[c] > 0 ? std::sqrt(hr[c] / hb[c]) : std::sqrt(hr[c]);
-    ff_out(Kh, Kl, ld, pos, n, b, out.K, out.dtype, out.ldk, s);
+    if (fixed)
+      fx_out(Kfx, ld, sh, pos, n, b, out.K, out.dtype, out.ldk, s);
+    else
+      ff_out(Kh, Kl, ld, pos, n, b, out.K, out.dtype, out.ldk, s);
     KATZ_CUDA(cudaStreamSynchronize(s));
   }
   const auto t3 = clk::now();
