@@ -23,10 +23,6 @@ __device__ __forceinline__ FF two_sum(float a, float b) {
   const float bb = s - a;
   return {s, (a - (s - bb)) + (b - bb)};
 }
-__device__ __forceinline__ FF fast_two_sum(float a, float b) {
-  const float s = a + b;
-  return {s, b - (s - a)};
-}
 // exact-ish split of a 64-bit integer into float hi + lo
 __device__ __forceinline__ FF ll_to_ff(long long v) {
   const float hi = __ll2float_rn(v);
@@ -83,10 +79,10 @@ __global__ void __launch_bounds__(256) fx_residual_kernel(Csr A, const long long
       const longlong2 a = *reinterpret_cast<const longlong2*>(K + i * ld + c);
       const longlong2 bq = *reinterpret_cast<const longlong2*>(K + i * ld + c + 2);
       float4 r;
-      r.x = fx_out(acc[0], beh, bel, a.x, 0.f, 0.f, shc[0]);
-      r.y = fx_out(acc[1], beh, bel, a.y, 0.f, 0.f, shc[1]);
-      r.z = fx_out(acc[2], beh, bel, bq.x, 0.f, 0.f, shc[2]);
-      r.w = fx_out(acc[3], beh, bel, bq.y, 0.f, 0.f, shc[3]);
+      r.x = fx_out(acc[0], a.x, beh, bel, 0.f, 0.f, shc[0]);
+      r.y = fx_out(acc[1], a.y, beh, bel, 0.f, 0.f, shc[1]);
+      r.z = fx_out(acc[2], bq.x, beh, bel, 0.f, 0.f, shc[2]);
+      r.w = fx_out(acc[3], bq.y, beh, bel, 0.f, 0.f, shc[3]);
       *reinterpret_cast<float4*>(R + i * ld + c) = r;
     }
   }
@@ -112,7 +108,7 @@ __global__ void fx_fix_rhs_kernel(Csr A, Csr W, const int32_t* q, const int32_t*
     // b in units of 2^-s as float-float
     const double bv = ldexp(beta, s);
     const float bh = float(bv), bl = float(bv - double(bh));
-    R[i * ld + j] = fx_out(acc, beh, bel, K[i * ld + j], bh, bl, s);
+    R[i * ld + j] = fx_out(acc, K[i * ld + j], beh, bel, bh, bl, s);
   }
 }
 
