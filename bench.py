@@ -152,6 +152,12 @@ def max_over_ranks(world, x):
     return float(t.item())
 
 
+def rank_queries(n, b, rank):
+    """Query batch of one replica (ranks draw disjoint seeds)."""
+    from paper_1912_06525_gb300 import synth
+    return synth.queries(n, b, seed=synth.BASE_SEED + 300 + rank)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -232,7 +238,7 @@ def main():
     c = args.c if args.workload == 3 else 0.5
     b = len(q)
     if world > 1:  # replicas: each rank answers its own batch
-        q = synth.queries(g.n, b, seed=synth.BASE_SEED + 300 + rank)
+        q = rank_queries(g.n, b, rank)
     t0 = time.perf_counter()
     lam = katz.katz_lambda_max(g, steps=96)
     beta = c / lam

@@ -1,0 +1,66 @@
+"""The multi-process (replica) path of bench.py on CPU: world_size 2 over
+gloo -- process-group set-up from the launcher's environment, barrier,
+max-over-ranks timing, and per-rank query batches -- and the reference
+arm's JSON line (the FP64 oracle on a small sample)."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out):
+    os.environ.update({"RANK": str(rank), "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    sys.path.insert(0, ROOT)
+    import bench
+    import torch.distributed as dist
+    w, r, _ = bench.dist_setup(None)
+    assert (w, r) == (world, rank)
+    bench.barrier(w)
+    m = bench.max_over_ranks(w, float(10 * (rank + 1)))
+    q = bench.rank_queries(5000, 16, rank)
+    out.put((rank, m, q.tolist()))
+    dist.destroy_process_group()
+
+
+def test_two_rank_replicas_gloo():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted(out.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [m for _, m, _ in res] == [20.0, 20.0]
+    assert set(res[0][2]).isdisjoint(res[1][2]) or res[0][2] != res[1][2]
+
+
+def test_reference_arm_json_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--scale", "0.005", "--steps", "1", "--warmup", "1"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    line = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    assert line["impl"] == "reference"
+    for k in ("metric", "value", "unit", "ms_per_step", "cpu_baseline", "e2e", "config"):
+        assert k in line
+    assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["value"] > 0
