@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
     ap.add_argument("--c", type=float, default=0.9, help="beta = c / lambda_max")
     ap.add_argument("--method", default="lrc", choices=["lrc", "cg"])
+    ap.add_argument("--batch", type=int, default=0,
+                    help="override the query batch width b (small profiling cases)")
     ap.add_argument("--workload", type=int, default=3, choices=[2, 3],
                     help="3: n=4M modular graph (the metric's workload); 2: n=1M power law")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -236,6 +238,8 @@ def main():
 
     g, q, c, rank_r = synth.workload(args.workload, args.scale)
     c = args.c if args.workload == 3 else 0.5
+    if args.batch > 0:
+        q = synth.queries(g.n, args.batch, seed=synth.BASE_SEED + 77)
     b = len(q)
     if world > 1:  # replicas: each rank answers its own batch
         q = rank_queries(g.n, b, rank)

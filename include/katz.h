@@ -59,6 +59,15 @@ extern "C" {
 #define KATZ_PREC_F64 2   /* every vector and reduction in FP64 (reference speed path) */
 
 /* ---- stopping criteria ---- */
+/* Kernel of the wide fused sparse products (KATZ_PREC_MIXED and F32 paths):
+ * AUTO uses what katz_autotune measured faster for the operator and width
+ * (the register kernel if untuned); REGISTER: warp-per-row register
+ * gathers; PIPELINED: TMA bulk-copy gathers into a shared-memory ring
+ * (used where applicable: padded width >= 64, weights unit/FP32/BF16). */
+#define KATZ_GATHER_AUTO 0
+#define KATZ_GATHER_REGISTER 1
+#define KATZ_GATHER_PIPELINED 2
+
 #define KATZ_TOL_RESIDUAL 0  /* stop column j when ||b_j - M k_j||_2 <= tol * ||b_j||_2 */
 #define KATZ_TOL_ERROR_INF 1 /* stop when ||b_j - M k_j||_2 <= tol * (1 - beta*lambda) * ||b_j||_inf,
                                 which guarantees ||k_j - k_j*||_inf <= tol * ||k_j*||_inf for
@@ -100,6 +109,8 @@ typedef struct {
   int32_t max_refine;  /* cap on FP64 refinement steps (0 = 12) */
   int32_t rhs_width;   /* columns solved together (0 = all b at once) */
   int32_t warm_start;  /* 1: start LRC from the learned warm start (needs a trained network) */
+  int32_t gather_kernel; /* KATZ_GATHER_*: kernel of the wide sparse products (Chebyshev
+                            steps of the large M11 blocks, refinement residual) */
 } katz_query_opts;
 
 typedef struct {
@@ -227,9 +238,12 @@ int katz_apply_M(const katz_index* idx, const void* X, void* Y, int32_t b,
  * product (columns per warp-row tile in {128..1024} x CTAs per SM in
  * {2..16}) on the index's operators for right-hand-side width b, keeps the
  * fastest per operator for later queries with that b, and caches the
- * choice per (rows, nnz, b, value type) in the process.  out[0] = chosen
- * column tile (0 = default), out[1] = CTAs per SM; ms[0] = best time,
- * ms[1] = time of the default shape (per product, FP32 vectors). */
+ * choice per (rows, nnz, b, value type) in the process; on the large-block
+ * operator it also chooses between the register and the pipelined (TMA
+ * bulk-copy) Chebyshev step.  out (3 ints): out[0] = chosen column tile
+ * (0 = default), out[1] = CTAs per SM, out[2] = 1 if the pipelined
+ * Chebyshev step was chosen; ms[0] = best time, ms[1] = time of the
+ * default shape (per product, FP32 vectors). */
 int katz_autotune(katz_index* idx, int32_t b, int32_t* out, double* ms, void* stream);
 
 /* D = A * B^T on the tcgen05 tensor cores (BF16 operands, FP32

@@ -2,10 +2,14 @@
 // candidate shapes (columns per warp-row tile x CTAs per SM) of the
 // multi-RHS CSR product on each operator of an index with CUDA events, keeps
 // the fastest per operator, and caches the choice per (rows, nnz, b, value
-// type) for the process so indexes of the same graph reuse it.
+// type) for the process so indexes of the same graph reuse it.  Where the
+// pipelined (TMA bulk-copy) kernels apply it also times them against the
+// register kernels -- the fused Chebyshev step on the large-block operator,
+// the refinement residual on the full operators -- and keeps the faster.
 #include <mutex>
 #include <tuple>
 
+#include "ff_residual.h"
 #include "index.h"
 
 namespace katz {
@@ -34,10 +38,58 @@ double time_cfg(const GraphPart& g, const SpmmCfg& c, const float* X, float* Y, 
   return ms / reps;
 }
 
-// Best shape for one operator (square operators only: X and Y share rows).
+enum class Fused { none, cheb, residual };
+
+// Mean time of `reps` launches of the fused product (after one warm-up).
+template <class F>
+double time_launches(F&& launch, cudaStream_t s, int reps) {
+  cudaEvent_t e0, e1;
+  KATZ_CUDA(cudaEventCreate(&e0));
+  KATZ_CUDA(cudaEventCreate(&e1));
+  launch();
+  KATZ_CUDA(cudaEventRecord(e0, s));
+  for (int r = 0; r < reps; ++r) launch();
+  KATZ_CUDA(cudaEventRecord(e1, s));
+  KATZ_CUDA(cudaEventSynchronize(e1));
+  float ms = 0;
+  KATZ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms / reps;
+}
+
+// Register (false) or pipelined (true) kernel faster for the fused product?
+bool pipe_faster(const GraphPart& g, Fused kind, bool unit, const SpmmCfg& c, float* X, float* Y,
+                 float* Z, int b, int64_t ld, Workspace& ws, cudaStream_t s, int reps) {
+  int* err = ws.get<int>("pipe.err", 1);
+  KATZ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  double t_reg, t_pipe;
+  if (kind == Fused::cheb) {
+    t_reg = time_launches([&] { cheb_step(g.view(), 0.01, 0.1, 1.0, X, X, X, Y, ld, b, s, &c); }, s, reps);
+    t_pipe = time_launches(
+        [&] { pipe_cheb_step(g.view(), g.ps, unit, 0.01, 0.1, 1.0, X, X, X, Y, ld, err, s); }, s, reps);
+  } else {
+    t_reg = time_launches(
+        [&] { ffr_update(g.view(), 0.01, X, Y, Z, nullptr, nullptr, true, ld, b, nullptr, &c, s); },
+        s, reps);
+    t_pipe = time_launches(
+        [&] {
+          pipe_residual(g.view(), g.ps, unit, 0.01, X, Y, Z, nullptr, nullptr, true, ld, b, nullptr,
+                        err, s);
+        },
+        s, reps);
+  }
+  int herr = 0;
+  KATZ_CUDA(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+  KATZ_REQUIRE(herr == 0, KATZ_ECUDA, "pipelined gather kernel: a wait timed out");
+  return t_pipe < t_reg;
+}
+
+// Best shape for one operator (square operators only: X and Y share rows);
+// kind: the fused product to choose the register or pipelined kernel for.
 SpmmCfg tune_part(GraphPart& g, int b, Workspace& ws, cudaStream_t s, double* best_ms,
-                  double* def_ms) {
-  const auto key = std::make_tuple(g.csr.nrows, g.csr.nnz, b, g.csr.vdt);
+                  double* def_ms, Fused kind = Fused::none, bool unit = false) {
+  const auto key = std::make_tuple(g.csr.nrows, g.csr.nnz, b, g.csr.vdt * 4 + int(kind));
   {
     std::lock_guard<std::mutex> l(g_mu);
     auto it = g_cache.find(key);
@@ -68,6 +120,11 @@ SpmmCfg tune_part(GraphPart& g, int b, Workspace& ws, cudaStream_t s, double* be
       }
     }
   }
+  if (kind != Fused::none && pipe_eligible(g.ps, ld) && (unit || g.csr.vdt != KATZ_F64)) {
+    float* Z = ws.get<float>("tune.Z", size_t(rows) * ld);
+    best.pipe = pipe_faster(g, kind, unit, best, X, Y, Z, b, ld, ws, s, reps);
+    ws.release("tune.Z");
+  }
   g.tuned[b] = best;
   std::lock_guard<std::mutex> l(g_mu);
   g_cache[key] = best;
@@ -78,15 +135,17 @@ SpmmCfg tune_part(GraphPart& g, int b, Workspace& ws, cudaStream_t s, double* be
 TuneResult autotune(katz_index& idx, int b, cudaStream_t s) {
   TuneResult r;
   double best = 0, def = 0;
-  SpmmCfg c = tune_part(idx.W, b, idx.ws, s, &best, &def);
+  SpmmCfg c = tune_part(idx.W, b, idx.ws, s, &best, &def, Fused::residual, idx.unit_weights);
   r.col_tile = c.col_tile;
   r.ctas_per_sm = c.ctas_per_sm;
   r.ms_best = best;
   r.ms_default = def;
   if (idx.lrc) {
     double b2, d2;
-    tune_part(idx.Wp, b, idx.ws, s, &b2, &d2);
-    if (idx.W11L.csr.nrows > 0) tune_part(idx.W11L, b, idx.ws, s, &b2, &d2);
+    tune_part(idx.Wp, b, idx.ws, s, &b2, &d2, Fused::residual, idx.unit_weights);
+    if (idx.W11L.csr.nrows > 0)
+      r.cheb_pipe =
+          tune_part(idx.W11L, b, idx.ws, s, &b2, &d2, Fused::cheb, idx.unit_weights).pipe;
   }
   // release the tuning scratch
   idx.ws.release("tune.X");

@@ -1,11 +1,13 @@
-// Residual of the full system, R = B - M K, evaluated in double-FP32
-// ("float-float") arithmetic.  K is kept as an unevaluated sum hi + lo of two
-// FP32 arrays; products and sums use the error-free transformations TwoSum
-// (Knuth) and TwoProd (Dekker, via FMA), giving ~48 significant bits with
-// FP32 instructions only.  On GB300 the FP64 pipe is ~60x slower than FP32,
-// so this is what makes the refinement residual cheap.  The rounding of R to
-// FP32 happens after the cancellation b - (k - beta W k) has been carried
-// out in float-float, so R is accurate to FP32 relative to itself.
+// Refinement residual of the full system in double-FP32 ("float-float")
+// arithmetic.  The solution is kept as an unevaluated sum Kh + Kl of two FP32
+// arrays and the residual as Rh + Rl; every pass gathers one FP32 operand X
+// (the first FP32 solution, then each FP32 correction) and updates
+//   R <- R - M X  (M = I - beta A),   K <- K + X,
+// with the sparse sums accumulated by the error-free transformations TwoSum
+// (Knuth) and TwoProd (Dekker, via FMA): ~48 significant bits with FP32
+// instructions only (GB300's FP64 pipe is ~60x slower than FP32) and 4-byte
+// gathers.  Rh, rounded to FP32 after the cancellation, is the right-hand
+// side of the next FP32 correction solve.
 #include "ff_residual.h"
 
 namespace katz {
@@ -28,26 +30,6 @@ __device__ __forceinline__ FF fast_two_sum(float a, float b) {  // |a| >= |b|
   return {s, b - (s - a)};
 }
 
-// acc += w * (xh + xl)
-__device__ __forceinline__ void ff_axpy(FF& acc, float w, float xh, float xl) {
-  const float p = w * xh;
-  const float pe = __fmaf_rn(w, xh, -p);
-  const FF s = two_sum(acc.hi, p);
-  acc.hi = s.hi;
-  acc.lo += s.lo + pe + w * xl;
-}
-
-// (beta_h + beta_l) * acc - (kh + kl) + (bh + bl), rounded to FP32
-__device__ __forceinline__ float ff_residual(FF acc, float beh, float bel, float kh, float kl,
-                                             float bh, float bl) {
-  acc = fast_two_sum(acc.hi, acc.lo);
-  const float ph = beh * acc.hi;
-  const float pe = __fmaf_rn(beh, acc.hi, -ph) + beh * acc.lo + bel * acc.hi;
-  const FF s1 = two_sum(ph, -kh);
-  const FF s2 = two_sum(s1.hi, bh);
-  return s2.hi + (s1.lo + s2.lo + pe - kl + bl);
-}
-
 template <int WT>
 __device__ __forceinline__ float weight(const void* val, int64_t k) {
   if constexpr (WT == KATZ_UNIT) return 1.f;
@@ -56,114 +38,178 @@ __device__ __forceinline__ float weight(const void* val, int64_t k) {
   else return __bfloat162float(static_cast<const __nv_bfloat16*>(val)[k]);
 }
 
-// Warp per row and 256-column tile (2 x 4 columns per lane).  Float-float
-// accumulation of sum_j w_ij (hi_j + lo_j); R = beta*acc - k (the sparse
-// RHS b is added by ff_fix_rhs_kernel).  FP64-weighted graphs use FP32
-// weights here (exact for the dyadic / unit weights used by this library's
-// workloads).
-template <int WT>
-__global__ void __launch_bounds__(256) ff_residual_kernel(Csr A, const float* __restrict__ Kh,
-                                                          const float* __restrict__ Kl, int64_t ld,
-                                                          float beh, float bel, float* R, int b) {
-  const int lane = threadIdx.x & 31;
+// acc += w * x (w * x exact through FMA)
+template <bool UNIT>
+__device__ __forceinline__ void ff_acc(FF& acc, float w, float x) {
+  if constexpr (UNIT) {
+    const FF t = two_sum(acc.hi, x);
+    acc.hi = t.hi;
+    acc.lo += t.lo;
+  } else {
+    const float p = w * x;
+    const float pe = __fmaf_rn(w, x, -p);
+    const FF t = two_sum(acc.hi, p);
+    acc.hi = t.hi;
+    acc.lo += t.lo + pe;
+  }
+}
+
+// (rh, rl) + beta * acc - x, renormalised (beta = beh + bel)
+__device__ __forceinline__ FF ff_res(FF acc, float beh, float bel, float x, float rh, float rl) {
+  const FF s = fast_two_sum(acc.hi, acc.lo);
+  const float ph = beh * s.hi;
+  const float pe = __fmaf_rn(beh, s.hi, -ph) + beh * s.lo + bel * s.hi;
+  const FF t1 = two_sum(ph, -x);
+  const FF t2 = two_sum(t1.hi, rh);
+  return fast_two_sum(t2.hi, t1.lo + t2.lo + pe + rl);
+}
+
+// Warp per row (grid-stride), VPT float4 column groups per lane per tile of
+// 128 * VPT columns.  Column sums of Rh^2: FP32 over at most 64 rows per
+// lane, then FP64 in shared memory per warp, then one atomic per column and
+// CTA.
+template <int WT, int VPT, bool INIT>
+__global__ void __launch_bounds__(256) ffr_rows_kernel(Csr A, const float* __restrict__ X,
+                                                       float* Rh, float* Rl, float* Kh, float* Kl,
+                                                       int64_t ld, float beh, float bel,
+                                                       double* rr, int b) {
+  constexpr int VW = 4;
+  constexpr int TILE = 32 * VW * VPT;
+  constexpr bool UNIT = WT == KATZ_UNIT;
+  __shared__ double red[8][TILE];
+  const int t = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  const int c0 = blockIdx.y * 256 + lane * 4;
-  const bool cv0 = c0 < b, cv1 = c0 + 128 < b;
+  const int64_t tile0 = int64_t(blockIdx.y) * TILE;
+  for (int c = threadIdx.x; c < 8 * TILE; c += blockDim.x) (&red[0][0])[c] = 0.0;
+  bool cval[VPT];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) cval[v] = tile0 + (v * 32 + t) * VW < ld;
+  float sq[VPT][VW];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v)
+#pragma unroll
+    for (int w = 0; w < VW; ++w) sq[v][w] = 0.f;
+  int nsq = 0;
+  __syncthreads();
   for (int64_t i = warp; i < A.nrows; i += nwarps) {
     const int64_t k0 = A.rowptr[i], k1 = A.rowptr[i + 1];
-    FF acc[8];
+    FF acc[VPT][VW];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) acc[t] = {0.f, 0.f};
+    for (int v = 0; v < VPT; ++v)
+#pragma unroll
+      for (int w = 0; w < VW; ++w) acc[v][w] = {0.f, 0.f};
     for (int64_t kb = k0; kb < k1; kb += 32) {
-      const int64_t k = kb + lane;
+      const int64_t k = kb + t;
       int cj = 0;
       float wj = 0.f;
       if (k < k1) {
         cj = A.col[k];
-        wj = weight<WT>(A.val, k);
+        if constexpr (!UNIT) wj = weight<WT>(A.val, k);
       }
       const int cnt = (int)(k1 - kb < 32 ? k1 - kb : 32);
 #pragma unroll 4
-      for (int s = 0; s < cnt; ++s) {
-        const int j = __shfl_sync(0xffffffffu, cj, s);
-        const float w = __shfl_sync(0xffffffffu, wj, s);
-        const float* hr = Kh + int64_t(j) * ld + c0;
-        const float* lr = Kl + int64_t(j) * ld + c0;
-        if (cv0) {
-          const float4 h = __ldg(reinterpret_cast<const float4*>(hr));
-          const float4 l = __ldg(reinterpret_cast<const float4*>(lr));
-          ff_axpy(acc[0], w, h.x, l.x);
-          ff_axpy(acc[1], w, h.y, l.y);
-          ff_axpy(acc[2], w, h.z, l.z);
-          ff_axpy(acc[3], w, h.w, l.w);
-        }
-        if (cv1) {
-          const float4 h = __ldg(reinterpret_cast<const float4*>(hr + 128));
-          const float4 l = __ldg(reinterpret_cast<const float4*>(lr + 128));
-          ff_axpy(acc[4], w, h.x, l.x);
-          ff_axpy(acc[5], w, h.y, l.y);
-          ff_axpy(acc[6], w, h.z, l.z);
-          ff_axpy(acc[7], w, h.w, l.w);
+      for (int s2 = 0; s2 < cnt; ++s2) {
+        const int j = __shfl_sync(0xffffffffu, cj, s2);
+        float wv = 1.f;
+        if constexpr (!UNIT) wv = __shfl_sync(0xffffffffu, wj, s2);
+        const float* xr = X + int64_t(j) * ld + tile0 + t * VW;
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          if (cval[v]) {
+            const float4 x = __ldg(reinterpret_cast<const float4*>(xr + v * 32 * VW));
+            ff_acc<UNIT>(acc[v][0], wv, x.x);
+            ff_acc<UNIT>(acc[v][1], wv, x.y);
+            ff_acc<UNIT>(acc[v][2], wv, x.z);
+            ff_acc<UNIT>(acc[v][3], wv, x.w);
+          }
         }
       }
     }
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int c = c0 + 128 * half;
-      if (half == 0 ? !cv0 : !cv1) continue;
-      const float4 h = *reinterpret_cast<const float4*>(Kh + i * ld + c);
-      const float4 l = *reinterpret_cast<const float4*>(Kl + i * ld + c);
-      float4 r;
-      r.x = ff_residual(acc[4 * half + 0], beh, bel, h.x, l.x, 0.f, 0.f);
-      r.y = ff_residual(acc[4 * half + 1], beh, bel, h.y, l.y, 0.f, 0.f);
-      r.z = ff_residual(acc[4 * half + 2], beh, bel, h.z, l.z, 0.f, 0.f);
-      r.w = ff_residual(acc[4 * half + 3], beh, bel, h.w, l.w, 0.f, 0.f);
-      *reinterpret_cast<float4*>(R + i * ld + c) = r;
+    for (int v = 0; v < VPT; ++v) {
+      if (!cval[v]) continue;
+      const int64_t o = i * ld + tile0 + (v * 32 + t) * VW;
+      const float4 x4 = __ldg(reinterpret_cast<const float4*>(X + o));
+      const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+      float rh0[4] = {0.f, 0.f, 0.f, 0.f}, rl0[4] = {0.f, 0.f, 0.f, 0.f};
+      float kh[4], kl[4];
+      if constexpr (!INIT) {
+        const float4 a1 = *reinterpret_cast<const float4*>(Rh + o);
+        const float4 a2 = *reinterpret_cast<const float4*>(Rl + o);
+        const float4 a3 = *reinterpret_cast<const float4*>(Kh + o);
+        const float4 a4 = *reinterpret_cast<const float4*>(Kl + o);
+        rh0[0] = a1.x; rh0[1] = a1.y; rh0[2] = a1.z; rh0[3] = a1.w;
+        rl0[0] = a2.x; rl0[1] = a2.y; rl0[2] = a2.z; rl0[3] = a2.w;
+        kh[0] = a3.x; kh[1] = a3.y; kh[2] = a3.z; kh[3] = a3.w;
+        kl[0] = a4.x; kl[1] = a4.y; kl[2] = a4.z; kl[3] = a4.w;
+      }
+      float rh[4], rl[4];
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const FF r = ff_res(acc[v][w], beh, bel, xs[w], rh0[w], rl0[w]);
+        rh[w] = r.hi;
+        rl[w] = r.lo;
+        sq[v][w] = __fmaf_rn(r.hi, r.hi, sq[v][w]);
+        if constexpr (!INIT) {
+          const FF k1s = two_sum(kh[w], xs[w]);
+          const FF k2 = fast_two_sum(k1s.hi, k1s.lo + kl[w]);
+          kh[w] = k2.hi;
+          kl[w] = k2.lo;
+        }
+      }
+      *reinterpret_cast<float4*>(Rh + o) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+      *reinterpret_cast<float4*>(Rl + o) = make_float4(rl[0], rl[1], rl[2], rl[3]);
+      if constexpr (!INIT) {
+        *reinterpret_cast<float4*>(Kh + o) = make_float4(kh[0], kh[1], kh[2], kh[3]);
+        *reinterpret_cast<float4*>(Kl + o) = make_float4(kl[0], kl[1], kl[2], kl[3]);
+      }
+    }
+    if (++nsq == 64) {
+#pragma unroll
+      for (int v = 0; v < VPT; ++v)
+#pragma unroll
+        for (int w = 0; w < VW; ++w) {
+          red[wib][(v * 32 + t) * VW + w] += sq[v][w];
+          sq[v][w] = 0.f;
+        }
+      nsq = 0;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < VPT; ++v)
+#pragma unroll
+    for (int w = 0; w < VW; ++w) red[wib][(v * 32 + t) * VW + w] += sq[v][w];
+  __syncthreads();
+  if (rr) {
+    for (int c = threadIdx.x; c < TILE; c += blockDim.x) {
+      double sum = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sum += red[q][c];
+      if (tile0 + c < b && sum != 0.0) atomicAdd(rr + tile0 + c, sum);
     }
   }
 }
 
-// Entries with a nonzero RHS, b_ij = beta * w(q_j, i) for i in N(q_j):
-// recompute them exactly with b included (one warp per entry).
+// (Rh, Rl)[pos(i), j] += beta w_{q_j i}; rr[j] += new Rh^2 - old Rh^2.
 template <int WT>
-__global__ void ff_fix_rhs_kernel(Csr A, Csr W, const int32_t* q, const int32_t* pos,
-                                  const float* __restrict__ Kh, const float* __restrict__ Kl,
-                                  int64_t ld, float beh, float bel, double beta, float* R) {
+__global__ void ffr_add_rhs_kernel(Csr W, const int32_t* q, const int32_t* pos, double beta,
+                                   float* Rh, float* Rl, int64_t ld, double* rr) {
   const int j = blockIdx.y;
-  const int lane = threadIdx.x & 31;
   const int64_t qq = q[j];
-  const int64_t e = W.rowptr[qq] + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t e = W.rowptr[qq] + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= W.rowptr[qq + 1]) return;
   const int64_t node = W.col[e];
+  const int64_t i = pos ? pos[node] : node;
   const double bv = beta * double(weight<WT>(W.val, e));
   const float bh = float(bv), bl = float(bv - double(bh));
-  const int64_t i = pos ? pos[node] : node;
-  FF acc = {0.f, 0.f};
-  for (int64_t k = A.rowptr[i] + lane; k < A.rowptr[i + 1]; k += 32) {
-    const int64_t jj = A.col[k];
-    ff_axpy(acc, weight<WT>(A.val, k), Kh[jj * ld + j], Kl[jj * ld + j]);
-  }
-  // combine the lanes' float-float partials
-  for (int o = 16; o > 0; o >>= 1) {
-    const float oh = __shfl_xor_sync(0xffffffffu, acc.hi, o);
-    const float ol = __shfl_xor_sync(0xffffffffu, acc.lo, o);
-    const FF s = two_sum(acc.hi, oh);
-    acc.hi = s.hi;
-    acc.lo += s.lo + ol;
-  }
-  if (lane == 0) R[i * ld + j] = ff_residual(acc, beh, bel, Kh[i * ld + j], Kl[i * ld + j], bh, bl);
-}
-
-__global__ void ff_add_kernel(float* __restrict__ Kh, float* __restrict__ Kl,
-                              const float* __restrict__ D, int64_t total) {
-  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
-       e += int64_t(gridDim.x) * blockDim.x) {
-    const FF s = two_sum(Kh[e], D[e]);
-    const FF t = fast_two_sum(s.hi, s.lo + Kl[e]);
-    Kh[e] = t.hi;
-    Kl[e] = t.lo;
-  }
+  const int64_t o = i * ld + j;
+  const float old = Rh[o];
+  const FF t = two_sum(old, bh);
+  const FF r = fast_two_sum(t.hi, t.lo + Rl[o] + bl);
+  Rh[o] = r.hi;
+  Rl[o] = r.lo;
+  if (rr) atomicAdd(rr + j, double(r.hi) * r.hi - double(old) * old);
 }
 
 __global__ void ff_out_kernel(const float* __restrict__ Kh, const float* __restrict__ Kl,
@@ -181,59 +227,64 @@ __global__ void ff_out_kernel(const float* __restrict__ Kh, const float* __restr
   }
 }
 
-__global__ void mask_columns_kernel(float* R, int64_t ld, int64_t total, int b, const int* conv) {
-  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
-       e += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t c = e % ld;
-    if (c >= b || conv[c]) R[e] = 0.f;
-  }
-}
-
 unsigned flat(int64_t total) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), int64_t(num_sms()) * 16));
 }
 
 }  // namespace
 
-void ff_residual(const Csr& A, const Csr& W, const int32_t* q, const int32_t* pos, int b,
-                 double beta, const float* Kh, const float* Kl, int64_t ld, float* R,
-                 int64_t maxdeg, cudaStream_t s) {
-  KATZ_REQUIRE(ld % 4 == 0 && reinterpret_cast<uintptr_t>(Kh) % 16 == 0 &&
-                   reinterpret_cast<uintptr_t>(Kl) % 16 == 0 &&
-                   reinterpret_cast<uintptr_t>(R) % 16 == 0 && ld >= b,
-               KATZ_EINVAL, "ff_residual: operands must be 16-byte aligned with padded rows");
+void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl, float* Kh,
+                float* Kl, bool init, int64_t ld, int b, double* rr, const SpmmCfg* cfg,
+                cudaStream_t s) {
+  KATZ_REQUIRE(ld % 4 == 0 && ld >= b && reinterpret_cast<uintptr_t>(X) % 16 == 0 &&
+                   reinterpret_cast<uintptr_t>(Rh) % 16 == 0 &&
+                   reinterpret_cast<uintptr_t>(Rl) % 16 == 0 &&
+                   (init || (reinterpret_cast<uintptr_t>(Kh) % 16 == 0 &&
+                             reinterpret_cast<uintptr_t>(Kl) % 16 == 0)),
+               KATZ_EINVAL, "ffr_update: operands must be 16-byte aligned with padded rows");
+  if (A.nrows <= 0) return;
   const float beh = float(beta), bel = float(beta - double(beh));
-  const int tiles = (int)ceil_div(b, 256);
-  int64_t ctas = std::min<int64_t>(ceil_div(A.nrows, 8), int64_t(num_sms()) * 8 / tiles);
-  dim3 grid((unsigned)std::max<int64_t>(1, ctas), (unsigned)tiles);
+  const int vpt = ld > 128 ? 2 : 1;
+  const int64_t tiles = ceil_div(ld, 128 * vpt);
+  const int cps = cfg && cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm : 8;
+  const int64_t ctas = std::min<int64_t>(ceil_div(A.nrows, 8),
+                                         std::max<int64_t>(1, int64_t(num_sms()) * cps / tiles));
+  const dim3 grid((unsigned)std::max<int64_t>(1, ctas), (unsigned)tiles);
   prof_begin(s);
-  switch (A.vdt) {
-    case KATZ_UNIT: ff_residual_kernel<KATZ_UNIT><<<grid, 256, 0, s>>>(A, Kh, Kl, ld, beh, bel, R, b); break;
-    case KATZ_F64: ff_residual_kernel<KATZ_F64><<<grid, 256, 0, s>>>(A, Kh, Kl, ld, beh, bel, R, b); break;
-    case KATZ_F32: ff_residual_kernel<KATZ_F32><<<grid, 256, 0, s>>>(A, Kh, Kl, ld, beh, bel, R, b); break;
-    default: ff_residual_kernel<KATZ_BF16><<<grid, 256, 0, s>>>(A, Kh, Kl, ld, beh, bel, R, b); break;
+#define KATZ_FFR(WT, V, I) \
+  ffr_rows_kernel<WT, V, I><<<grid, 256, 0, s>>>(A, X, Rh, Rl, Kh, Kl, ld, beh, bel, rr, b)
+#define KATZ_FFR_W(WT)                                                     \
+  if (vpt == 2) {                                                          \
+    if (init) KATZ_FFR(WT, 2, true); else KATZ_FFR(WT, 2, false);          \
+  } else {                                                                 \
+    if (init) KATZ_FFR(WT, 1, true); else KATZ_FFR(WT, 1, false);          \
   }
+  switch (A.vdt) {
+    case KATZ_UNIT: KATZ_FFR_W(KATZ_UNIT); break;
+    case KATZ_F32: KATZ_FFR_W(KATZ_F32); break;
+    case KATZ_BF16: KATZ_FFR_W(KATZ_BF16); break;
+    default: KATZ_FFR_W(KATZ_F64); break;
+  }
+#undef KATZ_FFR_W
+#undef KATZ_FFR
   KATZ_CHECK_LAUNCH();
   if (profiling())
     prof_end("ff_residual",
              8.0 * (A.nrows + 1) + double(A.nnz) * (4 + vdt_size(A.vdt)) +
-                 4.0 * b * (2.0 * A.ncols + A.nrows),
+                 4.0 * ld * (A.ncols + A.nrows * (init ? 3.0 : 9.0)),
              s);
-  if (maxdeg > 0) {
-    dim3 g2((unsigned)ceil_div(maxdeg, 8), (unsigned)b);
-    switch (A.vdt) {
-      case KATZ_UNIT: ff_fix_rhs_kernel<KATZ_UNIT><<<g2, 256, 0, s>>>(A, W, q, pos, Kh, Kl, ld, beh, bel, beta, R); break;
-      case KATZ_F64: ff_fix_rhs_kernel<KATZ_F64><<<g2, 256, 0, s>>>(A, W, q, pos, Kh, Kl, ld, beh, bel, beta, R); break;
-      case KATZ_F32: ff_fix_rhs_kernel<KATZ_F32><<<g2, 256, 0, s>>>(A, W, q, pos, Kh, Kl, ld, beh, bel, beta, R); break;
-      default: ff_fix_rhs_kernel<KATZ_BF16><<<g2, 256, 0, s>>>(A, W, q, pos, Kh, Kl, ld, beh, bel, beta, R); break;
-    }
-    KATZ_CHECK_LAUNCH();
-  }
 }
 
-void ff_add(float* Kh, float* Kl, const float* D, int64_t total, cudaStream_t s) {
-  if (total <= 0) return;
-  ff_add_kernel<<<flat(total), 256, 0, s>>>(Kh, Kl, D, total);
+void ffr_add_rhs(const Csr& W, const int32_t* q, const int32_t* pos, int b, double beta, float* Rh,
+                 float* Rl, int64_t ld, double* rr, int64_t maxdeg, cudaStream_t s) {
+  if (maxdeg <= 0 || b <= 0) return;
+  const dim3 grid(unsigned(ceil_div(maxdeg, 256)), unsigned(b));
+  switch (W.vdt) {
+    case KATZ_UNIT: ffr_add_rhs_kernel<KATZ_UNIT><<<grid, 256, 0, s>>>(W, q, pos, beta, Rh, Rl, ld, rr); break;
+    case KATZ_F64: ffr_add_rhs_kernel<KATZ_F64><<<grid, 256, 0, s>>>(W, q, pos, beta, Rh, Rl, ld, rr); break;
+    case KATZ_F32: ffr_add_rhs_kernel<KATZ_F32><<<grid, 256, 0, s>>>(W, q, pos, beta, Rh, Rl, ld, rr); break;
+    default: ffr_add_rhs_kernel<KATZ_BF16><<<grid, 256, 0, s>>>(W, q, pos, beta, Rh, Rl, ld, rr); break;
+  }
   KATZ_CHECK_LAUNCH();
 }
 
@@ -241,12 +292,6 @@ void ff_out(const float* Kh, const float* Kl, int64_t ld, const int32_t* map, in
             void* out, int out_dt, int64_t ldk, cudaStream_t s) {
   if (n * b <= 0) return;
   ff_out_kernel<<<flat(n * b), 256, 0, s>>>(Kh, Kl, ld, map, n, b, out, out_dt, ldk);
-  KATZ_CHECK_LAUNCH();
-}
-
-void mask_columns(float* R, int64_t ld, int64_t len, int b, const int* conv, cudaStream_t s) {
-  if (len * ld <= 0) return;
-  mask_columns_kernel<<<flat(len * ld), 256, 0, s>>>(R, ld, len * ld, b, conv);
   KATZ_CHECK_LAUNCH();
 }
 

@@ -5,6 +5,7 @@
 #include <memory>
 #include <string>
 
+#include "gather_pipe.h"
 #include "kernels.h"
 #include "mlp.h"
 
@@ -20,12 +21,14 @@ struct BlockClass {
   DBuf<double> inv64;
 };
 
-// A CSR with the list of its heavy rows and the SpMM launch shapes the
-// autotuner picked for it (per right-hand-side width b).
+// A CSR with the list of its heavy rows, its per-CTA row split for the
+// pipelined gather kernels, and the SpMM launch shapes the autotuner picked
+// for it (per right-hand-side width b).
 struct GraphPart {
   DevCsr csr;
   DBuf<int32_t> heavy;
   int64_t n_heavy = 0;
+  PipeSplit ps;
   std::map<int, SpmmCfg> tuned;
   Csr view() const { return csr.view(); }
   const SpmmCfg* cfg(int b) const {
@@ -59,6 +62,8 @@ struct katz_index {
   // spectral bound of the large-block W11 for the Chebyshev solve:
   // spectrum(M11_large) in [1 - beta*lam11, 1 + beta*lam11] (0 = use CG)
   double lam11 = 0;
+  // kernel preference of the query being run (KATZ_GATHER_*), set per query
+  int gather_pref = KATZ_GATHER_AUTO;
   katz::Partition part;
   katz::DBuf<int32_t> perm, iperm;
   katz::GraphPart Wp;    // W in index order (full), for FP64 residuals
@@ -146,6 +151,7 @@ void warm_start_guess(katz_index& idx, const int32_t* q, int b, float* K20, int6
 
 struct TuneResult {
   int col_tile = 0, ctas_per_sm = 0, rhs_width = 0;
+  bool cheb_pipe = false;  // the pipelined Chebyshev step was faster on the large block
   double ms_best = 0, ms_default = 0;
 };
 // Times candidate SpMM launch shapes on every operator of the index for

@@ -55,6 +55,7 @@ void upload_csr(const HostCsr& h, int vdt, DevCsr& d, cudaStream_t s) {
 
 static void upload_part(const HostCsr& h, int vdt, GraphPart& g, cudaStream_t s) {
   upload_csr(h, vdt, g.csr, s);
+  if (h.nrows > 0) pipe_split_build(h.rowptr, h.nrows, g.ps, s);
   std::vector<int32_t> heavy;
   for (int64_t i = 0; i < h.nrows; ++i)
     if (h.rowptr[i + 1] - h.rowptr[i] > kHeavyRowNnz) heavy.push_back((int32_t)i);

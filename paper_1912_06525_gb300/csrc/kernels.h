@@ -17,6 +17,7 @@ struct SpmmCfg {
   int warps_per_cta = 8;   // row groups of 32 threads per CTA
   int col_tile = 0;        // columns per CTA tile (0 = whole row up to 1024 floats / 512 doubles)
   int ctas_per_sm = 8;     // grid = SMs * ctas_per_sm (grid-stride over rows)
+  bool pipe = false;       // the pipelined (TMA bulk-copy) kernel measured faster here
 };
 
 // Y[i,:] = gamma * Z[i,:] + alpha * sum_k A[i,k] X[k,:]   for i < A.nrows.

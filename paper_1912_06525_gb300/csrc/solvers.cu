@@ -2,6 +2,7 @@
 // LRC-Katz solve (Lemma 1 with PCG on the Schur complement, Algorithm 2),
 // and the mixed-precision driver that wraps either one in FP64 iterative
 // refinement.
+#include <cfloat>
 #include <chrono>
 #include <cmath>
 
@@ -76,7 +77,9 @@ __global__ void rhs_add_kernel(Csr W, const int32_t* q, double beta, const int32
 }
 
 // Per column: converged = rr <= thr2; inner threshold
-//   thr2_in = max(tau^2 rr, (0.3)^2 thr2)   (0 for converged columns).
+//   thr2_in = max(tau^2 rr, (0.3)^2 thr2)
+// and, for converged columns, a threshold every residual meets (their
+// inner CG does no iteration and returns a zero correction).
 __global__ void inner_thresholds_kernel(const double* rr, const double* thr2, double tau, int b,
                                         int* conv, double* thr2_in, int* n_open) {
   __shared__ int cnt;
@@ -86,7 +89,7 @@ __global__ void inner_thresholds_kernel(const double* rr, const double* thr2, do
   for (int c = threadIdx.x; c < b; c += blockDim.x) {
     const int cv = rr[c] <= thr2[c];
     conv[c] = cv;
-    thr2_in[c] = cv ? 0.0 : fmax(tau * tau * rr[c], 0.09 * thr2[c]);
+    thr2_in[c] = cv ? DBL_MAX : fmax(tau * tau * rr[c], 0.09 * thr2[c]);
     local += !cv;
   }
   atomicAdd(&cnt, local);
@@ -215,6 +218,14 @@ const float* inv_of<float>(const BlockClass& c) { return c.inv32.p; }
 template <>
 const double* inv_of<double>(const BlockClass& c) { return c.inv64.p; }
 
+// Pipelined or register kernel for a fused product, by the query's choice
+// (AUTO: what the autotuner measured faster, register if untuned).
+static bool use_pipe(const katz_index& idx, const SpmmCfg* cfg) {
+  if (idx.gather_pref == KATZ_GATHER_PIPELINED) return true;
+  if (idx.gather_pref == KATZ_GATHER_REGISTER) return false;
+  return cfg && cfg->pipe;
+}
+
 // Y1 = M11^{-1} X1: dense block inverses for the small blocks (Step 4) and,
 // for blocks kept whole, CG on that diagonal block to relative tolerance tolL.
 // Chebyshev iteration (Saad, Iterative Methods, Alg. 12.1) on the large
@@ -243,12 +254,19 @@ static void m11_chebyshev(katz_index& idx, const float* X, float* Y, int b, int6
   const double sigma = 1.0 / delta;
   double rho_prev = delta;  // rho_0 = 1/sigma
   const SpmmCfg* cfg = idx.W11L.cfg(b);
+  const bool pipe = use_pipe(idx, cfg) && pipe_eligible(idx.W11L.ps, ld) &&
+                    (idx.unit_weights || idx.W11L.csr.vdt != KATZ_F64);
+  int* perr = idx.ws.get<int>("pipe.err", 1);
   for (int k = 1; k < K; ++k) {
     const double rho = 1.0 / (2.0 * sigma - rho_prev);
     const double ak = rho * rho_prev, ck = 2.0 * rho / delta;
     const float* xk = k == 1 ? X : slot(k);
     const float* xprev = k == 1 ? nullptr : (k == 2 ? X : slot(k - 1));
-    cheb_step(idx.W11L.view(), idx.beta, ak, ck, xk, xprev, X, slot(k + 1), ld, b, s, cfg);
+    if (pipe)
+      pipe_cheb_step(idx.W11L.view(), idx.W11L.ps, idx.unit_weights, idx.beta, ak, ck, xk, xprev,
+                     X, slot(k + 1), ld, perr, s);
+    else
+      cheb_step(idx.W11L.view(), idx.beta, ak, ck, xk, xprev, X, slot(k + 1), ld, b, s, cfg);
     rho_prev = rho;
   }
 }
@@ -506,9 +524,12 @@ static void residual64(katz_index& idx, bool use_lrc, const int32_t* q, int b, i
   coldot<double>(R64, ld, R64, ld, idx.n, b, rr, s);
 }
 
-// Mixed precision with a float-float residual (weights exact in FP32):
-// FP32 inner solves, K kept as an FP32 (hi, lo) pair, R = B - M K evaluated
-// in float-float and rounded to FP32 only after the cancellation.
+// Mixed-precision query for graphs whose weights are exact in FP32: FP32
+// solves, the solution kept as a float-float pair (Kh, Kl) and the residual
+// as (Rh, Rl), both updated by one pass per refinement step that gathers the
+// step's FP32 correction (R <- R - M D, K <- K + D), accurate to ~2^-48
+// relative to the terms.  Every column stops when its residual meets the
+// error-bound threshold.
 static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const int32_t* q_host,
                           int b, const katz_query_opts& o, const QueryOut& out, katz_stats* stats,
                           std::vector<int32_t>& iters, std::vector<double>& relres,
@@ -521,6 +542,9 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   const int max_refine = o.max_refine > 0 ? o.max_refine : 12;
   const int32_t* pos = use_lrc ? idx.iperm.p : nullptr;
   const GraphPart& G = use_lrc ? idx.Wp : idx.W;
+  const SpmmCfg* gcfg = G.cfg(b);
+  const bool pipe = use_pipe(idx, gcfg) && pipe_eligible(G.ps, ld) &&
+                    (idx.unit_weights || G.csr.vdt != KATZ_F64);
   Workspace& ws = idx.ws;
   iters.assign(b, 0);
   relres.assign(b, 0.0);
@@ -534,6 +558,7 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   double* rr = ws.get<double>("q.rr", bpad(b));
   int* conv = ws.get<int>("q.conv", b);
   int* nopen = ws.get<int>("q.nopen", 1);
+  int* perr = ws.get<int>("pipe.err", 1);
   rhs_norms(idx.W.view(), q, b, idx.beta, bn2, bmx, s);
   const double omc = std::max(1e-300, 1.0 - idx.beta * idx.lambda);
   make_thresholds(bn2, bmx, b, o.tol, o.tol_kind, omc, thr2, s);
@@ -541,32 +566,13 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   double tol_rel = (o.tol_kind == KATZ_TOL_RESIDUAL) ? o.tol : o.tol * omc;
   tol_rel = std::max(tol_rel * 0.3, tau);
 
-  float* R = ws.get<float>("q.Rin", size_t(n) * ld);
+  float* Rh = ws.get<float>("q.Rin", size_t(n) * ld);  // FP32 residual = RHS of the solves
+  float* Rl = ws.get<float>("q.Rl", size_t(n) * ld);
   float* D = ws.get<float>("q.D", size_t(n) * ld);
-  // K: 64-bit fixed point for unit-weight graphs, else a float-float pair
-  const bool fixed = idx.unit_weights && idx.vdt != KATZ_F64;
-  float* Kh = nullptr;
-  float* Kl = nullptr;
-  long long* Kfx = nullptr;
-  int* sh = ws.get<int>("q.sh", b);
-  if (fixed) {
-    Kfx = ws.get<long long>("q.Kfx", size_t(n) * ld);
-    std::vector<double> hb(b);
-    KATZ_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
-    KATZ_CUDA(cudaStreamSynchronize(s));
-    std::vector<int> hs(b);
-    for (int c = 0; c < b; ++c) {
-      const double B = std::sqrt(hb[c]) / omc;  // >= ||k_c||_inf
-      const double top = 16.0 * double(idx.maxdeg + 1) * B;
-      hs[c] = top > 0 ? std::min(100, std::max(0, int(std::floor(62.0 - std::log2(top))))) : 0;
-    }
-    KATZ_CUDA(cudaMemcpyAsync(sh, hs.data(), sizeof(int) * b, cudaMemcpyHostToDevice, s));
-  } else {
-    Kh = ws.get<float>("q.Kh", size_t(n) * ld);
-    Kl = ws.get<float>("q.Kl", size_t(n) * ld);
-  }
-  KATZ_CUDA(cudaMemsetAsync(R, 0, sizeof(float) * n * ld, s));
-  build_rhs<float>(idx.W.view(), q, b, idx.beta, pos, R, ld, s);
+  float* Kh = ws.get<float>("q.Kh", size_t(n) * ld);
+  float* Kl = ws.get<float>("q.Kl", size_t(n) * ld);
+  KATZ_CUDA(cudaMemsetAsync(Rh, 0, sizeof(float) * n * ld, s));
+  build_rhs<float>(idx.W.view(), q, b, idx.beta, pos, Rh, ld, s);
   inner_thresholds_kernel<<<1, 1024, 0, s>>>(bn2, thr2, tau, b, conv, thr2_in, nopen);
   KATZ_CHECK_LAUNCH();
   const float* K20 = nullptr;
@@ -578,12 +584,9 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
     K20 = g;
   }
   const auto t1 = clk::now();
-  int status = inner_solve<float>(idx, use_lrc, R, fixed ? D : Kh, b, ld, thr2_in, tol_rel,
-                                  max_iter, &iters, s, K20);
-  if (fixed)
-    fx_add(Kfx, D, n, ld, sh, b, true, s);
-  else
-    KATZ_CUDA(cudaMemsetAsync(Kl, 0, sizeof(float) * n * ld, s));
+  int status = inner_solve<float>(idx, use_lrc, Rh, Kh, b, ld, thr2_in, tol_rel, max_iter, &iters,
+                                  s, K20);
+  KATZ_CUDA(cudaMemsetAsync(Kl, 0, sizeof(float) * n * ld, s));
   KATZ_CUDA(cudaStreamSynchronize(s));
   const auto t2 = clk::now();
   double ms_res = 0;
@@ -591,20 +594,25 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   if (status == KATZ_OK || status == KATZ_ENOCONV) {
     for (;;) {
       const auto r0 = clk::now();
-      if (fixed)
-        fx_residual(G.view(), idx.W.view(), q, pos, b, idx.beta, Kfx, sh, ld, R, maxdeg, s);
-      else
-        ff_residual(G.view(), idx.W.view(), q, pos, b, idx.beta, Kh, Kl, ld, R, maxdeg, s);
       KATZ_CUDA(cudaMemsetAsync(rr, 0, sizeof(double) * bpad(b), s));
-      coldot<float>(R, ld, R, ld, n, b, rr, s);
+      // R = b - M K0 (K0 = Kh, Kl = 0) on the first pass, then R -= M D, K += D
+      const bool first = refine == 0;
+      const float* Xg = first ? Kh : D;
+      if (pipe)
+        pipe_residual(G.view(), G.ps, idx.unit_weights, idx.beta, Xg, Rh, Rl, Kh, Kl, first, ld,
+                      b, rr, perr, s);
+      else
+        ffr_update(G.view(), idx.beta, Xg, Rh, Rl, Kh, Kl, first, ld, b, rr, gcfg, s);
+      if (first) ffr_add_rhs(idx.W.view(), q, pos, b, idx.beta, Rh, Rl, ld, rr, maxdeg, s);
       inner_thresholds_kernel<<<1, 1024, 0, s>>>(rr, thr2, tau, b, conv, thr2_in, nopen);
       KATZ_CHECK_LAUNCH();
       ++refine;
       const int open = read_int(nopen, s);
+      KATZ_REQUIRE(read_int(perr, s) == 0, KATZ_ECUDA,
+                   "pipelined gather kernel: a wait on its shared-memory ring timed out");
       ms_res += std::chrono::duration<double, std::milli>(clk::now() - r0).count();
       if (open == 0) { status = KATZ_OK; break; }
       if (refine > max_refine) { status = KATZ_ENOCONV; break; }
-      mask_columns(R, ld, n, b, conv, s);
       // the correction solve only has to bring every open column below its
       // threshold: relative tolerance = tightest 0.3 * thr_c / ||r_c||
       double tol_step = 1.0;
@@ -617,23 +625,16 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
           if (hr[c] > ht[c] && hr[c] > 0) tol_step = std::min(tol_step, 0.3 * std::sqrt(ht[c] / hr[c]));
         tol_step = std::max(tol_step, tau);
       }
-      const int st = inner_solve<float>(idx, use_lrc, R, D, b, ld, thr2_in, tol_step, max_iter,
+      const int st = inner_solve<float>(idx, use_lrc, Rh, D, b, ld, thr2_in, tol_step, max_iter,
                                         &iters, s);
       if (st == KATZ_ENOTSPD) { status = st; break; }
-      if (fixed)
-        fx_add(Kfx, D, n, ld, sh, b, false, s);
-      else
-        ff_add(Kh, Kl, D, n * ld, s);
     }
     std::vector<double> hr(b), hb(b);
     KATZ_CUDA(cudaMemcpyAsync(hr.data(), rr, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
     KATZ_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
     KATZ_CUDA(cudaStreamSynchronize(s));
     for (int c = 0; c < b; ++c) relres[c] = hb[c] > 0 ? std::sqrt(hr[c] / hb[c]) : std::sqrt(hr[c]);
-    if (fixed)
-      fx_out(Kfx, ld, sh, pos, n, b, out.K, out.dtype, out.ldk, s);
-    else
-      ff_out(Kh, Kl, ld, pos, n, b, out.K, out.dtype, out.ldk, s);
+    ff_out(Kh, Kl, ld, pos, n, b, out.K, out.dtype, out.ldk, s);
     KATZ_CUDA(cudaStreamSynchronize(s));
   }
   const auto t3 = clk::now();
@@ -779,11 +780,21 @@ int run_queries(katz_index& idx, bool use_lrc, const int32_t* q_dev, const int32
   KATZ_REQUIRE(b > 0 && b <= 1024, KATZ_EINVAL, "b must be in [1, 1024]");
   // FP64-valued graphs keep the FP64 residual (their weights need not be
   // exact in FP32); the others use the float-float residual
+  KATZ_REQUIRE(o.gather_kernel >= KATZ_GATHER_AUTO && o.gather_kernel <= KATZ_GATHER_PIPELINED,
+               KATZ_EINVAL, "gather_kernel must be a KATZ_GATHER_* value");
+  idx.gather_pref = o.gather_kernel;
+  int* perr = idx.ws.get<int>("pipe.err", 1);
+  KATZ_CUDA(cudaMemsetAsync(perr, 0, sizeof(int), s));
+  int status;
   if (o.precision == KATZ_PREC_MIXED && idx.vdt != KATZ_F64)
-    return query_mixed_ff(idx, use_lrc, q_dev, q_host, b, o, out, st, iters, relres, s);
-  if (o.precision == KATZ_PREC_F64)
-    return query_impl<double>(idx, use_lrc, q_dev, b, o, out, st, iters, relres, s);
-  return query_impl<float>(idx, use_lrc, q_dev, b, o, out, st, iters, relres, s);
+    status = query_mixed_ff(idx, use_lrc, q_dev, q_host, b, o, out, st, iters, relres, s);
+  else if (o.precision == KATZ_PREC_F64)
+    status = query_impl<double>(idx, use_lrc, q_dev, b, o, out, st, iters, relres, s);
+  else
+    status = query_impl<float>(idx, use_lrc, q_dev, b, o, out, st, iters, relres, s);
+  KATZ_REQUIRE(read_int(perr, s) == 0, KATZ_ECUDA,
+               "pipelined gather kernel: a wait on its shared-memory ring timed out");
+  return status;
 }
 
 int run_queries_internal(katz_index& idx, const int32_t* q_dev, const int32_t* q_host, int b,

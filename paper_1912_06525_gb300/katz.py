@@ -21,6 +21,7 @@ KATZ_OK, KATZ_EINVAL, KATZ_ENOTSPD, KATZ_ENOCONV, KATZ_ENOMEM, KATZ_ECUDA = rang
 KATZ_UNIT, KATZ_F64, KATZ_F32, KATZ_BF16 = range(4)
 KATZ_PREC_F32, KATZ_PREC_MIXED, KATZ_PREC_F64 = range(3)
 KATZ_TOL_RESIDUAL, KATZ_TOL_ERROR_INF = range(2)
+KATZ_GATHER_AUTO, KATZ_GATHER_REGISTER, KATZ_GATHER_PIPELINED = range(3)
 
 STATUS_NAMES = {0: "KATZ_OK", 1: "KATZ_EINVAL", 2: "KATZ_ENOTSPD", 3: "KATZ_ENOCONV",
                 4: "KATZ_ENOMEM", 5: "KATZ_ECUDA"}
@@ -53,7 +54,7 @@ class katz_build_opts(C.Structure):
 class katz_query_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("tol_kind", C.c_int32), ("precision", C.c_int32),
                 ("max_iter", C.c_int32), ("max_refine", C.c_int32), ("rhs_width", C.c_int32),
-                ("warm_start", C.c_int32)]
+                ("warm_start", C.c_int32), ("gather_kernel", C.c_int32)]
 
 
 class katz_stats(C.Structure):
@@ -252,10 +253,10 @@ def katz_index_get_sigma(index: KatzIndex) -> np.ndarray:
 
 
 def _query(fn, index, q, K_out, out_dtype, tol, tol_kind, precision, max_iter, max_refine,
-           rhs_width, warm_start, stream):
+           rhs_width, warm_start, gather_kernel, stream):
     b = int(q.shape[0])
     o = katz_query_opts(float(tol), tol_kind, precision, max_iter, max_refine, rhs_width,
-                        warm_start)
+                        warm_start, gather_kernel)
     st = katz_stats()
     iters = np.zeros(b, dtype=np.int32)
     rel = np.zeros(b, dtype=np.float64)
@@ -270,19 +271,20 @@ def _query(fn, index, q, K_out, out_dtype, tol, tol_kind, precision, max_iter, m
 
 def katz_query_batch(index, q, K_out, out_dtype=KATZ_F32, tol=1e-6,
                      tol_kind=KATZ_TOL_ERROR_INF, precision=KATZ_PREC_MIXED, max_iter=0,
-                     max_refine=0, rhs_width=0, warm_start=0, stream=None):
+                     max_refine=0, rhs_width=0, warm_start=0, gather_kernel=KATZ_GATHER_AUTO,
+                     stream=None):
     """LRC-Katz (Algorithm 2).  q: int32 (b,) host or device; K_out: (n, b)
     node-major float32/float64, host or device.  Returns (stats, iters, rel_res)."""
     return _query(lib().katz_query_batch, index, q, K_out, out_dtype, tol, tol_kind, precision,
-                  max_iter, max_refine, rhs_width, warm_start, stream)
+                  max_iter, max_refine, rhs_width, warm_start, gather_kernel, stream)
 
 
 def cg_query_batch(index, q, K_out, out_dtype=KATZ_F32, tol=1e-6, tol_kind=KATZ_TOL_ERROR_INF,
                    precision=KATZ_PREC_MIXED, max_iter=0, max_refine=0, rhs_width=0,
-                   warm_start=0, stream=None):
+                   warm_start=0, gather_kernel=KATZ_GATHER_AUTO, stream=None):
     """Plain CG on M (the comparison method); same contract as katz_query_batch."""
     return _query(lib().cg_query_batch, index, q, K_out, out_dtype, tol, tol_kind, precision,
-                  max_iter, max_refine, rhs_width, warm_start, stream)
+                  max_iter, max_refine, rhs_width, warm_start, gather_kernel, stream)
 
 
 def linkpred_topk(index, q, K, k_dtype, k, ids_out, scores_out, stream=None):
@@ -334,11 +336,11 @@ def katz_gemm_bf16(A, B, C_out, K=None, alpha=1.0, beta=0.0, stream=None):
 
 def katz_autotune(index, b: int, stream=None) -> dict:
     """Tune the SpMM launch shape for width b; returns the choice and times."""
-    out = np.zeros(2, dtype=np.int32)
+    out = np.zeros(3, dtype=np.int32)
     ms = np.zeros(2, dtype=np.float64)
     _check(lib().katz_autotune(index.handle, b, out.ctypes.data, ms.ctypes.data, _stream(stream)))
-    return {"col_tile": int(out[0]), "ctas_per_sm": int(out[1]), "ms_best": float(ms[0]),
-            "ms_default": float(ms[1])}
+    return {"col_tile": int(out[0]), "ctas_per_sm": int(out[1]), "cheb_pipe": bool(out[2]),
+            "ms_best": float(ms[0]), "ms_default": float(ms[1])}
 
 
 class KatzMulti:
@@ -372,7 +374,7 @@ def katz_multi_query(multi, q, qpg, K_out, out_dtype=KATZ_F32, tol=1e-6,
                      tol_kind=KATZ_TOL_ERROR_INF, max_iter=0, max_refine=0, stream=None):
     """q: (g*qpg,) graph-local ids; K_out: (sum n_g, qpg).  Returns
     (stats, iters (g*qpg,), rel_res (g*qpg,))."""
-    o = katz_query_opts(float(tol), tol_kind, KATZ_PREC_MIXED, max_iter, max_refine, 0, 0)
+    o = katz_query_opts(float(tol), tol_kind, KATZ_PREC_MIXED, max_iter, max_refine, 0, 0, 0)
     st = katz_stats()
     total = len(multi.sizes) * qpg
     iters = np.zeros(total, dtype=np.int32)

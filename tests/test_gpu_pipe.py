@@ -1,0 +1,74 @@
+"""Parity of both kernels of the wide fused products -- the register kernels
+and the pipelined (TMA bulk-copy) ones, forced through the query option --
+against the FP64 oracle.  Widths b >= 61 (padded width >= 64) let the
+pipelined kernels take the large-block Chebyshev steps and the refinement
+residual; the graphs have a large component kept whole (split=False), a
+900-entry hub row that wraps the shared-memory ring many times, isolated
+nodes (rows without entries), and unit, FP32 and BF16 (dyadic, exact)
+weights."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1912_06525_gb300 import katz, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def graph(weighted, seed=11):
+    a = synth.chung_lu(3000, 2.2, 8.0, 300.0, seed=seed)
+    s = synth.star(900)
+    iso = synth.path(1)
+    g = synth.disjoint_union([a, s, iso, iso, iso])
+    r = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    m = r < g.col
+    u = np.concatenate([r[m], [0, 3000]])
+    v = np.concatenate([g.col[m], [3000, 7]])  # connect the star to the rest
+    wf = synth.dyadic_weights(seed + 3) if weighted else None
+    return synth.edges_to_graph(g.n, u, v, {"kind": "pipe"}, wf)
+
+
+@pytest.mark.parametrize("vdt", [katz.KATZ_UNIT, katz.KATZ_F32, katz.KATZ_BF16])
+@pytest.mark.parametrize("b", [61, 333, 1024])
+def test_pipelined_paths_match_oracle(vdt, b):
+    g = graph(weighted=vdt != katz.KATZ_UNIT)
+    W = O.adjacency(g.n, g.rowptr, g.col, g.val)
+    beta = 0.85 / O.lambda_max(W)
+    idx = katz.katz_index_build(g, beta, value_dtype=vdt, rank=16, n_hubs=30, block_max=32,
+                                split=False)
+    q = synth.queries(g.n, b, seed=b)
+    q[0] = 3000           # the star's hub (900 entries)
+    q[1] = g.n - 1        # an isolated node: its column is zero
+    ref = O.katz_direct(W, beta, q)
+    for kern in (katz.KATZ_GATHER_REGISTER, katz.KATZ_GATHER_PIPELINED):
+        for fn in (katz.katz_query_batch, katz.cg_query_batch):
+            K = torch.zeros((g.n, b), dtype=torch.float64, device="cuda")
+            st, it, rel = fn(idx, torch.from_numpy(q).cuda(), K, out_dtype=katz.KATZ_F64, tol=1e-6,
+                             gather_kernel=kern)
+            assert st["status"] == "KATZ_OK", (fn.__name__, kern, st)
+            Kh = K.cpu().numpy()
+            assert np.all(Kh[:, 1] == 0)
+            err = O.error_inf_rel(Kh, ref)
+            assert err.max() <= 1e-6, (fn.__name__, kern, err.max())
+
+
+def test_autotune_reports_kernel_choice():
+    g = graph(weighted=False)
+    beta = 0.85 / katz.katz_lambda_max(g, steps=96)
+    idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_UNIT, rank=16, n_hubs=30,
+                                block_max=32, split=False)
+    res = katz.katz_autotune(idx, 256)
+    assert isinstance(res["cheb_pipe"], bool)
+    q = synth.queries(g.n, 256, seed=5)
+    K = torch.zeros((g.n, 256), dtype=torch.float32, device="cuda")
+    st, _, _ = katz.katz_query_batch(idx, torch.from_numpy(q).cuda(), K, tol=1e-6)
+    assert st["status"] == "KATZ_OK"
