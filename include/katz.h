@@ -240,9 +240,12 @@ int katz_apply_M(const katz_index* idx, const void* X, void* Y, int32_t b,
  * fastest per operator for later queries with that b, and caches the
  * choice per (rows, nnz, b, value type) in the process; on the large-block
  * operator it also chooses between the register and the pipelined (TMA
- * bulk-copy) Chebyshev step.  out (3 ints): out[0] = chosen column tile
- * (0 = default), out[1] = CTAs per SM, out[2] = 1 if the pipelined
- * Chebyshev step was chosen; ms[0] = best time, ms[1] = time of the
+ * bulk-copy) Chebyshev step, and on the full operators between the two
+ * kernels of the first and of the later refinement-residual passes.
+ * out (5 ints): out[0] = chosen column tile (0 = default), out[1] = CTAs
+ * per SM, out[2] = 1 if the pipelined Chebyshev step was chosen, out[3] /
+ * out[4] = 1 if the pipelined kernel was chosen for the first / later
+ * residual passes of LRC queries; ms[0] = best time, ms[1] = time of the
  * default shape (per product, FP32 vectors). */
 int katz_autotune(katz_index* idx, int32_t b, int32_t* out, double* ms, void* stream);
 

@@ -451,6 +451,8 @@ int katz_autotune(katz_index* idx, int32_t b, int32_t* out, double* ms, void* st
     out[0] = r.col_tile;
     out[1] = r.ctas_per_sm;
     out[2] = r.cheb_pipe ? 1 : 0;
+    out[3] = r.res_first_pipe ? 1 : 0;
+    out[4] = r.res_pipe ? 1 : 0;
     ms[0] = r.ms_best;
     ms[1] = r.ms_default;
     return KATZ_OK;

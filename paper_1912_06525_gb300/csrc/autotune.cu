@@ -58,31 +58,40 @@ double time_launches(F&& launch, cudaStream_t s, int reps) {
   return ms / reps;
 }
 
-// Register (false) or pipelined (true) kernel faster for the fused product?
+// Is the pipelined kernel faster than the register one for the fused
+// product?  Residual: first[0] for the first pass, the return value for
+// the later passes.
 bool pipe_faster(const GraphPart& g, Fused kind, bool unit, const SpmmCfg& c, float* X, float* Y,
-                 float* Z, int b, int64_t ld, Workspace& ws, cudaStream_t s, int reps) {
+                 float* Z, float* K1, float* K2, int b, int64_t ld, Workspace& ws, cudaStream_t s,
+                 int reps, bool* first) {
   int* err = ws.get<int>("pipe.err", 1);
   KATZ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-  double t_reg, t_pipe;
+  bool faster;
   if (kind == Fused::cheb) {
-    t_reg = time_launches([&] { cheb_step(g.view(), 0.01, 0.1, 1.0, X, X, X, Y, ld, b, s, &c); }, s, reps);
-    t_pipe = time_launches(
+    const double t_reg =
+        time_launches([&] { cheb_step(g.view(), 0.01, 0.1, 1.0, X, X, X, Y, ld, b, s, &c); }, s, reps);
+    const double t_pipe = time_launches(
         [&] { pipe_cheb_step(g.view(), g.ps, unit, 0.01, 0.1, 1.0, X, X, X, Y, ld, err, s); }, s, reps);
+    faster = t_pipe < t_reg;
   } else {
-    t_reg = time_launches(
-        [&] { ffr_update(g.view(), 0.01, X, Y, Z, nullptr, nullptr, true, ld, b, nullptr, &c, s); },
-        s, reps);
-    t_pipe = time_launches(
-        [&] {
-          pipe_residual(g.view(), g.ps, unit, 0.01, X, Y, Z, nullptr, nullptr, true, ld, b, nullptr,
-                        err, s);
-        },
-        s, reps);
+    double t[2][2];  // [first/later][register/pipelined]
+    for (int f = 0; f < 2; ++f) {
+      const bool init = f == 0;
+      t[f][0] = time_launches(
+          [&] { ffr_update(g.view(), 0.01, X, Y, Z, K1, K2, init, ld, b, nullptr, &c, s); }, s, reps);
+      t[f][1] = time_launches(
+          [&] {
+            pipe_residual(g.view(), g.ps, unit, 0.01, X, Y, Z, K1, K2, init, ld, b, nullptr, err, s);
+          },
+          s, reps);
+    }
+    *first = t[0][1] < t[0][0];
+    faster = t[1][1] < t[1][0];
   }
   int herr = 0;
   KATZ_CUDA(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
   KATZ_REQUIRE(herr == 0, KATZ_ECUDA, "pipelined gather kernel: a wait timed out");
-  return t_pipe < t_reg;
+  return faster;
 }
 
 // Best shape for one operator (square operators only: X and Y share rows);
@@ -121,9 +130,21 @@ SpmmCfg tune_part(GraphPart& g, int b, Workspace& ws, cudaStream_t s, double* be
     }
   }
   if (kind != Fused::none && pipe_eligible(g.ps, ld) && (unit || g.csr.vdt != KATZ_F64)) {
+    const bool res = kind == Fused::residual;
     float* Z = ws.get<float>("tune.Z", size_t(rows) * ld);
-    best.pipe = pipe_faster(g, kind, unit, best, X, Y, Z, b, ld, ws, s, reps);
+    float* K1 = res ? ws.get<float>("tune.K1", size_t(rows) * ld) : nullptr;
+    float* K2 = res ? ws.get<float>("tune.K2", size_t(rows) * ld) : nullptr;
+    if (res) {
+      KATZ_CUDA(cudaMemsetAsync(K1, 0, sizeof(float) * rows * ld, s));
+      KATZ_CUDA(cudaMemsetAsync(K2, 0, sizeof(float) * rows * ld, s));
+    }
+    KATZ_CUDA(cudaMemsetAsync(Z, 0, sizeof(float) * rows * ld, s));
+    bool first = false;
+    best.pipe = pipe_faster(g, kind, unit, best, X, Y, Z, K1, K2, b, ld, ws, s, reps, &first);
+    best.pipe_first = first;
     ws.release("tune.Z");
+    ws.release("tune.K1");
+    ws.release("tune.K2");
   }
   g.tuned[b] = best;
   std::lock_guard<std::mutex> l(g_mu);
@@ -142,7 +163,9 @@ TuneResult autotune(katz_index& idx, int b, cudaStream_t s) {
   r.ms_default = def;
   if (idx.lrc) {
     double b2, d2;
-    tune_part(idx.Wp, b, idx.ws, s, &b2, &d2, Fused::residual, idx.unit_weights);
+    const SpmmCfg cp = tune_part(idx.Wp, b, idx.ws, s, &b2, &d2, Fused::residual, idx.unit_weights);
+    r.res_first_pipe = cp.pipe_first;
+    r.res_pipe = cp.pipe;
     if (idx.W11L.csr.nrows > 0)
       r.cheb_pipe =
           tune_part(idx.W11L, b, idx.ws, s, &b2, &d2, Fused::cheb, idx.unit_weights).pipe;

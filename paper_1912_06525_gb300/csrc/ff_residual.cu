@@ -64,6 +64,65 @@ __device__ __forceinline__ FF ff_res(FF acc, float beh, float bel, float x, floa
   return fast_two_sum(t2.hi, t1.lo + t2.lo + pe + rl);
 }
 
+constexpr int64_t kFp32Row = 64;  // longest row summed in FP32 by the update passes
+
+// acc[v][w] = sum_k w_ik X[col k][tile + (v * 32 + t) * 4 + w] over the stored
+// entries [k0, k1) of a row, float-float (FFACC) or FP32 (returned as hi).
+template <int WT, int VPT, bool FFACC>
+__device__ __forceinline__ void row_sum(const Csr& A, const float* __restrict__ X, int64_t ld,
+                                        int64_t tile0, int t, const bool (&cval)[VPT], int64_t k0,
+                                        int64_t k1, FF (&acc)[VPT][4]) {
+  constexpr bool UNIT = WT == KATZ_UNIT;
+  float sacc[VPT][4];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      acc[v][w] = {0.f, 0.f};
+      sacc[v][w] = 0.f;
+    }
+  for (int64_t kb = k0; kb < k1; kb += 32) {
+    const int64_t k = kb + t;
+    int cj = 0;
+    float wj = 0.f;
+    if (k < k1) {
+      cj = A.col[k];
+      if constexpr (!UNIT) wj = weight<WT>(A.val, k);
+    }
+    const int cnt = (int)(k1 - kb < 32 ? k1 - kb : 32);
+#pragma unroll 4
+    for (int s2 = 0; s2 < cnt; ++s2) {
+      const int j = __shfl_sync(0xffffffffu, cj, s2);
+      float wv = 1.f;
+      if constexpr (!UNIT) wv = __shfl_sync(0xffffffffu, wj, s2);
+      const float* xr = X + int64_t(j) * ld + tile0 + t * 4;
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        if (cval[v]) {
+          const float4 x = __ldg(reinterpret_cast<const float4*>(xr + v * 128));
+          if constexpr (FFACC) {
+            ff_acc<UNIT>(acc[v][0], wv, x.x);
+            ff_acc<UNIT>(acc[v][1], wv, x.y);
+            ff_acc<UNIT>(acc[v][2], wv, x.z);
+            ff_acc<UNIT>(acc[v][3], wv, x.w);
+          } else {
+            sacc[v][0] = __fmaf_rn(wv, x.x, sacc[v][0]);
+            sacc[v][1] = __fmaf_rn(wv, x.y, sacc[v][1]);
+            sacc[v][2] = __fmaf_rn(wv, x.z, sacc[v][2]);
+            sacc[v][3] = __fmaf_rn(wv, x.w, sacc[v][3]);
+          }
+        }
+      }
+    }
+  }
+  if constexpr (!FFACC) {
+#pragma unroll
+    for (int v = 0; v < VPT; ++v)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) acc[v][w] = {sacc[v][w], 0.f};
+  }
+}
+
 // Warp per row (grid-stride), VPT float4 column groups per lane per tile of
 // 128 * VPT columns.  Column sums of Rh^2: FP32 over at most 64 rows per
 // lane, then FP64 in shared memory per warp, then one atomic per column and
@@ -75,7 +134,6 @@ __global__ void __launch_bounds__(256) ffr_rows_kernel(Csr A, const float* __res
                                                        double* rr, int b) {
   constexpr int VW = 4;
   constexpr int TILE = 32 * VW * VPT;
-  constexpr bool UNIT = WT == KATZ_UNIT;
   __shared__ double red[8][TILE];
   const int t = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -95,37 +153,14 @@ __global__ void __launch_bounds__(256) ffr_rows_kernel(Csr A, const float* __res
   for (int64_t i = warp; i < A.nrows; i += nwarps) {
     const int64_t k0 = A.rowptr[i], k1 = A.rowptr[i + 1];
     FF acc[VPT][VW];
-#pragma unroll
-    for (int v = 0; v < VPT; ++v)
-#pragma unroll
-      for (int w = 0; w < VW; ++w) acc[v][w] = {0.f, 0.f};
-    for (int64_t kb = k0; kb < k1; kb += 32) {
-      const int64_t k = kb + t;
-      int cj = 0;
-      float wj = 0.f;
-      if (k < k1) {
-        cj = A.col[k];
-        if constexpr (!UNIT) wj = weight<WT>(A.val, k);
-      }
-      const int cnt = (int)(k1 - kb < 32 ? k1 - kb : 32);
-#pragma unroll 4
-      for (int s2 = 0; s2 < cnt; ++s2) {
-        const int j = __shfl_sync(0xffffffffu, cj, s2);
-        float wv = 1.f;
-        if constexpr (!UNIT) wv = __shfl_sync(0xffffffffu, wj, s2);
-        const float* xr = X + int64_t(j) * ld + tile0 + t * VW;
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-          if (cval[v]) {
-            const float4 x = __ldg(reinterpret_cast<const float4*>(xr + v * 32 * VW));
-            ff_acc<UNIT>(acc[v][0], wv, x.x);
-            ff_acc<UNIT>(acc[v][1], wv, x.y);
-            ff_acc<UNIT>(acc[v][2], wv, x.z);
-            ff_acc<UNIT>(acc[v][3], wv, x.w);
-          }
-        }
-      }
-    }
+    // the first pass (X = K0) cancels to the residual's size and needs the
+    // float-float sum; later passes gather a correction X = D with
+    // |M D| ~ |r|, where FP32 sums of short rows carry errors ~1e-7 of the
+    // result (rows longer than kFp32Row keep the float-float sum)
+    if (INIT || k1 - k0 > kFp32Row)
+      row_sum<WT, VPT, true>(A, X, ld, tile0, t, cval, k0, k1, acc);
+    else
+      row_sum<WT, VPT, false>(A, X, ld, tile0, t, cval, k0, k1, acc);
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
       if (!cval[v]) continue;

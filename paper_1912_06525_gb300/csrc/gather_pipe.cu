@@ -28,6 +28,7 @@ namespace katz {
 namespace {
 
 constexpr int kBatch = 8;         // stored entries a consumer warp takes per wait
+constexpr int kFp32Row = 64;      // longest row summed in FP32 by later residual passes
 constexpr int kMaxThreads = 544;  // producer warp + at most 16 consumer warps
 constexpr int kBlockRows = 31;    // rows per block (row pointers fit one warp register)
 constexpr int64_t kBlockWeight = 512;  // stored entries + 4 per row, per block
@@ -206,12 +207,13 @@ __device__ __forceinline__ Win blk_windows(const PipeArgs& a, const Blk& b, int 
   return w;
 }
 
-// One stored entry of a consumer lane: acc += w * x over its 4 columns.
-template <bool RES, bool UNIT>
+// One stored entry of a consumer lane: acc += w * x over its 4 columns,
+// float-float (FFSUM, into af) or FP32 (into acc).
+template <bool FFSUM, bool UNIT>
 __device__ __forceinline__ void take(const unsigned char* src, float w, float (&acc)[4],
                                      FF (&af)[4]) {
   const float4 x = *reinterpret_cast<const float4*>(src);
-  if constexpr (RES) {
+  if constexpr (FFSUM) {
     ff_acc<UNIT>(af[0], w, x.x);
     ff_acc<UNIT>(af[1], w, x.y);
     ff_acc<UNIT>(af[2], w, x.z);
@@ -420,6 +422,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pipe_kernel(const __grid_const
     uint32_t par = (P0 / uint32_t(S)) & 1u;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     FF af[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    // float-float sums for the first residual pass and long rows of later
+    // passes (whose gathered correction is of the residual's size, so FP32
+    // sums of short rows suffice); FP32 for the Chebyshev step
+    const bool ffsum = MODE == kResInit || (MODE == kResUpd && deg > kFp32Row);
     // entries in batches of up to kBatch: one vote over their barriers, the
     // shared-memory loads issued back to back, the slots released in parallel
     for (int t = 0; t < deg;) {
@@ -436,18 +442,26 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pipe_kernel(const __grid_const
         break;
       }
       if (cv) {
-        if (cnt == kBatch) {
+        if (ffsum) {
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            if (u < cnt) {
+              const int su = slot + u < S ? slot + u : slot + u - S;
+              take<true, UNIT>(ring_p + size_t(su) * RS + col * 4, UNIT ? 1.f : wring[su], acc, af);
+            }
+          }
+        } else if (cnt == kBatch) {
 #pragma unroll
           for (int u = 0; u < kBatch; ++u) {
             const int su = slot + u < S ? slot + u : slot + u - S;
-            take<RES, UNIT>(ring_p + size_t(su) * RS + col * 4, UNIT ? 1.f : wring[su], acc, af);
+            take<false, UNIT>(ring_p + size_t(su) * RS + col * 4, UNIT ? 1.f : wring[su], acc, af);
           }
         } else {
 #pragma unroll
           for (int u = 0; u < kBatch; ++u) {
             if (u < cnt) {
               const int su = slot + u < S ? slot + u : slot + u - S;
-              take<RES, UNIT>(ring_p + size_t(su) * RS + col * 4, UNIT ? 1.f : wring[su], acc, af);
+              take<false, UNIT>(ring_p + size_t(su) * RS + col * 4, UNIT ? 1.f : wring[su], acc, af);
             }
           }
         }
@@ -500,6 +514,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pipe_kernel(const __grid_const
         }
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
+          if (!ffsum) af[t] = {acc[t], 0.f};
           // beta * acc as ph + pe
           const FF s = fast_two_sum(af[t].hi, af[t].lo);
           const float ph = a.beh * s.hi;

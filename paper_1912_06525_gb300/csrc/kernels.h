@@ -18,6 +18,7 @@ struct SpmmCfg {
   int col_tile = 0;        // columns per CTA tile (0 = whole row up to 1024 floats / 512 doubles)
   int ctas_per_sm = 8;     // grid = SMs * ctas_per_sm (grid-stride over rows)
   bool pipe = false;       // the pipelined (TMA bulk-copy) kernel measured faster here
+  bool pipe_first = false; // ... for the first refinement-residual pass
 };
 
 // Y[i,:] = gamma * Z[i,:] + alpha * sum_k A[i,k] X[k,:]   for i < A.nrows.

@@ -294,18 +294,22 @@ void spd_inverse_inplace(double* A, int64_t n, int64_t lda, double* ws, int* fla
 // ---------------------------------------------------------------- top-k
 // Candidate order: score descending, node id ascending (a strict total
 // order, so every implementation selects the same set).
-__device__ __forceinline__ bool better(double sa, int ia, double sb, int ib) {
+template <class T>
+__device__ __forceinline__ bool better(T sa, int ia, T sb, int ib) {
   return sa > sb || (sa == sb && ia < ib);
 }
 
 constexpr int kTopMax = 64;
+constexpr int kTopUnroll = 8;  // rows loaded ahead per warp
 
 // Pass 1: CTA = (row slice, tile of 32 query columns); lane c of every warp
 // owns column tile*32 + c, so each warp reads K row by row in coalesced
-// 128-byte segments.  Each (warp, column) keeps a sorted top-k list in
-// local memory; a candidate is tested against q's neighbours (binary search
-// in the sorted CSR row) only when it beats the current k-th entry.
-// Lists go to the scratch as [column][slice*8 + warp][k].
+// 128-byte segments, kTopUnroll rows ahead.  Each (warp, column) keeps a
+// sorted top-k list in local memory (scores in K's own type, so the order
+// is decided in that precision) with its k-th entry held in registers; a
+// candidate is tested against q's neighbours (binary search in the sorted
+// CSR row) only when it beats the k-th entry.  Lists go to the scratch as
+// [column][slice*8 + warp][k].
 template <class VT>
 __global__ void __launch_bounds__(256) topk_partial_kernel(Csr W, const VT* K, int64_t ldk,
                                                            int64_t n, const int32_t* q, int b,
@@ -318,34 +322,50 @@ __global__ void __launch_bounds__(256) topk_partial_kernel(Csr W, const VT* K, i
   const int64_t r1 = min(n, r0 + rows_per_slice);
   const int64_t qq = cv ? q[j] : -1;
   const int64_t nb0 = cv ? W.rowptr[qq] : 0, nb1 = cv ? W.rowptr[qq + 1] : 0;
-  double ls[kTopMax];
+  VT ls[kTopMax];
   int li[kTopMax];
   int cnt = 0;
+  VT thv = VT(0);  // k-th entry once the list is full
+  int thi = 0;
   if (cv) {
-    for (int64_t i = r0 + warp; i < r1; i += 8) {
-      const double v = double(K[i * ldk + j]);
-      if (i == qq) continue;
-      if (cnt == k && !better(v, (int)i, ls[k - 1], li[k - 1])) continue;
-      int64_t lo = nb0, hi = nb1;
-      while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (W.col[mid] < i) lo = mid + 1; else hi = mid;
+    for (int64_t i0 = r0 + warp; i0 < r1; i0 += 8 * kTopUnroll) {
+      VT vals[kTopUnroll];
+#pragma unroll
+      for (int u = 0; u < kTopUnroll; ++u) {
+        const int64_t i = i0 + 8 * u;
+        vals[u] = i < r1 ? K[i * ldk + j] : VT(0);
       }
-      if (lo < nb1 && W.col[lo] == i) continue;
-      int p = cnt < k ? cnt++ : k - 1;
-      while (p > 0 && better(v, (int)i, ls[p - 1], li[p - 1])) {
-        ls[p] = ls[p - 1];
-        li[p] = li[p - 1];
-        --p;
+#pragma unroll
+      for (int u = 0; u < kTopUnroll; ++u) {
+        const int64_t i = i0 + 8 * u;
+        if (i >= r1 || i == qq) continue;
+        const VT v = vals[u];
+        if (cnt == k && !better(v, (int)i, thv, thi)) continue;
+        int64_t lo = nb0, hi = nb1;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (W.col[mid] < i) lo = mid + 1; else hi = mid;
+        }
+        if (lo < nb1 && W.col[lo] == i) continue;
+        int p = cnt < k ? cnt++ : k - 1;
+        while (p > 0 && better(v, (int)i, ls[p - 1], li[p - 1])) {
+          ls[p] = ls[p - 1];
+          li[p] = li[p - 1];
+          --p;
+        }
+        ls[p] = v;
+        li[p] = (int)i;
+        if (cnt == k) {
+          thv = ls[k - 1];
+          thi = li[k - 1];
+        }
       }
-      ls[p] = v;
-      li[p] = (int)i;
     }
     const int lists = gridDim.x * 8;
     const int64_t out = (int64_t(j) * lists + blockIdx.x * 8 + warp) * k;
     for (int t = 0; t < k; ++t) {
       pid[out + t] = t < cnt ? li[t] : -1;
-      psc[out + t] = t < cnt ? ls[t] : 0.0;
+      psc[out + t] = t < cnt ? double(ls[t]) : 0.0;
     }
   }
 }

@@ -219,11 +219,12 @@ template <>
 const double* inv_of<double>(const BlockClass& c) { return c.inv64.p; }
 
 // Pipelined or register kernel for a fused product, by the query's choice
-// (AUTO: what the autotuner measured faster, register if untuned).
-static bool use_pipe(const katz_index& idx, const SpmmCfg* cfg) {
+// (AUTO: what the autotuner measured faster, register if untuned); first:
+// the first refinement-residual pass.
+static bool use_pipe(const katz_index& idx, const SpmmCfg* cfg, bool first = false) {
   if (idx.gather_pref == KATZ_GATHER_PIPELINED) return true;
   if (idx.gather_pref == KATZ_GATHER_REGISTER) return false;
-  return cfg && cfg->pipe;
+  return cfg && (first ? cfg->pipe_first : cfg->pipe);
 }
 
 // Y1 = M11^{-1} X1: dense block inverses for the small blocks (Step 4) and,
@@ -543,8 +544,7 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   const int32_t* pos = use_lrc ? idx.iperm.p : nullptr;
   const GraphPart& G = use_lrc ? idx.Wp : idx.W;
   const SpmmCfg* gcfg = G.cfg(b);
-  const bool pipe = use_pipe(idx, gcfg) && pipe_eligible(G.ps, ld) &&
-                    (idx.unit_weights || G.csr.vdt != KATZ_F64);
+  const bool pipe_ok = pipe_eligible(G.ps, ld) && (idx.unit_weights || G.csr.vdt != KATZ_F64);
   Workspace& ws = idx.ws;
   iters.assign(b, 0);
   relres.assign(b, 0.0);
@@ -598,7 +598,7 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
       // R = b - M K0 (K0 = Kh, Kl = 0) on the first pass, then R -= M D, K += D
       const bool first = refine == 0;
       const float* Xg = first ? Kh : D;
-      if (pipe)
+      if (pipe_ok && use_pipe(idx, gcfg, first))
         pipe_residual(G.view(), G.ps, idx.unit_weights, idx.beta, Xg, Rh, Rl, Kh, Kl, first, ld,
                       b, rr, perr, s);
       else
