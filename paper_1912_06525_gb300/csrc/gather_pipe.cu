@@ -53,7 +53,7 @@ struct PipeArgs {
   const float* X;
   const float* H[5];
   float* O[4];
-  float beta, beh, bel, ak, ck;
+  float beta, beh, bel, ak, ck, sx, sp;
   double* rr;
   int b;
   int* err;
@@ -493,8 +493,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pipe_kernel(const __grid_const
         float out[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-          const float r = bs[t] - xs[t] + a.beta * acc[t];
-          out[t] = xs[t] + a.ak * (xs[t] - ps[t]) + a.ck * r;
+          const float x = a.sx * xs[t];
+          const float r = bs[t] - x + a.beta * (a.sx * acc[t]);
+          out[t] = x + a.ak * (x - a.sp * ps[t]) + a.ck * r;
         }
         *reinterpret_cast<float4*>(a.O[0] + o) = make_float4(out[0], out[1], out[2], out[3]);
       } else {
@@ -665,7 +666,7 @@ bool pipe_eligible(const PipeSplit& ps, int64_t ld) { return ps.nblocks > 0 && l
 
 void pipe_cheb_step(const Csr& A, const PipeSplit& ps, bool unit, double beta, double ak,
                     double ck, const float* Xk, const float* Xprev, const float* B, float* Xout,
-                    int64_t ld, int* err, cudaStream_t s) {
+                    int64_t ld, int* err, cudaStream_t s, double sx, double sp) {
   KATZ_REQUIRE(ld % 4 == 0 && Xk != Xout && aligned16(Xk) && aligned16(B) && aligned16(Xout) &&
                    (!Xprev || aligned16(Xprev)),
                KATZ_EINVAL, "pipe_cheb_step: operands must be 16-byte aligned, Xout != Xk");
@@ -680,6 +681,8 @@ void pipe_cheb_step(const Csr& A, const PipeSplit& ps, bool unit, double beta, d
   a.beta = float(beta);
   a.ak = float(ak);
   a.ck = float(ck);
+  a.sx = float(sx);
+  a.sp = float(sp);
   a.err = err;
   prof_begin(s);
   if (Xprev) pipe_launch<kCheb3>(A, ps, unit, a, s);

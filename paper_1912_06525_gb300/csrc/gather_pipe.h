@@ -32,12 +32,13 @@ void pipe_split_build(const std::vector<int64_t>& rowptr, int64_t nrows, PipeSpl
 // split (narrow blocks stay on the register kernels).
 bool pipe_eligible(const PipeSplit& ps, int64_t ld);
 
-// x_{k+1} = x_k + ak (x_k - x_{k-1}) + ck (B - x_k + beta A x_k) for the
-// ld-padded FP32 blocks; Xprev null means x_{k-1} = 0; Xout may alias Xprev
-// (not Xk).  unit: every stored weight is 1 (weights are not read).
+// x_{k+1} = x_k + ak (x_k - x_{k-1}) + ck (B - x_k + beta A x_k) with
+// x_k = sx * Xk and x_{k-1} = sp * Xprev, for the ld-padded FP32 blocks; Xprev null means
+// x_{k-1} = 0; Xout may alias Xprev (not Xk).  unit: every stored weight is
+// 1 (weights are not read).
 void pipe_cheb_step(const Csr& A, const PipeSplit& ps, bool unit, double beta, double ak,
                     double ck, const float* Xk, const float* Xprev, const float* B, float* Xout,
-                    int64_t ld, int* err, cudaStream_t s);
+                    int64_t ld, int* err, cudaStream_t s, double sx = 1.0, double sp = 1.0);
 
 // Refinement residual in float-float arithmetic with one gathered FP32
 // operand X (M = I - beta A):

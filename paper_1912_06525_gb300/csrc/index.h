@@ -59,9 +59,10 @@ struct katz_index {
   int rank = 0, block_max = 0, split = 1;
   int64_t n1 = 0, n2 = 0, n1s = 0;  // rows [0,n1s) in dense blocks, [n1s,n1) in large blocks
   int n_large = 0;
-  // spectral bound of the large-block W11 for the Chebyshev solve:
-  // spectrum(M11_large) in [1 - beta*lam11, 1 + beta*lam11] (0 = use CG)
-  double lam11 = 0;
+  // spectral bounds of the large-block W11 for the Chebyshev solve:
+  // spectrum(W11_large) in [lam11_min, lam11] (lam11 = 0: use CG), so
+  // spectrum(M11_large) in [1 - beta*lam11, 1 - beta*lam11_min]
+  double lam11 = 0, lam11_min = 0;
   // kernel preference of the query being run (KATZ_GATHER_*), set per query
   int gather_pref = KATZ_GATHER_AUTO;
   katz::Partition part;
@@ -117,7 +118,10 @@ namespace katz {
 Partition partition_graph(const HostCsr& W, int64_t n_hubs, int64_t block_max, bool split);
 
 // Largest eigenvalue of W by FP64 Lanczos on the GPU.
-double lambda_max_gpu(const GraphPart& W, int64_t n, int steps, Workspace& ws, cudaStream_t s);
+// Largest Ritz value of W after `steps` FP64 Lanczos steps (start: all-ones
+// if seed == 0, else SplitMix64(seed)); *lmin (optional) gets the smallest.
+double lambda_max_gpu(const GraphPart& W, int64_t n, int steps, Workspace& ws, cudaStream_t s,
+                      uint64_t seed = 0, double* lmin = nullptr);
 
 void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_build_opts& o,
                  cudaStream_t s);

@@ -274,16 +274,28 @@ static double dget(const double* p, cudaStream_t s) {
 // ----------------------------------------------------------- lambda_max
 // Plain Lanczos on W from the normalised all-ones vector; the largest Ritz
 // value of the tridiagonal matrix is returned.
-double lambda_max_gpu(const GraphPart& W, int64_t n, int steps, Workspace& ws, cudaStream_t s) {
+double lambda_max_gpu(const GraphPart& W, int64_t n, int steps, Workspace& ws, cudaStream_t s,
+                      uint64_t seed, double* lmin) {
+  if (lmin) *lmin = 0.0;
   if (n == 0 || W.csr.nnz == 0) return 0.0;
   const int64_t ld = 2;
   double* v = ws.get<double>("lm.v", n * ld);
   double* vp = ws.get<double>("lm.vp", n * ld);
   double* w = ws.get<double>("lm.w", n * ld);
   double* dd = ws.get<double>("lm.d", 2);
-  std::vector<double> ones(n * ld, 0.0);
-  for (int64_t i = 0; i < n; ++i) ones[i * ld] = 1.0 / std::sqrt(double(n));
-  KATZ_CUDA(cudaMemcpyAsync(v, ones.data(), sizeof(double) * n * ld, cudaMemcpyHostToDevice, s));
+  // start: the normalised all-ones vector (close to the Perron vector), or a
+  // SplitMix64 vector, which also has weight on the lower end of the spectrum
+  std::vector<double> start(n * ld, 0.0);
+  if (seed == 0) {
+    for (int64_t i = 0; i < n; ++i) start[i * ld] = 1.0 / std::sqrt(double(n));
+  } else {
+    const std::vector<double> u = splitmix64_uniform(seed, n);
+    double nrm = 0;
+    for (int64_t i = 0; i < n; ++i) nrm += (u[i] - 0.5) * (u[i] - 0.5);
+    nrm = std::sqrt(nrm);
+    for (int64_t i = 0; i < n; ++i) start[i * ld] = (u[i] - 0.5) / nrm;
+  }
+  KATZ_CUDA(cudaMemcpyAsync(v, start.data(), sizeof(double) * n * ld, cudaMemcpyHostToDevice, s));
   KATZ_CUDA(cudaMemsetAsync(vp, 0, sizeof(double) * n * ld, s));
   std::vector<double> al, be;
   double bprev = 0;
@@ -309,6 +321,7 @@ double lambda_max_gpu(const GraphPart& W, int64_t n, int steps, Workspace& ws, c
   std::vector<double> ev(al), Z;
   be.resize(std::max(0, m - 1));
   tridiag_ql(ev, be, Z, m);
+  if (lmin) *lmin = *std::min_element(ev.begin(), ev.end());
   return *std::max_element(ev.begin(), ev.end());
 }
 
@@ -469,10 +482,14 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   upload_part(W21, o.value_dtype, idx.W21, s);
   upload_part(W11L, o.value_dtype, idx.W11L, s);
   if (W11L.nrows > 0 && W11L.nnz() > 0) {
-    // Lanczos lower-bounds lambda_max; a 2% margin keeps the Chebyshev
-    // interval safe (the smallest eigenvalue of W11 is >= -lambda_max)
-    const double lam = 1.02 * lambda_max_gpu(idx.W11L, W11L.nrows, 96, idx.ws, s);
+    // Lanczos Ritz values lie inside the spectrum: widen both ends by 2% of
+    // its width; the lower end never below -lambda_max (W11 >= 0)
+    const double top = lambda_max_gpu(idx.W11L, W11L.nrows, 96, idx.ws, s);
+    double bot = 0;
+    lambda_max_gpu(idx.W11L, W11L.nrows, 96, idx.ws, s, 0x243F6A8885A308D3ull, &bot);
+    const double lam = 1.02 * top;
     idx.lam11 = beta * lam < 0.999 ? lam : 0.0;
+    idx.lam11_min = std::max(-lam, std::min(0.0, bot - 0.02 * (top - bot)));
   } else if (W11L.nrows > 0) {
     idx.lam11 = 1e-300;  // no edges: M11 = I
   }

@@ -30,12 +30,13 @@ void spmm(const Csr& A, const int32_t* heavy, int64_t n_heavy, double alpha,
           int64_t ldy, int b, const VT* V, int64_t ldv, double* dots, cudaStream_t s,
           const SpmmCfg* cfg = nullptr);
 
-// Fused Chebyshev step for (I - beta A) x = b (FP32):
+// Fused Chebyshev step for (I - beta A) x = b (FP32), with x_k = sx * Xk and
+// x_{k-1} = sp * Xprev:
 //   x_{k+1} = x_k + ak (x_k - x_{k-1}) + ck (b - x_k + beta A x_k)
 // Xk != Xout; Xprev null means x_{k-1} = 0; Xprev may equal Xout.
 void cheb_step(const Csr& A, double beta, double ak, double ck, const float* Xk,
                const float* Xprev, const float* B, float* Xout, int64_t ld, int b, cudaStream_t s,
-               const SpmmCfg* cfg = nullptr);
+               const SpmmCfg* cfg = nullptr, double sx = 1.0, double sp = 1.0);
 
 // dots[c] += sum_{i<len} A[i,c] * B[i,c]
 template <class VT>

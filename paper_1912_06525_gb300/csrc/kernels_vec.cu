@@ -346,6 +346,7 @@ template void spmm<double>(const Csr&, const int32_t*, int64_t, double, const do
 // and may equal Xout (each row reads its own x_{k-1} before writing).
 template <int WT, int VPT>
 __global__ void __launch_bounds__(256) cheb_step_kernel(Csr A, float beta, float ak, float ck,
+                                                        float sx, float sp,
                                                         const float* __restrict__ Xk,
                                                         const float* Xprev,
                                                         const float* __restrict__ B, float* Xout,
@@ -401,8 +402,9 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(Csr A, float beta, float
       if (Xprev) vload<float>(Xprev + o, xp);
 #pragma unroll
       for (int w = 0; w < VW; ++w) {
-        const float r = bo[w] - xo[w] + beta * acc[v][w];
-        xn[w] = xo[w] + ak * (xo[w] - xp[w]) + ck * r;
+        const float xs = sx * xo[w];
+        const float r = bo[w] - xs + beta * (sx * acc[v][w]);
+        xn[w] = xs + ak * (xs - sp * xp[w]) + ck * r;
       }
       vstore<float>(Xout + o, xn);
     }
@@ -411,7 +413,7 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(Csr A, float beta, float
 
 void cheb_step(const Csr& A, double beta, double ak, double ck, const float* Xk,
                const float* Xprev, const float* B, float* Xout, int64_t ld, int b, cudaStream_t s,
-               const SpmmCfg* cfg) {
+               const SpmmCfg* cfg, double sx, double sp) {
   KATZ_REQUIRE(ld % 4 == 0 && ld >= b && Xk != Xout &&
                    (reinterpret_cast<uintptr_t>(Xk) | reinterpret_cast<uintptr_t>(Xprev) |
                     reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(Xout)) % 16 == 0,
@@ -427,10 +429,10 @@ void cheb_step(const Csr& A, double beta, double ak, double ck, const float* Xk,
   prof_begin(s);
 #define KATZ_CHEB(WT)                                                                       \
   if (vpt == 2)                                                                             \
-    cheb_step_kernel<WT, 2><<<grid, 256, 0, s>>>(A, float(beta), float(ak), float(ck), Xk, Xprev, \
+    cheb_step_kernel<WT, 2><<<grid, 256, 0, s>>>(A, float(beta), float(ak), float(ck), float(sx), float(sp), Xk, Xprev, \
                                                  B, Xout, ld, b);                           \
   else                                                                                      \
-    cheb_step_kernel<WT, 1><<<grid, 256, 0, s>>>(A, float(beta), float(ak), float(ck), Xk, Xprev, \
+    cheb_step_kernel<WT, 1><<<grid, 256, 0, s>>>(A, float(beta), float(ak), float(ck), float(sx), float(sp), Xk, Xprev, \
                                                  B, Xout, ld, b)
   switch (A.vdt) {
     case KATZ_UNIT: KATZ_CHEB(KATZ_UNIT); break;

@@ -230,44 +230,50 @@ static bool use_pipe(const katz_index& idx, const SpmmCfg* cfg, bool first = fal
 // Y1 = M11^{-1} X1: dense block inverses for the small blocks (Step 4) and,
 // for blocks kept whole, CG on that diagonal block to relative tolerance tolL.
 // Chebyshev iteration (Saad, Iterative Methods, Alg. 12.1) on the large
-// M11 blocks, in three-term form: spectrum in [1 - delta, 1 + delta] with
-// delta = beta*lam11 (centre 1), so x_1 = b and
-//   x_{k+1} = x_k + rho_k rho_{k-1} (x_k - x_{k-1}) + (2 rho_k / delta) r_k,
-//   rho_0 = delta, rho_k = 1 / (2/delta - rho_{k-1}).
+// M11 blocks, in three-term form, for the spectrum of M11 in
+// [theta - d, theta + d] = [1 - beta*lam11, 1 - beta*lam11_min]:
+//   x_1 = b / theta,
+//   x_{k+1} = x_k + rho_k rho_{k-1} (x_k - x_{k-1}) + (2 rho_k / d) r_k,
+//   rho_0 = d / theta, rho_k = 1 / (2 theta / d - rho_{k-1}).
 // The iteration count follows from the bound 2 c^K <= tol with
-// c = (sqrt(kappa)-1)/(sqrt(kappa)+1).  No inner products, no host
-// synchronisation, one fused kernel per step; two buffers (x_{k+1}
+// c = (sqrt(kappa)-1)/(sqrt(kappa)+1), kappa = (theta + d) / (theta - d).
+// No inner products, no host synchronisation, one fused kernel per step
+// (x_1 enters the first one as b scaled by 1/theta); two buffers (x_{k+1}
 // overwrites x_{k-1} row by row).
 static void m11_chebyshev(katz_index& idx, const float* X, float* Y, int b, int64_t ld,
                           double tol, cudaStream_t s) {
   const int64_t len = idx.n1 - idx.n1s;
-  const double delta = idx.beta * idx.lam11;
-  const double kappa = (1.0 + delta) / (1.0 - delta);
+  const double lo = 1.0 - idx.beta * idx.lam11, hi = 1.0 - idx.beta * idx.lam11_min;
+  const double theta = 0.5 * (lo + hi), d = 0.5 * (hi - lo);
+  const double kappa = hi / lo;
   const double cf = (std::sqrt(kappa) - 1.0) / (std::sqrt(kappa) + 1.0);
   const int K = cf <= 0 ? 1 : std::max(1, int(std::ceil(std::log(tol / 2.0) / std::log(cf))));
   if (K == 1) {
-    KATZ_CUDA(cudaMemcpyAsync(Y, X, sizeof(float) * len * ld, cudaMemcpyDeviceToDevice, s));
+    scale_copy<float>(X, ld, Y, ld, len, int(ld), 1.0 / theta, false, s);
     return;
   }
   float* T = idx.ws.get<float>("ch.T", size_t(len) * ld);
   // x_k for k >= 2 alternates between Y and T so that x_K lands in Y
   auto slot = [&](int k) { return ((K - k) % 2 == 0) ? Y : T; };
-  const double sigma = 1.0 / delta;
-  double rho_prev = delta;  // rho_0 = 1/sigma
+  const double sigma = theta / d;
+  double rho_prev = d / theta;  // rho_0 = 1/sigma
   const SpmmCfg* cfg = idx.W11L.cfg(b);
   const bool pipe = use_pipe(idx, cfg) && pipe_eligible(idx.W11L.ps, ld) &&
                     (idx.unit_weights || idx.W11L.csr.vdt != KATZ_F64);
   int* perr = idx.ws.get<int>("pipe.err", 1);
   for (int k = 1; k < K; ++k) {
     const double rho = 1.0 / (2.0 * sigma - rho_prev);
-    const double ak = rho * rho_prev, ck = 2.0 * rho / delta;
+    const double ak = rho * rho_prev, ck = 2.0 * rho / d;
+    // x_1 = X / theta is never stored: it enters as Xk (k = 1) or Xprev (k = 2)
     const float* xk = k == 1 ? X : slot(k);
     const float* xprev = k == 1 ? nullptr : (k == 2 ? X : slot(k - 1));
+    const double sx = k == 1 ? 1.0 / theta : 1.0, sp = k == 2 ? 1.0 / theta : 1.0;
     if (pipe)
       pipe_cheb_step(idx.W11L.view(), idx.W11L.ps, idx.unit_weights, idx.beta, ak, ck, xk, xprev,
-                     X, slot(k + 1), ld, perr, s);
+                     X, slot(k + 1), ld, perr, s, sx, sp);
     else
-      cheb_step(idx.W11L.view(), idx.beta, ak, ck, xk, xprev, X, slot(k + 1), ld, b, s, cfg);
+      cheb_step(idx.W11L.view(), idx.beta, ak, ck, xk, xprev, X, slot(k + 1), ld, b, s, cfg, sx,
+                sp);
     rho_prev = rho;
   }
 }
