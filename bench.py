@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
     ap.add_argument("--c", type=float, default=0.9, help="beta = c / lambda_max")
     ap.add_argument("--method", default="lrc", choices=["lrc", "cg"])
+    ap.add_argument("--gather", default="auto", choices=["auto", "register", "pipelined"],
+                    help="kernel of the wide fused products (auto: the autotuner's choice)")
     ap.add_argument("--batch", type=int, default=0,
                     help="override the query batch width b (small profiling cases)")
     ap.add_argument("--workload", type=int, default=3, choices=[2, 3],
@@ -263,10 +265,12 @@ def main():
     ids = torch.empty((b, 20), dtype=torch.int32, device=dev)
     sc = torch.empty((b, 20), dtype=torch.float64, device=dev)
     qfn = katz.katz_query_batch if args.method == "lrc" else katz.cg_query_batch
+    gk = {"auto": katz.KATZ_GATHER_AUTO, "register": katz.KATZ_GATHER_REGISTER,
+          "pipelined": katz.KATZ_GATHER_PIPELINED}[args.gather]
     last = {}
 
     def step(qq, KK, ii, ss):
-        st, it, rel = qfn(idx, qq, KK, out_dtype=katz.KATZ_F32, tol=1e-6)
+        st, it, rel = qfn(idx, qq, KK, out_dtype=katz.KATZ_F32, tol=1e-6, gather_kernel=gk)
         katz.linkpred_topk(idx, qq, KK, katz.KATZ_F32, 20, ii, ss)
         last.update(st=st, it=it, rel=rel)
 
@@ -379,7 +383,7 @@ def main():
     if rank == 0:
         cfg = workload_desc(g, b, c, rank_r, args.scale, args.workload)
         cfg.update({"method": args.method, "parallelism": "replicas" if world > 1 else "single",
-                    "spmm_autotune": tune,
+                    "spmm_autotune": tune, "gather_kernel": args.gather,
                     "n2": info["n2"], "n1": info["n1"], "index_build_s": build_s,
                     "lambda_max": lam})
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

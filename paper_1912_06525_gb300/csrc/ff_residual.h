@@ -17,8 +17,9 @@ void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl,
                 cudaStream_t s);
 
 // (Rh, Rl)[pos(i), j] += beta W[q_j, i] for the stored entries of the query
-// rows (the sparse right-hand side), with rr[j] adjusted by the change of
-// Rh^2.  maxdeg bounds the query rows' lengths.
+// rows (the sparse right-hand side); rr (optional) is adjusted by the change
+// of Rh^2, which cancels badly when Rh ~ -b: prefer fresh column norms.
+// maxdeg bounds the query rows' lengths.
 void ffr_add_rhs(const Csr& W, const int32_t* q, const int32_t* pos, int b, double beta, float* Rh,
                  float* Rl, int64_t ld, double* rr, int64_t maxdeg, cudaStream_t s);
 

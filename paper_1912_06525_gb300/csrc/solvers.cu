@@ -601,15 +601,22 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
     for (;;) {
       const auto r0 = clk::now();
       KATZ_CUDA(cudaMemsetAsync(rr, 0, sizeof(double) * bpad(b), s));
-      // R = b - M K0 (K0 = Kh, Kl = 0) on the first pass, then R -= M D, K += D
+      // R = b - M K0 (K0 = Kh, Kl = 0) on the first pass, then R -= M D, K += D.
+      // The first pass adds the sparse b after the sweep, so its norms are
+      // taken afterwards (summing squares before and correcting by
+      // b_i^2 - r_i^2 would cancel catastrophically); later passes fuse them.
       const bool first = refine == 0;
       const float* Xg = first ? Kh : D;
+      double* rr_fused = first ? nullptr : rr;
       if (pipe_ok && use_pipe(idx, gcfg, first))
         pipe_residual(G.view(), G.ps, idx.unit_weights, idx.beta, Xg, Rh, Rl, Kh, Kl, first, ld,
-                      b, rr, perr, s);
+                      b, rr_fused, perr, s);
       else
-        ffr_update(G.view(), idx.beta, Xg, Rh, Rl, Kh, Kl, first, ld, b, rr, gcfg, s);
-      if (first) ffr_add_rhs(idx.W.view(), q, pos, b, idx.beta, Rh, Rl, ld, rr, maxdeg, s);
+        ffr_update(G.view(), idx.beta, Xg, Rh, Rl, Kh, Kl, first, ld, b, rr_fused, gcfg, s);
+      if (first) {
+        ffr_add_rhs(idx.W.view(), q, pos, b, idx.beta, Rh, Rl, ld, nullptr, maxdeg, s);
+        coldot<float>(Rh, ld, Rh, ld, n, b, rr, s);
+      }
       inner_thresholds_kernel<<<1, 1024, 0, s>>>(rr, thr2, tau, b, conv, thr2_in, nopen);
       KATZ_CHECK_LAUNCH();
       ++refine;
