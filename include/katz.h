@@ -179,13 +179,15 @@ int katz_index_get_sigma(const katz_index* idx, double* sigma);
  * RHS b_j = beta W e_{q_j} (Eq. 3); F = B2 - M12^T M11^{-1} B1 (Eq. 7); PCG
  * on S K2 = F preconditioned by S~^{-1} = M22^{-1} + W_r D W_r^T (Eq. 14);
  * K1 = M11^{-1}(B1 - M12 K2) (Eq. 6); merge and un-permute.  With
- * KATZ_PREC_MIXED the LRC solve runs in FP32 and FP64 residuals of the full
- * system drive iterative refinement until opts->tol is met.
+ * KATZ_PREC_MIXED the LRC solve runs in FP32 and FP64-class residuals of the
+ * full system (float-float, ~2^-48 relative to their terms; FP64 for
+ * FP64-valued graphs) drive iterative refinement until opts->tol is met.
  * q[b]: int32 node ids (host or device).  K_out: n x b node-major, ld = ldk,
  * element type out_dtype (KATZ_F32 or KATZ_F64), host or device.
  * stats may be NULL; iters_out[b] / rel_res_out[b] (host, may be NULL)
- * receive per-column iteration counts and final FP64 relative residuals.
- * Needs an index built with build_lrc = 1. */
+ * receive per-column iteration counts and the relative residuals
+ * ||b_j - M k_j||_2 / ||b_j||_2 of the returned K (NaN with KATZ_PREC_F32,
+ * which evaluates no residual).  Needs an index built with build_lrc = 1. */
 int katz_query_batch(const katz_index* idx, const int32_t* q, int32_t b,
                      const katz_query_opts* opts, void* K_out, int32_t out_dtype,
                      int64_t ldk, katz_stats* stats, int32_t* iters_out,

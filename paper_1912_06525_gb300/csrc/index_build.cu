@@ -376,7 +376,10 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   idx.unit_weights = true;
   for (double v : W.val)
     if (v != 1.0) { idx.unit_weights = false; break; }
-  upload_part(W, o.value_dtype, idx.W, s);
+  // graphs whose stored weights are all 1 keep no values on the device: every
+  // product then runs its unit-weight kernel (no weight loads or products)
+  const int sdt = idx.unit_weights ? int(KATZ_UNIT) : o.value_dtype;
+  upload_part(W, sdt, idx.W, s);
   idx.lambda = lambda_max_gpu(idx.W, idx.n, 96, idx.ws, s);
   KATZ_REQUIRE(beta * idx.lambda < 1.0, KATZ_ENOTSPD,
                "beta * lambda_max = " + std::to_string(beta * idx.lambda) +
@@ -477,10 +480,10 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   sub(W21, n1, n, 0, n1);
   sub(W22, n1, n, n1, n);
   sub(W11L, idx.n1s, n1, idx.n1s, n1);
-  upload_part(Wp, o.value_dtype, idx.Wp, s);
-  upload_part(W12, o.value_dtype, idx.W12, s);
-  upload_part(W21, o.value_dtype, idx.W21, s);
-  upload_part(W11L, o.value_dtype, idx.W11L, s);
+  upload_part(Wp, sdt, idx.Wp, s);
+  upload_part(W12, sdt, idx.W12, s);
+  upload_part(W21, sdt, idx.W21, s);
+  upload_part(W11L, sdt, idx.W11L, s);
   if (W11L.nrows > 0 && W11L.nnz() > 0) {
     // Lanczos Ritz values lie inside the spectrum: widen both ends by 2% of
     // its width; the lower end never below -lambda_max (W11 >= 0)
@@ -493,7 +496,7 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   } else if (W11L.nrows > 0) {
     idx.lam11 = 1e-300;  // no edges: M11 = I
   }
-  upload_part(W22, o.value_dtype, idx.W22, s);
+  upload_part(W22, sdt, idx.W22, s);
   const GraphPart& W22d = idx.W22;
 
   // --- M11 dense block inverses by size class (Step 4)
