@@ -59,11 +59,11 @@ double time_launches(F&& launch, cudaStream_t s, int reps) {
 }
 
 // Is the pipelined kernel faster than the register one for the fused
-// product?  Residual: first[0] for the first pass, the return value for
-// the later passes.
+// product?  Residual: *first for the first pass (the later passes have no
+// pipelined kernel).
 bool pipe_faster(const GraphPart& g, Fused kind, bool unit, const SpmmCfg& c, float* X, float* Y,
-                 float* Z, float* K1, float* K2, int b, int64_t ld, Workspace& ws, cudaStream_t s,
-                 int reps, bool* first) {
+                 float* Z, int b, int64_t ld, Workspace& ws, cudaStream_t s, int reps,
+                 bool* first) {
   int* err = ws.get<int>("pipe.err", 1);
   KATZ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
   bool faster;
@@ -74,19 +74,13 @@ bool pipe_faster(const GraphPart& g, Fused kind, bool unit, const SpmmCfg& c, fl
         [&] { pipe_cheb_step(g.view(), g.ps, unit, 0.01, 0.1, 1.0, X, X, X, Y, ld, err, s); }, s, reps);
     faster = t_pipe < t_reg;
   } else {
-    double t[2][2];  // [first/later][register/pipelined]
-    for (int f = 0; f < 2; ++f) {
-      const bool init = f == 0;
-      t[f][0] = time_launches(
-          [&] { ffr_update(g.view(), 0.01, X, Y, Z, K1, K2, init, ld, b, nullptr, &c, s); }, s, reps);
-      t[f][1] = time_launches(
-          [&] {
-            pipe_residual(g.view(), g.ps, unit, 0.01, X, Y, Z, K1, K2, init, ld, b, nullptr, err, s);
-          },
-          s, reps);
-    }
-    *first = t[0][1] < t[0][0];
-    faster = t[1][1] < t[1][0];
+    const double t_reg = time_launches(
+        [&] { ffr_update(g.view(), 0.01, X, Y, Z, true, ld, b, nullptr, &c, s); }, s, reps);
+    const double t_pipe = time_launches(
+        [&] { pipe_residual(g.view(), g.ps, unit, 0.01, X, Y, Z, ld, b, nullptr, err, s); }, s,
+        reps);
+    *first = t_pipe < t_reg;
+    faster = false;  // later passes: register kernel
   }
   int herr = 0;
   KATZ_CUDA(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -130,21 +124,12 @@ SpmmCfg tune_part(GraphPart& g, int b, Workspace& ws, cudaStream_t s, double* be
     }
   }
   if (kind != Fused::none && pipe_eligible(g.ps, ld) && (unit || g.csr.vdt != KATZ_F64)) {
-    const bool res = kind == Fused::residual;
     float* Z = ws.get<float>("tune.Z", size_t(rows) * ld);
-    float* K1 = res ? ws.get<float>("tune.K1", size_t(rows) * ld) : nullptr;
-    float* K2 = res ? ws.get<float>("tune.K2", size_t(rows) * ld) : nullptr;
-    if (res) {
-      KATZ_CUDA(cudaMemsetAsync(K1, 0, sizeof(float) * rows * ld, s));
-      KATZ_CUDA(cudaMemsetAsync(K2, 0, sizeof(float) * rows * ld, s));
-    }
     KATZ_CUDA(cudaMemsetAsync(Z, 0, sizeof(float) * rows * ld, s));
     bool first = false;
-    best.pipe = pipe_faster(g, kind, unit, best, X, Y, Z, K1, K2, b, ld, ws, s, reps, &first);
+    best.pipe = pipe_faster(g, kind, unit, best, X, Y, Z, b, ld, ws, s, reps, &first);
     best.pipe_first = first;
     ws.release("tune.Z");
-    ws.release("tune.K1");
-    ws.release("tune.K2");
   }
   g.tuned[b] = best;
   std::lock_guard<std::mutex> l(g_mu);

@@ -1,13 +1,15 @@
 // Refinement residual of the full system in double-FP32 ("float-float")
-// arithmetic.  The solution is kept as an unevaluated sum Kh + Kl of two FP32
-// arrays and the residual as Rh + Rl; every pass gathers one FP32 operand X
-// (the first FP32 solution, then each FP32 correction) and updates
-//   R <- R - M X  (M = I - beta A),   K <- K + X,
-// with the sparse sums accumulated by the error-free transformations TwoSum
-// (Knuth) and TwoProd (Dekker, via FMA): ~48 significant bits with FP32
-// instructions only (GB300's FP64 pipe is ~60x slower than FP32) and 4-byte
-// gathers.  Rh, rounded to FP32 after the cancellation, is the right-hand
-// side of the next FP32 correction solve.
+// arithmetic, gathering one FP32 operand X per pass (M = I - beta A):
+//   first pass : (Rh, Rl) = -M X for the first FP32 solution X = K0 (the
+//                sums in float-float: TwoSum (Knuth) / TwoProd (Dekker, via
+//                FMA), ~48 significant bits with FP32 instructions only, as
+//                GB300's FP64 pipe is ~60x slower); the sparse b is added
+//                after it in float-float;
+//   later passes: Rh = Rh (+ Rl) - M X for an FP32 correction X = D, FP32
+//                sums for short rows (|M D| is of the order of |R|).
+// Rh, rounded to FP32 after the cancellation, is the right-hand side of the
+// next FP32 correction solve.  The solution is kept as Kh + Kl (+ the last
+// correction, folded in by ff_out or ff_add).
 #include "ff_residual.h"
 
 namespace katz {
@@ -129,9 +131,8 @@ __device__ __forceinline__ void row_sum(const Csr& A, const float* __restrict__ 
 // CTA.
 template <int WT, int VPT, bool INIT>
 __global__ void __launch_bounds__(256) ffr_rows_kernel(Csr A, const float* __restrict__ X,
-                                                       float* Rh, float* Rl, float* Kh, float* Kl,
-                                                       int64_t ld, float beh, float bel,
-                                                       double* rr, int b) {
+                                                       float* Rh, float* Rl, int64_t ld, float beh,
+                                                       float bel, double* rr, int b) {
   constexpr int VW = 4;
   constexpr int TILE = 32 * VW * VPT;
   __shared__ double red[8][TILE];
@@ -168,16 +169,13 @@ __global__ void __launch_bounds__(256) ffr_rows_kernel(Csr A, const float* __res
       const float4 x4 = __ldg(reinterpret_cast<const float4*>(X + o));
       const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
       float rh0[4] = {0.f, 0.f, 0.f, 0.f}, rl0[4] = {0.f, 0.f, 0.f, 0.f};
-      float kh[4], kl[4];
       if constexpr (!INIT) {
         const float4 a1 = *reinterpret_cast<const float4*>(Rh + o);
-        const float4 a2 = *reinterpret_cast<const float4*>(Rl + o);
-        const float4 a3 = *reinterpret_cast<const float4*>(Kh + o);
-        const float4 a4 = *reinterpret_cast<const float4*>(Kl + o);
         rh0[0] = a1.x; rh0[1] = a1.y; rh0[2] = a1.z; rh0[3] = a1.w;
-        rl0[0] = a2.x; rl0[1] = a2.y; rl0[2] = a2.z; rl0[3] = a2.w;
-        kh[0] = a3.x; kh[1] = a3.y; kh[2] = a3.z; kh[3] = a3.w;
-        kl[0] = a4.x; kl[1] = a4.y; kl[2] = a4.z; kl[3] = a4.w;
+        if (Rl) {
+          const float4 a2 = *reinterpret_cast<const float4*>(Rl + o);
+          rl0[0] = a2.x; rl0[1] = a2.y; rl0[2] = a2.z; rl0[3] = a2.w;
+        }
       }
       float rh[4], rl[4];
 #pragma unroll
@@ -186,19 +184,10 @@ __global__ void __launch_bounds__(256) ffr_rows_kernel(Csr A, const float* __res
         rh[w] = r.hi;
         rl[w] = r.lo;
         sq[v][w] = __fmaf_rn(r.hi, r.hi, sq[v][w]);
-        if constexpr (!INIT) {
-          const FF k1s = two_sum(kh[w], xs[w]);
-          const FF k2 = fast_two_sum(k1s.hi, k1s.lo + kl[w]);
-          kh[w] = k2.hi;
-          kl[w] = k2.lo;
-        }
       }
       *reinterpret_cast<float4*>(Rh + o) = make_float4(rh[0], rh[1], rh[2], rh[3]);
-      *reinterpret_cast<float4*>(Rl + o) = make_float4(rl[0], rl[1], rl[2], rl[3]);
-      if constexpr (!INIT) {
-        *reinterpret_cast<float4*>(Kh + o) = make_float4(kh[0], kh[1], kh[2], kh[3]);
-        *reinterpret_cast<float4*>(Kl + o) = make_float4(kl[0], kl[1], kl[2], kl[3]);
-      }
+      if constexpr (INIT)
+        *reinterpret_cast<float4*>(Rl + o) = make_float4(rl[0], rl[1], rl[2], rl[3]);
     }
     if (++nsq == 64) {
 #pragma unroll
@@ -247,18 +236,34 @@ __global__ void ffr_add_rhs_kernel(Csr W, const int32_t* q, const int32_t* pos, 
   if (rr) atomicAdd(rr + j, double(r.hi) * r.hi - double(old) * old);
 }
 
+__global__ void ff_add_kernel(float* __restrict__ Kh, float* __restrict__ Kl,
+                              const float* __restrict__ D, int64_t total) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const FF t = two_sum(Kh[e], D[e]);
+    const FF u = fast_two_sum(t.hi, t.lo + Kl[e]);
+    Kh[e] = u.hi;
+    Kl[e] = u.lo;
+  }
+}
+
+// out = Kh + Kl (+ D), rounded once to the output type
 __global__ void ff_out_kernel(const float* __restrict__ Kh, const float* __restrict__ Kl,
-                              int64_t ld, const int32_t* map, int64_t n, int b, void* out,
-                              int out_dt, int64_t ldk) {
+                              const float* __restrict__ D, int64_t ld, const int32_t* map,
+                              int64_t n, int b, void* out, int out_dt, int64_t ldk) {
   const int64_t total = n * b;
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
        e += int64_t(gridDim.x) * blockDim.x) {
     const int64_t i = e / b, c = e - i * b;
     const int64_t r = map ? map[i] : i;
-    if (out_dt == KATZ_F64)
-      static_cast<double*>(out)[i * ldk + c] = double(Kh[r * ld + c]) + double(Kl[r * ld + c]);
-    else
-      static_cast<float*>(out)[i * ldk + c] = Kh[r * ld + c] + Kl[r * ld + c];
+    const int64_t o = r * ld + c;
+    const float d = D ? D[o] : 0.f;
+    if (out_dt == KATZ_F64) {
+      static_cast<double*>(out)[i * ldk + c] = (double(Kh[o]) + double(d)) + double(Kl[o]);
+    } else {
+      const FF t = two_sum(Kh[o], d);
+      static_cast<float*>(out)[i * ldk + c] = t.hi + (t.lo + Kl[o]);
+    }
   }
 }
 
@@ -268,14 +273,11 @@ unsigned flat(int64_t total) {
 
 }  // namespace
 
-void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl, float* Kh,
-                float* Kl, bool init, int64_t ld, int b, double* rr, const SpmmCfg* cfg,
-                cudaStream_t s) {
+void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl, bool init,
+                int64_t ld, int b, double* rr, const SpmmCfg* cfg, cudaStream_t s) {
   KATZ_REQUIRE(ld % 4 == 0 && ld >= b && reinterpret_cast<uintptr_t>(X) % 16 == 0 &&
                    reinterpret_cast<uintptr_t>(Rh) % 16 == 0 &&
-                   reinterpret_cast<uintptr_t>(Rl) % 16 == 0 &&
-                   (init || (reinterpret_cast<uintptr_t>(Kh) % 16 == 0 &&
-                             reinterpret_cast<uintptr_t>(Kl) % 16 == 0)),
+                   reinterpret_cast<uintptr_t>(Rl) % 16 == 0 && (Rl || !init),
                KATZ_EINVAL, "ffr_update: operands must be 16-byte aligned with padded rows");
   if (A.nrows <= 0) return;
   const float beh = float(beta), bel = float(beta - double(beh));
@@ -287,7 +289,7 @@ void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl,
   const dim3 grid((unsigned)std::max<int64_t>(1, ctas), (unsigned)tiles);
   prof_begin(s);
 #define KATZ_FFR(WT, V, I) \
-  ffr_rows_kernel<WT, V, I><<<grid, 256, 0, s>>>(A, X, Rh, Rl, Kh, Kl, ld, beh, bel, rr, b)
+  ffr_rows_kernel<WT, V, I><<<grid, 256, 0, s>>>(A, X, Rh, Rl, ld, beh, bel, rr, b)
 #define KATZ_FFR_W(WT)                                                     \
   if (vpt == 2) {                                                          \
     if (init) KATZ_FFR(WT, 2, true); else KATZ_FFR(WT, 2, false);          \
@@ -306,7 +308,7 @@ void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl,
   if (profiling())
     prof_end("ff_residual",
              8.0 * (A.nrows + 1) + double(A.nnz) * (4 + vdt_size(A.vdt)) +
-                 4.0 * ld * (A.ncols + A.nrows * (init ? 3.0 : 9.0)),
+                 4.0 * ld * (A.ncols + A.nrows * (init ? 3.0 : (Rl ? 4.0 : 3.0))),
              s);
 }
 
@@ -323,10 +325,16 @@ void ffr_add_rhs(const Csr& W, const int32_t* q, const int32_t* pos, int b, doub
   KATZ_CHECK_LAUNCH();
 }
 
-void ff_out(const float* Kh, const float* Kl, int64_t ld, const int32_t* map, int64_t n, int b,
-            void* out, int out_dt, int64_t ldk, cudaStream_t s) {
+void ff_add(float* Kh, float* Kl, const float* D, int64_t total, cudaStream_t s) {
+  if (total <= 0) return;
+  ff_add_kernel<<<flat(total), 256, 0, s>>>(Kh, Kl, D, total);
+  KATZ_CHECK_LAUNCH();
+}
+
+void ff_out(const float* Kh, const float* Kl, const float* D, int64_t ld, const int32_t* map,
+            int64_t n, int b, void* out, int out_dt, int64_t ldk, cudaStream_t s) {
   if (n * b <= 0) return;
-  ff_out_kernel<<<flat(n * b), 256, 0, s>>>(Kh, Kl, ld, map, n, b, out, out_dt, ldk);
+  ff_out_kernel<<<flat(n * b), 256, 0, s>>>(Kh, Kl, D, ld, map, n, b, out, out_dt, ldk);
   KATZ_CHECK_LAUNCH();
 }
 

@@ -8,13 +8,16 @@ namespace katz {
 
 // One refinement pass with the gathered FP32 operand X (M = I - beta A,
 // A's stored weights exact in FP32):
-//   init   : (Rh, Rl) = -X + beta A X
-//   update : (Rh, Rl) += -X + beta A X  and  (Kh, Kl) += X
-// and rr[c] += sum_i Rh[i][c]^2 for c < b (the caller zeroes rr).  Blocks
-// are ld-padded FP32, 16-byte aligned; cfg: the tuned CTAs per SM or null.
-void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl, float* Kh,
-                float* Kl, bool init, int64_t ld, int b, double* rr, const SpmmCfg* cfg,
-                cudaStream_t s);
+//   init   : (Rh, Rl) = -X + beta A X            (float-float sums)
+//   update : Rh = Rh (+ Rl if non-null) - X + beta A X   (Rl not written)
+// and rr[c] += sum_i Rh[i][c]^2 for c < b when rr is non-null (the caller
+// zeroes rr).  Blocks are ld-padded FP32, 16-byte aligned; cfg: the tuned
+// CTAs per SM or null.
+void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl, bool init,
+                int64_t ld, int b, double* rr, const SpmmCfg* cfg, cudaStream_t s);
+
+// (Kh, Kl) += D elementwise (TwoSum), total = rows * ld.
+void ff_add(float* Kh, float* Kl, const float* D, int64_t total, cudaStream_t s);
 
 // (Rh, Rl)[pos(i), j] += beta W[q_j, i] for the stored entries of the query
 // rows (the sparse right-hand side); rr (optional) is adjusted by the change
@@ -23,8 +26,9 @@ void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl,
 void ffr_add_rhs(const Csr& W, const int32_t* q, const int32_t* pos, int b, double beta, float* Rh,
                  float* Rl, int64_t ld, double* rr, int64_t maxdeg, cudaStream_t s);
 
-// out[i, c] = Kh[map(i), c] + Kl[map(i), c] in FP32 or FP64.
-void ff_out(const float* Kh, const float* Kl, int64_t ld, const int32_t* map, int64_t n, int b,
-            void* out, int out_dt, int64_t ldk, cudaStream_t s);
+// out[i, c] = Kh + Kl (+ D if non-null) at row map(i), column c, rounded
+// once to FP32 or FP64.
+void ff_out(const float* Kh, const float* Kl, const float* D, int64_t ld, const int32_t* map,
+            int64_t n, int b, void* out, int out_dt, int64_t ldk, cudaStream_t s);
 
 }  // namespace katz

@@ -28,7 +28,6 @@ namespace katz {
 namespace {
 
 constexpr int kBatch = 8;         // stored entries a consumer warp takes per wait
-constexpr int kFp32Row = 64;      // longest row summed in FP32 by later residual passes
 constexpr int kMaxThreads = 544;  // producer warp + at most 16 consumer warps
 constexpr int kBlockRows = 31;    // rows per block (row pointers fit one warp register)
 constexpr int64_t kBlockWeight = 512;  // stored entries + 4 per row, per block
@@ -37,9 +36,9 @@ constexpr int kMaxSlots = 256;
 constexpr int kSmemBudget = 220 * 1024;
 constexpr uint64_t kTimeoutNs = 2000000000ull;  // bound on every wait
 
-enum { kCheb2 = 0, kCheb3 = 1, kResInit = 2, kResUpd = 3 };
+enum { kCheb2 = 0, kCheb3 = 1, kResInit = 2 };
 __host__ __device__ constexpr int n_heads(int mode) {
-  return mode == kCheb2 ? 2 : mode == kCheb3 ? 3 : mode == kResInit ? 1 : 5;
+  return mode == kCheb2 ? 2 : mode == kCheb3 ? 3 : 1;
 }
 
 struct PipeArgs {
@@ -51,8 +50,8 @@ struct PipeArgs {
   int64_t ld;
   int tw, nslots, hstages, ngroups, nwg, chunk;
   const float* X;
-  const float* H[5];
-  float* O[4];
+  const float* H[3];
+  float* O[2];
   float beta, beh, bel, ak, ck, sx, sp;
   double* rr;
   int b;
@@ -422,10 +421,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pipe_kernel(const __grid_const
     uint32_t par = (P0 / uint32_t(S)) & 1u;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     FF af[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    // float-float sums for the first residual pass and long rows of later
-    // passes (whose gathered correction is of the residual's size, so FP32
-    // sums of short rows suffice); FP32 for the Chebyshev step
-    const bool ffsum = MODE == kResInit || (MODE == kResUpd && deg > kFp32Row);
+    // float-float sums for the residual pass, FP32 for the Chebyshev step
+    constexpr bool ffsum = RES;
     // entries in batches of up to kBatch: one vote over their barriers, the
     // shared-memory loads issued back to back, the slots released in parallel
     for (int t = 0; t < deg;) {
@@ -442,7 +439,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pipe_kernel(const __grid_const
         break;
       }
       if (cv) {
-        if (ffsum) {
+        if constexpr (ffsum) {
 #pragma unroll
           for (int u = 0; u < kBatch; ++u) {
             if (u < cnt) {
@@ -501,44 +498,21 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pipe_kernel(const __grid_const
       } else {
         const float4 xv = *reinterpret_cast<const float4*>(hb);
         const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
-        float rh[4], rl[4], rh0[4] = {0.f, 0.f, 0.f, 0.f}, rl0[4] = {0.f, 0.f, 0.f, 0.f};
-        float kh[4], kl[4];
-        if constexpr (MODE == kResUpd) {
-          const float4 a1 = *reinterpret_cast<const float4*>(hb + RS);
-          const float4 a2 = *reinterpret_cast<const float4*>(hb + 2 * RS);
-          const float4 a3 = *reinterpret_cast<const float4*>(hb + 3 * RS);
-          const float4 a4 = *reinterpret_cast<const float4*>(hb + 4 * RS);
-          rh0[0] = a1.x; rh0[1] = a1.y; rh0[2] = a1.z; rh0[3] = a1.w;
-          rl0[0] = a2.x; rl0[1] = a2.y; rl0[2] = a2.z; rl0[3] = a2.w;
-          kh[0] = a3.x; kh[1] = a3.y; kh[2] = a3.z; kh[3] = a3.w;
-          kl[0] = a4.x; kl[1] = a4.y; kl[2] = a4.z; kl[3] = a4.w;
-        }
+        float rh[4], rl[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-          if (!ffsum) af[t] = {acc[t], 0.f};
           // beta * acc as ph + pe
           const FF s = fast_two_sum(af[t].hi, af[t].lo);
           const float ph = a.beh * s.hi;
           const float pe = __fmaf_rn(a.beh, s.hi, -ph) + a.beh * s.lo + a.bel * s.hi;
           const FF t1 = two_sum(ph, -xs[t]);
-          const FF t2 = two_sum(t1.hi, rh0[t]);
-          const FF r = fast_two_sum(t2.hi, t1.lo + t2.lo + pe + rl0[t]);
+          const FF r = fast_two_sum(t1.hi, t1.lo + pe);
           rh[t] = r.hi;
           rl[t] = r.lo;
           sq[t] = __fmaf_rn(r.hi, r.hi, sq[t]);
-          if constexpr (MODE == kResUpd) {
-            const FF k1 = two_sum(kh[t], xs[t]);
-            const FF k2 = fast_two_sum(k1.hi, k1.lo + kl[t]);
-            kh[t] = k2.hi;
-            kl[t] = k2.lo;
-          }
         }
         *reinterpret_cast<float4*>(a.O[0] + o) = make_float4(rh[0], rh[1], rh[2], rh[3]);
         *reinterpret_cast<float4*>(a.O[1] + o) = make_float4(rl[0], rl[1], rl[2], rl[3]);
-        if constexpr (MODE == kResUpd) {
-          *reinterpret_cast<float4*>(a.O[2] + o) = make_float4(kh[0], kh[1], kh[2], kh[3]);
-          *reinterpret_cast<float4*>(a.O[3] + o) = make_float4(kl[0], kl[1], kl[2], kl[3]);
-        }
         if (++nsq == 64) {  // FP32 partial sums over at most 64 rows
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
@@ -697,39 +671,28 @@ void pipe_cheb_step(const Csr& A, const PipeSplit& ps, bool unit, double beta, d
 }
 
 void pipe_residual(const Csr& A, const PipeSplit& ps, bool unit, double beta, const float* X,
-                   float* Rh, float* Rl, float* Kh, float* Kl, bool init, int64_t ld, int b,
-                   double* rr, int* err, cudaStream_t s) {
-  KATZ_REQUIRE(ld % 4 == 0 && aligned16(X) && aligned16(Rh) && aligned16(Rl) &&
-                   (init || (aligned16(Kh) && aligned16(Kl))),
-               KATZ_EINVAL, "pipe_residual: operands must be 16-byte aligned");
+                   float* Rh, float* Rl, int64_t ld, int b, double* rr, int* err, cudaStream_t s) {
+  KATZ_REQUIRE(ld % 4 == 0 && aligned16(X) && aligned16(Rh) && aligned16(Rl), KATZ_EINVAL,
+               "pipe_residual: operands must be 16-byte aligned");
   if (A.nrows <= 0) return;
   PipeArgs a{};
   a.ld = ld;
   a.X = X;
   a.H[0] = X;
-  a.H[1] = Rh;
-  a.H[2] = Rl;
-  a.H[3] = Kh;
-  a.H[4] = Kl;
   a.O[0] = Rh;
   a.O[1] = Rl;
-  a.O[2] = Kh;
-  a.O[3] = Kl;
   a.beh = float(beta);
   a.bel = float(beta - double(a.beh));
   a.rr = rr;
   a.b = b;
   a.err = err;
   prof_begin(s);
-  if (init) pipe_launch<kResInit>(A, ps, unit, a, s);
-  else pipe_launch<kResUpd>(A, ps, unit, a, s);
-  if (profiling()) {
-    const double sv = 4.0 * ld;
+  pipe_launch<kResInit>(A, ps, unit, a, s);
+  if (profiling())
     prof_end("ff_residual",
              8.0 * (A.nrows + 1) + double(A.nnz) * (4 + (unit ? 0 : vdt_size(A.vdt))) +
-                 sv * A.ncols + sv * A.nrows * (init ? 3.0 : 9.0),
+                 4.0 * ld * (A.ncols + 3.0 * A.nrows),
              s);
-  }
 }
 
 }  // namespace katz

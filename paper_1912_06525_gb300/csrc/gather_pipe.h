@@ -1,5 +1,5 @@
 // Pipelined row-gather kernels for the wide sparse products of the query
-// path (the large-block Chebyshev step and the refinement residual).
+// path (the large-block Chebyshev step and the first refinement residual).
 //
 // One CTA per SM takes row blocks (<= 31 rows, ~512 stored entries) in
 // increasing order from a global counter.  A producer warp streams, with
@@ -40,13 +40,11 @@ void pipe_cheb_step(const Csr& A, const PipeSplit& ps, bool unit, double beta, d
                     double ck, const float* Xk, const float* Xprev, const float* B, float* Xout,
                     int64_t ld, int* err, cudaStream_t s, double sx = 1.0, double sp = 1.0);
 
-// Refinement residual in float-float arithmetic with one gathered FP32
-// operand X (M = I - beta A):
-//   init   : (Rh, Rl) = -X + beta A X
-//   update : (Rh, Rl) += -X + beta A X  and  (Kh, Kl) += X
-// and rr[c] += sum_i Rh[i][c]^2 for the columns c < b (the caller zeroes rr).
+// First refinement-residual pass in float-float arithmetic with the
+// gathered FP32 operand X (M = I - beta A): (Rh, Rl) = -X + beta A X, and
+// rr[c] += sum_i Rh[i][c]^2 for the columns c < b when rr is non-null (the
+// caller zeroes rr).
 void pipe_residual(const Csr& A, const PipeSplit& ps, bool unit, double beta, const float* X,
-                   float* Rh, float* Rl, float* Kh, float* Kl, bool init, int64_t ld, int b,
-                   double* rr, int* err, cudaStream_t s);
+                   float* Rh, float* Rl, int64_t ld, int b, double* rr, int* err, cudaStream_t s);
 
 }  // namespace katz

@@ -531,6 +531,14 @@ static void residual64(katz_index& idx, bool use_lrc, const int32_t* q, int b, i
   coldot<double>(R64, ld, R64, ld, idx.n, b, rr, s);
 }
 
+// Tolerance the solve must meet so that the returned K meets o.tol: an
+// infinity-norm error bound loses up to 2^-24 (1 + tol) more to the final
+// rounding to FP32 output.
+static double solve_tol(const katz_query_opts& o, const QueryOut& out) {
+  if (o.tol_kind != KATZ_TOL_ERROR_INF || out.dtype != KATZ_F32) return o.tol;
+  return std::max(0.5 * o.tol, o.tol - std::ldexp(1.0 + o.tol, -24));
+}
+
 // Mixed-precision query for graphs whose weights are exact in FP32: FP32
 // solves, the solution kept as a float-float pair (Kh, Kl) and the residual
 // as (Rh, Rl), both updated by one pass per refinement step that gathers the
@@ -567,7 +575,7 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   int* perr = ws.get<int>("pipe.err", 1);
   rhs_norms(idx.W.view(), q, b, idx.beta, bn2, bmx, s);
   const double omc = std::max(1e-300, 1.0 - idx.beta * idx.lambda);
-  make_thresholds(bn2, bmx, b, o.tol, o.tol_kind, omc, thr2, s);
+  make_thresholds(bn2, bmx, b, solve_tol(o, out), o.tol_kind, omc, thr2, s);
   const double tau = 2e-6;
   double tol_rel = (o.tol_kind == KATZ_TOL_RESIDUAL) ? o.tol : o.tol * omc;
   tol_rel = std::max(tol_rel * 0.3, tau);
@@ -597,25 +605,29 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   const auto t2 = clk::now();
   double ms_res = 0;
   int refine = 0;
+  bool pending = false;  // D holds a correction not yet added to K
   if (status == KATZ_OK || status == KATZ_ENOCONV) {
     for (;;) {
       const auto r0 = clk::now();
       KATZ_CUDA(cudaMemsetAsync(rr, 0, sizeof(double) * bpad(b), s));
-      // R = b - M K0 (K0 = Kh, Kl = 0) on the first pass, then R -= M D, K += D.
-      // The first pass adds the sparse b after the sweep, so its norms are
-      // taken afterwards (summing squares before and correcting by
-      // b_i^2 - r_i^2 would cancel catastrophically); later passes fuse them.
-      const bool first = refine == 0;
-      const float* Xg = first ? Kh : D;
-      double* rr_fused = first ? nullptr : rr;
-      if (pipe_ok && use_pipe(idx, gcfg, first))
-        pipe_residual(G.view(), G.ps, idx.unit_weights, idx.beta, Xg, Rh, Rl, Kh, Kl, first, ld,
-                      b, rr_fused, perr, s);
-      else
-        ffr_update(G.view(), idx.beta, Xg, Rh, Rl, Kh, Kl, first, ld, b, rr_fused, gcfg, s);
-      if (first) {
+      // R = b - M K0 (K0 = Kh, Kl = 0) on the first pass, then R -= M D for
+      // each correction D, which joins K (K += D) only when another correction
+      // is about to overwrite D, else in the output.  The first pass adds the
+      // sparse b after the sweep, so its norms are taken afterwards (summing
+      // squares before and correcting by b_i^2 - r_i^2 would cancel
+      // catastrophically); later passes fuse them.
+      if (refine == 0) {
+        if (pipe_ok && use_pipe(idx, gcfg, true))
+          pipe_residual(G.view(), G.ps, idx.unit_weights, idx.beta, Kh, Rh, Rl, ld, b, nullptr,
+                        perr, s);
+        else
+          ffr_update(G.view(), idx.beta, Kh, Rh, Rl, true, ld, b, nullptr, gcfg, s);
         ffr_add_rhs(idx.W.view(), q, pos, b, idx.beta, Rh, Rl, ld, nullptr, maxdeg, s);
         coldot<float>(Rh, ld, Rh, ld, n, b, rr, s);
+      } else {
+        // Rl carries the first pass's low part into the first update only
+        ffr_update(G.view(), idx.beta, D, Rh, refine == 1 ? Rl : nullptr, false, ld, b, rr, gcfg,
+                   s);
       }
       inner_thresholds_kernel<<<1, 1024, 0, s>>>(rr, thr2, tau, b, conv, thr2_in, nopen);
       KATZ_CHECK_LAUNCH();
@@ -638,16 +650,18 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
           if (hr[c] > ht[c] && hr[c] > 0) tol_step = std::min(tol_step, 0.3 * std::sqrt(ht[c] / hr[c]));
         tol_step = std::max(tol_step, tau);
       }
+      if (pending) ff_add(Kh, Kl, D, n * ld, s);  // D is about to be overwritten
       const int st = inner_solve<float>(idx, use_lrc, Rh, D, b, ld, thr2_in, tol_step, max_iter,
                                         &iters, s);
-      if (st == KATZ_ENOTSPD) { status = st; break; }
+      if (st == KATZ_ENOTSPD) { pending = false; status = st; break; }
+      pending = true;
     }
     std::vector<double> hr(b), hb(b);
     KATZ_CUDA(cudaMemcpyAsync(hr.data(), rr, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
     KATZ_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
     KATZ_CUDA(cudaStreamSynchronize(s));
     for (int c = 0; c < b; ++c) relres[c] = hb[c] > 0 ? std::sqrt(hr[c] / hb[c]) : std::sqrt(hr[c]);
-    ff_out(Kh, Kl, ld, pos, n, b, out.K, out.dtype, out.ldk, s);
+    ff_out(Kh, Kl, pending ? D : nullptr, ld, pos, n, b, out.K, out.dtype, out.ldk, s);
     KATZ_CUDA(cudaStreamSynchronize(s));
   }
   const auto t3 = clk::now();
@@ -699,7 +713,7 @@ static int query_impl(katz_index& idx, bool use_lrc, const int32_t* q, int b,
   int* nopen = ws.get<int>("q.nopen", 1);
   rhs_norms(idx.W.view(), q, b, idx.beta, bn2, bmx, s);
   const double omc = std::max(1e-300, 1.0 - idx.beta * idx.lambda);
-  make_thresholds(bn2, bmx, b, o.tol, o.tol_kind, omc, thr2, s);
+  make_thresholds(bn2, bmx, b, solve_tol(o, out), o.tol_kind, omc, thr2, s);
   // inner solves aim below the outer target but not below what the inner
   // precision can deliver
   const double tau = (sizeof(VT) == 4) ? 2e-6 : 1e-13;
