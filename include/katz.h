@@ -99,6 +99,11 @@ typedef struct {
   int32_t lanczos_steps; /* Lanczos steps on R; 0 = max(2r, r+20) */
   int32_t n2_max;        /* largest separator accepted (dense S and M22^{-1}); 0 = 16384 */
   uint64_t seed;         /* SplitMix64 seed of the Lanczos start vector */
+  int32_t coupling_gemm; /* store beta*M11^{-1} W12 (n1 x n2, TF32 hi/lo parts) so that LRC
+                            queries form K1 = Y1 + beta M11^{-1} W12 K2 (Eq. 6) on the tensor
+                            cores instead of a second M11 solve when that is cheaper:
+                            0 = when it fits in a third of device memory, 1 = always,
+                            -1 = never */
 } katz_build_opts;
 
 typedef struct {
@@ -261,6 +266,17 @@ int katz_autotune(katz_index* idx, int32_t b, int32_t* out, double* ms, void* st
  * reported a timeout. */
 int katz_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int32_t M, int32_t N,
                    int32_t K, float alpha, float beta, float* C, int64_t ldc, void* stream);
+
+/* FP32-accurate tensor-core product C = alpha * A B^T + beta * C from three
+ * TF32 tcgen05 products of the TF32 high/low parts of A and B (the kernel of
+ * the coupling product K1 = Y1 + beta M11^{-1} W12 K2), exposed for
+ * step-level testing.  A (M x K), B (N x K), C (M x N): device FP32
+ * row-major, row strides lda/ldb multiples of 4 elements, 16-byte aligned.
+ * Errors: KATZ_EINVAL on bad shapes/alignment, KATZ_ENOMEM, KATZ_ECUDA if
+ * the pipeline reported a timeout. */
+int katz_gemm_tf32x3(const float* A, int64_t lda, const float* B, int64_t ldb, int32_t M,
+                     int32_t N, int32_t K, float alpha, float beta, float* C, int64_t ldc,
+                     void* stream);
 
 /* ------------------------------------------------- learned warm start */
 

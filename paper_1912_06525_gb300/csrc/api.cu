@@ -480,6 +480,33 @@ int katz_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int32
   });
 }
 
+int katz_gemm_tf32x3(const float* A, int64_t lda, const float* B, int64_t ldb, int32_t M,
+                     int32_t N, int32_t K, float alpha, float beta, float* C, int64_t ldc,
+                     void* stream) {
+  return guarded([&]() {
+    KATZ_REQUIRE(A && B && C && M > 0 && N > 0 && K > 0, KATZ_EINVAL, "bad GEMM arguments");
+    KATZ_REQUIRE(lda >= K && ldb >= K && ldc >= N && lda % 4 == 0 && ldb % 4 == 0, KATZ_EINVAL,
+                 "GEMM strides: lda, ldb >= K and multiples of 4; ldc >= N");
+    KATZ_REQUIRE(is_device_ptr(A) && is_device_ptr(B) && is_device_ptr(C), KATZ_EINVAL,
+                 "GEMM operands must be device memory");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t ldk = (int64_t(K) + 3) / 4 * 4;
+    katz::DBuf<float> Ah(size_t(M) * ldk), Al(size_t(M) * ldk), Bh(size_t(N) * ldk),
+        Bl(size_t(N) * ldk);
+    katz::split_tf32<float>(A, lda, M, K, Ah.p, Al.p, ldk, s);
+    katz::split_tf32<float>(B, ldb, N, K, Bh.p, Bl.p, ldk, s);
+    katz::DBuf<int> err(1);
+    KATZ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    katz::tc_gemm_tf32x3(Ah.p, Al.p, ldk, Bh.p, Bl.p, ldk, M, N, K, alpha, beta, C, ldc, C, ldc,
+                         err.p, s);
+    int h = 0;
+    KATZ_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KATZ_CUDA(cudaStreamSynchronize(s));
+    KATZ_REQUIRE(h == 0, KATZ_ECUDA, "tcgen05 GEMM pipeline timed out");
+    return KATZ_OK;
+  });
+}
+
 int katz_apply_M(const katz_index* cidx, const void* X, void* Y, int32_t b, int32_t dtype,
                  void* stream) {
   return guarded([&]() {

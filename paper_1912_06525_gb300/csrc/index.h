@@ -84,6 +84,11 @@ struct katz_index {
   katz::DBuf<float> Wr32u;
   int64_t ldr4 = 0;
   katz::GraphPart W22;
+  // beta * M11^{-1} W12 (n1 x n2, row stride ldH) as TF32 high/low parts for
+  // the tensor-core back-substitution K1 = Y1 + beta M11^{-1} W12 K2 (Eq. 6)
+  katz::DBuf<float> Hh, Hl;
+  int64_t ldH = 0;
+  bool has_h = false;
   katz::Mlp mlp;
   katz::DBuf<float> feat;  // n x 32 node features
   std::vector<double> sigma;

@@ -11,6 +11,7 @@
 #include <thread>
 
 #include "index.h"
+#include "tc_gemm.h"
 #include "kernels_dense.h"
 
 namespace katz {
@@ -551,6 +552,22 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
     const int64_t ldc = (cw_max + 3) / 4 * 4;
     DBuf<double> E(size_t(n2) * ldc), U(size_t(std::max<int64_t>(n1, 1)) * ldc),
         V(size_t(std::max<int64_t>(n1, 1)) * ldc);
+    // V = beta M11^{-1} W12 by column chunks; kept (TF32 parts) for the
+    // tensor-core back-substitution where the large M11 blocks are solved
+    // iteratively and the two n1 x n2 FP32 arrays fit
+    idx.ldH = (n2 + 3) / 4 * 4;
+    {
+      size_t free_b = 0, total_b = 0;
+      KATZ_CUDA(cudaMemGetInfo(&free_b, &total_b));
+      const double bytes = 2.0 * 4.0 * double(n1) * double(idx.ldH);
+      idx.has_h = n1 > 0 && (o.coupling_gemm > 0 ||
+                             (o.coupling_gemm == 0 && idx.n1 > idx.n1s && idx.lam11 > 1e-100 &&
+                              bytes <= double(total_b) / 3.0 && bytes <= 0.8 * double(free_b)));
+    }
+    if (idx.has_h) {
+      idx.Hh.alloc(size_t(n1) * idx.ldH);
+      idx.Hl.alloc(size_t(n1) * idx.ldH);
+    }
     for (int64_t j0 = 0; j0 < n2; j0 += cw_max) {
       const int cw = (int)std::min<int64_t>(cw_max, n2 - j0);
       if (n1 == 0) break;
@@ -562,6 +579,8 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
                    ldc, U.p, ldc, cw, nullptr, 0, nullptr, s);
       const int st = m11_solve<double>(idx, U.p, V.p, cw, ldc, 1e-14, 5000, nullptr, s);
       KATZ_REQUIRE(st != KATZ_ENOTSPD, KATZ_ENOTSPD, "M11 is not positive definite");
+      if (idx.has_h)
+        split_tf32<double>(V.p, ldc, n1, cw, idx.Hh.p + j0, idx.Hl.p + j0, idx.ldH, s);
       spmm<double>(idx.W21.view(), idx.W21.heavy.p, idx.W21.n_heavy, beta, V.p, ldc, 0.0, nullptr,
                    ldc, T.p + j0, ld2, cw, nullptr, 0, nullptr, s);
     }

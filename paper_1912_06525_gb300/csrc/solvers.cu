@@ -432,6 +432,26 @@ int pcg_schur(katz_index& idx, const VT* F, VT* K2, int b, int64_t ld, const dou
   return active > 0 ? KATZ_ENOCONV : KATZ_OK;
 }
 
+// Chebyshev steps the large M11 blocks need for relative tolerance tol.
+static int cheb_steps(const katz_index& idx, double tol) {
+  const double lo = 1.0 - idx.beta * idx.lam11, hi = 1.0 - idx.beta * idx.lam11_min;
+  const double kappa = hi / lo;
+  const double cf = (std::sqrt(kappa) - 1.0) / (std::sqrt(kappa) + 1.0);
+  return cf <= 0 ? 1 : std::max(1, int(std::ceil(std::log(tol / 2.0) / std::log(cf))));
+}
+
+// Whether the back-substitution K1 = M11^{-1}(R1 + beta W12 K2) is cheaper as
+// K1 = Y1 + (beta M11^{-1} W12) K2 on the tensor cores: the second M11 solve
+// gathers ~4 ld bytes per stored entry of the large blocks per Chebyshev step
+// (at ~10 TB/s from L2), the product costs 6 n1 n2 ld flops (three TF32
+// products at ~0.8 PFLOP/s).
+static bool coupling_gemm_pays(const katz_index& idx, int64_t ld, double tol) {
+  if (!idx.has_h || idx.n1 <= idx.n1s || idx.lam11 <= 0) return false;
+  const double t_solve = cheb_steps(idx, tol) * double(idx.W11L.csr.nnz) * 4.0 * ld / 1.0e13;
+  const double t_gemm = 6.0 * double(idx.n1) * double(idx.n2) * ld / 0.8e15;
+  return t_gemm < t_solve;
+}
+
 // --------------------------------------------------------- LRC solve
 // D = M^{-1} Rin for n x b blocks in index order (Lemma 1):
 //   Y1 = M11^{-1} R1;  F = R2 - M12^T Y1 = R2 + beta W21 Y1   (Eq. 7)
@@ -462,6 +482,20 @@ int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double t
     merge(pcg_schur<VT>(idx, F, D2, b, ld, thr2, max_iter, iters, s, K2_0));
   }
   if (n1 > 0) {
+    if constexpr (sizeof(VT) == 4) {
+      if (n2 > 0 && coupling_gemm_pays(idx, ld, tol_l)) {
+        // K1 = Y1 + (beta M11^{-1} W12) K2 on the tensor cores (all ld columns,
+        // so the zero padding columns stay zero)
+        float* Bh = idx.ws.get<float>("lrc.K2h", size_t(ld) * idx.ldH);
+        float* Bl = idx.ws.get<float>("lrc.K2l", size_t(ld) * idx.ldH);
+        split_tf32_transposed(reinterpret_cast<const float*>(D2), ld, n2, int(ld), Bh, Bl,
+                              idx.ldH, s);
+        tc_gemm_tf32x3(idx.Hh.p, idx.Hl.p, idx.ldH, Bh, Bl, idx.ldH, int(n1), int(ld), int(n2),
+                       1.f, 1.f, reinterpret_cast<const float*>(Y1), ld,
+                       reinterpret_cast<float*>(D1), ld, idx.ws.get<int>("pipe.err", 1), s);
+        return status;
+      }
+    }
     const VT* T1 = R1;
     if (n2 > 0) {
       spmm<VT>(idx.W12.view(), idx.W12.heavy.p, idx.W12.n_heavy, idx.beta, D2, ld, 1.0, R1, ld, Y1,

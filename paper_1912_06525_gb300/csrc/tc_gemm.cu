@@ -15,69 +15,16 @@
 
 #include "kernels.h"
 #include "tc_gemm.h"
+#include "tc_util.cuh"
 
 namespace katz {
 
 namespace {
 
+using namespace tcu;
+
 constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
 constexpr int TILE_A = BM * BK * 2, TILE_B = BN * BK * 2;  // bytes per stage
-constexpr uint32_t kSpinLimit = 1u << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-// Bounded wait for the phase with parity `phase`; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
-  const uint32_t a = smem_u32(bar);
-  for (uint32_t it = 0; it < kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(phase)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major, 128-byte swizzled tile:
-// start address >> 4 (bits 0-13), leading byte offset 16 B (unused for this
-// layout, bits 16-29), stride byte offset 1024 B between 8-row groups
-// (bits 32-45), descriptor version 1 (bits 46-47), swizzle mode 2 =
-// 128-byte (bits 61-63).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  uint64_t d = 0;
-  d |= uint64_t((addr >> 4) & 0x3FFF);
-  d |= uint64_t(1) << 16;
-  d |= uint64_t(1024 >> 4) << 32;
-  d |= uint64_t(1) << 46;
-  d |= uint64_t(2) << 61;
-  return d;
-}
-
 // Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and
 // B BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
 // N >> 3 at bits 17-22, M >> 4 at bits 24-28.
@@ -231,44 +178,6 @@ __global__ void to_bf16_transposed_kernel(const float* X, int64_t ldx, int64_t r
   }
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    KATZ_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                               cudaEnableDefault, &q));
-    KATZ_REQUIRE(p != nullptr && q == cudaDriverEntryPointSuccess, KATZ_ECUDA,
-                 "cuTensorMapEncodeTiled unavailable");
-    fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
-}
-
-// 2D BF16 tensor map: rows x K (K contiguous, row stride ld elements),
-// box = box_rows x 64, 128-byte swizzle, zero fill out of bounds.
-CUtensorMap make_map(const __nv_bfloat16* ptr, int64_t rows, int64_t K, int64_t ld, int box_rows) {
-  KATZ_REQUIRE(reinterpret_cast<uintptr_t>(ptr) % 16 == 0 && (ld * 2) % 16 == 0, KATZ_EINVAL,
-               "tc_gemm: operands need 16-byte aligned base and row stride");
-  CUtensorMap m;
-  const cuuint64_t dims[2] = {cuuint64_t(K), cuuint64_t(rows)};
-  const cuuint64_t strides[1] = {cuuint64_t(ld * 2)};
-  const cuuint32_t box[2] = {cuuint32_t(BK), cuuint32_t(box_rows)};
-  const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                                 const_cast<__nv_bfloat16*>(ptr), dims, strides, box, estr,
-                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  KATZ_REQUIRE(r == CUDA_SUCCESS, KATZ_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
-  return m;
-}
-
 }  // namespace
 
 size_t tc_gemm_smem_bytes() { return size_t(STAGES) * (TILE_A + TILE_B) + 1024 + 256; }
@@ -277,8 +186,8 @@ void tc_gemm(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_
              int N, int K, float alpha, float beta, float* C, int64_t ldc, __nv_bfloat16* Ct,
              int64_t ldct, int mode, int* err, cudaStream_t s) {
   if (M <= 0 || N <= 0 || K <= 0) return;
-  const CUtensorMap ma = make_map(A, M, K, lda, BM);
-  const CUtensorMap mb = make_map(B, N, K, ldb, BN);
+  const CUtensorMap ma = tcu::make_map(A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, M, K, lda, BM);
+  const CUtensorMap mb = tcu::make_map(B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, N, K, ldb, BN);
   const size_t smem = tc_gemm_smem_bytes();
   static bool attr = false;
   if (!attr) {

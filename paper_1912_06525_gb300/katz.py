@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "KATZ_OK", 1: "KATZ_EINVAL", 2: "KATZ_ENOTSPD", 3: "KATZ_ENOC
 # every exported symbol of include/katz.h
 EXPORTS = ["katz_lambda_max", "katz_index_build", "katz_index_free", "katz_index_get_info",
            "katz_index_get_partition", "katz_partition", "katz_index_get_sigma", "katz_query_batch",
-           "cg_query_batch", "linkpred_topk", "linkpred_topk_noalloc", "katz_apply_M", "katz_autotune", "katz_gemm_bf16", "katz_launch_count",
+           "cg_query_batch", "linkpred_topk", "linkpred_topk_noalloc", "katz_apply_M", "katz_autotune", "katz_gemm_bf16", "katz_gemm_tf32x3", "katz_launch_count",
            "katz_profile_enable", "katz_profile_read", "katz_multi_build", "katz_multi_free",
            "katz_multi_query", "katz_warmstart_train", "katz_mlp_loss_grad", "katz_last_error"]
 
@@ -48,7 +48,8 @@ class katz_csr(C.Structure):
 class katz_build_opts(C.Structure):
     _fields_ = [("value_dtype", C.c_int32), ("build_lrc", C.c_int32), ("rank", C.c_int32),
                 ("n_hubs", C.c_int32), ("block_max", C.c_int32), ("split", C.c_int32),
-                ("lanczos_steps", C.c_int32), ("n2_max", C.c_int32), ("seed", C.c_uint64)]
+                ("lanczos_steps", C.c_int32), ("n2_max", C.c_int32), ("seed", C.c_uint64),
+                ("coupling_gemm", C.c_int32)]
 
 
 class katz_query_opts(C.Structure):
@@ -110,6 +111,8 @@ def lib() -> C.CDLL:
         L.katz_autotune.argtypes = [vp, i32, vp, vp, vp]
         L.katz_gemm_bf16.argtypes = [vp, i64, vp, i64, i32, i32, i32, C.c_float, C.c_float, vp,
                                      i64, vp]
+        L.katz_gemm_tf32x3.argtypes = [vp, i64, vp, i64, i32, i32, i32, C.c_float, C.c_float,
+                                       vp, i64, vp]
         L.katz_multi_build.argtypes = [i32, vp, vp, i32, vp, C.POINTER(vp)]
         L.katz_multi_free.argtypes = [vp]
         L.katz_multi_free.restype = None
@@ -209,10 +212,10 @@ class KatzIndex:
 def katz_index_build(graph, beta: float, value_dtype: int = KATZ_F32, build_lrc: bool = True,
                      rank: int = 16, n_hubs: int = 0, block_max: int = 64, split: bool = True,
                      lanczos_steps: int = 0, n2_max: int = 0, seed: int = 20191212,
-                     stream=None) -> KatzIndex:
+                     coupling_gemm: int = 0, stream=None) -> KatzIndex:
     c, keep = _csr(graph)
     o = katz_build_opts(value_dtype, int(build_lrc), rank, n_hubs, block_max, int(split),
-                        lanczos_steps, n2_max, seed)
+                        lanczos_steps, n2_max, seed, coupling_gemm)
     h = C.c_void_p()
     _check(lib().katz_index_build(C.byref(c), float(beta), C.byref(o), _stream(stream),
                                   C.byref(h)))
@@ -332,6 +335,16 @@ def katz_gemm_bf16(A, B, C_out, K=None, alpha=1.0, beta=0.0, stream=None):
     N = B.shape[0]
     _check(lib().katz_gemm_bf16(_ptr(A), _ld(A), _ptr(B), _ld(B), M, N, K, alpha, beta,
                                 _ptr(C_out), _ld(C_out), _stream(stream)))
+
+
+def katz_gemm_tf32x3(A, B, C_out, K=None, alpha=1.0, beta=0.0, stream=None):
+    """C_out = alpha * A[:, :K] @ B[:, :K].T + beta * C_out, FP32-accurate on the
+    tensor cores (three TF32 products); A: M x ld, B: N x ld, C_out: M x N float32."""
+    M = A.shape[0]
+    K = A.shape[1] if K is None else K
+    N = B.shape[0]
+    _check(lib().katz_gemm_tf32x3(_ptr(A), _ld(A), _ptr(B), _ld(B), M, N, K, alpha, beta,
+                                  _ptr(C_out), _ld(C_out), _stream(stream)))
 
 
 def katz_autotune(index, b: int, stream=None) -> dict:

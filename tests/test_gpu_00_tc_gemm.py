@@ -48,3 +48,30 @@ def test_tc_gemm_rejects_bad_strides():
     C = torch.zeros((16, 16), dtype=torch.float32, device="cuda")
     with pytest.raises(katz.KatzError):
         katz.katz_gemm_bf16(A, A, C)
+
+
+def fp32_matrix(rows, K, seed, ld=None):
+    ld = ld or (K + 3) // 4 * 4
+    g = torch.Generator().manual_seed(seed)
+    X = torch.zeros((rows, ld), dtype=torch.float32)
+    X[:, :K] = torch.randn((rows, K), generator=g) * torch.exp(torch.randn((rows, 1), generator=g))
+    return X.cuda()
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 32), (200, 72, 150), (1000, 1024, 2000),
+                                   (4097, 264, 37), (1, 16, 4), (333, 257, 777)])
+def test_tc_gemm_tf32x3_is_fp32_accurate(M, N, K):
+    """Three TF32 products of the split operands against an FP64 product:
+    the error stays within FP32 accumulation bounds, |err| <= (K + 8) 2^-23
+    sum_k |a_ik||b_jk| (a single TF32 product would be ~2^-11)."""
+    A = fp32_matrix(M, K, 1)
+    B = fp32_matrix(N, K, 2)
+    C = torch.randn((M, N), dtype=torch.float32, device="cuda")
+    C0 = C.clone()
+    katz.katz_gemm_tf32x3(A, B, C, K=K, alpha=0.75, beta=-1.5)
+    torch.cuda.synchronize()
+    Ad, Bd = A[:, :K].double(), B[:, :K].double()
+    ref = 0.75 * (Ad @ Bd.T) - 1.5 * C0.double()
+    bound = (K + 8) * 2.0 ** -23 * (0.75 * (Ad.abs() @ Bd.abs().T)) + 2.0 ** -22 * 1.5 * C0.double().abs()
+    err = (C.double() - ref).abs()
+    assert torch.all(err <= bound + 1e-30), float((err / (bound + 1e-30)).max())

@@ -72,3 +72,23 @@ def test_autotune_reports_kernel_choice():
     K = torch.zeros((g.n, 256), dtype=torch.float32, device="cuda")
     st, _, _ = katz.katz_query_batch(idx, torch.from_numpy(q).cuda(), K, tol=1e-6)
     assert st["status"] == "KATZ_OK"
+
+
+@pytest.mark.parametrize("coupling", [-1, 1])
+def test_coupling_product_paths_match_oracle(coupling):
+    """Back-substitution by a second M11 solve (coupling_gemm=-1) or by the
+    stored beta M11^{-1} W12 on the tensor cores (coupling_gemm=1)."""
+    g = graph(weighted=True)
+    W = O.adjacency(g.n, g.rowptr, g.col, g.val)
+    beta = 0.85 / O.lambda_max(W)
+    idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_F32, rank=16, n_hubs=30,
+                                block_max=32, split=False, coupling_gemm=coupling)
+    q = synth.queries(g.n, 200, seed=4)
+    ref = O.katz_direct(W, beta, q)
+    for prec in (katz.KATZ_PREC_MIXED, katz.KATZ_PREC_F32):
+        K = torch.zeros((g.n, len(q)), dtype=torch.float64, device="cuda")
+        st, it, rel = katz.katz_query_batch(idx, torch.from_numpy(q).cuda(), K,
+                                            out_dtype=katz.KATZ_F64, tol=1e-6, precision=prec)
+        assert st["status"] == "KATZ_OK"
+        bound = 1e-6 if prec == katz.KATZ_PREC_MIXED else 1e-4
+        assert O.error_inf_rel(K.cpu().numpy(), ref).max() <= bound
