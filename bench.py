@@ -170,6 +170,22 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# dense TF32 tensor rate relative to BF16 (nominal 1.1 vs 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
+# profiler tags whose algorithmic count is flops, not bytes
+FLOP_TAGS = ("tc_gemm_tf32x3",)
+
+
+def tf32_peak():
+    """TF32 dense peak in TFLOP/s: the measured BF16 burst rate times the
+    nominal TF32/BF16 ratio, else the fallback BF16 rate times that ratio."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["bf16_tflops"]) * TF32_PER_BF16, "measured bf16 x nominal tf32/bf16"
+    return 1900.0 * TF32_PER_BF16, "fallback bf16 x nominal tf32/bf16"
+
+
 def kernel_hash():
     h = hashlib.sha256()
     for f in ("kernels_vec.cu", "kernels.h", "common.cuh"):
@@ -297,8 +313,8 @@ def main():
     barrier(world)
     launches = katz.katz_launch_count() - l0
     prof = {t: katz.katz_profile_read(t) for t in
-            ("spmm_f32", "spmm_f64", "cheb_step", "ff_residual", "fx_residual",
-             "block_solve_f32", "gemm_f32", "tc_gemm")}
+            ("spmm_f32", "spmm_f64", "cheb_step", "ff_residual", "block_solve_f32",
+             "gemm_f32", "tc_gemm", "tc_gemm_tf32x3")}
     katz.katz_profile_enable(False)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
@@ -356,14 +372,22 @@ def main():
     dom = max(shares, key=shares.get) if shares else "spmm_f32"
     p = prof[dom]
     ach = p["bytes"] / (p["ms"] / 1e3) / 1e9 if p["ms"] else 0.0
-    roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-            "frac": ach / hbm, "peak_source": f"{src} (hbm_gbs)",
-            "traffic": NCU_TRAFFIC.get((dom, kernel_hash())),
-            "launches_per_step": p["launches"] / args.steps,
-            "alg_bytes_per_launch": p["bytes"] / max(1, p["launches"]),
-            "share_of_step": p["ms"] / (ms * args.steps)}
+    if dom in FLOP_TAGS:
+        tpk, tsrc = tf32_peak()
+        ach = p["bytes"] / (p["ms"] / 1e3) / 1e12 if p["ms"] else 0.0
+        roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": tpk, "unit": "TFLOP/s",
+                "frac": ach / tpk, "peak_source": tsrc, "traffic": None}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "peak_source": f"{src} (hbm_gbs)",
+                "traffic": NCU_TRAFFIC.get((dom, kernel_hash()))}
+    roof.update({"launches_per_step": p["launches"] / args.steps,
+                 "alg_units_per_launch": p["bytes"] / max(1, p["launches"]),
+                 "share_of_step": p["ms"] / (ms * args.steps)})
     kernels = {t: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
-                   "gbs": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] else None}
+                   ("tflops" if t in FLOP_TAGS else "gbs"):
+                       v["bytes"] / (v["ms"] / 1e3) / (1e12 if t in FLOP_TAGS else 1e9)
+                       if v["ms"] else None}
                for t, v in prof.items() if v["launches"]}
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1)

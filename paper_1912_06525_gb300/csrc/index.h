@@ -158,6 +158,12 @@ double warmstart_train(katz_index& idx, const int32_t* q_host, int n_train, int 
 void warm_start_guess(katz_index& idx, const int32_t* q, int b, float* K20, int64_t ld,
                       cudaStream_t s);
 
+// Chebyshev steps of the large M11 blocks for relative tolerance tol, and
+// whether the tensor-core back-substitution is cheaper than the second M11
+// solve at width ld and that tolerance (cost model).
+int cheb_steps(const katz_index& idx, double tol);
+bool coupling_gemm_pays(const katz_index& idx, int64_t ld, double tol);
+
 struct TuneResult {
   int col_tile = 0, ctas_per_sm = 0, rhs_width = 0;
   bool cheb_pipe = false;  // the pipelined Chebyshev step was faster on the large block

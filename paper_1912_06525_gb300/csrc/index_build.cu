@@ -560,8 +560,10 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
       size_t free_b = 0, total_b = 0;
       KATZ_CUDA(cudaMemGetInfo(&free_b, &total_b));
       const double bytes = 2.0 * 4.0 * double(n1) * double(idx.ldH);
+      // automatic: where the cost model favours the product at the FP32
+      // inner tolerance (2e-6) and the parts fit
       idx.has_h = n1 > 0 && (o.coupling_gemm > 0 ||
-                             (o.coupling_gemm == 0 && idx.n1 > idx.n1s && idx.lam11 > 1e-100 &&
+                             (o.coupling_gemm == 0 && coupling_gemm_pays(idx, 1024, 2e-6) &&
                               bytes <= double(total_b) / 3.0 && bytes <= 0.8 * double(free_b)));
     }
     if (idx.has_h) {

@@ -245,9 +245,7 @@ static void m11_chebyshev(katz_index& idx, const float* X, float* Y, int b, int6
   const int64_t len = idx.n1 - idx.n1s;
   const double lo = 1.0 - idx.beta * idx.lam11, hi = 1.0 - idx.beta * idx.lam11_min;
   const double theta = 0.5 * (lo + hi), d = 0.5 * (hi - lo);
-  const double kappa = hi / lo;
-  const double cf = (std::sqrt(kappa) - 1.0) / (std::sqrt(kappa) + 1.0);
-  const int K = cf <= 0 ? 1 : std::max(1, int(std::ceil(std::log(tol / 2.0) / std::log(cf))));
+  const int K = cheb_steps(idx, tol);
   if (K == 1) {
     scale_copy<float>(X, ld, Y, ld, len, int(ld), 1.0 / theta, false, s);
     return;
@@ -433,7 +431,7 @@ int pcg_schur(katz_index& idx, const VT* F, VT* K2, int b, int64_t ld, const dou
 }
 
 // Chebyshev steps the large M11 blocks need for relative tolerance tol.
-static int cheb_steps(const katz_index& idx, double tol) {
+int cheb_steps(const katz_index& idx, double tol) {
   const double lo = 1.0 - idx.beta * idx.lam11, hi = 1.0 - idx.beta * idx.lam11_min;
   const double kappa = hi / lo;
   const double cf = (std::sqrt(kappa) - 1.0) / (std::sqrt(kappa) + 1.0);
@@ -443,12 +441,13 @@ static int cheb_steps(const katz_index& idx, double tol) {
 // Whether the back-substitution K1 = M11^{-1}(R1 + beta W12 K2) is cheaper as
 // K1 = Y1 + (beta M11^{-1} W12) K2 on the tensor cores: the second M11 solve
 // gathers ~4 ld bytes per stored entry of the large blocks per Chebyshev step
-// (at ~10 TB/s from L2), the product costs 6 n1 n2 ld flops (three TF32
-// products at ~0.8 PFLOP/s).
-static bool coupling_gemm_pays(const katz_index& idx, int64_t ld, double tol) {
-  if (!idx.has_h || idx.n1 <= idx.n1s || idx.lam11 <= 0) return false;
+// (~10 TB/s from L2); the product costs 6 n1 n2 ld flops at the ~0.25
+// PFLOP/s measured for the three-TF32 GEMM with 128 x 128 tiles (bound by
+// streaming both split operands through L2).
+bool coupling_gemm_pays(const katz_index& idx, int64_t ld, double tol) {
+  if (idx.n1 <= idx.n1s || idx.lam11 <= 0) return false;
   const double t_solve = cheb_steps(idx, tol) * double(idx.W11L.csr.nnz) * 4.0 * ld / 1.0e13;
-  const double t_gemm = 6.0 * double(idx.n1) * double(idx.n2) * ld / 0.8e15;
+  const double t_gemm = 6.0 * double(idx.n1) * double(idx.n2) * ld / 0.25e15;
   return t_gemm < t_solve;
 }
 
@@ -483,7 +482,7 @@ int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double t
   }
   if (n1 > 0) {
     if constexpr (sizeof(VT) == 4) {
-      if (n2 > 0 && coupling_gemm_pays(idx, ld, tol_l)) {
+      if (n2 > 0 && idx.has_h && coupling_gemm_pays(idx, ld, tol_l)) {
         // K1 = Y1 + (beta M11^{-1} W12) K2 on the tensor cores (all ld columns,
         // so the zero padding columns stay zero)
         float* Bh = idx.ws.get<float>("lrc.K2h", size_t(ld) * idx.ldH);
