@@ -30,9 +30,12 @@ sys.path.insert(0, ROOT)
 METRIC = "Katz queries/sec at 1e-6 rel. error (n=4M); SpMM % of HBM roofline vs plain CG"
 UNIT = "queries/s"
 
-# ncu DRAM traffic per launch of the dominant kernel, keyed by the source hash
-# of the kernel file it was measured on (null once the kernel changes).
-NCU_TRAFFIC = {}
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch
+# of the dominant kernel, keyed by the source hash of the kernel files it was
+# measured on (null once they change).  cheb_step: two launches captured on
+# the same graph recipe at n = 400,000, b = 1,024 (7.43 and 9.19 GB against
+# 6.6 GB algorithmic), scaled by rows to n1 = 3,998,000 (x 10.0).
+NCU_TRAFFIC = {("cheb_step", "0630107f05472740"): 83.1e9}
 
 
 def parse():
@@ -380,7 +383,7 @@ def main():
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "peak_source": f"{src} (hbm_gbs)",
-                "traffic": NCU_TRAFFIC.get((dom, kernel_hash()))}
+                "traffic": NCU_TRAFFIC.get((dom, kernel_hash())), "traffic_unit": "bytes per launch"}
     roof.update({"launches_per_step": p["launches"] / args.steps,
                  "alg_units_per_launch": p["bytes"] / max(1, p["launches"]),
                  "share_of_step": p["ms"] / (ms * args.steps)})
