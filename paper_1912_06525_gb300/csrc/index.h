@@ -89,6 +89,10 @@ struct katz_index {
   katz::DBuf<float> Hh, Hl;
   int64_t ldH = 0;
   bool has_h = false;
+  // S and M22^{-1} (n2 x ld2) as TF32 high/low parts for the tensor-core
+  // Schur products of the FP32 solve (large separators only)
+  katz::DBuf<float> Sh, Sl, Mh, Ml;
+  bool dense_tc = false;
   katz::Mlp mlp;
   katz::DBuf<float> feat;  // n x 32 node features
   std::vector<double> sigma;

@@ -606,6 +606,14 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
     KATZ_CUDA(cudaStreamSynchronize(s));
     KATZ_REQUIRE(hflag == 0, KATZ_ENOTSPD, "M22 is not positive definite");
   }
+  // separators large enough for the dense n2 x n2 x b products to pay on
+  // the tensor cores keep S and M22^{-1} as TF32 parts as well
+  idx.dense_tc = n2 >= 512;
+  if (idx.dense_tc) {
+    for (auto* d : {&idx.Sh, &idx.Sl, &idx.Mh, &idx.Ml}) d->alloc(size_t(n2) * ld2);
+    split_tf32<double>(idx.S64.p, ld2, n2, int(n2), idx.Sh.p, idx.Sl.p, ld2, s);
+    split_tf32<double>(idx.M22inv64.p, ld2, n2, int(n2), idx.Mh.p, idx.Ml.p, ld2, s);
+  }
   idx.S32.alloc(size_t(n2) * ld2);
   idx.M22inv32.alloc(size_t(n2) * ld2);
   to_f32_kernel<<<blocks_for(n2 * ld2), 256, 0, s>>>(idx.S64.p, idx.S32.p, n2 * ld2);

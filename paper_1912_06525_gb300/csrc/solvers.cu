@@ -312,6 +312,30 @@ template <> struct Dense<double> {
   static const double* Wr(const katz_index& i) { return i.Wr64.p; }
 };
 
+// Y = alpha A X + beta Y for the dense n2 x n2 matrices A = S or M22^{-1}
+// and an n2 x ld block X: on the tensor cores (three TF32 products, FP32
+// accuracy; all ld columns so zero padding stays zero) where the index keeps
+// A's TF32 parts, else the FP32/FP64 SIMT GEMM.
+template <class VT>
+static void dense_n2(katz_index& idx, bool minv, const VT* X, int64_t ld, int b, double alpha,
+                     double beta, VT* Y, cudaStream_t s) {
+  const int64_t n2 = idx.n2;
+  if constexpr (sizeof(VT) == 4) {
+    if (idx.dense_tc) {
+      float* Xh = idx.ws.get<float>("S.Xh", size_t(ld) * idx.ld2);
+      float* Xl = idx.ws.get<float>("S.Xl", size_t(ld) * idx.ld2);
+      split_tf32_transposed(reinterpret_cast<const float*>(X), ld, n2, int(ld), Xh, Xl, idx.ld2, s);
+      tc_gemm_tf32x3(minv ? idx.Mh.p : idx.Sh.p, minv ? idx.Ml.p : idx.Sl.p, idx.ld2, Xh, Xl,
+                     idx.ld2, int(n2), int(ld), int(n2), float(alpha), float(beta),
+                     reinterpret_cast<const float*>(Y), ld, reinterpret_cast<float*>(Y), ld,
+                     idx.ws.get<int>("S.err", 1), s);
+      return;
+    }
+  }
+  gemm<VT>(false, n2, b, n2, alpha, minv ? Dense<VT>::Minv(idx) : Dense<VT>::S(idx), idx.ld2, X,
+           ld, beta, Y, ld, s);
+}
+
 // Z = S~^{-1} R = M22^{-1} R + W^ (W^T R), with W^ = W_r D^{1/2} (Eq. 14).
 // FP32 path: the two rank-r products run on the tcgen05 tensor cores with
 // BF16 operands (a preconditioner only needs to be a fixed SPD
@@ -321,7 +345,7 @@ template <class VT>
 static void precond(katz_index& idx, const VT* R, VT* Z, VT* Tm, int b, int64_t ld,
                     cudaStream_t s) {
   const int64_t n2 = idx.n2;
-  gemm<VT>(false, n2, b, n2, 1.0, Dense<VT>::Minv(idx), idx.ld2, R, ld, 0.0, Z, ld, s);
+  dense_n2<VT>(idx, true, R, ld, b, 1.0, 0.0, Z, s);
   if constexpr (sizeof(VT) == 4) {
     if (idx.rank > 0) {
       __nv_bfloat16* Rt = idx.ws.get<__nv_bfloat16>("S.Rt", size_t(b) * idx.ldn2);
@@ -386,7 +410,7 @@ int pcg_schur(katz_index& idx, const VT* F, VT* K2, int b, int64_t ld, const dou
   if (X0) {
     // warm start: R = F - S K2(0), per-column fallback to zero
     KATZ_CUDA(cudaMemcpyAsync(K2, X0, sizeof(VT) * n2 * ld, cudaMemcpyDeviceToDevice, s));
-    gemm<VT>(false, n2, b, n2, -1.0, Dense<VT>::S(idx), idx.ld2, K2, ld, 1.0, R, ld, s);
+    dense_n2<VT>(idx, false, K2, ld, b, -1.0, 1.0, R, s);
     double* ff = ws.get<double>("S.ff", bpad(b));
     int* nfb = ws.get<int>("S.nfb", 1);
     KATZ_CUDA(cudaMemsetAsync(ff, 0, sizeof(double) * b, s));
@@ -410,7 +434,7 @@ int pcg_schur(katz_index& idx, const VT* F, VT* K2, int b, int64_t ld, const dou
   KATZ_CHECK_LAUNCH();
   int active = read_int(st.n_active, s);
   for (int it = 0; it < max_iter && active > 0; ++it) {
-    gemm<VT>(false, n2, b, n2, 1.0, Dense<VT>::S(idx), idx.ld2, P, ld, 0.0, Q, ld, s);
+    dense_n2<VT>(idx, false, P, ld, b, 1.0, 0.0, Q, s);
     coldot<VT>(P, ld, Q, ld, n2, b, st.pq, s);
     colstate_check_pq(st, b, s);
     cg_update_xr<VT>(K2, P, R, Q, ld, n2, b, st, false, s);

@@ -92,3 +92,22 @@ def test_coupling_product_paths_match_oracle(coupling):
         assert st["status"] == "KATZ_OK"
         bound = 1e-6 if prec == katz.KATZ_PREC_MIXED else 1e-4
         assert O.error_inf_rel(K.cpu().numpy(), ref).max() <= bound
+
+
+def test_large_separator_tensor_core_schur_products_match_oracle():
+    """A separator of 700 hubs (>= 512) puts S P and M22^{-1} R of the FP32
+    Schur PCG on the tensor cores (three-TF32 products)."""
+    g = synth.chung_lu(30000, 2.1, 10.0, 3000.0, seed=31)
+    W = O.adjacency(g.n, g.rowptr, g.col, g.val)
+    beta = 0.9 / O.lambda_max(W)
+    idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_F32, rank=32, n_hubs=700,
+                                block_max=64, split=False)
+    assert katz.katz_index_get_info(idx)["n2"] == 700
+    q = synth.queries(g.n, 128, seed=6)
+    cols = [0, 1, 64, 127]
+    Kref, _ = O.katz_cg(W, beta, q[cols], rtol=1e-12)
+    for fn in (katz.katz_query_batch, katz.cg_query_batch):
+        K = torch.zeros((g.n, len(q)), dtype=torch.float64, device="cuda")
+        st, it, rel = fn(idx, torch.from_numpy(q).cuda(), K, out_dtype=katz.KATZ_F64, tol=1e-6)
+        assert st["status"] == "KATZ_OK", (fn.__name__, st)
+        assert O.error_inf_rel(K.cpu().numpy()[:, cols], Kref).max() <= 1e-6, fn.__name__
