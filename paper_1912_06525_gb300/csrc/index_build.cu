@@ -606,9 +606,11 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
     KATZ_CUDA(cudaStreamSynchronize(s));
     KATZ_REQUIRE(hflag == 0, KATZ_ENOTSPD, "M22 is not positive definite");
   }
-  // separators large enough for the dense n2 x n2 x b products to pay on
-  // the tensor cores keep S and M22^{-1} as TF32 parts as well
-  idx.dense_tc = n2 >= 512;
+  // separators large enough for the dense n2 x n2 x b products to dominate
+  // keep S and M22^{-1} as TF32 parts for the tensor cores (their ~2^-22
+  // rounding in S P costs the PCG about one iteration on hard problems,
+  // which only pays when the products are a large share of the solve)
+  idx.dense_tc = n2 >= 4096;
   if (idx.dense_tc) {
     for (auto* d : {&idx.Sh, &idx.Sl, &idx.Mh, &idx.Ml}) d->alloc(size_t(n2) * ld2);
     split_tf32<double>(idx.S64.p, ld2, n2, int(n2), idx.Sh.p, idx.Sl.p, ld2, s);

@@ -95,14 +95,14 @@ def test_coupling_product_paths_match_oracle(coupling):
 
 
 def test_large_separator_tensor_core_schur_products_match_oracle():
-    """A separator of 700 hubs (>= 512) puts S P and M22^{-1} R of the FP32
-    Schur PCG on the tensor cores (three-TF32 products)."""
-    g = synth.chung_lu(30000, 2.1, 10.0, 3000.0, seed=31)
+    """A separator of 4,200 hubs (>= 4,096) puts S P and M22^{-1} R of the
+    FP32 Schur PCG on the tensor cores (three-TF32 products)."""
+    g = synth.chung_lu(60000, 2.1, 10.0, 3000.0, seed=31)
     W = O.adjacency(g.n, g.rowptr, g.col, g.val)
     beta = 0.9 / O.lambda_max(W)
-    idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_F32, rank=32, n_hubs=700,
+    idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_F32, rank=32, n_hubs=4200,
                                 block_max=64, split=False)
-    assert katz.katz_index_get_info(idx)["n2"] == 700
+    assert katz.katz_index_get_info(idx)["n2"] == 4200
     q = synth.queries(g.n, 128, seed=6)
     cols = [0, 1, 64, 127]
     Kref, _ = O.katz_cg(W, beta, q[cols], rtol=1e-12)
