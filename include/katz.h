@@ -160,6 +160,25 @@ int katz_index_build(const katz_csr* W, double beta, const katz_build_opts* opts
 
 void katz_index_free(katz_index* idx);
 
+/* Persist a built index (the stored artefact of Algorithm 1, Section 3.2)
+ * to a file and read it back, so that queries can be served without
+ * repeating the partition, the block inverses, the Schur complement and the
+ * Lanczos low-rank correction.  The file holds every stored field: graph
+ * and reordered blocks, M11 block inverses, M12, S, M22^{-1}, W_r D^{1/2},
+ * sigma, beta, lambda_max, the autotuned launch shapes and the warm-start
+ * network with its optimiser state.  Format: versioned little-endian
+ * records with per-field tags and a checksum.
+ * katz_index_save: waits for all device work, then writes `path` (host
+ *   string; an existing file is replaced; a partial file is removed on
+ *   failure).  KATZ_EINVAL if the file cannot be written.
+ * katz_index_load: allocates a new index on the current device and fills
+ *   it from `path`; *out owns it (free with katz_index_free).  Queries on
+ *   the loaded index run exactly as on the saved one.  KATZ_EINVAL for a
+ *   missing, truncated, corrupt (checksum), foreign (magic) or other-version
+ *   file; *out is NULL on failure. */
+int katz_index_save(const katz_index* idx, const char* path);
+int katz_index_load(const char* path, katz_index** out);
+
 int katz_index_get_info(const katz_index* idx, katz_index_info* info);
 
 /* Copy the partition (host outputs): perm[n] (perm[new] = old node),

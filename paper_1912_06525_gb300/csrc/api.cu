@@ -209,6 +209,26 @@ int katz_index_build(const katz_csr* W, double beta, const katz_build_opts* opts
 
 void katz_index_free(katz_index* idx) { delete idx; }
 
+int katz_index_save(const katz_index* idx, const char* path) {
+  return guarded([&]() {
+    KATZ_REQUIRE(idx && path, KATZ_EINVAL, "null argument");
+    KATZ_CUDA(cudaDeviceSynchronize());
+    katz::save_index(*idx, path);
+    return KATZ_OK;
+  });
+}
+
+int katz_index_load(const char* path, katz_index** out) {
+  return guarded([&]() {
+    KATZ_REQUIRE(out && path, KATZ_EINVAL, "null argument");
+    *out = nullptr;
+    std::unique_ptr<katz_index> idx = katz::load_index(path);
+    KATZ_CUDA(cudaDeviceSynchronize());
+    *out = idx.release();
+    return KATZ_OK;
+  });
+}
+
 int katz_index_get_info(const katz_index* idx, katz_index_info* info) {
   return guarded([&]() {
     KATZ_REQUIRE(idx && info, KATZ_EINVAL, "null argument");

@@ -45,6 +45,8 @@ struct Partition {
 
 }  // namespace katz
 
+// Every field except `ws` and `gather_pref` is stored by save_index
+// (index_io.cu): a field added here is added to its list too.
 struct katz_index {
   int64_t n = 0, nnz = 0;
   double beta = 0, lambda = 0;
@@ -134,6 +136,12 @@ double lambda_max_gpu(const GraphPart& W, int64_t n, int steps, Workspace& ws, c
 
 void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_build_opts& o,
                  cudaStream_t s);
+
+// Versioned binary file of every stored field of an index (device buffers
+// staged through host memory); load validates magic, version, field tags,
+// sizes and a checksum and throws KATZ_EINVAL on any mismatch.
+void save_index(const katz_index& idx, const char* path);
+std::unique_ptr<katz_index> load_index(const char* path);
 
 struct QueryOut {
   void* K = nullptr;  // device

@@ -27,9 +27,11 @@ STATUS_NAMES = {0: "KATZ_OK", 1: "KATZ_EINVAL", 2: "KATZ_ENOTSPD", 3: "KATZ_ENOC
                 4: "KATZ_ENOMEM", 5: "KATZ_ECUDA"}
 
 # every exported symbol of include/katz.h
-EXPORTS = ["katz_lambda_max", "katz_index_build", "katz_index_free", "katz_index_get_info",
-           "katz_index_get_partition", "katz_partition", "katz_index_get_sigma", "katz_query_batch",
-           "cg_query_batch", "linkpred_topk", "linkpred_topk_noalloc", "katz_apply_M", "katz_autotune", "katz_gemm_bf16", "katz_gemm_tf32x3", "katz_launch_count",
+EXPORTS = ["katz_lambda_max", "katz_index_build", "katz_index_free", "katz_index_save",
+           "katz_index_load", "katz_index_get_info", "katz_index_get_partition", "katz_partition",
+           "katz_index_get_sigma", "katz_query_batch", "cg_query_batch", "linkpred_topk",
+           "linkpred_topk_noalloc", "katz_apply_M", "katz_autotune", "katz_gemm_bf16",
+           "katz_gemm_tf32x3", "katz_launch_count",
            "katz_profile_enable", "katz_profile_read", "katz_multi_build", "katz_multi_free",
            "katz_multi_query", "katz_warmstart_train", "katz_mlp_loss_grad", "katz_last_error"]
 
@@ -98,6 +100,8 @@ def lib() -> C.CDLL:
         L.katz_index_free.argtypes = [vp]
         L.katz_index_free.restype = None
         L.katz_index_get_info.argtypes = [vp, C.POINTER(katz_index_info)]
+        L.katz_index_save.argtypes = [vp, C.c_char_p]
+        L.katz_index_load.argtypes = [C.c_char_p, C.POINTER(vp)]
         L.katz_index_get_partition.argtypes = [vp, vp, vp]
         L.katz_index_get_sigma.argtypes = [vp, vp]
         L.katz_partition.argtypes = [C.POINTER(katz_csr), i32, i32, i32, vp, vp, vp, vp]
@@ -219,6 +223,18 @@ def katz_index_build(graph, beta: float, value_dtype: int = KATZ_F32, build_lrc:
     h = C.c_void_p()
     _check(lib().katz_index_build(C.byref(c), float(beta), C.byref(o), _stream(stream),
                                   C.byref(h)))
+    return KatzIndex(h.value)
+
+
+def katz_index_save(index: KatzIndex, path) -> None:
+    """Write every stored field of the index to `path`."""
+    _check(lib().katz_index_save(index.handle, os.fsencode(path)))
+
+
+def katz_index_load(path) -> KatzIndex:
+    """Read an index written by katz_index_save onto the current device."""
+    h = C.c_void_p()
+    _check(lib().katz_index_load(os.fsencode(path), C.byref(h)))
     return KatzIndex(h.value)
 
 

@@ -78,3 +78,29 @@ def test_partition_bit_exact_workload1(L):
     g, q, c, r = synth.workload(1)
     _same(g, 0, 64, True)
     _same(g, 20, 32, True)
+
+
+def _index_file_header(version=1, mark=0x01020304):
+    return b"KATZIDX\0" + np.array([version, mark], dtype="<u4").tobytes()
+
+
+def test_index_load_rejects_bad_files_on_the_host(L, tmp_path):
+    """katz_index_load validates the file before touching device memory:
+    missing, foreign, other-version and truncated files are KATZ_EINVAL."""
+    cases = {
+        "missing": None,
+        "foreign": b"PK\x03\x04" + bytes(60),
+        "version": _index_file_header(version=99) + bytes(16),
+        "byteorder": _index_file_header(mark=0x04030201) + bytes(16),
+        "truncated": _index_file_header() + bytes(5),
+        "empty": b"",
+    }
+    for name, data in cases.items():
+        path = tmp_path / f"{name}.katzidx"
+        if data is not None:
+            path.write_bytes(data)
+        with pytest.raises(katz.KatzError) as e:
+            katz.katz_index_load(path)
+        assert e.value.code == katz.KATZ_EINVAL, name
+    msg = katz.katz_last_error()
+    assert "truncated" in msg or "magic" in msg
