@@ -22,8 +22,8 @@ __all__ = [
     "adjacency", "lambda_max", "katz_matrix", "katz_series", "katz_direct",
     "katz_cg", "apply_M", "partition", "check_partition", "splitmix64", "splitmix64_uniform",
     "lrc_build", "lrc_query", "katz_lrc", "schur_precond_spectrum",
-    "linkpred_topk", "error_inf_rel", "gelu", "mlp_forward", "mlp_loss_grad",
-    "adamw_step",
+    "linkpred_topk", "top_nodes", "pearson", "sparse_katz", "error_inf_rel", "gelu",
+    "mlp_forward", "mlp_loss_grad", "adamw_step",
 ]
 
 
@@ -471,6 +471,72 @@ def linkpred_topk(W: sp.csr_matrix, K: np.ndarray, Q, k: int):
         ids[j, : len(order)] = cand[order]
         sc[j, : len(order)] = K[cand[order], j]
     return ids, sc
+
+
+def top_nodes(scores: np.ndarray, k: int, exclude=()) -> np.ndarray:
+    """The k nodes of highest score, score descending and node id ascending
+    on ties, leaving out the nodes in ``exclude`` (fewer than k if too few
+    remain)."""
+    keep = np.ones(scores.shape[0], dtype=bool)
+    keep[np.asarray(list(exclude), dtype=np.int64)] = False
+    cand = np.nonzero(keep)[0]
+    return cand[np.lexsort((cand, -scores[cand]))[:k]]
+
+
+def pearson(x: np.ndarray, y: np.ndarray) -> float:
+    """Pearson correlation of two equal-length vectors: the centred inner
+    product over the product of the centred norms.  Either vector constant
+    (zero spread; every vector of length 1) gives 0, no linear
+    association."""
+    xc = x - x.mean()
+    yc = y - y.mean()
+    sxx = float(xc @ xc)
+    syy = float(yc @ yc)
+    if sxx == 0.0 or syy == 0.0:
+        return 0.0
+    return float(xc @ yc) / np.sqrt(sxx * syy)
+
+
+def sparse_katz(W: sp.csr_matrix, beta: float, Q, s: int, T: int, solve=None):
+    """Sparse-Katz re-ranking of the link-prediction list (Algorithm 3,
+    Section 3.3, Fig. 2), in the algorithm's order:
+
+    1. k_q, the Katz vector of the query (Eq. 3);
+    2. the Top-s list: the s best link candidates of k_q (q and its current
+       neighbours left out, as in ``linkpred_topk``);
+    3. the T landmark nodes t: the T highest scores of k_q over every node
+       but q (neighbours included), and their Katz vectors k_t, the columns
+       of the n x T matrix K_T;
+    4. for every candidate j, rho_j = Pearson correlation of row q and row j
+       of K_T (the T-vectors (k_t[q])_t and (k_t[j])_t);
+    5. the Top-s list re-ordered by rho descending, ties kept in Katz order.
+
+    ``solve(W, beta, ids)`` returns Katz columns (default: dense Cholesky for
+    n <= 3000, else CG to 1e-13).  Returns (ids b x s, rho b x s, landmarks
+    b x T, Katz-ordered candidates b x s); missing candidates are id -1 with
+    rho 0 at the end of the row."""
+    if solve is None:
+        solve = (katz_direct if W.shape[0] <= 3000
+                 else (lambda W_, b_, ids: katz_cg(W_, b_, ids)[0]))
+    Q = np.asarray(Q)
+    b = len(Q)
+    Kq = solve(W, beta, Q)
+    ids = np.full((b, s), -1, dtype=np.int64)
+    rho = np.zeros((b, s))
+    land = np.zeros((b, T), dtype=np.int64)
+    cand_k = np.full((b, s), -1, dtype=np.int64)
+    for j, q in enumerate(Q):
+        nbrs = W.indices[W.indptr[q]:W.indptr[q + 1]]
+        cand = top_nodes(Kq[:, j], s, exclude=[q, *nbrs.tolist()])
+        lm = top_nodes(Kq[:, j], T, exclude=[q])
+        land[j, : len(lm)] = lm
+        cand_k[j, : len(cand)] = cand
+        KT = solve(W, beta, lm)
+        r = np.array([pearson(KT[q, :], KT[c, :]) for c in cand])
+        order = sorted(range(len(cand)), key=lambda i: (-r[i], i))
+        ids[j, : len(cand)] = cand[order]
+        rho[j, : len(cand)] = r[order]
+    return ids, rho, land, cand_k
 
 
 # ---------------------------------------------------- warm-start network
