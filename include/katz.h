@@ -234,6 +234,32 @@ int linkpred_topk(const katz_index* idx, const int32_t* q, int32_t b,
                   const void* K, int32_t k_dtype, int64_t ldk, int32_t k,
                   int32_t* ids_out, double* scores_out, void* stream);
 
+/* Sparse-Katz link prediction (Algorithm 3, Section 3.3, Fig. 2) for b
+ * queries q (host or device, 1 <= b <= 1024):
+ *   1. k_q by LRC-Katz (plain CG if the index has no LRC part), with the
+ *      accuracy that *opts asks for (as katz_query_batch);
+ *   2. the Top-s list: the s highest k_q[j] over j outside {q} and q's
+ *      neighbours (the linkpred_topk list);
+ *   3. the T landmarks: the T highest k_q[j] over j != q (neighbours
+ *      included), and their Katz vectors k_t, the columns of K_T (b*T more
+ *      solves, batched up to 1,024 columns);
+ *   4. rho_c = Pearson correlation of row q and row c of K_T (the
+ *      T-vectors (k_t[q])_t and (k_t[c])_t), in FP64; 0 when either row is
+ *      constant (always when T = 1);
+ *   5. the Top-s list re-ordered by rho descending, ties in Katz order.
+ * Scores are compared in FP32 (the stored Katz vectors) for the selections
+ * of steps 2-3, score descending and node id ascending.
+ * Outputs (host or device, row j = query j): ids_out[b*s] re-ranked
+ * candidates (-1 at the tail when fewer than s exist), rho_out[b*s] their
+ * correlations (0 for -1), landmarks_out[b*T] (may be NULL) the landmarks
+ * in Katz order.  1 <= s, T <= 64 and T < n, else KATZ_EINVAL.  stats (may
+ * be NULL): iterations, refinement steps and residual as the maximum over
+ * all the solves of the call, ms[0] its wall time.  KATZ_ENOCONV if any
+ * solve hit its cap (outputs still filled). */
+int sparse_katz_topk(const katz_index* idx, const int32_t* q, int32_t b, int32_t s, int32_t T,
+                     const katz_query_opts* opts, int32_t* ids_out, double* rho_out,
+                     int32_t* landmarks_out, katz_stats* stats, void* stream);
+
 /* linkpred_topk without any device allocation.  The paper has no
  * counterpart: this serves callers that must not allocate device memory
  * while they run -- work recorded into a CUDA stream capture (where

@@ -339,6 +339,38 @@ int linkpred_topk(const katz_index* cidx, const int32_t* q, int32_t b, const voi
   });
 }
 
+int sparse_katz_topk(const katz_index* cidx, const int32_t* q, int32_t b, int32_t s_top,
+                     int32_t T, const katz_query_opts* opts, int32_t* ids_out, double* rho_out,
+                     int32_t* landmarks_out, katz_stats* stats, void* stream) {
+  return guarded([&]() {
+    KATZ_REQUIRE(cidx && opts && ids_out && rho_out, KATZ_EINVAL, "null argument");
+    KATZ_REQUIRE(opts->tol > 0, KATZ_EINVAL, "tol must be positive");
+    katz_index* idx = const_cast<katz_index*>(cidx);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int32_t> qh;
+    const int32_t* qd = stage_queries(idx, q, b, s, &qh);
+    const bool dev_ids = is_device_ptr(ids_out), dev_rho = is_device_ptr(rho_out);
+    const bool dev_land = landmarks_out && is_device_ptr(landmarks_out);
+    int32_t* ids = dev_ids ? ids_out : idx->ws.get<int32_t>("sk.oid", size_t(b) * s_top);
+    double* rho = dev_rho ? rho_out : idx->ws.get<double>("sk.orho", size_t(b) * s_top);
+    int32_t* land = !landmarks_out ? nullptr
+                    : dev_land     ? landmarks_out
+                                   : idx->ws.get<int32_t>("sk.oland", size_t(b) * T);
+    const int st = katz::sparse_katz(*idx, qd, qh.data(), b, s_top, T, *opts, ids, rho, land,
+                                     stats, s);
+    if (st != KATZ_OK && st != KATZ_ENOCONV) return st;
+    if (!dev_ids)
+      KATZ_CUDA(cudaMemcpyAsync(ids_out, ids, 4 * size_t(b) * s_top, cudaMemcpyDeviceToHost, s));
+    if (!dev_rho)
+      KATZ_CUDA(cudaMemcpyAsync(rho_out, rho, 8 * size_t(b) * s_top, cudaMemcpyDeviceToHost, s));
+    if (landmarks_out && !dev_land)
+      KATZ_CUDA(cudaMemcpyAsync(landmarks_out, land, 4 * size_t(b) * T, cudaMemcpyDeviceToHost, s));
+    KATZ_CUDA(cudaStreamSynchronize(s));
+    if (st == KATZ_ENOCONV) g_last_error = "iteration or refinement cap reached";
+    return st;
+  });
+}
+
 int katz_warmstart_train(katz_index* idx, const int32_t* q_train, int32_t n_train,
                          const katz_train_opts* opts, katz_train_stats* stats, void* stream) {
   return guarded([&]() {

@@ -164,6 +164,13 @@ int multi_query(katz_multi& m, const int32_t* q_dev, int qpg, const katz_query_o
                 int out_dt, int64_t ldk, katz_stats* stats, std::vector<int32_t>& iters,
                 std::vector<double>& relres, cudaStream_t s);
 
+// Sparse-Katz (Algorithm 3) for b queries: ids/rho (device, b x s) get the
+// re-ranked Top-s candidates and their Pearson correlations, land (device,
+// b x T, may be null) the landmarks.
+int sparse_katz(katz_index& idx, const int32_t* q_dev, const int32_t* q_host, int b, int s_top,
+                int T, const katz_query_opts& o, int32_t* ids, double* rho, int32_t* land,
+                katz_stats* st, cudaStream_t s);
+
 double warmstart_train(katz_index& idx, const int32_t* q_host, int n_train, int hidden, int epochs,
                        int batch, float lr, float wd, uint64_t seed, double* init_loss, int* steps,
                        cudaStream_t s);

@@ -308,20 +308,22 @@ constexpr int kTopUnroll = 8;  // rows loaded ahead per warp
 // sorted top-k list in local memory (scores in K's own type, so the order
 // is decided in that precision) with its k-th entry held in registers; a
 // candidate is tested against q's neighbours (binary search in the sorted
-// CSR row) only when it beats the k-th entry.  Lists go to the scratch as
-// [column][slice*8 + warp][k].
+// CSR row; skipped when mask_nbrs is false) only when it beats the k-th
+// entry.  Lists go to the scratch as [column][slice*8 + warp][k].
 template <class VT>
 __global__ void __launch_bounds__(256) topk_partial_kernel(Csr W, const VT* K, int64_t ldk,
                                                            int64_t n, const int32_t* q, int b,
                                                            int k, int64_t rows_per_slice,
-                                                           int32_t* pid, double* psc) {
+                                                           bool mask_nbrs, int32_t* pid,
+                                                           double* psc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = blockIdx.y * 32 + lane;
   const bool cv = j < b;
   const int64_t r0 = int64_t(blockIdx.x) * rows_per_slice;
   const int64_t r1 = min(n, r0 + rows_per_slice);
   const int64_t qq = cv ? q[j] : -1;
-  const int64_t nb0 = cv ? W.rowptr[qq] : 0, nb1 = cv ? W.rowptr[qq + 1] : 0;
+  const int64_t nb0 = cv && mask_nbrs ? W.rowptr[qq] : 0;
+  const int64_t nb1 = cv && mask_nbrs ? W.rowptr[qq + 1] : 0;
   VT ls[kTopMax];
   int li[kTopMax];
   int cnt = 0;
@@ -402,11 +404,12 @@ __global__ void topk_merge_kernel(const int32_t* pid, const double* psc, int lis
 template <class VT>
 void topk_columns_ws(const Csr& W, const VT* K, int64_t ldk, int64_t n, const int32_t* q, int b,
                      int k, int32_t* ids, double* scores, int32_t* ws_id, double* ws_sc,
-                     int slices, cudaStream_t s) {
+                     int slices, cudaStream_t s, bool mask_nbrs) {
   KATZ_REQUIRE(slices * 8 <= 2 * kTopMax && k <= kTopMax, KATZ_EINVAL, "topk: too many lists");
   const int64_t rows_per = ceil_div(n, slices);
   dim3 grid((unsigned)slices, (unsigned)ceil_div(b, 32));
-  topk_partial_kernel<VT><<<grid, 256, 0, s>>>(W, K, ldk, n, q, b, k, rows_per, ws_id, ws_sc);
+  topk_partial_kernel<VT><<<grid, 256, 0, s>>>(W, K, ldk, n, q, b, k, rows_per, mask_nbrs, ws_id,
+                                               ws_sc);
   KATZ_CHECK_LAUNCH();
   topk_merge_kernel<<<(unsigned)ceil_div(b, 64), 64, 0, s>>>(ws_id, ws_sc, slices * 8, k, b, ids,
                                                              scores);
@@ -414,9 +417,9 @@ void topk_columns_ws(const Csr& W, const VT* K, int64_t ldk, int64_t n, const in
 }
 template void topk_columns_ws<float>(const Csr&, const float*, int64_t, int64_t, const int32_t*,
                                      int, int, int32_t*, double*, int32_t*, double*, int,
-                                     cudaStream_t);
+                                     cudaStream_t, bool);
 template void topk_columns_ws<double>(const Csr&, const double*, int64_t, int64_t,
                                       const int32_t*, int, int, int32_t*, double*, int32_t*,
-                                      double*, int, cudaStream_t);
+                                      double*, int, cudaStream_t, bool);
 
 }  // namespace katz

@@ -27,10 +27,12 @@ void block_inverses(const Csr& Wperm, const int64_t* start, const int32_t* size,
 void spd_inverse_inplace(double* A, int64_t n, int64_t lda, double* ws, int* flag,
                          cudaStream_t s);
 
-// Top-k per column with explicit scratch (slices*b*k ids and scores).
+// Top-k per column with explicit scratch (slices*8*b*k ids and scores):
+// for column j the k nodes i != q[j] of highest K[i][j] (score descending,
+// id ascending), leaving out q[j]'s neighbours when mask_nbrs.
 template <class VT>
 void topk_columns_ws(const Csr& W, const VT* K, int64_t ldk, int64_t n, const int32_t* q, int b,
                      int k, int32_t* ids, double* scores, int32_t* ws_id, double* ws_sc,
-                     int slices, cudaStream_t s);
+                     int slices, cudaStream_t s, bool mask_nbrs = true);
 
 }  // namespace katz

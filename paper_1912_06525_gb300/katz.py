@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "KATZ_OK", 1: "KATZ_EINVAL", 2: "KATZ_ENOTSPD", 3: "KATZ_ENOC
 EXPORTS = ["katz_lambda_max", "katz_index_build", "katz_index_free", "katz_index_save",
            "katz_index_load", "katz_index_get_info", "katz_index_get_partition", "katz_partition",
            "katz_index_get_sigma", "katz_query_batch", "cg_query_batch", "linkpred_topk",
-           "linkpred_topk_noalloc", "katz_apply_M", "katz_autotune", "katz_gemm_bf16",
+           "linkpred_topk_noalloc", "sparse_katz_topk", "katz_apply_M", "katz_autotune", "katz_gemm_bf16",
            "katz_gemm_tf32x3", "katz_launch_count",
            "katz_profile_enable", "katz_profile_read", "katz_multi_build", "katz_multi_free",
            "katz_multi_query", "katz_warmstart_train", "katz_mlp_loss_grad", "katz_last_error"]
@@ -111,6 +111,8 @@ def lib() -> C.CDLL:
         L.cg_query_batch.argtypes = qargs
         L.linkpred_topk.argtypes = [vp, vp, i32, vp, i32, i64, i32, vp, vp, vp]
         L.linkpred_topk_noalloc.argtypes = [vp, vp, i32, vp, i32, i64, i32, vp, vp, vp]
+        L.sparse_katz_topk.argtypes = [vp, vp, i32, i32, i32, C.POINTER(katz_query_opts), vp, vp,
+                                       vp, C.POINTER(katz_stats), vp]
         L.katz_apply_M.argtypes = [vp, vp, vp, i32, i32, vp]
         L.katz_autotune.argtypes = [vp, i32, vp, vp, vp]
         L.katz_gemm_bf16.argtypes = [vp, i64, vp, i64, i32, i32, i32, C.c_float, C.c_float, vp,
@@ -320,6 +322,24 @@ def linkpred_topk_noalloc(index, q, K, k_dtype, k, ids_out, scores_out, stream=N
     b = int(q.shape[0])
     _check(lib().linkpred_topk_noalloc(index.handle, _ptr(q), b, _ptr(K), k_dtype, _ld(K), k,
                                        _ptr(ids_out), _ptr(scores_out), _stream(stream)))
+
+
+def sparse_katz_topk(index, q, s, T, ids_out, rho_out, landmarks_out=None, tol=1e-6,
+                     tol_kind=KATZ_TOL_ERROR_INF, precision=KATZ_PREC_MIXED, max_iter=0,
+                     max_refine=0, gather_kernel=KATZ_GATHER_AUTO, stream=None) -> dict:
+    """Sparse-Katz (Algorithm 3): re-ranked Top-s candidates (ids_out, b x s
+    int32) with their Pearson correlations over T landmarks (rho_out, b x s
+    float64); landmarks_out (b x T int32) optional.  Returns the stats."""
+    b = int(q.shape[0])
+    o = katz_query_opts(float(tol), tol_kind, precision, max_iter, max_refine, 0, 0,
+                        gather_kernel)
+    st = katz_stats()
+    code = lib().sparse_katz_topk(index.handle, _ptr(q), b, s, T, C.byref(o), _ptr(ids_out),
+                                  _ptr(rho_out), _ptr(landmarks_out), C.byref(st),
+                                  _stream(stream))
+    _check(code, allow=(KATZ_OK, KATZ_ENOCONV))
+    return {"iters": st.iters, "refine_steps": st.refine_steps, "max_rel_res": st.max_rel_res,
+            "ms": list(st.ms), "status": STATUS_NAMES[code]}
 
 
 def katz_apply_M(index, X, Y, b, dtype, stream=None):

@@ -1,0 +1,192 @@
+"""Sparse-Katz (Algorithm 3) on the GPU against the FP64 oracle.
+
+The GPU selects landmarks and candidates on its FP32 Katz vectors (error
+<= 1e-6 of the column maximum), so a node within that band of the s-th or
+T-th score may legitimately be swapped with another; the checks are:
+  * every node clearly inside (outside) the oracle's selection is inside
+    (outside) the GPU's, with the band 2e-6 * max|k_q|;
+  * rho of every GPU candidate, recomputed by the oracle on the GPU's own
+    landmarks from FP64 Katz vectors, within the propagated bound
+        |d rho| <= 2 sqrt(T) eps m (1/|x - mean x| + 1/|y - mean y|),
+    eps = 1.1e-6, m = the largest entry of the landmark vectors (first
+    order in the Katz-vector errors: the gradient of a correlation in
+    either argument is at most 1/its centred norm);
+  * the GPU list is sorted by its own rho, and agrees with the oracle's
+    order wherever the oracle's rho values differ by more than the bounds.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1912_06525_gb300 import katz, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def graph(seed=3):
+    """Power-law part with a 300-leaf star attached, plus a separate small
+    component (zero Katz scores for its nodes from the others)."""
+    a = synth.chung_lu(2400, 2.1, 6.0, 300.0, seed=seed)
+    st = synth.star(300)
+    e = synth.erdos_renyi(60, 0.1, seed=seed + 1)
+    g = synth.disjoint_union([a, st, e])
+    r = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    m = r < g.col
+    u = np.concatenate([r[m], [0]])
+    v = np.concatenate([g.col[m], [2400]])
+    return synth.edges_to_graph(g.n, u, v, {"kind": "sk"}, synth.dyadic_weights(seed + 2))
+
+
+def check_selection(got, score, k, exclude):
+    """got: the GPU's k selected nodes (-1 padded) for one query; score:
+    the oracle's FP64 Katz column."""
+    keep = np.ones(score.shape[0], dtype=bool)
+    keep[list(exclude)] = False
+    idx = np.nonzero(keep)[0]
+    ref = idx[np.lexsort((idx, -score[idx]))[:k]]
+    band = 2e-6 * np.abs(score).max()
+    got = got[got >= 0]
+    assert len(got) == len(ref) and len(set(got.tolist())) == len(got)
+    assert keep[got].all()
+    kth = score[ref[-1]]
+    must = set(ref[score[ref] > kth + band].tolist())
+    assert must <= set(got.tolist())
+    assert (score[got] >= kth - band).all()
+
+
+def check_query(Kd, W, q, s, T, ids, rho, land):
+    score = Kd[:, q]
+    nb = W.indices[W.indptr[q]:W.indptr[q + 1]].tolist()
+    check_selection(land, score, T, [q])
+    check_selection(ids, score, s, [q, *nb])
+    KT = Kd[:, land]
+    m = np.abs(KT).max()
+    x = KT[q]
+    valid = ids >= 0
+    assert (rho[~valid] == 0).all()
+    ref, tol = [], []
+    for c in ids[valid]:
+        y = KT[c]
+        ref.append(O.pearson(x, y))
+        nx, ny = np.linalg.norm(x - x.mean()), np.linalg.norm(y - y.mean())
+        bound = np.inf if min(nx, ny) == 0 else 2 * np.sqrt(T) * 1.1e-6 * m * (1 / nx + 1 / ny)
+        tol.append(bound + 1e-12)
+    ref, tol = np.array(ref), np.array(tol)
+    got = rho[valid]
+    assert (np.abs(got - ref) <= tol).all(), np.max(np.abs(got - ref) - tol)
+    assert (np.diff(got) <= 0).all()
+    # the oracle's order wherever its values are separated by the bounds
+    for i in range(len(got) - 1):
+        assert ref[i] >= ref[i + 1] - tol[i] - tol[i + 1]
+
+
+@pytest.mark.parametrize("s,T,lrc", [(20, 9, True), (64, 64, True), (8, 1, True),
+                                     (20, 9, False)])
+def test_sparse_katz_matches_oracle(s, T, lrc):
+    g = graph()
+    W = O.adjacency(g.n, g.rowptr, g.col, g.val)
+    beta = 0.85 / O.lambda_max(W)
+    Kd = O.katz_matrix(W, beta)
+    idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_F32, build_lrc=lrc, rank=16,
+                                n_hubs=30, block_max=32)
+    q = np.concatenate([synth.queries(2400, 14, seed=5), [2400, 2401, 2700, 2750]]).astype(np.int32)
+    ids = torch.empty((len(q), s), dtype=torch.int32, device="cuda")
+    rho = torch.empty((len(q), s), dtype=torch.float64, device="cuda")
+    land = torch.empty((len(q), T), dtype=torch.int32, device="cuda")
+    st = katz.sparse_katz_topk(idx, torch.from_numpy(q).cuda(), s, T, ids, rho, land)
+    assert st["status"] == "KATZ_OK"
+    ids, rho, land = ids.cpu().numpy(), rho.cpu().numpy(), land.cpu().numpy()
+    for j, qq in enumerate(q):
+        check_query(Kd, W, int(qq), s, T, ids[j], rho[j], land[j])
+    if T == 1:
+        assert (rho == 0).all()
+
+
+def test_sparse_katz_host_outputs_and_oracle_ids():
+    """Host buffers; where no near-tie decides, the ids equal the oracle's."""
+    g = graph(seed=8)
+    W = O.adjacency(g.n, g.rowptr, g.col, g.val)
+    beta = 0.7 / O.lambda_max(W)
+    Kd = O.katz_matrix(W, beta)
+    idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_F32, rank=16, n_hubs=30,
+                                block_max=32)
+    q = synth.queries(2400, 6, seed=9)
+    s, T = 10, 9
+    ids = np.empty((len(q), s), dtype=np.int32)
+    rho = np.empty((len(q), s), dtype=np.float64)
+    land = np.empty((len(q), T), dtype=np.int32)
+    katz.sparse_katz_topk(idx, q, s, T, ids, rho, land)
+    rid, rrho, rland, _ = O.sparse_katz(W, beta, q, s, T, solve=lambda W_, b_, c: Kd[:, c])
+    for j, qq in enumerate(q):
+        check_query(Kd, W, int(qq), s, T, ids[j], rho[j], land[j])
+        if land[j].tolist() == rland[j].tolist() and set(ids[j].tolist()) == set(rid[j].tolist()):
+            sep = np.abs(np.diff(rrho[j])).min() if s > 1 else 1.0
+            if sep > 1e-4:
+                assert ids[j].tolist() == rid[j].tolist()
+                np.testing.assert_allclose(rho[j], rrho[j], atol=1e-4)
+
+
+def test_sparse_katz_argument_errors():
+    g = synth.erdos_renyi(30, 0.2, seed=2)
+    W = O.adjacency(g.n, g.rowptr, g.col, g.val)
+    idx = katz.katz_index_build(g, 0.5 / O.lambda_max(W), value_dtype=katz.KATZ_UNIT,
+                                build_lrc=False)
+    q = np.array([1, 2], dtype=np.int32)
+    for s, T in [(0, 3), (65, 3), (5, 0), (5, 65), (5, 30)]:
+        ids = np.empty((2, max(s, 1)), dtype=np.int32)
+        rho = np.empty((2, max(s, 1)), dtype=np.float64)
+        with pytest.raises(katz.KatzError) as e:
+            katz.sparse_katz_topk(idx, q, s, T, ids, rho)
+        assert e.value.code == katz.KATZ_EINVAL
+    ids = np.empty((2, 5), dtype=np.int32)
+    rho = np.empty((2, 5), dtype=np.float64)
+    with pytest.raises(katz.KatzError) as e:
+        katz.sparse_katz_topk(idx, np.array([30], dtype=np.int32), 5, 3, ids, rho)
+    assert e.value.code == katz.KATZ_EINVAL
+
+
+def test_sparse_katz_full_size_sampled():
+    """The n = 1M power-law graph's recipe at 1/20 scale (n = 50,000) with
+    b = 64 queries, s = 20, T = 9: four queries checked against FP64 CG."""
+    g, q, c, r = synth.workload(2, 0.05)
+    q = synth.queries(g.n, 64, seed=12)
+    W = O.adjacency(g.n, g.rowptr, g.col, g.val)
+    lam = katz.katz_lambda_max(g, steps=96)
+    beta = c / lam
+    idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_F32, rank=r, n_hubs=g.n // 100,
+                                block_max=64, split=False)
+    s, T = 20, 9
+    ids = torch.empty((len(q), s), dtype=torch.int32, device="cuda")
+    rho = torch.empty((len(q), s), dtype=torch.float64, device="cuda")
+    land = torch.empty((len(q), T), dtype=torch.int32, device="cuda")
+    katz.sparse_katz_topk(idx, torch.from_numpy(q).cuda(), s, T, ids, rho, land)
+    ids, rho, land = ids.cpu().numpy(), rho.cpu().numpy(), land.cpu().numpy()
+    for j in (0, 21, 42, 63):
+        cols = np.concatenate([[q[j]], land[j]])
+        Kc, _ = O.katz_cg(W, beta, cols, rtol=1e-12)
+        score = Kc[:, 0]
+        nb = W.indices[W.indptr[q[j]]:W.indptr[q[j] + 1]].tolist()
+        check_selection(land[j], score, T, [q[j]])
+        check_selection(ids[j], score, s, [q[j], *nb])
+        KT = Kc[:, 1:]
+        x = KT[q[j]]
+        m = np.abs(KT).max()
+        for c_, r_ in zip(ids[j], rho[j]):
+            if c_ < 0:
+                continue
+            y = KT[c_]
+            nx, ny = np.linalg.norm(x - x.mean()), np.linalg.norm(y - y.mean())
+            if min(nx, ny) == 0:
+                continue
+            bound = 2 * np.sqrt(T) * 1.1e-6 * m * (1 / nx + 1 / ny) + 1e-12
+            assert abs(r_ - O.pearson(x, y)) <= bound
+        assert (np.diff(rho[j][ids[j] >= 0]) <= 0).all()
