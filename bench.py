@@ -56,6 +56,8 @@ def parse():
                     help="override the query batch width b (small profiling cases)")
     ap.add_argument("--workload", type=int, default=3, choices=[2, 3],
                     help="3: n=4M modular graph (the metric's workload); 2: n=1M power law")
+    ap.add_argument("--rank", type=int, default=0,
+                    help="rank r of the low-rank correction (0: the workload's, 128 or 64)")
     ap.add_argument("--sparse-katz", type=int, default=0, metavar="T",
                     help="also time Sparse-Katz (Algorithm 3) with T landmarks and s = 20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -266,6 +268,8 @@ def main():
 
     g, q, c, rank_r = synth.workload(args.workload, args.scale)
     c = args.c if args.c is not None else (0.9 if args.workload == 3 else 0.5)
+    if args.rank > 0:
+        rank_r = args.rank
     if args.batch > 0:
         q = synth.queries(g.n, args.batch, seed=synth.BASE_SEED + 77)
     b = len(q)
@@ -441,6 +445,7 @@ def main():
         cfg.update({"method": args.method, "parallelism": "replicas" if world > 1 else "single",
                     "spmm_autotune": tune, "gather_kernel": args.gather,
                     "n2": info["n2"], "n1": info["n1"], "index_build_s": build_s,
+                    "index_device_bytes": info["device_bytes"],
                     "lambda_max": lam, "beta": beta,
                     "beta_rule": "1/(lambda_max+1)" if args.paper_beta else "c/lambda_max"})
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
