@@ -56,6 +56,10 @@ def parse():
                     help="override the query batch width b (small profiling cases)")
     ap.add_argument("--workload", type=int, default=3, choices=[2, 3],
                     help="3: n=4M modular graph (the metric's workload); 2: n=1M power law")
+    ap.add_argument("--standin", default="", choices=[""] + sorted(__import__(
+                        "paper_1912_06525_gb300.synth", fromlist=["TABLE1"]).TABLE1),
+                    help="a Table 1 stand-in graph instead of the workload (1,000 queries, "
+                         "unit weights, beta = 1/(lambda_max+1), r = 25 unless --rank)")
     ap.add_argument("--rank", type=int, default=0,
                     help="rank r of the low-rank correction (0: the workload's, 128 or 64)")
     ap.add_argument("--sparse-katz", type=int, default=0, metavar="T",
@@ -266,8 +270,14 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    g, q, c, rank_r = synth.workload(args.workload, args.scale)
-    c = args.c if args.c is not None else (0.9 if args.workload == 3 else 0.5)
+    if args.standin:  # Section 4's setting on a Table 1 stand-in
+        g = synth.table1_standin(args.standin, args.scale)
+        q = synth.queries(g.n, min(1000, g.n), seed=synth.BASE_SEED + 55)
+        c, rank_r = 0.5, 25
+        args.paper_beta = True
+    else:
+        g, q, c, rank_r = synth.workload(args.workload, args.scale)
+        c = args.c if args.c is not None else (0.9 if args.workload == 3 else 0.5)
     if args.rank > 0:
         rank_r = args.rank
     if args.batch > 0:
@@ -280,7 +290,10 @@ def main():
     if args.paper_beta:  # Section 4: beta = 1 / (||W||_2 + 1)
         c = lam / (lam + 1.0)
     beta = c / lam
-    if args.workload == 3:
+    if args.standin:  # unit weights; top-1% hubs, the rest kept whole
+        idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_UNIT, rank=rank_r,
+                                    n_hubs=g.n // 100, block_max=64, split=False)
+    elif args.workload == 3:
         n_hubs = int(g.meta["hubs"].shape[0])
         idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_BF16, rank=rank_r,
                                     n_hubs=n_hubs, block_max=64, split=False)
@@ -442,6 +455,12 @@ def main():
 
     if rank == 0:
         cfg = workload_desc(g, b, c, rank_r, args.scale, args.workload)
+        if args.standin:
+            n0, d0, l0 = synth.TABLE1[args.standin]
+            cfg["workload"] = (f"stand-in for {args.standin} (Table 1: n={n0:,}, average degree "
+                               f"{d0}, ||G||_2={l0}): Chung-Lu n={g.n:,}, nnz={g.nnz:,}, "
+                               f"lambda_max={lam:.1f}, unit weights, b={b} queries, r={rank_r}, "
+                               f"top-1% hubs, beta=1/(lambda_max+1), tol 1e-6")
         cfg.update({"method": args.method, "parallelism": "replicas" if world > 1 else "single",
                     "spmm_autotune": tune, "gather_kernel": args.gather,
                     "n2": info["n2"], "n1": info["n1"], "index_build_s": build_s,
