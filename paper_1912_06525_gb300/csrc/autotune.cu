@@ -74,8 +74,10 @@ bool pipe_faster(const GraphPart& g, Fused kind, bool unit, const SpmmCfg& c, fl
         [&] { pipe_cheb_step(g.view(), g.ps, unit, 0.01, 0.1, 1.0, X, X, X, Y, ld, err, s); }, s, reps);
     faster = t_pipe < t_reg;
   } else {
+    HeavyRows hv;
+    const HeavyRows* hvp = heavy_rows(g, ld, ws, hv);
     const double t_reg = time_launches(
-        [&] { ffr_update(g.view(), 0.01, X, Y, Z, true, ld, b, nullptr, &c, s); }, s, reps);
+        [&] { ffr_update(g.view(), 0.01, X, Y, Z, true, ld, b, nullptr, &c, s, hvp); }, s, reps);
     const double t_pipe = time_launches(
         [&] { pipe_residual(g.view(), g.ps, unit, 0.01, X, Y, Z, ld, b, nullptr, err, s); }, s,
         reps);

@@ -125,16 +125,84 @@ __device__ __forceinline__ void row_sum(const Csr& A, const float* __restrict__ 
   }
 }
 
+// Row epilogue: (Rh, Rl)[i] from the row sums acc, X[i] and (update) the
+// previous residual; sq accumulates Rh^2 per lane column.
+template <int VPT, bool INIT>
+__device__ __forceinline__ void row_epilogue(int64_t i, const FF (&acc)[VPT][4],
+                                             const float* __restrict__ X, float* Rh, float* Rl,
+                                             int64_t ld, int64_t tile0, int t,
+                                             const bool (&cval)[VPT], float beh, float bel,
+                                             float (&sq)[VPT][4]) {
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    if (!cval[v]) continue;
+    const int64_t o = i * ld + tile0 + (v * 32 + t) * 4;
+    const float4 x4 = __ldg(reinterpret_cast<const float4*>(X + o));
+    const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+    float rh0[4] = {0.f, 0.f, 0.f, 0.f}, rl0[4] = {0.f, 0.f, 0.f, 0.f};
+    if constexpr (!INIT) {
+      const float4 a1 = *reinterpret_cast<const float4*>(Rh + o);
+      rh0[0] = a1.x; rh0[1] = a1.y; rh0[2] = a1.z; rh0[3] = a1.w;
+      if (Rl) {
+        const float4 a2 = *reinterpret_cast<const float4*>(Rl + o);
+        rl0[0] = a2.x; rl0[1] = a2.y; rl0[2] = a2.z; rl0[3] = a2.w;
+      }
+    }
+    float rh[4], rl[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const FF r = ff_res(acc[v][w], beh, bel, xs[w], rh0[w], rl0[w]);
+      rh[w] = r.hi;
+      rl[w] = r.lo;
+      sq[v][w] = __fmaf_rn(r.hi, r.hi, sq[v][w]);
+    }
+    *reinterpret_cast<float4*>(Rh + o) = make_float4(rh[0], rh[1], rh[2], rh[3]);
+    if constexpr (INIT)
+      *reinterpret_cast<float4*>(Rl + o) = make_float4(rl[0], rl[1], rl[2], rl[3]);
+  }
+}
+
+// Per-CTA column sums of Rh^2 (red: [8 warps][TILE] in shared memory, each
+// warp's lanes add their sq), then one FP64 atomic per column and CTA.
+template <int VPT>
+__device__ __forceinline__ void flush_sq(double (*red)[128 * VPT], int wib, int t,
+                                         float (&sq)[VPT][4]) {
+#pragma unroll
+  for (int v = 0; v < VPT; ++v)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      red[wib][(v * 32 + t) * 4 + w] += sq[v][w];
+      sq[v][w] = 0.f;
+    }
+}
+
+template <int VPT>
+__device__ __forceinline__ void column_atomics(double (*red)[128 * VPT], int64_t tile0, int b,
+                                               double* rr) {
+  for (int c = threadIdx.x; c < 128 * VPT; c += blockDim.x) {
+    double sum = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sum += red[q][c];
+    if (tile0 + c < b && sum != 0.0) atomicAdd(rr + tile0 + c, sum);
+  }
+}
+
+__device__ __forceinline__ FF ff_plus(FF a, FF b) {
+  const FF t = two_sum(a.hi, b.hi);
+  return fast_two_sum(t.hi, t.lo + a.lo + b.lo);
+}
+
 // Warp per row (grid-stride), VPT float4 column groups per lane per tile of
-// 128 * VPT columns.  Column sums of Rh^2: FP32 over at most 64 rows per
-// lane, then FP64 in shared memory per warp, then one atomic per column and
-// CTA.
+// 128 * VPT columns; rows longer than kHeavyRowNnz are left to the split
+// kernels when skip_heavy.  Column sums of Rh^2: FP32 over at most 64 rows
+// per lane, then FP64 in shared memory per warp, then one atomic per column
+// and CTA.
 template <int WT, int VPT, bool INIT>
 __global__ void __launch_bounds__(256) ffr_rows_kernel(Csr A, const float* __restrict__ X,
                                                        float* Rh, float* Rl, int64_t ld, float beh,
-                                                       float bel, double* rr, int b) {
-  constexpr int VW = 4;
-  constexpr int TILE = 32 * VW * VPT;
+                                                       float bel, double* rr, int b,
+                                                       bool skip_heavy) {
+  constexpr int TILE = 128 * VPT;
   __shared__ double red[8][TILE];
   const int t = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -143,17 +211,18 @@ __global__ void __launch_bounds__(256) ffr_rows_kernel(Csr A, const float* __res
   for (int c = threadIdx.x; c < 8 * TILE; c += blockDim.x) (&red[0][0])[c] = 0.0;
   bool cval[VPT];
 #pragma unroll
-  for (int v = 0; v < VPT; ++v) cval[v] = tile0 + (v * 32 + t) * VW < ld;
-  float sq[VPT][VW];
+  for (int v = 0; v < VPT; ++v) cval[v] = tile0 + (v * 32 + t) * 4 < ld;
+  float sq[VPT][4];
 #pragma unroll
   for (int v = 0; v < VPT; ++v)
 #pragma unroll
-    for (int w = 0; w < VW; ++w) sq[v][w] = 0.f;
+    for (int w = 0; w < 4; ++w) sq[v][w] = 0.f;
   int nsq = 0;
   __syncthreads();
   for (int64_t i = warp; i < A.nrows; i += nwarps) {
     const int64_t k0 = A.rowptr[i], k1 = A.rowptr[i + 1];
-    FF acc[VPT][VW];
+    if (skip_heavy && k1 - k0 > kHeavyRowNnz) continue;
+    FF acc[VPT][4];
     // the first pass (X = K0) cancels to the residual's size and needs the
     // float-float sum; later passes gather a correction X = D with
     // |M D| ~ |r|, where FP32 sums of short rows carry errors ~1e-7 of the
@@ -162,57 +231,101 @@ __global__ void __launch_bounds__(256) ffr_rows_kernel(Csr A, const float* __res
       row_sum<WT, VPT, true>(A, X, ld, tile0, t, cval, k0, k1, acc);
     else
       row_sum<WT, VPT, false>(A, X, ld, tile0, t, cval, k0, k1, acc);
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      if (!cval[v]) continue;
-      const int64_t o = i * ld + tile0 + (v * 32 + t) * VW;
-      const float4 x4 = __ldg(reinterpret_cast<const float4*>(X + o));
-      const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
-      float rh0[4] = {0.f, 0.f, 0.f, 0.f}, rl0[4] = {0.f, 0.f, 0.f, 0.f};
-      if constexpr (!INIT) {
-        const float4 a1 = *reinterpret_cast<const float4*>(Rh + o);
-        rh0[0] = a1.x; rh0[1] = a1.y; rh0[2] = a1.z; rh0[3] = a1.w;
-        if (Rl) {
-          const float4 a2 = *reinterpret_cast<const float4*>(Rl + o);
-          rl0[0] = a2.x; rl0[1] = a2.y; rl0[2] = a2.z; rl0[3] = a2.w;
-        }
-      }
-      float rh[4], rl[4];
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        const FF r = ff_res(acc[v][w], beh, bel, xs[w], rh0[w], rl0[w]);
-        rh[w] = r.hi;
-        rl[w] = r.lo;
-        sq[v][w] = __fmaf_rn(r.hi, r.hi, sq[v][w]);
-      }
-      *reinterpret_cast<float4*>(Rh + o) = make_float4(rh[0], rh[1], rh[2], rh[3]);
-      if constexpr (INIT)
-        *reinterpret_cast<float4*>(Rl + o) = make_float4(rl[0], rl[1], rl[2], rl[3]);
-    }
+    row_epilogue<VPT, INIT>(i, acc, X, Rh, Rl, ld, tile0, t, cval, beh, bel, sq);
     if (++nsq == 64) {
-#pragma unroll
-      for (int v = 0; v < VPT; ++v)
-#pragma unroll
-        for (int w = 0; w < VW; ++w) {
-          red[wib][(v * 32 + t) * VW + w] += sq[v][w];
-          sq[v][w] = 0.f;
-        }
+      flush_sq<VPT>(red, wib, t, sq);
       nsq = 0;
     }
   }
+  flush_sq<VPT>(red, wib, t, sq);
+  __syncthreads();
+  if (rr) column_atomics<VPT>(red, tile0, b, rr);
+}
+
+// Heavy rows, pass 1: CTA = (segment of kHeavySeg entries, column tile);
+// each warp sums kHeavySeg / 8 entries in float-float, the 8 partials are
+// added in warp order in shared memory and stored as (P[g], P[nseg + g]).
+template <int WT, int VPT>
+__global__ void __launch_bounds__(256) ffr_heavy_partial_kernel(Csr A, const float* __restrict__ X,
+                                                                int64_t ld, HeavyRows hv) {
+  constexpr int TILE = 128 * VPT;
+  constexpr int64_t kPerWarp = kHeavySeg / 8;
+  __shared__ FF red[8][TILE];
+  const int t = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t g = blockIdx.x;
+  const int64_t tile0 = int64_t(blockIdx.y) * TILE;
+  const int h = hv.seg_row[g];
+  const int64_t row = hv.rows[h];
+  const int64_t r0 = A.rowptr[row], r1 = A.rowptr[row + 1];
+  const int64_t s0 = r0 + (g - hv.seg_ptr[h]) * kHeavySeg;
+  const int64_t k0 = min(r1, s0 + wib * kPerWarp), k1 = min(r1, s0 + (wib + 1) * kPerWarp);
+  bool cval[VPT];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) cval[v] = tile0 + (v * 32 + t) * 4 < ld;
+  FF acc[VPT][4];
+  row_sum<WT, VPT, true>(A, X, ld, tile0, t, cval, k0, k1, acc);
 #pragma unroll
   for (int v = 0; v < VPT; ++v)
 #pragma unroll
-    for (int w = 0; w < VW; ++w) red[wib][(v * 32 + t) * VW + w] += sq[v][w];
+    for (int w = 0; w < 4; ++w) red[wib][(v * 32 + t) * 4 + w] = acc[v][w];
   __syncthreads();
-  if (rr) {
-    for (int c = threadIdx.x; c < TILE; c += blockDim.x) {
-      double sum = 0.0;
+  for (int c = threadIdx.x; c < TILE; c += blockDim.x) {
+    if (tile0 + c >= ld) continue;
+    FF sum = red[0][c];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) sum += red[q][c];
-      if (tile0 + c < b && sum != 0.0) atomicAdd(rr + tile0 + c, sum);
-    }
+    for (int q = 1; q < 8; ++q) sum = ff_plus(sum, red[q][c]);
+    const int64_t o = g * ld + tile0 + c;
+    hv.scratch[o] = sum.hi;
+    hv.scratch[hv.nseg * ld + o] = sum.lo;
   }
+}
+
+// Heavy rows, pass 2: warp per heavy row; its segment partials are added
+// in segment order, then the row epilogue and the Rh^2 column sums.
+template <int VPT, bool INIT>
+__global__ void __launch_bounds__(256) ffr_heavy_finish_kernel(const float* __restrict__ X,
+                                                               float* Rh, float* Rl, int64_t ld,
+                                                               float beh, float bel, double* rr,
+                                                               int b, HeavyRows hv) {
+  constexpr int TILE = 128 * VPT;
+  __shared__ double red[8][TILE];
+  const int t = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t h = int64_t(blockIdx.x) * 8 + wib;
+  const int64_t tile0 = int64_t(blockIdx.y) * TILE;
+  for (int c = threadIdx.x; c < 8 * TILE; c += blockDim.x) (&red[0][0])[c] = 0.0;
+  bool cval[VPT];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) cval[v] = tile0 + (v * 32 + t) * 4 < ld;
+  float sq[VPT][4];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) sq[v][w] = 0.f;
+  __syncthreads();
+  if (h < hv.n) {
+    FF acc[VPT][4];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) acc[v][w] = {0.f, 0.f};
+    for (int64_t g = hv.seg_ptr[h]; g < hv.seg_ptr[h + 1]; ++g) {
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        if (!cval[v]) continue;
+        const int64_t o = g * ld + tile0 + (v * 32 + t) * 4;
+        const float4 ph = *reinterpret_cast<const float4*>(hv.scratch + o);
+        const float4 pl = *reinterpret_cast<const float4*>(hv.scratch + hv.nseg * ld + o);
+        acc[v][0] = ff_plus(acc[v][0], {ph.x, pl.x});
+        acc[v][1] = ff_plus(acc[v][1], {ph.y, pl.y});
+        acc[v][2] = ff_plus(acc[v][2], {ph.z, pl.z});
+        acc[v][3] = ff_plus(acc[v][3], {ph.w, pl.w});
+      }
+    }
+    row_epilogue<VPT, INIT>(hv.rows[h], acc, X, Rh, Rl, ld, tile0, t, cval, beh, bel, sq);
+  }
+  flush_sq<VPT>(red, wib, t, sq);
+  __syncthreads();
+  if (rr) column_atomics<VPT>(red, tile0, b, rr);
 }
 
 // (Rh, Rl)[pos(i), j] += beta w_{q_j i}; rr[j] += new Rh^2 - old Rh^2.
@@ -274,7 +387,8 @@ unsigned flat(int64_t total) {
 }  // namespace
 
 void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl, bool init,
-                int64_t ld, int b, double* rr, const SpmmCfg* cfg, cudaStream_t s) {
+                int64_t ld, int b, double* rr, const SpmmCfg* cfg, cudaStream_t s,
+                const HeavyRows* hv) {
   KATZ_REQUIRE(ld % 4 == 0 && ld >= b && reinterpret_cast<uintptr_t>(X) % 16 == 0 &&
                    reinterpret_cast<uintptr_t>(Rh) % 16 == 0 &&
                    reinterpret_cast<uintptr_t>(Rl) % 16 == 0 && (Rl || !init),
@@ -287,9 +401,12 @@ void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl,
   const int64_t ctas = std::min<int64_t>(ceil_div(A.nrows, 8),
                                          std::max<int64_t>(1, int64_t(num_sms()) * cps / tiles));
   const dim3 grid((unsigned)std::max<int64_t>(1, ctas), (unsigned)tiles);
+  const bool split = hv && hv->nseg > 0;
+  KATZ_REQUIRE(!split || (hv->scratch && reinterpret_cast<uintptr_t>(hv->scratch) % 16 == 0),
+               KATZ_EINVAL, "ffr_update: heavy-row scratch must be 16-byte aligned");
   prof_begin(s);
 #define KATZ_FFR(WT, V, I) \
-  ffr_rows_kernel<WT, V, I><<<grid, 256, 0, s>>>(A, X, Rh, Rl, ld, beh, bel, rr, b)
+  ffr_rows_kernel<WT, V, I><<<grid, 256, 0, s>>>(A, X, Rh, Rl, ld, beh, bel, rr, b, split)
 #define KATZ_FFR_W(WT)                                                     \
   if (vpt == 2) {                                                          \
     if (init) KATZ_FFR(WT, 2, true); else KATZ_FFR(WT, 2, false);          \
@@ -305,6 +422,29 @@ void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl,
 #undef KATZ_FFR_W
 #undef KATZ_FFR
   KATZ_CHECK_LAUNCH();
+  if (split) {
+    const dim3 pg((unsigned)hv->nseg, (unsigned)tiles);
+    const dim3 fg((unsigned)ceil_div(hv->n, 8), (unsigned)tiles);
+#define KATZ_FFH(WT)                                                                        \
+  if (vpt == 2) ffr_heavy_partial_kernel<WT, 2><<<pg, 256, 0, s>>>(A, X, ld, *hv);         \
+  else ffr_heavy_partial_kernel<WT, 1><<<pg, 256, 0, s>>>(A, X, ld, *hv)
+    switch (A.vdt) {
+      case KATZ_UNIT: KATZ_FFH(KATZ_UNIT); break;
+      case KATZ_F32: KATZ_FFH(KATZ_F32); break;
+      case KATZ_BF16: KATZ_FFH(KATZ_BF16); break;
+      default: KATZ_FFH(KATZ_F64); break;
+    }
+#undef KATZ_FFH
+    KATZ_CHECK_LAUNCH();
+    if (vpt == 2) {
+      if (init) ffr_heavy_finish_kernel<2, true><<<fg, 256, 0, s>>>(X, Rh, Rl, ld, beh, bel, rr, b, *hv);
+      else ffr_heavy_finish_kernel<2, false><<<fg, 256, 0, s>>>(X, Rh, Rl, ld, beh, bel, rr, b, *hv);
+    } else {
+      if (init) ffr_heavy_finish_kernel<1, true><<<fg, 256, 0, s>>>(X, Rh, Rl, ld, beh, bel, rr, b, *hv);
+      else ffr_heavy_finish_kernel<1, false><<<fg, 256, 0, s>>>(X, Rh, Rl, ld, beh, bel, rr, b, *hv);
+    }
+    KATZ_CHECK_LAUNCH();
+  }
   if (profiling())
     prof_end("ff_residual",
              8.0 * (A.nrows + 1) + double(A.nnz) * (4 + vdt_size(A.vdt)) +

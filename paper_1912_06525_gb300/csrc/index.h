@@ -5,6 +5,7 @@
 #include <memory>
 #include <string>
 
+#include "ff_residual.h"
 #include "gather_pipe.h"
 #include "kernels.h"
 #include "mlp.h"
@@ -28,6 +29,11 @@ struct GraphPart {
   DevCsr csr;
   DBuf<int32_t> heavy;
   int64_t n_heavy = 0;
+  // heavy rows cut into segments of kHeavySeg entries for the residual
+  // kernels: segments [hseg_ptr[h], hseg_ptr[h+1]) belong to heavy[h],
+  // hseg_row[g] = h
+  DBuf<int32_t> hseg_ptr, hseg_row;
+  int64_t n_hseg = 0;
   PipeSplit ps;
   std::map<int, SpmmCfg> tuned;
   Csr view() const { return csr.view(); }
@@ -36,6 +42,20 @@ struct GraphPart {
     return it == tuned.end() ? nullptr : &it->second;
   }
 };
+
+// The heavy rows of g split for the residual kernels, with their scratch
+// for width ld taken from ws (null when g has no heavy rows).
+inline const HeavyRows* heavy_rows(const GraphPart& g, int64_t ld, Workspace& ws,
+                                   HeavyRows& hv) {
+  if (g.n_hseg == 0) return nullptr;
+  hv.rows = g.heavy.p;
+  hv.seg_ptr = g.hseg_ptr.p;
+  hv.seg_row = g.hseg_row.p;
+  hv.n = g.n_heavy;
+  hv.nseg = g.n_hseg;
+  hv.scratch = ws.get<float>("ffr.heavy", size_t(2) * g.n_hseg * ld);
+  return &hv;
+}
 
 struct Partition {
   std::vector<int64_t> perm;       // perm[new] = old

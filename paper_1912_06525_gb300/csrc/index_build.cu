@@ -62,11 +62,25 @@ static void upload_part(const HostCsr& h, int vdt, GraphPart& g, cudaStream_t s)
     if (h.rowptr[i + 1] - h.rowptr[i] > kHeavyRowNnz) heavy.push_back((int32_t)i);
   g.n_heavy = (int64_t)heavy.size();
   g.heavy.alloc(std::max<size_t>(heavy.size(), 1));
+  std::vector<int32_t> seg_ptr(heavy.size() + 1, 0), seg_row;
+  for (size_t hh = 0; hh < heavy.size(); ++hh) {
+    const int64_t len = h.rowptr[heavy[hh] + 1] - h.rowptr[heavy[hh]];
+    const int64_t nseg = ceil_div(len, kHeavySeg);
+    for (int64_t k = 0; k < nseg; ++k) seg_row.push_back((int32_t)hh);
+    seg_ptr[hh + 1] = (int32_t)seg_row.size();
+  }
+  g.n_hseg = (int64_t)seg_row.size();
+  g.hseg_ptr.alloc(seg_ptr.size());
+  g.hseg_row.alloc(std::max<size_t>(seg_row.size(), 1));
+  KATZ_CUDA(cudaMemcpyAsync(g.hseg_ptr.p, seg_ptr.data(), sizeof(int32_t) * seg_ptr.size(),
+                            cudaMemcpyHostToDevice, s));
   if (!heavy.empty()) {
     KATZ_CUDA(cudaMemcpyAsync(g.heavy.p, heavy.data(), sizeof(int32_t) * heavy.size(),
                               cudaMemcpyHostToDevice, s));
-    KATZ_CUDA(cudaStreamSynchronize(s));
+    KATZ_CUDA(cudaMemcpyAsync(g.hseg_row.p, seg_row.data(), sizeof(int32_t) * seg_row.size(),
+                              cudaMemcpyHostToDevice, s));
   }
+  KATZ_CUDA(cudaStreamSynchronize(s));
 }
 
 // ------------------------------------------------------------ partition

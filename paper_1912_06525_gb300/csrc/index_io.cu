@@ -189,6 +189,9 @@ void io_part(Archive& a, const std::string& p, GraphPart& g) {
   a.dbuf(p + ".val", g.csr.val);
   a.dbuf(p + ".heavy", g.heavy);
   a.scalar(p + ".n_heavy", g.n_heavy);
+  a.dbuf(p + ".hseg_ptr", g.hseg_ptr);
+  a.dbuf(p + ".hseg_row", g.hseg_row);
+  a.scalar(p + ".n_hseg", g.n_hseg);
   a.dbuf(p + ".ps.bstart", g.ps.bstart);
   a.dbuf(p + ".ps.bentry", g.ps.bentry);
   a.dbuf(p + ".ps.ctr", g.ps.ctr);
@@ -313,10 +316,26 @@ void serialize(Archive& a, katz_index& x) {
 }
 
 // Consistency of a loaded index beyond what the records fix.
+void check_part(const GraphPart& g, const char* name) {
+  const DevCsr& c = g.csr;
+  const bool ok = c.nrows >= 0 && c.nnz >= 0 && c.col.n == size_t(c.nnz) &&
+                  (c.nrows == 0 || c.rowptr.n == size_t(c.nrows + 1)) &&
+                  c.val.n == size_t(c.nnz) * vdt_size(c.vdt) && g.heavy.n >= size_t(g.n_heavy) &&
+                  (g.n_hseg == 0 || (g.hseg_ptr.n == size_t(g.n_heavy + 1) &&
+                                     g.hseg_row.n >= size_t(g.n_hseg)));
+  if (!ok) throw Error(KATZ_EINVAL, std::string("index file: inconsistent operator ") + name);
+}
+
 void check_loaded(const katz_index& x) {
   auto fail = [](const char* what) {
     throw Error(KATZ_EINVAL, std::string("index file: inconsistent ") + what);
   };
+  check_part(x.W, "W");
+  check_part(x.Wp, "Wp");
+  check_part(x.W12, "W12");
+  check_part(x.W21, "W21");
+  check_part(x.W11L, "W11L");
+  check_part(x.W22, "W22");
   if (x.n < 0 || x.n >= (int64_t(1) << 31) || int64_t(x.deg_h.size()) != x.n) fail("n");
   if (x.W.csr.nrows != x.n || int64_t(x.W.csr.rowptr.n) != x.n + 1 ||
       int64_t(x.W.csr.col.n) != x.W.csr.nnz || x.W.csr.nnz != x.nnz)

@@ -11,6 +11,8 @@ namespace katz {
 // kernel (several warps per row, one column slice each) so that a few hub
 // rows do not serialise the sweep.
 constexpr int64_t kHeavyRowNnz = 384;
+// stored entries per segment of a heavy row in the split residual kernels
+constexpr int64_t kHeavySeg = 512;
 
 // Launch shape of the CSR SpMM (chosen by the autotuner or the default).
 struct SpmmCfg {

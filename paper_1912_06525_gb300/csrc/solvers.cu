@@ -663,6 +663,7 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   double ms_res = 0;
   int refine = 0;
   bool pending = false;  // D holds a correction not yet added to K
+  HeavyRows hv;  // the residual operator's heavy rows, split
   if (status == KATZ_OK || status == KATZ_ENOCONV) {
     for (;;) {
       const auto r0 = clk::now();
@@ -678,13 +679,14 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
           pipe_residual(G.view(), G.ps, idx.unit_weights, idx.beta, Kh, Rh, Rl, ld, b, nullptr,
                         perr, s);
         else
-          ffr_update(G.view(), idx.beta, Kh, Rh, Rl, true, ld, b, nullptr, gcfg, s);
+          ffr_update(G.view(), idx.beta, Kh, Rh, Rl, true, ld, b, nullptr, gcfg, s,
+                     heavy_rows(G, ld, ws, hv));
         ffr_add_rhs(idx.W.view(), q, pos, b, idx.beta, Rh, Rl, ld, nullptr, maxdeg, s);
         coldot<float>(Rh, ld, Rh, ld, n, b, rr, s);
       } else {
         // Rl carries the first pass's low part into the first update only
         ffr_update(G.view(), idx.beta, D, Rh, refine == 1 ? Rl : nullptr, false, ld, b, rr, gcfg,
-                   s);
+                   s, heavy_rows(G, ld, ws, hv));
       }
       inner_thresholds_kernel<<<1, 1024, 0, s>>>(rr, thr2, tau, b, conv, thr2_in, nopen);
       KATZ_CHECK_LAUNCH();
