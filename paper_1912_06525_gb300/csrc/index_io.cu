@@ -318,9 +318,12 @@ void serialize(Archive& a, katz_index& x) {
 // Consistency of a loaded index beyond what the records fix.
 void check_part(const GraphPart& g, const char* name) {
   const DevCsr& c = g.csr;
-  const bool ok = c.nrows >= 0 && c.nnz >= 0 && c.col.n == size_t(c.nnz) &&
-                  (c.nrows == 0 || c.rowptr.n == size_t(c.nrows + 1)) &&
-                  c.val.n == size_t(c.nnz) * vdt_size(c.vdt) && g.heavy.n >= size_t(g.n_heavy) &&
+  // (uploads give col at least one element; an operator never uploaded has
+  // no arrays at all)
+  const bool ok = c.nrows >= 0 && c.nnz >= 0 && c.col.n >= size_t(c.nnz) &&
+                  (c.rowptr.n == 0 ? c.nrows == 0 && c.nnz == 0
+                                   : c.rowptr.n == size_t(c.nrows + 1)) &&
+                  c.val.n >= size_t(c.nnz) * vdt_size(c.vdt) && g.heavy.n >= size_t(g.n_heavy) &&
                   (g.n_hseg == 0 || (g.hseg_ptr.n == size_t(g.n_heavy + 1) &&
                                      g.hseg_row.n >= size_t(g.n_hseg)));
   if (!ok) throw Error(KATZ_EINVAL, std::string("index file: inconsistent operator ") + name);
@@ -337,10 +340,8 @@ void check_loaded(const katz_index& x) {
   check_part(x.W11L, "W11L");
   check_part(x.W22, "W22");
   if (x.n < 0 || x.n >= (int64_t(1) << 31) || int64_t(x.deg_h.size()) != x.n) fail("n");
-  if (x.W.csr.nrows != x.n || int64_t(x.W.csr.rowptr.n) != x.n + 1 ||
-      int64_t(x.W.csr.col.n) != x.W.csr.nnz || x.W.csr.nnz != x.nnz)
+  if (x.W.csr.nrows != x.n || int64_t(x.W.csr.rowptr.n) != x.n + 1 || x.W.csr.nnz != x.nnz)
     fail("graph");
-  if (x.W.csr.val.n != size_t(x.nnz) * vdt_size(x.W.csr.vdt)) fail("graph values");
   if (!(x.beta > 0) || !(x.beta * x.lambda < 1)) fail("beta");
   if (x.lrc) {
     if (x.n1 + x.n2 != x.n || int64_t(x.part.perm.size()) != x.n ||
