@@ -465,6 +465,7 @@ def main():
                     "spmm_autotune": tune, "gather_kernel": args.gather,
                     "n2": info["n2"], "n1": info["n1"], "index_build_s": build_s,
                     "index_device_bytes": info["device_bytes"],
+                    "sigma_1": info["lambda_max_R"],
                     "lambda_max": lam, "beta": beta,
                     "beta_rule": "1/(lambda_max+1)" if args.paper_beta else "c/lambda_max"})
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
