@@ -288,17 +288,20 @@ int katz_apply_M(const katz_index* idx, const void* X, void* Y, int32_t b,
 
 /* Autotuner: times the candidate launch shapes of the multi-RHS CSR
  * product (columns per warp-row tile in {128..1024} x CTAs per SM in
- * {2..16}) on the index's operators for right-hand-side width b, keeps the
+ * {2..64}) on the index's operators for right-hand-side width b, keeps the
  * fastest per operator for later queries with that b, and caches the
- * choice per (rows, nnz, b, value type) in the process; on the large-block
+ * choice per (rows, nnz, b, value type) in the process; for the fused
+ * kernels (the large-block Chebyshev step, the refinement-residual pass)
+ * it times their own grids (CTAs per SM in {8..128}); on the large-block
  * operator it also chooses between the register and the pipelined (TMA
  * bulk-copy) Chebyshev step, and on the full operators between the two
  * kernels of the first and of the later refinement-residual passes.
- * out (5 ints): out[0] = chosen column tile (0 = default), out[1] = CTAs
+ * out (7 ints): out[0] = chosen column tile (0 = default), out[1] = CTAs
  * per SM, out[2] = 1 if the pipelined Chebyshev step was chosen, out[3] /
  * out[4] = 1 if the pipelined kernel was chosen for the first / later
- * residual passes of LRC queries; ms[0] = best time, ms[1] = time of the
- * default shape (per product, FP32 vectors). */
+ * residual passes of LRC queries, out[5] / out[6] = CTAs per SM of the
+ * Chebyshev step / of the residual pass (0 if not tuned); ms[0] = best
+ * time, ms[1] = time of the default shape (per product, FP32 vectors). */
 int katz_autotune(katz_index* idx, int32_t b, int32_t* out, double* ms, void* stream);
 
 /* D = A * B^T on the tcgen05 tensor cores (BF16 operands, FP32

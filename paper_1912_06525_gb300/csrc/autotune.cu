@@ -114,7 +114,7 @@ SpmmCfg tune_part(GraphPart& g, int b, Workspace& ws, cudaStream_t s, double* be
   *best_ms = *def_ms;
   for (int tile : {128, 256, 512, 1024}) {
     if (tile > 4 * ld && tile != 128) continue;
-    for (int cps : {2, 4, 8, 16}) {
+    for (int cps : {2, 4, 8, 16, 32, 64}) {
       SpmmCfg c;
       c.col_tile = tile;
       c.ctas_per_sm = cps;
@@ -124,6 +124,32 @@ SpmmCfg tune_part(GraphPart& g, int b, Workspace& ws, cudaStream_t s, double* be
         best = c;
       }
     }
+  }
+  if (kind != Fused::none && g.csr.nrows > 0 && (kind == Fused::cheb || g.csr.vdt != KATZ_F64)) {
+    // the fused kernel's own grid: its warps take one column tile of the
+    // rows at a time, and more resident-then-queued CTAs per SM than the
+    // plain product keeps the active rows' gathers in L2
+    float* Z = ws.get<float>("tune.Z", size_t(rows) * ld);
+    KATZ_CUDA(cudaMemsetAsync(Z, 0, sizeof(float) * rows * ld, s));
+    HeavyRows hv;
+    const HeavyRows* hvp = heavy_rows(g, ld, ws, hv);
+    double bestf = 0;
+    for (int cps : {8, 16, 32, 64, 128}) {
+      SpmmCfg c = best;
+      c.fused_cps = cps;
+      const double ms =
+          kind == Fused::cheb
+              ? time_launches(
+                    [&] { cheb_step(g.view(), 0.01, 0.1, 1.0, X, X, X, Y, ld, b, s, &c); }, s, reps)
+              : time_launches(
+                    [&] { ffr_update(g.view(), 0.01, X, Y, Z, true, ld, b, nullptr, &c, s, hvp); },
+                    s, reps);
+      if (best.fused_cps == 0 || ms < bestf) {
+        bestf = ms;
+        best.fused_cps = cps;
+      }
+    }
+    ws.release("tune.Z");
   }
   if (kind != Fused::none && pipe_eligible(g.ps, ld) && (unit || g.csr.vdt != KATZ_F64)) {
     float* Z = ws.get<float>("tune.Z", size_t(rows) * ld);
@@ -153,9 +179,14 @@ TuneResult autotune(katz_index& idx, int b, cudaStream_t s) {
     const SpmmCfg cp = tune_part(idx.Wp, b, idx.ws, s, &b2, &d2, Fused::residual, idx.unit_weights);
     r.res_first_pipe = cp.pipe_first;
     r.res_pipe = cp.pipe;
-    if (idx.W11L.csr.nrows > 0)
-      r.cheb_pipe =
-          tune_part(idx.W11L, b, idx.ws, s, &b2, &d2, Fused::cheb, idx.unit_weights).pipe;
+    r.res_cps = cp.fused_cps;
+    if (idx.W11L.csr.nrows > 0) {
+      const SpmmCfg cc = tune_part(idx.W11L, b, idx.ws, s, &b2, &d2, Fused::cheb, idx.unit_weights);
+      r.cheb_pipe = cc.pipe;
+      r.cheb_cps = cc.fused_cps;
+    }
+  } else {
+    r.res_cps = c.fused_cps;
   }
   // release the tuning scratch
   idx.ws.release("tune.X");

@@ -397,7 +397,9 @@ void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl,
   const float beh = float(beta), bel = float(beta - double(beh));
   const int vpt = ld > 128 ? 2 : 1;
   const int64_t tiles = ceil_div(ld, 128 * vpt);
-  const int cps = cfg && cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm : 8;
+  const int cps = cfg && cfg->fused_cps > 0     ? cfg->fused_cps
+                  : cfg && cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm
+                                                : 8;
   const int64_t ctas = std::min<int64_t>(ceil_div(A.nrows, 8),
                                          std::max<int64_t>(1, int64_t(num_sms()) * cps / tiles));
   const dim3 grid((unsigned)std::max<int64_t>(1, ctas), (unsigned)tiles);

@@ -207,6 +207,7 @@ struct TuneResult {
   int col_tile = 0, ctas_per_sm = 0, rhs_width = 0;
   bool cheb_pipe = false;  // the pipelined Chebyshev step was faster on the large block
   bool res_first_pipe = false, res_pipe = false;  // ... residual passes (LRC operator)
+  int cheb_cps = 0, res_cps = 0;  // CTAs per SM of the fused kernels
   double ms_best = 0, ms_default = 0;
 };
 // Times candidate SpMM launch shapes on every operator of the index for

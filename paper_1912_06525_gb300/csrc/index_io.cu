@@ -196,25 +196,31 @@ void io_part(Archive& a, const std::string& p, GraphPart& g) {
   a.dbuf(p + ".ps.bentry", g.ps.bentry);
   a.dbuf(p + ".ps.ctr", g.ps.ctr);
   a.scalar(p + ".ps.nblocks", g.ps.nblocks);
-  // autotuned launch shapes: (b, warps, col_tile, ctas, pipe, pipe_first)
+  // autotuned launch shapes: (b, warps, col_tile, ctas, pipe, pipe_first,
+  // fused_cps)
+  constexpr size_t kF = 7;
   std::vector<int32_t> t;
   if (a.saving())
     for (auto& kv : g.tuned) {
       const SpmmCfg& c = kv.second;
       t.insert(t.end(), {kv.first, c.warps_per_cta, c.col_tile, c.ctas_per_sm, int(c.pipe),
-                         int(c.pipe_first)});
+                         int(c.pipe_first), c.fused_cps});
     }
-  a.vec(p + ".tuned", t);
+  a.vec(p + ".tuned7", t);
   if (!a.saving()) {
-    KATZ_REQUIRE(t.size() % 6 == 0, KATZ_EINVAL, "index file: " + p + ".tuned");
+    KATZ_REQUIRE(t.size() % kF == 0, KATZ_EINVAL, "index file: " + p + ".tuned7");
     g.tuned.clear();
-    for (size_t i = 0; i < t.size(); i += 6) {
+    for (size_t i = 0; i < t.size(); i += kF) {
       SpmmCfg c;
       c.warps_per_cta = t[i + 1];
       c.col_tile = t[i + 2];
       c.ctas_per_sm = t[i + 3];
       c.pipe = t[i + 4] != 0;
       c.pipe_first = t[i + 5] != 0;
+      c.fused_cps = t[i + 6];
+      KATZ_REQUIRE(c.ctas_per_sm >= 0 && c.ctas_per_sm <= 1024 && c.fused_cps >= 0 &&
+                       c.fused_cps <= 1024 && c.col_tile >= 0 && c.col_tile <= 1024,
+                   KATZ_EINVAL, "index file: launch shape out of range in " + p);
       g.tuned[t[i]] = c;
     }
   }

@@ -21,6 +21,7 @@ struct SpmmCfg {
   int ctas_per_sm = 8;     // grid = SMs * ctas_per_sm (grid-stride over rows)
   bool pipe = false;       // the pipelined (TMA bulk-copy) kernel measured faster here
   bool pipe_first = false; // ... for the first refinement-residual pass
+  int fused_cps = 0;       // CTAs per SM of the fused Chebyshev / residual kernel (0: ctas_per_sm)
 };
 
 // Y[i,:] = gamma * Z[i,:] + alpha * sum_k A[i,k] X[k,:]   for i < A.nrows.

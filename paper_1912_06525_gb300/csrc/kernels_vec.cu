@@ -422,7 +422,9 @@ void cheb_step(const Csr& A, double beta, double ak, double ck, const float* Xk,
   const int vpt = b > 128 ? 2 : 1;
   const int tile = 128 * vpt;
   const int64_t tiles = ceil_div(b, tile);
-  const int cps = cfg && cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm : 8;
+  const int cps = cfg && cfg->fused_cps > 0     ? cfg->fused_cps
+                  : cfg && cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm
+                                                : 8;
   int64_t ctas = std::min<int64_t>(ceil_div(A.nrows, 8),
                                    std::max<int64_t>(1, int64_t(num_sms()) * cps / tiles));
   dim3 grid((unsigned)std::max<int64_t>(1, ctas), (unsigned)tiles);

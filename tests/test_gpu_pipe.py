@@ -68,6 +68,8 @@ def test_autotune_reports_kernel_choice():
                                 block_max=32, split=False)
     res = katz.katz_autotune(idx, 256)
     assert isinstance(res["cheb_pipe"], bool)
+    assert res["cheb_ctas_per_sm"] in (8, 16, 32, 64, 128)
+    assert res["residual_ctas_per_sm"] in (8, 16, 32, 64, 128)
     q = synth.queries(g.n, 256, seed=5)
     K = torch.zeros((g.n, 256), dtype=torch.float32, device="cuda")
     st, _, _ = katz.katz_query_batch(idx, torch.from_numpy(q).cuda(), K, tol=1e-6)
