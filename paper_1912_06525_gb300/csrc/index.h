@@ -119,6 +119,9 @@ struct katz_index {
   katz::DBuf<float> feat;  // n x 32 node features
   std::vector<double> sigma;
   int lanczos_steps = 0;
+  // an index of disjoint graphs: each graph's rank (its sigma and basis
+  // columns follow one another, graph-major); empty for one graph
+  std::vector<int> seg_rank;
 
   katz::Workspace ws;
 };
@@ -126,6 +129,9 @@ struct katz_index {
 // g independent graphs stored as one block-diagonal CSR (multi-graph batch).
 struct katz_multi {
   int32_t g = 0;
+  // per-graph LRC index over the union with each graph's damping folded
+  // into its weights (beta = 1): built by katz_index_build_many
+  std::unique_ptr<katz_index> lrc;
   int64_t n = 0, nnz = 0;
   int vdt = KATZ_F32;
   std::vector<int64_t> seg_ptr_h;
@@ -145,8 +151,23 @@ struct katz_multi {
 
 namespace katz {
 
-// Host partitioner (Section 3.2, Steps 2-3, with the BFS level-set reading).
-Partition partition_graph(const HostCsr& W, int64_t n_hubs, int64_t block_max, bool split);
+// Host partitioner (Section 3.2, Steps 2-3, with the BFS level-set reading);
+// hub_list, when given, is the hub set instead of the n_hubs largest degrees.
+Partition partition_graph(const HostCsr& W, int64_t n_hubs, int64_t block_max, bool split,
+                          const std::vector<int64_t>* hub_list = nullptr);
+
+// Index of g disjoint graphs stored as one block-diagonal graph: which graph
+// each node belongs to (node ids graph-major), the separator (each graph's
+// own hubs) and each graph's rank of the low-rank correction.  The Schur
+// complement and its correction are then block diagonal: S is formed by
+// column-packed solves (separator node l of every graph shares column l) and
+// Lanczos runs on every graph at once with per-graph scalars.
+struct SegSpec {
+  int32_t G = 0;
+  std::vector<int32_t> node_graph;
+  std::vector<int64_t> hubs;
+  std::vector<int> ranks;
+};
 
 // Largest eigenvalue of W by FP64 Lanczos on the GPU.
 // Largest Ritz value of W after `steps` FP64 Lanczos steps (start: all-ones
@@ -155,7 +176,7 @@ double lambda_max_gpu(const GraphPart& W, int64_t n, int steps, Workspace& ws, c
                       uint64_t seed = 0, double* lmin = nullptr);
 
 void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_build_opts& o,
-                 cudaStream_t s);
+                 cudaStream_t s, const SegSpec* seg = nullptr);
 
 // Versioned binary file of every stored field of an index (device buffers
 // staged through host memory); load validates magic, version, field tags,
@@ -178,11 +199,23 @@ int run_queries(katz_index& idx, bool use_lrc, const int32_t* q_dev, const int32
 template <class VT>
 void apply_M(const katz_index& idx, const VT* X, VT* Y, int b, int64_t ld, cudaStream_t s);
 
+// One FP32 LRC solve D ~ M^{-1} R (Lemma 1, Eqs. 6-7, PCG on S with the
+// preconditioner of Eq. 14) of ld-padded blocks in INDEX order, to relative
+// tolerance tol_rel; per-column iterations in *iters.
+int lrc_solve_f32(katz_index& idx, const float* R, float* D, int b, int64_t ld, double tol_rel,
+                  int max_iter, std::vector<int32_t>* iters, cudaStream_t s);
+
 void multi_build(katz_multi& m, const std::vector<HostCsr>& Ws, const double* betas, int vdt,
                  cudaStream_t s);
+// multi_build plus the per-graph LRC index (hubs per graph in proportion
+// to its size from a total of o.n_hubs; ranks from o.rank / 4 on the
+// smallest graph to o.rank on the largest, log-scaled, capped by the
+// graph's separator)
+void multi_build_lrc(katz_multi& m, const std::vector<HostCsr>& Ws, const double* betas,
+                     const katz_build_opts& o, cudaStream_t s);
 int multi_query(katz_multi& m, const int32_t* q_dev, int qpg, const katz_query_opts& o, void* Kout,
                 int out_dt, int64_t ldk, katz_stats* stats, std::vector<int32_t>& iters,
-                std::vector<double>& relres, cudaStream_t s);
+                std::vector<double>& relres, cudaStream_t s, bool use_lrc = false);
 
 // Sparse-Katz (Algorithm 3) for b queries: ids/rho (device, b x s) get the
 // re-ranked Top-s candidates and their Pearson correlations, land (device,

@@ -121,10 +121,16 @@ struct Bfs {
 };
 }  // namespace
 
-Partition partition_graph(const HostCsr& W, int64_t n_hubs, int64_t block_max, bool split) {
+Partition partition_graph(const HostCsr& W, int64_t n_hubs, int64_t block_max, bool split,
+                          const std::vector<int64_t>* hub_list) {
   const int64_t n = W.nrows;
   std::vector<char> sep(n, 0);
-  if (n_hubs > 0) {
+  if (hub_list) {
+    for (int64_t v : *hub_list) {
+      KATZ_REQUIRE(v >= 0 && v < n, KATZ_EINVAL, "hub id out of range");
+      sep[v] = 1;
+    }
+  } else if (n_hubs > 0) {
     std::vector<int64_t> ord(n);
     std::iota(ord.begin(), ord.end(), 0);
     auto deg = [&](int64_t v) { return W.rowptr[v + 1] - W.rowptr[v]; };
@@ -375,9 +381,287 @@ static unsigned blocks_for(int64_t total) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), int64_t(num_sms()) * 16));
 }
 
+// ------------------------------------- block-diagonal (per-graph) pieces
+// For an index of disjoint graphs: separator rows of graph g are
+// [gsep[g], gsep[g+1]) (node ids graph-major, separator in ascending node
+// order) and sg[p] is the graph of separator row p.
+
+// E[p][l] = 1 for separator rows p whose local index (p - gsep[g]) is l0 + l,
+// l < cw: column l of the packed right-hand side holds the local separator
+// node l0 + l of EVERY graph at once.
+__global__ void packed_identity_kernel(double* E, int64_t ldc, int64_t n2, const int32_t* sg,
+                                       const int64_t* gsep, int l0, int cw) {
+  for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < n2;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t l = p - gsep[sg[p]] - l0;
+    if (l >= 0 && l < cw) E[p * ldc + l] = 1.0;
+  }
+}
+
+// T[p][gsep[g] + l0 + l] = Tp[p][l] for p in graph g (the packed columns
+// back to their places in the block-diagonal n2 x n2 matrix).
+__global__ void packed_scatter_kernel(const double* Tp, int64_t ldc, double* T, int64_t ld2,
+                                      int64_t n2, const int32_t* sg, const int64_t* gsep, int l0,
+                                      int cw) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n2 * cw;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t p = e / cw;
+    const int l = int(e - p * cw);
+    const int g = sg[p];
+    const int64_t q = gsep[g] + l0 + l;
+    if (q < gsep[g + 1]) T[p * ld2 + q] = Tp[p * ldc + l];
+  }
+}
+
+// out[g] = sum over the rows p of graph g of x[p * incx] * y[p * incy]
+// (one CTA of 128 threads per graph, fixed summation order).
+__global__ void segdot_kernel(const double* x, int64_t incx, const double* y, int64_t incy,
+                              const int64_t* gsep, double* out) {
+  __shared__ double red[4];
+  const int g = blockIdx.x;
+  double acc = 0.0;
+  for (int64_t p = gsep[g] + threadIdx.x; p < gsep[g + 1]; p += blockDim.x)
+    acc += x[p * incx] * y[p * incy];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) out[g] = red[0] + red[1] + red[2] + red[3];
+}
+
+// C[k * G + g] = sum over the rows p of graph g of Q[p][k] * u[p], k < kk.
+__global__ void seg_coeff_kernel(const double* Q, int64_t ldq, const double* u,
+                                 const int64_t* gsep, int kk, int G, double* C) {
+  const int g = blockIdx.x;
+  for (int k = threadIdx.x; k < kk; k += blockDim.x) {
+    double acc = 0.0;
+    for (int64_t p = gsep[g]; p < gsep[g + 1]; ++p) acc += Q[p * ldq + k] * u[p];
+    C[int64_t(k) * G + g] = acc;
+  }
+}
+
+// w[p] -= sum_{k < kk} Q[p][k] * C[k * G + g(p)]
+__global__ void seg_reorth_kernel(const double* Q, int64_t ldq, const double* C, int kk, int G,
+                                  const int32_t* sg, int64_t n2, double* w) {
+  for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < n2;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    const int g = sg[p];
+    double acc = 0.0;
+    for (int k = 0; k < kk; ++k) acc += Q[p * ldq + k] * C[int64_t(k) * G + g];
+    w[p] -= acc;
+  }
+}
+
+// Q[p][col] = w[p] * scale[g(p)]
+__global__ void seg_scale_kernel(const double* w, const double* scale, const int32_t* sg,
+                                 int64_t n2, double* Q, int64_t ldq, int col) {
+  for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < n2;
+       p += int64_t(gridDim.x) * blockDim.x)
+    Q[p * ldq + col] = w[p] * scale[sg[p]];
+}
+
+// Stores the basis W_r (host, n2 x rk row-major, W_r^T M22 W_r = I on each
+// graph's block) with idx.sigma: the unscaled FP32 copy, W^ = W_r D^{1/2}
+// (D = diag(sigma / (1 - sigma))) in FP64 / FP32, and the BF16 copies of
+// W^ for the tensor-core products of the preconditioner (Eq. 14).
+static void store_basis(katz_index& idx, std::vector<double>& Wh, int rk, cudaStream_t s) {
+  const int64_t n2 = idx.n2;
+  idx.rank = rk;
+  idx.ldr4 = (rk + 3) / 4 * 4;
+  {
+    std::vector<float> wu(size_t(n2) * idx.ldr4, 0.f);
+    for (int64_t i = 0; i < n2; ++i)
+      for (int c = 0; c < rk; ++c) wu[size_t(i) * idx.ldr4 + c] = float(Wh[size_t(i) * rk + c]);
+    idx.Wr32u.alloc(wu.size());
+    KATZ_CUDA(cudaMemcpyAsync(idx.Wr32u.p, wu.data(), 4 * wu.size(), cudaMemcpyHostToDevice, s));
+    KATZ_CUDA(cudaStreamSynchronize(s));
+  }
+  std::vector<float> Wf(Wh.size());
+  for (int c = 0; c < rk; ++c) {
+    const double sg = std::min(std::max(idx.sigma[c], 0.0), 1.0 - 1e-12);
+    const double f = std::sqrt(sg / (1.0 - sg));
+    for (int64_t i = 0; i < n2; ++i) {
+      Wh[size_t(i) * rk + c] *= f;
+      Wf[size_t(i) * rk + c] = float(Wh[size_t(i) * rk + c]);
+    }
+  }
+  idx.ldr = (rk + 7) / 8 * 8;
+  idx.ldn2 = (n2 + 7) / 8 * 8;
+  std::vector<__nv_bfloat16> wb(size_t(n2) * idx.ldr, __float2bfloat16(0.f)),
+      wbt(size_t(rk) * idx.ldn2, __float2bfloat16(0.f));
+  for (int64_t i = 0; i < n2; ++i)
+    for (int c = 0; c < rk; ++c) {
+      const __nv_bfloat16 v = __double2bfloat16(Wh[size_t(i) * rk + c]);
+      wb[size_t(i) * idx.ldr + c] = v;
+      wbt[size_t(c) * idx.ldn2 + i] = v;
+    }
+  idx.Wb.alloc(wb.size());
+  idx.WbT.alloc(wbt.size());
+  KATZ_CUDA(cudaMemcpyAsync(idx.Wb.p, wb.data(), 2 * wb.size(), cudaMemcpyHostToDevice, s));
+  KATZ_CUDA(cudaMemcpyAsync(idx.WbT.p, wbt.data(), 2 * wbt.size(), cudaMemcpyHostToDevice, s));
+  idx.Wr64.alloc(Wh.size());
+  idx.Wr32.alloc(Wf.size());
+  KATZ_CUDA(cudaMemcpyAsync(idx.Wr64.p, Wh.data(), 8 * Wh.size(), cudaMemcpyHostToDevice, s));
+  KATZ_CUDA(cudaMemcpyAsync(idx.Wr32.p, Wf.data(), 4 * Wf.size(), cudaMemcpyHostToDevice, s));
+  KATZ_CUDA(cudaStreamSynchronize(s));
+}
+
+// Lanczos on every graph's block at once (the same iteration as the
+// single-graph build below, with every scalar kept per graph): on graph g,
+// A_g = M22_g^{-1} T_g in the M22_g inner product, full reorthogonalisation,
+// extended until the top r_g Ritz residuals converge, stopped early when the
+// Krylov space fills the graph's separator.  Returns the basis (host, n2 x
+// sum r_g, graph g's columns at its offset, zero outside its rows) and sets
+// idx.sigma (graph-major).
+static std::vector<double> seg_lanczos(katz_index& idx, const SegSpec& seg,
+                                       const std::vector<int64_t>& gsep_h, const int32_t* sg,
+                                       const int64_t* gsep, const double* T, const double* M22,
+                                       int64_t ld2, uint64_t seed, int lanczos_steps, int* rk_out,
+                                       std::vector<int>* rk_graph, cudaStream_t s) {
+  const int G = seg.G;
+  const int64_t n2 = idx.n2;
+  std::vector<int> r(G), mg(G), capg(G), check(G);
+  int capmax = 0;
+  for (int g = 0; g < G; ++g) {
+    const int64_t ng = gsep_h[g + 1] - gsep_h[g];
+    r[g] = (int)std::min<int64_t>(std::max(0, seg.ranks[g]), ng);
+    int m = lanczos_steps > 0 ? lanczos_steps : std::max(2 * r[g], r[g] + 20);
+    mg[g] = (int)std::min<int64_t>(std::max(m, r[g]), ng);
+    capg[g] = r[g] > 0 ? (int)std::min<int64_t>(ng, std::max(4 * mg[g], mg[g] + 200)) : 0;
+    check[g] = mg[g];
+    capmax = std::max(capmax, capg[g]);
+  }
+  rk_graph->assign(G, 0);
+  *rk_out = 0;
+  idx.sigma.clear();
+  if (capmax == 0) return {};
+  const int64_t ldq = capmax + 1;
+  DBuf<double> Q(size_t(n2) * ldq), t(n2), wv(n2), u(n2), dots(G), C(size_t(ldq) * G),
+      scale(G);
+  KATZ_CUDA(cudaMemsetAsync(Q.p, 0, Q.bytes(), s));
+  std::vector<double> v0 = splitmix64_uniform(seed, n2);
+  KATZ_CUDA(cudaMemcpyAsync(wv.p, v0.data(), 8 * n2, cudaMemcpyHostToDevice, s));
+  std::vector<double> hd(G), hs(G);
+  auto segdot = [&](const double* x, int64_t incx, const double* y) {  // per graph x^T y
+    segdot_kernel<<<G, 128, 0, s>>>(x, incx, y, 1, gsep, dots.p);
+    KATZ_CHECK_LAUNCH();
+    KATZ_CUDA(cudaMemcpyAsync(hd.data(), dots.p, 8 * G, cudaMemcpyDeviceToHost, s));
+    KATZ_CUDA(cudaStreamSynchronize(s));
+    return hd;
+  };
+  auto mdot = [&](const double* x) {  // per graph x^T M22 x
+    gemm<double>(false, n2, 1, n2, 1.0, M22, ld2, x, 1, 0.0, u.p, 1, s);
+    return segdot(x, 1, u.p);
+  };
+  auto put = [&](int col) {
+    KATZ_CUDA(cudaMemcpyAsync(scale.p, hs.data(), 8 * G, cudaMemcpyHostToDevice, s));
+    seg_scale_kernel<<<blocks_for(n2), 256, 0, s>>>(wv.p, scale.p, sg, n2, Q.p, ldq, col);
+    KATZ_CHECK_LAUNCH();
+  };
+  std::vector<char> active(G, 0);
+  {
+    const std::vector<double> nr = mdot(wv.p);
+    for (int g = 0; g < G; ++g) {
+      active[g] = r[g] > 0 && nr[g] > 0;
+      hs[g] = active[g] ? 1.0 / std::sqrt(nr[g]) : 0.0;
+    }
+    put(0);
+  }
+  std::vector<std::vector<double>> al(G), be(G);
+  std::vector<double> ev, Y;
+  for (int j = 0; j < capmax; ++j) {
+    bool any = false;
+    for (int g = 0; g < G; ++g) any |= active[g] != 0;
+    if (!any) break;
+    // t = T q_j ; w = M22^{-1} t ; alpha = q_j^T t
+    gemm<double>(false, n2, 1, n2, 1.0, T, ld2, Q.p + j, ldq, 0.0, t.p, 1, s);
+    gemm<double>(false, n2, 1, n2, 1.0, idx.M22inv64.p, ld2, t.p, 1, 0.0, wv.p, 1, s);
+    const std::vector<double> a = segdot(Q.p + j, ldq, t.p);
+    for (int g = 0; g < G; ++g)
+      if (active[g]) al[g].push_back(a[g]);
+    for (int pass = 0; pass < 2; ++pass) {
+      gemm<double>(false, n2, 1, n2, 1.0, M22, ld2, wv.p, 1, 0.0, u.p, 1, s);
+      seg_coeff_kernel<<<G, 128, 0, s>>>(Q.p, ldq, u.p, gsep, j + 1, G, C.p);
+      KATZ_CHECK_LAUNCH();
+      seg_reorth_kernel<<<blocks_for(n2), 256, 0, s>>>(Q.p, ldq, C.p, j + 1, G, sg, n2, wv.p);
+      KATZ_CHECK_LAUNCH();
+    }
+    const std::vector<double> bsq = mdot(wv.p);
+    for (int g = 0; g < G; ++g) {
+      hs[g] = 0.0;
+      if (!active[g]) continue;
+      const int64_t ng = gsep_h[g + 1] - gsep_h[g];
+      const double bj = std::sqrt(std::max(0.0, bsq[g]));
+      const int kk = (int)al[g].size();
+      bool stop = bj <= 1e-14 * std::max(1.0, std::fabs(al[g].back())) || kk >= ng;
+      if (!stop && (kk >= check[g] || kk == capg[g])) {
+        ev = al[g];
+        tridiag_ql(ev, be[g], Y, kk);
+        std::vector<int> o2(kk);
+        std::iota(o2.begin(), o2.end(), 0);
+        std::sort(o2.begin(), o2.end(), [&](int x, int y) { return ev[x] > ev[y]; });
+        bool ok = true;
+        for (int c = 0; c < std::min(r[g], kk); ++c)
+          ok &= bj * std::fabs(Y[size_t(kk - 1) * kk + o2[c]]) <=
+                1e-8 * std::max(1.0, std::fabs(ev[o2[c]]));
+        if (ok || kk == capg[g]) stop = true;
+        else check[g] = kk + std::max(10, kk / 2);
+      }
+      if (stop) {
+        active[g] = 0;
+      } else {
+        be[g].push_back(bj);
+        hs[g] = 1.0 / bj;
+      }
+    }
+    put(j + 1);
+  }
+  // Ritz vectors per graph: W_g = Q_g Y_g (top r_g)
+  std::vector<double> Qh(size_t(n2) * ldq);
+  KATZ_CUDA(cudaMemcpyAsync(Qh.data(), Q.p, 8 * Qh.size(), cudaMemcpyDeviceToHost, s));
+  KATZ_CUDA(cudaStreamSynchronize(s));
+  std::vector<std::vector<double>> Ysel(G);
+  std::vector<int> off(G + 1, 0);
+  for (int g = 0; g < G; ++g) {
+    const int k = (int)al[g].size();
+    int rk = 0;
+    if (r[g] > 0 && k > 0) {
+      ev = al[g];
+      std::vector<double> sub(be[g].begin(), be[g].begin() + std::max(0, k - 1));
+      tridiag_ql(ev, sub, Y, k);
+      std::vector<int> ord(k);
+      std::iota(ord.begin(), ord.end(), 0);
+      std::sort(ord.begin(), ord.end(), [&](int x, int y) { return ev[x] > ev[y]; });
+      rk = std::min(r[g], k);
+      Ysel[g].assign(size_t(k) * rk, 0.0);
+      for (int c = 0; c < rk; ++c) {
+        idx.sigma.push_back(ev[ord[c]]);
+        for (int i = 0; i < k; ++i) Ysel[g][size_t(i) * rk + c] = Y[size_t(i) * k + ord[c]];
+      }
+    }
+    (*rk_graph)[g] = rk;
+    off[g + 1] = off[g] + rk;
+  }
+  const int rk_tot = off[G];
+  *rk_out = rk_tot;
+  std::vector<double> Wh(size_t(n2) * rk_tot, 0.0);
+  for (int g = 0; g < G; ++g) {
+    const int rk = (*rk_graph)[g];
+    const int k = (int)al[g].size();
+    for (int64_t p = gsep_h[g]; p < gsep_h[g + 1]; ++p)
+      for (int c = 0; c < rk; ++c) {
+        double acc = 0.0;
+        for (int i = 0; i < k; ++i) acc += Qh[size_t(p) * ldq + i] * Ysel[g][size_t(i) * rk + c];
+        Wh[size_t(p) * rk_tot + off[g] + c] = acc;
+      }
+  }
+  idx.lanczos_steps = 0;
+  for (int g = 0; g < G; ++g) idx.lanczos_steps = std::max(idx.lanczos_steps, (int)al[g].size());
+  return Wh;
+}
+
 // ------------------------------------------------------------- build
 void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_build_opts& o,
-                 cudaStream_t s) {
+                 cudaStream_t s, const SegSpec* seg) {
   idx.n = W.nrows;
   idx.nnz = W.nnz();
   idx.beta = beta;
@@ -408,12 +692,41 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   KATZ_REQUIRE(idx.block_max <= 128, KATZ_EINVAL, "block_max must be <= 128");
   const int64_t n2_max = o.n2_max > 0 ? o.n2_max : 16384;
   Partition& P = idx.part;
-  P = partition_graph(W, std::max(0, o.n_hubs), idx.block_max, o.split != 0);
+  P = partition_graph(W, std::max(0, o.n_hubs), idx.block_max, o.split != 0,
+                      seg ? &seg->hubs : nullptr);
   const int64_t n = idx.n, n1 = P.n1, n2 = P.n2;
   idx.n1 = n1;
   idx.n2 = n2;
   KATZ_REQUIRE(n2 <= n2_max, KATZ_EINVAL,
                "separator has " + std::to_string(n2) + " nodes > n2_max " + std::to_string(n2_max));
+  // disjoint graphs: each graph's separator rows (contiguous, graph-major)
+  std::vector<int64_t> gsep_h;
+  DBuf<int32_t> sg_d;
+  DBuf<int64_t> gsep_d;
+  int64_t width = 0;  // largest separator of one graph
+  if (seg) {
+    KATZ_REQUIRE((int64_t)seg->node_graph.size() == n && seg->G > 0, KATZ_EINVAL,
+                 "segment map does not match the graph");
+    gsep_h.assign(seg->G + 1, 0);
+    std::vector<int32_t> sgh(std::max<int64_t>(n2, 1), 0);
+    int32_t prev = -1;
+    for (int64_t p = 0; p < n2; ++p) {
+      const int32_t g = seg->node_graph[P.perm[P.n1 + p]];
+      KATZ_REQUIRE(g >= prev, KATZ_EINVAL, "graph ids must be graph-major");
+      prev = g;
+      sgh[p] = g;
+      gsep_h[g + 1]++;
+    }
+    for (int g = 0; g < seg->G; ++g) {
+      width = std::max(width, gsep_h[g + 1]);
+      gsep_h[g + 1] += gsep_h[g];
+    }
+    sg_d.alloc(sgh.size());
+    gsep_d.alloc(gsep_h.size());
+    KATZ_CUDA(cudaMemcpyAsync(sg_d.p, sgh.data(), 4 * sgh.size(), cudaMemcpyHostToDevice, s));
+    KATZ_CUDA(cudaMemcpyAsync(gsep_d.p, gsep_h.data(), 8 * gsep_h.size(), cudaMemcpyHostToDevice,
+                              s));
+  }
   std::vector<int32_t> iperm(n), perm32(n);
   for (int64_t i = 0; i < n; ++i) {
     perm32[i] = (int32_t)P.perm[i];
@@ -576,7 +889,7 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
       const double bytes = 2.0 * 4.0 * double(n1) * double(idx.ldH);
       // automatic: where the cost model favours the product at the FP32
       // inner tolerance (2e-6) and the parts fit
-      idx.has_h = n1 > 0 && (o.coupling_gemm > 0 ||
+      idx.has_h = !seg && n1 > 0 && (o.coupling_gemm > 0 ||
                              (o.coupling_gemm == 0 && coupling_gemm_pays(idx, 1024, 2e-6) &&
                               bytes <= double(total_b) / 3.0 && bytes <= 0.8 * double(free_b)));
     }
@@ -584,7 +897,27 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
       idx.Hh.alloc(size_t(n1) * idx.ldH);
       idx.Hl.alloc(size_t(n1) * idx.ldH);
     }
-    for (int64_t j0 = 0; j0 < n2; j0 += cw_max) {
+    // disjoint graphs: packed columns, T_g of every graph from one solve of
+    // width (largest separator), scattered back to the block diagonal
+    for (int64_t l0 = 0; seg && l0 < width; l0 += cw_max) {
+      const int cw = (int)std::min<int64_t>(cw_max, width - l0);
+      if (n1 == 0) break;
+      KATZ_CUDA(cudaMemsetAsync(E.p, 0, E.bytes(), s));
+      packed_identity_kernel<<<blocks_for(n2), 256, 0, s>>>(E.p, ldc, n2, sg_d.p, gsep_d.p,
+                                                            (int)l0, cw);
+      KATZ_CHECK_LAUNCH();
+      KATZ_CUDA(cudaMemsetAsync(U.p, 0, U.bytes(), s));
+      spmm<double>(idx.W12.view(), idx.W12.heavy.p, idx.W12.n_heavy, beta, E.p, ldc, 0.0, nullptr,
+                   ldc, U.p, ldc, cw, nullptr, 0, nullptr, s);
+      const int st = m11_solve<double>(idx, U.p, V.p, cw, ldc, 1e-14, 5000, nullptr, s);
+      KATZ_REQUIRE(st != KATZ_ENOTSPD, KATZ_ENOTSPD, "M11 is not positive definite");
+      spmm<double>(idx.W21.view(), idx.W21.heavy.p, idx.W21.n_heavy, beta, V.p, ldc, 0.0, nullptr,
+                   ldc, E.p, ldc, cw, nullptr, 0, nullptr, s);
+      packed_scatter_kernel<<<blocks_for(n2 * cw), 256, 0, s>>>(E.p, ldc, T.p, ld2, n2, sg_d.p,
+                                                                gsep_d.p, (int)l0, cw);
+      KATZ_CHECK_LAUNCH();
+    }
+    for (int64_t j0 = 0; !seg && j0 < n2; j0 += cw_max) {
       const int cw = (int)std::min<int64_t>(cw_max, n2 - j0);
       if (n1 == 0) break;
       KATZ_CUDA(cudaMemsetAsync(E.p, 0, E.bytes(), s));
@@ -624,7 +957,7 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   // keep S and M22^{-1} as TF32 parts for the tensor cores (their ~2^-22
   // rounding in S P costs the PCG about one iteration on hard problems,
   // which only pays when the products are a large share of the solve)
-  idx.dense_tc = n2 >= 4096;
+  idx.dense_tc = !seg && n2 >= 4096;
   if (idx.dense_tc) {
     for (auto* d : {&idx.Sh, &idx.Sl, &idx.Mh, &idx.Ml}) d->alloc(size_t(n2) * ld2);
     split_tf32<double>(idx.S64.p, ld2, n2, int(n2), idx.Sh.p, idx.Sl.p, ld2, s);
@@ -642,6 +975,16 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   // Ritz vector u of R, w = L^{-T} u directly (w^T M22 w = 1).  L itself is
   // never formed.  Full reorthogonalisation (two Gram-Schmidt passes).
   idx.sigma.clear();
+  if (seg && idx.rank > 0) {
+    int rk = 0;
+    std::vector<int> rkg;
+    std::vector<double> Wh = seg_lanczos(idx, *seg, gsep_h, sg_d.p, gsep_d.p, T.p, M22.p, ld2,
+                                         o.seed, o.lanczos_steps, &rk, &rkg, s);
+    idx.seg_rank = rkg;
+    if (rk > 0) store_basis(idx, Wh, rk, s);
+    else idx.rank = 0;
+    return;
+  }
   if (idx.rank > 0) {
     const int r = (int)std::min<int64_t>(idx.rank, n2);
     int m = o.lanczos_steps > 0 ? o.lanczos_steps : std::max(2 * r, r + 20);
@@ -717,46 +1060,7 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
     std::vector<double> Wh(size_t(n2) * rk);
     KATZ_CUDA(cudaMemcpyAsync(Wh.data(), Wd.p, 8 * Wh.size(), cudaMemcpyDeviceToHost, s));
     KATZ_CUDA(cudaStreamSynchronize(s));
-    // unscaled basis (warm start features and targets)
-    idx.ldr4 = (rk + 3) / 4 * 4;
-    {
-      std::vector<float> wu(size_t(n2) * idx.ldr4, 0.f);
-      for (int64_t i = 0; i < n2; ++i)
-        for (int c = 0; c < rk; ++c) wu[size_t(i) * idx.ldr4 + c] = float(Wh[size_t(i) * rk + c]);
-      idx.Wr32u.alloc(wu.size());
-      KATZ_CUDA(cudaMemcpyAsync(idx.Wr32u.p, wu.data(), 4 * wu.size(), cudaMemcpyHostToDevice, s));
-      KATZ_CUDA(cudaStreamSynchronize(s));
-    }
-    // fold D = diag(sigma/(1-sigma)) in: W^ = W D^{1/2}
-    std::vector<float> Wf(Wh.size());
-    for (int c = 0; c < rk; ++c) {
-      const double sg = std::min(std::max(idx.sigma[c], 0.0), 1.0 - 1e-12);
-      const double f = std::sqrt(sg / (1.0 - sg));
-      for (int64_t i = 0; i < n2; ++i) {
-        Wh[size_t(i) * rk + c] *= f;
-        Wf[size_t(i) * rk + c] = float(Wh[size_t(i) * rk + c]);
-      }
-    }
-    // BF16 copies for the tensor-core products
-    idx.ldr = (rk + 7) / 8 * 8;
-    idx.ldn2 = (n2 + 7) / 8 * 8;
-    std::vector<__nv_bfloat16> wb(size_t(n2) * idx.ldr, __float2bfloat16(0.f)),
-        wbt(size_t(rk) * idx.ldn2, __float2bfloat16(0.f));
-    for (int64_t i = 0; i < n2; ++i)
-      for (int c = 0; c < rk; ++c) {
-        const __nv_bfloat16 v = __double2bfloat16(Wh[size_t(i) * rk + c]);
-        wb[size_t(i) * idx.ldr + c] = v;
-        wbt[size_t(c) * idx.ldn2 + i] = v;
-      }
-    idx.Wb.alloc(wb.size());
-    idx.WbT.alloc(wbt.size());
-    KATZ_CUDA(cudaMemcpyAsync(idx.Wb.p, wb.data(), 2 * wb.size(), cudaMemcpyHostToDevice, s));
-    KATZ_CUDA(cudaMemcpyAsync(idx.WbT.p, wbt.data(), 2 * wbt.size(), cudaMemcpyHostToDevice, s));
-    idx.Wr64.alloc(Wh.size());
-    idx.Wr32.alloc(Wf.size());
-    KATZ_CUDA(cudaMemcpyAsync(idx.Wr64.p, Wh.data(), 8 * Wh.size(), cudaMemcpyHostToDevice, s));
-    KATZ_CUDA(cudaMemcpyAsync(idx.Wr32.p, Wf.data(), 4 * Wf.size(), cudaMemcpyHostToDevice, s));
-    KATZ_CUDA(cudaStreamSynchronize(s));
+    store_basis(idx, Wh, rk, s);
   }
 }
 

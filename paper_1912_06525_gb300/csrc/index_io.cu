@@ -318,6 +318,7 @@ void serialize(Archive& a, katz_index& x) {
   a.dbuf("feat", x.feat);
   a.vec("sigma", x.sigma);
   a.scalar("lanczos_steps", x.lanczos_steps);
+  a.vec("seg_rank", x.seg_rank);
   a.end();
 }
 

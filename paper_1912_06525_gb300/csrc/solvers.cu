@@ -883,6 +883,11 @@ int run_queries(katz_index& idx, bool use_lrc, const int32_t* q_dev, const int32
   return status;
 }
 
+int lrc_solve_f32(katz_index& idx, const float* R, float* D, int b, int64_t ld, double tol_rel,
+                  int max_iter, std::vector<int32_t>* iters, cudaStream_t s) {
+  return lrc_solve<float>(idx, R, D, b, ld, tol_rel, tol_rel, max_iter, iters, s);
+}
+
 int run_queries_internal(katz_index& idx, const int32_t* q_dev, const int32_t* q_host, int b,
                          const katz_query_opts& o, void* Kout, int out_dt, int64_t ldk,
                          cudaStream_t s) {
