@@ -380,6 +380,34 @@ int katz_multi_build(int32_t g, const katz_csr* Ws, const double* betas, int32_t
 
 void katz_multi_free(katz_multi* m);
 
+/* The same g graphs with a per-graph LRC index (Algorithm 1 on every graph
+ * at once).  The graphs form one block-diagonal graph whose weights carry
+ * each graph's damping (W~ = beta_g W_g on graph g's block, beta = 1), so
+ * M = I - W~ and its Schur complement are block diagonal:
+ *   - separator: each graph's own highest-degree nodes (ties: smaller id),
+ *     max(1, round(opts->n_hubs * n_g / sum n)) of them (opts->n_hubs = 0:
+ *     min(8192, sum n / 1000), at least g); every other component is an
+ *     M11 block (dense inverse, or Chebyshev if larger than block_max);
+ *   - S_g for all graphs from one column-packed M11 solve (separator node l
+ *     of every graph shares column l), stored as the block-diagonal S;
+ *   - rank r_g per graph, log-scaled from opts->rank / 4 (smallest graph)
+ *     to opts->rank (largest; 0 = 32), capped by the graph's separator:
+ *     Lanczos on every graph's block at once with per-graph scalars.
+ * opts->value_dtype: KATZ_UNIT, KATZ_F32 or KATZ_BF16 (as katz_multi_build;
+ * the index stores the scaled weights in FP32).  opts->split,
+ * lanczos_steps, seed as for katz_index_build; n2_max is raised to the
+ * separator size.  Both katz_multi_query (CG) and katz_multi_query_lrc run
+ * on the result.  KATZ_ENOTSPD if some beta_g * lambda_g >= 1. */
+int katz_index_build_many(int32_t g, const katz_csr* Ws, const double* betas,
+                          const katz_build_opts* opts, void* stream, katz_multi** out);
+
+/* Per-graph shape of an index from katz_index_build_many (host outputs, any
+ * may be NULL): n2_out[g] separator size, ranks_out[g] rank r_g,
+ * sigma_out[sum r_g] the Ritz values of R_g (Eq. 11), graph-major,
+ * descending within a graph.  KATZ_EINVAL without the LRC part. */
+int katz_multi_get_info(const katz_multi* m, int64_t* n2_out, int32_t* ranks_out,
+                        double* sigma_out);
+
 /* qpg queries of every graph (Eq. 3 per graph), solved together: one
  * multi-RHS CG on the block-diagonal system with per-(graph, query) CG
  * scalars and stopping, the iteration sequence captured once in a CUDA graph
@@ -391,6 +419,18 @@ void katz_multi_free(katz_multi* m);
 int katz_multi_query(const katz_multi* m, const int32_t* q, int32_t qpg,
                      const katz_query_opts* opts, void* K_out, int32_t out_dtype, int64_t ldk,
                      katz_stats* stats, int32_t* iters_out, double* rel_res_out, void* stream);
+
+/* katz_multi_query with the per-graph LRC solve (Algorithm 2 per graph, all
+ * graphs in every launch) as the inner solver of the same float-float
+ * residual refinement and per-(graph, query) stopping.  The inner PCG on
+ * the block-diagonal S shares its scalars across a column's graphs (the
+ * refinement decides each pair on its own residual).  Same arguments and
+ * outputs; iters_out counts inner PCG iterations.  KATZ_EINVAL if m was not
+ * built by katz_index_build_many. */
+int katz_multi_query_lrc(const katz_multi* m, const int32_t* q, int32_t qpg,
+                         const katz_query_opts* opts, void* K_out, int32_t out_dtype, int64_t ldk,
+                         katz_stats* stats, int32_t* iters_out, double* rel_res_out,
+                         void* stream);
 
 /* ---------------------------------------------------------- measurement */
 

@@ -451,11 +451,58 @@ int katz_multi_build(int32_t g, const katz_csr* Ws, const double* betas, int32_t
   });
 }
 
+int katz_index_build_many(int32_t g, const katz_csr* Ws, const double* betas,
+                          const katz_build_opts* opts, void* stream, katz_multi** out) {
+  return guarded([&]() {
+    KATZ_REQUIRE(out && Ws && betas && opts && g > 0, KATZ_EINVAL, "bad multi-graph arguments");
+    *out = nullptr;
+    std::vector<katz::HostCsr> hs;
+    hs.reserve(g);
+    for (int32_t i = 0; i < g; ++i) {
+      hs.push_back(read_csr(&Ws[i]));
+      if (opts->value_dtype == KATZ_UNIT)
+        for (double v : hs.back().val)
+          KATZ_REQUIRE(v == 1.0, KATZ_EINVAL, "value_dtype UNIT needs all weights equal to 1");
+    }
+    auto* m = new katz_multi();
+    try {
+      katz::multi_build_lrc(*m, hs, betas, *opts, static_cast<cudaStream_t>(stream));
+    } catch (...) {
+      delete m;
+      throw;
+    }
+    *out = m;
+    return KATZ_OK;
+  });
+}
+
+int katz_multi_get_info(const katz_multi* m, int64_t* n2_out, int32_t* ranks_out,
+                        double* sigma_out) {
+  return guarded([&]() {
+    KATZ_REQUIRE(m && m->lrc, KATZ_EINVAL, "multi-graph index has no LRC part");
+    const katz_index& L = *m->lrc;
+    std::vector<int64_t> n2g(m->g, 0);
+    for (int64_t p = 0; p < L.n2; ++p) {
+      const int64_t node = L.part.perm[L.n1 + p];
+      const int32_t gi = int32_t(std::upper_bound(m->seg_ptr_h.begin(), m->seg_ptr_h.end(), node) -
+                                 m->seg_ptr_h.begin()) - 1;
+      n2g[gi]++;
+    }
+    if (n2_out) std::memcpy(n2_out, n2g.data(), 8 * n2g.size());
+    if (ranks_out)
+      for (int32_t gi = 0; gi < m->g; ++gi)
+        ranks_out[gi] = gi < (int32_t)L.seg_rank.size() ? L.seg_rank[gi] : 0;
+    if (sigma_out && !L.sigma.empty()) std::memcpy(sigma_out, L.sigma.data(), 8 * L.sigma.size());
+    return KATZ_OK;
+  });
+}
+
 void katz_multi_free(katz_multi* m) { delete m; }
 
-int katz_multi_query(const katz_multi* cm, const int32_t* q, int32_t qpg,
-                     const katz_query_opts* opts, void* K_out, int32_t out_dtype, int64_t ldk,
-                     katz_stats* stats, int32_t* iters_out, double* rel_res_out, void* stream) {
+static int multi_query_api(const katz_multi* cm, const int32_t* q, int32_t qpg,
+                           const katz_query_opts* opts, void* K_out, int32_t out_dtype,
+                           int64_t ldk, katz_stats* stats, int32_t* iters_out,
+                           double* rel_res_out, void* stream, bool use_lrc) {
   return guarded([&]() {
     KATZ_REQUIRE(cm && q && opts && K_out && qpg > 0 && qpg <= 64, KATZ_EINVAL, "bad arguments");
     KATZ_REQUIRE(out_dtype == KATZ_F32 || out_dtype == KATZ_F64, KATZ_EINVAL, "out_dtype");
@@ -483,7 +530,8 @@ int katz_multi_query(const katz_multi* cm, const int32_t* q, int32_t qpg,
     void* Kd = dev ? K_out : m->ws.get<uint8_t>("api.K", es * size_t(m->n) * ldk);
     std::vector<int32_t> it;
     std::vector<double> rr;
-    const int st = katz::multi_query(*m, qd, qpg, *opts, Kd, out_dtype, ldk, stats, it, rr, s);
+    const int st =
+        katz::multi_query(*m, qd, qpg, *opts, Kd, out_dtype, ldk, stats, it, rr, s, use_lrc);
     if (!dev && (st == KATZ_OK || st == KATZ_ENOCONV)) {
       KATZ_CUDA(cudaMemcpyAsync(K_out, Kd, es * size_t(m->n) * ldk, cudaMemcpyDeviceToHost, s));
       KATZ_CUDA(cudaStreamSynchronize(s));
@@ -494,6 +542,21 @@ int katz_multi_query(const katz_multi* cm, const int32_t* q, int32_t qpg,
     if (st == KATZ_ENOTSPD) g_last_error = "CG breakdown: p^T A p <= 0";
     return st;
   });
+}
+
+int katz_multi_query(const katz_multi* m, const int32_t* q, int32_t qpg,
+                     const katz_query_opts* opts, void* K_out, int32_t out_dtype, int64_t ldk,
+                     katz_stats* stats, int32_t* iters_out, double* rel_res_out, void* stream) {
+  return multi_query_api(m, q, qpg, opts, K_out, out_dtype, ldk, stats, iters_out, rel_res_out,
+                         stream, false);
+}
+
+int katz_multi_query_lrc(const katz_multi* m, const int32_t* q, int32_t qpg,
+                         const katz_query_opts* opts, void* K_out, int32_t out_dtype, int64_t ldk,
+                         katz_stats* stats, int32_t* iters_out, double* rel_res_out,
+                         void* stream) {
+  return multi_query_api(m, q, qpg, opts, K_out, out_dtype, ldk, stats, iters_out, rel_res_out,
+                         stream, true);
 }
 
 int katz_autotune(katz_index* idx, int32_t b, int32_t* out, double* ms, void* stream) {

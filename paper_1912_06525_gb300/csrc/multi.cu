@@ -15,6 +15,8 @@
 // single graph.
 #include <chrono>
 #include <cmath>
+#include <numeric>
+#include <algorithm>
 
 #include "index.h"
 
@@ -301,6 +303,20 @@ __global__ void seg_out_kernel(const float* Kh, const float* Kl, int64_t ld, int
   }
 }
 
+// Y[pos[i]] = X[i] (to index order) or Y[i] = X[pos[i]] (back), ld columns.
+__global__ void permute_rows_kernel(const float* __restrict__ X, float* __restrict__ Y,
+                                    const int32_t* __restrict__ pos, int64_t n, int64_t ld,
+                                    bool to_index) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n * ld;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / ld, c = e - i * ld;
+    if (to_index)
+      Y[int64_t(pos[i]) * ld + c] = X[e];
+    else
+      Y[e] = X[int64_t(pos[i]) * ld + c];
+  }
+}
+
 unsigned flat(int64_t total) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), int64_t(num_sms()) * 16));
 }
@@ -366,6 +382,69 @@ void multi_build(katz_multi& m, const std::vector<HostCsr>& Ws, const double* be
   KATZ_CUDA(cudaMemcpyAsync(m.bseg64.p, betas, 8 * m.g, cudaMemcpyHostToDevice, s));
   KATZ_CUDA(cudaStreamSynchronize(s));
   KATZ_CUDA(cudaStreamCreateWithFlags(&m.cap_stream, cudaStreamNonBlocking));
+}
+
+void multi_build_lrc(katz_multi& m, const std::vector<HostCsr>& Ws, const double* betas,
+                     const katz_build_opts& o, cudaStream_t s) {
+  KATZ_REQUIRE(o.value_dtype == KATZ_UNIT || o.value_dtype == KATZ_F32 ||
+                   o.value_dtype == KATZ_BF16, KATZ_EINVAL,
+               "multi-graph values must be UNIT, F32 or BF16 (exact in FP32)");
+  multi_build(m, Ws, betas, o.value_dtype, s);
+  const int G = m.g;
+  // the union with each graph's damping folded into its weights: M = I - W~,
+  // W~ = beta_g W_g on graph g's block (beta = 1 for the index)
+  HostCsr U;
+  U.nrows = U.ncols = m.n;
+  U.rowptr.assign(1, 0);
+  SegSpec seg;
+  seg.G = G;
+  seg.node_graph.resize(m.n);
+  int64_t n_min = INT64_MAX, n_max = 0;
+  for (int g = 0; g < G; ++g) {
+    const HostCsr& w = Ws[g];
+    const int64_t off = m.seg_ptr_h[g];
+    n_min = std::min(n_min, w.nrows);
+    n_max = std::max(n_max, w.nrows);
+    for (int64_t i = 0; i < w.nrows; ++i) {
+      for (int64_t k = w.rowptr[i]; k < w.rowptr[i + 1]; ++k) {
+        U.col.push_back((int32_t)(w.col[k] + off));
+        U.val.push_back(betas[g] * (w.val.empty() ? 1.0 : w.val[k]));
+      }
+      U.rowptr.push_back((int64_t)U.col.size());
+      seg.node_graph[off + i] = g;
+    }
+  }
+  // hubs: the largest degrees of each graph (ties: smaller id), a share of
+  // the separator budget in proportion to the graph's size, at least one
+  const int64_t budget =
+      o.n_hubs > 0 ? o.n_hubs : std::max<int64_t>(G, std::min<int64_t>(8192, m.n / 1000));
+  const int r_hi = o.rank > 0 ? o.rank : 32, r_lo = std::max(1, r_hi / 4);
+  seg.ranks.resize(G);
+  for (int g = 0; g < G; ++g) {
+    const HostCsr& w = Ws[g];
+    const int64_t ng = w.nrows;
+    int64_t h = std::max<int64_t>(1, (int64_t)std::llround(double(budget) * ng / double(m.n)));
+    h = std::min<int64_t>(h, std::max<int64_t>(0, ng - 1));
+    std::vector<int64_t> ord(ng);
+    std::iota(ord.begin(), ord.end(), 0);
+    auto deg = [&](int64_t v) { return w.rowptr[v + 1] - w.rowptr[v]; };
+    std::partial_sort(ord.begin(), ord.begin() + h, ord.end(), [&](int64_t a, int64_t b) {
+      return deg(a) != deg(b) ? deg(a) > deg(b) : a < b;
+    });
+    for (int64_t i = 0; i < h; ++i) seg.hubs.push_back(m.seg_ptr_h[g] + ord[i]);
+    const double t = n_max > n_min ? std::log(double(ng) / n_min) / std::log(double(n_max) / n_min)
+                                   : 1.0;
+    seg.ranks[g] = (int)std::min<int64_t>(h, std::llround(r_lo + (r_hi - r_lo) * t));
+  }
+  katz_build_opts bo = o;
+  bo.value_dtype = KATZ_F32;
+  bo.build_lrc = 1;
+  bo.rank = r_hi;
+  bo.n_hubs = 0;
+  bo.coupling_gemm = -1;
+  bo.n2_max = std::max<int64_t>(o.n2_max, (int64_t)seg.hubs.size());
+  m.lrc.reset(new katz_index());
+  build_index(*m.lrc, U, 1.0, bo, s, &seg);
 }
 
 namespace {
@@ -478,7 +557,9 @@ int seg_cg(katz_multi& m, const float* B, float* X, int64_t ld, int b, const dou
 
 int multi_query(katz_multi& m, const int32_t* q_dev, int qpg, const katz_query_opts& o, void* Kout,
                 int out_dt, int64_t ldk, katz_stats* stats, std::vector<int32_t>& iters,
-                std::vector<double>& relres, cudaStream_t s) {
+                std::vector<double>& relres, cudaStream_t s, bool use_lrc) {
+  KATZ_REQUIRE(!use_lrc || m.lrc, KATZ_EINVAL,
+               "LRC multi-graph queries need an index built by katz_index_build_many");
   using clk = std::chrono::steady_clock;
   const auto t0 = clk::now();
   KATZ_REQUIRE(qpg > 0 && qpg <= 64, KATZ_EINVAL, "queries per graph must be in [1, 64]");
@@ -531,9 +612,32 @@ int multi_query(katz_multi& m, const int32_t* q_dev, int qpg, const katz_query_o
   seg_inner_kernel<<<1, 1024, 0, s>>>(bn2, thr2, tau, total, conv, thr2_in, nopen);
   KATZ_CHECK_LAUNCH();
   int replays = 0;
-  int status = seg_cg(m, R, Kh, ld, b, thr2_in, max_iter, &replays, s);
   std::vector<int32_t> it_acc(total, 0);
+  // the per-graph LRC solve of all graphs at once (the union index), in its
+  // index order; its PCG stops each column at relative tolerance tol_rel
+  std::vector<int32_t> lit;
+  auto lrc_inner = [&](const float* Rn, float* Xn, double tol_rel) {
+    katz_index& L = *m.lrc;
+    float* Rp = m.ws.get<float>("ml.Rp", size_t(m.n) * ld);
+    float* Dp = m.ws.get<float>("ml.Dp", size_t(m.n) * ld);
+    permute_rows_kernel<<<flat(m.n * ld), 256, 0, s>>>(Rn, Rp, L.iperm.p, m.n, ld, true);
+    KATZ_CHECK_LAUNCH();
+    lit.clear();
+    const int st = lrc_solve_f32(L, Rp, Dp, b, ld, tol_rel, max_iter, &lit, s);
+    permute_rows_kernel<<<flat(m.n * ld), 256, 0, s>>>(Dp, Xn, L.iperm.p, m.n, ld, false);
+    KATZ_CHECK_LAUNCH();
+    for (int g = 0; g < m.g; ++g)
+      for (int c = 0; c < b && c < (int)lit.size(); ++c) it_acc[size_t(g) * b + c] += lit[c];
+    return st;
+  };
+  double omc_min = 1.0;
+  for (double v : omc) omc_min = std::min(omc_min, v);
+  double tol_first = (o.tol_kind == KATZ_TOL_RESIDUAL) ? o.tol : o.tol * omc_min;
+  tol_first = std::max(0.3 * tol_first, tau);
+  int status = use_lrc ? lrc_inner(R, Kh, tol_first)
+                       : seg_cg(m, R, Kh, ld, b, thr2_in, max_iter, &replays, s);
   auto harvest = [&]() {
+    if (use_lrc) return;
     std::vector<int32_t> h(total);
     KATZ_CUDA(cudaMemcpyAsync(h.data(), m.ws.get<int>("m.it", total), 4 * size_t(total),
                               cudaMemcpyDeviceToHost, s));
@@ -565,7 +669,18 @@ int multi_query(katz_multi& m, const int32_t* q_dev, int qpg, const katz_query_o
       if (refine > max_refine) { status = KATZ_ENOCONV; break; }
       seg_mask_kernel<<<flat(m.n * ld), 256, 0, s>>>(R, ld, m.n, b, m.seg.p, conv, b);
       KATZ_CHECK_LAUNCH();
-      const int st = seg_cg(m, R, D, ld, b, thr2_in, max_iter, &replays, s);
+      double tol_step = 1.0;
+      if (use_lrc) {  // tightest 0.3 * thr / ||r|| over the open pairs
+        std::vector<double> hr(total), ht(total);
+        KATZ_CUDA(cudaMemcpyAsync(hr.data(), rr, 8 * size_t(total), cudaMemcpyDeviceToHost, s));
+        KATZ_CUDA(cudaMemcpyAsync(ht.data(), thr2, 8 * size_t(total), cudaMemcpyDeviceToHost, s));
+        KATZ_CUDA(cudaStreamSynchronize(s));
+        for (int k = 0; k < total; ++k)
+          if (hr[k] > ht[k] && hr[k] > 0) tol_step = std::min(tol_step, 0.3 * std::sqrt(ht[k] / hr[k]));
+        tol_step = std::max(tol_step, tau);
+      }
+      const int st = use_lrc ? lrc_inner(R, D, tol_step)
+                             : seg_cg(m, R, D, ld, b, thr2_in, max_iter, &replays, s);
       harvest();
       if (st == KATZ_ENOTSPD) { status = st; break; }
       seg_ff_add_kernel<<<flat(m.n * ld), 256, 0, s>>>(Kh, Kl, D, m.n * ld);

@@ -33,7 +33,8 @@ EXPORTS = ["katz_lambda_max", "katz_index_build", "katz_index_free", "katz_index
            "linkpred_topk_noalloc", "sparse_katz_topk", "katz_apply_M", "katz_autotune", "katz_gemm_bf16",
            "katz_gemm_tf32x3", "katz_launch_count",
            "katz_profile_enable", "katz_profile_read", "katz_multi_build", "katz_multi_free",
-           "katz_multi_query", "katz_warmstart_train", "katz_mlp_loss_grad", "katz_last_error"]
+           "katz_multi_query", "katz_index_build_many", "katz_multi_get_info",
+           "katz_multi_query_lrc", "katz_warmstart_train", "katz_mlp_loss_grad", "katz_last_error"]
 
 
 class KatzError(RuntimeError):
@@ -120,6 +121,11 @@ def lib() -> C.CDLL:
         L.katz_gemm_tf32x3.argtypes = [vp, i64, vp, i64, i32, i32, i32, C.c_float, C.c_float,
                                        vp, i64, vp]
         L.katz_multi_build.argtypes = [i32, vp, vp, i32, vp, C.POINTER(vp)]
+        L.katz_index_build_many.argtypes = [i32, vp, vp, C.POINTER(katz_build_opts), vp,
+                                            C.POINTER(vp)]
+        L.katz_multi_get_info.argtypes = [vp, vp, vp, vp]
+        L.katz_multi_query_lrc.argtypes = [vp, vp, i32, C.POINTER(katz_query_opts), vp, i32, i64,
+                                           C.POINTER(katz_stats), vp, vp, vp]
         L.katz_multi_free.argtypes = [vp]
         L.katz_multi_free.restype = None
         L.katz_multi_query.argtypes = [vp, vp, i32, C.POINTER(katz_query_opts), vp, i32, i64,
@@ -421,8 +427,47 @@ def katz_multi_build(graphs, betas, value_dtype=KATZ_UNIT, stream=None) -> KatzM
     return KatzMulti(h.value, [g.n for g in graphs])
 
 
+def katz_index_build_many(graphs, betas, value_dtype=KATZ_UNIT, rank=32, n_hubs=0,
+                          block_max=64, split=False, lanczos_steps=0, seed=20191212,
+                          stream=None) -> KatzMulti:
+    """Per-graph LRC index of many graphs (see katz.h)."""
+    csrs, keep = [], []
+    for g in graphs:
+        c, k = _csr(g)
+        csrs.append(c)
+        keep.append(k)
+    arr = (katz_csr * len(csrs))(*csrs)
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    o = katz_build_opts(value_dtype, 1, rank, n_hubs, block_max, int(split), lanczos_steps, 0,
+                        seed, -1)
+    h = C.c_void_p()
+    _check(lib().katz_index_build_many(len(csrs), C.cast(arr, C.c_void_p), b.ctypes.data,
+                                       C.byref(o), _stream(stream), C.byref(h)))
+    return KatzMulti(h.value, [g.n for g in graphs])
+
+
+def katz_multi_get_info(multi):
+    """(separator sizes, ranks, Ritz values per graph) of a per-graph LRC index."""
+    G = len(multi.sizes)
+    n2 = np.zeros(G, dtype=np.int64)
+    r = np.zeros(G, dtype=np.int32)
+    _check(lib().katz_multi_get_info(multi.handle, n2.ctypes.data, r.ctypes.data, None))
+    sig = np.zeros(max(1, int(r.sum())), dtype=np.float64)
+    _check(lib().katz_multi_get_info(multi.handle, None, None, sig.ctypes.data))
+    offs = np.concatenate([[0], np.cumsum(r)])
+    return n2, r, [sig[offs[i]:offs[i + 1]] for i in range(G)]
+
+
+def katz_multi_query_lrc(multi, q, qpg, K_out, out_dtype=KATZ_F32, tol=1e-6,
+                         tol_kind=KATZ_TOL_ERROR_INF, max_iter=0, max_refine=0, stream=None):
+    """katz_multi_query with the per-graph LRC inner solve."""
+    return katz_multi_query(multi, q, qpg, K_out, out_dtype, tol, tol_kind, max_iter, max_refine,
+                            stream, _fn="katz_multi_query_lrc")
+
+
 def katz_multi_query(multi, q, qpg, K_out, out_dtype=KATZ_F32, tol=1e-6,
-                     tol_kind=KATZ_TOL_ERROR_INF, max_iter=0, max_refine=0, stream=None):
+                     tol_kind=KATZ_TOL_ERROR_INF, max_iter=0, max_refine=0, stream=None,
+                     _fn="katz_multi_query"):
     """q: (g*qpg,) graph-local ids; K_out: (sum n_g, qpg).  Returns
     (stats, iters (g*qpg,), rel_res (g*qpg,))."""
     o = katz_query_opts(float(tol), tol_kind, KATZ_PREC_MIXED, max_iter, max_refine, 0, 0, 0)
@@ -430,9 +475,9 @@ def katz_multi_query(multi, q, qpg, K_out, out_dtype=KATZ_F32, tol=1e-6,
     total = len(multi.sizes) * qpg
     iters = np.zeros(total, dtype=np.int32)
     rel = np.zeros(total, dtype=np.float64)
-    code = lib().katz_multi_query(multi.handle, _ptr(q), qpg, C.byref(o), _ptr(K_out), out_dtype,
-                                  _ld(K_out), C.byref(st), iters.ctypes.data, rel.ctypes.data,
-                                  _stream(stream))
+    code = getattr(lib(), _fn)(multi.handle, _ptr(q), qpg, C.byref(o), _ptr(K_out), out_dtype,
+                               _ld(K_out), C.byref(st), iters.ctypes.data, rel.ctypes.data,
+                               _stream(stream))
     _check(code, allow=(KATZ_OK, KATZ_ENOCONV))
     stats = {"iters": st.iters, "refine_steps": st.refine_steps, "max_rel_res": st.max_rel_res,
              "ms": list(st.ms), "graph_replays": int(st.ms[4]), "status": STATUS_NAMES[code]}

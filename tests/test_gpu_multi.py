@@ -41,3 +41,57 @@ def test_multi_graph_batch_matches_oracle(count, c, qpg):
         assert O.error_inf_rel(Kh[off:off + g.n], ref).max() <= 1e-6, gi
         off += g.n
     assert stats["graph_replays"] >= 1
+
+
+@pytest.fixture(scope="module")
+def lrc_case():
+    graphs = synth.multi_sbm(24, 60, 3000, seed=91)
+    Ws = [O.adjacency(g.n, g.rowptr, g.col, g.val) for g in graphs]
+    betas = [0.95 / O.lambda_max(W) for W in Ws]
+    n = sum(g.n for g in graphs)
+    m = katz.katz_index_build_many(graphs, betas, value_dtype=katz.KATZ_UNIT, rank=16,
+                                   n_hubs=max(24, n // 100), block_max=64)
+    return graphs, Ws, betas, m
+
+
+def test_multi_graph_lrc_matches_oracle(lrc_case):
+    """Per-graph LRC index (hubs of each graph, block-diagonal Schur
+    complement, per-graph ranks): every (graph, query) Katz vector matches
+    the FP64 oracle of that graph alone to 1e-6."""
+    graphs, Ws, betas, m = lrc_case
+    qpg = 8
+    rng = np.random.default_rng(2)
+    q = np.concatenate([rng.choice(g.n, size=qpg, replace=False) for g in graphs]).astype(np.int32)
+    n = sum(g.n for g in graphs)
+    for fn in (katz.katz_multi_query_lrc, katz.katz_multi_query):
+        K = torch.zeros((n, qpg), dtype=torch.float64, device="cuda")
+        stats, iters, rel = fn(m, torch.from_numpy(q).cuda(), qpg, K, out_dtype=katz.KATZ_F64,
+                               tol=1e-6)
+        assert stats["status"] == "KATZ_OK", (fn.__name__, stats)
+        Kh = K.cpu().numpy()
+        off = 0
+        for gi, (g, W, beta) in enumerate(zip(graphs, Ws, betas)):
+            ref = O.katz_direct(W, beta, q[gi * qpg:(gi + 1) * qpg])
+            assert O.error_inf_rel(Kh[off:off + g.n], ref).max() <= 1e-6, (fn.__name__, gi)
+            off += g.n
+        print(fn.__name__, "refinement steps", stats["refine_steps"], "mean inner iterations",
+              float(iters.mean()))
+
+
+def test_multi_graph_lrc_ritz_values_match_oracle(lrc_case):
+    """Each graph's Ritz values (segmented Lanczos on the block-diagonal
+    system) equal the top eigenvalues of that graph's own R (Eq. 11) from the
+    oracle's dense construction, to the FP32 rounding of the stored scaled
+    weights."""
+    graphs, Ws, betas, m = lrc_case
+    n2, ranks, sig = katz.katz_multi_get_info(m)
+    assert (n2 >= 1).all() and (ranks >= 1).all() and (ranks <= n2).all()
+    # ranks grow with the graph size (log-scaled from rank/4 to rank)
+    order = np.argsort([g.n for g in graphs])
+    assert ranks[order[0]] <= ranks[order[-1]]
+    for gi in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        g, W, beta = graphs[gi], Ws[gi], betas[gi]
+        p = O.partition(g.n, g.rowptr, g.col, int(n2[gi]), 64, False)
+        ref = O.lrc_build(W, beta, p, int(ranks[gi]), block_max=64)
+        dense = np.sort(np.linalg.eigvalsh(ref["R"]))[::-1][: ranks[gi]]
+        np.testing.assert_allclose(sig[gi], dense, rtol=1e-5, atol=1e-9)
