@@ -442,7 +442,8 @@ void multi_build_lrc(katz_multi& m, const std::vector<HostCsr>& Ws, const double
   bo.rank = r_hi;
   bo.n_hubs = 0;
   bo.coupling_gemm = -1;
-  bo.n2_max = std::max<int64_t>(o.n2_max, (int64_t)seg.hubs.size());
+  bo.n2_max = (int32_t)std::max<int64_t>(o.n2_max > 0 ? o.n2_max : 16384,
+                                         (int64_t)seg.hubs.size());
   m.lrc.reset(new katz_index());
   build_index(*m.lrc, U, 1.0, bo, s, &seg);
 }
