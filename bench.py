@@ -60,6 +60,10 @@ def parse():
                         "paper_1912_06525_gb300.synth", fromlist=["TABLE1"]).TABLE1),
                     help="a Table 1 stand-in graph instead of the workload (1,000 queries, "
                          "unit weights, beta = 1/(lambda_max+1), r = 25 unless --rank)")
+    ap.add_argument("--multi", action="store_true",
+                    help="the many-graphs workload instead: 2,048 SBM graphs (n log-uniform in "
+                         "[500, 50,000], scaled by --scale), beta = 0.95/lambda_max per graph, "
+                         "8 queries per graph, per-graph LRC index (ranks 8-32) against CG")
     ap.add_argument("--rank", type=int, default=0,
                     help="rank r of the low-rank correction (0: the workload's, 128 or 64)")
     ap.add_argument("--sparse-katz", type=int, default=0, metavar="T",
@@ -256,11 +260,85 @@ def run_reference(args, world, rank):
 
 
 # ---------------------------------------------------------------- ours
+def run_multi(args, world, rank, local):
+    """Many graphs of uneven size at once: per-graph LRC (katz_multi_query_lrc)
+    timed against the CUDA-graph-replayed CG of the same batch."""
+    import torch
+    import __graft_entry__
+    from paper_1912_06525_gb300 import katz, synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    count = max(8, int(round(2048 * args.scale)))
+    graphs = synth.multi_sbm(count, 500, 50_000, seed=synth.BASE_SEED + 5)
+    lams = [katz.katz_lambda_max(g, steps=64) for g in graphs]
+    betas = [0.95 / l for l in lams]
+    t0 = time.perf_counter()
+    m = katz.katz_index_build_many(graphs, betas, value_dtype=katz.KATZ_UNIT,
+                                   rank=args.rank or 32, block_max=64)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    n2, ranks, _ = katz.katz_multi_get_info(m)
+    qpg = 8
+    rng = np.random.default_rng(synth.BASE_SEED + 6 + rank)
+    q = np.concatenate([rng.choice(g.n, size=qpg, replace=False) for g in graphs]).astype(np.int32)
+    n = sum(g.n for g in graphs)
+    nnz = sum(g.nnz for g in graphs)
+    qd = torch.from_numpy(q).cuda()
+    K = torch.empty((n, qpg), dtype=torch.float32, device="cuda")
+    res = {}
+    for name, fn in (("lrc", katz.katz_multi_query_lrc), ("cg", katz.katz_multi_query)):
+        for _ in range(args.warmup):
+            fn(m, qd, qpg, K, tol=1e-6)
+        torch.cuda.synchronize()
+        barrier(world)
+        stream = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        katz.katz_profile_enable(name == "lrc")
+        l0 = katz.katz_launch_count()
+        e0.record(stream)
+        for _ in range(args.steps):
+            st, it, rel = fn(m, qd, qpg, K, tol=1e-6)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = max_over_ranks(world, e0.elapsed_time(e1) / args.steps)
+        prof = {t: katz.katz_profile_read(t) for t in
+                ("spmm_f32", "cheb_step", "ff_residual", "block_solve_f32", "gemm_f32",
+                 "tc_gemm")} if name == "lrc" else {}
+        katz.katz_profile_enable(False)
+        res[name] = {"queries_per_s": world * count * qpg / (ms / 1000), "ms_per_batch": ms,
+                     "mean_inner_iters": float(np.mean(it)),
+                     "refine_steps": st["refine_steps"], "max_rel_res": st["max_rel_res"],
+                     "status": st["status"], "launches": katz.katz_launch_count() - l0,
+                     "kernels": {t: {"launches": v["launches"], "ms_per_batch": v["ms"] / args.steps}
+                                 for t, v in prof.items() if v["launches"]}}
+    if rank == 0:
+        out = {"metric": "Katz queries/sec at 1e-6 rel. error, many graphs at once", "unit": UNIT,
+               "value": res["lrc"]["queries_per_s"], "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": res["lrc"]["ms_per_batch"],
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32 (f64-class refinement)", "data": "synthetic",
+               "config": {"workload": f"{count} SBM graphs, n log-uniform in [500, 50,000] "
+                                      f"(sum n = {n:,}, nnz = {nnz:,}), 4-64 communities, mean "
+                                      f"degree 8-32, beta = 0.95/lambda_max per graph, {qpg} "
+                                      f"queries per graph, per-graph LRC (ranks "
+                                      f"{int(ranks.min())}-{int(ranks.max())}, separator "
+                                      f"{int(n2.sum()):,} hubs), tol 1e-6",
+                          "graphs": count, "n": n, "nnz": nnz, "index_build_s": build_s},
+               "lrc": res["lrc"], "cg": res["cg"]}
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.multi:
+        run_multi(args, world, rank, local)
         return
     import torch
     import __graft_entry__
