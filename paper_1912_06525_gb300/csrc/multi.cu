@@ -623,7 +623,7 @@ int multi_query(katz_multi& m, const int32_t* q_dev, int qpg, const katz_query_o
     float* Dp = m.ws.get<float>("ml.Dp", size_t(m.n) * ld);
     permute_rows_kernel<<<flat(m.n * ld), 256, 0, s>>>(Rn, Rp, L.iperm.p, m.n, ld, true);
     KATZ_CHECK_LAUNCH();
-    lit.clear();
+    lit.assign(b, 0);
     const int st = lrc_solve_f32(L, Rp, Dp, b, ld, tol_rel, max_iter, &lit, s);
     permute_rows_kernel<<<flat(m.n * ld), 256, 0, s>>>(Dp, Xn, L.iperm.p, m.n, ld, false);
     KATZ_CHECK_LAUNCH();

@@ -154,9 +154,11 @@ static int read_int(const int* dev, cudaStream_t s) {
   return h;
 }
 
-// Adds the state's per-column iteration counts to iters (host).
+// Adds the state's per-column iteration counts to iters (host; grown to b
+// columns if shorter).
 static void harvest_iters(const ColState& st, int b, std::vector<int32_t>* iters, cudaStream_t s) {
   if (!iters) return;
+  if (iters->size() < size_t(b)) iters->resize(b, 0);
   std::vector<int32_t> h(b);
   KATZ_CUDA(cudaMemcpyAsync(h.data(), st.iters, sizeof(int) * b, cudaMemcpyDeviceToHost, s));
   KATZ_CUDA(cudaStreamSynchronize(s));
