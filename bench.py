@@ -54,7 +54,10 @@ def parse():
                     help="kernel of the wide fused products (auto: the autotuner's choice)")
     ap.add_argument("--batch", type=int, default=0,
                     help="override the query batch width b (small profiling cases)")
-    ap.add_argument("--workload", type=int, default=3, choices=[2, 3],
+    ap.add_argument("--warm", action="store_true",
+                    help="the learned warm start instead: train on 50,000 queries of the n=1M "
+                         "graph (scaled by --scale), evaluate 4,096 held-out queries cold and warm")
+    ap.add_argument("--workload", type=int, default=3, choices=[1, 2, 3],
                     help="3: n=4M modular graph (the metric's workload); 2: n=1M power law")
     ap.add_argument("--standin", default="", choices=[""] + sorted(__import__(
                         "paper_1912_06525_gb300.synth", fromlist=["TABLE1"]).TABLE1),
@@ -211,6 +214,23 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
+def host_cpu():
+    """The host CPU as the oracle sees it: model (or architecture) and the
+    logical cores present (the oracle itself runs on one)."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    import platform
+    return {"model": model or platform.machine(), "nproc": os.cpu_count()}
+
+
 def oracle_sample(g, beta, c, q_sample, tol):
     """FP64 oracle CG (as it stands) on a few query columns; the stopping
     rule is set so the oracle meets the same error bound as the GPU."""
@@ -252,6 +272,7 @@ def run_reference(args, world, rank):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": cfg,
            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
+                            "host": host_cpu(),
                             "sample": "1 query of the batch per step, FP64 CG (SciPy CSR) to "
                                       "the same 1e-6 error bound"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -331,9 +352,123 @@ def run_multi(args, world, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def run_small(args, world, rank, local):
+    """n = 2,000 SBM, FP64 weights, r = 16, 16 queries, LRC and CG to a
+    relative residual of 1e-10: latency-bound, so the line reports the time
+    per batch (not a roofline fraction)."""
+    import torch
+    import __graft_entry__
+    import oracle
+    from paper_1912_06525_gb300 import katz, synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    g, q, c, r = synth.workload(1)
+    lam = katz.katz_lambda_max(g, steps=200)
+    beta = c / lam
+    idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_F64, rank=r, block_max=64)
+    qd = torch.from_numpy(q).cuda()
+    K = torch.empty((g.n, len(q)), dtype=torch.float64, device="cuda")
+    res = {}
+    for name, fn in (("lrc", katz.katz_query_batch), ("cg", katz.cg_query_batch)):
+        kw = dict(out_dtype=katz.KATZ_F64, tol=1e-10, tol_kind=katz.KATZ_TOL_RESIDUAL)
+        for _ in range(args.warmup):
+            fn(idx, qd, K, **kw)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            st, it, rel = fn(idx, qd, K, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(world, e0.elapsed_time(e1) / args.steps)
+        W = oracle.adjacency(g.n, g.rowptr, g.col, g.val)
+        err = float(oracle.error_inf_rel(K.cpu().numpy(), oracle.katz_direct(W, beta, q)).max())
+        res[name] = {"ms_per_batch": ms, "queries_per_s": world * len(q) / (ms / 1000),
+                     "mean_iters": float(np.mean(it)), "max_rel_res": st["max_rel_res"],
+                     "max_err_vs_oracle": err, "status": st["status"]}
+    if rank == 0:
+        print(json.dumps({"metric": "Katz query batch latency at rel. residual 1e-10 (n=2,000)",
+                          "unit": "ms", "value": res["lrc"]["ms_per_batch"], "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": res["lrc"]["ms_per_batch"], "higher_is_better": False,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic",
+                          "config": {"workload": "SBM n=2,000, 8 communities, mean degree 10, "
+                                                 "10% inter, FP64 weights, beta=0.5/lambda_max, "
+                                                 "r=16, 16 queries, rel. residual 1e-10",
+                                     "n": g.n, "nnz": g.nnz, "global_batch": len(q)},
+                          "lrc": res["lrc"], "cg": res["cg"]}), flush=True)
+
+
+def run_warm(args, world, rank, local):
+    """Learned warm start on the n = 1M power-law graph: the network is
+    trained on the method's own Katz vectors of 50,000 queries (scaled by
+    --scale), then 4,096 held-out queries run cold and warm at 1e-6."""
+    import torch
+    import __graft_entry__
+    from paper_1912_06525_gb300 import katz, synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    g, _, c, r = synth.workload(4, args.scale)
+    lam = katz.katz_lambda_max(g, steps=96)
+    beta = c / lam
+    idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_F32, rank=r, n_hubs=g.n // 100,
+                                block_max=64, split=False)
+    rng = np.random.default_rng(synth.BASE_SEED + 44)
+    n_train = max(1024, int(50_000 * min(1.0, args.scale)))
+    perm = rng.permutation(g.n).astype(np.int32)
+    train, test = perm[:n_train], np.sort(perm[n_train:n_train + 4096])
+    t0 = time.perf_counter()
+    tr = katz.katz_warmstart_train(idx, train, hidden=256, epochs=20, batch=256, lr=1e-3)
+    train_s = time.perf_counter() - t0
+    b = 1024
+    katz.katz_autotune(idx, b)
+    res = {}
+    for name, warm in (("cold", 0), ("warm", 1)):
+        its, ms, fb = [], 0.0, 0
+        for j0 in range(0, len(test), b):
+            qd = torch.from_numpy(test[j0:j0 + b]).cuda()
+            Kb = torch.empty((g.n, len(qd)), dtype=torch.float32, device="cuda")
+            katz.katz_query_batch(idx, qd, Kb, tol=1e-6, warm_start=warm)  # untimed
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(torch.cuda.current_stream())
+            st, it, rel = katz.katz_query_batch(idx, qd, Kb, tol=1e-6, warm_start=warm)
+            e1.record(torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            its.extend(it.tolist())
+            fb += int(st["ms"][5])
+        res[name] = {"queries_per_s": len(test) / (ms / 1000), "ms": ms,
+                     "mean_pcg_iters": float(np.mean(its)), "warm_fallbacks": fb}
+    if rank == 0:
+        print(json.dumps({"metric": "Katz queries/sec at 1e-6 rel. error, warm vs cold start",
+                          "unit": UNIT, "value": res["warm"]["queries_per_s"], "n_gpus": world,
+                          "steps": 1, "warmup": 1, "ms_per_step": res["warm"]["ms"],
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "f32 (bf16 network)", "data": "synthetic",
+                          "config": {"workload": f"Chung-Lu n={g.n:,} (exponent 2.1, mean degree "
+                                                 f"16), r={r}, network 32-256-{r} (GELU), "
+                                                 f"{n_train:,} training queries, 4,096 held out",
+                                     "n": g.n, "train_s": train_s,
+                                     "train_loss": [tr["initial_loss"], tr["final_loss"]]},
+                          "cold": res["cold"], "warm": res["warm"]}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
+    if args.impl != "reference" and args.workload == 1:
+        run_small(args, world, rank, local)
+        return
+    if args.impl != "reference" and args.warm:
+        run_warm(args, world, rank, local)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
@@ -527,7 +662,7 @@ def main():
         import oracle
         Kg = K[:, :ns].double().cpu().numpy()
         parity = float(oracle.error_inf_rel(Kg, Kref).max())
-        cpu = {"value": ns / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": ns / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": f"{ns} of the {b} queries, FP64 CG (SciPy CSR, 1 thread) to the same "
                          f"1e-6 error bound (rtol {rtol:.2e}), {dt:.1f} s"}
 
