@@ -131,9 +131,4 @@ template <class VT>
 void gemm(bool transA, int64_t M, int64_t N, int64_t K, double alpha, const VT* A, int64_t lda,
           const VT* B, int64_t ldb, double beta, VT* C, int64_t ldc, cudaStream_t s);
 
-// Top-k of each column of K (n x b) excluding q_j and its W-neighbours.
-template <class VT>
-void topk_columns(const Csr& W, const VT* K, int64_t ldk, int64_t n, const int32_t* q, int b,
-                  int k, int32_t* ids, double* scores, cudaStream_t s);
-
 }  // namespace katz
