@@ -264,24 +264,29 @@ def test_damping_bound_and_bad_queries():
     assert e.value.code == katz.KATZ_EINVAL
 
 
-@pytest.mark.parametrize("full", [False, True])
-def test_rank_extremes(full):
+def test_rank_extremes():
     """r = 0: the preconditioner is M22^{-1} alone; r = n2: S~^{-1} = S^{-1}
-    (Theorem 1 with every eigenpair kept), so the Schur PCG converges in
-    one iteration (two allowed for FP32 rounding of the stored basis)."""
+    (Theorem 1 with every eigenpair kept), one Schur PCG iteration in exact
+    arithmetic; the FP32 solve applies W^ through BF16 tensor-core products
+    (~1e-2 relative), so a few iterations, and fewer than with r = 0."""
     g = hub_graph(9)
     W = W_of(g)
     beta = 0.9 / O.lambda_max(W)
     n_hubs = 40
-    idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_F32, rank=n_hubs if full else 0,
-                                n_hubs=n_hubs, block_max=32, split=False)
-    info = katz.katz_index_get_info(idx)
-    assert info["n2"] == n_hubs and info["rank"] == (n_hubs if full else 0)
     q = synth.queries(g.n, 40, seed=10)
-    K, st, it, rel = run(katz.katz_query_batch, idx, g, q, tol=1e-6, precision=katz.KATZ_PREC_F32)
-    assert O.error_inf_rel(K, O.katz_direct(W, beta, q)).max() <= 1e-4
-    if full:
-        assert it.max() <= 2, it
-    K, st, it, rel = run(katz.katz_query_batch, idx, g, q, tol=1e-6)
-    assert st["status"] == "KATZ_OK"
-    assert O.error_inf_rel(K, O.katz_direct(W, beta, q)).max() <= 1e-6
+    ref = O.katz_direct(W, beta, q)
+    iters = {}
+    for r in (0, n_hubs):
+        idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_F32, rank=r, n_hubs=n_hubs,
+                                    block_max=32, split=False)
+        info = katz.katz_index_get_info(idx)
+        assert info["n2"] == n_hubs and info["rank"] == r
+        K, st, it, rel = run(katz.katz_query_batch, idx, g, q, tol=1e-6,
+                             precision=katz.KATZ_PREC_F32)
+        assert O.error_inf_rel(K, ref).max() <= 1e-4
+        iters[r] = it
+        K, st, it, rel = run(katz.katz_query_batch, idx, g, q, tol=1e-6)
+        assert st["status"] == "KATZ_OK"
+        assert O.error_inf_rel(K, ref).max() <= 1e-6
+    assert iters[n_hubs].max() <= 4, iters[n_hubs]
+    assert iters[n_hubs].mean() < iters[0].mean(), (iters[n_hubs].mean(), iters[0].mean())
