@@ -281,9 +281,11 @@ def test_rank_extremes():
                                     block_max=32, split=False)
         info = katz.katz_index_get_info(idx)
         assert info["n2"] == n_hubs and info["rank"] == r
-        K, st, it, rel = run(katz.katz_query_batch, idx, g, q, tol=1e-6,
+        # a tolerance well inside FP32 so that the counts reflect the
+        # preconditioner, not FP32 stagnation
+        K, st, it, rel = run(katz.katz_query_batch, idx, g, q, tol=1e-4,
                              precision=katz.KATZ_PREC_F32)
-        assert O.error_inf_rel(K, ref).max() <= 1e-4
+        assert O.error_inf_rel(K, ref).max() <= 1e-3
         iters[r] = it
         K, st, it, rel = run(katz.katz_query_batch, idx, g, q, tol=1e-6)
         assert st["status"] == "KATZ_OK"
