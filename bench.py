@@ -603,7 +603,8 @@ def main():
         torch.cuda.synchronize()
         sk_ms = e2.elapsed_time(e3)
         sk = {"queries_per_s": b / (sk_ms / 1000), "ms_per_batch": sk_ms, "s": 20, "T": T,
-              "solves_per_query": 1 + T, "status": st_sk["status"],
+              "distinct_landmarks": st_sk["distinct_landmarks"],
+              "solves_per_query": 1 + st_sk["distinct_landmarks"] / b, "status": st_sk["status"],
               "max_rel_res": st_sk["max_rel_res"]}
 
     # ---- end to end through the C-ABI from host queries to host top-k lists:

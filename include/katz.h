@@ -241,8 +241,8 @@ int linkpred_topk(const katz_index* idx, const int32_t* q, int32_t b,
  *   2. the Top-s list: the s highest k_q[j] over j outside {q} and q's
  *      neighbours (the linkpred_topk list);
  *   3. the T landmarks: the T highest k_q[j] over j != q (neighbours
- *      included), and their Katz vectors k_t, the columns of K_T (b*T more
- *      solves, batched up to 1,024 columns);
+ *      included), and their Katz vectors k_t, the columns of K_T (one solve
+ *      per DISTINCT landmark of the batch, batched up to 1,024 columns);
  *   4. rho_c = Pearson correlation of row q and row c of K_T (the
  *      T-vectors (k_t[q])_t and (k_t[c])_t), in FP64; 0 when either row is
  *      constant (always when T = 1);
@@ -254,7 +254,8 @@ int linkpred_topk(const katz_index* idx, const int32_t* q, int32_t b,
  * correlations (0 for -1), landmarks_out[b*T] (may be NULL) the landmarks
  * in Katz order.  1 <= s, T <= 64 and T < n, else KATZ_EINVAL.  stats (may
  * be NULL): iterations, refinement steps and residual as the maximum over
- * all the solves of the call, ms[0] its wall time.  KATZ_ENOCONV if any
+ * all the solves of the call, ms[0] its wall time, ms[6] the number of
+ * distinct landmarks solved.  KATZ_ENOCONV if any
  * solve hit its cap (outputs still filled). */
 int sparse_katz_topk(const katz_index* idx, const int32_t* q, int32_t b, int32_t s, int32_t T,
                      const katz_query_opts* opts, int32_t* ids_out, double* rho_out,

@@ -5,9 +5,12 @@
 //   2. per column, the Top-s link candidates (q and its neighbours left
 //      out) and the T landmark nodes (the T highest scores, only q left
 //      out), by the two-pass top-k kernels;
-//   3. the b*T landmark Katz vectors k_t, solved in batches of up to 1,024
-//      columns; after each batch one kernel keeps only the entries the
-//      correlation needs, row q and the s candidate rows of K_T;
+//   3. the Katz vectors k_t of the DISTINCT landmarks of the batch (queries
+//      often share landmarks, e.g. hubs; k_t does not depend on which query
+//      chose t), solved in batches of up to 1,024 columns; after each batch
+//      one kernel keeps only the entries the correlation needs, row q and
+//      the s candidate rows of K_T, for every (query, landmark) pair whose
+//      landmark is in the batch;
 //   4. one CTA per query: rho_c = Pearson correlation of rows q and c of
 //      K_T in FP64, and the candidates re-ordered by rho descending (ties
 //      in Katz order).
@@ -23,17 +26,20 @@ namespace {
 constexpr int kSkMax = 64;      // s and T
 constexpr int kSkChunk = 1024;  // landmark columns per solve
 
-// Column c of this chunk of landmark solves is landmark t = g % T of query
-// j = g / T (g = c0 + c).  Row 0 of the block grid copies K_T[q_j][c] to
-// X[j][t]; row 1 + i copies K_T[cand_j,i][c] to Y[j][i][t] (0 for a missing
-// candidate).
+// Pair g = j * T + t (landmark t of query j) uses column umap[g] - c0 of
+// this batch of distinct-landmark solves when c0 <= umap[g] < c0 + w.  Row 0
+// of the block grid copies K_T[q_j][col] to X[j][t]; row 1 + i copies
+// K_T[cand_j,i][col] to Y[j][i][t] (0 for a missing candidate).
 __global__ void sk_gather_kernel(const float* __restrict__ KT, int64_t ldk, int64_t c0, int w,
+                                 const int32_t* __restrict__ umap, int64_t pairs,
                                  const int32_t* __restrict__ q, const int32_t* __restrict__ cand,
                                  int s, int T, double* __restrict__ X, double* __restrict__ Y) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= w) return;
+  const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (g >= pairs) return;
+  const int64_t c = int64_t(umap[g]) - c0;
+  if (c < 0 || c >= w) return;
   const int i = blockIdx.y;
-  const int64_t g = c0 + c, j = g / T, t = g % T;
+  const int64_t j = g / T, t = g % T;
   const int64_t row = i == 0 ? int64_t(q[j]) : int64_t(cand[j * s + i - 1]);
   const double v = row >= 0 ? double(KT[row * ldk + c]) : 0.0;
   if (i == 0)
@@ -136,25 +142,38 @@ int sparse_katz(katz_index& idx, const int32_t* q_dev, const int32_t* q_host, in
   KATZ_CUDA(cudaStreamSynchronize(s));
   for (int32_t v : land_h)
     KATZ_REQUIRE(v >= 0 && v < n, KATZ_ECUDA, "landmark selection returned an invalid node");
-  // 3. landmark solves, keeping rows q and the candidates of K_T
+  // 3. the distinct landmarks (ascending ids) and each pair's index among them
+  const int64_t pairs = int64_t(b) * T;
+  std::vector<int32_t> uniq(land_h.begin(), land_h.end());
+  std::sort(uniq.begin(), uniq.end());
+  uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+  std::vector<int32_t> umap_h(pairs);
+  for (int64_t g = 0; g < pairs; ++g)
+    umap_h[g] = int32_t(std::lower_bound(uniq.begin(), uniq.end(), land_h[g]) - uniq.begin());
+  const int64_t nu = (int64_t)uniq.size();
+  int32_t* uq = idx.ws.get<int32_t>("sk.uq", size_t(nu));
+  int32_t* umap = idx.ws.get<int32_t>("sk.umap", size_t(pairs));
+  KATZ_CUDA(cudaMemcpyAsync(uq, uniq.data(), 4 * size_t(nu), cudaMemcpyHostToDevice, s));
+  KATZ_CUDA(cudaMemcpyAsync(umap, umap_h.data(), 4 * size_t(pairs), cudaMemcpyHostToDevice, s));
+  if (st) st->ms[6] = double(nu);
+  // landmark solves, keeping rows q and the candidates of K_T
   double* X = idx.ws.get<double>("sk.X", size_t(b) * T);
   double* Y = idx.ws.get<double>("sk.Y", size_t(b) * s_top * T);
-  const int64_t total = int64_t(b) * T;
-  const int wmax = (int)std::min<int64_t>(kSkChunk, total);
+  const int wmax = (int)std::min<int64_t>(kSkChunk, nu);
   float* KT = idx.ws.get<float>("sk.KT", size_t(n) * wmax);
-  for (int64_t c0 = 0; c0 < total; c0 += wmax) {
-    const int w = (int)std::min<int64_t>(wmax, total - c0);
+  for (int64_t c0 = 0; c0 < nu; c0 += wmax) {
+    const int w = (int)std::min<int64_t>(wmax, nu - c0);
     QueryOut ot;
     ot.K = KT;
     ot.dtype = KATZ_F32;
     ot.ldk = w;
     one = katz_stats{};
-    const int st2 = run_queries(idx, lrc, land + c0, land_h.data() + c0, w, o, ot, &one, it, rr, s);
+    const int st2 = run_queries(idx, lrc, uq + c0, uniq.data() + c0, w, o, ot, &one, it, rr, s);
     if (st2 != KATZ_OK && st2 != KATZ_ENOCONV) return st2;
     if (st2 == KATZ_ENOCONV) status = KATZ_ENOCONV;
     merge_stats(&acc, one);
-    dim3 grid((unsigned)ceil_div(w, 128), (unsigned)(s_top + 1));
-    sk_gather_kernel<<<grid, 128, 0, s>>>(KT, w, c0, w, q_dev, cand, s_top, T, X, Y);
+    dim3 grid((unsigned)ceil_div(pairs, 128), (unsigned)(s_top + 1));
+    sk_gather_kernel<<<grid, 128, 0, s>>>(KT, w, c0, w, umap, pairs, q_dev, cand, s_top, T, X, Y);
     KATZ_CHECK_LAUNCH();
   }
   // 4. correlation and re-ranking
@@ -164,9 +183,11 @@ int sparse_katz(katz_index& idx, const int32_t* q_dev, const int32_t* q_host, in
     KATZ_CUDA(cudaMemcpyAsync(land_out, land, 4 * size_t(b) * T, cudaMemcpyDeviceToDevice, s));
   KATZ_CUDA(cudaStreamSynchronize(s));
   if (st) {
+    const double nu_d = st->ms[6];
     *st = acc;
     st->ms[0] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
                     .count();
+    st->ms[6] = nu_d;
   }
   return status;
 }

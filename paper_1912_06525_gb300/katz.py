@@ -345,7 +345,8 @@ def sparse_katz_topk(index, q, s, T, ids_out, rho_out, landmarks_out=None, tol=1
                                   _stream(stream))
     _check(code, allow=(KATZ_OK, KATZ_ENOCONV))
     return {"iters": st.iters, "refine_steps": st.refine_steps, "max_rel_res": st.max_rel_res,
-            "ms": list(st.ms), "status": STATUS_NAMES[code]}
+            "ms": list(st.ms), "distinct_landmarks": int(st.ms[6]),
+            "status": STATUS_NAMES[code]}
 
 
 def katz_apply_M(index, X, Y, b, dtype, stream=None):

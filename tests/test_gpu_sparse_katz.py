@@ -105,6 +105,8 @@ def test_sparse_katz_matches_oracle(s, T, lrc):
     st = katz.sparse_katz_topk(idx, torch.from_numpy(q).cuda(), s, T, ids, rho, land)
     assert st["status"] == "KATZ_OK"
     ids, rho, land = ids.cpu().numpy(), rho.cpu().numpy(), land.cpu().numpy()
+    # one solve per distinct landmark of the batch
+    assert st["distinct_landmarks"] == len(np.unique(land))
     for j, qq in enumerate(q):
         check_query(Kd, W, int(qq), s, T, ids[j], rho[j], land[j])
     if T == 1:
