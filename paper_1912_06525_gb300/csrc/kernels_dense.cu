@@ -300,7 +300,7 @@ __device__ __forceinline__ bool better(T sa, int ia, T sb, int ib) {
 }
 
 constexpr int kTopMax = 64;
-constexpr int kTopUnroll = 8;  // rows loaded ahead per warp
+constexpr int kTopUnroll = 16;  // rows loaded ahead per warp (2 KB in flight per warp)
 
 // Pass 1: CTA = (row slice, tile of 32 query columns); lane c of every warp
 // owns column tile*32 + c, so each warp reads K row by row in coalesced
