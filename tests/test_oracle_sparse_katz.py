@@ -108,3 +108,28 @@ def test_sparse_katz_one_landmark_keeps_katz_order():
     lp, _ = O.linkpred_topk(W, O.katz_direct(W, beta, Q), Q, 12)
     assert (rho == 0).all()
     assert ids.tolist() == lp.tolist() == cand.tolist()
+
+
+def test_sparse_katz_golden_star_fixture():
+    """The hand derivation in tests/golden/sparse_katz_star.txt, with the
+    closed-form Katz columns (exact ties) fed to the oracle."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "sparse_katz_star.txt")
+    fx = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            key, *vals = line.split()
+            fx[key] = vals
+    m = int(fx["graph"][1])
+    W = W_of(synth.star(m))
+    beta = 0.5 / np.sqrt(m)
+    d = 1 - m * beta * beta
+    K = np.full((m + 1, m + 1), beta * beta / d)
+    K[0, 1:] = K[1:, 0] = beta / d
+    K[0, 0] = m * beta * beta / d
+    ids, rho, land, cand = O.sparse_katz(W, beta, [int(fx["query"][0])], int(fx["s"][0]),
+                                         int(fx["T"][0]), solve=lambda W_, b_, c: K[:, c])
+    assert land[0].tolist() == [int(v) for v in fx["landmarks"]]
+    assert cand[0].tolist() == [int(v) for v in fx["candidates"]]
+    assert ids[0].tolist() == [int(v) for v in fx["ids"]]
+    np.testing.assert_allclose(rho[0], [float(v) for v in fx["rho"]], atol=1e-12)
