@@ -219,11 +219,19 @@ def host_cpu():
     """The host CPU as the oracle sees it: model (or architecture) and the
     logical cores present (the oracle itself runs on one)."""
     model = ""
+    try:  # lscpu names Arm cores (Neoverse-V2 on Grace); /proc/cpuinfo does not
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
                 key = line.split(":")[0].strip().lower()
-                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                if not model and key in ("model name", "cpu model", "hardware") and ":" in line:
                     model = line.split(":", 1)[1].strip()
                     break
     except OSError:
