@@ -438,6 +438,14 @@ int katz_multi_query_lrc(const katz_multi* m, const int32_t* q, int32_t qpg,
 /* Number of kernels this library has launched in this process (all calls). */
 int64_t katz_launch_count(void);
 
+/* Test hook (host-side fault injection; no GPU fault is involved): after
+ * `after` more device allocations by the library, the next one fails as if
+ * the device were out of memory -- no cudaMalloc is made for it -- and the
+ * call in progress returns KATZ_ENOMEM after releasing what it allocated.
+ * The hook then switches itself off; after < 0 switches it off at once.
+ * Process-wide.  Always returns KATZ_OK. */
+int katz_fault_inject_alloc(int64_t after);
+
 /* Start (on != 0) or stop timing tagged kernel launches with CUDA events on
  * their launching stream; every call resets the totals.  Tags:
  * "spmm_f32" / "spmm_f64" (CSR products, Eq. 3 and the couplings),

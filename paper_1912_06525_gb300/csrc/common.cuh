@@ -58,6 +58,9 @@ int64_t launch_count();
 bool profiling();
 void prof_begin(cudaStream_t s);
 void prof_end(const char* tag, double alg_bytes, cudaStream_t s);
+// true when the host-side fault injection (katz_fault_inject_alloc) makes
+// this device allocation fail
+bool alloc_fault();
 
 // ------------------------------------------------------------ device memory
 // Owning device buffer (cudaMalloc / cudaFree).
@@ -77,7 +80,10 @@ struct DBuf {
   ~DBuf() { release(); }
   void alloc(size_t count) {
     release();
-    if (count) KATZ_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    if (count) {
+      if (alloc_fault()) throw Error(KATZ_ENOMEM, "injected device allocation failure");
+      KATZ_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    }
     n = count;
   }
   // grow-only reallocation (contents not kept)

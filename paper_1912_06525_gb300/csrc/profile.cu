@@ -16,6 +16,17 @@ static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(); }
 
+// Host-side fault injection: after g_fail_after more device allocations the
+// next one fails (no CUDA call is made for it); -1 = off.
+static std::atomic<int64_t> g_fail_after{-1};
+bool alloc_fault() {
+  int64_t v = g_fail_after.load();
+  while (v >= 0) {
+    if (g_fail_after.compare_exchange_weak(v, v - 1)) return v == 0;
+  }
+  return false;
+}
+
 namespace {
 struct Rec {
   std::string tag;
@@ -83,6 +94,11 @@ void prof_end(const char* tag, double alg_bytes, cudaStream_t s) {
 extern "C" {
 
 int64_t katz_launch_count(void) { return katz::launch_count(); }
+
+int katz_fault_inject_alloc(int64_t after) {
+  katz::g_fail_after.store(after < 0 ? -1 : after);
+  return KATZ_OK;
+}
 
 int katz_profile_enable(int32_t on) {
   try {

@@ -31,7 +31,7 @@ EXPORTS = ["katz_lambda_max", "katz_index_build", "katz_index_free", "katz_index
            "katz_index_load", "katz_index_get_info", "katz_index_get_partition", "katz_partition",
            "katz_index_get_sigma", "katz_query_batch", "cg_query_batch", "linkpred_topk",
            "linkpred_topk_noalloc", "sparse_katz_topk", "katz_apply_M", "katz_autotune", "katz_gemm_bf16",
-           "katz_gemm_tf32x3", "katz_launch_count",
+           "katz_gemm_tf32x3", "katz_launch_count", "katz_fault_inject_alloc",
            "katz_profile_enable", "katz_profile_read", "katz_multi_build", "katz_multi_free",
            "katz_multi_query", "katz_index_build_many", "katz_multi_get_info",
            "katz_multi_query_lrc", "katz_warmstart_train", "katz_mlp_loss_grad", "katz_last_error"]
@@ -136,6 +136,7 @@ def lib() -> C.CDLL:
         L.katz_launch_count.argtypes = []
         L.katz_launch_count.restype = C.c_int64
         L.katz_profile_enable.argtypes = [i32]
+        L.katz_fault_inject_alloc.argtypes = [i64]
         L.katz_profile_read.argtypes = [C.c_char_p, vp, vp, vp]
         L.katz_last_error.restype = C.c_char_p
         for name in EXPORTS:
@@ -347,6 +348,11 @@ def sparse_katz_topk(index, q, s, T, ids_out, rho_out, landmarks_out=None, tol=1
     return {"iters": st.iters, "refine_steps": st.refine_steps, "max_rel_res": st.max_rel_res,
             "ms": list(st.ms), "distinct_landmarks": int(st.ms[6]),
             "status": STATUS_NAMES[code]}
+
+
+def katz_fault_inject_alloc(after: int) -> None:
+    """Test hook: the device allocation after `after` more fails (KATZ_ENOMEM)."""
+    _check(lib().katz_fault_inject_alloc(int(after)))
 
 
 def katz_apply_M(index, X, Y, b, dtype, stream=None):
