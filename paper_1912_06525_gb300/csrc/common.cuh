@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <cstdio>
@@ -61,6 +62,15 @@ void prof_end(const char* tag, double alg_bytes, cudaStream_t s);
 // true when the host-side fault injection (katz_fault_inject_alloc) makes
 // this device allocation fail
 bool alloc_fault();
+
+// Named NVTX range over a scope: the phases of a query show up in ncu /
+// nsys timelines (`--nvtx`); without a tool attached it costs a call.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ------------------------------------------------------------ device memory
 // Owning device buffer (cudaMalloc / cudaFree).

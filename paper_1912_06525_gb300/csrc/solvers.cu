@@ -494,8 +494,12 @@ int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double t
   VT* Y1 = idx.ws.get<VT>("lrc.Y1", size_t(std::max<int64_t>(n1, 1)) * ld);
   int status = KATZ_OK;
   auto merge = [&](int st) { if (st != KATZ_OK && status == KATZ_OK) status = st; };
-  if (n1 > 0) merge(m11_solve<VT>(idx, R1, Y1, b, ld, tol_l, max_iter, nullptr, s));
+  if (n1 > 0) {
+    NvtxRange r("katz.m11_solve");
+    merge(m11_solve<VT>(idx, R1, Y1, b, ld, tol_l, max_iter, nullptr, s));
+  }
   if (n2 > 0) {
+    NvtxRange r("katz.schur_pcg");
     VT* F = idx.ws.get<VT>("lrc.F", size_t(n2) * ld);
     if (n1 > 0)
       spmm<VT>(idx.W21.view(), idx.W21.heavy.p, idx.W21.n_heavy, idx.beta, Y1, ld, 1.0, R2, ld, F,
@@ -507,6 +511,7 @@ int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double t
     merge(pcg_schur<VT>(idx, F, D2, b, ld, thr2, max_iter, iters, s, K2_0));
   }
   if (n1 > 0) {
+    NvtxRange r("katz.backsolve");
     if constexpr (sizeof(VT) == 4) {
       if (n2 > 0 && idx.has_h && coupling_gemm_pays(idx, ld, tol_l)) {
         // K1 = Y1 + (beta M11^{-1} W12) K2 on the tensor cores (all ld columns,
@@ -645,7 +650,10 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   float* Kh = ws.get<float>("q.Kh", size_t(n) * ld);
   float* Kl = ws.get<float>("q.Kl", size_t(n) * ld);
   KATZ_CUDA(cudaMemsetAsync(Rh, 0, sizeof(float) * n * ld, s));
-  build_rhs<float>(idx.W.view(), q, b, idx.beta, pos, Rh, ld, s);
+  {
+    NvtxRange nr("katz.rhs");
+    build_rhs<float>(idx.W.view(), q, b, idx.beta, pos, Rh, ld, s);
+  }
   inner_thresholds_kernel<<<1, 1024, 0, s>>>(bn2, thr2, tau, b, conv, thr2_in, nopen);
   KATZ_CHECK_LAUNCH();
   const float* K20 = nullptr;
@@ -676,6 +684,7 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
       // sparse b after the sweep, so its norms are taken afterwards (summing
       // squares before and correcting by b_i^2 - r_i^2 would cancel
       // catastrophically); later passes fuse them.
+      NvtxRange nr(refine == 0 ? "katz.residual_first" : "katz.residual_update");
       if (refine == 0) {
         if (pipe_ok && use_pipe(idx, gcfg, true))
           pipe_residual(G.view(), G.ps, idx.unit_weights, idx.beta, Kh, Rh, Rl, ld, b, nullptr,
