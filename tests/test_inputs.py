@@ -23,3 +23,31 @@ def test_table1_standin_is_seeded():
     a = synth.table1_standin("email_enron", 0.1)
     b = synth.table1_standin("email_enron", 0.1)
     assert np.array_equal(a.rowptr, b.rowptr) and np.array_equal(a.col, b.col)
+
+
+def test_many_graph_recipe():
+    """multi_sbm: node counts log-uniform in [n_lo, n_hi], symmetric block
+    models; where communities are large enough to hold the target degree
+    (size >= 4 x the intra-community degree), the mean degree is within 25%
+    of the drawn target and about 10% of the edges run between communities
+    (smaller communities cannot hold it: repeated pairs are erased)."""
+    gs = synth.multi_sbm(40, 200, 4000, seed=3)
+    ns = np.array([g.n for g in gs])
+    assert ns.min() >= 200 and ns.max() <= 4000
+    # log-uniform: the geometric midpoint splits the counts roughly in half
+    assert 0.2 < (ns < np.sqrt(200 * 4000)).mean() < 0.8
+    checked = 0
+    for g in gs:
+        W = O.adjacency(g.n, g.rowptr, g.col, g.val)
+        assert (W != W.T).nnz == 0 and W.diagonal().sum() == 0
+        lab = np.asarray(g.meta["labels"])
+        k = len(set(lab.tolist()))
+        target = g.meta["mean_deg_target"]
+        if g.n / k < 4 * 0.9 * target:
+            continue
+        checked += 1
+        assert abs(g.nnz / g.n - target) <= 0.25 * target, (g.nnz / g.n, target)
+        r = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+        inter = (lab[r] != lab[g.col]).mean()
+        assert 0.05 <= inter <= 0.15, inter
+    assert checked >= 5
