@@ -293,6 +293,10 @@ def oracle_all_cores(g, beta, q_sample, rtol, workers):
     from multiprocessing import shared_memory
     import oracle
     W = oracle.adjacency(g.n, g.rowptr, g.col, g.val)
+    need = sum(a.nbytes for a in (W.indptr, W.indices, W.data))
+    st = os.statvfs("/dev/shm")
+    if st.f_bavail * st.f_frsize < 1.25 * need:  # a full tmpfs would SIGBUS the writer
+        raise RuntimeError(f"/dev/shm has room for less than {need / 1e9:.1f} GB")
     shms, specs = [], []
     try:
         for a in (W.indptr, W.indices, W.data):
