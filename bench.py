@@ -308,12 +308,12 @@ def oracle_all_cores(g, beta, q_sample, rtol, workers):
         # bounded waits: a pool whose workers cannot start would respawn them
         # forever; the context exit terminates it
         with ctx.Pool(workers, initializer=_pool_attach, initargs=(specs, g.n, beta)) as pool:
-            ready = pool.map_async(_pool_ready, range(workers), chunksize=1).get(timeout=120)
+            ready = pool.map_async(_pool_ready, range(workers), chunksize=1).get(timeout=90)
             if not all(ready):
                 raise RuntimeError("oracle workers did not attach the graph")
             t = time.perf_counter()
             pool.map_async(_pool_solve, [(int(q), rtol) for q in q_sample],
-                           chunksize=1).get(timeout=600)
+                           chunksize=1).get(timeout=180)
             return time.perf_counter() - t
     finally:
         for m in shms:
