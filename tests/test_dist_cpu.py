@@ -64,3 +64,22 @@ def test_reference_arm_json_line():
         assert k in line
     assert line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["value"] > 0
+
+
+def test_all_cores_oracle_helper():
+    """The CPU baseline's all-cores leg: the oracle run once per query
+    column in spawned processes over a shared-memory copy of the graph,
+    timed; the shared segments are released afterwards."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_1912_06525_gb300 import synth
+    g = synth.erdos_renyi(3000, 0.003, seed=2)
+    W = oracle.adjacency(g.n, g.rowptr, g.col, g.val)
+    beta = 0.5 / oracle.lambda_max(W)
+    before = set(os.listdir("/dev/shm"))
+    dt = bench.oracle_all_cores(g, beta, np.array([1, 7, 11]), 1e-10, 2)
+    assert dt > 0
+    assert set(os.listdir("/dev/shm")) - before == set()
+    info = bench.host_cpu()
+    assert info["nproc"] >= 1 and info["model"]
