@@ -222,3 +222,44 @@ def test_adamw_first_step_closed_form():
     p1, m, v = O.adamw_step(p, g, np.zeros(3), np.zeros(3), 1, lr=0.1, wd=0.01)
     want = p - 0.1 * (g / (np.abs(g) + 1e-8) + 0.01 * p)
     np.testing.assert_allclose(p1, want, rtol=1e-12)
+
+
+def test_union_with_folded_damping_is_block_diagonal():
+    """Disjoint graphs with each graph's damping folded into its weights
+    (W~ = beta_g W_g on graph g's block, index beta = 1): the union's Katz
+    column of a node is that graph's own Katz vector (zero on the other
+    graphs), and with each graph's own hubs as separator the union's Schur
+    complement and R (Eq. 11) are block diagonal, block g equal to the S_g
+    and R_g of graph g built alone (Lemma 1 on a block-diagonal M)."""
+    gs = [synth.erdos_renyi(45, 0.12, seed=s, weighted=s % 2 == 0) for s in (1, 2, 3)]
+    Ws = [W_of(g) for g in gs]
+    betas = [c / O.lambda_max(W) for c, W in zip((0.6, 0.8, 0.95), Ws)]
+    Wt = sp.block_diag([b * W for b, W in zip(betas, Ws)]).tocsr()
+    offs = np.concatenate([[0], np.cumsum([g.n for g in gs])])
+    for gi, g in enumerate(gs):
+        Ku = O.katz_direct(Wt, 1.0, [offs[gi] + 5])[:, 0]
+        Kg = O.katz_direct(Ws[gi], betas[gi], [5])[:, 0]
+        np.testing.assert_allclose(Ku[offs[gi]:offs[gi + 1]], Kg, rtol=1e-12, atol=1e-15)
+        assert np.abs(np.delete(Ku, np.arange(offs[gi], offs[gi + 1]))).max() == 0.0
+    # per-graph partitions (each graph's 4 highest degrees) joined graph-major
+    parts = [O.partition(g.n, g.rowptr, g.col, 4, 64, False) for g in gs]
+    blocks, seps, bptr = [], [], [0]
+    for gi, p in enumerate(parts):
+        bp = p["block_ptr"]
+        for k in range(len(bp) - 1):
+            blocks.append(offs[gi] + p["perm"][bp[k]:bp[k + 1]])
+            bptr.append(bptr[-1] + bp[k + 1] - bp[k])
+        seps.append(offs[gi] + p["perm"][p["n1"]:])
+    perm = np.concatenate(blocks + seps).astype(np.int64)
+    n1 = int(sum(p["n1"] for p in parts))
+    part_u = {"perm": perm, "block_ptr": np.array(bptr), "n1": n1, "n2": len(perm) - n1}
+    U = O.lrc_build(Wt, 1.0, part_u, 2)
+    s0 = 0
+    for gi, (g, p) in enumerate(zip(gs, parts)):
+        ref = O.lrc_build(Ws[gi], betas[gi], p, 2)
+        s1 = s0 + ref["n2"]
+        np.testing.assert_allclose(U["S"][s0:s1, s0:s1], ref["S"], rtol=1e-11, atol=1e-14)
+        np.testing.assert_allclose(U["R"][s0:s1, s0:s1], ref["R"], rtol=1e-10, atol=1e-13)
+        off = np.delete(U["S"][s0:s1], np.arange(s0, s1), axis=1)
+        assert np.abs(off).max() == 0.0
+        s0 = s1
