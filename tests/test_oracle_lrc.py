@@ -263,3 +263,34 @@ def test_union_with_folded_damping_is_block_diagonal():
         off = np.delete(U["S"][s0:s1], np.arange(s0, s1), axis=1)
         assert np.abs(off).max() == 0.0
         s0 = s1
+
+
+def test_packed_columns_give_every_graph_block():
+    """One M11 solve of width max_g n2_g, with separator node l of EVERY
+    graph in column l, yields each graph's block of T = M12^T M11^{-1} M12
+    (Lemma 1): the graphs' right-hand sides occupy disjoint rows of the
+    block-diagonal M11, so they never mix.  Dense FP64 on the union."""
+    gs = [synth.erdos_renyi(n, 0.1, seed=n) for n in (30, 45, 60)]
+    Ws = [W_of(g) for g in gs]
+    betas = [0.9 / O.lambda_max(W) for W in Ws]
+    Wt = sp.block_diag([b * W for b, W in zip(betas, Ws)]).tocsr()
+    offs = np.concatenate([[0], np.cumsum([g.n for g in gs])])
+    hubs = [offs[gi] + np.argsort(-np.diff(g.rowptr), kind="stable")[:h]
+            for gi, (g, h) in enumerate(zip(gs, (3, 5, 4)))]
+    sep = np.concatenate(hubs)
+    rest = np.setdiff1d(np.arange(offs[-1]), sep)
+    M = np.eye(offs[-1]) - Wt.toarray()
+    M11, M12 = M[np.ix_(rest, rest)], M[np.ix_(rest, sep)]
+    T = M12.T @ np.linalg.solve(M11, M12)          # the whole n2 x n2 at once
+    width = max(len(h) for h in hubs)
+    E = np.zeros((len(sep), width))
+    gstart = np.concatenate([[0], np.cumsum([len(h) for h in hubs])])
+    for gi in range(len(gs)):
+        for l in range(len(hubs[gi])):
+            E[gstart[gi] + l, l] = 1.0
+    Tp = M12.T @ np.linalg.solve(M11, M12 @ E)      # one packed solve
+    for gi in range(len(gs)):
+        a, b = gstart[gi], gstart[gi + 1]
+        np.testing.assert_allclose(Tp[a:b, :b - a], T[a:b, a:b], rtol=1e-12, atol=1e-14)
+        if b - a < width:  # columns past this graph's separator stay empty on its rows
+            assert np.abs(Tp[a:b, b - a:]).max() == 0.0
