@@ -104,3 +104,18 @@ def test_index_load_rejects_bad_files_on_the_host(L, tmp_path):
         assert e.value.code == katz.KATZ_EINVAL, name
     msg = katz.katz_last_error()
     assert "truncated" in msg or "magic" in msg
+
+
+def test_injected_allocation_failure_on_the_host(L):
+    """katz_fault_inject_alloc(0): the first device allocation of the build
+    fails before any CUDA call is made, so the build unwinds with
+    KATZ_ENOMEM on a machine without a GPU; the hook then switches off."""
+    g = synth.path(6)
+    try:
+        katz.katz_fault_inject_alloc(0)
+        with pytest.raises(katz.KatzError) as e:
+            katz.katz_index_build(g, 0.2, value_dtype=katz.KATZ_UNIT, build_lrc=False)
+        assert e.value.code == katz.KATZ_ENOMEM
+        assert "injected" in katz.katz_last_error()
+    finally:
+        katz.katz_fault_inject_alloc(-1)
