@@ -119,3 +119,19 @@ def test_injected_allocation_failure_on_the_host(L):
         assert "injected" in katz.katz_last_error()
     finally:
         katz.katz_fault_inject_alloc(-1)
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf"), 0.0, -1.0])
+def test_host_validation_rejects_bad_weights(L, bad):
+    """Weights must be positive and finite (NaN, infinity, zero and
+    negative values are rejected on the host with KATZ_EINVAL)."""
+    g = synth.path(5)
+    val = np.ones(len(g.col))
+    # the edge 1-2 in both directions
+    for i, j in ((1, 2), (2, 1)):
+        k = g.rowptr[i] + int(np.nonzero(g.col[g.rowptr[i]:g.rowptr[i + 1]] == j)[0][0])
+        val[k] = bad
+    w = synth.Graph(n=g.n, rowptr=g.rowptr, col=g.col, val=val)
+    with pytest.raises(katz.KatzError) as e:
+        katz.katz_partition(w, 0, 4)
+    assert e.value.code == katz.KATZ_EINVAL
