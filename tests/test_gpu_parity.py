@@ -262,6 +262,11 @@ def test_damping_bound_and_bad_queries():
     with pytest.raises(katz.KatzError) as e:
         katz.katz_query_batch(idx, np.array([1], dtype=np.int32), K)  # no LRC part
     assert e.value.code == katz.KATZ_EINVAL
+    # an empty batch is rejected on the host, before any launch
+    K0 = np.zeros((8, 1), dtype=np.float32)
+    with pytest.raises(katz.KatzError) as e:
+        katz.cg_query_batch(idx, np.zeros(0, dtype=np.int32), K0)
+    assert e.value.code == katz.KATZ_EINVAL
 
 
 def test_rank_extremes():
