@@ -476,7 +476,7 @@ def linkpred_topk(W: sp.csr_matrix, K: np.ndarray, Q, k: int):
 def top_nodes(scores: np.ndarray, k: int, exclude=()) -> np.ndarray:
     """The k nodes of highest score, score descending and node id ascending
     on ties, leaving out the nodes in ``exclude`` (fewer than k if too few
-    remain)."""
+    remain): the Top-s and Top-T selections of Algorithm 3 (Section 3.3)."""
     keep = np.ones(scores.shape[0], dtype=bool)
     keep[np.asarray(list(exclude), dtype=np.int64)] = False
     cand = np.nonzero(keep)[0]
@@ -484,8 +484,9 @@ def top_nodes(scores: np.ndarray, k: int, exclude=()) -> np.ndarray:
 
 
 def pearson(x: np.ndarray, y: np.ndarray) -> float:
-    """Pearson correlation of two equal-length vectors: the centred inner
-    product over the product of the centred norms.  Either vector constant
+    """Pearson correlation of two equal-length vectors (the row-wise
+    correlation of Algorithm 3, Section 3.3): the centred inner product over
+    the product of the centred norms.  Either vector constant
     (zero spread; every vector of length 1) gives 0, no linear
     association."""
     xc = x - x.mean()
