@@ -224,6 +224,30 @@ def test_adamw_first_step_closed_form():
     np.testing.assert_allclose(p1, want, rtol=1e-12)
 
 
+def test_adamw_steps_two_and_three_by_hand():
+    """Steps t = 2, 3 where the bias corrections 1 - b^t differ from the
+    first step's.  With b1 = 1/2, b2 = 3/4, lr = 1, eps = wd = 0 and the
+    scalar gradients 2, -2, 1 from p = 0, written out by hand:
+      t=1: m = 1,     v = 1,      m^ = 2,    v^ = 4,      p = -1
+      t=2: m = -1/2,  v = 7/4,    m^ = -2/3, v^ = 4,      p = -1 + 1/3
+      t=3: m = 1/4,   v = 25/16,  m^ = 2/7,  v^ = 100/37, p = -2/3 - sqrt(37)/35
+    and a constant gradient, for which every bias-corrected step is the
+    same -lr * g/(|g| + eps) - lr*wd*p whatever t is."""
+    p, m, v = np.zeros(1), np.zeros(1), np.zeros(1)
+    want = [-1.0, -2.0 / 3.0, -2.0 / 3.0 - np.sqrt(37.0) / 35.0]
+    for t, (g, w) in enumerate(zip((2.0, -2.0, 1.0), want), start=1):
+        p, m, v = O.adamw_step(p, np.array([g]), m, v, t, lr=1.0, b1=0.5, b2=0.75, eps=0.0)
+        np.testing.assert_allclose(p, [w], rtol=1e-14)
+    np.testing.assert_allclose(m, [0.25], rtol=1e-14)
+    np.testing.assert_allclose(v, [25.0 / 16.0], rtol=1e-14)
+    g = np.array([0.3, -0.02, 1e-3])
+    p, m, v = np.array([1.0, -2.0, 0.5]), np.zeros(3), np.zeros(3)
+    for t in range(1, 4):
+        want = p - 0.05 * (g / (np.abs(g) + 1e-8) + 0.01 * p)
+        p, m, v = O.adamw_step(p, g, m, v, t, lr=0.05, wd=0.01)
+        np.testing.assert_allclose(p, want, rtol=1e-12)
+
+
 def test_union_with_folded_damping_is_block_diagonal():
     """Disjoint graphs with each graph's damping folded into its weights
     (W~ = beta_g W_g on graph g's block, index beta = 1): the union's Katz
