@@ -263,20 +263,24 @@ int sparse_katz_topk(const katz_index* idx, const int32_t* q, int32_t b, int32_t
 
 /* linkpred_topk without any device allocation.  The paper has no
  * counterpart: this serves callers that must not allocate device memory
- * while they run -- work recorded into a CUDA stream capture (where
- * cudaMalloc is not allowed), latency-critical serving loops, or processes
- * whose device memory is held by another framework's caching allocator.
- * Same arguments and results as linkpred_topk, except that q, K, ids_out
- * and scores_out must all be DEVICE pointers.  The candidate lists live in
- * a fixed scratch array inside the library (3 MiB per GPU, held until the
- * process exits) that holds up to 2^18 entries: b * k must not exceed
- * 32,768, else KATZ_EINVAL.  No cudaMalloc, cudaFree or allocating library
- * routine is called.  The first call on each device looks up the scratch
- * array's device address (cudaGetSymbolAddress), so make that first call
- * before any stream capture.  All calls share the one scratch array (it
- * keeps the last call's contents): calls that overlap on the GPU -- on
- * different streams or threads -- race and must be serialised by the
- * caller.  Returns after the results are complete. */
+ * while they run -- a serving loop whose latency budget has no room for an
+ * allocation (cudaMalloc may synchronise the device), or a process whose
+ * device memory is already reserved by another framework's caching
+ * allocator, so that a fresh cudaMalloc would fail although the caller's
+ * own buffers are in place.  Same arguments and results as linkpred_topk,
+ * except that q, K, ids_out and scores_out must all be DEVICE pointers.
+ * The candidate lists live in a fixed scratch array inside the library
+ * (3 MiB per GPU that loads the library, held until the process exits)
+ * that holds up to 2^18 entries: b * k must not exceed 32,768, else
+ * KATZ_EINVAL.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.  The first call on each device looks up the scratch array's
+ * device address (cudaGetSymbolAddress, with that device current), so make
+ * that first call before any stream capture.  The call copies the query
+ * ids to the host to check them and synchronises `stream` before its
+ * kernels and again when they are done.  All calls share the one scratch
+ * array (it keeps the last call's contents): calls that overlap on the
+ * GPU -- on different streams or threads -- race and must be serialised by
+ * the caller. */
 int linkpred_topk_noalloc(const katz_index* idx, const int32_t* q, int32_t b, const void* K,
                           int32_t k_dtype, int64_t ldk, int32_t k, int32_t* ids_out,
                           double* scores_out, void* stream);

@@ -3,14 +3,15 @@
 // array instead of memory obtained from cudaMalloc.
 //
 // Who needs this: code that must not allocate device memory while it runs
-// -- for example work issued inside a CUDA stream capture (cudaMalloc is not
-// permitted there), a latency-critical serving loop that cannot afford an
-// allocation or its implicit synchronisation, or a process whose device
+// -- a serving loop whose latency budget has no room for an allocation
+// (cudaMalloc may synchronise the whole device), or a process whose device
 // memory is already reserved by another framework's caching allocator, so
 // that a fresh cudaMalloc would fail although the caller's own buffers are
 // in place.  Such callers pass every input and output; this entry point
 // touches no allocator (no cudaMalloc/cudaFree, no library routine that
-// allocates).
+// allocates).  It checks the query ids on the host (one small copy into a
+// fixed host array) and synchronises the caller's stream before and after
+// its kernels.
 #include <atomic>
 #include <cstring>
 #include <mutex>
