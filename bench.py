@@ -78,15 +78,23 @@ def parse():
     return ap.parse_args()
 
 
+def values_label(g, stored):
+    """What the index stores for the matrix values: unit-weight graphs keep
+    the pattern only (every weight 1, exact in any type)."""
+    if g.val is None or np.all(np.asarray(g.val) == 1.0):
+        return "pattern only (unit weights)"
+    return f"{stored} values"
+
+
 def workload_desc(g, b, c, rank, scale, workload=3):
     if workload == 2:
         desc = (f"Chung-Lu power law n={g.n:,} (exponent 2.1, mean degree 16, cap 20,000), "
-                f"FP32 values, b={b} queries, r={rank}, top-1% hubs, beta={c:.6g}/lambda_max, "
-                f"tol 1e-6 (inf-norm error bound)")
+                f"{values_label(g, 'FP32')}, b={b} queries, r={rank}, top-1% hubs, "
+                f"beta={c:.6g}/lambda_max, tol 1e-6 (inf-norm error bound)")
     else:
         desc = (f"modular SBM n={g.n:,} (512 lognormal communities, degree 20, 5% inter, "
-                f"2,000 hubs x ~5,000 edges), BF16 values, b={b} queries, r={rank}, "
-                f"beta={c:.6g}/lambda_max, tol 1e-6 (inf-norm error bound)")
+                f"2,000 hubs x ~5,000 edges), {values_label(g, 'BF16')}, b={b} queries, "
+                f"r={rank}, beta={c:.6g}/lambda_max, tol 1e-6 (inf-norm error bound)")
     return {
         "workload": desc,
         "n": g.n, "nnz": g.nnz, "global_batch": b, "rank": rank, "c": c, "scale": scale,
@@ -260,7 +268,7 @@ def oracle_sample(g, beta, c, q_sample, tol):
 _POOL_W = None
 
 
-def _pool_attach(specs, n, beta):
+def _pool_attach(specs, n, beta, out_spec=None):
     global _POOL_W
     import scipy.sparse as sp
     from multiprocessing import shared_memory
@@ -269,7 +277,12 @@ def _pool_attach(specs, n, beta):
         m = shared_memory.SharedMemory(name=name)
         keep.append(m)
         arrs.append(np.ndarray(shape, dtype=dtype, buffer=m.buf))
-    _POOL_W = (sp.csr_matrix((arrs[2], arrs[1], arrs[0]), shape=(n, n)), beta, keep)
+    out = None
+    if out_spec is not None:
+        m = shared_memory.SharedMemory(name=out_spec[0])
+        keep.append(m)
+        out = np.ndarray(out_spec[1], dtype=out_spec[2], buffer=m.buf)
+    _POOL_W = (sp.csr_matrix((arrs[2], arrs[1], arrs[0]), shape=(n, n)), beta, keep, out)
 
 
 def _pool_ready(_):
@@ -278,11 +291,13 @@ def _pool_ready(_):
 
 def _pool_solve(args):
     import oracle
-    q, rtol = args
-    W, beta, _ = _POOL_W
+    q, rtol, slot = args
+    W, beta, _, out = _POOL_W
     # column q of the symmetric W is its row q (an O(degree) slice)
     B = beta * W.getrow(q).toarray().reshape(-1, 1)
-    _, it = oracle.katz_cg(W, beta, [q], rtol=rtol, B=B)
+    X, it = oracle.katz_cg(W, beta, [q], rtol=rtol, B=B)
+    if out is not None and slot >= 0:  # keep the Katz vector for the parity check
+        out[:, slot] = X[:, 0]
     return int(it[0])
 
 
@@ -292,9 +307,10 @@ class OraclePool:
     query column per task.  Use as a context manager; solve() returns the
     wall time of one batch of columns solved at once."""
 
-    def __init__(self, g, beta, workers):
+    def __init__(self, g, beta, workers, keep_columns=0):
         self.g, self.beta, self.workers = g, beta, workers
-        self.shms, self.pool = [], None
+        self.keep = keep_columns  # > 0: solve() keeps up to this many Katz vectors
+        self.shms, self.pool, self.columns = [], None, None
 
     def __enter__(self):
         import multiprocessing as mp
@@ -303,6 +319,7 @@ class OraclePool:
         try:
             W = oracle.adjacency(self.g.n, self.g.rowptr, self.g.col, self.g.val)
             need = sum(a.nbytes for a in (W.indptr, W.indices, W.data))
+            need += 8 * self.g.n * self.keep
             st = os.statvfs("/dev/shm")
             if st.f_bavail * st.f_frsize < 1.25 * need:  # a full tmpfs would SIGBUS the writer
                 raise RuntimeError(f"/dev/shm has room for less than {need / 1e9:.1f} GB")
@@ -312,10 +329,18 @@ class OraclePool:
                 self.shms.append(m)
                 np.ndarray(a.shape, dtype=a.dtype, buffer=m.buf)[:] = a
                 specs.append((m.name, a.shape, a.dtype.str))
+            out_spec = None
+            if self.keep > 0:
+                shape = (self.g.n, self.keep)
+                m = shared_memory.SharedMemory(create=True, size=8 * self.g.n * self.keep)
+                self.shms.append(m)
+                self.columns = np.ndarray(shape, dtype=np.float64, buffer=m.buf)
+                out_spec = (m.name, shape, np.dtype(np.float64).str)
             # bounded waits: a pool whose workers cannot start would respawn
             # them forever; __exit__ terminates it
             self.pool = mp.get_context("spawn").Pool(
-                self.workers, initializer=_pool_attach, initargs=(specs, self.g.n, self.beta))
+                self.workers, initializer=_pool_attach,
+                initargs=(specs, self.g.n, self.beta, out_spec))
             ready = self.pool.map_async(_pool_ready, range(self.workers),
                                         chunksize=1).get(timeout=90)
             if not all(ready):
@@ -326,8 +351,12 @@ class OraclePool:
         return self
 
     def solve(self, q_sample, rtol):
+        """Wall time of the columns q_sample solved at once; with
+        keep_columns, column j of self.columns then holds k_{q_sample[j]}."""
         t = time.perf_counter()
-        self.pool.map_async(_pool_solve, [(int(q), rtol) for q in q_sample],
+        self.pool.map_async(_pool_solve,
+                            [(int(q), rtol, j if j < self.keep else -1)
+                             for j, q in enumerate(q_sample)],
                             chunksize=1).get(timeout=180)
         return time.perf_counter() - t
 
@@ -336,6 +365,7 @@ class OraclePool:
             self.pool.terminate()
             self.pool.join()
             self.pool = None
+        self.columns = None
         for m in self.shms:
             m.close()
             m.unlink()
@@ -345,9 +375,33 @@ class OraclePool:
 
 def oracle_all_cores(g, beta, q_sample, rtol, workers):
     """Wall time of the oracle's CG on len(q_sample) columns solved by
-    `workers` spawned processes at once (one column each)."""
-    with OraclePool(g, beta, workers) as pool:
-        return pool.solve(q_sample, rtol)
+    `workers` spawned processes at once (one column each), and the Katz
+    vectors they returned (n x len(q_sample))."""
+    with OraclePool(g, beta, workers, keep_columns=len(q_sample)) as pool:
+        dt = pool.solve(q_sample, rtol)
+        return dt, np.array(pool.columns)
+
+
+def topk_agreement(g, Kref, q_sample, ids_gpu, k=20, band_rel=2e-6):
+    """Share of the sampled queries whose GPU top-k list equals the oracle's
+    up to exact ties: every oracle candidate scoring more than band_rel *
+    ||k_q||_inf above the oracle's k-th score is in the GPU list, and every
+    GPU candidate scores within that band of the k-th score or above
+    (candidates, q and its neighbours excluded, follow the oracle's
+    link-prediction reading of Section 3.3)."""
+    import oracle
+    W = oracle.adjacency(g.n, g.rowptr, g.col, g.val)
+    rid, rsc = oracle.linkpred_topk(W, Kref, q_sample, k)
+    ok = 0
+    for j, q in enumerate(q_sample):
+        band = band_rel * np.abs(Kref[:, j]).max()
+        must = set(rid[j][rsc[j] > rsc[j][-1] + band].tolist())
+        got = set(int(x) for x in ids_gpu[j])
+        excl = set(W.indices[W.indptr[q]:W.indptr[q + 1]].tolist()) | {int(q)}
+        cand_ok = all(x >= 0 and x not in excl and Kref[x, j] >= rsc[j][-1] - band
+                      for x in got)
+        ok += int(must <= got and cand_ok and len(got) == k)
+    return ok / max(1, len(q_sample))
 
 
 # ---------------------------------------------------------------- reference
@@ -687,21 +741,33 @@ def main():
     lrc_stats = dict(last["st"])
     lrc_iters = float(np.mean(last["it"]))
 
-    # ---- plain CG on the same batch (the comparison method)
+    # ---- plain CG on the same batch (the comparison method), timed like the
+    # LRC arm: warm-up calls, then CUDA events on the stream over several
+    # batches (the same queries, the same 1e-6 error bound)
     cg = None
     if not args.no_cg:
+        cg_warm, cg_steps = max(1, min(args.warmup, 3)), max(1, min(args.steps, 5))
+        for _ in range(cg_warm):
+            katz.cg_query_batch(idx, qd, K, out_dtype=katz.KATZ_F32, tol=1e-6, gather_kernel=gk)
+        torch.cuda.synchronize()
         katz.katz_profile_enable(True)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(cg_steps):
+            st_cg, it_cg, rel_cg = katz.cg_query_batch(idx, qd, K, out_dtype=katz.KATZ_F32,
+                                                       tol=1e-6, gather_kernel=gk)
+        c1.record(stream)
         torch.cuda.synchronize()
-        c0 = time.perf_counter()
-        st_cg, it_cg, rel_cg = katz.cg_query_batch(idx, qd, K, out_dtype=katz.KATZ_F32, tol=1e-6)
-        torch.cuda.synchronize()
-        cg_ms = 1000 * (time.perf_counter() - c0)
+        cg_ms = max_over_ranks(world, c0.elapsed_time(c1) / cg_steps)
         pc = katz.katz_profile_read("spmm_f32")
         katz.katz_profile_enable(False)
         hbm, _ = peaks()
-        cg = {"queries_per_s": b / (cg_ms / 1000), "ms_per_batch": cg_ms,
+        cg = {"queries_per_s": world * b / (cg_ms / 1000), "ms_per_batch": cg_ms,
+              "steps": cg_steps, "warmup": cg_warm, "timing": "CUDA events over the steps",
               "mean_iters": float(np.mean(it_cg)), "refine_steps": st_cg["refine_steps"],
-              "max_rel_res": st_cg["max_rel_res"],
+              "max_rel_res": st_cg["max_rel_res"], "status": st_cg["status"],
+              "lrc_speedup": cg_ms / ms,
               "spmm_f32_gbs": pc["bytes"] / (pc["ms"] / 1e3) / 1e9 if pc["ms"] else None,
               "spmm_f32_frac": (pc["bytes"] / (pc["ms"] / 1e3) / 1e9) / hbm if pc["ms"] else None}
         # restore the LRC answer for the parity sample below
@@ -775,16 +841,16 @@ def main():
                        if v["ms"] else None}
                for t, v in prof.items() if v["launches"]}
 
-    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1)
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1), and
+    # parity of the GPU answers on every column the oracle solved: max
+    # infinity-norm relative error and top-20 agreement up to exact ties
     cpu = None
     parity = None
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
         ns = 2
         qs = q[:ns]
         Kref, dt, it, rtol = oracle_sample(g, beta, c, qs, 1e-6)
-        import oracle
-        Kg = K[:, :ns].double().cpu().numpy()
-        parity = float(oracle.error_inf_rel(Kg, Kref).max())
+        cols, refs = list(range(ns)), [Kref]
         cpu = {"value": ns / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": f"{ns} of the {b} queries, FP64 CG (SciPy CSR, 1 thread) to the same "
                          f"1e-6 error bound (rtol {rtol:.2e}), {dt:.1f} s"}
@@ -793,7 +859,9 @@ def main():
         if workers > 1:
             try:
                 qa = q[ns:ns + workers]
-                dta = oracle_all_cores(g, beta, qa, rtol, workers)
+                dta, Ka = oracle_all_cores(g, beta, qa, rtol, workers)
+                cols += list(range(ns, ns + len(qa)))
+                refs.append(Ka)
                 cpu.update({"value": len(qa) / dta, "cores": workers,
                             "value_1core": ns / dt,
                             "sample": f"{len(qa)} of the {b} queries solved at once, one per "
@@ -802,6 +870,14 @@ def main():
                                       f"1 core: {ns} queries in {dt:.1f} s"})
             except Exception as e:  # keep the single-core number
                 cpu["all_cores_error"] = str(e)[:200]
+        import oracle
+        Kref = np.concatenate(refs, axis=1)
+        Kg = K[:, cols].double().cpu().numpy()
+        err = oracle.error_inf_rel(Kg, Kref)
+        parity = {"columns": len(cols), "max_err_vs_oracle": float(err.max()),
+                  "topk_agree": topk_agreement(g, Kref, q[cols], ids[cols].cpu().numpy()),
+                  "oracle_bound": "FP64 CG to the same 1e-6 error bound (its own error is "
+                                  "at most that bound)"}
 
     if rank == 0:
         cfg = workload_desc(g, b, c, rank_r, args.scale, args.workload)
@@ -821,13 +897,17 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-               "dtype": "f32 (bf16 matrix values, f64 refinement)", "data": "synthetic",
+               "dtype": ("f32 (" + values_label(g, "bf16" if args.workload == 3 else "f32") +
+                         ", float-float f64-class residual refinement)"),
+               "data": "synthetic",
                "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clk,
                "lrc": {"mean_iters": lrc_iters, **{k: lrc_stats[k] for k in
                                                    ("refine_steps", "max_rel_res", "status")}},
                "cg": cg, "sparse_katz": sk, "kernels": kernels,
-               "max_err_vs_oracle_sample": parity}
+               "max_err_vs_oracle": parity["max_err_vs_oracle"] if parity else None,
+               "topk_agree": parity["topk_agree"] if parity else None,
+               "parity": parity}
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

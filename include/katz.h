@@ -68,10 +68,26 @@ extern "C" {
 #define KATZ_GATHER_REGISTER 1
 #define KATZ_GATHER_PIPELINED 2
 
+/* Gathers of the Chebyshev steps on the large M11 blocks (KATZ_PREC_MIXED
+ * and F32 paths).  The iterates are kept as two BF16 planes hi = bf16(x),
+ * lo = bf16(x - hi) (FP32 storage size, x to 2^-18 relative), so a step's
+ * product can gather the hi plane alone: half the bytes per gathered row,
+ * at ~2^-9 relative error per gathered term.
+ * AUTO: hi-plane gathers on every step whose perturbation a later step
+ * damps -- all steps after the first, except that the last step of a solve
+ * asked for a tolerance below 1e-4 gathers hi + lo;
+ * F32: FP32 iterates and FP32 gathers on every step;
+ * BF16: hi-plane gathers on every step after the first. */
+#define KATZ_CHEB_AUTO 0
+#define KATZ_CHEB_F32 1
+#define KATZ_CHEB_BF16 2
+
 #define KATZ_TOL_RESIDUAL 0  /* stop column j when ||b_j - M k_j||_2 <= tol * ||b_j||_2 */
 #define KATZ_TOL_ERROR_INF 1 /* stop when ||b_j - M k_j||_2 <= tol * (1 - beta*lambda) * ||b_j||_inf,
+                                lambda a rigorous upper bound on lambda_max (katz_lambda_bounds),
                                 which guarantees ||k_j - k_j*||_inf <= tol * ||k_j*||_inf for
-                                non-negative weights (||M^{-1}||_2 = 1/(1 - beta*lambda), k* >= b >= 0) */
+                                non-negative weights (||M^{-1}||_2 <= 1/(1 - beta*lambda),
+                                k* >= b >= 0) */
 
 typedef struct katz_index katz_index; /* opaque; owns all device memory of one graph */
 
@@ -116,6 +132,7 @@ typedef struct {
   int32_t warm_start;  /* 1: start LRC from the learned warm start (needs a trained network) */
   int32_t gather_kernel; /* KATZ_GATHER_*: kernel of the wide sparse products (Chebyshev
                             steps of the large M11 blocks, refinement residual) */
+  int32_t cheb_gather;   /* KATZ_CHEB_*: precision of the Chebyshev steps' gathers */
 } katz_query_opts;
 
 typedef struct {
@@ -132,6 +149,9 @@ typedef struct {
   double beta;
   double lambda_max_R; /* largest Ritz value sigma_1 of R (0 if rank 0) */
   int64_t device_bytes;
+  double lambda_max_W; /* largest Lanczos Ritz value of W (a lower bound on lambda_max) */
+  double lambda_upper; /* rigorous upper bound on lambda_max of W (Collatz-Wielandt); the SPD
+                          check and the KATZ_TOL_ERROR_INF rule use it */
 } katz_index_info;
 
 /* ---------------------------------------------------------------- graph */
@@ -139,8 +159,21 @@ typedef struct {
 /* Largest eigenvalue lambda_max of the symmetric W (= ||W||_2 for W >= 0),
  * the bound of Section 3.1 (beta < 1/||W||_2), by FP64 Lanczos on the GPU
  * (`steps` iterations, 0 = 64).  W is host CSR as above.  *out receives
- * lambda_max.  Errors: KATZ_EINVAL on a malformed CSR. */
+ * the largest Ritz value, an estimate from below.  Errors: KATZ_EINVAL on
+ * a malformed CSR. */
 int katz_lambda_max(const katz_csr* W, int32_t steps, double* out, void* stream);
+
+/* Both sides of lambda_max of W (host CSR, weights > 0) after `steps`
+ * Lanczos steps (0 = 64): *ritz (may be NULL) the largest Ritz value, which
+ * never exceeds lambda_max, and *upper (may be NULL) a rigorous upper
+ * bound, max_i (W x)_i / x_i for the positive vector x = |y| + f max|y| of
+ * the top Ritz vector y (the Collatz-Wielandt bound for W >= 0; the
+ * smallest over a few floors f, each valid).  The index build refuses beta
+ * unless beta * upper < 1 (M certified positive definite, Section 3.1),
+ * and the KATZ_TOL_ERROR_INF stopping rule uses 1 - beta * upper as the
+ * lower bound on the smallest eigenvalue of M.  Errors: KATZ_EINVAL. */
+int katz_lambda_bounds(const katz_csr* W, int32_t steps, double* ritz, double* upper,
+                       void* stream);
 
 /* Build the query index for damping `beta` (Algorithm 1, "Preprocess").
  * Always: validates W (CSR shape, symmetry), uploads it.  With
@@ -319,6 +352,16 @@ int katz_autotune(katz_index* idx, int32_t b, int32_t* out, double* ms, void* st
  * reported a timeout. */
 int katz_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int32_t M, int32_t N,
                    int32_t K, float alpha, float beta, float* C, int64_t ldc, void* stream);
+
+/* Test hook (no GPU fault is involved): while `on` is non-zero, the
+ * rank-r tensor-core GEMM (katz_gemm_bf16 and the preconditioner products)
+ * issues no TMA copy, so the wait of its MMA-issuing thread on the first
+ * pipeline stage runs out after its bounded spin (about two seconds) with
+ * nothing in flight; the kernel releases its tensor memory and reports the
+ * timeout, and the call returns KATZ_ECUDA.  Switch it off again (on = 0)
+ * for normal work; the library and the CUDA context stay usable.
+ * Process-wide.  Always returns KATZ_OK. */
+int katz_test_stall_copies(int32_t on);
 
 /* FP32-accurate tensor-core product C = alpha * A B^T + beta * C from three
  * TF32 tcgen05 products of the TF32 high/low parts of A and B (the kernel of

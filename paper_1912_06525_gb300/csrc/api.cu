@@ -163,9 +163,10 @@ extern "C" {
 
 const char* katz_last_error(void) { return g_last_error.c_str(); }
 
-int katz_lambda_max(const katz_csr* W, int32_t steps, double* out, void* stream) {
+int katz_lambda_bounds(const katz_csr* W, int32_t steps, double* ritz, double* upper,
+                       void* stream) {
   return guarded([&]() {
-    KATZ_REQUIRE(out, KATZ_EINVAL, "null output");
+    KATZ_REQUIRE(ritz || upper, KATZ_EINVAL, "null outputs");
     katz::HostCsr h = read_csr(W);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     katz::GraphPart g;
@@ -178,9 +179,18 @@ int katz_lambda_max(const katz_csr* W, int32_t steps, double* out, void* stream)
     if (!heavy.empty())
       KATZ_CUDA(cudaMemcpy(g.heavy.p, heavy.data(), 4 * heavy.size(), cudaMemcpyHostToDevice));
     katz::Workspace ws;
-    *out = katz::lambda_max_gpu(g, h.nrows, steps > 0 ? steps : 64, ws, s);
+    double up = 0;
+    const double r = katz::lambda_max_gpu(g, h.nrows, steps > 0 ? steps : 64, ws, s, 0, nullptr,
+                                          upper ? &up : nullptr);
+    if (ritz) *ritz = r;
+    if (upper) *upper = up;
     return KATZ_OK;
   });
+}
+
+int katz_lambda_max(const katz_csr* W, int32_t steps, double* out, void* stream) {
+  if (!out) return guarded([&]() -> int { throw katz::Error(KATZ_EINVAL, "null output"); });
+  return katz_lambda_bounds(W, steps, out, nullptr, stream);
 }
 
 int katz_index_build(const katz_csr* W, double beta, const katz_build_opts* opts, void* stream,
@@ -243,6 +253,8 @@ int katz_index_get_info(const katz_index* idx, katz_index_info* info) {
     info->value_dtype = idx->vdt;
     info->beta = idx->beta;
     info->lambda_max_R = idx->sigma.empty() ? 0.0 : idx->sigma[0];
+    info->lambda_max_W = idx->lambda;
+    info->lambda_upper = idx->lambda_up;
     int64_t bytes = idx->W.csr.bytes() + idx->Wp.csr.bytes() + idx->W12.csr.bytes() +
                     idx->W21.csr.bytes() + idx->W11L.csr.bytes() + idx->S32.bytes() +
                     idx->S64.bytes() + idx->M22inv32.bytes() + idx->M22inv64.bytes() +
@@ -595,6 +607,11 @@ int katz_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int32
     KATZ_REQUIRE(h == 0, KATZ_ECUDA, "tcgen05 GEMM pipeline timed out");
     return KATZ_OK;
   });
+}
+
+int katz_test_stall_copies(int32_t on) {
+  katz::set_test_stall_copies(on != 0);
+  return KATZ_OK;
 }
 
 int katz_gemm_tf32x3(const float* A, int64_t lda, const float* B, int64_t ldb, int32_t M,

@@ -65,11 +65,14 @@ struct Partition {
 
 }  // namespace katz
 
-// Every field except `ws` and `gather_pref` is stored by save_index
+// Every field except `ws`, `gather_pref` and `cheb_pref` is stored by save_index
 // (index_io.cu): a field added here is added to its list too.
 struct katz_index {
   int64_t n = 0, nnz = 0;
-  double beta = 0, lambda = 0;
+  // lambda: largest Lanczos Ritz value of W (a lower bound on lambda_max);
+  // lambda_up: rigorous upper bound, used for the SPD check and the
+  // error-bound stopping rule
+  double beta = 0, lambda = 0, lambda_up = 0;
   std::vector<int32_t> deg_h;  // node degrees (host), bound the RHS fix-up grid
   int64_t maxdeg = 0;
   bool unit_weights = false;  // every stored weight is exactly 1 (fixed-point residual)
@@ -87,6 +90,7 @@ struct katz_index {
   double lam11 = 0, lam11_min = 0;
   // kernel preference of the query being run (KATZ_GATHER_*), set per query
   int gather_pref = KATZ_GATHER_AUTO;
+  int cheb_pref = KATZ_CHEB_AUTO;  // per query, like gather_pref
   katz::Partition part;
   katz::DBuf<int32_t> perm, iperm;
   katz::GraphPart Wp;    // W in index order (full), for FP64 residuals
@@ -135,7 +139,7 @@ struct katz_multi {
   int64_t n = 0, nnz = 0;
   int vdt = KATZ_F32;
   std::vector<int64_t> seg_ptr_h;
-  std::vector<double> beta_h, lambda_h;
+  std::vector<double> beta_h, lambda_h;  // lambda_h: rigorous upper bounds on lambda_max
   std::vector<int32_t> deg_h;
   katz::GraphPart W;
   katz::DBuf<int64_t> seg_ptr;
@@ -169,11 +173,12 @@ struct SegSpec {
   std::vector<int> ranks;
 };
 
-// Largest eigenvalue of W by FP64 Lanczos on the GPU.
-// Largest Ritz value of W after `steps` FP64 Lanczos steps (start: all-ones
-// if seed == 0, else SplitMix64(seed)); *lmin (optional) gets the smallest.
+// Largest Ritz value of W after `steps` FP64 Lanczos steps on the GPU
+// (start: all-ones if seed == 0, else SplitMix64(seed)); *lmin (optional)
+// gets the smallest, *lup (optional) a rigorous upper bound on lambda_max
+// for W >= 0 (Collatz-Wielandt bound from the top Ritz vector).
 double lambda_max_gpu(const GraphPart& W, int64_t n, int steps, Workspace& ws, cudaStream_t s,
-                      uint64_t seed = 0, double* lmin = nullptr);
+                      uint64_t seed = 0, double* lmin = nullptr, double* lup = nullptr);
 
 void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_build_opts& o,
                  cudaStream_t s, const SegSpec* seg = nullptr);

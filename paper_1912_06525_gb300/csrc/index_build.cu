@@ -293,11 +293,50 @@ static double dget(const double* p, cudaStream_t s) {
 }
 
 // ----------------------------------------------------------- lambda_max
+// x_i = |y_i| + floor on column 0 of an ld-strided vector.
+__global__ void abs_floor_kernel(const double* y, double* x, int64_t ld, int64_t n, double fl) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    x[i * ld] = fabs(y[i * ld]) + fl;
+}
+// out = max_i (W x)_i / x_i for x > 0: non-negative doubles order like their
+// bit patterns, so atomicMax on the bits gives the maximum.
+__global__ void cw_ratio_kernel(const double* wx, const double* x, int64_t ld, int64_t n,
+                                unsigned long long* out) {
+  double m = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    m = fmax(m, wx[i * ld] / x[i * ld]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// x <- a w + c x on column 0 of ld-strided vectors.
+__global__ void axpby_col_kernel(const double* w, double* x, int64_t ld, int64_t n, double a,
+                                 double c) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    x[i * ld] = a * w[i * ld] + c * x[i * ld];
+}
+
 // Plain Lanczos on W from the normalised all-ones vector; the largest Ritz
-// value of the tridiagonal matrix is returned.
+// value of the tridiagonal matrix is returned.  The Ritz value is a lower
+// bound on lambda_max.  With `lup`, also a rigorous UPPER bound: for
+// W >= 0 and any x > 0, lambda_max = rho(W) <= max_i (W x)_i / x_i (the
+// Collatz-Wielandt bound: D^{-1} W D with D = diag(x) has these row sums
+// and the same spectrum).  x starts as |y| + f max|y| for the top Ritz
+// vector y (rebuilt by a second pass of the recurrence with the stored
+// coefficients); the floor f keeps x > 0.  Where y vanishes (components
+// that do not carry lambda_max) or is below its rounding, the ratio is
+// governed by the floor instead, so x is also smoothed by a few steps of
+// the positive map x <- (W x + s x) / (2 s), s the Ritz value, which moves
+// every component towards its own Perron vector and never raises the
+// largest ratio.  Every (floor, step) gives a valid bound; the smallest is
+// kept, times 1 + 1e-11 for the rounding of the ratios.
 double lambda_max_gpu(const GraphPart& W, int64_t n, int steps, Workspace& ws, cudaStream_t s,
-                      uint64_t seed, double* lmin) {
+                      uint64_t seed, double* lmin, double* lup) {
   if (lmin) *lmin = 0.0;
+  if (lup) *lup = 0.0;
   if (n == 0 || W.csr.nnz == 0) return 0.0;
   const int64_t ld = 2;
   double* v = ws.get<double>("lm.v", n * ld);
@@ -343,7 +382,49 @@ double lambda_max_gpu(const GraphPart& W, int64_t n, int steps, Workspace& ws, c
   be.resize(std::max(0, m - 1));
   tridiag_ql(ev, be, Z, m);
   if (lmin) *lmin = *std::min_element(ev.begin(), ev.end());
-  return *std::max_element(ev.begin(), ev.end());
+  const int top = int(std::max_element(ev.begin(), ev.end()) - ev.begin());
+  if (lup) {
+    // second pass: y = sum_j Z[j][top] v_j with the stored coefficients
+    double* y = ws.get<double>("lm.y", n * ld);
+    KATZ_CUDA(cudaMemcpyAsync(v, start.data(), sizeof(double) * n * ld, cudaMemcpyHostToDevice, s));
+    KATZ_CUDA(cudaMemsetAsync(vp, 0, sizeof(double) * n * ld, s));
+    KATZ_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n * ld, s));
+    for (int j = 0; j < m; ++j) {
+      scale_copy<double>(v, ld, y, ld, n, 1, Z[size_t(j) * m + top], true, s);
+      if (j == m - 1) break;
+      spmm<double>(W.view(), W.heavy.p, W.n_heavy, 1.0, v, ld, 0.0, nullptr, ld, w, ld, 1,
+                   nullptr, 0, nullptr, s);
+      scale_copy<double>(v, ld, w, ld, n, 1, -al[j], true, s);
+      if (j > 0) scale_copy<double>(vp, ld, w, ld, n, 1, -be[j - 1], true, s);
+      std::swap(vp, v);
+      scale_copy<double>(w, ld, v, ld, n, 1, 1.0 / be[j], false, s);
+    }
+    double* nrm = ws.get<double>("lm.n", 2);
+    double* mx = ws.get<double>("lm.mx", 2);
+    col_norms<double>(y, ld, n, 1, nrm, mx, s);
+    const double ymax = dget(mx, s);
+    double best = HUGE_VAL;
+    const double sig = std::max(ev[top], 1e-300);
+    const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 4096));
+    for (double f : {1e-12, 1e-8, 1e-4, 1e-1}) {
+      // x = |y| + f max|y| (the all-ones vector when y vanishes)
+      abs_floor_kernel<<<nb, 256, 0, s>>>(y, v, ld, n, ymax > 0 ? f * ymax : 1.0);
+      KATZ_CHECK_LAUNCH();
+      for (int k = 0; k <= 16; ++k) {
+        spmm<double>(W.view(), W.heavy.p, W.n_heavy, 1.0, v, ld, 0.0, nullptr, ld, w, ld, 1,
+                     nullptr, 0, nullptr, s);
+        KATZ_CUDA(cudaMemsetAsync(dd, 0, sizeof(double), s));
+        cw_ratio_kernel<<<nb, 256, 0, s>>>(w, v, ld, n, reinterpret_cast<unsigned long long*>(dd));
+        KATZ_CHECK_LAUNCH();
+        best = std::min(best, dget(dd, s));
+        axpby_col_kernel<<<nb, 256, 0, s>>>(w, v, ld, n, 0.5 / sig, 0.5);
+        KATZ_CHECK_LAUNCH();
+      }
+      if (ymax <= 0) break;
+    }
+    *lup = best * (1.0 + 1e-11);
+  }
+  return ev[top];
 }
 
 // --------------------------------------------------------- device helpers
@@ -679,10 +760,16 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   // product then runs its unit-weight kernel (no weight loads or products)
   const int sdt = idx.unit_weights ? int(KATZ_UNIT) : o.value_dtype;
   upload_part(W, sdt, idx.W, s);
-  idx.lambda = lambda_max_gpu(idx.W, idx.n, 96, idx.ws, s);
+  // Ritz value (a lower bound on lambda_max) and a rigorous upper bound: M is
+  // certified SPD and the error-bound stopping rule is sound only with the
+  // upper bound
+  idx.lambda = lambda_max_gpu(idx.W, idx.n, 96, idx.ws, s, 0, nullptr, &idx.lambda_up);
   KATZ_REQUIRE(beta * idx.lambda < 1.0, KATZ_ENOTSPD,
                "beta * lambda_max = " + std::to_string(beta * idx.lambda) +
                    " >= 1: M = I - beta W is not positive definite");
+  KATZ_REQUIRE(beta * idx.lambda_up < 1.0, KATZ_ENOTSPD,
+               "beta * (upper bound on lambda_max) = " + std::to_string(beta * idx.lambda_up) +
+                   " >= 1: M = I - beta W cannot be certified positive definite");
   if (!o.build_lrc) return;
 
   idx.lrc = true;
@@ -815,10 +902,13 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   if (W11L.nrows > 0 && W11L.nnz() > 0) {
     // Lanczos Ritz values lie inside the spectrum: widen both ends by 2% of
     // its width; the lower end never below -lambda_max (W11 >= 0)
-    const double top = lambda_max_gpu(idx.W11L, W11L.nrows, 96, idx.ws, s);
-    double bot = 0;
+    double up = 0, bot = 0;
+    const double top = lambda_max_gpu(idx.W11L, W11L.nrows, 96, idx.ws, s, 0, nullptr, &up);
     lambda_max_gpu(idx.W11L, W11L.nrows, 96, idx.ws, s, 0x243F6A8885A308D3ull, &bot);
-    const double lam = 1.02 * top;
+    // the upper end is the rigorous bound (so no eigenvalue of M11 lies below
+    // the interval, where the iteration would diverge); the lower end widened
+    // by 2% of the width (an eigenvalue slightly above it costs only speed)
+    const double lam = up;
     idx.lam11 = beta * lam < 0.999 ? lam : 0.0;
     idx.lam11_min = std::max(-lam, std::min(0.0, bot - 0.02 * (top - bot)));
   } else if (W11L.nrows > 0) {

@@ -2,7 +2,7 @@
 // Algorithm 1, Section 3.2: partition, M11 block inverses, couplings, S and
 // M22^{-1}, the rank-r correction W_r D^{1/2}, the warm-start network).
 //
-// File layout (little-endian, version 1):
+// File layout (little-endian, version 2):
 //   magic "KATZIDX\0", u32 version, u32 endian mark 0x01020304,
 //   then one record per field in the order of serialize() below:
 //     u64 tag (FNV-1a of the field name), u32 element size, u64 count,
@@ -22,7 +22,7 @@ namespace katz {
 namespace {
 
 constexpr char kMagic[8] = {'K', 'A', 'T', 'Z', 'I', 'D', 'X', '\0'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 constexpr uint32_t kEndianMark = 0x01020304u;
 constexpr size_t kChunk = size_t(64) << 20;  // staging chunk (a multiple of 8)
 
@@ -235,6 +235,7 @@ void serialize(Archive& a, katz_index& x) {
   a.scalar("nnz", x.nnz);
   a.scalar("beta", x.beta);
   a.scalar("lambda", x.lambda);
+  a.scalar("lambda_up", x.lambda_up);
   a.vec("deg_h", x.deg_h);
   a.scalar("maxdeg", x.maxdeg);
   a.flag("unit_weights", x.unit_weights);
@@ -349,7 +350,7 @@ void check_loaded(const katz_index& x) {
   if (x.n < 0 || x.n >= (int64_t(1) << 31) || int64_t(x.deg_h.size()) != x.n) fail("n");
   if (x.W.csr.nrows != x.n || int64_t(x.W.csr.rowptr.n) != x.n + 1 || x.W.csr.nnz != x.nnz)
     fail("graph");
-  if (!(x.beta > 0) || !(x.beta * x.lambda < 1)) fail("beta");
+  if (!(x.beta > 0) || !(x.lambda_up >= x.lambda) || !(x.beta * x.lambda_up < 1)) fail("beta");
   if (x.lrc) {
     if (x.n1 + x.n2 != x.n || int64_t(x.part.perm.size()) != x.n ||
         int64_t(x.perm.n) != x.n || int64_t(x.iperm.n) != x.n)

@@ -41,6 +41,16 @@ void cheb_step(const Csr& A, double beta, double ak, double ck, const float* Xk,
                const float* Xprev, const float* B, float* Xout, int64_t ld, int b, cudaStream_t s,
                const SpmmCfg* cfg = nullptr, double sx = 1.0, double sp = 1.0);
 
+// The same step with iterates in FP32 rows or in the split form (two BF16
+// planes hi = bf16(x), lo = bf16(x - hi) in an FP32-sized rows x ld buffer,
+// lo starting at element rows * ld).  in_mode: 0 FP32 Xk; 1 split Xk whose
+// product gathers hi alone; 2 split Xk gathered as hi + lo.  prev_mode: 0
+// none (Xprev null), 1 FP32, 2 split.  out_split: write x_{k+1} split.
+void cheb_step_ex(const Csr& A, double beta, double ak, double ck, const void* Xk, int in_mode,
+                  const void* Xprev, int prev_mode, const float* B, void* Xout, int out_split,
+                  int64_t ld, int b, cudaStream_t s, const SpmmCfg* cfg = nullptr,
+                  double sx = 1.0, double sp = 1.0);
+
 // dots[c] += sum_{i<len} A[i,c] * B[i,c]
 template <class VT>
 void coldot(const VT* A, int64_t lda, const VT* B, int64_t ldb, int64_t len, int b,

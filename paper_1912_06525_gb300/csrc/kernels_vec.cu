@@ -342,26 +342,79 @@ template void spmm<double>(const Csr&, const int32_t*, int64_t, double, const do
 // product:
 //   r = b - A x_k = b - x_k + beta W x_k
 //   x_{k+1} = x_k + a_k (x_k - x_{k-1}) + c_k r
-// Xk is gathered and must differ from Xout; Xprev may be null (x_{k-1} = 0)
-// and may equal Xout (each row reads its own x_{k-1} before writing).
-template <int WT, int VPT>
-__global__ void __launch_bounds__(256) cheb_step_kernel(Csr A, float beta, float ak, float ck,
-                                                        float sx, float sp,
-                                                        const float* __restrict__ Xk,
-                                                        const float* Xprev,
-                                                        const float* __restrict__ B, float* Xout,
-                                                        int64_t ld, int b) {
+// Iterates are stored either as FP32 rows or in the split form: an n x ld
+// FP32-sized buffer holding two BF16 planes, hi = bf16(x) (rows of ld
+// elements from the buffer start) and lo = bf16(x - hi) (the same from
+// element `plane` = rows * ld), so that hi + lo carries x to 2^-18
+// relative in the same bytes.  The product's gathers then read either the
+// FP32 rows, the hi plane alone (half the bytes per gathered row; the
+// product's relative error grows to ~2^-9 per term, the accuracy a step of
+// an inexact inner solve can use) or hi and lo (FP32-accurate).  The row's
+// own x_k, x_{k-1} and b are always read in full precision.
+namespace {
+
+enum : int { kInF32 = 0, kInHi = 1, kInHiLo = 2 };
+
+__device__ __forceinline__ void bf16x4_ro(const __nv_bfloat16* p, float (&o)[4]) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+  o[0] = __uint_as_float(u.x << 16);
+  o[1] = __uint_as_float(u.x & 0xffff0000u);
+  o[2] = __uint_as_float(u.y << 16);
+  o[3] = __uint_as_float(u.y & 0xffff0000u);
+}
+__device__ __forceinline__ void bf16x4(const __nv_bfloat16* p, float (&o)[4]) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  o[0] = __uint_as_float(u.x << 16);
+  o[1] = __uint_as_float(u.x & 0xffff0000u);
+  o[2] = __uint_as_float(u.y << 16);
+  o[3] = __uint_as_float(u.y & 0xffff0000u);
+}
+__device__ __forceinline__ uint32_t bf16_bits(float x) {
+  return uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(x)));
+}
+// hi = bf16(x), lo = bf16(x - hi) for 4 consecutive columns
+__device__ __forceinline__ void split_store4(__nv_bfloat16* hi, __nv_bfloat16* lo,
+                                             const float (&x)[4]) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    h[w] = bf16_bits(x[w]);
+    l[w] = bf16_bits(x[w] - __uint_as_float(h[w] << 16));
+  }
+  *reinterpret_cast<uint2*>(hi) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+  *reinterpret_cast<uint2*>(lo) = make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
+}
+
+struct ChebArgs {
+  Csr A;
+  float beta, ak, ck, sx, sp;
+  const void* Xk;     // FP32 rows or split planes
+  const void* Xprev;  // null, FP32 rows or split planes
+  const float* B;
+  void* Xout;         // FP32 rows or split planes
+  int64_t ld, plane;  // plane: element offset of the lo plane in a split buffer
+  int b;
+  int prev_mode;  // 0: x_{k-1} = 0, 1: FP32, 2: split
+  int out_split;  // 1: write x_{k+1} split, 0: FP32
+};
+
+template <int WT, int VPT, int IN>
+__global__ void __launch_bounds__(256) cheb_step_kernel(ChebArgs p) {
   constexpr int VW = 4;
   constexpr int TILE = 32 * VW * VPT;
   const int t = threadIdx.x & 31;
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
   const int tile0 = blockIdx.y * TILE;
+  const int64_t ld = p.ld;
+  const float* Xf = static_cast<const float*>(p.Xk);
+  const __nv_bfloat16* Xh = static_cast<const __nv_bfloat16*>(p.Xk);
+  const __nv_bfloat16* Xl = Xh + p.plane;
   bool cval[VPT];
 #pragma unroll
-  for (int v = 0; v < VPT; ++v) cval[v] = tile0 + (v * 32 + t) * VW < b;
-  for (int64_t i = warp; i < A.nrows; i += nwarps) {
-    const int64_t k0 = A.rowptr[i], k1 = A.rowptr[i + 1];
+  for (int v = 0; v < VPT; ++v) cval[v] = tile0 + (v * 32 + t) * VW < p.b;
+  for (int64_t i = warp; i < p.A.nrows; i += nwarps) {
+    const int64_t k0 = p.A.rowptr[i], k1 = p.A.rowptr[i + 1];
     float acc[VPT][VW];
 #pragma unroll
     for (int v = 0; v < VPT; ++v)
@@ -372,20 +425,30 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(Csr A, float beta, float
       int cj = 0;
       float wj = 0.f;
       if (k < k1) {
-        cj = A.col[k];
-        wj = load_weight<WT, float>(A.val, k);
+        cj = p.A.col[k];
+        wj = load_weight<WT, float>(p.A.val, k);
       }
       const int cnt = (int)(k1 - kb < 32 ? k1 - kb : 32);
 #pragma unroll 4
       for (int s2 = 0; s2 < cnt; ++s2) {
         const int j = __shfl_sync(0xffffffffu, cj, s2);
         const float wv = (WT == KATZ_UNIT) ? 1.f : __shfl_sync(0xffffffffu, wj, s2);
-        const float* xr = Xk + int64_t(j) * ld + tile0 + t * VW;
+        const int64_t off = int64_t(j) * ld + tile0 + t * VW;
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
           if (cval[v]) {
             float xv[VW];
-            vload_ro<float>(xr + v * 32 * VW, xv);
+            if constexpr (IN == kInF32) {
+              vload_ro<float>(Xf + off + v * 32 * VW, xv);
+            } else {
+              bf16x4_ro(Xh + off + v * 32 * VW, xv);
+              if constexpr (IN == kInHiLo) {
+                float xl[VW];
+                bf16x4_ro(Xl + off + v * 32 * VW, xl);
+#pragma unroll
+                for (int w = 0; w < VW; ++w) xv[w] += xl[w];
+              }
+            }
 #pragma unroll
             for (int w = 0; w < VW; ++w) acc[v][w] += wv * xv[w];
           }
@@ -397,24 +460,49 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(Csr A, float beta, float
       if (!cval[v]) continue;
       const int64_t o = i * ld + tile0 + (v * 32 + t) * VW;
       float xo[VW], bo[VW], xp[VW] = {0.f, 0.f, 0.f, 0.f}, xn[VW];
-      vload_ro<float>(Xk + o, xo);
-      vload<float>(B + o, bo);
-      if (Xprev) vload<float>(Xprev + o, xp);
+      if constexpr (IN == kInF32) {
+        vload_ro<float>(Xf + o, xo);
+      } else {
+        float xl[VW];
+        bf16x4_ro(Xh + o, xo);
+        bf16x4_ro(Xl + o, xl);
+#pragma unroll
+        for (int w = 0; w < VW; ++w) xo[w] += xl[w];
+      }
+      vload<float>(p.B + o, bo);
+      if (p.prev_mode == 1) {
+        vload<float>(static_cast<const float*>(p.Xprev) + o, xp);
+      } else if (p.prev_mode == 2) {
+        const __nv_bfloat16* ph = static_cast<const __nv_bfloat16*>(p.Xprev);
+        float xl[VW];
+        bf16x4(ph + o, xp);
+        bf16x4(ph + p.plane + o, xl);
+#pragma unroll
+        for (int w = 0; w < VW; ++w) xp[w] += xl[w];
+      }
 #pragma unroll
       for (int w = 0; w < VW; ++w) {
-        const float xs = sx * xo[w];
-        const float r = bo[w] - xs + beta * (sx * acc[v][w]);
-        xn[w] = xs + ak * (xs - sp * xp[w]) + ck * r;
+        const float xs = p.sx * xo[w];
+        const float r = bo[w] - xs + p.beta * (p.sx * acc[v][w]);
+        xn[w] = xs + p.ak * (xs - p.sp * xp[w]) + p.ck * r;
       }
-      vstore<float>(Xout + o, xn);
+      if (p.out_split) {
+        __nv_bfloat16* oh = static_cast<__nv_bfloat16*>(p.Xout);
+        split_store4(oh + o, oh + p.plane + o, xn);
+      } else {
+        vstore<float>(static_cast<float*>(p.Xout) + o, xn);
+      }
     }
   }
 }
 
-void cheb_step(const Csr& A, double beta, double ak, double ck, const float* Xk,
-               const float* Xprev, const float* B, float* Xout, int64_t ld, int b, cudaStream_t s,
-               const SpmmCfg* cfg, double sx, double sp) {
-  KATZ_REQUIRE(ld % 4 == 0 && ld >= b && Xk != Xout &&
+}  // namespace
+
+void cheb_step_ex(const Csr& A, double beta, double ak, double ck, const void* Xk, int in_mode,
+                  const void* Xprev, int prev_mode, const float* B, void* Xout, int out_split,
+                  int64_t ld, int b, cudaStream_t s, const SpmmCfg* cfg, double sx, double sp) {
+  KATZ_REQUIRE(ld % 4 == 0 && ld >= b && Xk != Xout && in_mode >= 0 && in_mode <= 2 &&
+                   prev_mode >= 0 && prev_mode <= 2 && (prev_mode == 0) == (Xprev == nullptr) &&
                    (reinterpret_cast<uintptr_t>(Xk) | reinterpret_cast<uintptr_t>(Xprev) |
                     reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(Xout)) % 16 == 0,
                KATZ_EINVAL, "cheb_step: operands must be 16-byte aligned with padded rows");
@@ -428,14 +516,21 @@ void cheb_step(const Csr& A, double beta, double ak, double ck, const float* Xk,
   int64_t ctas = std::min<int64_t>(ceil_div(A.nrows, 8),
                                    std::max<int64_t>(1, int64_t(num_sms()) * cps / tiles));
   dim3 grid((unsigned)std::max<int64_t>(1, ctas), (unsigned)tiles);
+  ChebArgs a{A,     float(beta), float(ak), float(ck), float(sx), float(sp), Xk, Xprev, B,
+             Xout,  ld,          A.nrows * ld,          b,         prev_mode, out_split};
   prof_begin(s);
-#define KATZ_CHEB(WT)                                                                       \
-  if (vpt == 2)                                                                             \
-    cheb_step_kernel<WT, 2><<<grid, 256, 0, s>>>(A, float(beta), float(ak), float(ck), float(sx), float(sp), Xk, Xprev, \
-                                                 B, Xout, ld, b);                           \
-  else                                                                                      \
-    cheb_step_kernel<WT, 1><<<grid, 256, 0, s>>>(A, float(beta), float(ak), float(ck), float(sx), float(sp), Xk, Xprev, \
-                                                 B, Xout, ld, b)
+#define KATZ_CHEB_IN(WT, V)                                                          \
+  switch (in_mode) {                                                                 \
+    case kInF32: cheb_step_kernel<WT, V, kInF32><<<grid, 256, 0, s>>>(a); break;     \
+    case kInHi: cheb_step_kernel<WT, V, kInHi><<<grid, 256, 0, s>>>(a); break;       \
+    default: cheb_step_kernel<WT, V, kInHiLo><<<grid, 256, 0, s>>>(a); break;        \
+  }
+#define KATZ_CHEB(WT)         \
+  if (vpt == 2) {             \
+    KATZ_CHEB_IN(WT, 2)       \
+  } else {                    \
+    KATZ_CHEB_IN(WT, 1)       \
+  }
   switch (A.vdt) {
     case KATZ_UNIT: KATZ_CHEB(KATZ_UNIT); break;
     case KATZ_F32: KATZ_CHEB(KATZ_F32); break;
@@ -443,15 +538,26 @@ void cheb_step(const Csr& A, double beta, double ak, double ck, const float* Xk,
     default: KATZ_CHEB(KATZ_F64); break;
   }
 #undef KATZ_CHEB
+#undef KATZ_CHEB_IN
   KATZ_CHECK_LAUNCH();
   if (profiling()) {
-    // algorithmic: CSR once, x_k once, rows of x_k, b, x_{k-1} read once, x_{k+1} written
+    // algorithmic: CSR once, x_k once (FP32 rows, or its hi and lo planes),
+    // b and x_{k-1} read once, x_{k+1} written once; each n x b block is
+    // 4 bytes per entry in either form.  Launches that gather the hi plane
+    // alone are tagged apart.
     const double sv = 4.0 * b;
-    prof_end("cheb_step",
+    prof_end(in_mode == kInHi ? "cheb_step_bf16g" : "cheb_step",
              8.0 * (A.nrows + 1) + double(A.nnz) * (4 + vdt_size(A.vdt)) + sv * A.ncols +
-                 sv * A.nrows * (Xprev ? 3.0 : 2.0),
+                 sv * A.nrows * (prev_mode ? 3.0 : 2.0),
              s);
   }
+}
+
+void cheb_step(const Csr& A, double beta, double ak, double ck, const float* Xk,
+               const float* Xprev, const float* B, float* Xout, int64_t ld, int b, cudaStream_t s,
+               const SpmmCfg* cfg, double sx, double sp) {
+  cheb_step_ex(A, beta, ak, ck, Xk, kInF32, Xprev, Xprev ? 1 : 0, B, Xout, 0, ld, b, s, cfg, sx,
+               sp);
 }
 
 // ------------------------------------------------------- 2D vector launches

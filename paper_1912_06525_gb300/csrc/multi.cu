@@ -360,9 +360,16 @@ void multi_build(katz_multi& m, const std::vector<HostCsr>& Ws, const double* be
     GraphPart one;
     upload_csr(Ws[gi], vdt, one.csr, s);
     one.heavy.alloc(1);
-    m.lambda_h[gi] = lambda_max_gpu(one, Ws[gi].nrows, 48, m.ws, s);
-    KATZ_REQUIRE(betas[gi] > 0 && betas[gi] * m.lambda_h[gi] < 1.0, KATZ_ENOTSPD,
+    // the rigorous upper bound (Collatz-Wielandt) certifies M_g SPD and makes
+    // the per-graph error-bound stopping rule sound
+    double up = 0;
+    const double ritz = lambda_max_gpu(one, Ws[gi].nrows, 48, m.ws, s, 0, nullptr, &up);
+    m.lambda_h[gi] = up;
+    KATZ_REQUIRE(betas[gi] > 0 && betas[gi] * ritz < 1.0, KATZ_ENOTSPD,
                  "graph " + std::to_string(gi) + ": beta * lambda_max >= 1");
+    KATZ_REQUIRE(betas[gi] * up < 1.0, KATZ_ENOTSPD,
+                 "graph " + std::to_string(gi) +
+                     ": beta * (upper bound on lambda_max) >= 1, M cannot be certified SPD");
   }
   m.ws.clear();
   std::vector<float> bh(m.g), bl(m.g);

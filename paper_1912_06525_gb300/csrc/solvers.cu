@@ -240,8 +240,18 @@ static bool use_pipe(const katz_index& idx, const SpmmCfg* cfg, bool first = fal
 // The iteration count follows from the bound 2 c^K <= tol with
 // c = (sqrt(kappa)-1)/(sqrt(kappa)+1), kappa = (theta + d) / (theta - d).
 // No inner products, no host synchronisation, one fused kernel per step
-// (x_1 enters the first one as b scaled by 1/theta); two buffers (x_{k+1}
-// overwrites x_{k-1} row by row).
+// (x_1 enters the first one as b scaled by 1/theta).
+// Iterates x_2 .. x_{K-1} are kept in the split BF16 form (two scratch
+// buffers, x_{k+1} overwriting x_{k-1} row by row) unless the query asks
+// for FP32 gathers; their products gather the hi plane alone except, under
+// KATZ_CHEB_AUTO, the last step of a solve asked for a tolerance below
+// kHiGatherTol: a step's gather error (~2^-9 relative per term, ~1e-4 of
+// beta W x after the sum) is damped by each later step by about the
+// convergence factor c (~0.05 on the benchmark graph), so the hi-plane
+// gathers leave the solve within its tolerance when a hi + lo step closes
+// it.  x_K is written to Y in FP32.
+constexpr double kHiGatherTol = 1e-4;
+
 static void m11_chebyshev(katz_index& idx, const float* X, float* Y, int b, int64_t ld,
                           double tol, cudaStream_t s) {
   const int64_t len = idx.n1 - idx.n1s;
@@ -252,28 +262,51 @@ static void m11_chebyshev(katz_index& idx, const float* X, float* Y, int b, int6
     scale_copy<float>(X, ld, Y, ld, len, int(ld), 1.0 / theta, false, s);
     return;
   }
-  float* T = idx.ws.get<float>("ch.T", size_t(len) * ld);
-  // x_k for k >= 2 alternates between Y and T so that x_K lands in Y
-  auto slot = [&](int k) { return ((K - k) % 2 == 0) ? Y : T; };
   const double sigma = theta / d;
   double rho_prev = d / theta;  // rho_0 = 1/sigma
   const SpmmCfg* cfg = idx.W11L.cfg(b);
   const bool pipe = use_pipe(idx, cfg) && pipe_eligible(idx.W11L.ps, ld) &&
                     (idx.unit_weights || idx.W11L.csr.vdt != KATZ_F64);
-  int* perr = idx.ws.get<int>("pipe.err", 1);
+  if (idx.cheb_pref == KATZ_CHEB_F32 || pipe) {
+    // FP32 iterates: x_k for k >= 2 alternates between Y and T so that x_K
+    // lands in Y (x_{k+1} overwrites x_{k-1} row by row)
+    float* T = idx.ws.get<float>("ch.T", size_t(len) * ld);
+    auto slot = [&](int k) { return ((K - k) % 2 == 0) ? Y : T; };
+    int* perr = idx.ws.get<int>("pipe.err", 1);
+    for (int k = 1; k < K; ++k) {
+      const double rho = 1.0 / (2.0 * sigma - rho_prev);
+      const double ak = rho * rho_prev, ck = 2.0 * rho / d;
+      // x_1 = X / theta is never stored: it enters as Xk (k = 1) or Xprev (k = 2)
+      const float* xk = k == 1 ? X : slot(k);
+      const float* xprev = k == 1 ? nullptr : (k == 2 ? X : slot(k - 1));
+      const double sx = k == 1 ? 1.0 / theta : 1.0, sp = k == 2 ? 1.0 / theta : 1.0;
+      if (pipe)
+        pipe_cheb_step(idx.W11L.view(), idx.W11L.ps, idx.unit_weights, idx.beta, ak, ck, xk,
+                       xprev, X, slot(k + 1), ld, perr, s, sx, sp);
+      else
+        cheb_step(idx.W11L.view(), idx.beta, ak, ck, xk, xprev, X, slot(k + 1), ld, b, s, cfg, sx,
+                  sp);
+      rho_prev = rho;
+    }
+    return;
+  }
+  // split iterates x_2 .. x_{K-1} in T and U (x_j in T for even j)
+  float* T = idx.ws.get<float>("ch.T", size_t(len) * ld);
+  float* U = K > 3 ? idx.ws.get<float>("ch.U", size_t(len) * ld) : nullptr;
+  auto slot = [&](int j) -> void* { return (j % 2 == 0) ? static_cast<void*>(T) : U; };
+  const bool last_exact = idx.cheb_pref == KATZ_CHEB_AUTO && tol < kHiGatherTol;
   for (int k = 1; k < K; ++k) {
     const double rho = 1.0 / (2.0 * sigma - rho_prev);
     const double ak = rho * rho_prev, ck = 2.0 * rho / d;
-    // x_1 = X / theta is never stored: it enters as Xk (k = 1) or Xprev (k = 2)
-    const float* xk = k == 1 ? X : slot(k);
-    const float* xprev = k == 1 ? nullptr : (k == 2 ? X : slot(k - 1));
+    const bool last = k == K - 1;
+    const void* xk = k == 1 ? static_cast<const void*>(X) : slot(k);
+    const int in_mode = k == 1 ? 0 : (last && last_exact ? 2 : 1);
+    const void* xprev = k == 1 ? nullptr : (k == 2 ? static_cast<const void*>(X) : slot(k - 1));
+    const int prev_mode = k == 1 ? 0 : (k == 2 ? 1 : 2);
+    void* out = last ? static_cast<void*>(Y) : slot(k + 1);
     const double sx = k == 1 ? 1.0 / theta : 1.0, sp = k == 2 ? 1.0 / theta : 1.0;
-    if (pipe)
-      pipe_cheb_step(idx.W11L.view(), idx.W11L.ps, idx.unit_weights, idx.beta, ak, ck, xk, xprev,
-                     X, slot(k + 1), ld, perr, s, sx, sp);
-    else
-      cheb_step(idx.W11L.view(), idx.beta, ak, ck, xk, xprev, X, slot(k + 1), ld, b, s, cfg, sx,
-                sp);
+    cheb_step_ex(idx.W11L.view(), idx.beta, ak, ck, xk, in_mode, xprev, prev_mode, X, out,
+                 last ? 0 : 1, ld, b, s, cfg, sx, sp);
     rho_prev = rho;
   }
 }
@@ -638,7 +671,7 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   int* nopen = ws.get<int>("q.nopen", 1);
   int* perr = ws.get<int>("pipe.err", 1);
   rhs_norms(idx.W.view(), q, b, idx.beta, bn2, bmx, s);
-  const double omc = std::max(1e-300, 1.0 - idx.beta * idx.lambda);
+  const double omc = std::max(1e-300, 1.0 - idx.beta * idx.lambda_up);
   make_thresholds(bn2, bmx, b, solve_tol(o, out), o.tol_kind, omc, thr2, s);
   const double tau = 2e-6;
   double tol_rel = (o.tol_kind == KATZ_TOL_RESIDUAL) ? o.tol : o.tol * omc;
@@ -782,7 +815,7 @@ static int query_impl(katz_index& idx, bool use_lrc, const int32_t* q, int b,
   int* conv = ws.get<int>("q.conv", b);
   int* nopen = ws.get<int>("q.nopen", 1);
   rhs_norms(idx.W.view(), q, b, idx.beta, bn2, bmx, s);
-  const double omc = std::max(1e-300, 1.0 - idx.beta * idx.lambda);
+  const double omc = std::max(1e-300, 1.0 - idx.beta * idx.lambda_up);
   make_thresholds(bn2, bmx, b, solve_tol(o, out), o.tol_kind, omc, thr2, s);
   // inner solves aim below the outer target but not below what the inner
   // precision can deliver
@@ -880,6 +913,9 @@ int run_queries(katz_index& idx, bool use_lrc, const int32_t* q_dev, const int32
   KATZ_REQUIRE(o.gather_kernel >= KATZ_GATHER_AUTO && o.gather_kernel <= KATZ_GATHER_PIPELINED,
                KATZ_EINVAL, "gather_kernel must be a KATZ_GATHER_* value");
   idx.gather_pref = o.gather_kernel;
+  KATZ_REQUIRE(o.cheb_gather >= KATZ_CHEB_AUTO && o.cheb_gather <= KATZ_CHEB_BF16, KATZ_EINVAL,
+               "cheb_gather must be a KATZ_CHEB_* value");
+  idx.cheb_pref = o.cheb_gather;
   int* perr = idx.ws.get<int>("pipe.err", 1);
   KATZ_CUDA(cudaMemsetAsync(perr, 0, sizeof(int), s));
   int status;

@@ -13,6 +13,8 @@
 // in *err and skips the rest of its work.
 #include <cuda.h>
 
+#include <atomic>
+
 #include "kernels.h"
 #include "tc_gemm.h"
 #include "tc_util.cuh"
@@ -36,7 +38,7 @@ __host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
 __global__ void __launch_bounds__(128, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    int M, int N, int K, float alpha, float beta, float* C, int64_t ldc,
-                   __nv_bfloat16* Ct, int64_t ldct, int mode, int* err) {
+                   __nv_bfloat16* Ct, int64_t ldct, int mode, int* err, int stall) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned tiles (required by the 128-byte swizzle atoms)
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -73,8 +75,10 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // TMA producer
-    for (int kb = 0; kb < nkb; ++kb) {
+    // TMA producer (stall: a test switch under which no copy is issued, so
+    // the MMA issuer's bounded wait on the first stage runs out with nothing
+    // in flight)
+    for (int kb = 0; kb < nkb && !stall; ++kb) {
       const int s = kb % STAGES;
       if (kb >= STAGES && !mbar_wait(empty + s, ((kb / STAGES) - 1) & 1)) {
         atomicExch(&failed, 1);
@@ -178,7 +182,11 @@ __global__ void to_bf16_transposed_kernel(const float* X, int64_t ldx, int64_t r
   }
 }
 
+std::atomic<int> g_stall_copies{0};
+
 }  // namespace
+
+void set_test_stall_copies(bool on) { g_stall_copies.store(on ? 1 : 0); }
 
 size_t tc_gemm_smem_bytes() { return size_t(STAGES) * (TILE_A + TILE_B) + 1024 + 256; }
 
@@ -198,7 +206,7 @@ void tc_gemm(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_
   dim3 grid((unsigned)ceil_div(N, BN), (unsigned)ceil_div(M, BM));
   prof_begin(s);
   tc_gemm_kernel<<<grid, 128, smem, s>>>(ma, mb, M, N, K, alpha, beta, C, ldc, Ct, ldct, mode,
-                                         err);
+                                         err, g_stall_copies.load());
   KATZ_CHECK_LAUNCH();
   if (profiling())
     prof_end("tc_gemm", 2.0 * (double(M) * K + double(N) * K) +

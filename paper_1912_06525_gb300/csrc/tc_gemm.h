@@ -17,6 +17,10 @@ void tc_gemm(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_
 
 size_t tc_gemm_smem_bytes();
 
+// Test switch (process-wide): while on, tc_gemm's producer issues no TMA
+// copy, so the kernel's bounded wait runs out and *err is set.
+void set_test_stall_copies(bool on);
+
 // C (FP32, M x N, ldc) = alpha * A B^T + beta * Cin (ldcin; Cin may be C)
 // with FP32-level accuracy from three TF32 tensor-core products: A = Ah + Al
 // (M x K) and B = Bh + Bl (N x K), K contiguous, row strides multiples of 4

@@ -22,16 +22,17 @@ KATZ_UNIT, KATZ_F64, KATZ_F32, KATZ_BF16 = range(4)
 KATZ_PREC_F32, KATZ_PREC_MIXED, KATZ_PREC_F64 = range(3)
 KATZ_TOL_RESIDUAL, KATZ_TOL_ERROR_INF = range(2)
 KATZ_GATHER_AUTO, KATZ_GATHER_REGISTER, KATZ_GATHER_PIPELINED = range(3)
+KATZ_CHEB_AUTO, KATZ_CHEB_F32, KATZ_CHEB_BF16 = range(3)
 
 STATUS_NAMES = {0: "KATZ_OK", 1: "KATZ_EINVAL", 2: "KATZ_ENOTSPD", 3: "KATZ_ENOCONV",
                 4: "KATZ_ENOMEM", 5: "KATZ_ECUDA"}
 
 # every exported symbol of include/katz.h
-EXPORTS = ["katz_lambda_max", "katz_index_build", "katz_index_free", "katz_index_save",
+EXPORTS = ["katz_lambda_max", "katz_lambda_bounds", "katz_index_build", "katz_index_free", "katz_index_save",
            "katz_index_load", "katz_index_get_info", "katz_index_get_partition", "katz_partition",
            "katz_index_get_sigma", "katz_query_batch", "cg_query_batch", "linkpred_topk",
            "linkpred_topk_noalloc", "sparse_katz_topk", "katz_apply_M", "katz_autotune", "katz_gemm_bf16",
-           "katz_gemm_tf32x3", "katz_launch_count", "katz_fault_inject_alloc",
+           "katz_gemm_tf32x3", "katz_launch_count", "katz_fault_inject_alloc", "katz_test_stall_copies",
            "katz_profile_enable", "katz_profile_read", "katz_multi_build", "katz_multi_free",
            "katz_multi_query", "katz_index_build_many", "katz_multi_get_info",
            "katz_multi_query_lrc", "katz_warmstart_train", "katz_mlp_loss_grad", "katz_last_error"]
@@ -58,7 +59,8 @@ class katz_build_opts(C.Structure):
 class katz_query_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("tol_kind", C.c_int32), ("precision", C.c_int32),
                 ("max_iter", C.c_int32), ("max_refine", C.c_int32), ("rhs_width", C.c_int32),
-                ("warm_start", C.c_int32), ("gather_kernel", C.c_int32)]
+                ("warm_start", C.c_int32), ("gather_kernel", C.c_int32),
+                ("cheb_gather", C.c_int32)]
 
 
 class katz_stats(C.Structure):
@@ -80,7 +82,8 @@ class katz_index_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("n1", C.c_int64), ("n2", C.c_int64),
                 ("n_blocks", C.c_int32), ("n_large_blocks", C.c_int32), ("rank", C.c_int32),
                 ("value_dtype", C.c_int32), ("beta", C.c_double), ("lambda_max_R", C.c_double),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("lambda_max_W", C.c_double),
+                ("lambda_upper", C.c_double)]
 
 
 _lib = None
@@ -96,6 +99,8 @@ def lib() -> C.CDLL:
         L = C.CDLL(LIB_PATH)
         vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
         L.katz_lambda_max.argtypes = [C.POINTER(katz_csr), i32, C.POINTER(dbl), vp]
+        L.katz_lambda_bounds.argtypes = [C.POINTER(katz_csr), i32, C.POINTER(dbl),
+                                         C.POINTER(dbl), vp]
         L.katz_index_build.argtypes = [C.POINTER(katz_csr), dbl, C.POINTER(katz_build_opts), vp,
                                        C.POINTER(vp)]
         L.katz_index_free.argtypes = [vp]
@@ -137,6 +142,7 @@ def lib() -> C.CDLL:
         L.katz_launch_count.restype = C.c_int64
         L.katz_profile_enable.argtypes = [i32]
         L.katz_fault_inject_alloc.argtypes = [i64]
+        L.katz_test_stall_copies.argtypes = [i32]
         L.katz_profile_read.argtypes = [C.c_char_p, vp, vp, vp]
         L.katz_last_error.restype = C.c_char_p
         for name in EXPORTS:
@@ -205,6 +211,15 @@ def katz_lambda_max(graph, steps: int = 0, stream=None) -> float:
     out = C.c_double()
     _check(lib().katz_lambda_max(C.byref(c), steps, C.byref(out), _stream(stream)))
     return out.value
+
+
+def katz_lambda_bounds(graph, steps: int = 0, stream=None) -> tuple[float, float]:
+    """(largest Ritz value, rigorous upper bound) of lambda_max of W."""
+    c, keep = _csr(graph)
+    lo, up = C.c_double(), C.c_double()
+    _check(lib().katz_lambda_bounds(C.byref(c), steps, C.byref(lo), C.byref(up),
+                                    _stream(stream)))
+    return lo.value, up.value
 
 
 class KatzIndex:
@@ -281,10 +296,10 @@ def katz_index_get_sigma(index: KatzIndex) -> np.ndarray:
 
 
 def _query(fn, index, q, K_out, out_dtype, tol, tol_kind, precision, max_iter, max_refine,
-           rhs_width, warm_start, gather_kernel, stream):
+           rhs_width, warm_start, gather_kernel, stream, cheb_gather=KATZ_CHEB_AUTO):
     b = int(q.shape[0])
     o = katz_query_opts(float(tol), tol_kind, precision, max_iter, max_refine, rhs_width,
-                        warm_start, gather_kernel)
+                        warm_start, gather_kernel, cheb_gather)
     st = katz_stats()
     iters = np.zeros(b, dtype=np.int32)
     rel = np.zeros(b, dtype=np.float64)
@@ -300,11 +315,12 @@ def _query(fn, index, q, K_out, out_dtype, tol, tol_kind, precision, max_iter, m
 def katz_query_batch(index, q, K_out, out_dtype=KATZ_F32, tol=1e-6,
                      tol_kind=KATZ_TOL_ERROR_INF, precision=KATZ_PREC_MIXED, max_iter=0,
                      max_refine=0, rhs_width=0, warm_start=0, gather_kernel=KATZ_GATHER_AUTO,
-                     stream=None):
+                     stream=None, cheb_gather=KATZ_CHEB_AUTO):
     """LRC-Katz (Algorithm 2).  q: int32 (b,) host or device; K_out: (n, b)
     node-major float32/float64, host or device.  Returns (stats, iters, rel_res)."""
     return _query(lib().katz_query_batch, index, q, K_out, out_dtype, tol, tol_kind, precision,
-                  max_iter, max_refine, rhs_width, warm_start, gather_kernel, stream)
+                  max_iter, max_refine, rhs_width, warm_start, gather_kernel, stream,
+                  cheb_gather)
 
 
 def cg_query_batch(index, q, K_out, out_dtype=KATZ_F32, tol=1e-6, tol_kind=KATZ_TOL_ERROR_INF,
@@ -348,6 +364,12 @@ def sparse_katz_topk(index, q, s, T, ids_out, rho_out, landmarks_out=None, tol=1
     return {"iters": st.iters, "refine_steps": st.refine_steps, "max_rel_res": st.max_rel_res,
             "ms": list(st.ms), "distinct_landmarks": int(st.ms[6]),
             "status": STATUS_NAMES[code]}
+
+
+def katz_test_stall_copies(on: bool) -> None:
+    """Test hook: the tensor-core GEMM issues no TMA copies while on, so its
+    bounded pipeline wait runs out and the call returns KATZ_ECUDA."""
+    _check(lib().katz_test_stall_copies(1 if on else 0))
 
 
 def katz_fault_inject_alloc(after: int) -> None:
@@ -477,7 +499,8 @@ def katz_multi_query(multi, q, qpg, K_out, out_dtype=KATZ_F32, tol=1e-6,
                      _fn="katz_multi_query"):
     """q: (g*qpg,) graph-local ids; K_out: (sum n_g, qpg).  Returns
     (stats, iters (g*qpg,), rel_res (g*qpg,))."""
-    o = katz_query_opts(float(tol), tol_kind, KATZ_PREC_MIXED, max_iter, max_refine, 0, 0, 0)
+    o = katz_query_opts(float(tol), tol_kind, KATZ_PREC_MIXED, max_iter, max_refine, 0, 0, 0,
+                        KATZ_CHEB_AUTO)
     st = katz_stats()
     total = len(multi.sizes) * qpg
     iters = np.zeros(total, dtype=np.int32)

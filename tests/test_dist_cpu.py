@@ -78,8 +78,21 @@ def test_all_cores_oracle_helper():
     W = oracle.adjacency(g.n, g.rowptr, g.col, g.val)
     beta = 0.5 / oracle.lambda_max(W)
     before = set(os.listdir("/dev/shm"))
-    dt = bench.oracle_all_cores(g, beta, np.array([1, 7, 11]), 1e-10, 2)
-    assert dt > 0
+    qs = np.array([1, 7, 11])
+    dt, Ka = bench.oracle_all_cores(g, beta, qs, 1e-10, 2)
+    assert dt > 0 and Ka.shape == (g.n, 3)
     assert set(os.listdir("/dev/shm")) - before == set()
+    # the vectors the workers kept are the oracle's own solves of those columns
+    Kd = oracle.katz_direct(W, beta, qs)
+    assert oracle.error_inf_rel(Ka, Kd).max() < 1e-8
+    # top-20 agreement of a list with itself is 1; with a planted swap of a
+    # clear winner for a poor candidate it drops
+    ids, _ = oracle.linkpred_topk(W, Kd, qs, 20)
+    assert bench.topk_agreement(g, Kd, qs, ids) == 1.0
+    bad = ids.copy()
+    order = np.argsort(Kd[:, 0])
+    worst = [int(x) for x in order if x not in set(ids[0]) and x != qs[0]][0]
+    bad[0, 0] = worst
+    assert bench.topk_agreement(g, Kd, qs, bad) == 2 / 3
     info = bench.host_cpu()
     assert info["nproc"] >= 1 and info["model"]

@@ -74,3 +74,27 @@ def test_injected_allocation_failure_is_enomem_and_recoverable(after):
     st, it, rel = katz.katz_query_batch(idx, qd, K, out_dtype=katz.KATZ_F64, tol=1e-6)
     assert st["status"] == "KATZ_OK"
     assert O.error_inf_rel(K.cpu().numpy(), O.katz_direct(W, beta, q)).max() <= 1e-6
+
+
+def test_bounded_pipeline_wait_reports_timeout_and_library_recovers():
+    """A wait that nothing completes: with the test switch on, the tcgen05
+    GEMM's producer issues no TMA copy, so the MMA issuer's bounded wait on
+    the first stage runs out (nothing is in flight), the kernel frees its
+    tensor memory and the call returns KATZ_ECUDA.  With the switch off the
+    same call then succeeds and matches an FP32 product of the BF16
+    operands."""
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    A = torch.randn((128, 64), generator=gen, device="cuda").to(torch.bfloat16)
+    B = torch.randn((96, 64), generator=gen, device="cuda").to(torch.bfloat16)
+    C = torch.zeros((128, 96), dtype=torch.float32, device="cuda")
+    try:
+        katz.katz_test_stall_copies(True)
+        with pytest.raises(katz.KatzError) as e:
+            katz.katz_gemm_bf16(A, B, C)
+        assert e.value.code == katz.KATZ_ECUDA
+    finally:
+        katz.katz_test_stall_copies(False)
+    katz.katz_gemm_bf16(A, B, C)
+    torch.cuda.synchronize()
+    ref = A.float() @ B.float().T
+    assert torch.allclose(C, ref, rtol=1e-5, atol=1e-4)

@@ -57,6 +57,38 @@ def test_lambda_max(maker):
     assert lam == pytest.approx(O.lambda_max(W_of(g)), rel=1e-9)
 
 
+@pytest.mark.parametrize("maker", [
+    lambda: synth.sbm_bernoulli([300] * 6, 0.05, 0.004, seed=21),
+    lambda: hub_graph(5, weighted=True),
+    lambda: synth.disjoint_union([synth.erdos_renyi(400, 0.03, seed=4), synth.star(60),
+                                  synth.path(9)]),
+])
+def test_lambda_upper_bound_is_rigorous(maker):
+    """A few Lanczos steps leave the Ritz value visibly below lambda_max;
+    the Collatz-Wielandt bound stays above it at every step count (it holds
+    for any positive vector), and is tight once the Ritz vector converges.
+    The index build certifies beta with the upper bound: a beta chosen from
+    the underestimate (beta * lambda_max > 1) is refused, and the index
+    reports both sides."""
+    g = maker()
+    lam = O.lambda_max(W_of(g))
+    lo2, up2 = katz.katz_lambda_bounds(g, steps=2)
+    assert lo2 < lam * (1 - 1e-3), "two steps should underestimate visibly"
+    for steps in (2, 3, 5, 12, 200):
+        lo, up = katz.katz_lambda_bounds(g, steps=steps)
+        assert lo <= lam * (1 + 1e-12) and up >= lam, (steps, lo, up, lam)
+    assert up <= lam * (1 + 1e-6)
+    beta_bad = 0.999 / lo2
+    if beta_bad * lam >= 1:
+        with pytest.raises(katz.KatzError) as e:
+            katz.katz_index_build(g, beta_bad, value_dtype=katz.KATZ_F64, build_lrc=False)
+        assert e.value.code == katz.KATZ_ENOTSPD
+    idx = katz.katz_index_build(g, 0.9 / lam, value_dtype=katz.KATZ_F64, build_lrc=False)
+    info = idx.info()
+    assert info["lambda_max_W"] <= lam * (1 + 1e-12) <= info["lambda_upper"] * (1 + 1e-12)
+    assert info["lambda_upper"] <= lam * (1 + 1e-6)
+
+
 # ------------------------------------------------------- sparse product
 @pytest.mark.parametrize("b", [1, 3, 16, 257])
 @pytest.mark.parametrize("vdt", [katz.KATZ_F64, katz.KATZ_F32, katz.KATZ_BF16])

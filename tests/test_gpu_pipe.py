@@ -61,6 +61,33 @@ def test_pipelined_paths_match_oracle(vdt, b):
             assert err.max() <= 1e-6, (fn.__name__, kern, err.max())
 
 
+@pytest.mark.parametrize("vdt", [katz.KATZ_UNIT, katz.KATZ_BF16])
+@pytest.mark.parametrize("b", [5, 333, 1024])
+def test_chebyshev_gather_precisions_match_oracle(vdt, b):
+    """The large M11 block's Chebyshev steps with FP32 iterates, with split
+    BF16 iterates gathered as hi + lo on a solve's last step (AUTO), and
+    with hi-plane gathers on every step (BF16): the refined answers all meet
+    the 1e-6 bound; column tiles of 128 (b = 5) and 256 columns, ragged
+    tails, unit and BF16 weights."""
+    g = graph(weighted=vdt != katz.KATZ_UNIT, seed=13)
+    W = O.adjacency(g.n, g.rowptr, g.col, g.val)
+    beta = 0.9 / O.lambda_max(W)
+    idx = katz.katz_index_build(g, beta, value_dtype=vdt, rank=16, n_hubs=30, block_max=32,
+                                split=False)
+    assert idx.info()["n_large_blocks"] >= 1
+    q = synth.queries(g.n, b, seed=b + 1)
+    q[0] = 3000
+    ref = O.katz_direct(W, beta, q)
+    for mode in (katz.KATZ_CHEB_AUTO, katz.KATZ_CHEB_F32, katz.KATZ_CHEB_BF16):
+        K = torch.zeros((g.n, b), dtype=torch.float32, device="cuda")
+        st, it, rel = katz.katz_query_batch(idx, torch.from_numpy(q).cuda(), K, tol=1e-6,
+                                            gather_kernel=katz.KATZ_GATHER_REGISTER,
+                                            cheb_gather=mode)
+        assert st["status"] == "KATZ_OK", (mode, st)
+        err = O.error_inf_rel(K.double().cpu().numpy(), ref)
+        assert err.max() <= 1e-6, (mode, err.max())
+
+
 def test_autotune_reports_kernel_choice():
     g = graph(weighted=False)
     beta = 0.85 / katz.katz_lambda_max(g, steps=96)
