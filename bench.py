@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--method", default="lrc", choices=["lrc", "cg"])
     ap.add_argument("--gather", default="auto", choices=["auto", "register", "pipelined"],
                     help="kernel of the wide fused products (auto: the autotuner's choice)")
+    ap.add_argument("--cheb", default="auto", choices=["auto", "f32", "bf16", "mixed"],
+                    help="gathers of the large M11 block's Chebyshev steps: auto (the "
+                         "library's choice), f32, bf16 (hi plane on every step after the "
+                         "first), mixed (hi plane except a closing hi + lo step)")
     ap.add_argument("--batch", type=int, default=0,
                     help="override the query batch width b (small profiling cases)")
     ap.add_argument("--warm", action="store_true",
@@ -604,24 +608,30 @@ def run_warm(args, world, rank, local):
     b = 1024
     katz.katz_autotune(idx, b)
     res = {}
-    for name, warm in (("cold", 0), ("warm", 1)):
-        its, ms, fb = [], 0.0, 0
+    for name, fn, warm in (("cold", katz.katz_query_batch, 0),
+                           ("warm", katz.katz_query_batch, 1),
+                           ("cg_cold", katz.cg_query_batch, 0),
+                           ("cg_warm", katz.cg_query_batch, 1)):
+        its, ms, fb, ref = [], 0.0, 0, []
         for j0 in range(0, len(test), b):
             qd = torch.from_numpy(test[j0:j0 + b]).cuda()
             Kb = torch.empty((g.n, len(qd)), dtype=torch.float32, device="cuda")
-            katz.katz_query_batch(idx, qd, Kb, tol=1e-6, warm_start=warm)  # untimed
+            fn(idx, qd, Kb, tol=1e-6, warm_start=warm)  # untimed
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(torch.cuda.current_stream())
-            st, it, rel = katz.katz_query_batch(idx, qd, Kb, tol=1e-6, warm_start=warm)
+            st, it, rel = fn(idx, qd, Kb, tol=1e-6, warm_start=warm)
             e1.record(torch.cuda.current_stream())
             torch.cuda.synchronize()
             ms += e0.elapsed_time(e1)
             its.extend(it.tolist())
             fb += int(st["ms"][5])
+            ref.append(st["refine_steps"])
         res[name] = {"queries_per_s": len(test) / (ms / 1000), "ms": ms,
-                     "mean_pcg_iters": float(np.mean(its)), "warm_fallbacks": fb}
+                     ("mean_pcg_iters" if fn is katz.katz_query_batch else "mean_cg_iters"):
+                         float(np.mean(its)),
+                     "warm_fallbacks": fb, "refine_steps": ref}
     if rank == 0:
         print(json.dumps({"metric": "Katz queries/sec at 1e-6 rel. error, warm vs cold start",
                           "unit": UNIT, "value": res["warm"]["queries_per_s"], "n_gpus": world,
@@ -633,7 +643,8 @@ def run_warm(args, world, rank, local):
                                                  f"{n_train:,} training queries, 4,096 held out",
                                      "n": g.n, "train_s": train_s,
                                      "train_loss": [tr["initial_loss"], tr["final_loss"]]},
-                          "cold": res["cold"], "warm": res["warm"]}), flush=True)
+                          "cold": res["cold"], "warm": res["warm"],
+                          "cg_cold": res["cg_cold"], "cg_warm": res["cg_warm"]}), flush=True)
 
 
 def main():
@@ -703,8 +714,12 @@ def main():
           "pipelined": katz.KATZ_GATHER_PIPELINED}[args.gather]
     last = {}
 
+    cg_mode = {"auto": katz.KATZ_CHEB_AUTO, "f32": katz.KATZ_CHEB_F32,
+               "bf16": katz.KATZ_CHEB_BF16, "mixed": katz.KATZ_CHEB_MIXED}[args.cheb]
+    qkw = {"cheb_gather": cg_mode} if args.method == "lrc" else {}
+
     def step(qq, KK, ii, ss):
-        st, it, rel = qfn(idx, qq, KK, out_dtype=katz.KATZ_F32, tol=1e-6, gather_kernel=gk)
+        st, it, rel = qfn(idx, qq, KK, out_dtype=katz.KATZ_F32, tol=1e-6, gather_kernel=gk, **qkw)
         katz.linkpred_topk(idx, qq, KK, katz.KATZ_F32, 20, ii, ss)
         last.update(st=st, it=it, rel=rel)
 
@@ -731,8 +746,8 @@ def main():
     barrier(world)
     launches = katz.katz_launch_count() - l0
     prof = {t: katz.katz_profile_read(t) for t in
-            ("spmm_f32", "spmm_f64", "cheb_step", "ff_residual", "block_solve_f32",
-             "gemm_f32", "tc_gemm", "tc_gemm_tf32x3")}
+            ("spmm_f32", "spmm_f64", "cheb_step", "cheb_step_bf16g", "ff_residual",
+             "block_solve_f32", "gemm_f32", "tc_gemm", "tc_gemm_tf32x3")}
     katz.katz_profile_enable(False)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
@@ -816,12 +831,16 @@ def main():
                "h2d_bytes_per_step": int(q.nbytes),
                "d2h_bytes_per_step": int(b * 20 * (4 + 8))}
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant kernel; the Chebyshev step's launches
+    # (FP32 or hi-plane gathers, the same algorithmic bytes) count as one kernel
     hbm, src = peaks()
-    shares = {t: p["ms"] for t, p in prof.items() if p["launches"]}
+    ch = [prof[t] for t in ("cheb_step", "cheb_step_bf16g")]
+    prof_dom = {t: v for t, v in prof.items() if not t.startswith("cheb_step")}
+    prof_dom["cheb_step"] = {k: sum(v[k] for v in ch) for k in ("launches", "ms", "bytes")}
+    shares = {t: p["ms"] for t, p in prof_dom.items() if p["launches"]}
     tot = sum(shares.values()) or 1.0
     dom = max(shares, key=shares.get) if shares else "spmm_f32"
-    p = prof[dom]
+    p = prof_dom[dom]
     ach = p["bytes"] / (p["ms"] / 1e3) / 1e9 if p["ms"] else 0.0
     if dom in FLOP_TAGS:
         tpk, tsrc = tf32_peak()
@@ -889,6 +908,7 @@ def main():
                                f"top-1% hubs, beta=1/(lambda_max+1), tol 1e-6")
         cfg.update({"method": args.method, "parallelism": "replicas" if world > 1 else "single",
                     "spmm_autotune": tune, "gather_kernel": args.gather,
+                    "cheb_gather": args.cheb,
                     "n2": info["n2"], "n1": info["n1"], "index_build_s": build_s,
                     "index_device_bytes": info["device_bytes"],
                     "sigma_1": info["lambda_max_R"],

@@ -69,18 +69,18 @@ extern "C" {
 #define KATZ_GATHER_PIPELINED 2
 
 /* Gathers of the Chebyshev steps on the large M11 blocks (KATZ_PREC_MIXED
- * and F32 paths).  The iterates are kept as two BF16 planes hi = bf16(x),
- * lo = bf16(x - hi) (FP32 storage size, x to 2^-18 relative), so a step's
- * product can gather the hi plane alone: half the bytes per gathered row,
- * at ~2^-9 relative error per gathered term.
- * AUTO: hi-plane gathers on every step whose perturbation a later step
- * damps -- all steps after the first, except that the last step of a solve
- * asked for a tolerance below 1e-4 gathers hi + lo;
- * F32: FP32 iterates and FP32 gathers on every step;
- * BF16: hi-plane gathers on every step after the first. */
+ * and F32 paths).  F32: FP32 iterates and FP32 gathers.  The other modes
+ * keep the iterates as two BF16 planes hi = bf16(x), lo = bf16(x - hi)
+ * (FP32 storage size, x to 2^-18 relative), so that a step's product can
+ * gather the hi plane alone: half the bytes per gathered row, at ~2^-9
+ * relative error per gathered term.  BF16: hi-plane gathers on every step
+ * after the first; MIXED: the same, except that the last step of a solve
+ * asked for a tolerance below 1e-4 gathers hi + lo.  AUTO: the mode
+ * measured fastest on the benchmark graph, currently F32. */
 #define KATZ_CHEB_AUTO 0
 #define KATZ_CHEB_F32 1
 #define KATZ_CHEB_BF16 2
+#define KATZ_CHEB_MIXED 3
 
 #define KATZ_TOL_RESIDUAL 0  /* stop column j when ||b_j - M k_j||_2 <= tol * ||b_j||_2 */
 #define KATZ_TOL_ERROR_INF 1 /* stop when ||b_j - M k_j||_2 <= tol * (1 - beta*lambda) * ||b_j||_inf,
@@ -113,7 +113,10 @@ typedef struct {
   int32_t split;         /* 1: split components larger than block_max by BFS level sets;
                             0: keep them whole (their M11 block is solved iteratively) */
   int32_t lanczos_steps; /* Lanczos steps on R; 0 = max(2r, r+20) */
-  int32_t n2_max;        /* largest separator accepted (dense S and M22^{-1}); 0 = 16384 */
+  int32_t n2_max;        /* largest separator whose Schur complement S is stored dense
+                            (0 = 16384).  Larger separators (up to 49,152 nodes) apply S
+                            implicitly in each PCG iteration, S P = M22 P - M12^T M11^{-1}
+                            (M12 P) with one M11 solve (Lemma 1); M22^{-1} stays dense */
   uint64_t seed;         /* SplitMix64 seed of the Lanczos start vector */
   int32_t coupling_gemm; /* store beta*M11^{-1} W12 (n1 x n2, TF32 hi/lo parts) so that LRC
                             queries form K1 = Y1 + beta M11^{-1} W12 K2 (Eq. 6) on the tensor
@@ -152,6 +155,7 @@ typedef struct {
   double lambda_max_W; /* largest Lanczos Ritz value of W (a lower bound on lambda_max) */
   double lambda_upper; /* rigorous upper bound on lambda_max of W (Collatz-Wielandt); the SPD
                           check and the KATZ_TOL_ERROR_INF rule use it */
+  int32_t schur_implicit; /* 1: the separator exceeds n2_max and S is applied implicitly */
 } katz_index_info;
 
 /* ---------------------------------------------------------------- graph */

@@ -255,6 +255,7 @@ int katz_index_get_info(const katz_index* idx, katz_index_info* info) {
     info->lambda_max_R = idx->sigma.empty() ? 0.0 : idx->sigma[0];
     info->lambda_max_W = idx->lambda;
     info->lambda_upper = idx->lambda_up;
+    info->schur_implicit = idx->s_implicit ? 1 : 0;
     int64_t bytes = idx->W.csr.bytes() + idx->Wp.csr.bytes() + idx->W12.csr.bytes() +
                     idx->W21.csr.bytes() + idx->W11L.csr.bytes() + idx->S32.bytes() +
                     idx->S64.bytes() + idx->M22inv32.bytes() + idx->M22inv64.bytes() +

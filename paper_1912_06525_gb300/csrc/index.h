@@ -67,6 +67,10 @@ struct Partition {
 
 // Every field except `ws`, `gather_pref` and `cheb_pref` is stored by save_index
 // (index_io.cu): a field added here is added to its list too.
+// Largest separator of a single-graph LRC index: M22 and M22^{-1} are kept
+// dense (n2 x n2 FP64 and FP32) even when S is applied implicitly.
+constexpr int64_t kDenseM22Max = 49152;
+
 struct katz_index {
   int64_t n = 0, nnz = 0;
   // lambda: largest Lanczos Ritz value of W (a lower bound on lambda_max);
@@ -119,8 +123,12 @@ struct katz_index {
   // Schur products of the FP32 solve (large separators only)
   katz::DBuf<float> Sh, Sl, Mh, Ml;
   bool dense_tc = false;
+  // separators above n2_max: S is never formed; PCG applies
+  // S P = M22 P - beta^2 W21 M11^{-1} (W12 P) (Lemma 1, Eqs. 4-7)
+  bool s_implicit = false;
   katz::Mlp mlp;
   katz::DBuf<float> feat;  // n x 32 node features
+  katz::DBuf<float> Hr;    // beta M11^{-1} W12 W_r (n1 x ldr4), for the CG warm start
   std::vector<double> sigma;
   int lanczos_steps = 0;
   // an index of disjoint graphs: each graph's rank (its sigma and basis
@@ -234,6 +242,9 @@ double warmstart_train(katz_index& idx, const int32_t* q_host, int n_train, int 
                        cudaStream_t s);
 void warm_start_guess(katz_index& idx, const int32_t* q, int b, float* K20, int64_t ld,
                       cudaStream_t s);
+// Initial guess of CG on M from the network (node order, n x b, ld).
+void warm_cg_guess(katz_index& idx, const int32_t* q, int b, float* X, int64_t ld,
+                   cudaStream_t s);
 
 // Chebyshev steps of the large M11 blocks for relative tolerance tol, and
 // whether the tensor-core back-substitution is cheaper than the second M11

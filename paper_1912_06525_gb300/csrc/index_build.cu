@@ -784,8 +784,12 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   const int64_t n = idx.n, n1 = P.n1, n2 = P.n2;
   idx.n1 = n1;
   idx.n2 = n2;
-  KATZ_REQUIRE(n2 <= n2_max, KATZ_EINVAL,
-               "separator has " + std::to_string(n2) + " nodes > n2_max " + std::to_string(n2_max));
+  // separators above n2_max keep S implicit (single graphs); M22 and its
+  // inverse stay dense, which bounds the separator at kDenseM22Max
+  idx.s_implicit = !seg && n2 > n2_max;
+  KATZ_REQUIRE((seg && n2 <= n2_max) || (!seg && n2 <= kDenseM22Max), KATZ_EINVAL,
+               "separator has " + std::to_string(n2) + " nodes > " +
+                   std::to_string(seg ? n2_max : kDenseM22Max));
   // disjoint graphs: each graph's separator rows (contiguous, graph-major)
   std::vector<int64_t> gsep_h;
   DBuf<int32_t> sg_d;
@@ -962,7 +966,7 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   // --- T = M12^T M11^{-1} M12 = beta^2 W21 M11^{-1} W12 (FP64, by columns)
   const int64_t ld2 = (n2 + 3) / 4 * 4;
   idx.ld2 = ld2;
-  DBuf<double> T(size_t(n2) * ld2);
+  DBuf<double> T(idx.s_implicit ? size_t(1) : size_t(n2) * ld2);
   KATZ_CUDA(cudaMemsetAsync(T.p, 0, T.bytes(), s));
   {
     const int cw_max = (int)std::min<int64_t>(256, (n2 + 1) / 2 * 2);
@@ -979,7 +983,7 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
       const double bytes = 2.0 * 4.0 * double(n1) * double(idx.ldH);
       // automatic: where the cost model favours the product at the FP32
       // inner tolerance (2e-6) and the parts fit
-      idx.has_h = !seg && n1 > 0 && (o.coupling_gemm > 0 ||
+      idx.has_h = !seg && !idx.s_implicit && n1 > 0 && (o.coupling_gemm > 0 ||
                              (o.coupling_gemm == 0 && coupling_gemm_pays(idx, 1024, 2e-6) &&
                               bytes <= double(total_b) / 3.0 && bytes <= 0.8 * double(free_b)));
     }
@@ -1007,7 +1011,7 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
                                                                 gsep_d.p, (int)l0, cw);
       KATZ_CHECK_LAUNCH();
     }
-    for (int64_t j0 = 0; !seg && j0 < n2; j0 += cw_max) {
+    for (int64_t j0 = 0; !seg && !idx.s_implicit && j0 < n2; j0 += cw_max) {
       const int cw = (int)std::min<int64_t>(cw_max, n2 - j0);
       if (n1 == 0) break;
       KATZ_CUDA(cudaMemsetAsync(E.p, 0, E.bytes(), s));
@@ -1030,9 +1034,11 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   dense_from_csr_kernel<<<(unsigned)std::min<int64_t>(n2, 65535), 128, 0, s>>>(W22d.view(), beta,
                                                                                M22.p, ld2);
   KATZ_CHECK_LAUNCH();
-  idx.S64.alloc(size_t(n2) * ld2);
-  sub_kernel<<<blocks_for(n2 * ld2), 256, 0, s>>>(M22.p, T.p, idx.S64.p, n2 * ld2);
-  KATZ_CHECK_LAUNCH();
+  if (!idx.s_implicit) {
+    idx.S64.alloc(size_t(n2) * ld2);
+    sub_kernel<<<blocks_for(n2 * ld2), 256, 0, s>>>(M22.p, T.p, idx.S64.p, n2 * ld2);
+    KATZ_CHECK_LAUNCH();
+  }
   idx.M22inv64.alloc(size_t(n2) * ld2);
   KATZ_CUDA(cudaMemcpyAsync(idx.M22inv64.p, M22.p, M22.bytes(), cudaMemcpyDeviceToDevice, s));
   {
@@ -1049,15 +1055,21 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   // which only pays when the products are a large share of the solve)
   idx.dense_tc = !seg && n2 >= 4096;
   if (idx.dense_tc) {
-    for (auto* d : {&idx.Sh, &idx.Sl, &idx.Mh, &idx.Ml}) d->alloc(size_t(n2) * ld2);
-    split_tf32<double>(idx.S64.p, ld2, n2, int(n2), idx.Sh.p, idx.Sl.p, ld2, s);
+    for (auto* d : {&idx.Mh, &idx.Ml}) d->alloc(size_t(n2) * ld2);
     split_tf32<double>(idx.M22inv64.p, ld2, n2, int(n2), idx.Mh.p, idx.Ml.p, ld2, s);
+    if (!idx.s_implicit) {
+      for (auto* d : {&idx.Sh, &idx.Sl}) d->alloc(size_t(n2) * ld2);
+      split_tf32<double>(idx.S64.p, ld2, n2, int(n2), idx.Sh.p, idx.Sl.p, ld2, s);
+    }
   }
-  idx.S32.alloc(size_t(n2) * ld2);
   idx.M22inv32.alloc(size_t(n2) * ld2);
-  to_f32_kernel<<<blocks_for(n2 * ld2), 256, 0, s>>>(idx.S64.p, idx.S32.p, n2 * ld2);
   to_f32_kernel<<<blocks_for(n2 * ld2), 256, 0, s>>>(idx.M22inv64.p, idx.M22inv32.p, n2 * ld2);
   KATZ_CHECK_LAUNCH();
+  if (!idx.s_implicit) {
+    idx.S32.alloc(size_t(n2) * ld2);
+    to_f32_kernel<<<blocks_for(n2 * ld2), 256, 0, s>>>(idx.S64.p, idx.S32.p, n2 * ld2);
+    KATZ_CHECK_LAUNCH();
+  }
 
   // --- Lanczos for the top-r eigenpairs of R = L^{-1} T L^{-T}.  R is
   // similar to A = M22^{-1} T, which is self-adjoint in <x,y> = x^T M22 y;
@@ -1094,9 +1106,30 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
     copy2d<double>(wv.p, 1, Q.p, ldq, n2, 1, 1.0 / nrm, s);
     std::vector<double> al, be, ev, Y;
     int check = m;
+    // implicit S: T q = beta^2 W21 M11^{-1} (W12 q) by one FP64 M11 solve
+    DBuf<double> q2, u2, v2;
+    if (idx.s_implicit) {
+      q2.alloc(size_t(n2) * 2);
+      u2.alloc(size_t(std::max<int64_t>(n1, 1)) * 2);
+      v2.alloc(size_t(std::max<int64_t>(n1, 1)) * 2);
+      KATZ_CUDA(cudaMemsetAsync(q2.p, 0, q2.bytes(), s));
+    }
     for (int j = 0; j < cap; ++j) {
       // t = T q_j ; w = M22^{-1} t
-      gemm<double>(false, n2, 1, n2, 1.0, T.p, ld2, Q.p + j, ldq, 0.0, t.p, 1, s);
+      if (!idx.s_implicit) {
+        gemm<double>(false, n2, 1, n2, 1.0, T.p, ld2, Q.p + j, ldq, 0.0, t.p, 1, s);
+      } else if (n1 == 0) {
+        KATZ_CUDA(cudaMemsetAsync(t.p, 0, t.bytes(), s));
+      } else {
+        copy2d<double>(Q.p + j, ldq, q2.p, 2, n2, 1, 1.0, s);
+        spmm<double>(idx.W12.view(), idx.W12.heavy.p, idx.W12.n_heavy, beta, q2.p, 2, 0.0,
+                     nullptr, 2, u2.p, 2, 1, nullptr, 0, nullptr, s);
+        const int st = m11_solve<double>(idx, u2.p, v2.p, 1, 2, 1e-14, 5000, nullptr, s);
+        KATZ_REQUIRE(st != KATZ_ENOTSPD, KATZ_ENOTSPD, "M11 is not positive definite");
+        spmm<double>(idx.W21.view(), idx.W21.heavy.p, idx.W21.n_heavy, beta, v2.p, 2, 0.0,
+                     nullptr, 2, q2.p, 2, 1, nullptr, 0, nullptr, s);
+        copy2d<double>(q2.p, 2, t.p, 1, n2, 1, 1.0, s);
+      }
       gemm<double>(false, n2, 1, n2, 1.0, idx.M22inv64.p, ld2, t.p, 1, 0.0, wv.p, 1, s);
       gemm<double>(true, 1, 1, n2, 1.0, Q.p + j, ldq, t.p, 1, 0.0, sc.p, 1, s);
       al.push_back(dget(sc.p, s));

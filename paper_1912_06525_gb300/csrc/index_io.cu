@@ -303,6 +303,7 @@ void serialize(Archive& a, katz_index& x) {
   a.dbuf("Mh", x.Mh);
   a.dbuf("Ml", x.Ml);
   a.flag("dense_tc", x.dense_tc);
+  a.flag("s_implicit", x.s_implicit);
 
   // warm-start network with its optimiser state (training can resume)
   a.scalar("mlp.din", x.mlp.din);

@@ -57,6 +57,100 @@ __device__ __forceinline__ void vstore(VT* p, const VT (&o)[VecOf<VT>::width]) {
   *reinterpret_cast<V*>(p) = v;
 }
 
+namespace {
+// CW consecutive columns of one row per lane: 4 (16-byte FP32 / 8-byte BF16
+// accesses) or 8 (32-byte FP32 accesses, the 256-bit vector loads and
+// stores of sm_100+, and 16-byte BF16 accesses).  "ro": read-only data
+// (non-coherent path).
+template <int CW> struct Lane;
+template <> struct Lane<4> {
+  static __device__ __forceinline__ void f32_ro(const float* p, float (&o)[4]) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+  static __device__ __forceinline__ void f32(const float* p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+  static __device__ __forceinline__ void st_f32(float* p, const float (&o)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  }
+  static __device__ __forceinline__ void bf16_ro(const __nv_bfloat16* p, float (&o)[4]) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    unpack(u.x, o[0], o[1]);
+    unpack(u.y, o[2], o[3]);
+  }
+  static __device__ __forceinline__ void bf16(const __nv_bfloat16* p, float (&o)[4]) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    unpack(u.x, o[0], o[1]);
+    unpack(u.y, o[2], o[3]);
+  }
+  static __device__ __forceinline__ void st_bf16(__nv_bfloat16* p, const uint32_t (&w)[2]) {
+    *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+  }
+  static __device__ __forceinline__ void unpack(uint32_t u, float& a, float& b) {
+    a = __uint_as_float(u << 16);
+    b = __uint_as_float(u & 0xffff0000u);
+  }
+};
+template <> struct Lane<8> {
+  static __device__ __forceinline__ void f32_ro(const float* p, float (&o)[8]) {
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]),
+          "=f"(o[7])
+        : "l"(p));
+  }
+  static __device__ __forceinline__ void f32(const float* p, float (&o)[8]) {
+    asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]), "=f"(o[4]), "=f"(o[5]),
+                   "=f"(o[6]), "=f"(o[7])
+                 : "l"(p)
+                 : "memory");
+  }
+  static __device__ __forceinline__ void st_f32(float* p, const float (&o)[8]) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(o[0]),
+                 "f"(o[1]), "f"(o[2]), "f"(o[3]), "f"(o[4]), "f"(o[5]), "f"(o[6]), "f"(o[7])
+                 : "memory");
+  }
+  static __device__ __forceinline__ void bf16_ro(const __nv_bfloat16* p, float (&o)[8]) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+    Lane<4>::unpack(u.x, o[0], o[1]);
+    Lane<4>::unpack(u.y, o[2], o[3]);
+    Lane<4>::unpack(u.z, o[4], o[5]);
+    Lane<4>::unpack(u.w, o[6], o[7]);
+  }
+  static __device__ __forceinline__ void bf16(const __nv_bfloat16* p, float (&o)[8]) {
+    const uint4 u = *reinterpret_cast<const uint4*>(p);
+    Lane<4>::unpack(u.x, o[0], o[1]);
+    Lane<4>::unpack(u.y, o[2], o[3]);
+    Lane<4>::unpack(u.z, o[4], o[5]);
+    Lane<4>::unpack(u.w, o[6], o[7]);
+  }
+  static __device__ __forceinline__ void st_bf16(__nv_bfloat16* p, const uint32_t (&w)[4]) {
+    *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+};
+
+}  // namespace
+
+// n-wide row accesses of the SpMM: VW = VecOf<VT>::width (16 bytes), or 8
+// floats (32 bytes) for FP32 rows whose leading dimensions allow it.
+template <class VT, int VW>
+__device__ __forceinline__ void rload_ro(const VT* p, VT (&o)[VW]) {
+  if constexpr (VW == 8) Lane<8>::f32_ro(p, o);
+  else vload_ro<VT>(p, o);
+}
+template <class VT, int VW>
+__device__ __forceinline__ void rload(const VT* p, VT (&o)[VW]) {
+  if constexpr (VW == 8) Lane<8>::f32(p, o);
+  else vload<VT>(p, o);
+}
+template <class VT, int VW>
+__device__ __forceinline__ void rstore(VT* p, const VT (&o)[VW]) {
+  if constexpr (VW == 8) Lane<8>::st_f32(p, o);
+  else vstore<VT>(p, o);
+}
+
 // Column accumulator: FP32 partial sums are flushed into FP64 every
 // kFlush rows so long reductions keep FP64 accuracy at FP32 cost.
 constexpr int kFlush = 16;
@@ -80,9 +174,8 @@ struct SpmmParams {
 //   tile0 + (v*TPR + t)*VW .. +VW-1, v < VPT.
 // Rows are visited grid-stride so concurrent groups sweep neighbouring rows
 // (their gathers share L2 lines of X for graphs with locality).
-template <class VT, int WT, int TPR, int VPT, bool DOT>
+template <class VT, int WT, int TPR, int VPT, bool DOT, int VW = VecOf<VT>::width>
 __global__ void __launch_bounds__(256) spmm_rows_kernel(SpmmParams<VT> p) {
-  constexpr int VW = VecOf<VT>::width;
   constexpr int TILE = TPR * VW * VPT;
   using A = typename Acc<VT>::type;
   const int t = threadIdx.x % TPR;
@@ -129,7 +222,7 @@ __global__ void __launch_bounds__(256) spmm_rows_kernel(SpmmParams<VT> p) {
         for (int v = 0; v < VPT; ++v) {
           if (cval[v]) {
             VT xv[VW];
-            vload_ro<VT>(xr + v * TPR * VW, xv);
+            rload_ro<VT, VW>(xr + v * TPR * VW, xv);
 #pragma unroll
             for (int w = 0; w < VW; ++w) acc[v][w] += wv * xv[w];
           }
@@ -143,17 +236,17 @@ __global__ void __launch_bounds__(256) spmm_rows_kernel(SpmmParams<VT> p) {
       VT y[VW];
       if (p.Z != nullptr) {
         VT z[VW];
-        vload<VT>(p.Z + i * p.ldz + c, z);
+        rload<VT, VW>(p.Z + i * p.ldz + c, z);
 #pragma unroll
         for (int w = 0; w < VW; ++w) y[w] = VT(gamma * z[w] + alpha * acc[v][w]);
       } else {
 #pragma unroll
         for (int w = 0; w < VW; ++w) y[w] = VT(alpha * acc[v][w]);
       }
-      vstore<VT>(p.Y + i * p.ldy + c, y);
+      rstore<VT, VW>(p.Y + i * p.ldy + c, y);
       if constexpr (DOT) {
         VT vv[VW];
-        vload<VT>(p.V + i * p.ldv + c, vv);
+        rload<VT, VW>(p.V + i * p.ldv + c, vv);
 #pragma unroll
         for (int w = 0; w < VW; ++w) dpart[v][w] += A(y[w]) * A(vv[w]);
       }
@@ -248,12 +341,12 @@ __global__ void __launch_bounds__(256) spmm_heavy_kernel(SpmmParams<VT> p, const
   }
 }
 
-template <class VT, int WT, int TPR, int VPT>
+template <class VT, int WT, int TPR, int VPT, int VW = VecOf<VT>::width>
 static void launch_rows(const SpmmParams<VT>& p, dim3 grid, cudaStream_t s) {
   if (p.dots)
-    spmm_rows_kernel<VT, WT, TPR, VPT, true><<<grid, 256, 0, s>>>(p);
+    spmm_rows_kernel<VT, WT, TPR, VPT, true, VW><<<grid, 256, 0, s>>>(p);
   else
-    spmm_rows_kernel<VT, WT, TPR, VPT, false><<<grid, 256, 0, s>>>(p);
+    spmm_rows_kernel<VT, WT, TPR, VPT, false, VW><<<grid, 256, 0, s>>>(p);
 }
 
 template <class VT, int WT>
@@ -278,13 +371,34 @@ static void spmm_dispatch(SpmmParams<VT>& p, const int32_t* heavy, int64_t n_hea
   ctas = std::max<int64_t>(1, std::min<int64_t>(ctas, std::max<int64_t>(1, cap / tiles)));
   dim3 grid((unsigned)ctas, (unsigned)tiles);
   p.skip_heavy = heavy != nullptr && n_heavy > 0;
+  // FP32 rows whose strides and bases allow 32-byte accesses: half the
+  // vectors per thread at 8 floats each (the same tile)
+  bool w8 = false;
+  if constexpr (sizeof(VT) == 4) {
+    const uintptr_t al = reinterpret_cast<uintptr_t>(p.X) | reinterpret_cast<uintptr_t>(p.Y) |
+                         reinterpret_cast<uintptr_t>(p.Z) |
+                         reinterpret_cast<uintptr_t>(p.dots ? p.V : nullptr);
+    w8 = tpr == 32 && vpt >= 2 && al % 32 == 0 && p.ldx % 8 == 0 && p.ldy % 8 == 0 &&
+         (p.Z == nullptr || p.ldz % 8 == 0) && (p.dots == nullptr || p.ldv % 8 == 0);
+  }
   if (p.A.nrows > 0) {
 #define KATZ_ROWS(T, V) \
   if (tpr == T && vpt == V) { launch_rows<VT, WT, T, V>(p, grid, s); }
-    KATZ_ROWS(1, 1) else KATZ_ROWS(2, 1) else KATZ_ROWS(4, 1) else KATZ_ROWS(8, 1)
-    else KATZ_ROWS(16, 1) else KATZ_ROWS(32, 1) else KATZ_ROWS(32, 2) else KATZ_ROWS(32, 4)
-    else KATZ_ROWS(32, 8) else throw Error(KATZ_EINVAL, "spmm: unsupported shape");
+#define KATZ_ROWS8(V) \
+  if (vpt == V) { launch_rows<VT, WT, 32, V / 2, 8>(p, grid, s); }
+    if constexpr (sizeof(VT) == 4) {
+      if (w8) {
+        KATZ_ROWS8(2) else KATZ_ROWS8(4) else KATZ_ROWS8(8)
+        else throw Error(KATZ_EINVAL, "spmm: unsupported shape");
+      }
+    }
+    if (!w8) {
+      KATZ_ROWS(1, 1) else KATZ_ROWS(2, 1) else KATZ_ROWS(4, 1) else KATZ_ROWS(8, 1)
+      else KATZ_ROWS(16, 1) else KATZ_ROWS(32, 1) else KATZ_ROWS(32, 2) else KATZ_ROWS(32, 4)
+      else KATZ_ROWS(32, 8) else throw Error(KATZ_EINVAL, "spmm: unsupported shape");
+    }
 #undef KATZ_ROWS
+#undef KATZ_ROWS8
     KATZ_CHECK_LAUNCH();
   }
   if (p.skip_heavy) {
@@ -355,34 +469,24 @@ namespace {
 
 enum : int { kInF32 = 0, kInHi = 1, kInHiLo = 2 };
 
-__device__ __forceinline__ void bf16x4_ro(const __nv_bfloat16* p, float (&o)[4]) {
-  const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-  o[0] = __uint_as_float(u.x << 16);
-  o[1] = __uint_as_float(u.x & 0xffff0000u);
-  o[2] = __uint_as_float(u.y << 16);
-  o[3] = __uint_as_float(u.y & 0xffff0000u);
-}
-__device__ __forceinline__ void bf16x4(const __nv_bfloat16* p, float (&o)[4]) {
-  const uint2 u = *reinterpret_cast<const uint2*>(p);
-  o[0] = __uint_as_float(u.x << 16);
-  o[1] = __uint_as_float(u.x & 0xffff0000u);
-  o[2] = __uint_as_float(u.y << 16);
-  o[3] = __uint_as_float(u.y & 0xffff0000u);
-}
 __device__ __forceinline__ uint32_t bf16_bits(float x) {
   return uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(x)));
 }
-// hi = bf16(x), lo = bf16(x - hi) for 4 consecutive columns
-__device__ __forceinline__ void split_store4(__nv_bfloat16* hi, __nv_bfloat16* lo,
-                                             const float (&x)[4]) {
-  uint32_t h[4], l[4];
+// hi = bf16(x), lo = bf16(x - hi) for CW consecutive columns
+template <int CW>
+__device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo,
+                                            const float (&x)[CW]) {
+  uint32_t h[CW / 2], l[CW / 2];
 #pragma unroll
-  for (int w = 0; w < 4; ++w) {
-    h[w] = bf16_bits(x[w]);
-    l[w] = bf16_bits(x[w] - __uint_as_float(h[w] << 16));
+  for (int w = 0; w < CW; w += 2) {
+    const uint32_t h0 = bf16_bits(x[w]), h1 = bf16_bits(x[w + 1]);
+    const uint32_t l0 = bf16_bits(x[w] - __uint_as_float(h0 << 16));
+    const uint32_t l1 = bf16_bits(x[w + 1] - __uint_as_float(h1 << 16));
+    h[w / 2] = h0 | (h1 << 16);
+    l[w / 2] = l0 | (l1 << 16);
   }
-  *reinterpret_cast<uint2*>(hi) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
-  *reinterpret_cast<uint2*>(lo) = make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
+  Lane<CW>::st_bf16(hi, h);
+  Lane<CW>::st_bf16(lo, l);
 }
 
 struct ChebArgs {
@@ -398,28 +502,26 @@ struct ChebArgs {
   int out_split;  // 1: write x_{k+1} split, 0: FP32
 };
 
-template <int WT, int VPT, int IN>
+// One warp per row and column tile of 32 * CW columns; lane t owns the CW
+// consecutive columns tile0 + t*CW .. +CW-1 (one vector access each).
+template <int WT, int CW, int IN>
 __global__ void __launch_bounds__(256) cheb_step_kernel(ChebArgs p) {
-  constexpr int VW = 4;
-  constexpr int TILE = 32 * VW * VPT;
+  constexpr int TILE = 32 * CW;
+  using L = Lane<CW>;
   const int t = threadIdx.x & 31;
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  const int tile0 = blockIdx.y * TILE;
   const int64_t ld = p.ld;
+  const int64_t c0 = int64_t(blockIdx.y) * TILE + t * CW;
+  const bool cval = c0 < p.b;
   const float* Xf = static_cast<const float*>(p.Xk);
   const __nv_bfloat16* Xh = static_cast<const __nv_bfloat16*>(p.Xk);
   const __nv_bfloat16* Xl = Xh + p.plane;
-  bool cval[VPT];
-#pragma unroll
-  for (int v = 0; v < VPT; ++v) cval[v] = tile0 + (v * 32 + t) * VW < p.b;
   for (int64_t i = warp; i < p.A.nrows; i += nwarps) {
     const int64_t k0 = p.A.rowptr[i], k1 = p.A.rowptr[i + 1];
-    float acc[VPT][VW];
+    float acc[CW];
 #pragma unroll
-    for (int v = 0; v < VPT; ++v)
-#pragma unroll
-      for (int w = 0; w < VW; ++w) acc[v][w] = 0.f;
+    for (int w = 0; w < CW; ++w) acc[w] = 0.f;
     for (int64_t kb = k0; kb < k1; kb += 32) {
       const int64_t k = kb + t;
       int cj = 0;
@@ -433,65 +535,62 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(ChebArgs p) {
       for (int s2 = 0; s2 < cnt; ++s2) {
         const int j = __shfl_sync(0xffffffffu, cj, s2);
         const float wv = (WT == KATZ_UNIT) ? 1.f : __shfl_sync(0xffffffffu, wj, s2);
-        const int64_t off = int64_t(j) * ld + tile0 + t * VW;
+        if (cval) {
+          const int64_t off = int64_t(j) * ld + c0;
+          float xv[CW];
+          if constexpr (IN == kInF32) {
+            L::f32_ro(Xf + off, xv);
+          } else {
+            L::bf16_ro(Xh + off, xv);
+            if constexpr (IN == kInHiLo) {
+              float xl[CW];
+              L::bf16_ro(Xl + off, xl);
 #pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-          if (cval[v]) {
-            float xv[VW];
-            if constexpr (IN == kInF32) {
-              vload_ro<float>(Xf + off + v * 32 * VW, xv);
-            } else {
-              bf16x4_ro(Xh + off + v * 32 * VW, xv);
-              if constexpr (IN == kInHiLo) {
-                float xl[VW];
-                bf16x4_ro(Xl + off + v * 32 * VW, xl);
-#pragma unroll
-                for (int w = 0; w < VW; ++w) xv[w] += xl[w];
-              }
+              for (int w = 0; w < CW; ++w) xv[w] += xl[w];
             }
-#pragma unroll
-            for (int w = 0; w < VW; ++w) acc[v][w] += wv * xv[w];
           }
+#pragma unroll
+          for (int w = 0; w < CW; ++w) acc[w] += wv * xv[w];
         }
       }
     }
+    if (!cval) continue;
+    const int64_t o = i * ld + c0;
+    float xo[CW], bo[CW], xp[CW], xn[CW];
+    if constexpr (IN == kInF32) {
+      L::f32_ro(Xf + o, xo);
+    } else {
+      float xl[CW];
+      L::bf16_ro(Xh + o, xo);
+      L::bf16_ro(Xl + o, xl);
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      if (!cval[v]) continue;
-      const int64_t o = i * ld + tile0 + (v * 32 + t) * VW;
-      float xo[VW], bo[VW], xp[VW] = {0.f, 0.f, 0.f, 0.f}, xn[VW];
-      if constexpr (IN == kInF32) {
-        vload_ro<float>(Xf + o, xo);
-      } else {
-        float xl[VW];
-        bf16x4_ro(Xh + o, xo);
-        bf16x4_ro(Xl + o, xl);
+      for (int w = 0; w < CW; ++w) xo[w] += xl[w];
+    }
+    L::f32(p.B + o, bo);
+    if (p.prev_mode == 1) {
+      L::f32(static_cast<const float*>(p.Xprev) + o, xp);
+    } else if (p.prev_mode == 2) {
+      const __nv_bfloat16* ph = static_cast<const __nv_bfloat16*>(p.Xprev);
+      float xl[CW];
+      L::bf16(ph + o, xp);
+      L::bf16(ph + p.plane + o, xl);
 #pragma unroll
-        for (int w = 0; w < VW; ++w) xo[w] += xl[w];
-      }
-      vload<float>(p.B + o, bo);
-      if (p.prev_mode == 1) {
-        vload<float>(static_cast<const float*>(p.Xprev) + o, xp);
-      } else if (p.prev_mode == 2) {
-        const __nv_bfloat16* ph = static_cast<const __nv_bfloat16*>(p.Xprev);
-        float xl[VW];
-        bf16x4(ph + o, xp);
-        bf16x4(ph + p.plane + o, xl);
+      for (int w = 0; w < CW; ++w) xp[w] += xl[w];
+    } else {
 #pragma unroll
-        for (int w = 0; w < VW; ++w) xp[w] += xl[w];
-      }
+      for (int w = 0; w < CW; ++w) xp[w] = 0.f;
+    }
 #pragma unroll
-      for (int w = 0; w < VW; ++w) {
-        const float xs = p.sx * xo[w];
-        const float r = bo[w] - xs + p.beta * (p.sx * acc[v][w]);
-        xn[w] = xs + p.ak * (xs - p.sp * xp[w]) + p.ck * r;
-      }
-      if (p.out_split) {
-        __nv_bfloat16* oh = static_cast<__nv_bfloat16*>(p.Xout);
-        split_store4(oh + o, oh + p.plane + o, xn);
-      } else {
-        vstore<float>(static_cast<float*>(p.Xout) + o, xn);
-      }
+    for (int w = 0; w < CW; ++w) {
+      const float xs = p.sx * xo[w];
+      const float r = bo[w] - xs + p.beta * (p.sx * acc[w]);
+      xn[w] = xs + p.ak * (xs - p.sp * xp[w]) + p.ck * r;
+    }
+    if (p.out_split) {
+      __nv_bfloat16* oh = static_cast<__nv_bfloat16*>(p.Xout);
+      split_store<CW>(oh + o, oh + p.plane + o, xn);
+    } else {
+      L::st_f32(static_cast<float*>(p.Xout) + o, xn);
     }
   }
 }
@@ -507,8 +606,13 @@ void cheb_step_ex(const Csr& A, double beta, double ak, double ck, const void* X
                     reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(Xout)) % 16 == 0,
                KATZ_EINVAL, "cheb_step: operands must be 16-byte aligned with padded rows");
   if (A.nrows <= 0) return;
-  const int vpt = b > 128 ? 2 : 1;
-  const int tile = 128 * vpt;
+  // 256-column tiles of 32-byte lane accesses where the rows allow them
+  // (ld a multiple of 8 elements, 32-byte aligned bases), else 128-column
+  // tiles of 16-byte accesses
+  const bool wide = b > 128 && ld % 8 == 0 &&
+                    ((reinterpret_cast<uintptr_t>(Xk) | reinterpret_cast<uintptr_t>(Xprev) |
+                      reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(Xout)) % 32) == 0;
+  const int tile = wide ? 256 : 128;
   const int64_t tiles = ceil_div(b, tile);
   const int cps = cfg && cfg->fused_cps > 0     ? cfg->fused_cps
                   : cfg && cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm
@@ -519,17 +623,17 @@ void cheb_step_ex(const Csr& A, double beta, double ak, double ck, const void* X
   ChebArgs a{A,     float(beta), float(ak), float(ck), float(sx), float(sp), Xk, Xprev, B,
              Xout,  ld,          A.nrows * ld,          b,         prev_mode, out_split};
   prof_begin(s);
-#define KATZ_CHEB_IN(WT, V)                                                          \
+#define KATZ_CHEB_IN(WT, C)                                                          \
   switch (in_mode) {                                                                 \
-    case kInF32: cheb_step_kernel<WT, V, kInF32><<<grid, 256, 0, s>>>(a); break;     \
-    case kInHi: cheb_step_kernel<WT, V, kInHi><<<grid, 256, 0, s>>>(a); break;       \
-    default: cheb_step_kernel<WT, V, kInHiLo><<<grid, 256, 0, s>>>(a); break;        \
+    case kInF32: cheb_step_kernel<WT, C, kInF32><<<grid, 256, 0, s>>>(a); break;     \
+    case kInHi: cheb_step_kernel<WT, C, kInHi><<<grid, 256, 0, s>>>(a); break;       \
+    default: cheb_step_kernel<WT, C, kInHiLo><<<grid, 256, 0, s>>>(a); break;        \
   }
 #define KATZ_CHEB(WT)         \
-  if (vpt == 2) {             \
-    KATZ_CHEB_IN(WT, 2)       \
+  if (wide) {                 \
+    KATZ_CHEB_IN(WT, 8)       \
   } else {                    \
-    KATZ_CHEB_IN(WT, 1)       \
+    KATZ_CHEB_IN(WT, 4)       \
   }
   switch (A.vdt) {
     case KATZ_UNIT: KATZ_CHEB(KATZ_UNIT); break;

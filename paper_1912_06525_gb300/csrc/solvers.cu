@@ -131,6 +131,10 @@ static unsigned flat_blocks(int64_t total) {
 // Column arrays that receive vectorised reductions are padded to a multiple
 // of 4 entries (a reduction over a 4-wide vector writes all 4 lanes).
 static int bpad(int b) { return (b + 3) / 4 * 4; }
+// Leading dimension of the query's n x b blocks: a multiple of 8 elements
+// for wide batches (32-byte row accesses in the fused gather kernels),
+// else of 4.
+static int64_t query_ld(int b) { return b > 128 ? (b + 7) / 8 * 8 : (b + 3) / 4 * 4; }
 
 // ------------------------------------------------------------ col state
 static ColState make_state(Workspace& ws, const std::string& tag, int b, bool with_rr) {
@@ -244,7 +248,7 @@ static bool use_pipe(const katz_index& idx, const SpmmCfg* cfg, bool first = fal
 // Iterates x_2 .. x_{K-1} are kept in the split BF16 form (two scratch
 // buffers, x_{k+1} overwriting x_{k-1} row by row) unless the query asks
 // for FP32 gathers; their products gather the hi plane alone except, under
-// KATZ_CHEB_AUTO, the last step of a solve asked for a tolerance below
+// KATZ_CHEB_MIXED, the last step of a solve asked for a tolerance below
 // kHiGatherTol: a step's gather error (~2^-9 relative per term, ~1e-4 of
 // beta W x after the sum) is damped by each later step by about the
 // convergence factor c (~0.05 on the benchmark graph), so the hi-plane
@@ -267,7 +271,7 @@ static void m11_chebyshev(katz_index& idx, const float* X, float* Y, int b, int6
   const SpmmCfg* cfg = idx.W11L.cfg(b);
   const bool pipe = use_pipe(idx, cfg) && pipe_eligible(idx.W11L.ps, ld) &&
                     (idx.unit_weights || idx.W11L.csr.vdt != KATZ_F64);
-  if (idx.cheb_pref == KATZ_CHEB_F32 || pipe) {
+  if (idx.cheb_pref == KATZ_CHEB_F32 || idx.cheb_pref == KATZ_CHEB_AUTO || pipe) {
     // FP32 iterates: x_k for k >= 2 alternates between Y and T so that x_K
     // lands in Y (x_{k+1} overwrites x_{k-1} row by row)
     float* T = idx.ws.get<float>("ch.T", size_t(len) * ld);
@@ -294,7 +298,7 @@ static void m11_chebyshev(katz_index& idx, const float* X, float* Y, int b, int6
   float* T = idx.ws.get<float>("ch.T", size_t(len) * ld);
   float* U = K > 3 ? idx.ws.get<float>("ch.U", size_t(len) * ld) : nullptr;
   auto slot = [&](int j) -> void* { return (j % 2 == 0) ? static_cast<void*>(T) : U; };
-  const bool last_exact = idx.cheb_pref == KATZ_CHEB_AUTO && tol < kHiGatherTol;
+  const bool last_exact = idx.cheb_pref == KATZ_CHEB_MIXED && tol < kHiGatherTol;
   for (int k = 1; k < K; ++k) {
     const double rho = 1.0 / (2.0 * sigma - rho_prev);
     const double ak = rho * rho_prev, ck = 2.0 * rho / d;
@@ -351,10 +355,40 @@ template <> struct Dense<double> {
 // and an n2 x ld block X: on the tensor cores (three TF32 products, FP32
 // accuracy; all ld columns so zero padding stays zero) where the index keeps
 // A's TF32 parts, else the FP32/FP64 SIMT GEMM.
+// Y = alpha S X + beta Y (beta 0 or 1) for a separator too large to store S:
+//   S X = M22 X - M12^T M11^{-1} M12 X = X - b W22 X - b W21 M11^{-1} (b W12 X)
+// (Lemma 1, Eqs. 4-7; b the damping).  The M11 solve runs to 1e-7 relative
+// (FP32) or 1e-14 (FP64), below what the PCG asks of S P.
+template <class VT>
+static void implicit_S(katz_index& idx, const VT* X, int64_t ld, int b, double alpha, double beta,
+                       VT* Y, cudaStream_t s) {
+  KATZ_REQUIRE(beta == 0.0 || beta == 1.0, KATZ_EINVAL, "implicit S: beta must be 0 or 1");
+  const int64_t n1 = idx.n1, n2 = idx.n2;
+  VT* Tm = idx.ws.get<VT>("Si.T", size_t(n2) * ld);
+  spmm<VT>(idx.W22.view(), idx.W22.heavy.p, idx.W22.n_heavy, -idx.beta, X, ld, 1.0, X, ld, Tm, ld,
+           b, nullptr, 0, nullptr, s, idx.W22.cfg(b));
+  if (n1 > 0) {
+    VT* U = idx.ws.get<VT>("Si.U", size_t(n1) * ld);
+    VT* V = idx.ws.get<VT>("Si.V", size_t(n1) * ld);
+    spmm<VT>(idx.W12.view(), idx.W12.heavy.p, idx.W12.n_heavy, idx.beta, X, ld, 0.0, nullptr, ld,
+             U, ld, b, nullptr, 0, nullptr, s, idx.W12.cfg(b));
+    const int st = m11_solve<VT>(idx, U, V, b, ld, sizeof(VT) == 4 ? 1e-7 : 1e-14, 5000,
+                                 nullptr, s);
+    KATZ_REQUIRE(st != KATZ_ENOTSPD, KATZ_ENOTSPD, "M11 is not positive definite");
+    spmm<VT>(idx.W21.view(), idx.W21.heavy.p, idx.W21.n_heavy, -idx.beta, V, ld, 1.0, Tm, ld, Tm,
+             ld, b, nullptr, 0, nullptr, s, idx.W21.cfg(b));
+  }
+  scale_copy<VT>(Tm, ld, Y, ld, n2, int(ld), alpha, beta != 0.0, s);
+}
+
 template <class VT>
 static void dense_n2(katz_index& idx, bool minv, const VT* X, int64_t ld, int b, double alpha,
                      double beta, VT* Y, cudaStream_t s) {
   const int64_t n2 = idx.n2;
+  if (!minv && idx.s_implicit) {
+    implicit_S<VT>(idx, X, ld, b, alpha, beta, Y, s);
+    return;
+  }
   if constexpr (sizeof(VT) == 4) {
     if (idx.dense_tc) {
       float* Xh = idx.ws.get<float>("S.Xh", size_t(ld) * idx.ld2);
@@ -636,6 +670,21 @@ static double solve_tol(const katz_query_opts& o, const QueryOut& out) {
   return std::max(0.5 * o.tol, o.tol - std::ldexp(1.0 + o.tol, -24));
 }
 
+// CG warm start: columns c whose residual of the guess is not below the
+// right-hand side's (rr[c] >= bn2[c]) are zeroed in K (restart from zero);
+// *count gets n for each such column (every row of the column counts one).
+__global__ void warm_cg_fallback_kernel(float* K, int64_t ld, int64_t n, int b, const double* rr,
+                                        const double* bn2, int* count) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n * ld;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int c = int(e % ld);
+    if (c < b && rr[c] >= bn2[c]) {
+      K[e] = 0.f;
+      atomicAdd(count, 1);
+    }
+  }
+}
+
 // Mixed-precision query for graphs whose weights are exact in FP32: FP32
 // solves, the solution kept as a float-float pair (Kh, Kl) and the residual
 // as (Rh, Rl), both updated by one pass per refinement step that gathers the
@@ -649,7 +698,7 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   using clk = std::chrono::steady_clock;
   const auto t0 = clk::now();
   const int64_t n = idx.n;
-  const int64_t ld = (b + 3) / 4 * 4;
+  const int64_t ld = query_ld(b);
   const int max_iter = o.max_iter > 0 ? o.max_iter : 2000;
   const int max_refine = o.max_refine > 0 ? o.max_refine : 12;
   const int32_t* pos = use_lrc ? idx.iperm.p : nullptr;
@@ -690,22 +739,36 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   inner_thresholds_kernel<<<1, 1024, 0, s>>>(bn2, thr2, tau, b, conv, thr2_in, nopen);
   KATZ_CHECK_LAUNCH();
   const float* K20 = nullptr;
+  const bool cg_warm = o.warm_start && !use_lrc;
   if (o.warm_start) {
-    KATZ_REQUIRE(use_lrc && idx.mlp.ready, KATZ_EINVAL,
-                 "warm_start needs an LRC query and a trained warm-start network");
-    float* g = ws.get<float>("q.K20", size_t(std::max<int64_t>(idx.n2, 1)) * ld);
-    warm_start_guess(idx, q, b, g, ld, s);
-    K20 = g;
+    KATZ_REQUIRE(idx.lrc && idx.mlp.ready, KATZ_EINVAL,
+                 "warm_start needs an index with the LRC part and a trained warm-start network");
+    if (use_lrc) {
+      float* g = ws.get<float>("q.K20", size_t(std::max<int64_t>(idx.n2, 1)) * ld);
+      warm_start_guess(idx, q, b, g, ld, s);
+      K20 = g;
+    }
   }
   const auto t1 = clk::now();
-  int status = inner_solve<float>(idx, use_lrc, Rh, Kh, b, ld, thr2_in, tol_rel, max_iter, &iters,
-                                  s, K20);
+  int status = KATZ_OK;
+  if (cg_warm) {
+    // CG from the network's guess: the first residual pass below evaluates
+    // b - M K0 for it, and columns whose guess is not better than zero
+    // (||b - M K0|| >= ||b||) restart from zero
+    KATZ_CUDA(cudaMemsetAsync(Kh, 0, sizeof(float) * n * ld, s));
+    warm_cg_guess(idx, q, b, Kh, ld, s);
+  } else {
+    status = inner_solve<float>(idx, use_lrc, Rh, Kh, b, ld, thr2_in, tol_rel, max_iter, &iters,
+                                s, K20);
+  }
   KATZ_CUDA(cudaMemsetAsync(Kl, 0, sizeof(float) * n * ld, s));
   KATZ_CUDA(cudaStreamSynchronize(s));
   const auto t2 = clk::now();
   double ms_res = 0;
   int refine = 0;
   bool pending = false;  // D holds a correction not yet added to K
+  bool warm_checked = false;
+  int64_t warm_fallbacks = 0;
   HeavyRows hv;  // the residual operator's heavy rows, split
   if (status == KATZ_OK || status == KATZ_ENOCONV) {
     for (;;) {
@@ -727,6 +790,17 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
                      heavy_rows(G, ld, ws, hv));
         ffr_add_rhs(idx.W.view(), q, pos, b, idx.beta, Rh, Rl, ld, nullptr, maxdeg, s);
         coldot<float>(Rh, ld, Rh, ld, n, b, rr, s);
+        if (cg_warm && !warm_checked) {
+          warm_checked = true;
+          int* nfb = ws.get<int>("q.nfb", 1);
+          KATZ_CUDA(cudaMemsetAsync(nfb, 0, sizeof(int), s));
+          warm_cg_fallback_kernel<<<(unsigned)std::max<int64_t>(
+                                        1, std::min<int64_t>(ceil_div(n * ld, 256), 4096)),
+                                    256, 0, s>>>(Kh, ld, n, b, rr, bn2, nfb);
+          KATZ_CHECK_LAUNCH();
+          warm_fallbacks = read_int(nfb, s) / std::max<int64_t>(1, n);
+          if (warm_fallbacks > 0) continue;  // the zeroed columns: first pass again
+        }
       } else {
         // Rl carries the first pass's low part into the first update only
         ffr_update(G.view(), idx.beta, D, Rh, refine == 1 ? Rl : nullptr, false, ld, b, rr, gcfg,
@@ -782,10 +856,12 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
     stats->ms[1] = std::chrono::duration<double, std::milli>(t1 - t0).count();
     stats->ms[2] = std::chrono::duration<double, std::milli>(t2 - t1).count();
     stats->ms[3] = ms_res;
-    if (o.warm_start) {
+    if (o.warm_start && use_lrc) {
       int h = 0;
       KATZ_CUDA(cudaMemcpy(&h, ws.get<int>("S.nfb", 1), sizeof(int), cudaMemcpyDeviceToHost));
       stats->ms[5] = h;  // columns whose warm start fell back to zero
+    } else if (o.warm_start) {
+      stats->ms[5] = double(warm_fallbacks);
     }
   }
   return status;
@@ -798,7 +874,7 @@ static int query_impl(katz_index& idx, bool use_lrc, const int32_t* q, int b,
   using clk = std::chrono::steady_clock;
   const auto t0 = clk::now();
   const int64_t n = idx.n;
-  const int64_t ld = (b + 3) / 4 * 4;
+  const int64_t ld = query_ld(b);
   const int max_iter = o.max_iter > 0 ? o.max_iter : 2000;
   const int max_refine = o.max_refine > 0 ? o.max_refine : 12;
   const bool mixed = o.precision == KATZ_PREC_MIXED;
@@ -913,7 +989,7 @@ int run_queries(katz_index& idx, bool use_lrc, const int32_t* q_dev, const int32
   KATZ_REQUIRE(o.gather_kernel >= KATZ_GATHER_AUTO && o.gather_kernel <= KATZ_GATHER_PIPELINED,
                KATZ_EINVAL, "gather_kernel must be a KATZ_GATHER_* value");
   idx.gather_pref = o.gather_kernel;
-  KATZ_REQUIRE(o.cheb_gather >= KATZ_CHEB_AUTO && o.cheb_gather <= KATZ_CHEB_BF16, KATZ_EINVAL,
+  KATZ_REQUIRE(o.cheb_gather >= KATZ_CHEB_AUTO && o.cheb_gather <= KATZ_CHEB_MIXED, KATZ_EINVAL,
                "cheb_gather must be a KATZ_CHEB_* value");
   idx.cheb_pref = o.cheb_gather;
   int* perr = idx.ws.get<int>("pipe.err", 1);

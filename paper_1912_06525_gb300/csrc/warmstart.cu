@@ -127,10 +127,28 @@ void warm_features(katz_index& idx, cudaStream_t s) {
   KATZ_CHECK_LAUNCH();
   col_scale_kernel<<<blocks(n * kFeat), 256, 0, s>>>(idx.feat.p, n, mom, mom + kFeat);
   KATZ_CHECK_LAUNCH();
+  // keep H (the harmonic extension of the basis) for the CG warm start
+  if (n1 > 0) {
+    idx.Hr.alloc(size_t(n1) * ldr);
+    KATZ_CUDA(cudaMemcpyAsync(idx.Hr.p, H, 4 * size_t(n1) * ldr, cudaMemcpyDeviceToDevice, s));
+  }
   idx.ws.release("wf.U");
   idx.ws.release("wf.H");
   KATZ_CUDA(cudaStreamSynchronize(s));
   (void)n2;
+}
+
+// H = beta M11^{-1} W12 W_r (n1 x ldr4), recomputed when an index was loaded
+// from a file (the features are stored, H is not).
+static void ensure_harmonic_basis(katz_index& idx, cudaStream_t s) {
+  const int64_t n1 = idx.n1, ldr = idx.ldr4;
+  if (idx.Hr.p || n1 == 0) return;
+  float* U = idx.ws.get<float>("wf.U", size_t(n1) * ldr);
+  idx.Hr.alloc(size_t(n1) * ldr);
+  spmm<float>(idx.W12.view(), idx.W12.heavy.p, idx.W12.n_heavy, idx.beta, idx.Wr32u.p, ldr, 0.0,
+              nullptr, ldr, U, ldr, idx.rank, nullptr, 0, nullptr, s);
+  m11_solve<float>(idx, U, idx.Hr.p, idx.rank, ldr, 1e-5, 500, nullptr, s);
+  idx.ws.release("wf.U");
 }
 
 // Targets c* (b x r, row j = query j) from K (node order, n x b, ldk).
@@ -150,9 +168,8 @@ static void targets_from_K(katz_index& idx, const float* K, int64_t ldk, int b, 
   gemm2<float>(true, false, b, r, n2, 1.0, mk, ld, idx.Wr32u.p, idx.ldr4, 0.0, T, r, false, s);
 }
 
-// K2(0) (n2 x b, ld) = W_r C^T with C = MLP(features of q) (b x r)
-void warm_start_guess(katz_index& idx, const int32_t* q, int b, float* K20, int64_t ld,
-                      cudaStream_t s) {
+// C (b x r) = MLP(features of q): the predicted coordinates c_hat.
+static const float* warm_coeffs(katz_index& idx, const int32_t* q, int b, cudaStream_t s) {
   const int r = idx.rank;
   float* X = idx.ws.get<float>("ws.X", size_t(b) * kFeat);
   float* Hp = idx.ws.get<float>("ws.Hp", size_t(b) * idx.mlp.dh);
@@ -161,8 +178,60 @@ void warm_start_guess(katz_index& idx, const int32_t* q, int b, float* K20, int6
   gather_feat_kernel<<<blocks(int64_t(b) * kFeat), 256, 0, s>>>(idx.feat.p, q, b, X);
   KATZ_CHECK_LAUNCH();
   idx.mlp.forward(X, b, Hp, Hh, C, s);
+  return C;
+}
+
+// K2(0) (n2 x b, ld) = W_r C^T with C = MLP(features of q) (b x r)
+void warm_start_guess(katz_index& idx, const int32_t* q, int b, float* K20, int64_t ld,
+                      cudaStream_t s) {
+  const float* C = warm_coeffs(idx, q, b, s);
   KATZ_CUDA(cudaMemsetAsync(K20, 0, 4 * idx.n2 * ld, s));
-  gemm2<float>(false, true, idx.n2, b, r, 1.0, idx.Wr32u.p, idx.ldr4, C, r, 0.0, K20, ld, false, s);
+  gemm2<float>(false, true, idx.n2, b, idx.rank, 1.0, idx.Wr32u.p, idx.ldr4, C, idx.rank, 0.0, K20,
+               ld, false, s);
+}
+
+namespace {
+// Xn[i] = Xi[iperm[i]] (rows of b columns, both ld): index order -> node order
+__global__ void unpermute_rows_kernel(const float* Xi, const int32_t* iperm, int64_t n, int b,
+                                      int64_t ld, float* Xn) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n * b;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / b;
+    const int j = int(e - i * b);
+    Xn[i * ld + j] = Xi[int64_t(iperm[i]) * ld + j];
+  }
+}
+}  // namespace
+
+// Initial guess of CG on M (node order, n x b, ld; padding columns zero):
+// the whole Katz vector the LRC decomposition predicts from c_hat,
+//   K2(0) = W_r c_hat,  K1(0) = M11^{-1} B1 + beta M11^{-1} W12 W_r c_hat
+// (Eq. 6 with K2 replaced by the network's separator part; the first term
+// is one M11 solve of the right-hand side to 1e-4, the second the stored
+// harmonic extension H of the basis times c_hat).  Its error is the
+// harmonic extension of the separator error K2 - W_r c_hat alone.
+void warm_cg_guess(katz_index& idx, const int32_t* q, int b, float* X, int64_t ld,
+                   cudaStream_t s) {
+  KATZ_REQUIRE(idx.lrc && idx.rank > 0 && idx.mlp.ready && idx.feat.p, KATZ_EINVAL,
+               "warm start needs an LRC index with a trained warm-start network");
+  ensure_harmonic_basis(idx, s);
+  const int64_t n = idx.n, n1 = idx.n1, n2 = idx.n2;
+  const int r = idx.rank;
+  float* Bi = idx.ws.get<float>("wg.B", size_t(n) * ld);
+  float* Xi = idx.ws.get<float>("wg.X", size_t(n) * ld);
+  KATZ_CUDA(cudaMemsetAsync(Bi, 0, 4 * size_t(n) * ld, s));
+  KATZ_CUDA(cudaMemsetAsync(Xi, 0, 4 * size_t(n) * ld, s));
+  const float* C = warm_coeffs(idx, q, b, s);
+  // separator rows: W_r c_hat
+  gemm2<float>(false, true, n2, b, r, 1.0, idx.Wr32u.p, idx.ldr4, C, r, 0.0, Xi + n1 * ld, ld,
+               false, s);
+  if (n1 > 0) {
+    build_rhs<float>(idx.W.view(), q, b, idx.beta, idx.iperm.p, Bi, ld, s);
+    m11_solve<float>(idx, Bi, Xi, b, ld, 1e-4, 500, nullptr, s);
+    gemm2<float>(false, true, n1, b, r, 1.0, idx.Hr.p, idx.ldr4, C, r, 1.0, Xi, ld, false, s);
+  }
+  unpermute_rows_kernel<<<blocks(n * b), 256, 0, s>>>(Xi, idx.iperm.p, n, b, ld, X);
+  KATZ_CHECK_LAUNCH();
 }
 
 double warmstart_train(katz_index& idx, const int32_t* q_host, int n_train, int hidden, int epochs,

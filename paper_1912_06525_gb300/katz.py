@@ -22,7 +22,7 @@ KATZ_UNIT, KATZ_F64, KATZ_F32, KATZ_BF16 = range(4)
 KATZ_PREC_F32, KATZ_PREC_MIXED, KATZ_PREC_F64 = range(3)
 KATZ_TOL_RESIDUAL, KATZ_TOL_ERROR_INF = range(2)
 KATZ_GATHER_AUTO, KATZ_GATHER_REGISTER, KATZ_GATHER_PIPELINED = range(3)
-KATZ_CHEB_AUTO, KATZ_CHEB_F32, KATZ_CHEB_BF16 = range(3)
+KATZ_CHEB_AUTO, KATZ_CHEB_F32, KATZ_CHEB_BF16, KATZ_CHEB_MIXED = range(4)
 
 STATUS_NAMES = {0: "KATZ_OK", 1: "KATZ_EINVAL", 2: "KATZ_ENOTSPD", 3: "KATZ_ENOCONV",
                 4: "KATZ_ENOMEM", 5: "KATZ_ECUDA"}
@@ -83,7 +83,7 @@ class katz_index_info(C.Structure):
                 ("n_blocks", C.c_int32), ("n_large_blocks", C.c_int32), ("rank", C.c_int32),
                 ("value_dtype", C.c_int32), ("beta", C.c_double), ("lambda_max_R", C.c_double),
                 ("device_bytes", C.c_int64), ("lambda_max_W", C.c_double),
-                ("lambda_upper", C.c_double)]
+                ("lambda_upper", C.c_double), ("schur_implicit", C.c_int32)]
 
 
 _lib = None

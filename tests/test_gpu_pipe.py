@@ -64,11 +64,12 @@ def test_pipelined_paths_match_oracle(vdt, b):
 @pytest.mark.parametrize("vdt", [katz.KATZ_UNIT, katz.KATZ_BF16])
 @pytest.mark.parametrize("b", [5, 333, 1024])
 def test_chebyshev_gather_precisions_match_oracle(vdt, b):
-    """The large M11 block's Chebyshev steps with FP32 iterates, with split
-    BF16 iterates gathered as hi + lo on a solve's last step (AUTO), and
-    with hi-plane gathers on every step (BF16): the refined answers all meet
-    the 1e-6 bound; column tiles of 128 (b = 5) and 256 columns, ragged
-    tails, unit and BF16 weights."""
+    """The large M11 block's Chebyshev steps with FP32 iterates (AUTO, F32),
+    with split BF16 iterates gathered as hi + lo on a solve's last step
+    (MIXED), and with hi-plane gathers on every step (BF16): the refined
+    answers all meet the 1e-6 bound; 128-column tiles of 16-byte lane
+    accesses (b = 5) and 256-column tiles of 32-byte ones, ragged tails,
+    unit and BF16 weights."""
     g = graph(weighted=vdt != katz.KATZ_UNIT, seed=13)
     W = O.adjacency(g.n, g.rowptr, g.col, g.val)
     beta = 0.9 / O.lambda_max(W)
@@ -78,7 +79,8 @@ def test_chebyshev_gather_precisions_match_oracle(vdt, b):
     q = synth.queries(g.n, b, seed=b + 1)
     q[0] = 3000
     ref = O.katz_direct(W, beta, q)
-    for mode in (katz.KATZ_CHEB_AUTO, katz.KATZ_CHEB_F32, katz.KATZ_CHEB_BF16):
+    for mode in (katz.KATZ_CHEB_AUTO, katz.KATZ_CHEB_F32, katz.KATZ_CHEB_BF16,
+                 katz.KATZ_CHEB_MIXED):
         K = torch.zeros((g.n, b), dtype=torch.float32, device="cuda")
         st, it, rel = katz.katz_query_batch(idx, torch.from_numpy(q).cuda(), K, tol=1e-6,
                                             gather_kernel=katz.KATZ_GATHER_REGISTER,
