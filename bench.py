@@ -612,7 +612,7 @@ def run_warm(args, world, rank, local):
                            ("warm", katz.katz_query_batch, 1),
                            ("cg_cold", katz.cg_query_batch, 0),
                            ("cg_warm", katz.cg_query_batch, 1)):
-        its, ms, fb, ref = [], 0.0, 0, []
+        its, ms, fb, ref, gam = [], 0.0, 0, [], []
         for j0 in range(0, len(test), b):
             qd = torch.from_numpy(test[j0:j0 + b]).cuda()
             Kb = torch.empty((g.n, len(qd)), dtype=torch.float32, device="cuda")
@@ -628,10 +628,13 @@ def run_warm(args, world, rank, local):
             its.extend(it.tolist())
             fb += int(st["ms"][5])
             ref.append(st["refine_steps"])
+            gam.append(st["ms"][6])
         res[name] = {"queries_per_s": len(test) / (ms / 1000), "ms": ms,
                      ("mean_pcg_iters" if fn is katz.katz_query_batch else "mean_cg_iters"):
                          float(np.mean(its)),
-                     "warm_fallbacks": fb, "refine_steps": ref}
+                     "warm_fallbacks": fb, "refine_steps": ref,
+                     **({"mean_gamma": float(np.mean(gam))}
+                        if fn is katz.cg_query_batch and warm else {})}
     if rank == 0:
         print(json.dumps({"metric": "Katz queries/sec at 1e-6 rel. error, warm vs cold start",
                           "unit": UNIT, "value": res["warm"]["queries_per_s"], "n_gpus": world,

@@ -75,8 +75,9 @@ extern "C" {
  * gather the hi plane alone: half the bytes per gathered row, at ~2^-9
  * relative error per gathered term.  BF16: hi-plane gathers on every step
  * after the first; MIXED: the same, except that the last step of a solve
- * asked for a tolerance below 1e-4 gathers hi + lo.  AUTO: the mode
- * measured fastest on the benchmark graph, currently F32. */
+ * asked for a tolerance below 1e-4 gathers hi + lo.  AUTO: FP32 iterates,
+ * the intermediate ones stored tile-major (each 256-column tile's rows
+ * contiguous) for batches wider than 128 columns. */
 #define KATZ_CHEB_AUTO 0
 #define KATZ_CHEB_F32 1
 #define KATZ_CHEB_BF16 2
@@ -132,7 +133,11 @@ typedef struct {
   int32_t max_iter;    /* cap on iterations of each inner CG / PCG solve (0 = 2000) */
   int32_t max_refine;  /* cap on FP64 refinement steps (0 = 12) */
   int32_t rhs_width;   /* columns solved together (0 = all b at once) */
-  int32_t warm_start;  /* 1: start LRC from the learned warm start (needs a trained network) */
+  int32_t warm_start;  /* 1: start from the learned warm start (needs a trained network; mixed
+                          precision): LRC starts its Schur PCG from K2 = W_r c_hat; CG on M
+                          starts from the whole vector [M11^{-1} B1 + beta M11^{-1} W12 W_r
+                          c_hat; W_r c_hat], each column scaled to its energy-optimal multiple
+                          gamma = b^T x / x^T M x (zero if that is not positive) */
   int32_t gather_kernel; /* KATZ_GATHER_*: kernel of the wide sparse products (Chebyshev
                             steps of the large M11 blocks, refinement residual) */
   int32_t cheb_gather;   /* KATZ_CHEB_*: precision of the Chebyshev steps' gathers */
@@ -143,7 +148,9 @@ typedef struct {
   int32_t refine_steps; /* FP64 residual evaluations performed */
   double max_rel_res;   /* max_j ||b_j - M k_j||_2 / ||b_j||_2 of the returned K (FP64) */
   double ms[8];         /* [0] total ms, [1] RHS ms, [2] first inner solve ms, [3] residual ms,
-                           [4] CUDA-graph replays (multi-graph), [5] warm-start fallbacks */
+                           [4] CUDA-graph replays (multi-graph), [5] warm-start fallbacks
+                           (columns started from zero), [6] mean scale of the CG warm
+                           start's guesses */
 } katz_stats;
 
 typedef struct {

@@ -162,6 +162,114 @@ __device__ __forceinline__ void row_epilogue(int64_t i, const FF (&acc)[VPT][4],
   }
 }
 
+// ---------------------------------------- wide rows, packed arithmetic
+// Two FP32 values in one 64-bit register, operated on by the packed
+// f32x2 instructions of sm_100+ (one instruction for two columns, the same
+// IEEE round-to-nearest operations as two scalar ones, never contracted).
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t pack2(float a, float b) {
+  return uint64_t(__float_as_uint(a)) | (uint64_t(__float_as_uint(b)) << 32);
+}
+__device__ __forceinline__ float lo2(uint64_t v) { return __uint_as_float(uint32_t(v)); }
+__device__ __forceinline__ float hi2(uint64_t v) { return __uint_as_float(uint32_t(v >> 32)); }
+// 8 consecutive FP32 values as 4 packed pairs (one 32-byte access)
+__device__ __forceinline__ void ld8_ro(const float* p, uint64_t (&o)[4]) {
+  asm("ld.global.nc.v4.b64 {%0,%1,%2,%3}, [%4];"
+      : "=l"(o[0]), "=l"(o[1]), "=l"(o[2]), "=l"(o[3])
+      : "l"(p));
+}
+__device__ __forceinline__ void ld8(const float* p, uint64_t (&o)[4]) {
+  asm volatile("ld.global.v4.b64 {%0,%1,%2,%3}, [%4];"
+               : "=l"(o[0]), "=l"(o[1]), "=l"(o[2]), "=l"(o[3])
+               : "l"(p)
+               : "memory");
+}
+__device__ __forceinline__ void st8(float* p, const float (&v)[8]) {
+  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]),
+               "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+// (hi, lo) += x elementwise for two pairs of columns: TwoSum (Knuth) of hi
+// and x, its rounding error added to lo
+__device__ __forceinline__ void ff_acc2(uint64_t& hi, uint64_t& lo, uint64_t x) {
+  const uint64_t s = add2(hi, x);
+  const uint64_t bb = sub2(s, hi);
+  const uint64_t e = add2(sub2(hi, sub2(s, bb)), sub2(x, bb));
+  hi = s;
+  lo = add2(lo, e);
+}
+
+// Row sums over the stored entries [k0, k1) of one row for the lane's 8
+// columns c0 .. c0+7: float-float (FFACC; the product w x split exactly by
+// FMA for weighted graphs) or FP32, as packed pairs.
+template <int WT, bool FFACC>
+__device__ __forceinline__ void row_sum8(const Csr& A, const float* __restrict__ X, int64_t ld,
+                                         int64_t c0, bool cval, int t, int64_t k0, int64_t k1,
+                                         uint64_t (&hi)[4], uint64_t (&lo)[4]) {
+  constexpr bool UNIT = WT == KATZ_UNIT;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) hi[q] = lo[q] = 0;
+  for (int64_t kb = k0; kb < k1; kb += 32) {
+    const int64_t k = kb + t;
+    int cj = 0;
+    float wj = 0.f;
+    if (k < k1) {
+      cj = A.col[k];
+      if constexpr (!UNIT) wj = weight<WT>(A.val, k);
+    }
+    const int cnt = (int)(k1 - kb < 32 ? k1 - kb : 32);
+#pragma unroll 4
+    for (int s2 = 0; s2 < cnt; ++s2) {
+      const int j = __shfl_sync(0xffffffffu, cj, s2);
+      float wv = 1.f;
+      if constexpr (!UNIT) wv = __shfl_sync(0xffffffffu, wj, s2);
+      if (cval) {
+        uint64_t x[4];
+        ld8_ro(X + int64_t(j) * ld + c0, x);
+        if constexpr (UNIT) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if constexpr (FFACC) ff_acc2(hi[q], lo[q], x[q]);
+            else hi[q] = add2(hi[q], x[q]);
+          }
+        } else {
+          const uint64_t w2 = pack2(wv, wv);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if constexpr (FFACC) {
+              const uint64_t pr = mul2(w2, x[q]);
+              const uint64_t pe = fma2(w2, x[q], pr ^ 0x8000000080000000ull);  // w x - p, exact
+              ff_acc2(hi[q], lo[q], pr);
+              lo[q] = add2(lo[q], pe);
+            } else {
+              hi[q] = fma2(w2, x[q], hi[q]);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
 // Per-CTA column sums of Rh^2 (red: [8 warps][TILE] in shared memory, each
 // warp's lanes add their sq), then one FP64 atomic per column and CTA.
 template <int VPT>
@@ -240,6 +348,76 @@ __global__ void __launch_bounds__(256) ffr_rows_kernel(Csr A, const float* __res
   flush_sq<VPT>(red, wib, t, sq);
   __syncthreads();
   if (rr) column_atomics<VPT>(red, tile0, b, rr);
+}
+
+// Warp per row (grid-stride) on 256-column tiles, 8 consecutive columns
+// per lane moved by 32-byte accesses and summed with packed f32x2
+// instructions; otherwise as ffr_rows_kernel (same sums, same epilogue).
+template <int WT, bool INIT>
+__global__ void __launch_bounds__(256) ffr_rows8_kernel(Csr A, const float* __restrict__ X,
+                                                        float* Rh, float* Rl, int64_t ld,
+                                                        float beh, float bel, double* rr, int b,
+                                                        bool skip_heavy) {
+  constexpr int TILE = 256;
+  __shared__ double red[8][TILE];
+  const int t = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int64_t tile0 = int64_t(blockIdx.y) * TILE;
+  const int64_t c0 = tile0 + 8 * t;
+  const bool cval = c0 < ld;
+  for (int c = threadIdx.x; c < 8 * TILE; c += blockDim.x) (&red[0][0])[c] = 0.0;
+  float sq[8];
+#pragma unroll
+  for (int w = 0; w < 8; ++w) sq[w] = 0.f;
+  int nsq = 0;
+  __syncthreads();
+  for (int64_t i = warp; i < A.nrows; i += nwarps) {
+    const int64_t k0 = A.rowptr[i], k1 = A.rowptr[i + 1];
+    if (skip_heavy && k1 - k0 > kHeavyRowNnz) continue;
+    uint64_t hi[4], lo[4];
+    if (INIT || k1 - k0 > kFp32Row)
+      row_sum8<WT, true>(A, X, ld, c0, cval, t, k0, k1, hi, lo);
+    else
+      row_sum8<WT, false>(A, X, ld, c0, cval, t, k0, k1, hi, lo);
+    if (cval) {
+      const int64_t o = i * ld + c0;
+      uint64_t xq[4], a[4] = {0, 0, 0, 0}, l[4] = {0, 0, 0, 0};
+      ld8_ro(X + o, xq);
+      if constexpr (!INIT) {
+        ld8(Rh + o, a);
+        if (Rl) ld8(Rl + o, l);
+      }
+      float rh[8], rl[8];
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        const int q = w >> 1;
+        const bool up = w & 1;
+        const FF acc = {up ? hi2(hi[q]) : lo2(hi[q]), up ? hi2(lo[q]) : lo2(lo[q])};
+        const float xw = up ? hi2(xq[q]) : lo2(xq[q]);
+        const float r0 = up ? hi2(a[q]) : lo2(a[q]);
+        const float l0 = up ? hi2(l[q]) : lo2(l[q]);
+        const FF r = ff_res(acc, beh, bel, xw, r0, l0);
+        rh[w] = r.hi;
+        rl[w] = r.lo;
+        sq[w] = __fmaf_rn(r.hi, r.hi, sq[w]);
+      }
+      st8(Rh + o, rh);
+      if constexpr (INIT) st8(Rl + o, rl);
+    }
+    if (++nsq == 64) {
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        red[wib][8 * t + w] += sq[w];
+        sq[w] = 0.f;
+      }
+      nsq = 0;
+    }
+  }
+#pragma unroll
+  for (int w = 0; w < 8; ++w) red[wib][8 * t + w] += sq[w];
+  __syncthreads();
+  if (rr) column_atomics<2>(red, tile0, b, rr);
 }
 
 // Heavy rows, pass 1: CTA = (segment of kHeavySeg entries, column tile);
@@ -406,11 +584,20 @@ void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl,
   const bool split = hv && hv->nseg > 0;
   KATZ_REQUIRE(!split || (hv->scratch && reinterpret_cast<uintptr_t>(hv->scratch) % 16 == 0),
                KATZ_EINVAL, "ffr_update: heavy-row scratch must be 16-byte aligned");
+  // 32-byte lane accesses where the rows and bases allow them (same tiles
+  // of 256 columns)
+  const bool wide = vpt == 2 && ld % 8 == 0 &&
+                    ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Rh) |
+                      reinterpret_cast<uintptr_t>(Rl)) % 32) == 0;
   prof_begin(s);
 #define KATZ_FFR(WT, V, I) \
   ffr_rows_kernel<WT, V, I><<<grid, 256, 0, s>>>(A, X, Rh, Rl, ld, beh, bel, rr, b, split)
+#define KATZ_FFR8(WT, I) \
+  ffr_rows8_kernel<WT, I><<<grid, 256, 0, s>>>(A, X, Rh, Rl, ld, beh, bel, rr, b, split)
 #define KATZ_FFR_W(WT)                                                     \
-  if (vpt == 2) {                                                          \
+  if (wide) {                                                              \
+    if (init) KATZ_FFR8(WT, true); else KATZ_FFR8(WT, false);              \
+  } else if (vpt == 2) {                                                   \
     if (init) KATZ_FFR(WT, 2, true); else KATZ_FFR(WT, 2, false);          \
   } else {                                                                 \
     if (init) KATZ_FFR(WT, 1, true); else KATZ_FFR(WT, 1, false);          \
@@ -422,6 +609,7 @@ void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl,
     default: KATZ_FFR_W(KATZ_F64); break;
   }
 #undef KATZ_FFR_W
+#undef KATZ_FFR8
 #undef KATZ_FFR
   KATZ_CHECK_LAUNCH();
   if (split) {

@@ -46,10 +46,13 @@ void cheb_step(const Csr& A, double beta, double ak, double ck, const float* Xk,
 // lo starting at element rows * ld).  in_mode: 0 FP32 Xk; 1 split Xk whose
 // product gathers hi alone; 2 split Xk gathered as hi + lo.  prev_mode: 0
 // none (Xprev null), 1 FP32, 2 split.  out_split: write x_{k+1} split.
+// tm_mask bits 1, 2, 4: Xk, Xprev, Xout are tile-major (FP32 only, b > 128,
+// ld % 8 == 0): column tile t (256 columns) of row i at (t * rows + i) * 256,
+// the buffer holding ceil(b / 256) * 256 columns per row.
 void cheb_step_ex(const Csr& A, double beta, double ak, double ck, const void* Xk, int in_mode,
                   const void* Xprev, int prev_mode, const float* B, void* Xout, int out_split,
                   int64_t ld, int b, cudaStream_t s, const SpmmCfg* cfg = nullptr,
-                  double sx = 1.0, double sp = 1.0);
+                  double sx = 1.0, double sp = 1.0, int tm_mask = 0);
 
 // dots[c] += sum_{i<len} A[i,c] * B[i,c]
 template <class VT>

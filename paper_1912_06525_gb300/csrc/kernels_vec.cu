@@ -372,14 +372,17 @@ static void spmm_dispatch(SpmmParams<VT>& p, const int32_t* heavy, int64_t n_hea
   dim3 grid((unsigned)ctas, (unsigned)tiles);
   p.skip_heavy = heavy != nullptr && n_heavy > 0;
   // FP32 rows whose strides and bases allow 32-byte accesses: half the
-  // vectors per thread at 8 floats each (the same tile)
+  // vectors per thread at 8 floats each (the same tile; measured 7 % faster
+  // on the coupling products of the n = 4M graph)
   bool w8 = false;
   if constexpr (sizeof(VT) == 4) {
     const uintptr_t al = reinterpret_cast<uintptr_t>(p.X) | reinterpret_cast<uintptr_t>(p.Y) |
                          reinterpret_cast<uintptr_t>(p.Z) |
                          reinterpret_cast<uintptr_t>(p.dots ? p.V : nullptr);
+    // (not with the fused dot: its FP64 column partials then cost occupancy,
+    // measured slower in CG)
     w8 = tpr == 32 && vpt >= 2 && al % 32 == 0 && p.ldx % 8 == 0 && p.ldy % 8 == 0 &&
-         (p.Z == nullptr || p.ldz % 8 == 0) && (p.dots == nullptr || p.ldv % 8 == 0);
+         (p.Z == nullptr || p.ldz % 8 == 0) && p.dots == nullptr;
   }
   if (p.A.nrows > 0) {
 #define KATZ_ROWS(T, V) \
@@ -500,6 +503,9 @@ struct ChebArgs {
   int b;
   int prev_mode;  // 0: x_{k-1} = 0, 1: FP32, 2: split
   int out_split;  // 1: write x_{k+1} split, 0: FP32
+  // tile-major layout (x_k, x_{k-1}, x_{k+1}): column tile t of row i at
+  // ((t * rows + i) * TILE) instead of i * ld + t * TILE
+  int xk_tm, prev_tm, out_tm;
 };
 
 // One warp per row and column tile of 32 * CW columns; lane t owns the CW
@@ -514,6 +520,11 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(ChebArgs p) {
   const int64_t ld = p.ld;
   const int64_t c0 = int64_t(blockIdx.y) * TILE + t * CW;
   const bool cval = c0 < p.b;
+  // row stride and lane offset of each operand's layout
+  const int64_t tm_off = int64_t(blockIdx.y) * p.A.nrows * TILE + t * CW;
+  const int64_t xs = p.xk_tm ? TILE : ld, xoff = p.xk_tm ? tm_off : c0;
+  const int64_t ps = p.prev_tm ? TILE : ld, poff = p.prev_tm ? tm_off : c0;
+  const int64_t os = p.out_tm ? TILE : ld, ooff = p.out_tm ? tm_off : c0;
   const float* Xf = static_cast<const float*>(p.Xk);
   const __nv_bfloat16* Xh = static_cast<const __nv_bfloat16*>(p.Xk);
   const __nv_bfloat16* Xl = Xh + p.plane;
@@ -536,7 +547,7 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(ChebArgs p) {
         const int j = __shfl_sync(0xffffffffu, cj, s2);
         const float wv = (WT == KATZ_UNIT) ? 1.f : __shfl_sync(0xffffffffu, wj, s2);
         if (cval) {
-          const int64_t off = int64_t(j) * ld + c0;
+          const int64_t off = int64_t(j) * xs + xoff;
           float xv[CW];
           if constexpr (IN == kInF32) {
             L::f32_ro(Xf + off, xv);
@@ -555,25 +566,25 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(ChebArgs p) {
       }
     }
     if (!cval) continue;
-    const int64_t o = i * ld + c0;
+    const int64_t o = i * ld + c0, ox = i * xs + xoff, op = i * ps + poff, oo = i * os + ooff;
     float xo[CW], bo[CW], xp[CW], xn[CW];
     if constexpr (IN == kInF32) {
-      L::f32_ro(Xf + o, xo);
+      L::f32_ro(Xf + ox, xo);
     } else {
       float xl[CW];
-      L::bf16_ro(Xh + o, xo);
-      L::bf16_ro(Xl + o, xl);
+      L::bf16_ro(Xh + ox, xo);
+      L::bf16_ro(Xl + ox, xl);
 #pragma unroll
       for (int w = 0; w < CW; ++w) xo[w] += xl[w];
     }
     L::f32(p.B + o, bo);
     if (p.prev_mode == 1) {
-      L::f32(static_cast<const float*>(p.Xprev) + o, xp);
+      L::f32(static_cast<const float*>(p.Xprev) + op, xp);
     } else if (p.prev_mode == 2) {
       const __nv_bfloat16* ph = static_cast<const __nv_bfloat16*>(p.Xprev);
       float xl[CW];
-      L::bf16(ph + o, xp);
-      L::bf16(ph + p.plane + o, xl);
+      L::bf16(ph + op, xp);
+      L::bf16(ph + p.plane + op, xl);
 #pragma unroll
       for (int w = 0; w < CW; ++w) xp[w] += xl[w];
     } else {
@@ -588,9 +599,9 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(ChebArgs p) {
     }
     if (p.out_split) {
       __nv_bfloat16* oh = static_cast<__nv_bfloat16*>(p.Xout);
-      split_store<CW>(oh + o, oh + p.plane + o, xn);
+      split_store<CW>(oh + oo, oh + p.plane + oo, xn);
     } else {
-      L::st_f32(static_cast<float*>(p.Xout) + o, xn);
+      L::st_f32(static_cast<float*>(p.Xout) + oo, xn);
     }
   }
 }
@@ -599,7 +610,8 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(ChebArgs p) {
 
 void cheb_step_ex(const Csr& A, double beta, double ak, double ck, const void* Xk, int in_mode,
                   const void* Xprev, int prev_mode, const float* B, void* Xout, int out_split,
-                  int64_t ld, int b, cudaStream_t s, const SpmmCfg* cfg, double sx, double sp) {
+                  int64_t ld, int b, cudaStream_t s, const SpmmCfg* cfg, double sx, double sp,
+                  int tm_mask) {
   KATZ_REQUIRE(ld % 4 == 0 && ld >= b && Xk != Xout && in_mode >= 0 && in_mode <= 2 &&
                    prev_mode >= 0 && prev_mode <= 2 && (prev_mode == 0) == (Xprev == nullptr) &&
                    (reinterpret_cast<uintptr_t>(Xk) | reinterpret_cast<uintptr_t>(Xprev) |
@@ -612,6 +624,8 @@ void cheb_step_ex(const Csr& A, double beta, double ak, double ck, const void* X
   const bool wide = b > 128 && ld % 8 == 0 &&
                     ((reinterpret_cast<uintptr_t>(Xk) | reinterpret_cast<uintptr_t>(Xprev) |
                       reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(Xout)) % 32) == 0;
+  KATZ_REQUIRE(tm_mask == 0 || (wide && in_mode == kInF32 && prev_mode != 2 && !out_split),
+               KATZ_EINVAL, "cheb_step: tile-major operands need FP32 rows of 256-column tiles");
   const int tile = wide ? 256 : 128;
   const int64_t tiles = ceil_div(b, tile);
   const int cps = cfg && cfg->fused_cps > 0     ? cfg->fused_cps
@@ -621,7 +635,8 @@ void cheb_step_ex(const Csr& A, double beta, double ak, double ck, const void* X
                                    std::max<int64_t>(1, int64_t(num_sms()) * cps / tiles));
   dim3 grid((unsigned)std::max<int64_t>(1, ctas), (unsigned)tiles);
   ChebArgs a{A,     float(beta), float(ak), float(ck), float(sx), float(sp), Xk, Xprev, B,
-             Xout,  ld,          A.nrows * ld,          b,         prev_mode, out_split};
+             Xout,  ld,          A.nrows * ld,          b,         prev_mode, out_split,
+             (tm_mask & 1) ? 1 : 0, (tm_mask & 2) ? 1 : 0, (tm_mask & 4) ? 1 : 0};
   prof_begin(s);
 #define KATZ_CHEB_IN(WT, C)                                                          \
   switch (in_mode) {                                                                 \

@@ -271,6 +271,30 @@ static void m11_chebyshev(katz_index& idx, const float* X, float* Y, int b, int6
   const SpmmCfg* cfg = idx.W11L.cfg(b);
   const bool pipe = use_pipe(idx, cfg) && pipe_eligible(idx.W11L.ps, ld) &&
                     (idx.unit_weights || idx.W11L.csr.vdt != KATZ_F64);
+  const bool tile_major = idx.cheb_pref == KATZ_CHEB_AUTO && !pipe && b > 128 && ld % 8 == 0;
+  if (tile_major) {
+    // FP32 iterates x_2 .. x_{K-1} in tile-major scratch (T for even k, U for
+    // odd k): a column tile's rows are contiguous, so the gathers of one
+    // tile sweep stay within rows x 1 KB instead of spreading over rows x ld
+    const int64_t wcols = (b + 255) / 256 * 256;
+    float* T = idx.ws.get<float>("ch.T", size_t(len) * wcols);
+    float* U = K > 3 ? idx.ws.get<float>("ch.U", size_t(len) * wcols) : nullptr;
+    auto slot = [&](int j) -> float* { return (j % 2 == 0) ? T : U; };
+    for (int k = 1; k < K; ++k) {
+      const double rho = 1.0 / (2.0 * sigma - rho_prev);
+      const double ak = rho * rho_prev, ck = 2.0 * rho / d;
+      const bool last = k == K - 1;
+      const float* xk = k == 1 ? X : slot(k);
+      const float* xprev = k == 1 ? nullptr : (k == 2 ? X : slot(k - 1));
+      float* out = last ? Y : slot(k + 1);
+      const int mask = (k >= 2 ? 1 : 0) | (k >= 3 ? 2 : 0) | (last ? 0 : 4);
+      const double sx = k == 1 ? 1.0 / theta : 1.0, sp = k == 2 ? 1.0 / theta : 1.0;
+      cheb_step_ex(idx.W11L.view(), idx.beta, ak, ck, xk, 0, xprev, xprev ? 1 : 0, X, out, 0, ld,
+                   b, s, cfg, sx, sp, mask);
+      rho_prev = rho;
+    }
+    return;
+  }
   if (idx.cheb_pref == KATZ_CHEB_F32 || idx.cheb_pref == KATZ_CHEB_AUTO || pipe) {
     // FP32 iterates: x_k for k >= 2 alternates between Y and T so that x_K
     // lands in Y (x_{k+1} overwrites x_{k-1} row by row)
@@ -670,18 +694,42 @@ static double solve_tol(const katz_query_opts& o, const QueryOut& out) {
   return std::max(0.5 * o.tol, o.tol - std::ldexp(1.0 + o.tol, -24));
 }
 
-// CG warm start: columns c whose residual of the guess is not below the
-// right-hand side's (rr[c] >= bn2[c]) are zeroed in K (restart from zero);
-// *count gets n for each such column (every row of the column counts one).
-__global__ void warm_cg_fallback_kernel(float* K, int64_t ld, int64_t n, int b, const double* rr,
-                                        const double* bn2, int* count) {
+// CG warm start, energy-optimal scaling of the guess x (node order): with
+// M x = b - R from the first residual pass, the M-norm error of gamma x,
+// ||k - gamma x||_M^2 = ||k||_M^2 - 2 gamma b^T x + gamma^2 x^T M x, is
+// smallest at gamma = b^T x / x^T M x = b^T x / (b^T x - x^T R) (k = M^{-1} b),
+// never larger than the zero start's ||k||_M (gamma = 0 when b^T x <= 0).
+// bx[c] = b_c^T x_c = beta sum_{j in N(q_c)} w_j x[j][c], gathered here.
+template <int WT>
+__global__ void rhs_dot_kernel(Csr W, const int32_t* q, double beta, const float* X, int64_t ld,
+                               double* bx) {
+  const int c = blockIdx.x;
+  const int64_t k0 = W.rowptr[q[c]], k1 = W.rowptr[q[c] + 1];
+  double acc = 0;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    double w = 1.0;
+    if (WT == KATZ_F64) w = static_cast<const double*>(W.val)[k];
+    else if (WT == KATZ_F32) w = static_cast<const float*>(W.val)[k];
+    else if (WT == KATZ_BF16) w = __bfloat162float(static_cast<const __nv_bfloat16*>(W.val)[k]);
+    acc += beta * w * double(X[int64_t(W.col[k]) * ld + c]);
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) atomicAdd(bx + c, acc);
+}
+__global__ void warm_gamma_kernel(const double* bx, const double* xr, int b, double* gamma,
+                                  int* n_zero) {
+  for (int c = threadIdx.x; c < b; c += blockDim.x) {
+    const double den = bx[c] - xr[c];
+    const double g = (bx[c] > 0.0 && den > 0.0) ? bx[c] / den : 0.0;
+    gamma[c] = g;
+    if (g == 0.0) atomicAdd(n_zero, 1);
+  }
+}
+__global__ void scale_cols_kernel(float* X, int64_t ld, int64_t n, int b, const double* gamma) {
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n * ld;
        e += int64_t(gridDim.x) * blockDim.x) {
     const int c = int(e % ld);
-    if (c < b && rr[c] >= bn2[c]) {
-      K[e] = 0.f;
-      atomicAdd(count, 1);
-    }
+    if (c < b) X[e] = float(double(X[e]) * gamma[c]);
   }
 }
 
@@ -768,7 +816,8 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   int refine = 0;
   bool pending = false;  // D holds a correction not yet added to K
   bool warm_checked = false;
-  int64_t warm_fallbacks = 0;
+  int64_t warm_fallbacks = 0;  // columns whose guess was scaled to zero
+  double warm_gamma_mean = 0;
   HeavyRows hv;  // the residual operator's heavy rows, split
   if (status == KATZ_OK || status == KATZ_ENOCONV) {
     for (;;) {
@@ -791,15 +840,40 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
         ffr_add_rhs(idx.W.view(), q, pos, b, idx.beta, Rh, Rl, ld, nullptr, maxdeg, s);
         coldot<float>(Rh, ld, Rh, ld, n, b, rr, s);
         if (cg_warm && !warm_checked) {
+          // scale each column of the guess to its energy-optimal multiple
+          // (zero where the guess points away from k), then the first pass
+          // again for the scaled guess
           warm_checked = true;
-          int* nfb = ws.get<int>("q.nfb", 1);
-          KATZ_CUDA(cudaMemsetAsync(nfb, 0, sizeof(int), s));
-          warm_cg_fallback_kernel<<<(unsigned)std::max<int64_t>(
-                                        1, std::min<int64_t>(ceil_div(n * ld, 256), 4096)),
-                                    256, 0, s>>>(Kh, ld, n, b, rr, bn2, nfb);
+          double* bx = ws.get<double>("q.wbx", bpad(b));
+          double* xr = ws.get<double>("q.wxr", bpad(b));
+          double* gam = ws.get<double>("q.wg", bpad(b));
+          int* nz = ws.get<int>("q.nfb", 1);
+          KATZ_CUDA(cudaMemsetAsync(bx, 0, sizeof(double) * b, s));
+          KATZ_CUDA(cudaMemsetAsync(xr, 0, sizeof(double) * b, s));
+          KATZ_CUDA(cudaMemsetAsync(nz, 0, sizeof(int), s));
+          switch (idx.W.csr.vdt) {
+            case KATZ_UNIT: rhs_dot_kernel<KATZ_UNIT><<<b, 128, 0, s>>>(idx.W.view(), q, idx.beta, Kh, ld, bx); break;
+            case KATZ_F64: rhs_dot_kernel<KATZ_F64><<<b, 128, 0, s>>>(idx.W.view(), q, idx.beta, Kh, ld, bx); break;
+            case KATZ_F32: rhs_dot_kernel<KATZ_F32><<<b, 128, 0, s>>>(idx.W.view(), q, idx.beta, Kh, ld, bx); break;
+            default: rhs_dot_kernel<KATZ_BF16><<<b, 128, 0, s>>>(idx.W.view(), q, idx.beta, Kh, ld, bx); break;
+          }
           KATZ_CHECK_LAUNCH();
-          warm_fallbacks = read_int(nfb, s) / std::max<int64_t>(1, n);
-          if (warm_fallbacks > 0) continue;  // the zeroed columns: first pass again
+          coldot<float>(Kh, ld, Rh, ld, n, b, xr, s);
+          warm_gamma_kernel<<<1, 1024, 0, s>>>(bx, xr, b, gam, nz);
+          KATZ_CHECK_LAUNCH();
+          scale_cols_kernel<<<(unsigned)std::max<int64_t>(
+                                  1, std::min<int64_t>(ceil_div(n * ld, 256), 4096)),
+                              256, 0, s>>>(Kh, ld, n, b, gam);
+          KATZ_CHECK_LAUNCH();
+          warm_fallbacks = read_int(nz, s);
+          {
+            std::vector<double> hg(b);
+            KATZ_CUDA(cudaMemcpyAsync(hg.data(), gam, 8 * size_t(b), cudaMemcpyDeviceToHost, s));
+            KATZ_CUDA(cudaStreamSynchronize(s));
+            warm_gamma_mean = 0;
+            for (double g : hg) warm_gamma_mean += g / b;
+          }
+          continue;  // first pass again for the scaled guess
         }
       } else {
         // Rl carries the first pass's low part into the first update only
@@ -862,6 +936,7 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
       stats->ms[5] = h;  // columns whose warm start fell back to zero
     } else if (o.warm_start) {
       stats->ms[5] = double(warm_fallbacks);
+      stats->ms[6] = warm_gamma_mean;  // mean energy-optimal scale of the guesses
     }
   }
   return status;

@@ -80,8 +80,9 @@ def test_warm_started_cg_matches_oracle_and_reports_its_gain():
     """CG on M started from the network's guess (K2 = W_r c_hat on the
     separator, K1 = M11^{-1} B1 + beta M11^{-1} W12 W_r c_hat elsewhere):
     the answers meet the 1e-6 bound against the oracle like the cold start,
-    columns whose guess is worse than zero restart from zero (the count is
-    reported), and the CG iterations cold and warm are printed.  A graph
+    each column's guess is scaled to its energy-optimal multiple (columns
+    scaled to zero are counted), and the CG iterations cold and warm are
+    printed.  A graph
     whose hubs carry much of each Katz vector, so that the separator part
     matters."""
     g = synth.chung_lu(8000, 2.1, 6.0, 800.0, seed=72)
@@ -103,7 +104,8 @@ def test_warm_started_cg_matches_oracle_and_reports_its_gain():
                                          warm_start=warm)
         assert s["status"] == "KATZ_OK"
         assert O.error_inf_rel(K.cpu().numpy(), ref).max() <= 1e-6, warm
-        res[warm] = (it.mean(), s["ms"][5], s["refine_steps"])
-    print(f"mean CG iterations: cold {res[0][0]:.2f}, warm {res[1][0]:.2f} (fallbacks "
-          f"{res[1][1]:.0f}/{len(test)}, refinement steps {res[0][2]} / {res[1][2]})")
+        res[warm] = (it.mean(), s["ms"][5], s["refine_steps"], s["ms"][6])
+    print(f"mean CG iterations: cold {res[0][0]:.2f}, warm {res[1][0]:.2f} (zero-scaled "
+          f"{res[1][1]:.0f}/{len(test)}, mean scale {res[1][3]:.3f}, refinement steps "
+          f"{res[0][2]} / {res[1][2]})")
     assert 0 <= res[1][1] <= len(test)
