@@ -345,11 +345,13 @@ int katz_apply_M(const katz_index* idx, const void* X, void* Y, int32_t b,
  * operator it also chooses between the register and the pipelined (TMA
  * bulk-copy) Chebyshev step, and on the full operators between the two
  * kernels of the first and of the later refinement-residual passes.
- * out (7 ints): out[0] = chosen column tile (0 = default), out[1] = CTAs
+ * out (8 ints): out[0] = chosen column tile (0 = default), out[1] = CTAs
  * per SM, out[2] = 1 if the pipelined Chebyshev step was chosen, out[3] /
  * out[4] = 1 if the pipelined kernel was chosen for the first / later
  * residual passes of LRC queries, out[5] / out[6] = CTAs per SM of the
- * Chebyshev step / of the residual pass (0 if not tuned); ms[0] = best
+ * Chebyshev step / of the residual pass (0 if not tuned), out[7] = rows
+ * the Chebyshev step gathers together per lane (0: the compiler's
+ * schedule, 4 or 8); ms[0] = best
  * time, ms[1] = time of the default shape (per product, FP32 vectors). */
 int katz_autotune(katz_index* idx, int32_t b, int32_t* out, double* ms, void* stream);
 
@@ -443,15 +445,18 @@ void katz_multi_free(katz_multi* m);
  * at once).  The graphs form one block-diagonal graph whose weights carry
  * each graph's damping (W~ = beta_g W_g on graph g's block, beta = 1), so
  * M = I - W~ and its Schur complement are block diagonal:
+ *   - rank target r_g per graph, log-scaled from opts->rank / 4 (smallest
+ *     graph) to opts->rank (largest; 0 = 32; at most 64);
  *   - separator: each graph's own highest-degree nodes (ties: smaller id),
- *     max(1, round(opts->n_hubs * n_g / sum n)) of them (opts->n_hubs = 0:
- *     min(8192, sum n / 1000), at least g); every other component is an
- *     M11 block (dense inverse, or Chebyshev if larger than block_max);
+ *     max(1, round(opts->n_hubs * n_g / sum n), 2 r_g) of them, at most 256
+ *     and n_g - 1 (opts->n_hubs = 0: min(8192, sum n / 1000), at least g);
+ *     every other component is an M11 block (dense inverse, or Chebyshev if
+ *     larger than block_max);
  *   - S_g for all graphs from one column-packed M11 solve (separator node l
- *     of every graph shares column l), stored as the block-diagonal S;
- *   - rank r_g per graph, log-scaled from opts->rank / 4 (smallest graph)
- *     to opts->rank (largest; 0 = 32), capped by the graph's separator:
- *     Lanczos on every graph's block at once with per-graph scalars.
+ *     of every graph shares column l); S_g, M22_g^{-1} and W^_g are stored
+ *     block by block (one dense block per graph, no union-wide array);
+ *   - rank r_g = min(target, separator): Lanczos on every graph's block at
+ *     once with per-graph scalars.
  * opts->value_dtype: KATZ_UNIT, KATZ_F32 or KATZ_BF16 (as katz_multi_build;
  * the index stores the scaled weights in FP32).  opts->split,
  * lanczos_steps, seed as for katz_index_build; n2_max is raised to the
@@ -482,10 +487,10 @@ int katz_multi_query(const katz_multi* m, const int32_t* q, int32_t qpg,
 /* katz_multi_query with the per-graph LRC solve (Algorithm 2 per graph, all
  * graphs in every launch) as the inner solver of the same float-float
  * residual refinement and per-(graph, query) stopping.  The inner PCG on
- * the block-diagonal S shares its scalars across a column's graphs (the
- * refinement decides each pair on its own residual).  Same arguments and
- * outputs; iters_out counts inner PCG iterations.  KATZ_EINVAL if m was not
- * built by katz_index_build_many. */
+ * the block-diagonal S keeps one set of CG coefficients per (graph, query)
+ * pair, each stopping on its own rows' residual.  Same arguments and
+ * outputs; iters_out counts each pair's inner PCG iterations.  KATZ_EINVAL
+ * if m was not built by katz_index_build_many. */
 int katz_multi_query_lrc(const katz_multi* m, const int32_t* q, int32_t qpg,
                          const katz_query_opts* opts, void* K_out, int32_t out_dtype, int64_t ldk,
                          katz_stats* stats, int32_t* iters_out, double* rel_res_out,

@@ -103,7 +103,8 @@ SpmmCfg tune_part(GraphPart& g, int b, Workspace& ws, cudaStream_t s, double* be
       return it->second;
     }
   }
-  const int64_t ld = (b + 3) / 4 * 4;
+  // the queries' leading dimension (multiple of 8 for batches above 128)
+  const int64_t ld = b > 128 ? (b + 7) / 8 * 8 : (b + 3) / 4 * 4;
   const int64_t rows = std::max(g.csr.nrows, g.csr.ncols);
   float* X = ws.get<float>("tune.X", size_t(rows) * ld);
   float* Y = ws.get<float>("tune.Y", size_t(rows) * ld);
@@ -149,6 +150,19 @@ SpmmCfg tune_part(GraphPart& g, int b, Workspace& ws, cudaStream_t s, double* be
         best.fused_cps = cps;
       }
     }
+    if (kind == Fused::cheb) {
+      // gathered rows loaded together per lane
+      for (int gd : {4, 8}) {
+        SpmmCfg c = best;
+        c.gather_depth = gd;
+        const double ms = time_launches(
+            [&] { cheb_step(g.view(), 0.01, 0.1, 1.0, X, X, X, Y, ld, b, s, &c); }, s, reps);
+        if (ms < bestf) {
+          bestf = ms;
+          best.gather_depth = gd;
+        }
+      }
+    }
     ws.release("tune.Z");
   }
   if (kind != Fused::none && pipe_eligible(g.ps, ld) && (unit || g.csr.vdt != KATZ_F64)) {
@@ -184,6 +198,7 @@ TuneResult autotune(katz_index& idx, int b, cudaStream_t s) {
       const SpmmCfg cc = tune_part(idx.W11L, b, idx.ws, s, &b2, &d2, Fused::cheb, idx.unit_weights);
       r.cheb_pipe = cc.pipe;
       r.cheb_cps = cc.fused_cps;
+      r.cheb_depth = cc.gather_depth;
     }
   } else {
     r.res_cps = c.fused_cps;

@@ -67,6 +67,24 @@ struct Partition {
 
 // Every field except `ws`, `gather_pref` and `cheb_pref` is stored by save_index
 // (index_io.cu): a field added here is added to its list too.
+// Block-diagonal Schur objects of an index over many disjoint graphs: the
+// separator rows of graph g are [gsep[g], gsep[g+1]) (graph-major, n2_g of
+// them); S_g, M22_g^{-1} (n2_g x n2_g, row-major) are packed at moff[g]
+// (the sum of the earlier n2_h^2) and W^_g = W_g D_g^{1/2} (n2_g x r_g,
+// row-major) at woff[g].  Products with them run one CTA per graph.
+struct SegBlocks {
+  int32_t G = 0;
+  int64_t nmat = 0, nw = 0;
+  std::vector<int64_t> gsep_h, moff_h, woff_h;
+  std::vector<int32_t> rk_h;
+  katz::DBuf<int64_t> gsep, moff, woff;
+  katz::DBuf<int32_t> rk, sg;  // rank of each graph; graph of each separator row
+  katz::DBuf<float> S32, Minv32, W32;
+  katz::DBuf<double> S64, Minv64, W64;
+};
+// Largest separator of one graph in a block-diagonal (many-graph) index.
+constexpr int64_t kSegBlockMax = 256;
+
 // Largest separator of a single-graph LRC index: M22 and M22^{-1} are kept
 // dense (n2 x n2 FP64 and FP32) even when S is applied implicitly.
 constexpr int64_t kDenseM22Max = 49152;
@@ -126,6 +144,11 @@ struct katz_index {
   // separators above n2_max: S is never formed; PCG applies
   // S P = M22 P - beta^2 W21 M11^{-1} (W12 P) (Lemma 1, Eqs. 4-7)
   bool s_implicit = false;
+  // many graphs: S, M22^{-1} and W^ kept block by block (seg_blocked), the
+  // Schur PCG with per-graph scalars; seg_iters[g * b + c] its iterations
+  bool seg_blocked = false;
+  SegBlocks sb;
+  std::vector<int32_t> seg_iters;
   katz::Mlp mlp;
   katz::DBuf<float> feat;  // n x 32 node features
   katz::DBuf<float> Hr;    // beta M11^{-1} W12 W_r (n1 x ldr4), for the CG warm start
@@ -180,6 +203,26 @@ struct SegSpec {
   std::vector<int64_t> hubs;
   std::vector<int> ranks;
 };
+
+// Block-diagonal Schur pieces of a many-graph index (seg_blocks.cu).
+// Scatter the packed T columns of column block [l0, l0 + cw) into the
+// per-graph T blocks (Tb, packed like S).
+void seg_scatter_T(const SegBlocks& sb, const double* E, int64_t ldc, int64_t n2, int l0, int cw,
+                   double* Tb, cudaStream_t s);
+// S_g = M22_g - T_g and M22_g^{-1} (in place, Gauss-Jordan on the SPD block)
+// for every graph; W22 is the union's separator block (local columns).
+// Returns false if a block is not positive definite.
+bool seg_build_blocks(SegBlocks& sb, const Csr& W22, double beta, const double* Tb,
+                      double* M22b, cudaStream_t s);
+// y_g = A_g x_g for FP64 block-diagonal A (packed at moff), strided x / y.
+void seg_block_mv64(const SegBlocks& sb, const double* A, const double* x, int64_t incx, double* y,
+                    int64_t incy, cudaStream_t s);
+// Schur PCG with per-graph scalars on S K2 = F (n2 x b, ld): every (graph,
+// column) pair has its own CG coefficients and stops when
+// ||F - S K2||_2 <= tol ||F||_2 on its rows.  iters_gc (G * b) receives the
+// iterations of each pair.
+int seg_pcg(katz_index& idx, const float* F, float* K2, int b, int64_t ld, double tol,
+            int max_iter, std::vector<int32_t>& iters_gc, cudaStream_t s);
 
 // Largest Ritz value of W after `steps` FP64 Lanczos steps on the GPU
 // (start: all-ones if seed == 0, else SplitMix64(seed)); *lmin (optional)
@@ -256,6 +299,7 @@ struct TuneResult {
   int col_tile = 0, ctas_per_sm = 0, rhs_width = 0;
   bool cheb_pipe = false;  // the pipelined Chebyshev step was faster on the large block
   bool res_first_pipe = false, res_pipe = false;  // ... residual passes (LRC operator)
+  int cheb_depth = 0;
   int cheb_cps = 0, res_cps = 0;  // CTAs per SM of the fused kernels
   double ms_best = 0, ms_default = 0;
 };

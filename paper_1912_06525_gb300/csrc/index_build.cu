@@ -593,6 +593,43 @@ static void store_basis(katz_index& idx, std::vector<double>& Wh, int rk, cudaSt
 // Krylov space fills the graph's separator.  Returns the basis (host, n2 x
 // sum r_g, graph g's columns at its offset, zero outside its rows) and sets
 // idx.sigma (graph-major).
+// The per-graph bases W_g (packed, n2_g x r_g each) scaled by
+// D_g^{1/2} = diag(sqrt(sigma / (1 - sigma))) into W^_g (Eq. 14).
+static void store_seg_basis(katz_index& idx, std::vector<double>& Wh, const std::vector<int>& rkg,
+                            cudaStream_t s) {
+  SegBlocks& sb = idx.sb;
+  const int G = sb.G;
+  sb.rk_h.assign(rkg.begin(), rkg.end());
+  sb.woff_h.assign(G + 1, 0);
+  for (int g = 0; g < G; ++g)
+    sb.woff_h[g + 1] = sb.woff_h[g] + (sb.gsep_h[g + 1] - sb.gsep_h[g]) * rkg[g];
+  sb.nw = sb.woff_h[G];
+  int so = 0;  // offset of graph g's Ritz values in idx.sigma
+  for (int g = 0; g < G; ++g) {
+    const int r = rkg[g];
+    KATZ_REQUIRE(r <= kSegBlockMax / 4, KATZ_EINVAL, "per-graph rank above 64");
+    const int64_t n = sb.gsep_h[g + 1] - sb.gsep_h[g];
+    for (int c = 0; c < r; ++c) {
+      const double sg = std::min(std::max(idx.sigma[so + c], 0.0), 1.0 - 1e-12);
+      const double f = std::sqrt(sg / (1.0 - sg));
+      for (int64_t i = 0; i < n; ++i) Wh[sb.woff_h[g] + i * r + c] *= f;
+    }
+    so += r;
+  }
+  idx.rank = so;
+  std::vector<float> Wf(Wh.begin(), Wh.end());
+  sb.W64.alloc(Wh.size());
+  sb.W32.alloc(Wf.size());
+  sb.woff.alloc(sb.woff_h.size());
+  sb.rk.alloc(std::max(G, 1));
+  KATZ_CUDA(cudaMemcpyAsync(sb.W64.p, Wh.data(), 8 * Wh.size(), cudaMemcpyHostToDevice, s));
+  KATZ_CUDA(cudaMemcpyAsync(sb.W32.p, Wf.data(), 4 * Wf.size(), cudaMemcpyHostToDevice, s));
+  KATZ_CUDA(cudaMemcpyAsync(sb.woff.p, sb.woff_h.data(), 8 * sb.woff_h.size(),
+                            cudaMemcpyHostToDevice, s));
+  KATZ_CUDA(cudaMemcpyAsync(sb.rk.p, sb.rk_h.data(), 4 * sb.rk_h.size(), cudaMemcpyHostToDevice, s));
+  KATZ_CUDA(cudaStreamSynchronize(s));
+}
+
 static std::vector<double> seg_lanczos(katz_index& idx, const SegSpec& seg,
                                        const std::vector<int64_t>& gsep_h, const int32_t* sg,
                                        const int64_t* gsep, const double* T, const double* M22,
@@ -629,8 +666,9 @@ static std::vector<double> seg_lanczos(katz_index& idx, const SegSpec& seg,
     KATZ_CUDA(cudaStreamSynchronize(s));
     return hd;
   };
+  const SegBlocks& sb = idx.sb;
   auto mdot = [&](const double* x) {  // per graph x^T M22 x
-    gemm<double>(false, n2, 1, n2, 1.0, M22, ld2, x, 1, 0.0, u.p, 1, s);
+    seg_block_mv64(sb, M22, x, 1, u.p, 1, s);
     return segdot(x, 1, u.p);
   };
   auto put = [&](int col) {
@@ -653,14 +691,14 @@ static std::vector<double> seg_lanczos(katz_index& idx, const SegSpec& seg,
     bool any = false;
     for (int g = 0; g < G; ++g) any |= active[g] != 0;
     if (!any) break;
-    // t = T q_j ; w = M22^{-1} t ; alpha = q_j^T t
-    gemm<double>(false, n2, 1, n2, 1.0, T, ld2, Q.p + j, ldq, 0.0, t.p, 1, s);
-    gemm<double>(false, n2, 1, n2, 1.0, idx.M22inv64.p, ld2, t.p, 1, 0.0, wv.p, 1, s);
+    // t = T q_j ; w = M22^{-1} t ; alpha = q_j^T t (block by block)
+    seg_block_mv64(sb, T, Q.p + j, ldq, t.p, 1, s);
+    seg_block_mv64(sb, sb.Minv64.p, t.p, 1, wv.p, 1, s);
     const std::vector<double> a = segdot(Q.p + j, ldq, t.p);
     for (int g = 0; g < G; ++g)
       if (active[g]) al[g].push_back(a[g]);
     for (int pass = 0; pass < 2; ++pass) {
-      gemm<double>(false, n2, 1, n2, 1.0, M22, ld2, wv.p, 1, 0.0, u.p, 1, s);
+      seg_block_mv64(sb, M22, wv.p, 1, u.p, 1, s);
       seg_coeff_kernel<<<G, 128, 0, s>>>(Q.p, ldq, u.p, gsep, j + 1, G, C.p);
       KATZ_CHECK_LAUNCH();
       seg_reorth_kernel<<<blocks_for(n2), 256, 0, s>>>(Q.p, ldq, C.p, j + 1, G, sg, n2, wv.p);
@@ -724,7 +762,11 @@ static std::vector<double> seg_lanczos(katz_index& idx, const SegSpec& seg,
   }
   const int rk_tot = off[G];
   *rk_out = rk_tot;
-  std::vector<double> Wh(size_t(n2) * rk_tot, 0.0);
+  // W_g (n2_g x r_g, row-major) packed graph after graph
+  int64_t nw = 0;
+  for (int g = 0; g < G; ++g) nw += (gsep_h[g + 1] - gsep_h[g]) * (*rk_graph)[g];
+  std::vector<double> Wh(size_t(std::max<int64_t>(nw, 1)), 0.0);
+  int64_t wo = 0;
   for (int g = 0; g < G; ++g) {
     const int rk = (*rk_graph)[g];
     const int k = (int)al[g].size();
@@ -732,8 +774,9 @@ static std::vector<double> seg_lanczos(katz_index& idx, const SegSpec& seg,
       for (int c = 0; c < rk; ++c) {
         double acc = 0.0;
         for (int i = 0; i < k; ++i) acc += Qh[size_t(p) * ldq + i] * Ysel[g][size_t(i) * rk + c];
-        Wh[size_t(p) * rk_tot + off[g] + c] = acc;
+        Wh[wo + (p - gsep_h[g]) * rk + c] = acc;
       }
+    wo += (gsep_h[g + 1] - gsep_h[g]) * rk;
   }
   idx.lanczos_steps = 0;
   for (int g = 0; g < G; ++g) idx.lanczos_steps = std::max(idx.lanczos_steps, (int)al[g].size());
@@ -817,6 +860,27 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
     KATZ_CUDA(cudaMemcpyAsync(sg_d.p, sgh.data(), 4 * sgh.size(), cudaMemcpyHostToDevice, s));
     KATZ_CUDA(cudaMemcpyAsync(gsep_d.p, gsep_h.data(), 8 * gsep_h.size(), cudaMemcpyHostToDevice,
                               s));
+    // block-by-block storage of S, M22^{-1} and W^ (one block per graph)
+    KATZ_REQUIRE(width <= kSegBlockMax, KATZ_EINVAL,
+                 "a graph's separator has " + std::to_string(width) + " nodes > " +
+                     std::to_string(kSegBlockMax));
+    SegBlocks& sb = idx.sb;
+    idx.seg_blocked = true;
+    sb.G = seg->G;
+    sb.gsep_h = gsep_h;
+    sb.moff_h.assign(seg->G + 1, 0);
+    for (int g = 0; g < seg->G; ++g) {
+      const int64_t ng = gsep_h[g + 1] - gsep_h[g];
+      sb.moff_h[g + 1] = sb.moff_h[g] + ng * ng;
+    }
+    sb.nmat = sb.moff_h[seg->G];
+    sb.gsep.alloc(gsep_h.size());
+    sb.moff.alloc(sb.moff_h.size());
+    sb.sg.alloc(sgh.size());
+    KATZ_CUDA(cudaMemcpyAsync(sb.gsep.p, gsep_h.data(), 8 * gsep_h.size(), cudaMemcpyHostToDevice, s));
+    KATZ_CUDA(cudaMemcpyAsync(sb.moff.p, sb.moff_h.data(), 8 * sb.moff_h.size(),
+                              cudaMemcpyHostToDevice, s));
+    KATZ_CUDA(cudaMemcpyAsync(sb.sg.p, sgh.data(), 4 * sgh.size(), cudaMemcpyHostToDevice, s));
   }
   std::vector<int32_t> iperm(n), perm32(n);
   for (int64_t i = 0; i < n; ++i) {
@@ -966,7 +1030,10 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   // --- T = M12^T M11^{-1} M12 = beta^2 W21 M11^{-1} W12 (FP64, by columns)
   const int64_t ld2 = (n2 + 3) / 4 * 4;
   idx.ld2 = ld2;
-  DBuf<double> T(idx.s_implicit ? size_t(1) : size_t(n2) * ld2);
+  // (many graphs: the per-graph blocks T_g, packed; else dense n2 x n2)
+  DBuf<double> T(idx.s_implicit ? size_t(1)
+                 : seg         ? size_t(std::max<int64_t>(idx.sb.nmat, 1))
+                               : size_t(n2) * ld2);
   KATZ_CUDA(cudaMemsetAsync(T.p, 0, T.bytes(), s));
   {
     const int cw_max = (int)std::min<int64_t>(256, (n2 + 1) / 2 * 2);
@@ -1007,9 +1074,7 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
       KATZ_REQUIRE(st != KATZ_ENOTSPD, KATZ_ENOTSPD, "M11 is not positive definite");
       spmm<double>(idx.W21.view(), idx.W21.heavy.p, idx.W21.n_heavy, beta, V.p, ldc, 0.0, nullptr,
                    ldc, E.p, ldc, cw, nullptr, 0, nullptr, s);
-      packed_scatter_kernel<<<blocks_for(n2 * cw), 256, 0, s>>>(E.p, ldc, T.p, ld2, n2, sg_d.p,
-                                                                gsep_d.p, (int)l0, cw);
-      KATZ_CHECK_LAUNCH();
+      seg_scatter_T(idx.sb, E.p, ldc, n2, (int)l0, cw, T.p, s);
     }
     for (int64_t j0 = 0; !seg && !idx.s_implicit && j0 < n2; j0 += cw_max) {
       const int cw = (int)std::min<int64_t>(cw_max, n2 - j0);
@@ -1027,6 +1092,24 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
       spmm<double>(idx.W21.view(), idx.W21.heavy.p, idx.W21.n_heavy, beta, V.p, ldc, 0.0, nullptr,
                    ldc, T.p + j0, ld2, cw, nullptr, 0, nullptr, s);
     }
+  }
+  if (seg) {
+    // --- per graph: M22_g, S_g = M22_g - T_g, M22_g^{-1}, then Lanczos on
+    // each graph's block at once
+    DBuf<double> M22b(size_t(std::max<int64_t>(idx.sb.nmat, 1)));
+    KATZ_REQUIRE(seg_build_blocks(idx.sb, W22d.view(), beta, T.p, M22b.p, s), KATZ_ENOTSPD,
+                 "a graph's M22 block is not positive definite");
+    idx.sigma.clear();
+    if (idx.rank > 0) {
+      int rk = 0;
+      std::vector<int> rkg;
+      std::vector<double> Wh = seg_lanczos(idx, *seg, gsep_h, sg_d.p, gsep_d.p, T.p, M22b.p, 0,
+                                           o.seed, o.lanczos_steps, &rk, &rkg, s);
+      idx.seg_rank = rkg;
+      if (rk > 0) store_seg_basis(idx, Wh, rkg, s);
+      else idx.rank = 0;
+    }
+    return;
   }
   // --- M22 (dense), S = M22 - T, M22^{-1}
   DBuf<double> M22(size_t(n2) * ld2);
@@ -1077,16 +1160,6 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
   // Ritz vector u of R, w = L^{-T} u directly (w^T M22 w = 1).  L itself is
   // never formed.  Full reorthogonalisation (two Gram-Schmidt passes).
   idx.sigma.clear();
-  if (seg && idx.rank > 0) {
-    int rk = 0;
-    std::vector<int> rkg;
-    std::vector<double> Wh = seg_lanczos(idx, *seg, gsep_h, sg_d.p, gsep_d.p, T.p, M22.p, ld2,
-                                         o.seed, o.lanczos_steps, &rk, &rkg, s);
-    idx.seg_rank = rkg;
-    if (rk > 0) store_basis(idx, Wh, rk, s);
-    else idx.rank = 0;
-    return;
-  }
   if (idx.rank > 0) {
     const int r = (int)std::min<int64_t>(idx.rank, n2);
     int m = o.lanczos_steps > 0 ? o.lanczos_steps : std::max(2 * r, r + 20);

@@ -197,18 +197,18 @@ void io_part(Archive& a, const std::string& p, GraphPart& g) {
   a.dbuf(p + ".ps.ctr", g.ps.ctr);
   a.scalar(p + ".ps.nblocks", g.ps.nblocks);
   // autotuned launch shapes: (b, warps, col_tile, ctas, pipe, pipe_first,
-  // fused_cps)
-  constexpr size_t kF = 7;
+  // fused_cps, gather_depth)
+  constexpr size_t kF = 8;
   std::vector<int32_t> t;
   if (a.saving())
     for (auto& kv : g.tuned) {
       const SpmmCfg& c = kv.second;
       t.insert(t.end(), {kv.first, c.warps_per_cta, c.col_tile, c.ctas_per_sm, int(c.pipe),
-                         int(c.pipe_first), c.fused_cps});
+                         int(c.pipe_first), c.fused_cps, c.gather_depth});
     }
-  a.vec(p + ".tuned7", t);
+  a.vec(p + ".tuned8", t);
   if (!a.saving()) {
-    KATZ_REQUIRE(t.size() % kF == 0, KATZ_EINVAL, "index file: " + p + ".tuned7");
+    KATZ_REQUIRE(t.size() % kF == 0, KATZ_EINVAL, "index file: " + p + ".tuned8");
     g.tuned.clear();
     for (size_t i = 0; i < t.size(); i += kF) {
       SpmmCfg c;
@@ -218,8 +218,10 @@ void io_part(Archive& a, const std::string& p, GraphPart& g) {
       c.pipe = t[i + 4] != 0;
       c.pipe_first = t[i + 5] != 0;
       c.fused_cps = t[i + 6];
+      c.gather_depth = t[i + 7];
       KATZ_REQUIRE(c.ctas_per_sm >= 0 && c.ctas_per_sm <= 1024 && c.fused_cps >= 0 &&
-                       c.fused_cps <= 1024 && c.col_tile >= 0 && c.col_tile <= 1024,
+                       c.fused_cps <= 1024 && c.col_tile >= 0 && c.col_tile <= 1024 &&
+                       (c.gather_depth == 0 || c.gather_depth == 4 || c.gather_depth == 8),
                    KATZ_EINVAL, "index file: launch shape out of range in " + p);
       g.tuned[t[i]] = c;
     }

@@ -22,6 +22,7 @@ struct SpmmCfg {
   bool pipe = false;       // the pipelined (TMA bulk-copy) kernel measured faster here
   bool pipe_first = false; // ... for the first refinement-residual pass
   int fused_cps = 0;       // CTAs per SM of the fused Chebyshev / residual kernel (0: ctas_per_sm)
+  int gather_depth = 0;    // fused Chebyshev step: gathered rows loaded together (0, 4 or 8)
 };
 
 // Y[i,:] = gamma * Z[i,:] + alpha * sum_k A[i,k] X[k,:]   for i < A.nrows.

@@ -510,7 +510,11 @@ struct ChebArgs {
 
 // One warp per row and column tile of 32 * CW columns; lane t owns the CW
 // consecutive columns tile0 + t*CW .. +CW-1 (one vector access each).
-template <int WT, int CW, int IN>
+// GD > 0: the row's entries are taken GD at a time, all GD gathered rows
+// loaded before any is summed (GD loads in flight per lane; entries past
+// the row's end load nothing and add zero); GD = 0: one entry at a time in
+// a loop unrolled by 4 (the compiler's schedule).
+template <int WT, int CW, int IN, int GD>
 __global__ void __launch_bounds__(256) cheb_step_kernel(ChebArgs p) {
   constexpr int TILE = 32 * CW;
   using L = Lane<CW>;
@@ -542,26 +546,58 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(ChebArgs p) {
         wj = load_weight<WT, float>(p.A.val, k);
       }
       const int cnt = (int)(k1 - kb < 32 ? k1 - kb : 32);
-#pragma unroll 4
-      for (int s2 = 0; s2 < cnt; ++s2) {
-        const int j = __shfl_sync(0xffffffffu, cj, s2);
-        const float wv = (WT == KATZ_UNIT) ? 1.f : __shfl_sync(0xffffffffu, wj, s2);
-        if (cval) {
-          const int64_t off = int64_t(j) * xs + xoff;
-          float xv[CW];
-          if constexpr (IN == kInF32) {
-            L::f32_ro(Xf + off, xv);
-          } else {
-            L::bf16_ro(Xh + off, xv);
-            if constexpr (IN == kInHiLo) {
-              float xl[CW];
-              L::bf16_ro(Xl + off, xl);
+      auto gather = [&](int j, float (&xv)[CW]) {
+        const int64_t off = int64_t(j) * xs + xoff;
+        if constexpr (IN == kInF32) {
+          L::f32_ro(Xf + off, xv);
+        } else {
+          L::bf16_ro(Xh + off, xv);
+          if constexpr (IN == kInHiLo) {
+            float xl[CW];
+            L::bf16_ro(Xl + off, xl);
 #pragma unroll
-              for (int w = 0; w < CW; ++w) xv[w] += xl[w];
-            }
+            for (int w = 0; w < CW; ++w) xv[w] += xl[w];
           }
+        }
+      };
+      if constexpr (GD == 0) {
+#pragma unroll 4
+        for (int s2 = 0; s2 < cnt; ++s2) {
+          const int j = __shfl_sync(0xffffffffu, cj, s2);
+          const float wv = (WT == KATZ_UNIT) ? 1.f : __shfl_sync(0xffffffffu, wj, s2);
+          if (cval) {
+            float xv[CW];
+            gather(j, xv);
 #pragma unroll
-          for (int w = 0; w < CW; ++w) acc[w] += wv * xv[w];
+            for (int w = 0; w < CW; ++w) acc[w] += wv * xv[w];
+          }
+        }
+      } else {
+        for (int s2 = 0; s2 < cnt; s2 += GD) {
+          int jj[GD];
+          float ww[GD];
+#pragma unroll
+          for (int u = 0; u < GD; ++u) {
+            jj[u] = __shfl_sync(0xffffffffu, cj, (s2 + u) & 31);
+            ww[u] = (WT == KATZ_UNIT) ? 1.f : __shfl_sync(0xffffffffu, wj, (s2 + u) & 31);
+            if (s2 + u >= cnt) ww[u] = 0.f;
+          }
+          if (cval) {
+            float xv[GD][CW];
+#pragma unroll
+            for (int u = 0; u < GD; ++u) {
+              if (s2 + u < cnt) {
+                gather(jj[u], xv[u]);
+              } else {
+#pragma unroll
+                for (int w = 0; w < CW; ++w) xv[u][w] = 0.f;
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < GD; ++u)
+#pragma unroll
+              for (int w = 0; w < CW; ++w) acc[w] += ww[u] * xv[u][w];
+          }
         }
       }
     }
@@ -638,11 +674,16 @@ void cheb_step_ex(const Csr& A, double beta, double ak, double ck, const void* X
              Xout,  ld,          A.nrows * ld,          b,         prev_mode, out_split,
              (tm_mask & 1) ? 1 : 0, (tm_mask & 2) ? 1 : 0, (tm_mask & 4) ? 1 : 0};
   prof_begin(s);
+  const int gd = cfg ? cfg->gather_depth : 0;
+#define KATZ_CHEB_GD(WT, C, I)                                                      \
+  if (gd == 8) cheb_step_kernel<WT, C, I, 8><<<grid, 256, 0, s>>>(a);              \
+  else if (gd == 4) cheb_step_kernel<WT, C, I, 4><<<grid, 256, 0, s>>>(a);         \
+  else cheb_step_kernel<WT, C, I, 0><<<grid, 256, 0, s>>>(a)
 #define KATZ_CHEB_IN(WT, C)                                                          \
   switch (in_mode) {                                                                 \
-    case kInF32: cheb_step_kernel<WT, C, kInF32><<<grid, 256, 0, s>>>(a); break;     \
-    case kInHi: cheb_step_kernel<WT, C, kInHi><<<grid, 256, 0, s>>>(a); break;       \
-    default: cheb_step_kernel<WT, C, kInHiLo><<<grid, 256, 0, s>>>(a); break;        \
+    case kInF32: KATZ_CHEB_GD(WT, C, kInF32); break;                                 \
+    case kInHi: KATZ_CHEB_GD(WT, C, kInHi); break;                                   \
+    default: KATZ_CHEB_GD(WT, C, kInHiLo); break;                                    \
   }
 #define KATZ_CHEB(WT)         \
   if (wide) {                 \
@@ -658,6 +699,7 @@ void cheb_step_ex(const Csr& A, double beta, double ak, double ck, const void* X
   }
 #undef KATZ_CHEB
 #undef KATZ_CHEB_IN
+#undef KATZ_CHEB_GD
   KATZ_CHECK_LAUNCH();
   if (profiling()) {
     // algorithmic: CSR once, x_k once (FP32 rows, or its hi and lo planes),

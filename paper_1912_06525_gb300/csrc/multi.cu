@@ -421,17 +421,24 @@ void multi_build_lrc(katz_multi& m, const std::vector<HostCsr>& Ws, const double
       seg.node_graph[off + i] = g;
     }
   }
-  // hubs: the largest degrees of each graph (ties: smaller id), a share of
-  // the separator budget in proportion to the graph's size, at least one
+  // hubs: the largest degrees of each graph (ties: smaller id): a share of
+  // the separator budget in proportion to the graph's size, and at least
+  // twice the graph's rank (the rank r_g is log-scaled with the graph's
+  // size from r/4 to r), at most kSegBlockMax (the block storage's limit)
   const int64_t budget =
       o.n_hubs > 0 ? o.n_hubs : std::max<int64_t>(G, std::min<int64_t>(8192, m.n / 1000));
   const int r_hi = o.rank > 0 ? o.rank : 32, r_lo = std::max(1, r_hi / 4);
+  KATZ_REQUIRE(r_hi <= kSegBlockMax / 4, KATZ_EINVAL, "per-graph rank must be <= 64");
   seg.ranks.resize(G);
   for (int g = 0; g < G; ++g) {
     const HostCsr& w = Ws[g];
     const int64_t ng = w.nrows;
+    const double t = n_max > n_min ? std::log(double(ng) / n_min) / std::log(double(n_max) / n_min)
+                                   : 1.0;
+    const int64_t r_target = std::llround(r_lo + (r_hi - r_lo) * t);
     int64_t h = std::max<int64_t>(1, (int64_t)std::llround(double(budget) * ng / double(m.n)));
-    h = std::min<int64_t>(h, std::max<int64_t>(0, ng - 1));
+    h = std::max<int64_t>(h, 2 * r_target);
+    h = std::min<int64_t>({h, kSegBlockMax, std::max<int64_t>(0, ng - 1)});
     std::vector<int64_t> ord(ng);
     std::iota(ord.begin(), ord.end(), 0);
     auto deg = [&](int64_t v) { return w.rowptr[v + 1] - w.rowptr[v]; };
@@ -439,9 +446,7 @@ void multi_build_lrc(katz_multi& m, const std::vector<HostCsr>& Ws, const double
       return deg(a) != deg(b) ? deg(a) > deg(b) : a < b;
     });
     for (int64_t i = 0; i < h; ++i) seg.hubs.push_back(m.seg_ptr_h[g] + ord[i]);
-    const double t = n_max > n_min ? std::log(double(ng) / n_min) / std::log(double(n_max) / n_min)
-                                   : 1.0;
-    seg.ranks[g] = (int)std::min<int64_t>(h, std::llround(r_lo + (r_hi - r_lo) * t));
+    seg.ranks[g] = (int)std::min<int64_t>(h, r_target);
   }
   katz_build_opts bo = o;
   bo.value_dtype = KATZ_F32;
@@ -634,8 +639,11 @@ int multi_query(katz_multi& m, const int32_t* q_dev, int qpg, const katz_query_o
     const int st = lrc_solve_f32(L, Rp, Dp, b, ld, tol_rel, max_iter, &lit, s);
     permute_rows_kernel<<<flat(m.n * ld), 256, 0, s>>>(Dp, Xn, L.iperm.p, m.n, ld, false);
     KATZ_CHECK_LAUNCH();
+    // per-(graph, query) PCG iterations of the block-diagonal solve
+    const bool per_graph = L.seg_blocked && (int64_t)L.seg_iters.size() == int64_t(m.g) * b;
     for (int g = 0; g < m.g; ++g)
-      for (int c = 0; c < b && c < (int)lit.size(); ++c) it_acc[size_t(g) * b + c] += lit[c];
+      for (int c = 0; c < b && c < (int)lit.size(); ++c)
+        it_acc[size_t(g) * b + c] += per_graph ? L.seg_iters[size_t(g) * b + c] : lit[c];
     return st;
   };
   double omc_min = 1.0;

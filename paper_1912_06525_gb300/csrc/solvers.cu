@@ -597,9 +597,24 @@ int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double t
                ld, b, nullptr, 0, nullptr, s, idx.W21.cfg(b));
     else
       KATZ_CUDA(cudaMemcpyAsync(F, R2, sizeof(VT) * n2 * ld, cudaMemcpyDeviceToDevice, s));
-    double* thr2 = idx.ws.get<double>("lrc.thrF", b);
-    rel_thresholds<VT>(F, ld, n2, b, tol_s, thr2, idx.ws, "lrcF", s);
-    merge(pcg_schur<VT>(idx, F, D2, b, ld, thr2, max_iter, iters, s, K2_0));
+    if (idx.seg_blocked) {
+      // many graphs: block-diagonal S with per-(graph, column) PCG scalars
+      if constexpr (sizeof(VT) == 4) {
+        merge(seg_pcg(idx, F, D2, b, ld, tol_s, max_iter, idx.seg_iters, s));
+        if (iters) {
+          iters->resize(b, 0);
+          for (int g = 0; g < idx.sb.G; ++g)
+            for (int c = 0; c < b; ++c)
+              (*iters)[c] = std::max((*iters)[c], idx.seg_iters[size_t(g) * b + c]);
+        }
+      } else {
+        throw Error(KATZ_EINVAL, "a many-graph index answers FP32 (mixed-precision) queries");
+      }
+    } else {
+      double* thr2 = idx.ws.get<double>("lrc.thrF", b);
+      rel_thresholds<VT>(F, ld, n2, b, tol_s, thr2, idx.ws, "lrcF", s);
+      merge(pcg_schur<VT>(idx, F, D2, b, ld, thr2, max_iter, iters, s, K2_0));
+    }
   }
   if (n1 > 0) {
     NvtxRange r("katz.backsolve");

@@ -55,8 +55,9 @@ def lrc_case():
 
 
 def test_multi_graph_lrc_matches_oracle(lrc_case):
-    """Per-graph LRC index (hubs of each graph, block-diagonal Schur
-    complement, per-graph ranks): every (graph, query) Katz vector matches
+    """Per-graph LRC index (hubs of each graph, the Schur complement,
+    M22^{-1} and the rank-r correction stored block by block, per-graph ranks,
+    per-(graph, query) PCG scalars): every (graph, query) Katz vector matches
     the FP64 oracle of that graph alone to 1e-6."""
     graphs, Ws, betas, m = lrc_case
     qpg = 8
@@ -75,7 +76,7 @@ def test_multi_graph_lrc_matches_oracle(lrc_case):
             assert O.error_inf_rel(Kh[off:off + g.n], ref).max() <= 1e-6, (fn.__name__, gi)
             off += g.n
         print(fn.__name__, "refinement steps", stats["refine_steps"], "mean inner iterations",
-              float(iters.mean()))
+              float(iters.mean()), "range", int(iters.min()), int(iters.max()))
 
 
 def test_multi_graph_lrc_ritz_values_match_oracle(lrc_case):
@@ -86,9 +87,13 @@ def test_multi_graph_lrc_ritz_values_match_oracle(lrc_case):
     graphs, Ws, betas, m = lrc_case
     n2, ranks, sig = katz.katz_multi_get_info(m)
     assert (n2 >= 1).all() and (ranks >= 1).all() and (ranks <= n2).all()
-    # ranks grow with the graph size (log-scaled from rank/4 to rank)
+    # ranks grow with the graph size (log-scaled from rank/4 to rank), each
+    # graph's separator holding at least twice its rank (block storage: the
+    # union's separator is not capped)
     order = np.argsort([g.n for g in graphs])
     assert ranks[order[0]] <= ranks[order[-1]]
+    assert ranks.min() >= 4 and ranks.max() == 16
+    assert (n2 >= np.minimum(2 * ranks, [g.n - 1 for g in graphs])).all()
     for gi in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
         g, W, beta = graphs[gi], Ws[gi], betas[gi]
         p = O.partition(g.n, g.rowptr, g.col, int(n2[gi]), 64, False)
