@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--paper-beta", action="store_true",
                     help="the paper's damping beta = 1 / (lambda_max + 1) instead of --c")
     ap.add_argument("--method", default="lrc", choices=["lrc", "cg"])
-    ap.add_argument("--gather", default="auto", choices=["auto", "register", "pipelined"],
+    ap.add_argument("--gather", default="auto", choices=["auto", "register", "pipelined", "rowpipe"],
                     help="kernel of the wide fused products (auto: the autotuner's choice)")
     ap.add_argument("--cheb", default="auto", choices=["auto", "f32", "bf16", "mixed"],
                     help="gathers of the large M11 block's Chebyshev steps: auto (the "
@@ -74,6 +74,13 @@ def parse():
                          "8 queries per graph, per-graph LRC index (ranks 8-32) against CG")
     ap.add_argument("--rank", type=int, default=0,
                     help="rank r of the low-rank correction (0: the workload's, 128 or 64)")
+    ap.add_argument("--weights", default="unit", choices=["unit", "dyadic"],
+                    help="dyadic: the workload's pattern with symmetric weights k/64 in "
+                         "[0.5, 2), stored and streamed as BF16 values")
+    ap.add_argument("--rank-sweep", default="", metavar="STANDIN",
+                    help="iterations and throughput against the rank r on a Table 1 stand-in: "
+                         "Schur PCG iterations of one FP32 solve at a fixed relative residual "
+                         "(1e-5), and mixed-precision queries/s at the 1e-6 bound")
     ap.add_argument("--sparse-katz", type=int, default=0, metavar="T",
                     help="also time Sparse-Katz (Algorithm 3) with T landmarks and s = 20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -650,6 +657,68 @@ def run_warm(args, world, rank, local):
                           "cg_cold": res["cg_cold"], "cg_warm": res["cg_warm"]}), flush=True)
 
 
+def run_rank_sweep(args, world, rank, local):
+    """Iterations and throughput against the rank r of the correction
+    (the analogue of the paper's Figs. 3-4) on a Table 1 stand-in, in the
+    paper's setting (beta = 1/(lambda_max + 1), top-1% hubs): for each r the
+    mean Schur PCG iterations of one FP32 solve stopped at relative residual
+    1e-5 (a fixed inner tolerance, so the count reflects the preconditioner),
+    plain CG's iterations at the same tolerance, the mixed-precision
+    queries/s at the 1e-6 bound, and the index's device bytes."""
+    import torch
+    import __graft_entry__
+    from paper_1912_06525_gb300 import katz, synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    g = synth.table1_standin(args.rank_sweep, args.scale)
+    q = synth.queries(g.n, min(1000, g.n), seed=synth.BASE_SEED + 55)
+    lam = katz.katz_lambda_max(g, steps=96)
+    beta = 1.0 / (lam + 1.0)
+    qd = torch.from_numpy(q).cuda()
+    K = torch.empty((g.n, len(q)), dtype=torch.float32, device="cuda")
+    rows, cg_it = [], None
+    for r in (0, 5, 10, 15, 20, 25, 50, 100):
+        idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_UNIT, rank=r,
+                                    n_hubs=g.n // 100, block_max=64, split=False)
+        katz.katz_autotune(idx, len(q))
+        st, it, _ = katz.katz_query_batch(idx, qd, K, tol=1e-5, tol_kind=katz.KATZ_TOL_RESIDUAL,
+                                          precision=katz.KATZ_PREC_F32)
+        if cg_it is None:
+            _, itc, _ = katz.cg_query_batch(idx, qd, K, tol=1e-5,
+                                            tol_kind=katz.KATZ_TOL_RESIDUAL,
+                                            precision=katz.KATZ_PREC_F32)
+            cg_it = float(np.mean(itc))
+        for _ in range(2):
+            katz.katz_query_batch(idx, qd, K, tol=1e-6)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream())
+        for _ in range(3):
+            stm, itm, _ = katz.katz_query_batch(idx, qd, K, tol=1e-6)
+        e1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        info = idx.info()
+        rows.append({"rank": info["rank"], "pcg_iters_fixed_tol": float(np.mean(it)),
+                     "queries_per_s": len(q) / (ms / 1000), "mixed_iters": float(np.mean(itm)),
+                     "refine_steps": stm["refine_steps"], "sigma_1": info["lambda_max_R"],
+                     "index_device_bytes": info["device_bytes"]})
+        del idx
+    if rank == 0:
+        n0, d0, l0 = synth.TABLE1[args.rank_sweep]
+        print(json.dumps({"metric": "Schur PCG iterations against the rank r (fixed inner "
+                                    "tolerance 1e-5)", "unit": "iterations",
+                          "value": rows[-1]["pcg_iters_fixed_tol"], "n_gpus": world,
+                          "higher_is_better": False, "data": "synthetic",
+                          "config": {"workload": f"stand-in for {args.rank_sweep} (n={g.n:,}, "
+                                                 f"nnz={g.nnz:,}, lambda_max={lam:.1f}), "
+                                                 f"beta=1/(lambda_max+1), top-1% hubs, "
+                                                 f"{len(q)} queries"},
+                          "cg_iters_fixed_tol": cg_it, "sweep": rows}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -658,6 +727,9 @@ def main():
         return
     if args.impl != "reference" and args.warm:
         run_warm(args, world, rank, local)
+        return
+    if args.impl != "reference" and args.rank_sweep:
+        run_rank_sweep(args, world, rank, local)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -681,6 +753,8 @@ def main():
     else:
         g, q, c, rank_r = synth.workload(args.workload, args.scale)
         c = args.c if args.c is not None else (0.9 if args.workload == 3 else 0.5)
+        if args.weights == "dyadic":
+            g = synth.with_dyadic_weights(g, synth.BASE_SEED + 9)
     if args.rank > 0:
         rank_r = args.rank
     if args.batch > 0:
@@ -714,7 +788,7 @@ def main():
     sc = torch.empty((b, 20), dtype=torch.float64, device=dev)
     qfn = katz.katz_query_batch if args.method == "lrc" else katz.cg_query_batch
     gk = {"auto": katz.KATZ_GATHER_AUTO, "register": katz.KATZ_GATHER_REGISTER,
-          "pipelined": katz.KATZ_GATHER_PIPELINED}[args.gather]
+          "pipelined": katz.KATZ_GATHER_PIPELINED, "rowpipe": katz.KATZ_GATHER_ROWPIPE}[args.gather]
     last = {}
 
     cg_mode = {"auto": katz.KATZ_CHEB_AUTO, "f32": katz.KATZ_CHEB_F32,

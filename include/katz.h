@@ -67,6 +67,10 @@ extern "C" {
 #define KATZ_GATHER_AUTO 0
 #define KATZ_GATHER_REGISTER 1
 #define KATZ_GATHER_PIPELINED 2
+#define KATZ_GATHER_ROWPIPE 3 /* the row-pipelined register kernel for the Chebyshev steps
+                                 (FP32 iterates, b > 128; each warp fetches the next row's
+                                 indices and this row's own operands during this row's
+                                 gathers), the register kernel elsewhere */
 
 /* Gathers of the Chebyshev steps on the large M11 blocks (KATZ_PREC_MIXED
  * and F32 paths).  F32: FP32 iterates and FP32 gathers.  The other modes
@@ -345,13 +349,15 @@ int katz_apply_M(const katz_index* idx, const void* X, void* Y, int32_t b,
  * operator it also chooses between the register and the pipelined (TMA
  * bulk-copy) Chebyshev step, and on the full operators between the two
  * kernels of the first and of the later refinement-residual passes.
- * out (8 ints): out[0] = chosen column tile (0 = default), out[1] = CTAs
+ * out (9 ints): out[0] = chosen column tile (0 = default), out[1] = CTAs
  * per SM, out[2] = 1 if the pipelined Chebyshev step was chosen, out[3] /
  * out[4] = 1 if the pipelined kernel was chosen for the first / later
  * residual passes of LRC queries, out[5] / out[6] = CTAs per SM of the
  * Chebyshev step / of the residual pass (0 if not tuned), out[7] = rows
  * the Chebyshev step gathers together per lane (0: the compiler's
- * schedule, 4 or 8); ms[0] = best
+ * schedule, 4 or 8), out[8] = 1 if the row-pipelined Chebyshev kernel (the
+ * next row's indices and this row's own operands fetched during this
+ * row's gathers) was chosen; ms[0] = best
  * time, ms[1] = time of the default shape (per product, FP32 vectors). */
 int katz_autotune(katz_index* idx, int32_t b, int32_t* out, double* ms, void* stream);
 

@@ -151,7 +151,7 @@ SpmmCfg tune_part(GraphPart& g, int b, Workspace& ws, cudaStream_t s, double* be
       }
     }
     if (kind == Fused::cheb) {
-      // gathered rows loaded together per lane
+      // gathered rows loaded together per lane, and the row-pipelined kernel
       for (int gd : {4, 8}) {
         SpmmCfg c = best;
         c.gather_depth = gd;
@@ -160,6 +160,16 @@ SpmmCfg tune_part(GraphPart& g, int b, Workspace& ws, cudaStream_t s, double* be
         if (ms < bestf) {
           bestf = ms;
           best.gather_depth = gd;
+        }
+      }
+      {
+        SpmmCfg c = best;
+        c.row_pipeline = true;
+        const double ms = time_launches(
+            [&] { cheb_step(g.view(), 0.01, 0.1, 1.0, X, X, X, Y, ld, b, s, &c); }, s, reps);
+        if (ms < bestf) {
+          bestf = ms;
+          best.row_pipeline = true;
         }
       }
     }
@@ -199,6 +209,7 @@ TuneResult autotune(katz_index& idx, int b, cudaStream_t s) {
       r.cheb_pipe = cc.pipe;
       r.cheb_cps = cc.fused_cps;
       r.cheb_depth = cc.gather_depth;
+      r.cheb_rowpipe = cc.row_pipeline;
     }
   } else {
     r.res_cps = c.fused_cps;

@@ -300,6 +300,7 @@ struct TuneResult {
   bool cheb_pipe = false;  // the pipelined Chebyshev step was faster on the large block
   bool res_first_pipe = false, res_pipe = false;  // ... residual passes (LRC operator)
   int cheb_depth = 0;
+  bool cheb_rowpipe = false;  // the row-pipelined Chebyshev kernel was faster
   int cheb_cps = 0, res_cps = 0;  // CTAs per SM of the fused kernels
   double ms_best = 0, ms_default = 0;
 };

@@ -197,18 +197,18 @@ void io_part(Archive& a, const std::string& p, GraphPart& g) {
   a.dbuf(p + ".ps.ctr", g.ps.ctr);
   a.scalar(p + ".ps.nblocks", g.ps.nblocks);
   // autotuned launch shapes: (b, warps, col_tile, ctas, pipe, pipe_first,
-  // fused_cps, gather_depth)
-  constexpr size_t kF = 8;
+  // fused_cps, gather_depth, row_pipeline)
+  constexpr size_t kF = 9;
   std::vector<int32_t> t;
   if (a.saving())
     for (auto& kv : g.tuned) {
       const SpmmCfg& c = kv.second;
       t.insert(t.end(), {kv.first, c.warps_per_cta, c.col_tile, c.ctas_per_sm, int(c.pipe),
-                         int(c.pipe_first), c.fused_cps, c.gather_depth});
+                         int(c.pipe_first), c.fused_cps, c.gather_depth, int(c.row_pipeline)});
     }
-  a.vec(p + ".tuned8", t);
+  a.vec(p + ".tuned9", t);
   if (!a.saving()) {
-    KATZ_REQUIRE(t.size() % kF == 0, KATZ_EINVAL, "index file: " + p + ".tuned8");
+    KATZ_REQUIRE(t.size() % kF == 0, KATZ_EINVAL, "index file: " + p + ".tuned9");
     g.tuned.clear();
     for (size_t i = 0; i < t.size(); i += kF) {
       SpmmCfg c;
@@ -219,6 +219,7 @@ void io_part(Archive& a, const std::string& p, GraphPart& g) {
       c.pipe_first = t[i + 5] != 0;
       c.fused_cps = t[i + 6];
       c.gather_depth = t[i + 7];
+      c.row_pipeline = t[i + 8] != 0;
       KATZ_REQUIRE(c.ctas_per_sm >= 0 && c.ctas_per_sm <= 1024 && c.fused_cps >= 0 &&
                        c.fused_cps <= 1024 && c.col_tile >= 0 && c.col_tile <= 1024 &&
                        (c.gather_depth == 0 || c.gather_depth == 4 || c.gather_depth == 8),

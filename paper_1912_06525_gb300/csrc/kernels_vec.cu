@@ -642,6 +642,132 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(ChebArgs p) {
   }
 }
 
+// Row-pipelined FP32 step (256-column tiles, 8 columns per lane): each
+// warp overlaps the serial chain of a row (its bounds, its column indices,
+// its gathers, its own operands) with the next row's: at the start of row
+// i the operands of the epilogue (b, x_k and x_{k-1} of row i) are copied
+// asynchronously into the warp's shared memory (cp.async, no registers
+// held), the next row's bounds are loaded, the gathers run, the next row's
+// first 32 column indices are loaded, and only then does the warp wait for
+// the copies and finish row i.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
+template <int WT>
+__global__ void __launch_bounds__(256) cheb_rows_pipe_kernel(ChebArgs p) {
+  constexpr int CW = 8, TILE = 256;
+  using L = Lane<CW>;
+  __shared__ __align__(16) float stage[8][3][TILE];  // per warp: b, x_k, x_{k-1} of its row
+  const int t = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int64_t ld = p.ld;
+  const int64_t c0 = int64_t(blockIdx.y) * TILE + t * CW;
+  const bool cval = c0 < p.b;
+  const int64_t tm_off = int64_t(blockIdx.y) * p.A.nrows * TILE + t * CW;
+  const int64_t xs = p.xk_tm ? TILE : ld, xoff = p.xk_tm ? tm_off : c0;
+  const int64_t ps = p.prev_tm ? TILE : ld, poff = p.prev_tm ? tm_off : c0;
+  const int64_t os = p.out_tm ? TILE : ld, ooff = p.out_tm ? tm_off : c0;
+  const float* Xf = static_cast<const float*>(p.Xk);
+  const float* Xp = static_cast<const float*>(p.Xprev);
+  float* sb = stage[wib][0] + t * CW;
+  float* sx = stage[wib][1] + t * CW;
+  float* sp = stage[wib][2] + t * CW;
+  int64_t i = warp;
+  if (i >= p.A.nrows) return;
+  int64_t k0 = p.A.rowptr[i], k1 = p.A.rowptr[i + 1];
+  int cj = 0;
+  float wj = 0.f;
+  if (k0 + t < k1) {
+    cj = p.A.col[k0 + t];
+    wj = load_weight<WT, float>(p.A.val, k0 + t);
+  }
+  for (;;) {
+    // 1. this row's epilogue operands, asynchronously
+    if (cval) {
+      const int64_t o = i * ld + c0, ox = i * xs + xoff, op = i * ps + poff;
+      cp_async16(sb, p.B + o);
+      cp_async16(sb + 4, p.B + o + 4);
+      cp_async16(sx, Xf + ox);
+      cp_async16(sx + 4, Xf + ox + 4);
+      if (p.prev_mode == 1) {
+        cp_async16(sp, Xp + op);
+        cp_async16(sp + 4, Xp + op + 4);
+      }
+    }
+    // 2. the next row's bounds
+    const int64_t inext = i + nwarps;
+    const bool more = inext < p.A.nrows;
+    int64_t n0 = 0, n1 = 0;
+    if (more) {
+      n0 = p.A.rowptr[inext];
+      n1 = p.A.rowptr[inext + 1];
+    }
+    // 3. gathers of this row (first 32 indices already in registers)
+    float acc[CW];
+#pragma unroll
+    for (int w = 0; w < CW; ++w) acc[w] = 0.f;
+    for (int64_t kb = k0; kb < k1; kb += 32) {
+      if (kb > k0) {
+        const int64_t k = kb + t;
+        cj = 0;
+        wj = 0.f;
+        if (k < k1) {
+          cj = p.A.col[k];
+          wj = load_weight<WT, float>(p.A.val, k);
+        }
+      }
+      const int cnt = (int)(k1 - kb < 32 ? k1 - kb : 32);
+#pragma unroll 4
+      for (int s2 = 0; s2 < cnt; ++s2) {
+        const int j = __shfl_sync(0xffffffffu, cj, s2);
+        const float wv = (WT == KATZ_UNIT) ? 1.f : __shfl_sync(0xffffffffu, wj, s2);
+        if (cval) {
+          float xv[CW];
+          L::f32_ro(Xf + int64_t(j) * xs + xoff, xv);
+#pragma unroll
+          for (int w = 0; w < CW; ++w) acc[w] += wv * xv[w];
+        }
+      }
+    }
+    // 4. the next row's first column indices
+    int ncj = 0;
+    float nwj = 0.f;
+    if (more && n0 + t < n1) {
+      ncj = p.A.col[n0 + t];
+      nwj = load_weight<WT, float>(p.A.val, n0 + t);
+    }
+    // 5. this row's epilogue
+    cp_async_wait_all();
+    __syncwarp();
+    if (cval) {
+      float xn[CW];
+#pragma unroll
+      for (int w = 0; w < CW; ++w) {
+        const float xsv = p.sx * sx[w];
+        const float xpv = p.prev_mode == 1 ? sp[w] : 0.f;
+        const float r = sb[w] - xsv + p.beta * (p.sx * acc[w]);
+        xn[w] = xsv + p.ak * (xsv - p.sp * xpv) + p.ck * r;
+      }
+      L::st_f32(static_cast<float*>(p.Xout) + i * os + ooff, xn);
+    }
+    __syncwarp();  // the stage is refilled by the next row
+    if (!more) break;
+    i = inext;
+    k0 = n0;
+    k1 = n1;
+    cj = ncj;
+    wj = nwj;
+  }
+}
+
 }  // namespace
 
 void cheb_step_ex(const Csr& A, double beta, double ak, double ck, const void* Xk, int in_mode,
@@ -675,6 +801,8 @@ void cheb_step_ex(const Csr& A, double beta, double ak, double ck, const void* X
              (tm_mask & 1) ? 1 : 0, (tm_mask & 2) ? 1 : 0, (tm_mask & 4) ? 1 : 0};
   prof_begin(s);
   const int gd = cfg ? cfg->gather_depth : 0;
+  const bool row_pipe = cfg && cfg->row_pipeline && wide && in_mode == kInF32 && prev_mode != 2 &&
+                        !out_split;
 #define KATZ_CHEB_GD(WT, C, I)                                                      \
   if (gd == 8) cheb_step_kernel<WT, C, I, 8><<<grid, 256, 0, s>>>(a);              \
   else if (gd == 4) cheb_step_kernel<WT, C, I, 4><<<grid, 256, 0, s>>>(a);         \
@@ -691,11 +819,20 @@ void cheb_step_ex(const Csr& A, double beta, double ak, double ck, const void* X
   } else {                    \
     KATZ_CHEB_IN(WT, 4)       \
   }
-  switch (A.vdt) {
-    case KATZ_UNIT: KATZ_CHEB(KATZ_UNIT); break;
-    case KATZ_F32: KATZ_CHEB(KATZ_F32); break;
-    case KATZ_BF16: KATZ_CHEB(KATZ_BF16); break;
-    default: KATZ_CHEB(KATZ_F64); break;
+  if (row_pipe) {
+    switch (A.vdt) {
+      case KATZ_UNIT: cheb_rows_pipe_kernel<KATZ_UNIT><<<grid, 256, 0, s>>>(a); break;
+      case KATZ_F32: cheb_rows_pipe_kernel<KATZ_F32><<<grid, 256, 0, s>>>(a); break;
+      case KATZ_BF16: cheb_rows_pipe_kernel<KATZ_BF16><<<grid, 256, 0, s>>>(a); break;
+      default: cheb_rows_pipe_kernel<KATZ_F64><<<grid, 256, 0, s>>>(a); break;
+    }
+  } else {
+    switch (A.vdt) {
+      case KATZ_UNIT: KATZ_CHEB(KATZ_UNIT); break;
+      case KATZ_F32: KATZ_CHEB(KATZ_F32); break;
+      case KATZ_BF16: KATZ_CHEB(KATZ_BF16); break;
+      default: KATZ_CHEB(KATZ_F64); break;
+    }
   }
 #undef KATZ_CHEB
 #undef KATZ_CHEB_IN

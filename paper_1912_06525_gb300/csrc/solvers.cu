@@ -229,7 +229,8 @@ const double* inv_of<double>(const BlockClass& c) { return c.inv64.p; }
 // the first refinement-residual pass.
 static bool use_pipe(const katz_index& idx, const SpmmCfg* cfg, bool first = false) {
   if (idx.gather_pref == KATZ_GATHER_PIPELINED) return true;
-  if (idx.gather_pref == KATZ_GATHER_REGISTER) return false;
+  if (idx.gather_pref == KATZ_GATHER_REGISTER || idx.gather_pref == KATZ_GATHER_ROWPIPE)
+    return false;
   return cfg && (first ? cfg->pipe_first : cfg->pipe);
 }
 
@@ -269,6 +270,16 @@ static void m11_chebyshev(katz_index& idx, const float* X, float* Y, int b, int6
   const double sigma = theta / d;
   double rho_prev = d / theta;  // rho_0 = 1/sigma
   const SpmmCfg* cfg = idx.W11L.cfg(b);
+  SpmmCfg forced;  // the query asked for the row-pipelined kernel
+  if (idx.gather_pref == KATZ_GATHER_ROWPIPE) {
+    forced = cfg ? *cfg : SpmmCfg{};
+    forced.row_pipeline = true;
+    cfg = &forced;
+  } else if (idx.gather_pref == KATZ_GATHER_REGISTER && cfg && cfg->row_pipeline) {
+    forced = *cfg;
+    forced.row_pipeline = false;
+    cfg = &forced;
+  }
   const bool pipe = use_pipe(idx, cfg) && pipe_eligible(idx.W11L.ps, ld) &&
                     (idx.unit_weights || idx.W11L.csr.vdt != KATZ_F64);
   const bool tile_major = idx.cheb_pref == KATZ_CHEB_AUTO && !pipe && b > 128 && ld % 8 == 0;
@@ -1076,7 +1087,7 @@ int run_queries(katz_index& idx, bool use_lrc, const int32_t* q_dev, const int32
   KATZ_REQUIRE(b > 0 && b <= 1024, KATZ_EINVAL, "b must be in [1, 1024]");
   // FP64-valued graphs keep the FP64 residual (their weights need not be
   // exact in FP32); the others use the float-float residual
-  KATZ_REQUIRE(o.gather_kernel >= KATZ_GATHER_AUTO && o.gather_kernel <= KATZ_GATHER_PIPELINED,
+  KATZ_REQUIRE(o.gather_kernel >= KATZ_GATHER_AUTO && o.gather_kernel <= KATZ_GATHER_ROWPIPE,
                KATZ_EINVAL, "gather_kernel must be a KATZ_GATHER_* value");
   idx.gather_pref = o.gather_kernel;
   KATZ_REQUIRE(o.cheb_gather >= KATZ_CHEB_AUTO && o.cheb_gather <= KATZ_CHEB_MIXED, KATZ_EINVAL,

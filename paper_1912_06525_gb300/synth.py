@@ -100,6 +100,22 @@ def dyadic_weights(seed: int):
     return fn
 
 
+def with_dyadic_weights(g: Graph, seed: int) -> Graph:
+    """The same pattern with symmetric weights k/64 in [0.5, 2) (exact in
+    BF16): each undirected edge's weight is a hash of (min, max, seed), so
+    both stored directions carry the same value."""
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.rowptr))
+    cols = g.col.astype(np.int64)
+    lo, hi = np.minimum(rows, cols), np.maximum(rows, cols)
+    z = (lo * 0x9E3779B1 + hi * 0x85EBCA77 + seed * 0xC2B2AE3D) & 0xFFFFFFFF
+    z ^= z >> 15
+    z = (z * 0x2C1B3C6D) & 0xFFFFFFFF
+    z ^= z >> 12
+    w = (32 + (z % 96)) / 64.0
+    return Graph(n=g.n, rowptr=g.rowptr, col=g.col, val=w.astype(np.float64),
+                 meta=dict(g.meta, weights="dyadic"))
+
+
 # ----------------------------------------------------------------- tiny graphs
 def single_edge() -> Graph:
     return edges_to_graph(2, np.array([0]), np.array([1]), {"kind": "single_edge"})

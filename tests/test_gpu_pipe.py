@@ -64,7 +64,8 @@ def test_pipelined_paths_match_oracle(vdt, b):
 @pytest.mark.parametrize("vdt", [katz.KATZ_UNIT, katz.KATZ_BF16])
 @pytest.mark.parametrize("b", [5, 333, 1024])
 def test_chebyshev_gather_precisions_match_oracle(vdt, b):
-    """The large M11 block's Chebyshev steps with FP32 iterates (AUTO, F32),
+    """The large M11 block's Chebyshev steps with FP32 iterates (AUTO, F32;
+    the register kernel and the row-pipelined one),
     with split BF16 iterates gathered as hi + lo on a solve's last step
     (MIXED), and with hi-plane gathers on every step (BF16): the refined
     answers all meet the 1e-6 bound; 128-column tiles of 16-byte lane
@@ -79,12 +80,15 @@ def test_chebyshev_gather_precisions_match_oracle(vdt, b):
     q = synth.queries(g.n, b, seed=b + 1)
     q[0] = 3000
     ref = O.katz_direct(W, beta, q)
-    for mode in (katz.KATZ_CHEB_AUTO, katz.KATZ_CHEB_F32, katz.KATZ_CHEB_BF16,
-                 katz.KATZ_CHEB_MIXED):
+    for mode, kern in ((katz.KATZ_CHEB_AUTO, katz.KATZ_GATHER_REGISTER),
+                       (katz.KATZ_CHEB_F32, katz.KATZ_GATHER_REGISTER),
+                       (katz.KATZ_CHEB_BF16, katz.KATZ_GATHER_REGISTER),
+                       (katz.KATZ_CHEB_MIXED, katz.KATZ_GATHER_REGISTER),
+                       (katz.KATZ_CHEB_AUTO, katz.KATZ_GATHER_ROWPIPE),
+                       (katz.KATZ_CHEB_F32, katz.KATZ_GATHER_ROWPIPE)):
         K = torch.zeros((g.n, b), dtype=torch.float32, device="cuda")
         st, it, rel = katz.katz_query_batch(idx, torch.from_numpy(q).cuda(), K, tol=1e-6,
-                                            gather_kernel=katz.KATZ_GATHER_REGISTER,
-                                            cheb_gather=mode)
+                                            gather_kernel=kern, cheb_gather=mode)
         assert st["status"] == "KATZ_OK", (mode, st)
         err = O.error_inf_rel(K.double().cpu().numpy(), ref)
         assert err.max() <= 1e-6, (mode, err.max())
