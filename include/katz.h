@@ -494,7 +494,9 @@ int katz_multi_query(const katz_multi* m, const int32_t* q, int32_t qpg,
  * graphs in every launch) as the inner solver of the same float-float
  * residual refinement and per-(graph, query) stopping.  The inner PCG on
  * the block-diagonal S keeps one set of CG coefficients per (graph, query)
- * pair, each stopping on its own rows' residual.  Same arguments and
+ * pair, each stopping on its own rows' residual; its iterations are
+ * captured once into a CUDA graph and replayed (stats->ms[4] counts the
+ * replays of both inner solvers).  Same arguments and
  * outputs; iters_out counts each pair's inner PCG iterations.  KATZ_EINVAL
  * if m was not built by katz_index_build_many. */
 int katz_multi_query_lrc(const katz_multi* m, const int32_t* q, int32_t qpg,

@@ -149,6 +149,7 @@ struct katz_index {
   bool seg_blocked = false;
   SegBlocks sb;
   std::vector<int32_t> seg_iters;
+  int64_t seg_replays = 0;  // CUDA-graph replays of the many-graph Schur PCG
   katz::Mlp mlp;
   katz::DBuf<float> feat;  // n x 32 node features
   katz::DBuf<float> Hr;    // beta M11^{-1} W12 W_r (n1 x ldr4), for the CG warm start

@@ -636,7 +636,9 @@ int multi_query(katz_multi& m, const int32_t* q_dev, int qpg, const katz_query_o
     permute_rows_kernel<<<flat(m.n * ld), 256, 0, s>>>(Rn, Rp, L.iperm.p, m.n, ld, true);
     KATZ_CHECK_LAUNCH();
     lit.assign(b, 0);
+    const int64_t rep0 = L.seg_replays;
     const int st = lrc_solve_f32(L, Rp, Dp, b, ld, tol_rel, max_iter, &lit, s);
+    replays += int(L.seg_replays - rep0);
     permute_rows_kernel<<<flat(m.n * ld), 256, 0, s>>>(Dp, Xn, L.iperm.p, m.n, ld, false);
     KATZ_CHECK_LAUNCH();
     // per-(graph, query) PCG iterations of the block-diagonal solve

@@ -354,26 +354,72 @@ int seg_pcg(katz_index& idx, const float* F, float* K2, int b, int64_t ld, doubl
     return h;
   };
   int open = open_pairs();
-  for (int iter = 0; iter < max_iter && open > 0; ++iter) {
-    block_mm32_kernel<<<sb.G, 256, 0, s>>>(sb.S32.p, sb.gsep.p, sb.moff.p, P, ld, b, 1.f, 0.f, Q);
+  // one PCG iteration of every pair; converged pairs are masked, so extra
+  // iterations change nothing
+  auto iteration = [&](cudaStream_t st) {
+    block_mm32_kernel<<<sb.G, 256, 0, st>>>(sb.S32.p, sb.gsep.p, sb.moff.p, P, ld, b, 1.f, 0.f, Q);
     KATZ_CHECK_LAUNCH();
-    segcoldot_kernel<<<sb.G, 256, 0, s>>>(P, Q, ld, b, sb.gsep.p, pq);
+    segcoldot_kernel<<<sb.G, 256, 0, st>>>(P, Q, ld, b, sb.gsep.p, pq);
     KATZ_CHECK_LAUNCH();
-    seg_alpha_kernel<<<pb, 256, 0, s>>>(rz, pq, pairs, active, al, flags);
+    seg_alpha_kernel<<<pb, 256, 0, st>>>(rz, pq, pairs, active, al, flags);
     KATZ_CHECK_LAUNCH();
-    seg_xr_kernel<<<vb, 256, 0, s>>>(K2, P, R, Q, ld, n2, b, sb.sg.p, al);
+    seg_xr_kernel<<<vb, 256, 0, st>>>(K2, P, R, Q, ld, n2, b, sb.sg.p, al);
     KATZ_CHECK_LAUNCH();
-    segcoldot_kernel<<<sb.G, 256, 0, s>>>(R, R, ld, b, sb.gsep.p, rr);
+    segcoldot_kernel<<<sb.G, 256, 0, st>>>(R, R, ld, b, sb.gsep.p, rr);
     KATZ_CHECK_LAUNCH();
-    seg_precond(sb, R, Z, ld, b, s);
-    segcoldot_kernel<<<sb.G, 256, 0, s>>>(R, Z, ld, b, sb.gsep.p, rzn);
+    seg_precond(sb, R, Z, ld, b, st);
+    segcoldot_kernel<<<sb.G, 256, 0, st>>>(R, Z, ld, b, sb.gsep.p, rzn);
     KATZ_CHECK_LAUNCH();
-    KATZ_CUDA(cudaMemsetAsync(flags + 1, 0, sizeof(int), s));
-    seg_beta_kernel<<<pb, 256, 0, s>>>(rr, thr2, rz, rzn, pairs, active, be, it, flags + 1);
+    KATZ_CUDA(cudaMemsetAsync(flags + 1, 0, sizeof(int), st));
+    seg_beta_kernel<<<pb, 256, 0, st>>>(rr, thr2, rz, rzn, pairs, active, be, it, flags + 1);
     KATZ_CHECK_LAUNCH();
-    seg_p_kernel<<<vb, 256, 0, s>>>(P, Z, ld, n2, b, sb.sg.p, active, be);
+    seg_p_kernel<<<vb, 256, 0, st>>>(P, Z, ld, n2, b, sb.sg.p, active, be);
     KATZ_CHECK_LAUNCH();
-    open = open_pairs();
+  };
+  // kItersPerReplay iterations captured once into a CUDA graph (on a stream
+  // of its own, ordered after the caller's by events) and replayed until no
+  // pair is open; the host reads the open count once per replay
+  if (open > 0) {
+    constexpr int kItersPerReplay = 4;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto cleanup = [&]() {
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+      if (ev) cudaEventDestroy(ev);
+      if (cs) cudaStreamDestroy(cs);
+    };
+    try {
+      KATZ_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      KATZ_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      KATZ_CUDA(cudaEventRecord(ev, s));
+      KATZ_CUDA(cudaStreamWaitEvent(cs, ev, 0));
+      KATZ_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      try {
+        for (int t = 0; t < kItersPerReplay; ++t) iteration(cs);
+      } catch (...) {
+        cudaStreamEndCapture(cs, &graph);
+        throw;
+      }
+      KATZ_CUDA(cudaStreamEndCapture(cs, &graph));
+      KATZ_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+      for (int done = 0; done < max_iter && open > 0; done += kItersPerReplay) {
+        KATZ_CUDA(cudaGraphLaunch(exec, cs));
+        ++idx.seg_replays;
+        int h = 0;
+        KATZ_CUDA(cudaMemcpyAsync(&h, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, cs));
+        KATZ_CUDA(cudaStreamSynchronize(cs));
+        open = h;
+      }
+      KATZ_CUDA(cudaEventRecord(ev, cs));
+      KATZ_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    } catch (...) {
+      cleanup();
+      throw;
+    }
+    cleanup();
   }
   iters_gc.resize(pairs);
   int fl = 0;

@@ -77,6 +77,8 @@ def test_multi_graph_lrc_matches_oracle(lrc_case):
             off += g.n
         print(fn.__name__, "refinement steps", stats["refine_steps"], "mean inner iterations",
               float(iters.mean()), "range", int(iters.min()), int(iters.max()))
+        # both inner solvers replay CUDA graphs of their iterations
+        assert stats["graph_replays"] >= 1, fn.__name__
 
 
 def test_multi_graph_lrc_ritz_values_match_oracle(lrc_case):
