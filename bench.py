@@ -33,10 +33,10 @@ UNIT = "queries/s"
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch
 # of the dominant kernel, keyed by the source hash of the kernel files it was
 # measured on (null once they change).  cheb_step: two launches captured on
-# the same graph recipe at n = 400,000, b = 1,024 on the autotuned grid (7.38
-# and 9.14 GB against 4.9 and 6.6 GB algorithmic), their mean scaled by rows
-# to n1 = 3,998,000 (x 10.0).
-NCU_TRAFFIC = {("cheb_step", "21255f1e51a9e8f1"): 82.6e9}
+# the same graph recipe at n = 400,000, b = 323 (2.29 and 2.83 GB against
+# 1.59 and 2.11 GB algorithmic), their mean scaled by rows and columns to
+# n1 = 3,998,000, ld = 1,024 (x 31.2).
+NCU_TRAFFIC = {("cheb_step", "89b34e7979f857b4"): 80.0e9}
 
 
 def parse():

@@ -558,6 +558,35 @@ __global__ void ff_out_kernel(const float* __restrict__ Kh, const float* __restr
   }
 }
 
+// The same, a warp per output row (rows grid-stride) and 4 columns per lane
+// moved as float4 (FP32 output, every leading dimension a multiple of 4 and
+// 16-byte aligned bases): no per-element index division.
+__global__ void ff_out_rows_kernel(const float* __restrict__ Kh, const float* __restrict__ Kl,
+                                   const float* __restrict__ D, int64_t ld, const int32_t* map,
+                                   int64_t n, int b, float* out, int64_t ldk) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; i < n;
+       i += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+    const int64_t r = map ? map[i] : i;
+    for (int c = lane * 4; c < b; c += 128) {
+      const int64_t o = r * ld + c;
+      const float4 h = __ldg(reinterpret_cast<const float4*>(Kh + o));
+      const float4 l = __ldg(reinterpret_cast<const float4*>(Kl + o));
+      const float4 d = D ? __ldg(reinterpret_cast<const float4*>(D + o)) : make_float4(0, 0, 0, 0);
+      const FF t0 = two_sum(h.x, d.x), t1 = two_sum(h.y, d.y), t2 = two_sum(h.z, d.z),
+               t3 = two_sum(h.w, d.w);
+      const float4 v = make_float4(t0.hi + (t0.lo + l.x), t1.hi + (t1.lo + l.y),
+                                   t2.hi + (t2.lo + l.z), t3.hi + (t3.lo + l.w));
+      if (c + 4 <= b) {
+        *reinterpret_cast<float4*>(out + i * ldk + c) = v;
+      } else {  // ragged tail inside ld: only the columns < b
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+        for (int w = 0; c + w < b; ++w) out[i * ldk + c + w] = vv[w];
+      }
+    }
+  }
+}
+
 unsigned flat(int64_t total) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), int64_t(num_sms()) * 16));
 }
@@ -664,7 +693,17 @@ void ff_add(float* Kh, float* Kl, const float* D, int64_t total, cudaStream_t s)
 void ff_out(const float* Kh, const float* Kl, const float* D, int64_t ld, const int32_t* map,
             int64_t n, int b, void* out, int out_dt, int64_t ldk, cudaStream_t s) {
   if (n * b <= 0) return;
-  ff_out_kernel<<<flat(n * b), 256, 0, s>>>(Kh, Kl, D, ld, map, n, b, out, out_dt, ldk);
+  const bool rows = out_dt == KATZ_F32 && ld % 4 == 0 && ldk % 4 == 0 &&
+                    ((reinterpret_cast<uintptr_t>(Kh) | reinterpret_cast<uintptr_t>(Kl) |
+                      reinterpret_cast<uintptr_t>(D) | reinterpret_cast<uintptr_t>(out)) % 16) == 0;
+  if (rows) {
+    const unsigned blocks =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 8), int64_t(num_sms()) * 16));
+    ff_out_rows_kernel<<<blocks, 256, 0, s>>>(Kh, Kl, D, ld, map, n, b, static_cast<float*>(out),
+                                              ldk);
+  } else {
+    ff_out_kernel<<<flat(n * b), 256, 0, s>>>(Kh, Kl, D, ld, map, n, b, out, out_dt, ldk);
+  }
   KATZ_CHECK_LAUNCH();
 }
 

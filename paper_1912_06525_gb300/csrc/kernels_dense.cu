@@ -302,14 +302,16 @@ __device__ __forceinline__ bool better(T sa, int ia, T sb, int ib) {
 constexpr int kTopMax = 64;
 constexpr int kTopUnroll = 16;  // rows loaded ahead per warp (2 KB in flight per warp)
 
-// Pass 1: CTA = (row slice, tile of 32 query columns); lane c of every warp
-// owns column tile*32 + c, so each warp reads K row by row in coalesced
-// 128-byte segments, kTopUnroll rows ahead.  Each (warp, column) keeps a
-// sorted top-k list in local memory (scores in K's own type, so the order
-// is decided in that precision) with its k-th entry held in registers; a
+// Pass 1: CTA = (row slice, 8 tiles of 32 query columns); warp w takes
+// column tile blockIdx.y * 8 + w and lane c its column tile * 32 + c, so
+// the CTA's warps read neighbouring 128-byte segments of the same rows (a
+// 1 KB stretch of each row of K at a time) and each warp walks every row
+// of the slice, kTopUnroll rows ahead.  Each (warp, column) keeps a sorted
+// top-k list in local memory (scores in K's own type, so the order is
+// decided in that precision) with its k-th entry held in registers; a
 // candidate is tested against q's neighbours (binary search in the sorted
 // CSR row; skipped when mask_nbrs is false) only when it beats the k-th
-// entry.  Lists go to the scratch as [column][slice*8 + warp][k].
+// entry.  Lists go to the scratch as [column][slice][k].
 template <class VT>
 __global__ void __launch_bounds__(256) topk_partial_kernel(Csr W, const VT* K, int64_t ldk,
                                                            int64_t n, const int32_t* q, int b,
@@ -317,7 +319,7 @@ __global__ void __launch_bounds__(256) topk_partial_kernel(Csr W, const VT* K, i
                                                            bool mask_nbrs, int32_t* pid,
                                                            double* psc) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int j = blockIdx.y * 32 + lane;
+  const int j = (blockIdx.y * 8 + warp) * 32 + lane;
   const bool cv = j < b;
   const int64_t r0 = int64_t(blockIdx.x) * rows_per_slice;
   const int64_t r1 = min(n, r0 + rows_per_slice);
@@ -330,16 +332,16 @@ __global__ void __launch_bounds__(256) topk_partial_kernel(Csr W, const VT* K, i
   VT thv = VT(0);  // k-th entry once the list is full
   int thi = 0;
   if (cv) {
-    for (int64_t i0 = r0 + warp; i0 < r1; i0 += 8 * kTopUnroll) {
+    for (int64_t i0 = r0; i0 < r1; i0 += kTopUnroll) {
       VT vals[kTopUnroll];
 #pragma unroll
       for (int u = 0; u < kTopUnroll; ++u) {
-        const int64_t i = i0 + 8 * u;
+        const int64_t i = i0 + u;
         vals[u] = i < r1 ? K[i * ldk + j] : VT(0);
       }
 #pragma unroll
       for (int u = 0; u < kTopUnroll; ++u) {
-        const int64_t i = i0 + 8 * u;
+        const int64_t i = i0 + u;
         if (i >= r1 || i == qq) continue;
         const VT v = vals[u];
         if (cnt == k && !better(v, (int)i, thv, thi)) continue;
@@ -363,8 +365,8 @@ __global__ void __launch_bounds__(256) topk_partial_kernel(Csr W, const VT* K, i
         }
       }
     }
-    const int lists = gridDim.x * 8;
-    const int64_t out = (int64_t(j) * lists + blockIdx.x * 8 + warp) * k;
+    const int lists = gridDim.x;
+    const int64_t out = (int64_t(j) * lists + blockIdx.x) * k;
     for (int t = 0; t < k; ++t) {
       pid[out + t] = t < cnt ? li[t] : -1;
       psc[out + t] = t < cnt ? double(ls[t]) : 0.0;
@@ -406,8 +408,10 @@ void topk_columns_ws(const Csr& W, const VT* K, int64_t ldk, int64_t n, const in
                      int k, int32_t* ids, double* scores, int32_t* ws_id, double* ws_sc,
                      int slices, cudaStream_t s, bool mask_nbrs) {
   KATZ_REQUIRE(slices * 8 <= 2 * kTopMax && k <= kTopMax, KATZ_EINVAL, "topk: too many lists");
-  const int64_t rows_per = ceil_div(n, slices);
-  dim3 grid((unsigned)slices, (unsigned)ceil_div(b, 32));
+  // 8 row slices per requested slice: 8 lists of k per column and slice, as
+  // the scratch is sized
+  const int64_t rows_per = ceil_div(n, int64_t(slices) * 8);
+  dim3 grid((unsigned)(slices * 8), (unsigned)ceil_div(b, 256));
   topk_partial_kernel<VT><<<grid, 256, 0, s>>>(W, K, ldk, n, q, b, k, rows_per, mask_nbrs, ws_id,
                                                ws_sc);
   KATZ_CHECK_LAUNCH();
