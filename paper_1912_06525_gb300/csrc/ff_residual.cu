@@ -458,6 +458,44 @@ __global__ void __launch_bounds__(256) ffr_heavy_partial_kernel(Csr A, const flo
   }
 }
 
+// Heavy rows, pass 1, on 256-column tiles of 32-byte lanes with packed
+// f32x2 float-float sums (the partials' layout as ffr_heavy_partial_kernel).
+template <int WT>
+__global__ void __launch_bounds__(256) ffr_heavy_partial8_kernel(Csr A, const float* __restrict__ X,
+                                                                 int64_t ld, HeavyRows hv) {
+  constexpr int TILE = 256;
+  constexpr int64_t kPerWarp = kHeavySeg / 8;
+  __shared__ FF red[8][TILE];
+  const int t = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t g = blockIdx.x;
+  const int64_t tile0 = int64_t(blockIdx.y) * TILE;
+  const int64_t c0 = tile0 + 8 * t;
+  const bool cval = c0 < ld;
+  const int h = hv.seg_row[g];
+  const int64_t row = hv.rows[h];
+  const int64_t r0 = A.rowptr[row], r1 = A.rowptr[row + 1];
+  const int64_t s0 = r0 + (g - hv.seg_ptr[h]) * kHeavySeg;
+  const int64_t k0 = min(r1, s0 + wib * kPerWarp), k1 = min(r1, s0 + (wib + 1) * kPerWarp);
+  uint64_t hi[4], lo[4];
+  row_sum8<WT, true>(A, X, ld, c0, cval, t, k0, k1, hi, lo);
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    const int q = w >> 1;
+    const bool up = w & 1;
+    red[wib][8 * t + w] = {up ? hi2(hi[q]) : lo2(hi[q]), up ? hi2(lo[q]) : lo2(lo[q])};
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < TILE; c += blockDim.x) {
+    if (tile0 + c >= ld) continue;
+    FF sum = red[0][c];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) sum = ff_plus(sum, red[q][c]);
+    const int64_t o = g * ld + tile0 + c;
+    hv.scratch[o] = sum.hi;
+    hv.scratch[hv.nseg * ld + o] = sum.lo;
+  }
+}
+
 // Heavy rows, pass 2: warp per heavy row; its segment partials are added
 // in segment order, then the row epilogue and the Rh^2 column sums.
 template <int VPT, bool INIT>
@@ -645,7 +683,8 @@ void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl,
     const dim3 pg((unsigned)hv->nseg, (unsigned)tiles);
     const dim3 fg((unsigned)ceil_div(hv->n, 8), (unsigned)tiles);
 #define KATZ_FFH(WT)                                                                        \
-  if (vpt == 2) ffr_heavy_partial_kernel<WT, 2><<<pg, 256, 0, s>>>(A, X, ld, *hv);         \
+  if (wide) ffr_heavy_partial8_kernel<WT><<<pg, 256, 0, s>>>(A, X, ld, *hv);               \
+  else if (vpt == 2) ffr_heavy_partial_kernel<WT, 2><<<pg, 256, 0, s>>>(A, X, ld, *hv);    \
   else ffr_heavy_partial_kernel<WT, 1><<<pg, 256, 0, s>>>(A, X, ld, *hv)
     switch (A.vdt) {
       case KATZ_UNIT: KATZ_FFH(KATZ_UNIT); break;

@@ -360,7 +360,10 @@ static void spmm_dispatch(SpmmParams<VT>& p, const int32_t* heavy, int64_t n_hea
   int vpt = 1;
   // columns per warp-row tile: 256 floats / 128 doubles by default, so the
   // accumulators and fused dot partials stay in registers without spills
-  const int vcap = cfg.col_tile > 0 ? max(1, cfg.col_tile / (VW * 32)) : 2;
+  // (with the fused dot at most 2: its FP64 column partials per vector
+  // cost registers, and the tuned tile is measured without the dot)
+  int vcap = cfg.col_tile > 0 ? max(1, cfg.col_tile / (VW * 32)) : 2;
+  if (p.dots) vcap = std::min(vcap, 2);
   if (tpr == 32)
     while (vpt < vcap && vpt * 32 < nvec) vpt *= 2;
   const int tile = tpr * VW * vpt;

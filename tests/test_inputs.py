@@ -51,3 +51,20 @@ def test_many_graph_recipe():
         inter = (lab[r] != lab[g.col]).mean()
         assert 0.05 <= inter <= 0.15, inter
     assert checked >= 5
+
+
+def test_dyadic_weights_on_a_pattern_are_symmetric_and_exact_in_bf16():
+    """The weighted variant of a workload keeps its pattern and gives both
+    stored directions of an edge the same weight k/64 in [0.5, 2), a value
+    BF16 holds exactly (8 significant bits)."""
+    import numpy as np
+    from paper_1912_06525_gb300 import synth
+    g = synth.sbm_bernoulli([60] * 5, 0.2, 0.02, seed=4)
+    gw = synth.with_dyadic_weights(g, 9)
+    assert np.array_equal(gw.rowptr, g.rowptr) and np.array_equal(gw.col, g.col)
+    W = O.adjacency(gw.n, gw.rowptr, gw.col, gw.val)
+    assert abs(W - W.T).max() == 0.0
+    k = gw.val * 64
+    assert np.all(k == np.round(k)) and k.min() >= 32 and k.max() < 128
+    # k/64 with k < 256 needs at most 8 significant bits
+    assert np.all(np.frexp(gw.val)[0] * 256 == np.round(np.frexp(gw.val)[0] * 256))
