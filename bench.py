@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (tests only)")
+    ap.add_argument("--rhs-coupling", default="auto", choices=["auto", "on", "off"],
+                    help="store Z = beta M11^-1 W12 for the first Schur right-hand side")
     ap.add_argument("--c", type=float, default=None,
                     help="beta = c / lambda_max (default 0.9 on the n=4M graph, 0.5 on n=1M)")
     ap.add_argument("--paper-beta", action="store_true",
@@ -767,16 +769,19 @@ def main():
     if args.paper_beta:  # Section 4: beta = 1 / (||W||_2 + 1)
         c = lam / (lam + 1.0)
     beta = c / lam
+    rc = {"auto": 0, "on": 1, "off": -1}[args.rhs_coupling]
     if args.standin:  # unit weights; top-1% hubs, the rest kept whole
         idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_UNIT, rank=rank_r,
-                                    n_hubs=g.n // 100, block_max=64, split=False)
+                                    n_hubs=g.n // 100, block_max=64, split=False,
+                                    rhs_coupling=rc)
     elif args.workload == 3:
         n_hubs = int(g.meta["hubs"].shape[0])
         idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_BF16, rank=rank_r,
-                                    n_hubs=n_hubs, block_max=64, split=False)
+                                    n_hubs=n_hubs, block_max=64, split=False, rhs_coupling=rc)
     else:  # power law: top-1% hubs; the rest keeps a giant component, kept whole
         idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_F32, rank=rank_r,
-                                    n_hubs=g.n // 100, block_max=64, split=False)
+                                    n_hubs=g.n // 100, block_max=64, split=False,
+                                    rhs_coupling=rc)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     info = idx.info()
@@ -988,6 +993,7 @@ def main():
                     "cheb_gather": args.cheb,
                     "n2": info["n2"], "n1": info["n1"], "index_build_s": build_s,
                     "index_device_bytes": info["device_bytes"],
+                    "rhs_coupling": bool(info["rhs_coupling"]),
                     "sigma_1": info["lambda_max_R"],
                     "lambda_max": lam, "beta": beta,
                     "beta_rule": "1/(lambda_max+1)" if args.paper_beta else "c/lambda_max"})

@@ -128,6 +128,14 @@ typedef struct {
                             cores instead of a second M11 solve when that is cheaper:
                             0 = when it fits in a third of device memory, 1 = always,
                             -1 = never */
+  int32_t rhs_coupling;  /* store Z = beta M11^{-1} W12 (n1 x n2, FP32; the build solves for
+                            it anyway to form S) so that the first Schur right-hand side of a
+                            query, F = B2 - M12^T M11^{-1} B1 = B2 + Z^T B1 (Eq. 7, M11
+                            symmetric), is gathered from the deg(q) rows of Z that the sparse
+                            B1 = beta W e_q touches instead of costing an M11 solve of the
+                            whole n1 x b block: 0 = where M11 has blocks solved iteratively,
+                            S is dense and Z fits in a quarter of device memory, 1 = always
+                            (single graph, dense S), -1 = never */
 } katz_build_opts;
 
 typedef struct {
@@ -154,7 +162,8 @@ typedef struct {
   double ms[8];         /* [0] total ms, [1] RHS ms, [2] first inner solve ms, [3] residual ms,
                            [4] CUDA-graph replays (multi-graph), [5] warm-start fallbacks
                            (columns started from zero), [6] mean scale of the CG warm
-                           start's guesses */
+                           start's guesses, [7] 1 when the first Schur right-hand side
+                           came from the stored Z (rhs_coupling) instead of an M11 solve */
 } katz_stats;
 
 typedef struct {
@@ -167,6 +176,7 @@ typedef struct {
   double lambda_upper; /* rigorous upper bound on lambda_max of W (Collatz-Wielandt); the SPD
                           check and the KATZ_TOL_ERROR_INF rule use it */
   int32_t schur_implicit; /* 1: the separator exceeds n2_max and S is applied implicitly */
+  int32_t rhs_coupling;   /* 1: Z = beta M11^{-1} W12 is stored (see katz_build_opts) */
 } katz_index_info;
 
 /* ---------------------------------------------------------------- graph */

@@ -256,10 +256,15 @@ int katz_index_get_info(const katz_index* idx, katz_index_info* info) {
     info->lambda_max_W = idx->lambda;
     info->lambda_upper = idx->lambda_up;
     info->schur_implicit = idx->s_implicit ? 1 : 0;
+    info->rhs_coupling = idx->has_z ? 1 : 0;
     int64_t bytes = idx->W.csr.bytes() + idx->Wp.csr.bytes() + idx->W12.csr.bytes() +
-                    idx->W21.csr.bytes() + idx->W11L.csr.bytes() + idx->S32.bytes() +
-                    idx->S64.bytes() + idx->M22inv32.bytes() + idx->M22inv64.bytes() +
-                    idx->Wr32.bytes() + idx->Wr64.bytes() + (int64_t)idx->ws.bytes();
+                    idx->W21.csr.bytes() + idx->W11L.csr.bytes() + idx->W22.csr.bytes() +
+                    idx->S32.bytes() + idx->S64.bytes() + idx->M22inv32.bytes() +
+                    idx->M22inv64.bytes() + idx->Wr32.bytes() + idx->Wr64.bytes() +
+                    idx->Wb.bytes() + idx->WbT.bytes() + idx->Wr32u.bytes() + idx->Hh.bytes() +
+                    idx->Hl.bytes() + idx->Zc.bytes() + idx->Sh.bytes() + idx->Sl.bytes() +
+                    idx->Mh.bytes() + idx->Ml.bytes() + idx->Hr.bytes() + idx->feat.bytes() +
+                    (int64_t)idx->ws.bytes();
     for (auto& c : idx->classes) bytes += c.inv32.bytes() + c.inv64.bytes();
     info->device_bytes = bytes;
     return KATZ_OK;

@@ -137,6 +137,12 @@ struct katz_index {
   katz::DBuf<float> Hh, Hl;
   int64_t ldH = 0;
   bool has_h = false;
+  // Z = beta M11^{-1} W12 (n1 x n2 FP32, row stride ldZ): the first Schur
+  // right-hand side of a query, F = B2 - M12^T M11^{-1} B1 = B2 + Z^T B1
+  // (Eq. 7), from the deg(q) rows of Z that B1 = beta W e_q touches
+  katz::DBuf<float> Zc;
+  int64_t ldZ = 0;
+  bool has_z = false;
   // S and M22^{-1} (n2 x ld2) as TF32 high/low parts for the tensor-core
   // Schur products of the FP32 solve (large separators only)
   katz::DBuf<float> Sh, Sl, Mh, Ml;

@@ -452,6 +452,17 @@ __global__ void sub_kernel(const double* A, const double* B, double* C, int64_t 
     C[e] = A[e] - B[e];
 }
 
+// Z[:, j0 + c] = V[:, c] for c < cw (V: rows x ldv FP64, Z: rows x ldz FP32)
+__global__ void cols_to_f32_kernel(const double* V, int64_t ldv, int64_t rows, int cw, float* Z,
+                                   int64_t ldz, int64_t j0) {
+  const int64_t total = rows * cw;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / cw, c = e % cw;
+    Z[i * ldz + j0 + c] = float(V[i * ldv + c]);
+  }
+}
+
 __global__ void to_f32_kernel(const double* A, float* B, int64_t total) {
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
        e += int64_t(gridDim.x) * blockDim.x)
@@ -1058,6 +1069,21 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
       idx.Hh.alloc(size_t(n1) * idx.ldH);
       idx.Hl.alloc(size_t(n1) * idx.ldH);
     }
+    // Z = beta M11^{-1} W12 in FP32 for the first Schur right-hand side of a
+    // query (automatic: where the first M11 solve of a query is iterative)
+    idx.ldZ = (n2 + 3) / 4 * 4;
+    {
+      size_t free_b = 0, total_b = 0;
+      KATZ_CUDA(cudaMemGetInfo(&free_b, &total_b));
+      const double bytes = 4.0 * double(n1) * double(idx.ldZ);
+      idx.has_z = !seg && !idx.s_implicit && n1 > 0 && o.rhs_coupling >= 0 &&
+                  (o.rhs_coupling > 0 || (n1 > idx.n1s && bytes <= double(total_b) / 4.0 &&
+                                          bytes <= 0.6 * double(free_b)));
+    }
+    if (idx.has_z) {
+      idx.Zc.alloc(size_t(n1) * idx.ldZ);
+      KATZ_CUDA(cudaMemsetAsync(idx.Zc.p, 0, idx.Zc.bytes(), s));
+    }
     // disjoint graphs: packed columns, T_g of every graph from one solve of
     // width (largest separator), scattered back to the block diagonal
     for (int64_t l0 = 0; seg && l0 < width; l0 += cw_max) {
@@ -1089,6 +1115,11 @@ void build_index(katz_index& idx, const HostCsr& W, double beta, const katz_buil
       KATZ_REQUIRE(st != KATZ_ENOTSPD, KATZ_ENOTSPD, "M11 is not positive definite");
       if (idx.has_h)
         split_tf32<double>(V.p, ldc, n1, cw, idx.Hh.p + j0, idx.Hl.p + j0, idx.ldH, s);
+      if (idx.has_z) {
+        cols_to_f32_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n1 * cw, 256), 8192), 256, 0,
+                             s>>>(V.p, ldc, n1, cw, idx.Zc.p, idx.ldZ, j0);
+        KATZ_CHECK_LAUNCH();
+      }
       spmm<double>(idx.W21.view(), idx.W21.heavy.p, idx.W21.n_heavy, beta, V.p, ldc, 0.0, nullptr,
                    ldc, T.p + j0, ld2, cw, nullptr, 0, nullptr, s);
     }

@@ -2,7 +2,7 @@
 // Algorithm 1, Section 3.2: partition, M11 block inverses, couplings, S and
 // M22^{-1}, the rank-r correction W_r D^{1/2}, the warm-start network).
 //
-// File layout (little-endian, version 2):
+// File layout (little-endian, version 3):
 //   magic "KATZIDX\0", u32 version, u32 endian mark 0x01020304,
 //   then one record per field in the order of serialize() below:
 //     u64 tag (FNV-1a of the field name), u32 element size, u64 count,
@@ -22,7 +22,7 @@ namespace katz {
 namespace {
 
 constexpr char kMagic[8] = {'K', 'A', 'T', 'Z', 'I', 'D', 'X', '\0'};
-constexpr uint32_t kVersion = 2;
+constexpr uint32_t kVersion = 3;
 constexpr uint32_t kEndianMark = 0x01020304u;
 constexpr size_t kChunk = size_t(64) << 20;  // staging chunk (a multiple of 8)
 
@@ -301,6 +301,9 @@ void serialize(Archive& a, katz_index& x) {
   a.dbuf("Hl", x.Hl);
   a.scalar("ldH", x.ldH);
   a.flag("has_h", x.has_h);
+  a.dbuf("Zc", x.Zc);
+  a.scalar("ldZ", x.ldZ);
+  a.flag("has_z", x.has_z);
   a.dbuf("Sh", x.Sh);
   a.dbuf("Sl", x.Sl);
   a.dbuf("Mh", x.Mh);
@@ -360,7 +363,11 @@ void check_loaded(const katz_index& x) {
         int64_t(x.perm.n) != x.n || int64_t(x.iperm.n) != x.n)
       fail("partition");
     if (int64_t(x.sigma.size()) != x.rank) fail("rank");
+    if (x.has_z && (x.ldZ < x.n2 || x.ldZ % 4 != 0 ||
+                    int64_t(x.Zc.n) != x.n1 * x.ldZ))
+      fail("stored coupling Z");
   }
+  if (x.has_z && !x.lrc) fail("stored coupling Z");
 }
 
 }  // namespace

@@ -918,19 +918,37 @@ __global__ void coldot_kernel(const VT* __restrict__ A, int64_t lda, const VT* _
 #pragma unroll
   for (int w = 0; w < VW; ++w) { tot[w] = 0; part[w] = VT(0); }
   int cnt = 0;
+  // a sum of squares (A == B) loads each row once; four rows per trip, all
+  // loads issued before the products
+  const bool same = A == B && lda == ldb;
   if (valid) {
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.y + threadIdx.y; i < len;
-         i += int64_t(gridDim.x) * blockDim.y) {
+    const int64_t step = int64_t(gridDim.x) * blockDim.y;
+    int64_t i = int64_t(blockIdx.x) * blockDim.y + threadIdx.y;
+    for (; i + 3 * step < len; i += 4 * step) {
+      VT a[4][VW], bb[4][VW];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) vload<VT>(A + (i + u * step) * lda + c, a[u]);
+      if (!same) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) vload<VT>(B + (i + u * step) * ldb + c, bb[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < VW; ++w) part[w] += a[u][w] * (same ? a[u][w] : bb[u][w]);
+      cnt += 4;
+      if (cnt >= kFlush) {
+        cnt = 0;
+#pragma unroll
+        for (int w = 0; w < VW; ++w) { tot[w] += double(part[w]); part[w] = VT(0); }
+      }
+    }
+    for (; i < len; i += step) {
       VT a[VW], bb[VW];
       vload<VT>(A + i * lda + c, a);
       vload<VT>(B + i * ldb + c, bb);
 #pragma unroll
       for (int w = 0; w < VW; ++w) part[w] += a[w] * bb[w];
-      if (++cnt == kFlush) {
-        cnt = 0;
-#pragma unroll
-        for (int w = 0; w < VW; ++w) { tot[w] += double(part[w]); part[w] = VT(0); }
-      }
     }
   }
 #pragma unroll

@@ -76,6 +76,85 @@ __global__ void rhs_add_kernel(Csr W, const int32_t* q, double beta, const int32
   }
 }
 
+// First Schur right-hand side of a query from the stored Z = beta M11^{-1} W12
+// (Eq. 7; M11 symmetric, so M12^T M11^{-1} = -Z^T):
+//   F[:, c] = B2[:, c] + Z^T B1[:, c],  B1[:, c] = beta W[q_c, :] restricted to
+// the rows pos(u) < n1.  Column c reads the deg(q_c) rows of Z that B1 touches:
+// the (row, weight) pairs are staged in shared memory 256 at a time (pairs of
+// separator nodes become (0, 0)), then every thread adds its KP entries of
+// the staged rows, four rows in flight, in FP64.  grid (b, ceil(n2 / (256 KP))).
+template <int WT>
+__global__ void __launch_bounds__(256) schur_rhs_from_z_kernel(
+    Csr W, const int32_t* __restrict__ q, double beta, const int32_t* __restrict__ pos,
+    int64_t n1, const float* __restrict__ Z, int64_t ldz, int64_t n2,
+    const float* __restrict__ R2, int64_t ld, float* __restrict__ F) {
+  constexpr int KP = 8;
+  __shared__ int64_t srow[256];
+  __shared__ double sw[256];
+  const int c = blockIdx.x;
+  const int64_t k0 = int64_t(blockIdx.y) * 256 * KP + threadIdx.x;
+  double acc[KP];
+#pragma unroll
+  for (int i = 0; i < KP; ++i) acc[i] = 0.0;
+  const int64_t e0 = W.rowptr[q[c]], e1 = W.rowptr[q[c] + 1];
+  for (int64_t base = e0; base < e1; base += 256) {
+    const int cnt = int(e1 - base < 256 ? e1 - base : 256);
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      const int64_t e = base + threadIdx.x;
+      const int64_t r = pos[W.col[e]];
+      const bool in1 = r < n1;
+      srow[threadIdx.x] = in1 ? r : 0;
+      double w = 1.0;
+      if (WT == KATZ_F64) w = static_cast<const double*>(W.val)[e];
+      else if (WT == KATZ_F32) w = static_cast<const float*>(W.val)[e];
+      else if (WT == KATZ_BF16) w = __bfloat162float(static_cast<const __nv_bfloat16*>(W.val)[e]);
+      sw[threadIdx.x] = in1 ? beta * w : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int j = 0; j < cnt; ++j) {
+      const float* zr = Z + srow[j] * ldz;
+      const double w = sw[j];
+#pragma unroll
+      for (int i = 0; i < KP; ++i) {
+        const int64_t k = k0 + int64_t(i) * 256;
+        if (k < n2) acc[i] = fma(w, double(__ldg(zr + k)), acc[i]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < KP; ++i) {
+    const int64_t k = k0 + int64_t(i) * 256;
+    if (k < n2) F[k * ld + c] = float(double(R2[k * ld + c]) + acc[i]);
+  }
+}
+
+static void schur_rhs_from_z(const katz_index& idx, const int32_t* q, int b, const float* R2,
+                             int64_t ld, float* F, cudaStream_t s) {
+  const dim3 grid((unsigned)b, (unsigned)ceil_div(idx.n2, 256 * 8));
+  const Csr W = idx.W.view();
+  switch (W.vdt) {
+    case KATZ_UNIT:
+      schur_rhs_from_z_kernel<KATZ_UNIT><<<grid, 256, 0, s>>>(W, q, idx.beta, idx.iperm.p, idx.n1,
+                                                              idx.Zc.p, idx.ldZ, idx.n2, R2, ld, F);
+      break;
+    case KATZ_F64:
+      schur_rhs_from_z_kernel<KATZ_F64><<<grid, 256, 0, s>>>(W, q, idx.beta, idx.iperm.p, idx.n1,
+                                                             idx.Zc.p, idx.ldZ, idx.n2, R2, ld, F);
+      break;
+    case KATZ_F32:
+      schur_rhs_from_z_kernel<KATZ_F32><<<grid, 256, 0, s>>>(W, q, idx.beta, idx.iperm.p, idx.n1,
+                                                             idx.Zc.p, idx.ldZ, idx.n2, R2, ld, F);
+      break;
+    default:
+      schur_rhs_from_z_kernel<KATZ_BF16><<<grid, 256, 0, s>>>(W, q, idx.beta, idx.iperm.p, idx.n1,
+                                                              idx.Zc.p, idx.ldZ, idx.n2, R2, ld, F);
+      break;
+  }
+  KATZ_CHECK_LAUNCH();
+}
+
 // Per column: converged = rr <= thr2; inner threshold
 //   thr2_in = max(tau^2 rr, (0.3)^2 thr2)
 // and, for converged columns, a threshold every residual meets (their
@@ -587,7 +666,7 @@ bool coupling_gemm_pays(const katz_index& idx, int64_t ld, double tol) {
 template <class VT>
 int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double tol_s,
               double tol_l, int max_iter, std::vector<int32_t>* iters, cudaStream_t s,
-              const VT* K2_0 = nullptr) {
+              const VT* K2_0 = nullptr, const int32_t* q_rhs = nullptr) {
   const int64_t n1 = idx.n1, n2 = idx.n2;
   const VT* R1 = Rin;
   const VT* R2 = Rin + n1 * ld;
@@ -596,14 +675,19 @@ int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double t
   VT* Y1 = idx.ws.get<VT>("lrc.Y1", size_t(std::max<int64_t>(n1, 1)) * ld);
   int status = KATZ_OK;
   auto merge = [&](int st) { if (st != KATZ_OK && status == KATZ_OK) status = st; };
-  if (n1 > 0) {
+  // Rin = beta W e_q (q_rhs given) and Z stored: F from the rows of Z, no Y1
+  const bool from_z = sizeof(VT) == 4 && q_rhs && idx.has_z && n1 > 0 && n2 > 0 &&
+                      !idx.seg_blocked;
+  if (n1 > 0 && !from_z) {
     NvtxRange r("katz.m11_solve");
     merge(m11_solve<VT>(idx, R1, Y1, b, ld, tol_l, max_iter, nullptr, s));
   }
   if (n2 > 0) {
     NvtxRange r("katz.schur_pcg");
     VT* F = idx.ws.get<VT>("lrc.F", size_t(n2) * ld);
-    if (n1 > 0)
+    if (from_z) {
+      if constexpr (sizeof(VT) == 4) schur_rhs_from_z(idx, q_rhs, b, R2, ld, F, s);
+    } else if (n1 > 0)
       spmm<VT>(idx.W21.view(), idx.W21.heavy.p, idx.W21.n_heavy, idx.beta, Y1, ld, 1.0, R2, ld, F,
                ld, b, nullptr, 0, nullptr, s, idx.W21.cfg(b));
     else
@@ -630,7 +714,7 @@ int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double t
   if (n1 > 0) {
     NvtxRange r("katz.backsolve");
     if constexpr (sizeof(VT) == 4) {
-      if (n2 > 0 && idx.has_h && coupling_gemm_pays(idx, ld, tol_l)) {
+      if (n2 > 0 && !from_z && idx.has_h && coupling_gemm_pays(idx, ld, tol_l)) {
         // K1 = Y1 + (beta M11^{-1} W12) K2 on the tensor cores (all ld columns,
         // so the zero padding columns stay zero)
         float* Bh = idx.ws.get<float>("lrc.K2h", size_t(ld) * idx.ldH);
@@ -668,9 +752,10 @@ template void apply_M<double>(const katz_index&, const double*, double*, int, in
 template <class VT>
 static int inner_solve(katz_index& idx, bool use_lrc, const VT* Rin, VT* D, int b, int64_t ld,
                        const double* thr2_in, double tol_rel, int max_iter,
-                       std::vector<int32_t>* iters, cudaStream_t s, const VT* K2_0 = nullptr) {
+                       std::vector<int32_t>* iters, cudaStream_t s, const VT* K2_0 = nullptr,
+                       const int32_t* q_rhs = nullptr) {
   if (use_lrc)
-    return lrc_solve<VT>(idx, Rin, D, b, ld, tol_rel, tol_rel, max_iter, iters, s, K2_0);
+    return lrc_solve<VT>(idx, Rin, D, b, ld, tol_rel, tol_rel, max_iter, iters, s, K2_0, q_rhs);
   // shares the scratch of the large-block M11 solve (never live at once)
   return cg_solve<VT>(idx.W, idx.beta, Rin, ld, idx.n, b, D, thr2_in, max_iter, idx.ws, "L",
                       iters, s);
@@ -832,8 +917,10 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
     KATZ_CUDA(cudaMemsetAsync(Kh, 0, sizeof(float) * n * ld, s));
     warm_cg_guess(idx, q, b, Kh, ld, s);
   } else {
+    // (the first right-hand side is beta W e_q itself: the Schur system's
+    // comes from the stored Z where there is one)
     status = inner_solve<float>(idx, use_lrc, Rh, Kh, b, ld, thr2_in, tol_rel, max_iter, &iters,
-                                s, K20);
+                                s, K20, q);
   }
   KATZ_CUDA(cudaMemsetAsync(Kl, 0, sizeof(float) * n * ld, s));
   KATZ_CUDA(cudaStreamSynchronize(s));
@@ -956,6 +1043,8 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
     stats->ms[1] = std::chrono::duration<double, std::milli>(t1 - t0).count();
     stats->ms[2] = std::chrono::duration<double, std::milli>(t2 - t1).count();
     stats->ms[3] = ms_res;
+    // the first Schur right-hand side came from the stored Z (no M11 solve)
+    stats->ms[7] = (use_lrc && !cg_warm && idx.has_z && idx.n1 > 0 && idx.n2 > 0) ? 1.0 : 0.0;
     if (o.warm_start && use_lrc) {
       int h = 0;
       KATZ_CUDA(cudaMemcpy(&h, ws.get<int>("S.nfb", 1), sizeof(int), cudaMemcpyDeviceToHost));

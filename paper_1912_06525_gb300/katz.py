@@ -53,7 +53,7 @@ class katz_build_opts(C.Structure):
     _fields_ = [("value_dtype", C.c_int32), ("build_lrc", C.c_int32), ("rank", C.c_int32),
                 ("n_hubs", C.c_int32), ("block_max", C.c_int32), ("split", C.c_int32),
                 ("lanczos_steps", C.c_int32), ("n2_max", C.c_int32), ("seed", C.c_uint64),
-                ("coupling_gemm", C.c_int32)]
+                ("coupling_gemm", C.c_int32), ("rhs_coupling", C.c_int32)]
 
 
 class katz_query_opts(C.Structure):
@@ -83,7 +83,8 @@ class katz_index_info(C.Structure):
                 ("n_blocks", C.c_int32), ("n_large_blocks", C.c_int32), ("rank", C.c_int32),
                 ("value_dtype", C.c_int32), ("beta", C.c_double), ("lambda_max_R", C.c_double),
                 ("device_bytes", C.c_int64), ("lambda_max_W", C.c_double),
-                ("lambda_upper", C.c_double), ("schur_implicit", C.c_int32)]
+                ("lambda_upper", C.c_double), ("schur_implicit", C.c_int32),
+                ("rhs_coupling", C.c_int32)]
 
 
 _lib = None
@@ -240,10 +241,11 @@ class KatzIndex:
 def katz_index_build(graph, beta: float, value_dtype: int = KATZ_F32, build_lrc: bool = True,
                      rank: int = 16, n_hubs: int = 0, block_max: int = 64, split: bool = True,
                      lanczos_steps: int = 0, n2_max: int = 0, seed: int = 20191212,
-                     coupling_gemm: int = 0, stream=None) -> KatzIndex:
+                     coupling_gemm: int = 0, rhs_coupling: int = 0,
+                     stream=None) -> KatzIndex:
     c, keep = _csr(graph)
     o = katz_build_opts(value_dtype, int(build_lrc), rank, n_hubs, block_max, int(split),
-                        lanczos_steps, n2_max, seed, coupling_gemm)
+                        lanczos_steps, n2_max, seed, coupling_gemm, rhs_coupling)
     h = C.c_void_p()
     _check(lib().katz_index_build(C.byref(c), float(beta), C.byref(o), _stream(stream),
                                   C.byref(h)))

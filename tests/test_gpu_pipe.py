@@ -112,12 +112,15 @@ def test_autotune_reports_kernel_choice():
 @pytest.mark.parametrize("coupling", [-1, 1])
 def test_coupling_product_paths_match_oracle(coupling):
     """Back-substitution by a second M11 solve (coupling_gemm=-1) or by the
-    stored beta M11^{-1} W12 on the tensor cores (coupling_gemm=1)."""
+    stored beta M11^{-1} W12 on the tensor cores (coupling_gemm=1); the first
+    Schur right-hand side by an M11 solve (rhs_coupling=-1), which the
+    tensor-core back-substitution needs (Y1)."""
     g = graph(weighted=True)
     W = O.adjacency(g.n, g.rowptr, g.col, g.val)
     beta = 0.85 / O.lambda_max(W)
     idx = katz.katz_index_build(g, beta, value_dtype=katz.KATZ_F32, rank=16, n_hubs=30,
-                                block_max=32, split=False, coupling_gemm=coupling)
+                                block_max=32, split=False, coupling_gemm=coupling,
+                                rhs_coupling=-1)
     q = synth.queries(g.n, 200, seed=4)
     ref = O.katz_direct(W, beta, q)
     for prec in (katz.KATZ_PREC_MIXED, katz.KATZ_PREC_F32):
