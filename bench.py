@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--paper-beta", action="store_true",
                     help="the paper's damping beta = 1 / (lambda_max + 1) instead of --c")
     ap.add_argument("--method", default="lrc", choices=["lrc", "cg"])
-    ap.add_argument("--gather", default="auto", choices=["auto", "register", "pipelined", "rowpipe"],
+    ap.add_argument("--gather", default="auto",
+                    choices=["auto", "register", "pipelined", "rowpipe", "chunked"],
                     help="kernel of the wide fused products (auto: the autotuner's choice)")
     ap.add_argument("--cheb", default="auto", choices=["auto", "f32", "bf16", "mixed"],
                     help="gathers of the large M11 block's Chebyshev steps: auto (the "
@@ -793,7 +794,8 @@ def main():
     sc = torch.empty((b, 20), dtype=torch.float64, device=dev)
     qfn = katz.katz_query_batch if args.method == "lrc" else katz.cg_query_batch
     gk = {"auto": katz.KATZ_GATHER_AUTO, "register": katz.KATZ_GATHER_REGISTER,
-          "pipelined": katz.KATZ_GATHER_PIPELINED, "rowpipe": katz.KATZ_GATHER_ROWPIPE}[args.gather]
+          "pipelined": katz.KATZ_GATHER_PIPELINED, "rowpipe": katz.KATZ_GATHER_ROWPIPE,
+          "chunked": katz.KATZ_GATHER_CHUNKED}[args.gather]
     last = {}
 
     cg_mode = {"auto": katz.KATZ_CHEB_AUTO, "f32": katz.KATZ_CHEB_F32,

@@ -590,6 +590,7 @@ int katz_autotune(katz_index* idx, int32_t b, int32_t* out, double* ms, void* st
     out[6] = r.res_cps;
     out[7] = r.cheb_depth;
     out[8] = r.cheb_rowpipe ? 1 : 0;
+    out[9] = r.cheb_chunk;
     ms[0] = r.ms_best;
     ms[1] = r.ms_default;
     return KATZ_OK;

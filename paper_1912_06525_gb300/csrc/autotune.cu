@@ -162,6 +162,17 @@ SpmmCfg tune_part(GraphPart& g, int b, Workspace& ws, cudaStream_t s, double* be
           best.gather_depth = gd;
         }
       }
+      // contiguous row chunks per CTA (the resident CTAs' rows neighbours)
+      for (int rc : {32, 64, 128, 256}) {
+        SpmmCfg c = best;
+        c.row_chunk = rc;
+        const double ms = time_launches(
+            [&] { cheb_step(g.view(), 0.01, 0.1, 1.0, X, X, X, Y, ld, b, s, &c); }, s, reps);
+        if (ms < bestf) {
+          bestf = ms;
+          best.row_chunk = rc;
+        }
+      }
       {
         SpmmCfg c = best;
         c.row_pipeline = true;
@@ -210,6 +221,7 @@ TuneResult autotune(katz_index& idx, int b, cudaStream_t s) {
       r.cheb_cps = cc.fused_cps;
       r.cheb_depth = cc.gather_depth;
       r.cheb_rowpipe = cc.row_pipeline;
+      r.cheb_chunk = cc.row_chunk;
     }
   } else {
     r.res_cps = c.fused_cps;

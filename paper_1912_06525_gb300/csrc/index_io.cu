@@ -197,18 +197,19 @@ void io_part(Archive& a, const std::string& p, GraphPart& g) {
   a.dbuf(p + ".ps.ctr", g.ps.ctr);
   a.scalar(p + ".ps.nblocks", g.ps.nblocks);
   // autotuned launch shapes: (b, warps, col_tile, ctas, pipe, pipe_first,
-  // fused_cps, gather_depth, row_pipeline)
-  constexpr size_t kF = 9;
+  // fused_cps, gather_depth, row_pipeline, row_chunk)
+  constexpr size_t kF = 10;
   std::vector<int32_t> t;
   if (a.saving())
     for (auto& kv : g.tuned) {
       const SpmmCfg& c = kv.second;
       t.insert(t.end(), {kv.first, c.warps_per_cta, c.col_tile, c.ctas_per_sm, int(c.pipe),
-                         int(c.pipe_first), c.fused_cps, c.gather_depth, int(c.row_pipeline)});
+                         int(c.pipe_first), c.fused_cps, c.gather_depth, int(c.row_pipeline),
+                         c.row_chunk});
     }
-  a.vec(p + ".tuned9", t);
+  a.vec(p + ".tuned10", t);
   if (!a.saving()) {
-    KATZ_REQUIRE(t.size() % kF == 0, KATZ_EINVAL, "index file: " + p + ".tuned9");
+    KATZ_REQUIRE(t.size() % kF == 0, KATZ_EINVAL, "index file: " + p + ".tuned10");
     g.tuned.clear();
     for (size_t i = 0; i < t.size(); i += kF) {
       SpmmCfg c;
@@ -220,9 +221,12 @@ void io_part(Archive& a, const std::string& p, GraphPart& g) {
       c.fused_cps = t[i + 6];
       c.gather_depth = t[i + 7];
       c.row_pipeline = t[i + 8] != 0;
+      c.row_chunk = t[i + 9];
       KATZ_REQUIRE(c.ctas_per_sm >= 0 && c.ctas_per_sm <= 1024 && c.fused_cps >= 0 &&
                        c.fused_cps <= 1024 && c.col_tile >= 0 && c.col_tile <= 1024 &&
-                       (c.gather_depth == 0 || c.gather_depth == 4 || c.gather_depth == 8),
+                       (c.gather_depth == 0 || c.gather_depth == 4 || c.gather_depth == 8) &&
+                       c.row_chunk >= 0 && c.row_chunk <= 65536 &&
+                       (c.row_chunk == 0 || c.row_chunk >= 8),
                    KATZ_EINVAL, "index file: launch shape out of range in " + p);
       g.tuned[t[i]] = c;
     }

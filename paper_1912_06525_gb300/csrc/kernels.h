@@ -24,6 +24,8 @@ struct SpmmCfg {
   int fused_cps = 0;       // CTAs per SM of the fused Chebyshev / residual kernel (0: ctas_per_sm)
   int gather_depth = 0;    // fused Chebyshev step: gathered rows loaded together (0, 4 or 8)
   bool row_pipeline = false;  // fused Chebyshev step: the row-pipelined kernel
+  int row_chunk = 0;  // fused Chebyshev step: CTA c takes rows [c, c+1) * row_chunk (0: the
+                      // warps stride over all rows)
 };
 
 // Y[i,:] = gamma * Z[i,:] + alpha * sum_k A[i,k] X[k,:]   for i < A.nrows.

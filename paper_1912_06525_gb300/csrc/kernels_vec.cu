@@ -509,6 +509,10 @@ struct ChebArgs {
   // tile-major layout (x_k, x_{k-1}, x_{k+1}): column tile t of row i at
   // ((t * rows + i) * TILE) instead of i * ld + t * TILE
   int xk_tm, prev_tm, out_tm;
+  // > 0: CTA c of a column tile takes the rows [c * chunk, (c + 1) * chunk),
+  // its warps interleaved, so that the CTAs resident at once work on
+  // neighbouring rows; 0: every warp strides over all rows
+  int64_t chunk;
 };
 
 // One warp per row and column tile of 32 * CW columns; lane t owns the CW
@@ -535,7 +539,13 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(ChebArgs p) {
   const float* Xf = static_cast<const float*>(p.Xk);
   const __nv_bfloat16* Xh = static_cast<const __nv_bfloat16*>(p.Xk);
   const __nv_bfloat16* Xl = Xh + p.plane;
-  for (int64_t i = warp; i < p.A.nrows; i += nwarps) {
+  int64_t i0 = warp, i1 = p.A.nrows, istep = nwarps;
+  if (p.chunk > 0) {
+    i0 = int64_t(blockIdx.x) * p.chunk + (threadIdx.x >> 5);
+    i1 = min(p.A.nrows, int64_t(blockIdx.x + 1) * p.chunk);
+    istep = blockDim.x >> 5;
+  }
+  for (int64_t i = i0; i < i1; i += istep) {
     const int64_t k0 = p.A.rowptr[i], k1 = p.A.rowptr[i + 1];
     float acc[CW];
 #pragma unroll
@@ -798,14 +808,17 @@ void cheb_step_ex(const Csr& A, double beta, double ak, double ck, const void* X
                                                 : 8;
   int64_t ctas = std::min<int64_t>(ceil_div(A.nrows, 8),
                                    std::max<int64_t>(1, int64_t(num_sms()) * cps / tiles));
+  const bool row_pipe = cfg && cfg->row_pipeline && wide && in_mode == kInF32 && prev_mode != 2 &&
+                        !out_split;
+  const int64_t chunk = (cfg && !row_pipe && cfg->row_chunk > 0) ? cfg->row_chunk : 0;
+  if (chunk > 0) ctas = ceil_div(A.nrows, chunk);
+  KATZ_REQUIRE(ctas < (int64_t(1) << 31), KATZ_EINVAL, "cheb_step: row chunk too small");
   dim3 grid((unsigned)std::max<int64_t>(1, ctas), (unsigned)tiles);
   ChebArgs a{A,     float(beta), float(ak), float(ck), float(sx), float(sp), Xk, Xprev, B,
              Xout,  ld,          A.nrows * ld,          b,         prev_mode, out_split,
-             (tm_mask & 1) ? 1 : 0, (tm_mask & 2) ? 1 : 0, (tm_mask & 4) ? 1 : 0};
+             (tm_mask & 1) ? 1 : 0, (tm_mask & 2) ? 1 : 0, (tm_mask & 4) ? 1 : 0, chunk};
   prof_begin(s);
   const int gd = cfg ? cfg->gather_depth : 0;
-  const bool row_pipe = cfg && cfg->row_pipeline && wide && in_mode == kInF32 && prev_mode != 2 &&
-                        !out_split;
 #define KATZ_CHEB_GD(WT, C, I)                                                      \
   if (gd == 8) cheb_step_kernel<WT, C, I, 8><<<grid, 256, 0, s>>>(a);              \
   else if (gd == 4) cheb_step_kernel<WT, C, I, 4><<<grid, 256, 0, s>>>(a);         \

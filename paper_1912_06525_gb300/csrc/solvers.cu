@@ -308,7 +308,8 @@ const double* inv_of<double>(const BlockClass& c) { return c.inv64.p; }
 // the first refinement-residual pass.
 static bool use_pipe(const katz_index& idx, const SpmmCfg* cfg, bool first = false) {
   if (idx.gather_pref == KATZ_GATHER_PIPELINED) return true;
-  if (idx.gather_pref == KATZ_GATHER_REGISTER || idx.gather_pref == KATZ_GATHER_ROWPIPE)
+  if (idx.gather_pref == KATZ_GATHER_REGISTER || idx.gather_pref == KATZ_GATHER_ROWPIPE ||
+      idx.gather_pref == KATZ_GATHER_CHUNKED)
     return false;
   return cfg && (first ? cfg->pipe_first : cfg->pipe);
 }
@@ -354,9 +355,16 @@ static void m11_chebyshev(katz_index& idx, const float* X, float* Y, int b, int6
     forced = cfg ? *cfg : SpmmCfg{};
     forced.row_pipeline = true;
     cfg = &forced;
-  } else if (idx.gather_pref == KATZ_GATHER_REGISTER && cfg && cfg->row_pipeline) {
+  } else if (idx.gather_pref == KATZ_GATHER_REGISTER && cfg &&
+             (cfg->row_pipeline || cfg->row_chunk > 0)) {
     forced = *cfg;
     forced.row_pipeline = false;
+    forced.row_chunk = 0;
+    cfg = &forced;
+  } else if (idx.gather_pref == KATZ_GATHER_CHUNKED) {
+    forced = cfg ? *cfg : SpmmCfg{};
+    forced.row_pipeline = false;
+    if (forced.row_chunk == 0) forced.row_chunk = 64;
     cfg = &forced;
   }
   const bool pipe = use_pipe(idx, cfg) && pipe_eligible(idx.W11L.ps, ld) &&
@@ -1176,7 +1184,7 @@ int run_queries(katz_index& idx, bool use_lrc, const int32_t* q_dev, const int32
   KATZ_REQUIRE(b > 0 && b <= 1024, KATZ_EINVAL, "b must be in [1, 1024]");
   // FP64-valued graphs keep the FP64 residual (their weights need not be
   // exact in FP32); the others use the float-float residual
-  KATZ_REQUIRE(o.gather_kernel >= KATZ_GATHER_AUTO && o.gather_kernel <= KATZ_GATHER_ROWPIPE,
+  KATZ_REQUIRE(o.gather_kernel >= KATZ_GATHER_AUTO && o.gather_kernel <= KATZ_GATHER_CHUNKED,
                KATZ_EINVAL, "gather_kernel must be a KATZ_GATHER_* value");
   idx.gather_pref = o.gather_kernel;
   KATZ_REQUIRE(o.cheb_gather >= KATZ_CHEB_AUTO && o.cheb_gather <= KATZ_CHEB_MIXED, KATZ_EINVAL,

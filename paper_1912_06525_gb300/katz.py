@@ -21,7 +21,8 @@ KATZ_OK, KATZ_EINVAL, KATZ_ENOTSPD, KATZ_ENOCONV, KATZ_ENOMEM, KATZ_ECUDA = rang
 KATZ_UNIT, KATZ_F64, KATZ_F32, KATZ_BF16 = range(4)
 KATZ_PREC_F32, KATZ_PREC_MIXED, KATZ_PREC_F64 = range(3)
 KATZ_TOL_RESIDUAL, KATZ_TOL_ERROR_INF = range(2)
-KATZ_GATHER_AUTO, KATZ_GATHER_REGISTER, KATZ_GATHER_PIPELINED, KATZ_GATHER_ROWPIPE = range(4)
+(KATZ_GATHER_AUTO, KATZ_GATHER_REGISTER, KATZ_GATHER_PIPELINED, KATZ_GATHER_ROWPIPE,
+ KATZ_GATHER_CHUNKED) = range(5)
 KATZ_CHEB_AUTO, KATZ_CHEB_F32, KATZ_CHEB_BF16, KATZ_CHEB_MIXED = range(4)
 
 STATUS_NAMES = {0: "KATZ_OK", 1: "KATZ_EINVAL", 2: "KATZ_ENOTSPD", 3: "KATZ_ENOCONV",
@@ -422,13 +423,14 @@ def katz_gemm_tf32x3(A, B, C_out, K=None, alpha=1.0, beta=0.0, stream=None):
 
 def katz_autotune(index, b: int, stream=None) -> dict:
     """Tune the SpMM launch shape for width b; returns the choice and times."""
-    out = np.zeros(9, dtype=np.int32)
+    out = np.zeros(10, dtype=np.int32)
     ms = np.zeros(2, dtype=np.float64)
     _check(lib().katz_autotune(index.handle, b, out.ctypes.data, ms.ctypes.data, _stream(stream)))
     return {"col_tile": int(out[0]), "ctas_per_sm": int(out[1]), "cheb_pipe": bool(out[2]),
             "residual_first_pipe": bool(out[3]), "residual_pipe": bool(out[4]),
             "cheb_ctas_per_sm": int(out[5]), "residual_ctas_per_sm": int(out[6]),
             "cheb_gather_depth": int(out[7]), "cheb_row_pipeline": bool(out[8]),
+            "cheb_row_chunk": int(out[9]),
             "ms_best": float(ms[0]), "ms_default": float(ms[1])}
 
 

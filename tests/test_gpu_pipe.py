@@ -49,7 +49,8 @@ def test_pipelined_paths_match_oracle(vdt, b):
     q[0] = 3000           # the star's hub (900 entries)
     q[1] = g.n - 1        # an isolated node: its column is zero
     ref = O.katz_direct(W, beta, q)
-    for kern in (katz.KATZ_GATHER_REGISTER, katz.KATZ_GATHER_PIPELINED):
+    for kern in (katz.KATZ_GATHER_REGISTER, katz.KATZ_GATHER_PIPELINED,
+                 katz.KATZ_GATHER_CHUNKED):
         for fn in (katz.katz_query_batch, katz.cg_query_batch):
             K = torch.zeros((g.n, b), dtype=torch.float64, device="cuda")
             st, it, rel = fn(idx, torch.from_numpy(q).cuda(), K, out_dtype=katz.KATZ_F64, tol=1e-6,
@@ -65,7 +66,8 @@ def test_pipelined_paths_match_oracle(vdt, b):
 @pytest.mark.parametrize("b", [5, 333, 1024])
 def test_chebyshev_gather_precisions_match_oracle(vdt, b):
     """The large M11 block's Chebyshev steps with FP32 iterates (AUTO, F32;
-    the register kernel and the row-pipelined one),
+    the register kernel with strided rows or contiguous row runs per CTA,
+    and the row-pipelined one),
     with split BF16 iterates gathered as hi + lo on a solve's last step
     (MIXED), and with hi-plane gathers on every step (BF16): the refined
     answers all meet the 1e-6 bound; 128-column tiles of 16-byte lane
@@ -85,7 +87,10 @@ def test_chebyshev_gather_precisions_match_oracle(vdt, b):
                        (katz.KATZ_CHEB_BF16, katz.KATZ_GATHER_REGISTER),
                        (katz.KATZ_CHEB_MIXED, katz.KATZ_GATHER_REGISTER),
                        (katz.KATZ_CHEB_AUTO, katz.KATZ_GATHER_ROWPIPE),
-                       (katz.KATZ_CHEB_F32, katz.KATZ_GATHER_ROWPIPE)):
+                       (katz.KATZ_CHEB_F32, katz.KATZ_GATHER_ROWPIPE),
+                       (katz.KATZ_CHEB_AUTO, katz.KATZ_GATHER_CHUNKED),
+                       (katz.KATZ_CHEB_F32, katz.KATZ_GATHER_CHUNKED),
+                       (katz.KATZ_CHEB_BF16, katz.KATZ_GATHER_CHUNKED)):
         K = torch.zeros((g.n, b), dtype=torch.float32, device="cuda")
         st, it, rel = katz.katz_query_batch(idx, torch.from_numpy(q).cuda(), K, tol=1e-6,
                                             gather_kernel=kern, cheb_gather=mode)
@@ -102,6 +107,7 @@ def test_autotune_reports_kernel_choice():
     res = katz.katz_autotune(idx, 256)
     assert isinstance(res["cheb_pipe"], bool)
     assert res["cheb_ctas_per_sm"] in (8, 16, 32, 64, 128)
+    assert res["cheb_row_chunk"] in (0, 32, 64, 128, 256)
     assert res["residual_ctas_per_sm"] in (8, 16, 32, 64, 128)
     q = synth.queries(g.n, 256, seed=5)
     K = torch.zeros((g.n, 256), dtype=torch.float32, device="cuda")
