@@ -62,8 +62,26 @@ namespace {
 // accesses) or 8 (32-byte FP32 accesses, the 256-bit vector loads and
 // stores of sm_100+, and 16-byte BF16 accesses).  "ro": read-only data
 // (non-coherent path).
+// Two FP32 values in one 64-bit register for the packed f32x2 arithmetic of
+// sm_100+ (one instruction per column pair; the same round-to-nearest
+// results as two scalar operations, fused where the scalar form is fused)
+__device__ __forceinline__ uint64_t padd2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t pfma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 template <int CW> struct Lane;
 template <> struct Lane<4> {
+  // the lane's 4 columns as 2 packed pairs (read-only path)
+  static __device__ __forceinline__ void p32_ro(const float* p, uint64_t (&o)[2]) {
+    asm("ld.global.nc.v2.b64 {%0,%1}, [%2];" : "=l"(o[0]), "=l"(o[1]) : "l"(p));
+  }
   static __device__ __forceinline__ void f32_ro(const float* p, float (&o)[4]) {
     const float4 v = __ldg(reinterpret_cast<const float4*>(p));
     o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
@@ -94,6 +112,11 @@ template <> struct Lane<4> {
   }
 };
 template <> struct Lane<8> {
+  static __device__ __forceinline__ void p32_ro(const float* p, uint64_t (&o)[4]) {
+    asm("ld.global.nc.v4.b64 {%0,%1,%2,%3}, [%4];"
+        : "=l"(o[0]), "=l"(o[1]), "=l"(o[2]), "=l"(o[3])
+        : "l"(p));
+  }
   static __device__ __forceinline__ void f32_ro(const float* p, float (&o)[8]) {
     asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]),
@@ -550,7 +573,98 @@ __global__ void __launch_bounds__(256) cheb_step_kernel(ChebArgs p) {
     float acc[CW];
 #pragma unroll
     for (int w = 0; w < CW; ++w) acc[w] = 0.f;
-    for (int64_t kb = k0; kb < k1; kb += 32) {
+    if constexpr (IN == kInF32 && GD > 0) {
+      // FP32 iterates: whole groups of GD entries without bound checks, all
+      // GD rows loaded before any is added, then the last partial group with
+      // checks; sums kept as packed column pairs (the same additions in the
+      // same order as the scalar form)
+      uint64_t ap[CW / 2];
+#pragma unroll
+      for (int q = 0; q < CW / 2; ++q) ap[q] = 0;
+      const float* xb = Xf + xoff;
+      for (int64_t kb = k0; kb < k1; kb += 32) {
+        const int64_t k = kb + t;
+        int cj = 0;
+        float wj = 0.f;
+        if (k < k1) {
+          cj = p.A.col[k];
+          wj = load_weight<WT, float>(p.A.val, k);
+        }
+        const int cnt = (int)(k1 - kb < 32 ? k1 - kb : 32);
+        int s2 = 0;
+        for (; s2 + GD <= cnt; s2 += GD) {
+          int jj[GD];
+          float ww[GD];
+#pragma unroll
+          for (int u = 0; u < GD; ++u) {
+            jj[u] = __shfl_sync(0xffffffffu, cj, s2 + u);
+            if constexpr (WT != KATZ_UNIT) ww[u] = __shfl_sync(0xffffffffu, wj, s2 + u);
+          }
+          if (cval) {
+            uint64_t xv[GD][CW / 2];
+#pragma unroll
+            for (int u = 0; u < GD; ++u) L::p32_ro(xb + int64_t(jj[u]) * xs, xv[u]);
+#pragma unroll
+            for (int u = 0; u < GD; ++u) {
+              if constexpr (WT == KATZ_UNIT) {
+#pragma unroll
+                for (int q = 0; q < CW / 2; ++q) ap[q] = padd2(ap[q], xv[u][q]);
+              } else {
+                const uint64_t w2 = uint64_t(__float_as_uint(ww[u])) |
+                                    (uint64_t(__float_as_uint(ww[u])) << 32);
+#pragma unroll
+                for (int q = 0; q < CW / 2; ++q) ap[q] = pfma2(w2, xv[u][q], ap[q]);
+              }
+            }
+          }
+        }
+        if (s2 < cnt) {
+          // the last, partial group: its rows loaded together as well (rows
+          // past the end load nothing and add zero)
+          const int rem = cnt - s2;
+          int jj[GD];
+          float ww[GD];
+#pragma unroll
+          for (int u = 0; u < GD; ++u) {
+            jj[u] = __shfl_sync(0xffffffffu, cj, (s2 + u) & 31);
+            ww[u] = 1.f;
+            if constexpr (WT != KATZ_UNIT) ww[u] = __shfl_sync(0xffffffffu, wj, (s2 + u) & 31);
+          }
+          if (cval) {
+            uint64_t xv[GD][CW / 2];
+#pragma unroll
+            for (int u = 0; u < GD; ++u) {
+              if (u < rem) {
+                L::p32_ro(xb + int64_t(jj[u]) * xs, xv[u]);
+              } else {
+#pragma unroll
+                for (int q = 0; q < CW / 2; ++q) xv[u][q] = 0;
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < GD; ++u) {
+              if (u < rem) {
+                if constexpr (WT == KATZ_UNIT) {
+#pragma unroll
+                  for (int q = 0; q < CW / 2; ++q) ap[q] = padd2(ap[q], xv[u][q]);
+                } else {
+                  const uint64_t w2 = uint64_t(__float_as_uint(ww[u])) |
+                                      (uint64_t(__float_as_uint(ww[u])) << 32);
+#pragma unroll
+                  for (int q = 0; q < CW / 2; ++q) ap[q] = pfma2(w2, xv[u][q], ap[q]);
+                }
+              }
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < CW / 2; ++q) {
+        acc[2 * q] = __uint_as_float(uint32_t(ap[q]));
+        acc[2 * q + 1] = __uint_as_float(uint32_t(ap[q] >> 32));
+      }
+    }
+    for (int64_t kb = k0; (IN != kInF32 || GD == 0) && kb < k1; kb += 32) {
       const int64_t k = kb + t;
       int cj = 0;
       float wj = 0.f;
