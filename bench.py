@@ -830,8 +830,8 @@ def main():
     barrier(world)
     launches = katz.katz_launch_count() - l0
     prof = {t: katz.katz_profile_read(t) for t in
-            ("spmm_f32", "spmm_f64", "cheb_step", "cheb_step_bf16g", "ff_residual",
-             "block_solve_f32", "gemm_f32", "tc_gemm", "tc_gemm_tf32x3")}
+            ("spmm_f32", "spmm_f64", "cheb_step", "cheb_step_bf16g", "ff_residual", "ff_out",
+             "block_solve_f32", "gemm_f32", "tc_gemm", "tc_gemm_tf32x3", "topk")}
     katz.katz_profile_enable(False)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps

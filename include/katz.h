@@ -535,8 +535,13 @@ int katz_fault_inject_alloc(int64_t after);
 /* Start (on != 0) or stop timing tagged kernel launches with CUDA events on
  * their launching stream; every call resets the totals.  Tags:
  * "spmm_f32" / "spmm_f64" (CSR products, Eq. 3 and the couplings),
- * "block_solve_f32" / "block_solve_f64" (M11 blocks), "gemm_f32" /
- * "gemm_f64" (dense Schur / preconditioner products). */
+ * "cheb_step" / "cheb_step_bf16g" (fused Chebyshev steps on the large M11
+ * blocks), "ff_residual" (refinement-residual passes), "ff_out" (the
+ * float-float solution to the output), "block_solve_f32" /
+ * "block_solve_f64" (M11 blocks), "gemm_f32" / "gemm_f64" (dense Schur /
+ * preconditioner products), "tc_gemm" / "tc_gemm_tf32x3" (tcgen05
+ * products; the latter counts FLOPs instead of bytes), "topk" (link
+ * prediction). */
 int katz_profile_enable(int32_t on);
 
 /* Totals for one tag since the last katz_profile_enable: launches, summed

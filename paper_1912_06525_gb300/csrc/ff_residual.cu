@@ -735,6 +735,7 @@ void ff_out(const float* Kh, const float* Kl, const float* D, int64_t ld, const 
   const bool rows = out_dt == KATZ_F32 && ld % 4 == 0 && ldk % 4 == 0 &&
                     ((reinterpret_cast<uintptr_t>(Kh) | reinterpret_cast<uintptr_t>(Kl) |
                       reinterpret_cast<uintptr_t>(D) | reinterpret_cast<uintptr_t>(out)) % 16) == 0;
+  prof_begin(s);
   if (rows) {
     const unsigned blocks =
         (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 8), int64_t(num_sms()) * 16));
@@ -744,6 +745,10 @@ void ff_out(const float* Kh, const float* Kl, const float* D, int64_t ld, const 
     ff_out_kernel<<<flat(n * b), 256, 0, s>>>(Kh, Kl, D, ld, map, n, b, out, out_dt, ldk);
   }
   KATZ_CHECK_LAUNCH();
+  // algorithmic: Kh, Kl (and D) read once, K written once
+  if (profiling())
+    prof_end("ff_out", double(n) * b * (4.0 * (D ? 3 : 2) + (out_dt == KATZ_F64 ? 8.0 : 4.0)),
+             s);
 }
 
 }  // namespace katz

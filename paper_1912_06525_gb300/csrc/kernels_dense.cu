@@ -301,6 +301,8 @@ __device__ __forceinline__ bool better(T sa, int ia, T sb, int ib) {
 
 constexpr int kTopMax = 64;
 constexpr int kTopUnroll = 16;  // rows loaded ahead per warp (2 KB in flight per warp)
+constexpr int kTopFilterDeg = 512;  // neighbour lists filtered bit by bit up to this length
+constexpr int kTopSmemK = 32;       // lists of up to this length kept in shared memory
 
 // Pass 1: CTA = (row slice, 8 tiles of 32 query columns); warp w takes
 // column tile blockIdx.y * 8 + w and lane c its column tile * 32 + c, so
@@ -309,15 +311,35 @@ constexpr int kTopUnroll = 16;  // rows loaded ahead per warp (2 KB in flight pe
 // of the slice, kTopUnroll rows ahead.  Each (warp, column) keeps a sorted
 // top-k list in local memory (scores in K's own type, so the order is
 // decided in that precision) with its k-th entry held in registers; a
-// candidate is tested against q's neighbours (binary search in the sorted
-// CSR row; skipped when mask_nbrs is false) only when it beats the k-th
-// entry.  Lists go to the scratch as [column][slice][k].
-template <class VT>
+// candidate is tested against q's neighbours (skipped when mask_nbrs is
+// false) only when it beats the k-th entry: first against a 512-bit filter
+// of the neighbour ids in shared memory (bit id mod 512; all bits set for
+// more than kTopFilterDeg neighbours), then, where the bit is set, by binary
+// search in the sorted CSR row.  SL: the lists live in shared memory (entry
+// t of the thread's list at [t][threadIdx.x], k <= kTopSmemK), else in local
+// memory.  Lists go to the scratch as [column][slice][k].
+template <class VT, bool SL>
 __global__ void __launch_bounds__(256) topk_partial_kernel(Csr W, const VT* K, int64_t ldk,
                                                            int64_t n, const int32_t* q, int b,
                                                            int k, int64_t rows_per_slice,
                                                            bool mask_nbrs, int32_t* pid,
                                                            double* psc) {
+  // filter word w of the thread's column at nbm[w][threadIdx.x] (each
+  // thread writes and reads its own column only)
+  __shared__ uint32_t nbm[16][256];
+  extern __shared__ __align__(16) unsigned char tk_smem[];
+  VT* s_sc = reinterpret_cast<VT*>(tk_smem);
+  int* s_id = reinterpret_cast<int*>(tk_smem + sizeof(VT) * 256 * size_t(k));
+  VT l_sc[SL ? 1 : kTopMax];
+  int l_id[SL ? 1 : kTopMax];
+  auto LS = [&](int t) -> VT& {
+    if constexpr (SL) return s_sc[t * 256 + threadIdx.x];
+    else return l_sc[t];
+  };
+  auto LI = [&](int t) -> int& {
+    if constexpr (SL) return s_id[t * 256 + threadIdx.x];
+    else return l_id[t];
+  };
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = (blockIdx.y * 8 + warp) * 32 + lane;
   const bool cv = j < b;
@@ -326,8 +348,16 @@ __global__ void __launch_bounds__(256) topk_partial_kernel(Csr W, const VT* K, i
   const int64_t qq = cv ? q[j] : -1;
   const int64_t nb0 = cv && mask_nbrs ? W.rowptr[qq] : 0;
   const int64_t nb1 = cv && mask_nbrs ? W.rowptr[qq + 1] : 0;
-  VT ls[kTopMax];
-  int li[kTopMax];
+  {
+    const uint32_t fill = nb1 - nb0 > kTopFilterDeg ? 0xffffffffu : 0u;
+#pragma unroll
+    for (int w = 0; w < 16; ++w) nbm[w][threadIdx.x] = fill;
+    if (fill == 0u)
+      for (int64_t e = nb0; e < nb1; ++e) {
+        const int c = W.col[e];
+        nbm[(c >> 5) & 15][threadIdx.x] |= 1u << (c & 31);
+      }
+  }
   int cnt = 0;
   VT thv = VT(0);  // k-th entry once the list is full
   int thi = 0;
@@ -345,31 +375,33 @@ __global__ void __launch_bounds__(256) topk_partial_kernel(Csr W, const VT* K, i
         if (i >= r1 || i == qq) continue;
         const VT v = vals[u];
         if (cnt == k && !better(v, (int)i, thv, thi)) continue;
-        int64_t lo = nb0, hi = nb1;
-        while (lo < hi) {
-          const int64_t mid = (lo + hi) >> 1;
-          if (W.col[mid] < i) lo = mid + 1; else hi = mid;
+        if ((nbm[(i >> 5) & 15][threadIdx.x] >> (i & 31)) & 1u) {
+          int64_t lo = nb0, hi = nb1;
+          while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (W.col[mid] < i) lo = mid + 1; else hi = mid;
+          }
+          if (lo < nb1 && W.col[lo] == i) continue;
         }
-        if (lo < nb1 && W.col[lo] == i) continue;
         int p = cnt < k ? cnt++ : k - 1;
-        while (p > 0 && better(v, (int)i, ls[p - 1], li[p - 1])) {
-          ls[p] = ls[p - 1];
-          li[p] = li[p - 1];
+        while (p > 0 && better(v, (int)i, LS(p - 1), LI(p - 1))) {
+          LS(p) = LS(p - 1);
+          LI(p) = LI(p - 1);
           --p;
         }
-        ls[p] = v;
-        li[p] = (int)i;
+        LS(p) = v;
+        LI(p) = (int)i;
         if (cnt == k) {
-          thv = ls[k - 1];
-          thi = li[k - 1];
+          thv = LS(k - 1);
+          thi = LI(k - 1);
         }
       }
     }
     const int lists = gridDim.x;
     const int64_t out = (int64_t(j) * lists + blockIdx.x) * k;
     for (int t = 0; t < k; ++t) {
-      pid[out + t] = t < cnt ? li[t] : -1;
-      psc[out + t] = t < cnt ? double(ls[t]) : 0.0;
+      pid[out + t] = t < cnt ? LI(t) : -1;
+      psc[out + t] = t < cnt ? double(LS(t)) : 0.0;
     }
   }
 }
@@ -412,12 +444,26 @@ void topk_columns_ws(const Csr& W, const VT* K, int64_t ldk, int64_t n, const in
   // the scratch is sized
   const int64_t rows_per = ceil_div(n, int64_t(slices) * 8);
   dim3 grid((unsigned)(slices * 8), (unsigned)ceil_div(b, 256));
-  topk_partial_kernel<VT><<<grid, 256, 0, s>>>(W, K, ldk, n, q, b, k, rows_per, mask_nbrs, ws_id,
-                                               ws_sc);
+  prof_begin(s);
+  if (k <= kTopSmemK) {
+    const size_t smem = size_t(256) * k * (sizeof(VT) + sizeof(int));
+    KATZ_CUDA(cudaFuncSetAttribute(topk_partial_kernel<VT, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    topk_partial_kernel<VT, true><<<grid, 256, smem, s>>>(W, K, ldk, n, q, b, k, rows_per,
+                                                          mask_nbrs, ws_id, ws_sc);
+  } else {
+    topk_partial_kernel<VT, false><<<grid, 256, 0, s>>>(W, K, ldk, n, q, b, k, rows_per,
+                                                        mask_nbrs, ws_id, ws_sc);
+  }
   KATZ_CHECK_LAUNCH();
   topk_merge_kernel<<<(unsigned)ceil_div(b, 64), 64, 0, s>>>(ws_id, ws_sc, slices * 8, k, b, ids,
                                                              scores);
   KATZ_CHECK_LAUNCH();
+  // algorithmic: K read once, the lists written and read once, the result
+  if (profiling())
+    prof_end("topk",
+             double(n) * b * sizeof(VT) + 2.0 * 12.0 * double(slices) * 8 * b * k + 12.0 * b * k,
+             s);
 }
 template void topk_columns_ws<float>(const Csr&, const float*, int64_t, int64_t, const int32_t*,
                                      int, int, int32_t*, double*, int32_t*, double*, int,
