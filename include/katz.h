@@ -71,9 +71,9 @@ extern "C" {
                                  (FP32 iterates, b > 128; each warp fetches the next row's
                                  indices and this row's own operands during this row's
                                  gathers), the register kernel elsewhere */
-#define KATZ_GATHER_CHUNKED 4 /* the register kernel for the Chebyshev steps with each CTA
-                                 taking a contiguous run of rows (the tuned run length, else
-                                 64 rows), the register kernel elsewhere */
+#define KATZ_GATHER_CHUNKED 4 /* the register kernels of the Chebyshev steps and of the
+                                 refinement residual with each CTA taking a contiguous run of
+                                 rows (the tuned run lengths, else 64 rows) */
 
 /* Gathers of the Chebyshev steps on the large M11 blocks (KATZ_PREC_MIXED
  * and F32 paths).  F32: FP32 iterates and FP32 gathers.  The other modes
@@ -362,7 +362,7 @@ int katz_apply_M(const katz_index* idx, const void* X, void* Y, int32_t b,
  * operator it also chooses between the register and the pipelined (TMA
  * bulk-copy) Chebyshev step, and on the full operators between the two
  * kernels of the first and of the later refinement-residual passes.
- * out (10 ints): out[0] = chosen column tile (0 = default), out[1] = CTAs
+ * out (11 ints): out[0] = chosen column tile (0 = default), out[1] = CTAs
  * per SM, out[2] = 1 if the pipelined Chebyshev step was chosen, out[3] /
  * out[4] = 1 if the pipelined kernel was chosen for the first / later
  * residual passes of LRC queries, out[5] / out[6] = CTAs per SM of the
@@ -372,7 +372,8 @@ int katz_apply_M(const katz_index* idx, const void* X, void* Y, int32_t b,
  * next row's indices and this row's own operands fetched during this
  * row's gathers) was chosen, out[9] = rows per CTA of the Chebyshev step
  * when each CTA takes a contiguous run of rows (0: its warps stride over
- * all rows); ms[0] = best
+ * all rows), out[10] = rows per CTA of the refinement-residual passes in
+ * the same sense; ms[0] = best
  * time, ms[1] = time of the default shape (per product, FP32 vectors). */
 int katz_autotune(katz_index* idx, int32_t b, int32_t* out, double* ms, void* stream);
 

@@ -591,6 +591,7 @@ int katz_autotune(katz_index* idx, int32_t b, int32_t* out, double* ms, void* st
     out[7] = r.cheb_depth;
     out[8] = r.cheb_rowpipe ? 1 : 0;
     out[9] = r.cheb_chunk;
+    out[10] = r.res_chunk;
     ms[0] = r.ms_best;
     ms[1] = r.ms_default;
     return KATZ_OK;

@@ -134,20 +134,40 @@ SpmmCfg tune_part(GraphPart& g, int b, Workspace& ws, cudaStream_t s, double* be
     KATZ_CUDA(cudaMemsetAsync(Z, 0, sizeof(float) * rows * ld, s));
     HeavyRows hv;
     const HeavyRows* hvp = heavy_rows(g, ld, ws, hv);
+    double* rr = ws.get<double>("tune.rr", size_t(ld));
+    // residual: the first pass (float-float sums) and a later one (R -= M D
+    // with the column norms) share the launch shape; both are timed
+    auto fused_ms = [&](const SpmmCfg& c) {
+      if (kind == Fused::cheb)
+        return time_launches(
+            [&] { cheb_step(g.view(), 0.01, 0.1, 1.0, X, X, X, Y, ld, b, s, &c); }, s, reps);
+      return time_launches(
+                 [&] { ffr_update(g.view(), 0.01, X, Y, Z, true, ld, b, nullptr, &c, s, hvp); }, s,
+                 reps) +
+             time_launches(
+                 [&] { ffr_update(g.view(), 0.01, X, Y, Z, false, ld, b, rr, &c, s, hvp); }, s,
+                 reps);
+    };
     double bestf = 0;
     for (int cps : {8, 16, 32, 64, 128}) {
       SpmmCfg c = best;
       c.fused_cps = cps;
-      const double ms =
-          kind == Fused::cheb
-              ? time_launches(
-                    [&] { cheb_step(g.view(), 0.01, 0.1, 1.0, X, X, X, Y, ld, b, s, &c); }, s, reps)
-              : time_launches(
-                    [&] { ffr_update(g.view(), 0.01, X, Y, Z, true, ld, b, nullptr, &c, s, hvp); },
-                    s, reps);
+      const double ms = fused_ms(c);
       if (best.fused_cps == 0 || ms < bestf) {
         bestf = ms;
         best.fused_cps = cps;
+      }
+    }
+    if (kind == Fused::residual) {
+      // contiguous row runs per CTA
+      for (int rc : {32, 64, 128, 256}) {
+        SpmmCfg c = best;
+        c.row_chunk = rc;
+        const double ms = fused_ms(c);
+        if (ms < bestf) {
+          bestf = ms;
+          best.row_chunk = rc;
+        }
       }
     }
     if (kind == Fused::cheb) {
@@ -185,6 +205,7 @@ SpmmCfg tune_part(GraphPart& g, int b, Workspace& ws, cudaStream_t s, double* be
       }
     }
     ws.release("tune.Z");
+    ws.release("tune.rr");
   }
   if (kind != Fused::none && pipe_eligible(g.ps, ld) && (unit || g.csr.vdt != KATZ_F64)) {
     float* Z = ws.get<float>("tune.Z", size_t(rows) * ld);
@@ -215,6 +236,7 @@ TuneResult autotune(katz_index& idx, int b, cudaStream_t s) {
     r.res_first_pipe = cp.pipe_first;
     r.res_pipe = cp.pipe;
     r.res_cps = cp.fused_cps;
+    r.res_chunk = cp.row_chunk;
     if (idx.W11L.csr.nrows > 0) {
       const SpmmCfg cc = tune_part(idx.W11L, b, idx.ws, s, &b2, &d2, Fused::cheb, idx.unit_weights);
       r.cheb_pipe = cc.pipe;
@@ -225,6 +247,7 @@ TuneResult autotune(katz_index& idx, int b, cudaStream_t s) {
     }
   } else {
     r.res_cps = c.fused_cps;
+    r.res_chunk = c.row_chunk;
   }
   // release the tuning scratch
   idx.ws.release("tune.X");

@@ -300,8 +300,9 @@ __device__ __forceinline__ FF ff_plus(FF a, FF b) {
   return fast_two_sum(t.hi, t.lo + a.lo + b.lo);
 }
 
-// Warp per row (grid-stride), VPT float4 column groups per lane per tile of
-// 128 * VPT columns; rows longer than kHeavyRowNnz are left to the split
+// Warp per row, VPT float4 column groups per lane per tile of 128 * VPT
+// columns (the warps stride over all rows, or with chunk > 0 CTA c takes the
+// rows [c, c + 1) * chunk, its warps interleaved); rows longer than kHeavyRowNnz are left to the split
 // kernels when skip_heavy.  Column sums of Rh^2: FP32 over at most 64 rows
 // per lane, then FP64 in shared memory per warp, then one atomic per column
 // and CTA.
@@ -309,7 +310,7 @@ template <int WT, int VPT, bool INIT>
 __global__ void __launch_bounds__(256) ffr_rows_kernel(Csr A, const float* __restrict__ X,
                                                        float* Rh, float* Rl, int64_t ld, float beh,
                                                        float bel, double* rr, int b,
-                                                       bool skip_heavy) {
+                                                       bool skip_heavy, int64_t chunk) {
   constexpr int TILE = 128 * VPT;
   __shared__ double red[8][TILE];
   const int t = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -327,7 +328,13 @@ __global__ void __launch_bounds__(256) ffr_rows_kernel(Csr A, const float* __res
     for (int w = 0; w < 4; ++w) sq[v][w] = 0.f;
   int nsq = 0;
   __syncthreads();
-  for (int64_t i = warp; i < A.nrows; i += nwarps) {
+  int64_t i0 = warp, i1 = A.nrows, is = nwarps;
+  if (chunk > 0) {
+    i0 = int64_t(blockIdx.x) * chunk + wib;
+    i1 = min(A.nrows, int64_t(blockIdx.x + 1) * chunk);
+    is = blockDim.x >> 5;
+  }
+  for (int64_t i = i0; i < i1; i += is) {
     const int64_t k0 = A.rowptr[i], k1 = A.rowptr[i + 1];
     if (skip_heavy && k1 - k0 > kHeavyRowNnz) continue;
     FF acc[VPT][4];
@@ -350,14 +357,14 @@ __global__ void __launch_bounds__(256) ffr_rows_kernel(Csr A, const float* __res
   if (rr) column_atomics<VPT>(red, tile0, b, rr);
 }
 
-// Warp per row (grid-stride) on 256-column tiles, 8 consecutive columns
+// Warp per row (either row schedule of ffr_rows_kernel) on 256-column tiles, 8 consecutive columns
 // per lane moved by 32-byte accesses and summed with packed f32x2
 // instructions; otherwise as ffr_rows_kernel (same sums, same epilogue).
 template <int WT, bool INIT>
 __global__ void __launch_bounds__(256) ffr_rows8_kernel(Csr A, const float* __restrict__ X,
                                                         float* Rh, float* Rl, int64_t ld,
                                                         float beh, float bel, double* rr, int b,
-                                                        bool skip_heavy) {
+                                                        bool skip_heavy, int64_t chunk) {
   constexpr int TILE = 256;
   __shared__ double red[8][TILE];
   const int t = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -372,7 +379,13 @@ __global__ void __launch_bounds__(256) ffr_rows8_kernel(Csr A, const float* __re
   for (int w = 0; w < 8; ++w) sq[w] = 0.f;
   int nsq = 0;
   __syncthreads();
-  for (int64_t i = warp; i < A.nrows; i += nwarps) {
+  int64_t i0 = warp, i1 = A.nrows, is = nwarps;
+  if (chunk > 0) {
+    i0 = int64_t(blockIdx.x) * chunk + wib;
+    i1 = min(A.nrows, int64_t(blockIdx.x + 1) * chunk);
+    is = blockDim.x >> 5;
+  }
+  for (int64_t i = i0; i < i1; i += is) {
     const int64_t k0 = A.rowptr[i], k1 = A.rowptr[i + 1];
     if (skip_heavy && k1 - k0 > kHeavyRowNnz) continue;
     uint64_t hi[4], lo[4];
@@ -645,8 +658,12 @@ void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl,
   const int cps = cfg && cfg->fused_cps > 0     ? cfg->fused_cps
                   : cfg && cfg->ctas_per_sm > 0 ? cfg->ctas_per_sm
                                                 : 8;
-  const int64_t ctas = std::min<int64_t>(ceil_div(A.nrows, 8),
-                                         std::max<int64_t>(1, int64_t(num_sms()) * cps / tiles));
+  const int64_t chunk = cfg && cfg->row_chunk > 0 ? cfg->row_chunk : 0;
+  const int64_t ctas = chunk > 0 ? ceil_div(A.nrows, chunk)
+                                 : std::min<int64_t>(ceil_div(A.nrows, 8),
+                                                     std::max<int64_t>(1, int64_t(num_sms()) *
+                                                                              cps / tiles));
+  KATZ_REQUIRE(ctas < (int64_t(1) << 31), KATZ_EINVAL, "ffr_update: row chunk too small");
   const dim3 grid((unsigned)std::max<int64_t>(1, ctas), (unsigned)tiles);
   const bool split = hv && hv->nseg > 0;
   KATZ_REQUIRE(!split || (hv->scratch && reinterpret_cast<uintptr_t>(hv->scratch) % 16 == 0),
@@ -658,9 +675,9 @@ void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl,
                       reinterpret_cast<uintptr_t>(Rl)) % 32) == 0;
   prof_begin(s);
 #define KATZ_FFR(WT, V, I) \
-  ffr_rows_kernel<WT, V, I><<<grid, 256, 0, s>>>(A, X, Rh, Rl, ld, beh, bel, rr, b, split)
+  ffr_rows_kernel<WT, V, I><<<grid, 256, 0, s>>>(A, X, Rh, Rl, ld, beh, bel, rr, b, split, chunk)
 #define KATZ_FFR8(WT, I) \
-  ffr_rows8_kernel<WT, I><<<grid, 256, 0, s>>>(A, X, Rh, Rl, ld, beh, bel, rr, b, split)
+  ffr_rows8_kernel<WT, I><<<grid, 256, 0, s>>>(A, X, Rh, Rl, ld, beh, bel, rr, b, split, chunk)
 #define KATZ_FFR_W(WT)                                                     \
   if (wide) {                                                              \
     if (init) KATZ_FFR8(WT, true); else KATZ_FFR8(WT, false);              \

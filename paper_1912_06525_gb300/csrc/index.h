@@ -309,6 +309,7 @@ struct TuneResult {
   int cheb_depth = 0;
   bool cheb_rowpipe = false;  // the row-pipelined Chebyshev kernel was faster
   int cheb_chunk = 0;         // rows per CTA of the Chebyshev step (0: strided)
+  int res_chunk = 0;          // rows per CTA of the residual passes (0: strided)
   int cheb_cps = 0, res_cps = 0;  // CTAs per SM of the fused kernels
   double ms_best = 0, ms_default = 0;
 };

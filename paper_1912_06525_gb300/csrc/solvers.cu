@@ -871,6 +871,16 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   const int32_t* pos = use_lrc ? idx.iperm.p : nullptr;
   const GraphPart& G = use_lrc ? idx.Wp : idx.W;
   const SpmmCfg* gcfg = G.cfg(b);
+  SpmmCfg gforced;  // the query asked for one row schedule of the residual passes
+  if (idx.gather_pref == KATZ_GATHER_CHUNKED) {
+    gforced = gcfg ? *gcfg : SpmmCfg{};
+    if (gforced.row_chunk == 0) gforced.row_chunk = 64;
+    gcfg = &gforced;
+  } else if (idx.gather_pref == KATZ_GATHER_REGISTER && gcfg && gcfg->row_chunk > 0) {
+    gforced = *gcfg;
+    gforced.row_chunk = 0;
+    gcfg = &gforced;
+  }
   const bool pipe_ok = pipe_eligible(G.ps, ld) && (idx.unit_weights || G.csr.vdt != KATZ_F64);
   Workspace& ws = idx.ws;
   iters.assign(b, 0);

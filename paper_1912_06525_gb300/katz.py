@@ -423,14 +423,14 @@ def katz_gemm_tf32x3(A, B, C_out, K=None, alpha=1.0, beta=0.0, stream=None):
 
 def katz_autotune(index, b: int, stream=None) -> dict:
     """Tune the SpMM launch shape for width b; returns the choice and times."""
-    out = np.zeros(10, dtype=np.int32)
+    out = np.zeros(11, dtype=np.int32)
     ms = np.zeros(2, dtype=np.float64)
     _check(lib().katz_autotune(index.handle, b, out.ctypes.data, ms.ctypes.data, _stream(stream)))
     return {"col_tile": int(out[0]), "ctas_per_sm": int(out[1]), "cheb_pipe": bool(out[2]),
             "residual_first_pipe": bool(out[3]), "residual_pipe": bool(out[4]),
             "cheb_ctas_per_sm": int(out[5]), "residual_ctas_per_sm": int(out[6]),
             "cheb_gather_depth": int(out[7]), "cheb_row_pipeline": bool(out[8]),
-            "cheb_row_chunk": int(out[9]),
+            "cheb_row_chunk": int(out[9]), "residual_row_chunk": int(out[10]),
             "ms_best": float(ms[0]), "ms_default": float(ms[1])}
 
 

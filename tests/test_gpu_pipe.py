@@ -108,6 +108,7 @@ def test_autotune_reports_kernel_choice():
     assert isinstance(res["cheb_pipe"], bool)
     assert res["cheb_ctas_per_sm"] in (8, 16, 32, 64, 128)
     assert res["cheb_row_chunk"] in (0, 32, 64, 128, 256)
+    assert res["residual_row_chunk"] in (0, 32, 64, 128, 256)
     assert res["residual_ctas_per_sm"] in (8, 16, 32, 64, 128)
     q = synth.queries(g.n, 256, seed=5)
     K = torch.zeros((g.n, 256), dtype=torch.float32, device="cuda")
