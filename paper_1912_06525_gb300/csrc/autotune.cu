@@ -245,6 +245,11 @@ TuneResult autotune(katz_index& idx, int b, cudaStream_t s) {
       r.cheb_rowpipe = cc.row_pipeline;
       r.cheb_chunk = cc.row_chunk;
     }
+    // the couplings (W12 rows stream the M11 block, W21 rows are hubs)
+    if (idx.n1 > 0 && idx.n2 > 0) {
+      tune_part(idx.W12, b, idx.ws, s, &b2, &d2);
+      tune_part(idx.W21, b, idx.ws, s, &b2, &d2);
+    }
   } else {
     r.res_cps = c.fused_cps;
     r.res_chunk = c.row_chunk;
