@@ -361,41 +361,51 @@ __global__ void __launch_bounds__(256) topk_partial_kernel(Csr W, const VT* K, i
   int cnt = 0;
   VT thv = VT(0);  // k-th entry once the list is full
   int thi = 0;
+  // every score below the gate loses: -infinity until the list is full,
+  // then the k-th entry's score (equal scores are decided by the id)
+  VT gate = -VT(INFINITY);
+  // a candidate that passed the gate: q itself and q's neighbours are
+  // skipped, the rest is inserted in order if it beats the k-th entry
+  auto offer = [&](VT v, int64_t i) {
+    if (i == qq) return;
+    if (cnt == k && !better(v, (int)i, thv, thi)) return;
+    if ((nbm[(i >> 5) & 15][threadIdx.x] >> (i & 31)) & 1u) {
+      int64_t lo = nb0, hi = nb1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (W.col[mid] < i) lo = mid + 1; else hi = mid;
+      }
+      if (lo < nb1 && W.col[lo] == i) return;
+    }
+    int p = cnt < k ? cnt++ : k - 1;
+    while (p > 0 && better(v, (int)i, LS(p - 1), LI(p - 1))) {
+      LS(p) = LS(p - 1);
+      LI(p) = LI(p - 1);
+      --p;
+    }
+    LS(p) = v;
+    LI(p) = (int)i;
+    if (cnt == k) {
+      thv = LS(k - 1);
+      thi = LI(k - 1);
+      gate = thv;
+    }
+  };
   if (cv) {
-    for (int64_t i0 = r0; i0 < r1; i0 += kTopUnroll) {
+    // whole batches of kTopUnroll rows: all loads issued first, then one
+    // comparison per row against the gate on the common path
+    int64_t i0 = r0;
+    for (; i0 + kTopUnroll <= r1; i0 += kTopUnroll) {
       VT vals[kTopUnroll];
 #pragma unroll
-      for (int u = 0; u < kTopUnroll; ++u) {
-        const int64_t i = i0 + u;
-        vals[u] = i < r1 ? K[i * ldk + j] : VT(0);
-      }
+      for (int u = 0; u < kTopUnroll; ++u) vals[u] = K[(i0 + u) * ldk + j];
 #pragma unroll
-      for (int u = 0; u < kTopUnroll; ++u) {
-        const int64_t i = i0 + u;
-        if (i >= r1 || i == qq) continue;
-        const VT v = vals[u];
-        if (cnt == k && !better(v, (int)i, thv, thi)) continue;
-        if ((nbm[(i >> 5) & 15][threadIdx.x] >> (i & 31)) & 1u) {
-          int64_t lo = nb0, hi = nb1;
-          while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (W.col[mid] < i) lo = mid + 1; else hi = mid;
-          }
-          if (lo < nb1 && W.col[lo] == i) continue;
-        }
-        int p = cnt < k ? cnt++ : k - 1;
-        while (p > 0 && better(v, (int)i, LS(p - 1), LI(p - 1))) {
-          LS(p) = LS(p - 1);
-          LI(p) = LI(p - 1);
-          --p;
-        }
-        LS(p) = v;
-        LI(p) = (int)i;
-        if (cnt == k) {
-          thv = LS(k - 1);
-          thi = LI(k - 1);
-        }
-      }
+      for (int u = 0; u < kTopUnroll; ++u)
+        if (vals[u] >= gate) offer(vals[u], i0 + u);
+    }
+    for (; i0 < r1; ++i0) {
+      const VT v = K[i0 * ldk + j];
+      if (v >= gate) offer(v, i0);
     }
     const int lists = gridDim.x;
     const int64_t out = (int64_t(j) * lists + blockIdx.x) * k;
@@ -406,31 +416,52 @@ __global__ void __launch_bounds__(256) topk_partial_kernel(Csr W, const VT* K, i
   }
 }
 
-// Pass 2: one thread per column merges its sorted lists (k-way selection).
-__global__ void topk_merge_kernel(const int32_t* pid, const double* psc, int lists, int k, int b,
-                                  int32_t* ids, double* scores) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+// Pass 2: one warp per column merges its sorted lists (k-way selection):
+// lane l holds the heads of lists l, l + 32, ... (lists <= 128), the best
+// head of the warp is found by a shuffle reduction and advanced.  Ids are
+// unique across a column's lists (the row slices are disjoint), so the
+// (score, id) order picks one winner per step.
+__global__ void topk_merge_warp_kernel(const int32_t* pid, const double* psc, int lists, int k,
+                                       int b, int32_t* ids, double* scores) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   if (j >= b) return;
-  const int64_t base = int64_t(j) * lists * k;
-  int head[kTopMax * 2];  // enough for up to 128 lists (16 slices x 8 warps)
-  for (int l = 0; l < lists; ++l) head[l] = 0;
+  const int64_t base = j * lists * k;
+  int head[4] = {0, 0, 0, 0};
   for (int t = 0; t < k; ++t) {
-    double best = 0.0;
-    int bid = -1, bl = -1;
-    for (int l = 0; l < lists; ++l) {
-      if (head[l] >= k) continue;
-      const int id = pid[base + int64_t(l) * k + head[l]];
+    double bs = 0.0;
+    int bid = -1, bm = -1;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int l = lane + 32 * m;
+      if (l >= lists || head[m] >= k) continue;
+      const int64_t o = base + int64_t(l) * k + head[m];
+      const int id = pid[o];
       if (id < 0) continue;
-      const double sc = psc[base + int64_t(l) * k + head[l]];
-      if (bl < 0 || better(sc, id, best, bid)) { best = sc; bid = id; bl = l; }
+      const double sc = psc[o];
+      if (bm < 0 || better(sc, id, bs, bid)) { bs = sc; bid = id; bm = m; }
     }
-    if (bl >= 0) {
-      ids[int64_t(j) * k + t] = bid;
-      scores[int64_t(j) * k + t] = best;
-      head[bl]++;
-    } else {
-      ids[int64_t(j) * k + t] = -1;
-      scores[int64_t(j) * k + t] = 0.0;
+    int wl = bm >= 0 ? lane : -1;  // lane holding the warp's best head so far
+    for (int off = 16; off > 0; off >>= 1) {
+      const double os = __shfl_xor_sync(0xffffffffu, bs, off);
+      const int oid = __shfl_xor_sync(0xffffffffu, bid, off);
+      const int ol = __shfl_xor_sync(0xffffffffu, wl, off);
+      if (ol >= 0 && (wl < 0 || better(os, oid, bs, bid))) { bs = os; bid = oid; wl = ol; }
+    }
+    if (wl < 0) {
+      if (lane == 0) {
+        ids[j * k + t] = -1;
+        scores[j * k + t] = 0.0;
+      }
+      continue;
+    }
+    if (lane == wl) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) head[m] += m == bm ? 1 : 0;
+    }
+    if (lane == 0) {
+      ids[j * k + t] = bid;
+      scores[j * k + t] = bs;
     }
   }
 }
@@ -456,8 +487,8 @@ void topk_columns_ws(const Csr& W, const VT* K, int64_t ldk, int64_t n, const in
                                                         mask_nbrs, ws_id, ws_sc);
   }
   KATZ_CHECK_LAUNCH();
-  topk_merge_kernel<<<(unsigned)ceil_div(b, 64), 64, 0, s>>>(ws_id, ws_sc, slices * 8, k, b, ids,
-                                                             scores);
+  topk_merge_warp_kernel<<<(unsigned)ceil_div(int64_t(b) * 32, 256), 256, 0, s>>>(
+      ws_id, ws_sc, slices * 8, k, b, ids, scores);
   KATZ_CHECK_LAUNCH();
   // algorithmic: K read once, the lists written and read once, the result
   if (profiling())
