@@ -113,6 +113,10 @@ struct katz_index {
   // kernel preference of the query being run (KATZ_GATHER_*), set per query
   int gather_pref = KATZ_GATHER_AUTO;
   int cheb_pref = KATZ_CHEB_AUTO;  // per query, like gather_pref
+  // LRC corrections (refinement passes after the first) take Y1 = M11^{-1}R1
+  // from one Chebyshev step (it only feeds their Schur right-hand side)
+  // until a correction made that way leaves a column above its threshold
+  bool loose_y1 = true;
   katz::Partition part;
   katz::DBuf<int32_t> perm, iperm;
   katz::GraphPart Wp;    // W in index order (full), for FP64 residuals

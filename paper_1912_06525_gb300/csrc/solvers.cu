@@ -674,7 +674,7 @@ bool coupling_gemm_pays(const katz_index& idx, int64_t ld, double tol) {
 template <class VT>
 int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double tol_s,
               double tol_l, int max_iter, std::vector<int32_t>* iters, cudaStream_t s,
-              const VT* K2_0 = nullptr, const int32_t* q_rhs = nullptr) {
+              const VT* K2_0 = nullptr, const int32_t* q_rhs = nullptr, double tol_y1 = 0.0) {
   const int64_t n1 = idx.n1, n2 = idx.n2;
   const VT* R1 = Rin;
   const VT* R2 = Rin + n1 * ld;
@@ -688,7 +688,7 @@ int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double t
                       !idx.seg_blocked;
   if (n1 > 0 && !from_z) {
     NvtxRange r("katz.m11_solve");
-    merge(m11_solve<VT>(idx, R1, Y1, b, ld, tol_l, max_iter, nullptr, s));
+    merge(m11_solve<VT>(idx, R1, Y1, b, ld, tol_y1 > 0 ? tol_y1 : tol_l, max_iter, nullptr, s));
   }
   if (n2 > 0) {
     NvtxRange r("katz.schur_pcg");
@@ -761,9 +761,10 @@ template <class VT>
 static int inner_solve(katz_index& idx, bool use_lrc, const VT* Rin, VT* D, int b, int64_t ld,
                        const double* thr2_in, double tol_rel, int max_iter,
                        std::vector<int32_t>* iters, cudaStream_t s, const VT* K2_0 = nullptr,
-                       const int32_t* q_rhs = nullptr) {
+                       const int32_t* q_rhs = nullptr, double tol_y1 = 0.0) {
   if (use_lrc)
-    return lrc_solve<VT>(idx, Rin, D, b, ld, tol_rel, tol_rel, max_iter, iters, s, K2_0, q_rhs);
+    return lrc_solve<VT>(idx, Rin, D, b, ld, tol_rel, tol_rel, max_iter, iters, s, K2_0, q_rhs,
+                         tol_y1);
   // shares the scratch of the large-block M11 solve (never live at once)
   return cg_solve<VT>(idx.W, idx.beta, Rin, ld, idx.n, b, D, thr2_in, max_iter, idx.ws, "L",
                       iters, s);
@@ -946,6 +947,7 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   double ms_res = 0;
   int refine = 0;
   bool pending = false;  // D holds a correction not yet added to K
+  bool loose_y1_used = false;  // the last correction took Y1 from one Chebyshev step
   bool warm_checked = false;
   int64_t warm_fallbacks = 0;  // columns whose guess was scaled to zero
   double warm_gamma_mean = 0;
@@ -1015,6 +1017,10 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
       KATZ_CHECK_LAUNCH();
       ++refine;
       const int open = read_int(nopen, s);
+      // a correction with the one-step Y1 that left columns open: later
+      // corrections (of this and later queries) solve for Y1 in full
+      if (open > 0 && loose_y1_used) idx.loose_y1 = false;
+      loose_y1_used = false;
       KATZ_REQUIRE(read_int(perr, s) == 0, KATZ_ECUDA,
                    "pipelined gather kernel: a wait on its shared-memory ring timed out");
       ms_res += std::chrono::duration<double, std::milli>(clk::now() - r0).count();
@@ -1033,8 +1039,11 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
         tol_step = std::max(tol_step, tau);
       }
       if (pending) ff_add(Kh, Kl, D, n * ld, s);  // D is about to be overwritten
+      // Y1 of a correction feeds only its Schur right-hand side; where the
+      // index has not seen that fail, it is the first Chebyshev iterate
+      loose_y1_used = use_lrc && idx.loose_y1 && idx.n1 > idx.n1s && idx.lam11 > 0 && idx.n2 > 0;
       const int st = inner_solve<float>(idx, use_lrc, Rh, D, b, ld, thr2_in, tol_step, max_iter,
-                                        &iters, s);
+                                        &iters, s, nullptr, nullptr, loose_y1_used ? 1.0 : 0.0);
       if (st == KATZ_ENOTSPD) { pending = false; status = st; break; }
       pending = true;
     }
