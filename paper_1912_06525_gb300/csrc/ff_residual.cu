@@ -579,11 +579,11 @@ __global__ void ffr_add_rhs_kernel(Csr W, const int32_t* q, const int32_t* pos, 
 }
 
 __global__ void ff_add_kernel(float* __restrict__ Kh, float* __restrict__ Kl,
-                              const float* __restrict__ D, int64_t total) {
+                              const float* __restrict__ D, int64_t total, bool kl_zero) {
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
        e += int64_t(gridDim.x) * blockDim.x) {
     const FF t = two_sum(Kh[e], D[e]);
-    const FF u = fast_two_sum(t.hi, t.lo + Kl[e]);
+    const FF u = fast_two_sum(t.hi, kl_zero ? t.lo : t.lo + Kl[e]);
     Kh[e] = u.hi;
     Kl[e] = u.lo;
   }
@@ -600,11 +600,12 @@ __global__ void ff_out_kernel(const float* __restrict__ Kh, const float* __restr
     const int64_t r = map ? map[i] : i;
     const int64_t o = r * ld + c;
     const float d = D ? D[o] : 0.f;
+    const float kl = Kl ? Kl[o] : 0.f;
     if (out_dt == KATZ_F64) {
-      static_cast<double*>(out)[i * ldk + c] = (double(Kh[o]) + double(d)) + double(Kl[o]);
+      static_cast<double*>(out)[i * ldk + c] = (double(Kh[o]) + double(d)) + double(kl);
     } else {
       const FF t = two_sum(Kh[o], d);
-      static_cast<float*>(out)[i * ldk + c] = t.hi + (t.lo + Kl[o]);
+      static_cast<float*>(out)[i * ldk + c] = t.hi + (t.lo + kl);
     }
   }
 }
@@ -622,7 +623,7 @@ __global__ void ff_out_rows_kernel(const float* __restrict__ Kh, const float* __
     for (int c = lane * 4; c < b; c += 128) {
       const int64_t o = r * ld + c;
       const float4 h = __ldg(reinterpret_cast<const float4*>(Kh + o));
-      const float4 l = __ldg(reinterpret_cast<const float4*>(Kl + o));
+      const float4 l = Kl ? __ldg(reinterpret_cast<const float4*>(Kl + o)) : make_float4(0, 0, 0, 0);
       const float4 d = D ? __ldg(reinterpret_cast<const float4*>(D + o)) : make_float4(0, 0, 0, 0);
       const FF t0 = two_sum(h.x, d.x), t1 = two_sum(h.y, d.y), t2 = two_sum(h.z, d.z),
                t3 = two_sum(h.w, d.w);
@@ -740,9 +741,9 @@ void ffr_add_rhs(const Csr& W, const int32_t* q, const int32_t* pos, int b, doub
   KATZ_CHECK_LAUNCH();
 }
 
-void ff_add(float* Kh, float* Kl, const float* D, int64_t total, cudaStream_t s) {
+void ff_add(float* Kh, float* Kl, const float* D, int64_t total, cudaStream_t s, bool kl_zero) {
   if (total <= 0) return;
-  ff_add_kernel<<<flat(total), 256, 0, s>>>(Kh, Kl, D, total);
+  ff_add_kernel<<<flat(total), 256, 0, s>>>(Kh, Kl, D, total, kl_zero);
   KATZ_CHECK_LAUNCH();
 }
 
@@ -762,9 +763,10 @@ void ff_out(const float* Kh, const float* Kl, const float* D, int64_t ld, const 
     ff_out_kernel<<<flat(n * b), 256, 0, s>>>(Kh, Kl, D, ld, map, n, b, out, out_dt, ldk);
   }
   KATZ_CHECK_LAUNCH();
-  // algorithmic: Kh, Kl (and D) read once, K written once
+  // algorithmic: Kh (Kl, D) read once, K written once
   if (profiling())
-    prof_end("ff_out", double(n) * b * (4.0 * (D ? 3 : 2) + (out_dt == KATZ_F64 ? 8.0 : 4.0)),
+    prof_end("ff_out",
+             double(n) * b * (4.0 * (1 + (Kl ? 1 : 0) + (D ? 1 : 0)) + (out_dt == KATZ_F64 ? 8.0 : 4.0)),
              s);
 }
 

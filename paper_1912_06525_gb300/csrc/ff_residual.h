@@ -28,8 +28,10 @@ void ffr_update(const Csr& A, double beta, const float* X, float* Rh, float* Rl,
                 int64_t ld, int b, double* rr, const SpmmCfg* cfg, cudaStream_t s,
                 const HeavyRows* hv = nullptr);
 
-// (Kh, Kl) += D elementwise (TwoSum), total = rows * ld.
-void ff_add(float* Kh, float* Kl, const float* D, int64_t total, cudaStream_t s);
+// (Kh, Kl) += D elementwise (TwoSum), total = rows * ld; kl_zero: Kl is
+// taken as zero (not read) and written.
+void ff_add(float* Kh, float* Kl, const float* D, int64_t total, cudaStream_t s,
+            bool kl_zero = false);
 
 // (Rh, Rl)[pos(i), j] += beta W[q_j, i] for the stored entries of the query
 // rows (the sparse right-hand side); rr (optional) is adjusted by the change
@@ -38,8 +40,8 @@ void ff_add(float* Kh, float* Kl, const float* D, int64_t total, cudaStream_t s)
 void ffr_add_rhs(const Csr& W, const int32_t* q, const int32_t* pos, int b, double beta, float* Rh,
                  float* Rl, int64_t ld, double* rr, int64_t maxdeg, cudaStream_t s);
 
-// out[i, c] = Kh + Kl (+ D if non-null) at row map(i), column c, rounded
-// once to FP32 or FP64.
+// out[i, c] = Kh (+ Kl if non-null) (+ D if non-null) at row map(i), column
+// c, rounded once to FP32 or FP64.
 void ff_out(const float* Kh, const float* Kl, const float* D, int64_t ld, const int32_t* map,
             int64_t n, int b, void* out, int out_dt, int64_t ldk, cudaStream_t s);
 

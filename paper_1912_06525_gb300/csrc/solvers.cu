@@ -130,6 +130,31 @@ __global__ void __launch_bounds__(256) schur_rhs_from_z_kernel(
   }
 }
 
+// T[pos(u), c] += beta W[q_c, u] for the rows pos(u) < rows: the M11 part of
+// the query right-hand sides added to a dense block (no duplicate entries in
+// a CSR row, so one block per column writes distinct rows).
+template <int WT>
+__global__ void rhs_add_rows_kernel(Csr W, const int32_t* q, double beta, const int32_t* pos,
+                                    int64_t rows, float* T, int64_t ld) {
+  const int c = blockIdx.x;
+  const int64_t k0 = W.rowptr[q[c]], k1 = W.rowptr[q[c] + 1];
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    double w = 1.0;
+    if (WT == KATZ_F64) w = static_cast<const double*>(W.val)[k];
+    else if (WT == KATZ_F32) w = static_cast<const float*>(W.val)[k];
+    else if (WT == KATZ_BF16) w = __bfloat162float(static_cast<const __nv_bfloat16*>(W.val)[k]);
+    const int64_t r = pos[W.col[k]];
+    if (r < rows) T[r * ld + c] += float(beta * w);
+  }
+}
+
+// Whether the first LRC pass of a query takes its Schur right-hand side
+// from the stored Z (and then reads only the separator rows of its
+// right-hand side block).
+static bool first_rhs_from_z(const katz_index& idx) {
+  return idx.has_z && idx.n1 > 0 && idx.n2 > 0 && !idx.seg_blocked;
+}
+
 static void schur_rhs_from_z(const katz_index& idx, const int32_t* q, int b, const float* R2,
                              int64_t ld, float* F, cudaStream_t s) {
   const dim3 grid((unsigned)b, (unsigned)ceil_div(idx.n2, 256 * 8));
@@ -684,8 +709,7 @@ int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double t
   int status = KATZ_OK;
   auto merge = [&](int st) { if (st != KATZ_OK && status == KATZ_OK) status = st; };
   // Rin = beta W e_q (q_rhs given) and Z stored: F from the rows of Z, no Y1
-  const bool from_z = sizeof(VT) == 4 && q_rhs && idx.has_z && n1 > 0 && n2 > 0 &&
-                      !idx.seg_blocked;
+  const bool from_z = sizeof(VT) == 4 && q_rhs && first_rhs_from_z(idx);
   if (n1 > 0 && !from_z) {
     NvtxRange r("katz.m11_solve");
     merge(m11_solve<VT>(idx, R1, Y1, b, ld, tol_y1 > 0 ? tol_y1 : tol_l, max_iter, nullptr, s));
@@ -736,7 +760,22 @@ int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double t
       }
     }
     const VT* T1 = R1;
-    if (n2 > 0) {
+    if (from_z) {
+      // R1 is not read on this path: T1 = beta W12 K2 plus the sparse B1
+      if constexpr (sizeof(VT) == 4) {
+        spmm<VT>(idx.W12.view(), idx.W12.heavy.p, idx.W12.n_heavy, idx.beta, D2, ld, 0.0, nullptr,
+                 ld, Y1, ld, b, nullptr, 0, nullptr, s, idx.W12.cfg(b));
+        const Csr W = idx.W.view();
+        switch (W.vdt) {
+          case KATZ_UNIT: rhs_add_rows_kernel<KATZ_UNIT><<<b, 128, 0, s>>>(W, q_rhs, idx.beta, idx.iperm.p, n1, Y1, ld); break;
+          case KATZ_F64: rhs_add_rows_kernel<KATZ_F64><<<b, 128, 0, s>>>(W, q_rhs, idx.beta, idx.iperm.p, n1, Y1, ld); break;
+          case KATZ_F32: rhs_add_rows_kernel<KATZ_F32><<<b, 128, 0, s>>>(W, q_rhs, idx.beta, idx.iperm.p, n1, Y1, ld); break;
+          default: rhs_add_rows_kernel<KATZ_BF16><<<b, 128, 0, s>>>(W, q_rhs, idx.beta, idx.iperm.p, n1, Y1, ld); break;
+        }
+        KATZ_CHECK_LAUNCH();
+        T1 = Y1;
+      }
+    } else if (n2 > 0) {
       spmm<VT>(idx.W12.view(), idx.W12.heavy.p, idx.W12.n_heavy, idx.beta, D2, ld, 1.0, R1, ld, Y1,
                ld, b, nullptr, 0, nullptr, s, idx.W12.cfg(b));
       T1 = Y1;
@@ -909,7 +948,13 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
   float* D = ws.get<float>("q.D", size_t(n) * ld);
   float* Kh = ws.get<float>("q.Kh", size_t(n) * ld);
   float* Kl = ws.get<float>("q.Kl", size_t(n) * ld);
-  KATZ_CUDA(cudaMemsetAsync(Rh, 0, sizeof(float) * n * ld, s));
+  // the first LRC pass that forms its Schur right-hand side from Z reads
+  // only the separator rows of the right-hand side (the first residual pass
+  // then writes every row)
+  if (use_lrc && first_rhs_from_z(idx))
+    KATZ_CUDA(cudaMemsetAsync(Rh + idx.n1 * ld, 0, sizeof(float) * idx.n2 * ld, s));
+  else
+    KATZ_CUDA(cudaMemsetAsync(Rh, 0, sizeof(float) * n * ld, s));
   {
     NvtxRange nr("katz.rhs");
     build_rhs<float>(idx.W.view(), q, b, idx.beta, pos, Rh, ld, s);
@@ -941,7 +986,7 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
     status = inner_solve<float>(idx, use_lrc, Rh, Kh, b, ld, thr2_in, tol_rel, max_iter, &iters,
                                 s, K20, q);
   }
-  KATZ_CUDA(cudaMemsetAsync(Kl, 0, sizeof(float) * n * ld, s));
+  bool kl_zero = true;  // Kl (the low part of K) is zero and not yet written
   KATZ_CUDA(cudaStreamSynchronize(s));
   const auto t2 = clk::now();
   double ms_res = 0;
@@ -1038,7 +1083,10 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
           if (hr[c] > ht[c] && hr[c] > 0) tol_step = std::min(tol_step, 0.3 * std::sqrt(ht[c] / hr[c]));
         tol_step = std::max(tol_step, tau);
       }
-      if (pending) ff_add(Kh, Kl, D, n * ld, s);  // D is about to be overwritten
+      if (pending) {  // D is about to be overwritten
+        ff_add(Kh, Kl, D, n * ld, s, kl_zero);
+        kl_zero = false;
+      }
       // Y1 of a correction feeds only its Schur right-hand side; where the
       // index has not seen that fail, it is the first Chebyshev iterate
       loose_y1_used = use_lrc && idx.loose_y1 && idx.n1 > idx.n1s && idx.lam11 > 0 && idx.n2 > 0;
@@ -1052,7 +1100,8 @@ static int query_mixed_ff(katz_index& idx, bool use_lrc, const int32_t* q, const
     KATZ_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * b, cudaMemcpyDeviceToHost, s));
     KATZ_CUDA(cudaStreamSynchronize(s));
     for (int c = 0; c < b; ++c) relres[c] = hb[c] > 0 ? std::sqrt(hr[c] / hb[c]) : std::sqrt(hr[c]);
-    ff_out(Kh, Kl, pending ? D : nullptr, ld, pos, n, b, out.K, out.dtype, out.ldk, s);
+    ff_out(Kh, kl_zero ? nullptr : Kl, pending ? D : nullptr, ld, pos, n, b, out.K, out.dtype,
+           out.ldk, s);
     KATZ_CUDA(cudaStreamSynchronize(s));
   }
   const auto t3 = clk::now();
