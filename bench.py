@@ -32,11 +32,13 @@ UNIT = "queries/s"
 
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch
 # of the dominant kernel, keyed by the source hash of the kernel files it was
-# measured on (null once they change).  cheb_step: two launches captured on
-# the same graph recipe at n = 400,000, b = 323 (2.29 and 2.83 GB against
-# 1.59 and 2.11 GB algorithmic), their mean scaled by rows and columns to
-# n1 = 3,998,000, ld = 1,024 (x 31.2).
-NCU_TRAFFIC = {("cheb_step", "89b34e7979f857b4"): 80.0e9}
+# measured on (null once they change).  cheb_step: the five launches of one
+# query step captured on the same graph recipe at n = 400,000, b = 323
+# (12.23 GB of DRAM traffic against 9.48 GB algorithmic, 1.29x: two launches
+# without x_{k-1} at 1.15x, three with it at 1.16-1.49x), the ratio applied
+# to the full step's 59.3 GB algorithmic per launch (the same five-launch
+# mix at n = 4,000,000, b = 1,024).
+NCU_TRAFFIC = {("cheb_step", "4ee85f96c8132900"): 76.5e9}
 
 
 def parse():

@@ -710,16 +710,26 @@ int lrc_solve(katz_index& idx, const VT* Rin, VT* D, int b, int64_t ld, double t
   auto merge = [&](int st) { if (st != KATZ_OK && status == KATZ_OK) status = st; };
   // Rin = beta W e_q (q_rhs given) and Z stored: F from the rows of Z, no Y1
   const bool from_z = sizeof(VT) == 4 && q_rhs && first_rhs_from_z(idx);
-  if (n1 > 0 && !from_z) {
+  // a one-step Y1 on an M11 that is one large block is R1 / theta: folded
+  // into the coupling product below instead of being written out (not
+  // where the tensor-core back-substitution reads Y1)
+  const double tol_y = tol_y1 > 0 ? tol_y1 : tol_l;
+  const bool y1_scaled = sizeof(VT) == 4 && !from_z && n1 > 0 && n2 > 0 && idx.n1s == 0 &&
+                         idx.lam11 > 0 && !idx.has_h && cheb_steps(idx, tol_y) == 1;
+  const double theta = 1.0 - 0.5 * idx.beta * (idx.lam11 + idx.lam11_min);
+  if (n1 > 0 && !from_z && !y1_scaled) {
     NvtxRange r("katz.m11_solve");
-    merge(m11_solve<VT>(idx, R1, Y1, b, ld, tol_y1 > 0 ? tol_y1 : tol_l, max_iter, nullptr, s));
+    merge(m11_solve<VT>(idx, R1, Y1, b, ld, tol_y, max_iter, nullptr, s));
   }
   if (n2 > 0) {
     NvtxRange r("katz.schur_pcg");
     VT* F = idx.ws.get<VT>("lrc.F", size_t(n2) * ld);
     if (from_z) {
       if constexpr (sizeof(VT) == 4) schur_rhs_from_z(idx, q_rhs, b, R2, ld, F, s);
-    } else if (n1 > 0)
+    } else if (y1_scaled)
+      spmm<VT>(idx.W21.view(), idx.W21.heavy.p, idx.W21.n_heavy, idx.beta / theta, R1, ld, 1.0, R2,
+               ld, F, ld, b, nullptr, 0, nullptr, s, idx.W21.cfg(b));
+    else if (n1 > 0)
       spmm<VT>(idx.W21.view(), idx.W21.heavy.p, idx.W21.n_heavy, idx.beta, Y1, ld, 1.0, R2, ld, F,
                ld, b, nullptr, 0, nullptr, s, idx.W21.cfg(b));
     else
