@@ -73,6 +73,68 @@ __global__ void __launch_bounds__(256) gemm_kernel(int64_t M, int64_t N, int64_t
   }
 }
 
+// FP32, neither operand transposed: 128 x 64 output tile per CTA, K step
+// 16, each of the 256 threads owning an 8 x 4 micro-tile (rows ty + 16 i,
+// columns tx + 16 j), so a K step costs 12 shared loads per 32 FMAs.  Every
+// output element sums its K products in the same order as gemm_kernel.
+__global__ void __launch_bounds__(256) sgemm_nn_kernel(int64_t M, int64_t N, int64_t K,
+                                                       float alpha, const float* __restrict__ A,
+                                                       int64_t lda, const float* __restrict__ B,
+                                                       int64_t ldb, float beta,
+                                                       float* __restrict__ C, int64_t ldc) {
+  __shared__ float As[16][128 + 4];
+  __shared__ float Bs[16][64 + 4];
+  const int64_t m0 = int64_t(blockIdx.y) * 128, n0 = int64_t(blockIdx.x) * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int64_t k0 = 0; k0 < K; k0 += 16) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int e = threadIdx.x + 256 * r;
+      const int mm = e >> 4, kk = e & 15;
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < M && gk < K) ? A[gm * lda + gk] : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int e = threadIdx.x + 256 * r;
+      const int kk = e >> 6, nn = e & 63;
+      const int64_t gn = n0 + nn, gk = k0 + kk;
+      Bs[kk][nn] = (gn < N && gk < K) ? B[gk * ldb + gn] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[8], bb[4];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      float* cp = C + gm * ldc + gn;
+      *cp = beta == 0.f ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*cp);
+    }
+  }
+}
+
 template <class VT>
 void gemm2(bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alpha, const VT* A,
            int64_t lda, const VT* B, int64_t ldb, double beta, VT* C, int64_t ldc, bool lower_only,
@@ -84,6 +146,17 @@ void gemm2(bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alp
 #define KATZ_G(TA, TB)                                                                   \
   gemm_kernel<VT, TA, TB><<<grid, 256, 0, s>>>(M, N, K, VT(alpha), A, lda, B, ldb, VT(beta), C, \
                                                ldc, lo)
+  if constexpr (sizeof(VT) == 4) {
+    if (!transA && !transB && !lower_only && M >= 128) {
+      const dim3 g2((unsigned)ceil_div(N, 64), (unsigned)ceil_div(M, 128));
+      sgemm_nn_kernel<<<g2, 256, 0, s>>>(M, N, K, float(alpha), A, lda, B, ldb, float(beta), C,
+                                         ldc);
+      KATZ_CHECK_LAUNCH();
+      if (profiling())
+        prof_end("gemm_f32", 4.0 * (double(M) * K + double(K) * N + double(M) * N), s);
+      return;
+    }
+  }
   if (!transA && !transB) KATZ_G(false, false);
   else if (transA && !transB) KATZ_G(true, false);
   else if (!transA && transB) KATZ_G(false, true);
