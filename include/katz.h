@@ -279,7 +279,10 @@ int katz_query_batch(const katz_index* idx, const int32_t* q, int32_t b,
                      double* rel_res_out, void* stream);
 
 /* Same contract, solved by plain multi-RHS conjugate gradients on M (the
- * comparison method of Sections 1 and 4), zero initial guess. */
+ * comparison method of Sections 1 and 4) from a zero initial guess, or,
+ * with opts->warm_start = 1 on an index with a trained warm-start network,
+ * from the network's whole-vector guess described at katz_query_opts.
+ * An index built without the LRC part serves this call alone. */
 int cg_query_batch(const katz_index* idx, const int32_t* q, int32_t b,
                    const katz_query_opts* opts, void* K_out, int32_t out_dtype,
                    int64_t ldk, katz_stats* stats, int32_t* iters_out,
@@ -435,8 +438,10 @@ typedef struct {
  * beta M11^{-1} W12 W_r otherwise; unit RMS per column).  Network: 32 ->
  * hidden (exact GELU) -> r, BF16 weights, FP32 accumulation and FP32
  * master weights, MSE loss, AdamW.  Afterwards katz_query_batch with
- * opts->warm_start = 1 starts the Schur PCG from K2 = W_r MLP(x_q); a column
- * whose warm residual is not below ||F|| starts from zero instead. */
+ * opts->warm_start = 1 starts the Schur PCG from K2 = W_r MLP(x_q) (a
+ * column whose warm residual is not below ||F|| starts from zero instead),
+ * and cg_query_batch with opts->warm_start = 1 starts CG on M from the
+ * guess's extension to the whole vector (see katz_query_opts). */
 int katz_warmstart_train(katz_index* idx, const int32_t* q_train, int32_t n_train,
                          const katz_train_opts* opts, katz_train_stats* stats, void* stream);
 

@@ -57,6 +57,19 @@ def test_complete_graph_closed_form(n):
     np.testing.assert_allclose(np.diag(K), kii, rtol=1e-11)
 
 
+def test_apply_M_written_out_on_a_weighted_path():
+    """M X = X - beta W X (Eq. 3) on the path 0 -(2)- 1 -(1/2)- 2 at
+    beta = 1/4, so M = [[1, -1/2, 0], [-1/2, 1, -1/8], [0, -1/8, 1]]; the
+    products below are worked out by hand (all exact in binary)."""
+    rowptr = np.array([0, 1, 3, 4])
+    col = np.array([1, 0, 2, 1])
+    val = np.array([2.0, 2.0, 0.5, 0.5])
+    W = O.adjacency(3, rowptr, col, val)
+    X = np.array([[1.0, 0.0], [2.0, 1.0], [4.0, -8.0]])
+    Y = O.apply_M(W, 0.25, X)
+    np.testing.assert_array_equal(Y, [[0.0, -0.5], [1.0, 2.0], [3.75, -8.125]])
+
+
 @pytest.mark.parametrize("n", [3, 8, 13])
 def test_cycle_spectral_form(n):
     """C_n is circulant: eigenvalues 2 cos(2 pi k / n), Fourier vectors."""

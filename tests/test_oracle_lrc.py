@@ -184,10 +184,51 @@ def test_pcg_fewer_iterations_with_more_rank():
 
 
 # ------------------------------------------------------------ warm-start MLP
-def test_gelu_exact_values():
-    from math import erf, sqrt
-    for x in [-3.0, -0.5, 0.0, 0.7, 2.5]:
-        assert O.gelu(np.array(x)) == pytest.approx(0.5 * x * (1 + erf(x / sqrt(2))), rel=1e-14, abs=1e-300)
+# Phi(1) and phi(1) of the standard normal distribution (printed tables;
+# phi(1) = exp(-1/2) / sqrt(2 pi)).
+PHI1 = 0.8413447460685429
+DPHI1 = 0.24197072451914337
+
+
+def test_gelu_against_normal_table_values():
+    """GELU(x) = x Phi(x): GELU(0) = 0, GELU(1) = Phi(1), GELU(-1) =
+    -(1 - Phi(1)), the odd part GELU(x) - GELU(-x) = x, GELU(x) -> x for
+    large x; its derivative Phi(x) + x phi(x) is 1/2 at 0 and
+    Phi(1) + phi(1) at 1."""
+    from oracle import katz_oracle
+    assert O.gelu(np.array(0.0)) == 0.0
+    assert O.gelu(np.array(1.0)) == pytest.approx(PHI1, rel=1e-15)
+    assert O.gelu(np.array(-1.0)) == pytest.approx(-(1.0 - PHI1), rel=1e-14)
+    x = np.array([-3.0, -0.5, 0.7, 2.5, 9.0])
+    np.testing.assert_allclose(O.gelu(x) - O.gelu(-x), x, rtol=1e-14)
+    assert O.gelu(np.array(12.0)) == pytest.approx(12.0, rel=1e-15)
+    assert katz_oracle._gelu_grad(np.array(0.0)) == pytest.approx(0.5, rel=1e-15)
+    assert katz_oracle._gelu_grad(np.array(1.0)) == pytest.approx(PHI1 + DPHI1, rel=1e-14)
+
+
+def test_mlp_forward_written_out():
+    """A 2 -> 2 -> 1 network by hand: with W1 = [[1, 0], [0, -1]], b1 = 0
+    and x = (1, 1) the hidden pre-activations are (1, -1), so the hidden
+    layer is (Phi(1), -(1 - Phi(1))); W2 = [[1, 2]], b2 = 1/2 gives
+    y = Phi(1) - 2 (1 - Phi(1)) + 1/2.  A second row x = (0, 0) gives
+    y = b2 (GELU(0) = 0)."""
+    X = np.array([[1.0, 1.0], [0.0, 0.0]])
+    W1 = np.array([[1.0, 0.0], [0.0, -1.0]])
+    b1 = np.zeros(2)
+    W2 = np.array([[1.0, 2.0]])
+    b2 = np.array([0.5])
+    Y, Hp, H = O.mlp_forward(X, W1, b1, W2, b2)
+    np.testing.assert_array_equal(Hp, [[1.0, -1.0], [0.0, 0.0]])
+    np.testing.assert_allclose(H[0], [PHI1, -(1.0 - PHI1)], rtol=1e-14)
+    assert Y.shape == (2, 1)
+    assert Y[0, 0] == pytest.approx(PHI1 - 2.0 * (1.0 - PHI1) + 0.5, rel=1e-14)
+    assert Y[1, 0] == 0.5
+    # loss of the target row t = y - 1 (error 1 on one row, 0 on the other)
+    # is mean(||e||^2) / 2 = 1/4, and dL/db2 = mean(e) = 1/2
+    T = Y - np.array([[1.0], [0.0]])
+    loss, (_, _, _, db2) = O.mlp_loss_grad(X, T, W1, b1, W2, b2)
+    assert loss == pytest.approx(0.25, rel=1e-14)
+    np.testing.assert_allclose(db2, [0.5], rtol=1e-14)
 
 
 def test_mlp_gradients_finite_differences():
