@@ -41,6 +41,17 @@ UNIT = "queries/s"
 NCU_TRAFFIC = {("cheb_step", "4ee85f96c8132900"): 76.5e9}
 
 
+def traffic_measured_on(args):
+    """The NCU_TRAFFIC figures hold for the run they were captured on: the
+    n = 4M graph's unit-weight pattern at the default damping, batch, rank,
+    gathers and method.  Other runs report traffic as null."""
+    return (not args.standin and not args.multi and args.workload == 3
+            and args.weights == "unit" and args.scale == 1.0 and args.batch == 0
+            and args.rank == 0 and args.c in (None, 0.9) and not args.paper_beta
+            and args.method == "lrc" and args.gather == "auto" and args.cheb == "auto"
+            and args.rhs_coupling == "auto")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -936,7 +947,8 @@ def main():
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "peak_source": f"{src} (hbm_gbs)",
-                "traffic": NCU_TRAFFIC.get((dom, kernel_hash())), "traffic_unit": "bytes per launch"}
+                "traffic": (NCU_TRAFFIC.get((dom, kernel_hash())) if traffic_measured_on(args)
+                            else None), "traffic_unit": "bytes per launch"}
     roof.update({"launches_per_step": p["launches"] / args.steps,
                  "alg_units_per_launch": p["bytes"] / max(1, p["launches"]),
                  "share_of_step": p["ms"] / (ms * args.steps)})

@@ -96,3 +96,23 @@ def test_all_cores_oracle_helper():
     assert bench.topk_agreement(g, Kd, qs, bad) == 2 / 3
     info = bench.host_cpu()
     assert info["nproc"] >= 1 and info["model"]
+
+
+def test_ncu_traffic_only_on_the_captured_workload(monkeypatch):
+    """The bench line's roofline traffic (ncu DRAM bytes per launch) is
+    given for the default n = 4M unit-weight run only; a variant such as
+    BF16 dyadic weights, another damping or a smaller batch reports null."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    def args_of(*argv):
+        monkeypatch.setattr(sys, "argv", ["bench.py", *argv])
+        return bench.parse()
+
+    assert bench.traffic_measured_on(args_of())
+    assert bench.traffic_measured_on(args_of("--steps", "20", "--warmup", "5", "--c", "0.9"))
+    for variant in (["--weights", "dyadic"], ["--c", "0.5"], ["--paper-beta"],
+                    ["--batch", "256"], ["--scale", "0.1"], ["--workload", "2"],
+                    ["--method", "cg"], ["--cheb", "bf16"], ["--standin", "gowalla"],
+                    ["--multi"], ["--rank", "64"]):
+        assert not bench.traffic_measured_on(args_of(*variant)), variant
