@@ -147,7 +147,14 @@ typedef struct {
   int32_t precision;   /* KATZ_PREC_* */
   int32_t max_iter;    /* cap on iterations of each inner CG / PCG solve (0 = 2000) */
   int32_t max_refine;  /* cap on FP64 refinement steps (0 = 12) */
-  int32_t rhs_width;   /* columns solved together (0 = all b at once) */
+  int32_t rhs_width;   /* columns solved together: the b queries are solved in chunks of
+                          rhs_width columns, one after another, each written to its own
+                          column range of K_out (0 = all b at once).  At most 1,024
+                          columns are solved together, so b > 1,024 needs
+                          1 <= rhs_width <= 1,024; negative -> KATZ_EINVAL.  With
+                          chunks, katz_stats holds the maxima of iters, refine_steps
+                          and max_rel_res over the chunks, the sums of ms[0..5], the
+                          column-weighted mean of ms[6] and the maximum of ms[7] */
   int32_t warm_start;  /* 1: start from the learned warm start (needs a trained network; mixed
                           precision): LRC starts its Schur PCG from K2 = W_r c_hat; CG on M
                           starts from the whole vector [M11^{-1} B1 + beta M11^{-1} W12 W_r
@@ -267,7 +274,8 @@ int katz_index_get_sigma(const katz_index* idx, double* sigma);
  * KATZ_PREC_MIXED the LRC solve runs in FP32 and FP64-class residuals of the
  * full system (float-float, ~2^-48 relative to their terms; FP64 for
  * FP64-valued graphs) drive iterative refinement until opts->tol is met.
- * q[b]: int32 node ids (host or device).  K_out: n x b node-major, ld = ldk,
+ * q[b]: int32 node ids (host or device); b <= 1,024 unless opts->rhs_width
+ * splits the batch into chunks of at most 1,024.  K_out: n x b node-major, ld = ldk,
  * element type out_dtype (KATZ_F32 or KATZ_F64), host or device.
  * stats may be NULL; iters_out[b] / rel_res_out[b] (host, may be NULL)
  * receive per-column iteration counts and the relative residuals

@@ -140,11 +140,56 @@ int do_query(const katz_index* cidx, bool lrc, const int32_t* q, int32_t b,
     } else {
       out.K = idx->ws.get<uint8_t>("api.K", es * size_t(idx->n) * ldk);
     }
+    KATZ_REQUIRE(opts->rhs_width >= 0, KATZ_EINVAL, "rhs_width must be >= 0");
+    const int32_t w = opts->rhs_width > 0 ? std::min(opts->rhs_width, b) : b;
+    KATZ_REQUIRE(w <= 1024, KATZ_EINVAL,
+                 "at most 1024 columns are solved together: b > 1024 needs rhs_width in [1, 1024]");
     std::vector<int32_t> it;
     std::vector<double> rr;
-    const int st = katz::run_queries(*idx, lrc, qd, qh.data(), b, *opts, out, stats, it, rr, s);
+    int st = KATZ_OK;
+    if (w == b) {
+      st = katz::run_queries(*idx, lrc, qd, qh.data(), b, *opts, out, stats, it, rr, s);
+    } else {
+      // Column chunks of w queries, one solve each, in order; the chunk's
+      // output is the column range [j0, j0 + bj) of K (node-major, so the
+      // base moves by j0 elements and the leading dimension stays ldk).
+      katz_stats acc{};
+      double gamma_sum = 0;
+      for (int32_t j0 = 0; j0 < b; j0 += w) {
+        const int32_t bj = std::min(w, b - j0);
+        katz::QueryOut oj = out;
+        oj.K = static_cast<uint8_t*>(out.K) + es * size_t(j0);
+        katz_stats sj{};
+        std::vector<int32_t> itj;
+        std::vector<double> rrj;
+        const int stj = katz::run_queries(*idx, lrc, qd + j0, qh.data() + j0, bj, *opts, oj,
+                                          stats ? &sj : nullptr, itj, rrj, s);
+        if (stj != KATZ_OK && stj != KATZ_ENOCONV) {
+          st = stj;
+          break;
+        }
+        if (stj == KATZ_ENOCONV) st = KATZ_ENOCONV;
+        it.insert(it.end(), itj.begin(), itj.end());
+        rr.insert(rr.end(), rrj.begin(), rrj.end());
+        if (stats) {
+          acc.iters = std::max(acc.iters, sj.iters);
+          acc.refine_steps = std::max(acc.refine_steps, sj.refine_steps);
+          acc.max_rel_res = std::max(acc.max_rel_res, sj.max_rel_res);
+          for (int k : {0, 1, 2, 3, 4, 5}) acc.ms[k] += sj.ms[k];
+          gamma_sum += sj.ms[6] * bj;
+          acc.ms[7] = std::max(acc.ms[7], sj.ms[7]);
+        }
+      }
+      if (stats) {
+        acc.ms[6] = gamma_sum / b;
+        *stats = acc;
+      }
+    }
     if (!dev && (st == KATZ_OK || st == KATZ_ENOCONV)) {
-      KATZ_CUDA(cudaMemcpyAsync(K_out, out.K, es * size_t(idx->n) * ldk, cudaMemcpyDeviceToHost, s));
+      // the b columns of each row only: the caller's entries between b and
+      // ldk stay as they were, as with a device K_out
+      KATZ_CUDA(cudaMemcpy2DAsync(K_out, es * size_t(ldk), out.K, es * size_t(ldk),
+                                  es * size_t(b), size_t(idx->n), cudaMemcpyDeviceToHost, s));
       KATZ_CUDA(cudaStreamSynchronize(s));
     }
     if (iters_out) std::memcpy(iters_out, it.data(), 4 * it.size());
